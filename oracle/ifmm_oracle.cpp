@@ -1,0 +1,1551 @@
+/*
+ * ifmm_oracle.cpp -- CPU oracle for the Inverse Fast Multipole Method
+ * (Ambikasaran & Darve, arXiv:1407.1572).
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the tests, the smoke check and the bench's CPU-baseline
+ * leg; never by the product library, with which it shares no code.
+ *
+ * Plain FP64, no BLAS: every linear-algebra step (matrix products, LU with partial pivoting,
+ * Householder QR with column pivoting, the pivoted Gram-Schmidt range finder) is written out
+ * below. The method follows the paper's order and notation:
+ *   - uniform 2^d tree (d = 2), lists N_i (neighbours incl. self) and I_i (interaction list),
+ *     Section 4.2, Table "table_cluster";
+ *   - FMM operators P2P, P2M, L2P, M2L (Table "table_FMM_operators") from Chebyshev
+ *     interpolation (Section 5), orthonormalised by a QR of the nested bases;
+ *   - the extended sparse system of particles x, multipoles y and locals z
+ *     (Eqs. "extended_sparsity", "extended_sparsity_reordered"; non-leaf particles are the
+ *     children's multipoles, Eq. "particles_multipoles");
+ *   - Algorithm 1 (elimination phase / upward pass) with the equations P2P(i,k) and
+ *     P2M(i,k) (Eqs. "equation_p2p", "equation_p2m"), fill-in classification per pair (p,q)
+ *     of neighbours of the eliminated box, compression of well-separated fill into the
+ *     box bases (Table "table_IFMM_operators");
+ *   - dense solve at level 1, then Algorithm 2 (back substitution / downward pass).
+ *
+ * Readings where the paper is silent (each is stated again where it is used):
+ *   R1 elimination order inside a level: colour-major, colour = (ix mod 3) + 3 (iy mod 3),
+ *      Morton order inside a colour (order = 0); or plain Morton order (order = 1).
+ *   R2 fill compression: the paper names a "tweaked ACA" at tolerance 1e-14 without details.
+ *      Here: the old basis W_q is kept; the stacked well-separated fill S_q of box q is
+ *      projected onto the complement of W_q and a column-pivoted QR (pivoted Gram-Schmidt)
+ *      of the remainder appends directions while the largest remaining column norm exceeds
+ *      eps * (largest column norm of S_q). One basis serves both L2P_qq and P2M_qq^T.
+ *   R3 orthonormalisation ("Chebyshev interpolation followed by SVD", Section 5): a
+ *      column-pivoted Householder QR of each leaf basis and of each stacked parent transfer,
+ *      with the R factors folded into M2L and the parent transfers; rank cut at 1e-13
+ *      relative to the largest column norm (only reached when a box holds fewer points than
+ *      p^2).
+ *   R4 the diagonal A_ii is a parameter (sqrt(N) for the 1/r workloads, the paper's unit
+ *      diagonal of Eq. "main_Solving_Equation" is diag = 1).
+ *   R5 the reference of the compression threshold (the paper's tolerance 1e-14 does not say
+ *      relative to what): tau_ref = 0 takes the fill itself (largest column norm of S_q),
+ *      tau_ref = 1 takes the scale of the matrix, s_A = largest column norm over the leaf
+ *      diagonal blocks P2P_ii.
+ */
+#include "ifmm_oracle.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------------------------------
+// dense matrices
+// ------------------------------------------------------------------------------------------
+struct Counter {
+    double flops = 0.0, bytes = 0.0, compressions = 0.0, overflows = 0.0, added = 0.0;
+    void add(const Counter& o) {
+        flops += o.flops; bytes += o.bytes; compressions += o.compressions;
+        overflows += o.overflows; added += o.added;
+    }
+};
+
+// Row-major dense block. An empty block (no storage) stands for a zero block.
+struct Mat {
+    int r = 0, c = 0;
+    std::vector<double> a;
+    Mat() = default;
+    Mat(int r_, int c_) : r(r_), c(c_), a((size_t)r_ * (size_t)c_, 0.0) {}
+    bool present() const { return !a.empty(); }
+    double& at(int i, int j) { return a[(size_t)i * c + j]; }
+    double at(int i, int j) const { return a[(size_t)i * c + j]; }
+    void clear() { r = c = 0; std::vector<double>().swap(a); }
+};
+
+// C = A B
+Mat mul(const Mat& A, const Mat& B, Counter& ct) {
+    Mat C(A.r, B.c);
+    for (int i = 0; i < A.r; ++i)
+        for (int k = 0; k < A.c; ++k) {
+            double s = A.at(i, k);
+            if (s == 0.0) continue;
+            const double* b = &B.a[(size_t)k * B.c];
+            double* cr = &C.a[(size_t)i * C.c];
+            for (int j = 0; j < B.c; ++j) cr[j] += s * b[j];
+        }
+    ct.flops += 2.0 * A.r * A.c * B.c;
+    return C;
+}
+
+// C = A^T B
+Mat mul_tn(const Mat& A, const Mat& B, Counter& ct) {
+    Mat C(A.c, B.c);
+    for (int k = 0; k < A.r; ++k)
+        for (int i = 0; i < A.c; ++i) {
+            double s = A.at(k, i);
+            if (s == 0.0) continue;
+            const double* b = &B.a[(size_t)k * B.c];
+            double* cr = &C.a[(size_t)i * C.c];
+            for (int j = 0; j < B.c; ++j) cr[j] += s * b[j];
+        }
+    ct.flops += 2.0 * A.r * A.c * B.c;
+    return C;
+}
+
+Mat transpose(const Mat& A) {
+    Mat T(A.c, A.r);
+    for (int i = 0; i < A.r; ++i)
+        for (int j = 0; j < A.c; ++j) T.at(j, i) = A.at(i, j);
+    return T;
+}
+
+// enlarge M to at least r x c with zeros (the "zero-padding" of the operators when a basis
+// grows); a missing block becomes an explicit zero block
+void pad_to(Mat& M, int r, int c) {
+    if (M.present() && M.r >= r && M.c >= c) return;
+    int nr = std::max(M.present() ? M.r : 0, r), nc = std::max(M.present() ? M.c : 0, c);
+    Mat N(nr, nc);
+    if (M.present())
+        for (int i = 0; i < M.r; ++i)
+            for (int j = 0; j < M.c; ++j) N.at(i, j) = M.at(i, j);
+    M = std::move(N);
+}
+
+// C[0:A.r, 0:A.c] += s * A  (C padded first)
+void add_into(Mat& C, const Mat& A, double s, Counter& ct) {
+    if (!A.present()) return;
+    pad_to(C, A.r, A.c);
+    for (int i = 0; i < A.r; ++i)
+        for (int j = 0; j < A.c; ++j) C.at(i, j) += s * A.at(i, j);
+    ct.flops += (double)A.r * A.c;
+}
+
+// LU with partial pivoting, ties to the lowest row index. Returns false on an exactly zero
+// pivot column.
+bool lu_factor(Mat& A, std::vector<int>& piv, Counter& ct) {
+    int n = A.r;
+    piv.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double best = std::fabs(A.at(k, k));
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(A.at(i, k)) > best) { best = std::fabs(A.at(i, k)); p = i; }
+        piv[k] = p;
+        if (best == 0.0 || !std::isfinite(best)) return false;
+        if (p != k)
+            for (int j = 0; j < n; ++j) std::swap(A.at(k, j), A.at(p, j));
+        double d = A.at(k, k);
+        for (int i = k + 1; i < n; ++i) {
+            double l = A.at(i, k) / d;
+            A.at(i, k) = l;
+            if (l == 0.0) continue;
+            for (int j = k + 1; j < n; ++j) A.at(i, j) -= l * A.at(k, j);
+        }
+    }
+    ct.flops += 2.0 / 3.0 * (double)n * n * n;
+    return true;
+}
+
+// B <- A^{-1} B using the factors of lu_factor
+void lu_solve(const Mat& LU, const std::vector<int>& piv, Mat& B, Counter& ct) {
+    int n = LU.r, m = B.c;
+    for (int k = 0; k < n; ++k)
+        if (piv[k] != k)
+            for (int j = 0; j < m; ++j) std::swap(B.at(k, j), B.at(piv[k], j));
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < i; ++k) {
+            double l = LU.at(i, k);
+            if (l == 0.0) continue;
+            for (int j = 0; j < m; ++j) B.at(i, j) -= l * B.at(k, j);
+        }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int k = i + 1; k < n; ++k) {
+            double u = LU.at(i, k);
+            if (u == 0.0) continue;
+            for (int j = 0; j < m; ++j) B.at(i, j) -= u * B.at(k, j);
+        }
+        double d = LU.at(i, i);
+        for (int j = 0; j < m; ++j) B.at(i, j) /= d;
+    }
+    ct.flops += 2.0 * (double)n * n * m;
+}
+
+double col_norm(const Mat& A, int j, int row0 = 0) {
+    double s = 0.0;
+    for (int i = row0; i < A.r; ++i) s += A.at(i, j) * A.at(i, j);
+    return std::sqrt(s);
+}
+
+// Householder QR with column pivoting: A (m x n) ~= Q (m x rank) * Rt (rank x n), Q with
+// orthonormal columns. Stops when the largest remaining column norm is <= tol * (largest
+// column norm of A) (reading R3).
+void cpqr(const Mat& A, double tol, Mat& Q, Mat& Rt, Counter& ct) {
+    int m = A.r, n = A.c;
+    Mat R = A;
+    std::vector<int> perm(n);
+    for (int j = 0; j < n; ++j) perm[j] = j;
+    std::vector<std::vector<double>> vs;
+    std::vector<double> betas;
+    double first = -1.0;
+    int kmax = std::min(m, n);
+    int rank = 0;
+    for (int k = 0; k < kmax; ++k) {
+        int jb = k;
+        double best = -1.0;
+        for (int j = k; j < n; ++j) {
+            double v = col_norm(R, j, k);
+            if (v > best) { best = v; jb = j; }
+        }
+        if (first < 0.0) first = best;
+        if (!(best > tol * first) || best == 0.0) break;
+        if (jb != k) {
+            for (int i = 0; i < m; ++i) std::swap(R.at(i, k), R.at(i, jb));
+            std::swap(perm[k], perm[jb]);
+        }
+        // reflector H = I - beta v v^T with H x = alpha e_1
+        std::vector<double> v(m - k);
+        for (int i = k; i < m; ++i) v[i - k] = R.at(i, k);
+        double nx = best;
+        double alpha = v[0] >= 0.0 ? -nx : nx;
+        v[0] -= alpha;
+        double vtv = 0.0;
+        for (double t : v) vtv += t * t;
+        double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        for (int j = k; j < n; ++j) {
+            double s = 0.0;
+            for (int i = k; i < m; ++i) s += v[i - k] * R.at(i, j);
+            s *= beta;
+            for (int i = k; i < m; ++i) R.at(i, j) -= s * v[i - k];
+        }
+        for (int i = k + 1; i < m; ++i) R.at(i, k) = 0.0;
+        ct.flops += 4.0 * (double)(m - k) * (n - k);
+        vs.push_back(std::move(v));
+        betas.push_back(beta);
+        ++rank;
+    }
+    // Q = H_0 H_1 ... H_{rank-1} [I; 0]
+    Q = Mat(m, rank);
+    for (int j = 0; j < rank; ++j) Q.at(j, j) = 1.0;
+    for (int k = rank - 1; k >= 0; --k) {
+        const std::vector<double>& v = vs[k];
+        for (int j = 0; j < rank; ++j) {
+            double s = 0.0;
+            for (int i = k; i < m; ++i) s += v[i - k] * Q.at(i, j);
+            s *= betas[k];
+            for (int i = k; i < m; ++i) Q.at(i, j) -= s * v[i - k];
+        }
+    }
+    Rt = Mat(rank, n);
+    for (int i = 0; i < rank; ++i)
+        for (int j = 0; j < n; ++j) Rt.at(i, perm[j]) = R.at(i, j);
+}
+
+// Reading R2: append to the orthonormal basis W (n x r) the directions of S (n x m) that W
+// misses, by a column-pivoted QR of (I - W W^T) S written as pivoted Gram-Schmidt. A column
+// is taken while its remaining norm exceeds eps * max_j ||S_j|| (or eps * ref when ref > 0,
+// reading R5); ties go to the lowest column index. The rank never exceeds min(n, cap).
+int augment_basis(Mat& W, const Mat& S, double eps, double ref, int cap, Counter& ct, bool& overflow) {
+    int n = S.r, m = S.c;
+    overflow = false;
+    if (n == 0 || m == 0) return 0;
+    int r = W.present() ? W.c : 0;
+    double smax = 0.0;
+    for (int j = 0; j < m; ++j) smax = std::max(smax, col_norm(S, j));
+    if (smax == 0.0) return 0;
+    double tau = eps * (ref > 0.0 ? ref : smax);
+    // R = (I - W W^T) S, applied twice
+    Mat R = S;
+    if (r > 0)
+        for (int pass = 0; pass < 2; ++pass) {
+            Mat T = mul_tn(W, R, ct);  // r x m
+            Mat WT = mul(W, T, ct);
+            for (size_t t = 0; t < R.a.size(); ++t) R.a[t] -= WT.a[t];
+        }
+    int limit = std::min(n, cap > 0 ? cap : n);
+    std::vector<std::vector<double>> U;
+    std::vector<double> norms(m);
+    for (;;) {
+        int jb = 0;
+        double best = -1.0;
+        for (int j = 0; j < m; ++j) {
+            norms[j] = col_norm(R, j);
+            if (norms[j] > best) { best = norms[j]; jb = j; }
+        }
+        ct.flops += 2.0 * n * m;
+        if (!(best > tau)) break;
+        if (r + (int)U.size() >= limit) {
+            if (limit < n) overflow = true;
+            break;
+        }
+        std::vector<double> u(n);
+        for (int i = 0; i < n; ++i) u[i] = R.at(i, jb) / best;
+        // re-orthogonalise against W and the directions already taken, twice
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j < r; ++j) {
+                double s = 0.0;
+                for (int i = 0; i < n; ++i) s += W.at(i, j) * u[i];
+                for (int i = 0; i < n; ++i) u[i] -= s * W.at(i, j);
+            }
+            for (const auto& w : U) {
+                double s = 0.0;
+                for (int i = 0; i < n; ++i) s += w[i] * u[i];
+                for (int i = 0; i < n; ++i) u[i] -= s * w[i];
+            }
+        }
+        double nu = 0.0;
+        for (double t : u) nu += t * t;
+        nu = std::sqrt(nu);
+        if (!(nu >= 0.5)) {
+            // the candidate lies in the span of the basis to working precision ("twice is
+            // enough": an independent direction keeps most of its norm); drop the column
+            for (int i = 0; i < n; ++i) R.at(i, jb) = 0.0;
+            continue;
+        }
+        for (double& t : u) t /= nu;
+        // remove the new direction from every remaining column
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += u[i] * R.at(i, j);
+            for (int i = 0; i < n; ++i) R.at(i, j) -= s * u[i];
+        }
+        ct.flops += 4.0 * n * m + 8.0 * n * (r + U.size());
+        U.push_back(std::move(u));
+    }
+    int add = (int)U.size();
+    if (add > 0) {
+        Mat Wn(n, r + add);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < r; ++j) Wn.at(i, j) = W.at(i, j);
+            for (int j = 0; j < add; ++j) Wn.at(i, r + j) = U[j][i];
+        }
+        W = std::move(Wn);
+    }
+    return add;
+}
+
+// ------------------------------------------------------------------------------------------
+// kernels, Chebyshev interpolation
+// ------------------------------------------------------------------------------------------
+double kernel_value(const oracle_params& p, double ax, double ay, double bx, double by) {
+    double dx = ax - bx, dy = ay - by;
+    double r = std::sqrt(dx * dx + dy * dy);
+    switch (p.kernel) {
+        case ORACLE_K_INV_R: return 1.0 / r;
+        case ORACLE_K_EXP: return std::exp(-r / p.kparam[0]);
+        case ORACLE_K_POLY: return (1.0 + ax * bx) * (1.0 + ay * by);
+        default: return 0.0;
+    }
+}
+
+// first-kind Chebyshev nodes on [-1, 1]: t_m = cos((2m+1) pi / (2p)), m = 0..p-1
+void cheb_nodes(int p, double* t) {
+    for (int m = 0; m < p; ++m) t[m] = std::cos((2.0 * m + 1.0) * kPi / (2.0 * p));
+}
+
+// Lagrange basis l_m(x) = prod_{j != m} (x - t_j) / (t_m - t_j)
+void lagrange(int p, const double* t, double x, double* out) {
+    for (int m = 0; m < p; ++m) {
+        double v = 1.0;
+        for (int j = 0; j < p; ++j)
+            if (j != m) v *= (x - t[j]) / (t[m] - t[j]);
+        out[m] = v;
+    }
+}
+
+inline int d49(int dx, int dy) { return (dx + 3) + 7 * (dy + 3); }
+inline int d9(int dx, int dy) { return (dx + 1) + 3 * (dy + 1); }
+
+uint64_t morton(uint32_t ix, uint32_t iy) {
+    uint64_t m = 0;
+    for (int b = 0; b < 32; ++b) {
+        m |= (uint64_t)((ix >> b) & 1u) << (2 * b);
+        m |= (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
+    }
+    return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// state
+// ------------------------------------------------------------------------------------------
+struct OpsLevel {              // operators after orthonormalisation, level k
+    int k = 0, side = 0;
+    std::vector<int> rank;     // r_i
+    std::vector<Mat> W;        // leaf: n_i x r_i; non-leaf: (sum_c r_c) x r_i, children in Morton order
+    std::vector<Mat> Rt;       // r_i x p^2, the factor folded into M2L
+    std::vector<Mat> M2L;      // [box*49 + d49], interaction-list pairs only, r_i x r_j
+};
+
+enum { ROW_P2P = 0, ROW_M2L = 1 };  // active equation of a box: P2P(i,k) before, M2L after
+enum { COL_X = 0, COL_Y = 1 };      // active unknown of a box: x before, y after
+
+struct Panel { int box; int kind; Mat blk; };
+struct BoxFactor {
+    int n = 0, r = 0;
+    Mat LU;
+    std::vector<int> piv;
+    std::vector<Panel> C;  // active rows of the neighbours at pivot column x_e
+    std::vector<Panel> B;  // pivot row P2P_e at the active columns of the neighbours
+};
+
+struct ElimLevel {
+    int k = 0, side = 0, nb = 0;
+    std::vector<int> n, r, E;
+    std::vector<int> xoff;     // non-leaf: 5 offsets per box of the children's y inside x_i
+    std::vector<Mat> W;        // L2P_ii; P2M_ii = W^T
+    std::vector<Mat> P2P, M2P, P2L, M2L;  // [box*49 + d49]
+    std::vector<int> order;
+    std::vector<BoxFactor> fac;
+};
+
+struct Handle {
+    oracle_params prm{};
+    int64_t N = 0;
+    int depth = 0, p = 0, r0 = 0;
+    std::vector<double> px, py;         // tree order
+    std::vector<int64_t> perm;          // tree position -> caller index
+    std::vector<int64_t> leaf_start;    // per leaf (grid index)
+    std::vector<int> leaf_count;
+    std::vector<OpsLevel> ops;          // by level, valid for k >= 2
+    std::vector<Mat> leafP2P;           // [leaf*9 + d9]
+    bool factored = false;
+    std::vector<ElimLevel> el;          // by level
+    Mat rootLU;
+    std::vector<int> rootPiv, rootOff;  // offsets of the level-2 boxes in the root system
+    Counter ct;
+    int max_rank = 0;
+    double eliminations = 0.0, factor_seconds = 0.0;
+    double scale_A = 0.0;   // largest column norm over the leaf diagonal blocks
+};
+
+int side_of(int k) { return 1 << k; }
+double box_h(const Handle& h, int k) { return h.prm.box[2] / (double)side_of(k); }
+
+// Chebyshev nodes of box (ix, iy) at level k, index m = mx + p*my
+void box_nodes(const Handle& h, int k, int ix, int iy, std::vector<double>& nx, std::vector<double>& ny) {
+    int p = h.p;
+    std::vector<double> t(p);
+    cheb_nodes(p, t.data());
+    double hh = box_h(h, k);
+    double lx = h.prm.box[0] + ix * hh, ly = h.prm.box[1] + iy * hh;
+    nx.resize(p * p); ny.resize(p * p);
+    for (int my = 0; my < p; ++my)
+        for (int mx = 0; mx < p; ++mx) {
+            nx[mx + p * my] = lx + 0.5 * (t[mx] + 1.0) * hh;
+            ny[mx + p * my] = ly + 0.5 * (t[my] + 1.0) * hh;
+        }
+}
+
+// S_m(x, y) for box (ix, iy) at level k: tensor Lagrange basis, out[p^2]
+void box_basis(const Handle& h, int k, int ix, int iy, double x, double y, double* out) {
+    int p = h.p;
+    std::vector<double> t(p), lx(p), ly(p);
+    cheb_nodes(p, t.data());
+    double hh = box_h(h, k);
+    double ux = 2.0 * (x - (h.prm.box[0] + ix * hh)) / hh - 1.0;
+    double uy = 2.0 * (y - (h.prm.box[1] + iy * hh)) / hh - 1.0;
+    lagrange(p, t.data(), ux, lx.data());
+    lagrange(p, t.data(), uy, ly.data());
+    for (int my = 0; my < p; ++my)
+        for (int mx = 0; mx < p; ++mx) out[mx + p * my] = lx[mx] * ly[my];
+}
+
+int cheb_dist(int ax, int ay, int bx, int by) { return std::max(std::abs(ax - bx), std::abs(ay - by)); }
+
+// interaction list at level k >= 1: Chebyshev distance >= 2 and parents are neighbours
+bool in_interaction_list(int ax, int ay, int bx, int by) {
+    return cheb_dist(ax, ay, bx, by) >= 2 && cheb_dist(ax >> 1, ay >> 1, bx >> 1, by >> 1) <= 1;
+}
+
+int colour_of(int ix, int iy) { return (ix % 3) + 3 * (iy % 3); }
+
+std::vector<int> elimination_order(int k, int order_kind) {
+    int side = side_of(k);
+    std::vector<std::pair<uint64_t, int>> keys;
+    for (int iy = 0; iy < side; ++iy)
+        for (int ix = 0; ix < side; ++ix) {
+            uint64_t key = morton(ix, iy);
+            if (order_kind == 0) key |= (uint64_t)colour_of(ix, iy) << 60;
+            keys.push_back({key, ix + side * iy});
+        }
+    std::sort(keys.begin(), keys.end());
+    std::vector<int> out;
+    for (auto& kv : keys) out.push_back(kv.second);
+    return out;
+}
+
+// ------------------------------------------------------------------------------------------
+// build: tree, operators, orthonormalisation
+// ------------------------------------------------------------------------------------------
+bool build(Handle& h, const double* pts) {
+    const oracle_params& P = h.prm;
+    int kap = h.depth, side = side_of(kap);
+    int64_t N = h.N;
+    std::vector<std::pair<uint64_t, int64_t>> keys(N);
+    std::vector<int> lix(N), liy(N);
+    for (int64_t a = 0; a < N; ++a) {
+        double x = pts[2 * a], y = pts[2 * a + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) return false;
+        double ux = (x - P.box[0]) / P.box[2], uy = (y - P.box[1]) / P.box[2];
+        if (ux < 0.0 || ux > 1.0 || uy < 0.0 || uy > 1.0) return false;
+        int ix = std::min((int)std::floor(ux * side), side - 1);
+        int iy = std::min((int)std::floor(uy * side), side - 1);
+        keys[a] = {morton(ix, iy), a};
+    }
+    std::sort(keys.begin(), keys.end());
+    h.perm.resize(N); h.px.resize(N); h.py.resize(N);
+    h.leaf_start.assign(side * side, 0);
+    h.leaf_count.assign(side * side, 0);
+    for (int64_t t = 0; t < N; ++t) {
+        int64_t a = keys[t].second;
+        h.perm[t] = a;
+        h.px[t] = pts[2 * a]; h.py[t] = pts[2 * a + 1];
+    }
+    for (int64_t t = N - 1; t >= 0; --t) {
+        double ux = (h.px[t] - P.box[0]) / P.box[2], uy = (h.py[t] - P.box[1]) / P.box[2];
+        int ix = std::min((int)std::floor(ux * side), side - 1);
+        int iy = std::min((int)std::floor(uy * side), side - 1);
+        int g = ix + side * iy;
+        h.leaf_start[g] = t;
+        h.leaf_count[g]++;
+    }
+    int p = h.p, r0 = h.r0;
+    const double rank_tol = 1e-13;
+    h.ops.assign(kap + 1, OpsLevel());
+    Counter ct;
+    // leaf bases V_i[a, m] = S_m(x_a), orthonormalised
+    {
+        OpsLevel& L = h.ops[kap];
+        L.k = kap; L.side = side;
+        L.rank.assign(side * side, 0); L.W.resize(side * side); L.Rt.resize(side * side);
+        for (int iy = 0; iy < side; ++iy)
+            for (int ix = 0; ix < side; ++ix) {
+                int g = ix + side * iy, n = h.leaf_count[g];
+                Mat V(n, r0);
+                for (int a = 0; a < n; ++a) {
+                    int64_t t = h.leaf_start[g] + a;
+                    box_basis(h, kap, ix, iy, h.px[t], h.py[t], &V.a[(size_t)a * r0]);
+                }
+                cpqr(V, rank_tol, L.W[g], L.Rt[g], ct);
+                L.rank[g] = L.W[g].c;
+            }
+    }
+    // transfer T_c[m', m] = S^parent_m(child node m'), child c = a + 2b
+    std::vector<Mat> T(4, Mat(r0, r0));
+    {
+        std::vector<double> t(p), lx(p), ly(p);
+        cheb_nodes(p, t.data());
+        for (int c = 0; c < 4; ++c) {
+            int a = c & 1, b = c >> 1;
+            for (int my = 0; my < p; ++my)
+                for (int mx = 0; mx < p; ++mx) {
+                    double ux = 0.5 * (t[mx] - 1.0) + a, uy = 0.5 * (t[my] - 1.0) + b;
+                    lagrange(p, t.data(), ux, lx.data());
+                    lagrange(p, t.data(), uy, ly.data());
+                    for (int ny = 0; ny < p; ++ny)
+                        for (int nx = 0; nx < p; ++nx) T[c].at(mx + p * my, nx + p * ny) = lx[nx] * ly[ny];
+                }
+        }
+    }
+    for (int k = kap - 1; k >= 2; --k) {
+        OpsLevel& L = h.ops[k];
+        const OpsLevel& Cl = h.ops[k + 1];
+        int s = side_of(k);
+        L.k = k; L.side = s;
+        L.rank.assign(s * s, 0); L.W.resize(s * s); L.Rt.resize(s * s);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int rows = 0;
+                std::vector<Mat> parts;
+                for (int c = 0; c < 4; ++c) {
+                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
+                    parts.push_back(mul(Cl.Rt[cg], T[c], ct));   // r_c x p^2
+                    rows += parts.back().r;
+                }
+                Mat Z(rows, r0);
+                int off = 0;
+                for (int c = 0; c < 4; ++c) {
+                    for (int i = 0; i < parts[c].r; ++i)
+                        for (int j = 0; j < r0; ++j) Z.at(off + i, j) = parts[c].at(i, j);
+                    off += parts[c].r;
+                }
+                int g = ix + s * iy;
+                cpqr(Z, rank_tol, L.W[g], L.Rt[g], ct);
+                L.rank[g] = L.W[g].c;
+            }
+    }
+    // M2L_ij = Rt_i K(nodes_i, nodes_j) Rt_j^T for j in I_i
+    for (int k = 2; k <= kap; ++k) {
+        OpsLevel& L = h.ops[k];
+        int s = side_of(k);
+        L.M2L.assign((size_t)s * s * 49, Mat());
+        std::vector<std::vector<double>> NX(s * s), NY(s * s);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) box_nodes(h, k, ix, iy, NX[ix + s * iy], NY[ix + s * iy]);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix)
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dx = -3; dx <= 3; ++dx) {
+                        int jx = ix + dx, jy = iy + dy;
+                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
+                        if (!in_interaction_list(ix, iy, jx, jy)) continue;
+                        int gi = ix + s * iy, gj = jx + s * jy;
+                        Mat Kc(r0, r0);
+                        for (int m = 0; m < r0; ++m)
+                            for (int l = 0; l < r0; ++l)
+                                Kc.at(m, l) = kernel_value(P, NX[gi][m], NY[gi][m], NX[gj][l], NY[gj][l]);
+                        Mat t1 = mul(L.Rt[gi], Kc, ct);
+                        L.M2L[(size_t)gi * 49 + d49(dx, dy)] = mul(t1, transpose(L.Rt[gj]), ct);
+                    }
+    }
+    // leaf P2P_ij[a, b] = K(x_a, x_b), diagonal A_aa = diag (reading R4)
+    h.leafP2P.assign((size_t)side * side * 9, Mat());
+    for (int iy = 0; iy < side; ++iy)
+        for (int ix = 0; ix < side; ++ix)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int jx = ix + dx, jy = iy + dy;
+                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
+                    int gi = ix + side * iy, gj = jx + side * jy;
+                    int ni = h.leaf_count[gi], nj = h.leaf_count[gj];
+                    Mat B(ni, nj);
+                    for (int a = 0; a < ni; ++a)
+                        for (int b = 0; b < nj; ++b) {
+                            int64_t ta = h.leaf_start[gi] + a, tb = h.leaf_start[gj] + b;
+                            B.at(a, b) = (ta == tb) ? P.diag : kernel_value(P, h.px[ta], h.py[ta], h.px[tb], h.py[tb]);
+                        }
+                    if (dx == 0 && dy == 0)
+                        for (int j = 0; j < B.c; ++j) h.scale_A = std::max(h.scale_A, col_norm(B, j));
+                    h.leafP2P[(size_t)gi * 9 + d9(dx, dy)] = std::move(B);
+                }
+    h.ct.add(ct);
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// elimination (Algorithm 1)
+// ------------------------------------------------------------------------------------------
+struct Ctx { Handle* h; ElimLevel* L; };
+
+inline int gx(const ElimLevel& L, int g) { return g % L.side; }
+inline int gy(const ElimLevel& L, int g) { return g / L.side; }
+inline Mat& blk(std::vector<Mat>& v, const ElimLevel& L, int p, int q) {
+    return v[(size_t)p * 49 + d49(gx(L, q) - gx(L, p), gy(L, q) - gy(L, p))];
+}
+bool well_separated(const ElimLevel& L, int p, int q) {
+    return cheb_dist(gx(L, p), gy(L, p), gx(L, q), gy(L, q)) >= 2;
+}
+std::vector<int> neighbours(const ElimLevel& L, int g) {  // N_g, grid order, self included
+    std::vector<int> out;
+    int ix = gx(L, g), iy = gy(L, g);
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int jx = ix + dx, jy = iy + dy;
+            if (jx < 0 || jy < 0 || jx >= L.side || jy >= L.side) continue;
+            out.push_back(jx + L.side * jy);
+        }
+    return out;
+}
+
+// width of the active row / column of box b
+inline int row_size(const ElimLevel& L, int b) { return L.E[b] ? L.r[b] : L.n[b]; }
+
+// The block at (active row of p, active column of q):
+//   (P2P_p, x_q) = P2P_pq, (P2P_p, y_q) = M2P_pq, (M2L_p, x_q) = P2L_pq, (M2L_p, y_q) = M2L_pq.
+Mat& active_block(ElimLevel& L, int p, int q) {
+    if (!L.E[p]) return L.E[q] ? blk(L.M2P, L, p, q) : blk(L.P2P, L, p, q);
+    return L.E[q] ? blk(L.M2L, L, p, q) : blk(L.P2L, L, p, q);
+}
+
+// Fill compression after eliminating e (Algorithm 1, "if p and q are well-separated" branches;
+// reading R2 for how).
+void compress_fill(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& ct) {
+    std::vector<int> nb = neighbours(L, e);
+    for (int q : nb) {
+        if (q == e || L.E[q]) continue;
+        // S_q: well-separated fill in q's P2P row (P2P_qp / M2P_qp) and in q's column x_q
+        // (P2P_pq / P2L_pq, transposed)
+        std::vector<const Mat*> cols, rows;
+        for (int p : nb) {
+            if (p == q || !well_separated(L, p, q)) continue;
+            Mat& f1 = active_block(L, q, p);
+            if (f1.present()) cols.push_back(&f1);
+            Mat& f2 = active_block(L, p, q);
+            if (f2.present()) rows.push_back(&f2);
+        }
+        if (cols.empty() && rows.empty()) continue;
+        int nq = L.n[q], m = 0;
+        for (auto* f : cols) m += f->c;
+        for (auto* f : rows) m += f->r;
+        Mat S(nq, m);
+        int off = 0;
+        for (auto* f : cols) {
+            for (int i = 0; i < nq; ++i)
+                for (int j = 0; j < f->c; ++j) S.at(i, off + j) = f->at(i, j);
+            off += f->c;
+        }
+        for (auto* f : rows) {
+            for (int i = 0; i < nq; ++i)
+                for (int j = 0; j < f->r; ++j) S.at(i, off + j) = f->at(j, i);
+            off += f->r;
+        }
+        bool over = false;
+        int add = augment_basis(L.W[q], S, eps, ref, rcap, ct, over);
+        if (!L.W[q].present()) L.W[q] = Mat(nq, 0);
+        L.r[q] = L.W[q].c;
+        ct.compressions += 1.0;
+        ct.added += add;
+        if (over) ct.overflows += 1.0;
+    }
+    // redirect each well-separated fill through the bases into M2L_pq
+    for (int p : nb) {
+        if (p == e) continue;
+        for (int q : nb) {
+            if (q == e || p == q || !well_separated(L, p, q)) continue;
+            if (L.E[p] && L.E[q]) continue;  // M2L_pq was updated directly
+            Mat& F = active_block(L, p, q);
+            if (!F.present()) continue;
+            Mat G;
+            if (!L.E[p] && !L.E[q]) {        // P2P_pq = L2P_pp M2L_pq P2M_qq
+                Mat t = mul_tn(L.W[p], F, ct);
+                G = mul(t, L.W[q], ct);
+            } else if (L.E[p] && !L.E[q]) {  // P2L_pq = M2L_pq P2M_qq
+                G = mul(F, L.W[q], ct);
+            } else {                         // M2P_pq = L2P_pp M2L_pq
+                G = mul_tn(L.W[p], F, ct);
+            }
+            Mat& M = blk(L.M2L, L, p, q);
+            pad_to(M, L.r[p], L.r[q]);
+            add_into(M, G, 1.0, ct);
+            F.clear();
+        }
+    }
+}
+
+// Eliminate x_e and z_e with the equations P2P(e,k) and P2M(e,k); returns false on a
+// singular pivot block.
+bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& ct) {
+    int n = L.n[e], r = L.r[e];
+    BoxFactor& F = L.fac[e];
+    F.n = n; F.r = r;
+    // pivot block [[P2P_ee, L2P_ee], [P2M_ee, 0]], rows (P2P_e; P2M_e), columns (x_e; z_e)
+    Mat piv(n + r, n + r);
+    Mat& Pee = blk(L.P2P, L, e, e);
+    if (Pee.present())
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) piv.at(i, j) = Pee.at(i, j);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < r; ++j) {
+            piv.at(i, n + j) = L.W[e].at(i, j);
+            piv.at(n + j, i) = L.W[e].at(i, j);
+        }
+    if (n + r > 0 && !lu_factor(piv, F.piv, ct)) return false;
+    F.LU = std::move(piv);
+    std::vector<int> nb = neighbours(L, e);
+    // C: active rows rho of the other neighbours, coefficient at x_e (zero at z_e)
+    for (int p : nb) {
+        if (p == e) continue;
+        Mat& c = active_block(L, p, e);
+        if (c.present()) F.C.push_back({p, L.E[p] ? ROW_M2L : ROW_P2P, c});
+    }
+    // B: pivot row P2P_e at the active columns gamma of the other neighbours (row P2M_e is 0)
+    for (int q : nb) {
+        if (q == e) continue;
+        Mat& b = active_block(L, e, q);
+        if (b.present()) F.B.push_back({q, L.E[q] ? COL_Y : COL_X, b});
+    }
+    // X_gamma = Piv^{-1} [B_gamma; 0] and X_ye = Piv^{-1} [0; -I]
+    std::vector<Mat> X(F.B.size());
+    for (size_t t = 0; t < F.B.size(); ++t) {
+        const Mat& b = F.B[t].blk;
+        Mat rhs(n + r, b.c);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < b.c; ++j) rhs.at(i, j) = b.at(i, j);
+        lu_solve(F.LU, F.piv, rhs, ct);
+        X[t] = std::move(rhs);
+    }
+    Mat Xy(n + r, r);
+    for (int j = 0; j < r; ++j) Xy.at(n + j, j) = -1.0;
+    if (n + r > 0) lu_solve(F.LU, F.piv, Xy, ct);
+    // consumed blocks: column x_e and row P2P_e leave the system
+    for (int p : nb) {
+        blk(L.P2P, L, p, e).clear(); blk(L.P2L, L, p, e).clear();
+        blk(L.P2P, L, e, p).clear(); blk(L.M2P, L, e, p).clear();
+    }
+    // Schur complement A[rho, gamma] -= C_rho X_gamma (rows of the neighbours)
+    for (const Panel& cp : F.C) {
+        int p = cp.box;
+        for (size_t t = 0; t < F.B.size(); ++t) {
+            int q = F.B[t].box;
+            Mat Xx(n, X[t].c);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < X[t].c; ++j) Xx.at(i, j) = X[t].at(i, j);
+            Mat upd = mul(cp.blk, Xx, ct);
+            Mat& tgt = active_block(L, p, q);
+            if (L.E[p] && L.E[q]) pad_to(tgt, L.r[p], L.r[q]);
+            add_into(tgt, upd, -1.0, ct);
+            ct.bytes += 8.0 * ((double)cp.blk.r * cp.blk.c + (double)Xx.r * Xx.c + 2.0 * upd.r * upd.c);
+        }
+        // new column y_e in row rho: M2P_pe (p not eliminated) or M2L_pe (p eliminated)
+        Mat Xx(n, r);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < r; ++j) Xx.at(i, j) = Xy.at(i, j);
+        Mat upd = mul(cp.blk, Xx, ct);
+        Mat& tgt = L.E[p] ? blk(L.M2L, L, p, e) : blk(L.M2P, L, p, e);
+        add_into(tgt, upd, -1.0, ct);
+    }
+    // row M2L_e has coefficient -I at z_e: A[M2L_e, gamma] += X_gamma[z rows]
+    for (size_t t = 0; t < F.B.size(); ++t) {
+        int q = F.B[t].box;
+        Mat Xz(r, X[t].c);
+        for (int i = 0; i < r; ++i)
+            for (int j = 0; j < X[t].c; ++j) Xz.at(i, j) = X[t].at(n + i, j);
+        Mat& tgt = L.E[q] ? blk(L.M2L, L, e, q) : blk(L.P2L, L, e, q);
+        if (L.E[q]) pad_to(tgt, r, L.r[q]);
+        add_into(tgt, Xz, 1.0, ct);
+    }
+    {
+        Mat Xz(r, r);
+        for (int i = 0; i < r; ++i)
+            for (int j = 0; j < r; ++j) Xz.at(i, j) = Xy.at(n + i, j);
+        Mat& tgt = blk(L.M2L, L, e, e);
+        pad_to(tgt, r, r);
+        add_into(tgt, Xz, 1.0, ct);
+    }
+    L.E[e] = 1;
+    compress_fill(L, e, eps, ref, rcap, ct);
+    return true;
+}
+
+// level k from the operators (leaf) or from level k+1 (non-leaf), Remark on P2P at non-leaf
+// levels and Eq. "particles_multipoles"
+void make_level(Handle& h, int k) {
+    ElimLevel& L = h.el[k];
+    const OpsLevel& O = h.ops[k];
+    int s = side_of(k);
+    L.k = k; L.side = s; L.nb = s * s;
+    L.n.assign(L.nb, 0); L.r.assign(L.nb, 0); L.E.assign(L.nb, 0);
+    L.W.assign(L.nb, Mat());
+    size_t nblk = (size_t)L.nb * 49;
+    L.P2P.assign(nblk, Mat()); L.M2P.assign(nblk, Mat()); L.P2L.assign(nblk, Mat()); L.M2L.assign(nblk, Mat());
+    L.fac.assign(L.nb, BoxFactor());
+    L.order = elimination_order(k, h.prm.order);
+    for (int g = 0; g < L.nb; ++g) L.r[g] = O.rank[g];
+    if (k == h.depth) {
+        for (int g = 0; g < L.nb; ++g) {
+            L.n[g] = h.leaf_count[g];
+            L.W[g] = O.W[g];
+            if (!L.W[g].present()) L.W[g] = Mat(L.n[g], 0);
+        }
+        for (int g = 0; g < L.nb; ++g)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
+                    if (B.present()) L.P2P[(size_t)g * 49 + d49(dx, dy)] = B;
+                }
+    } else {
+        ElimLevel& C = h.el[k + 1];
+        const OpsLevel& OC = h.ops[k + 1];
+        L.xoff.assign((size_t)L.nb * 5, 0);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int g = ix + s * iy;
+                int off = 0, ooff = 0;
+                std::vector<int> offs(4), ooffs(4), cg(4);
+                for (int c = 0; c < 4; ++c) {
+                    cg[c] = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
+                    offs[c] = off; ooffs[c] = ooff;
+                    L.xoff[(size_t)g * 5 + c] = off;
+                    off += C.r[cg[c]];
+                    ooff += OC.rank[cg[c]];
+                }
+                L.xoff[(size_t)g * 5 + 4] = off;
+                L.n[g] = off;
+                // L2P of the parent = stacked children L2L; augmented child components get
+                // zero rows
+                Mat W(off, O.rank[g]);
+                for (int c = 0; c < 4; ++c)
+                    for (int t = 0; t < OC.rank[cg[c]]; ++t)
+                        for (int j = 0; j < O.rank[g]; ++j) W.at(offs[c] + t, j) = O.W[g].at(ooffs[c] + t, j);
+                L.W[g] = std::move(W);
+            }
+        // P2P_PQ = [M2L_{c d}] over the children of neighbours P, Q
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int jx = ix + dx, jy = iy + dy;
+                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
+                        int g = ix + s * iy, q = jx + s * jy;
+                        Mat B(L.n[g], L.n[q]);
+                        for (int a = 0; a < 4; ++a)
+                            for (int b = 0; b < 4; ++b) {
+                                int ca = (2 * ix + (a & 1)) + 2 * s * (2 * iy + (a >> 1));
+                                int db = (2 * jx + (b & 1)) + 2 * s * (2 * jy + (b >> 1));
+                                const Mat& M = blk(C.M2L, C, ca, db);
+                                if (!M.present()) continue;
+                                int ro = L.xoff[(size_t)g * 5 + a], co = L.xoff[(size_t)q * 5 + b];
+                                for (int i = 0; i < M.r; ++i)
+                                    for (int j = 0; j < M.c; ++j) B.at(ro + i, co + j) = M.at(i, j);
+                            }
+                        L.P2P[(size_t)g * 49 + d49(dx, dy)] = std::move(B);
+                    }
+    }
+    for (size_t t = 0; t < nblk; ++t)
+        if (O.M2L[t].present()) L.M2L[t] = O.M2L[t];
+}
+
+int do_factor(Handle& h) {
+    auto t0 = std::chrono::steady_clock::now();
+    int kap = h.depth;
+    h.el.assign(kap + 1, ElimLevel());
+    double eps = h.prm.eps;
+    double ref = h.prm.tau_ref == 1 ? h.scale_A : 0.0;
+    int rcap = h.prm.r_cap;
+    int status = 0;
+    for (int k = kap; k >= 2; --k) {
+        make_level(h, k);
+        ElimLevel& L = h.el[k];
+        if (h.prm.order == 0) {
+            // same-colour boxes are at Chebyshev distance >= 3 and touch disjoint blocks
+            for (int col = 0; col < 9; ++col) {
+                std::vector<int> boxes;
+                for (int g : L.order)
+                    if (colour_of(gx(L, g), gy(L, g)) == col) boxes.push_back(g);
+                int bad = 0;
+                Counter tot;
+#pragma omp parallel
+                {
+                    Counter ct;
+#pragma omp for schedule(dynamic, 1)
+                    for (int t = 0; t < (int)boxes.size(); ++t)
+                        if (!eliminate(L, boxes[t], eps, ref, rcap, ct)) {
+#pragma omp atomic write
+                            bad = 1;
+                        }
+#pragma omp critical
+                    tot.add(ct);
+                }
+                h.ct.add(tot);
+                if (bad) { status = 4; break; }
+            }
+        } else {
+            Counter ct;
+            for (int g : L.order)
+                if (!eliminate(L, g, eps, ref, rcap, ct)) { status = 4; break; }
+            h.ct.add(ct);
+        }
+        if (status) break;
+        h.eliminations += L.nb;
+        for (int g = 0; g < L.nb; ++g) h.max_rank = std::max(h.max_rank, L.r[g]);
+        // the P2P, P2L and M2P blocks of this level are all consumed; M2L feeds level k-1
+        for (auto& m : L.P2P) m.clear();
+        for (auto& m : L.P2L) m.clear();
+        for (auto& m : L.M2P) m.clear();
+        if (k + 1 <= kap) {
+            for (auto& m : h.el[k + 1].M2L) m.clear();
+        }
+    }
+    if (status == 0) {
+        // level 1: the particles are the level-2 multipoles, P2P^(1) = [M2L^(2)_{cd}] (dense)
+        ElimLevel& L2 = h.el[2];
+        h.rootOff.assign(L2.nb + 1, 0);
+        for (int g = 0; g < L2.nb; ++g) h.rootOff[g + 1] = h.rootOff[g] + L2.r[g];
+        int M = h.rootOff[L2.nb];
+        Mat D(M, M);
+        for (int g = 0; g < L2.nb; ++g)
+            for (int q = 0; q < L2.nb; ++q) {
+                const Mat& B = blk(L2.M2L, L2, g, q);
+                if (!B.present()) continue;
+                for (int i = 0; i < B.r; ++i)
+                    for (int j = 0; j < B.c; ++j) D.at(h.rootOff[g] + i, h.rootOff[q] + j) = B.at(i, j);
+            }
+        if (M > 0 && !lu_factor(D, h.rootPiv, h.ct)) status = 4;
+        h.rootLU = std::move(D);
+        for (auto& m : L2.M2L) m.clear();
+    }
+    h.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    h.factored = (status == 0);
+    return status;
+}
+
+// Forward replay of the eliminations on the right-hand side, dense level-1 solve, then
+// Algorithm 2 (levels 2..kappa, reverse order inside each level).
+int do_solve(Handle& h, const double* b, double* x, int nrhs) {
+    if (!h.factored) return 8;
+    int kap = h.depth;
+    Counter ct;
+    std::vector<std::vector<Mat>> rhsP(kap + 1), rhsZ(kap + 1), xs(kap + 1), ys(kap + 1);
+    // leaf right-hand side in tree order
+    {
+        ElimLevel& L = h.el[kap];
+        rhsP[kap].assign(L.nb, Mat());
+        for (int g = 0; g < L.nb; ++g) {
+            Mat R(L.n[g], nrhs);
+            for (int a = 0; a < L.n[g]; ++a)
+                for (int j = 0; j < nrhs; ++j)
+                    R.at(a, j) = b[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]];
+            rhsP[kap][g] = std::move(R);
+        }
+    }
+    for (int k = kap; k >= 2; --k) {
+        ElimLevel& L = h.el[k];
+        rhsZ[k].assign(L.nb, Mat());
+        for (int g = 0; g < L.nb; ++g) rhsZ[k][g] = Mat(L.r[g], nrhs);
+        for (int e : L.order) {
+            BoxFactor& F = L.fac[e];
+            Mat v(F.n + F.r, nrhs);
+            for (int i = 0; i < F.n; ++i)
+                for (int j = 0; j < nrhs; ++j) v.at(i, j) = rhsP[k][e].at(i, j);
+            if (F.n + F.r > 0) lu_solve(F.LU, F.piv, v, ct);
+            Mat vx(F.n, nrhs);
+            for (int i = 0; i < F.n; ++i)
+                for (int j = 0; j < nrhs; ++j) vx.at(i, j) = v.at(i, j);
+            for (const Panel& cp : F.C) {
+                Mat upd = mul(cp.blk, vx, ct);
+                Mat& tgt = cp.kind == ROW_P2P ? rhsP[k][cp.box] : rhsZ[k][cp.box];
+                for (int i = 0; i < upd.r; ++i)
+                    for (int j = 0; j < nrhs; ++j) tgt.at(i, j) -= upd.at(i, j);
+            }
+            for (int i = 0; i < F.r; ++i)
+                for (int j = 0; j < nrhs; ++j) rhsZ[k][e].at(i, j) += v.at(F.n + i, j);
+        }
+        if (k > 2) {
+            ElimLevel& U = h.el[k - 1];
+            rhsP[k - 1].assign(U.nb, Mat());
+            for (int g = 0; g < U.nb; ++g) {
+                int ix = g % U.side, iy = g / U.side;
+                Mat R(U.n[g], nrhs);
+                for (int c = 0; c < 4; ++c) {
+                    int cg = (2 * ix + (c & 1)) + L.side * (2 * iy + (c >> 1));
+                    int off = U.xoff[(size_t)g * 5 + c];
+                    for (int i = 0; i < L.r[cg]; ++i)
+                        for (int j = 0; j < nrhs; ++j) R.at(off + i, j) = rhsZ[k][cg].at(i, j);
+                }
+                rhsP[k - 1][g] = std::move(R);
+            }
+        }
+    }
+    // level 1
+    {
+        ElimLevel& L2 = h.el[2];
+        int M = h.rootOff[L2.nb];
+        Mat R(M, nrhs);
+        for (int g = 0; g < L2.nb; ++g)
+            for (int i = 0; i < L2.r[g]; ++i)
+                for (int j = 0; j < nrhs; ++j) R.at(h.rootOff[g] + i, j) = rhsZ[2][g].at(i, j);
+        if (M > 0) lu_solve(h.rootLU, h.rootPiv, R, ct);
+        ys[2].assign(L2.nb, Mat());
+        for (int g = 0; g < L2.nb; ++g) {
+            Mat Y(L2.r[g], nrhs);
+            for (int i = 0; i < L2.r[g]; ++i)
+                for (int j = 0; j < nrhs; ++j) Y.at(i, j) = R.at(h.rootOff[g] + i, j);
+            ys[2][g] = std::move(Y);
+        }
+    }
+    for (int k = 2; k <= kap; ++k) {
+        ElimLevel& L = h.el[k];
+        xs[k].assign(L.nb, Mat());
+        for (auto it = L.order.rbegin(); it != L.order.rend(); ++it) {
+            int e = *it;
+            BoxFactor& F = L.fac[e];
+            Mat v(F.n + F.r, nrhs);
+            for (int i = 0; i < F.n; ++i)
+                for (int j = 0; j < nrhs; ++j) v.at(i, j) = rhsP[k][e].at(i, j);
+            for (const Panel& bp : F.B) {
+                const Mat& u = bp.kind == COL_X ? xs[k][bp.box] : ys[k][bp.box];
+                Mat uu(bp.blk.c, nrhs);
+                for (int i = 0; i < bp.blk.c; ++i)
+                    for (int j = 0; j < nrhs; ++j) uu.at(i, j) = u.at(i, j);
+                Mat upd = mul(bp.blk, uu, ct);
+                for (int i = 0; i < F.n; ++i)
+                    for (int j = 0; j < nrhs; ++j) v.at(i, j) -= upd.at(i, j);
+            }
+            // row P2M_e: W^T x_e - y_e = 0
+            for (int i = 0; i < F.r; ++i)
+                for (int j = 0; j < nrhs; ++j) v.at(F.n + i, j) = ys[k][e].at(i, j);
+            if (F.n + F.r > 0) lu_solve(F.LU, F.piv, v, ct);
+            Mat X(F.n, nrhs);
+            for (int i = 0; i < F.n; ++i)
+                for (int j = 0; j < nrhs; ++j) X.at(i, j) = v.at(i, j);
+            xs[k][e] = std::move(X);
+        }
+        if (k < kap) {  // the children's multipoles are the particles of this level
+            ElimLevel& C = h.el[k + 1];
+            ys[k + 1].assign(C.nb, Mat());
+            for (int g = 0; g < L.nb; ++g) {
+                int ix = g % L.side, iy = g / L.side;
+                for (int c = 0; c < 4; ++c) {
+                    int cg = (2 * ix + (c & 1)) + C.side * (2 * iy + (c >> 1));
+                    int off = L.xoff[(size_t)g * 5 + c];
+                    Mat Y(C.r[cg], nrhs);
+                    for (int i = 0; i < C.r[cg]; ++i)
+                        for (int j = 0; j < nrhs; ++j) Y.at(i, j) = xs[k][g].at(off + i, j);
+                    ys[k + 1][cg] = std::move(Y);
+                }
+            }
+        }
+    }
+    ElimLevel& L = h.el[kap];
+    for (int g = 0; g < L.nb; ++g)
+        for (int a = 0; a < L.n[g]; ++a)
+            for (int j = 0; j < nrhs; ++j)
+                x[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]] = xs[kap][g].at(a, j);
+    return 0;
+}
+
+// FMM matvec with the operators of the build: y = A~ x
+void do_matvec(Handle& h, const double* x, double* y, int nrhs) {
+    int kap = h.depth;
+    Counter ct;
+    std::vector<std::vector<Mat>> Y(kap + 1), Z(kap + 1);
+    int side = side_of(kap);
+    std::vector<Mat> xl(side * side);
+    for (int g = 0; g < side * side; ++g) {
+        Mat X(h.leaf_count[g], nrhs);
+        for (int a = 0; a < X.r; ++a)
+            for (int j = 0; j < nrhs; ++j) X.at(a, j) = x[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]];
+        xl[g] = std::move(X);
+    }
+    // upward pass: P2M, M2M
+    Y[kap].resize(side * side);
+    for (int g = 0; g < side * side; ++g) Y[kap][g] = mul_tn(h.ops[kap].W[g], xl[g], ct);
+    for (int k = kap - 1; k >= 2; --k) {
+        int s = side_of(k);
+        Y[k].resize(s * s);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int g = ix + s * iy;
+                int rows = 0;
+                for (int c = 0; c < 4; ++c) rows += h.ops[k + 1].rank[(2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1))];
+                Mat X(rows, nrhs);
+                int off = 0;
+                for (int c = 0; c < 4; ++c) {
+                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
+                    for (int i = 0; i < Y[k + 1][cg].r; ++i)
+                        for (int j = 0; j < nrhs; ++j) X.at(off + i, j) = Y[k + 1][cg].at(i, j);
+                    off += Y[k + 1][cg].r;
+                }
+                Y[k][g] = mul_tn(h.ops[k].W[g], X, ct);
+            }
+    }
+    // M2L
+    for (int k = 2; k <= kap; ++k) {
+        int s = side_of(k);
+        Z[k].resize(s * s);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int g = ix + s * iy;
+                Mat acc(h.ops[k].rank[g], nrhs);
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dx = -3; dx <= 3; ++dx) {
+                        int jx = ix + dx, jy = iy + dy;
+                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
+                        const Mat& M = h.ops[k].M2L[(size_t)g * 49 + d49(dx, dy)];
+                        if (!M.present()) continue;
+                        Mat t = mul(M, Y[k][jx + s * jy], ct);
+                        add_into(acc, t, 1.0, ct);
+                    }
+                Z[k][g] = std::move(acc);
+            }
+    }
+    // downward pass: L2L
+    for (int k = 2; k < kap; ++k) {
+        int s = side_of(k);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int g = ix + s * iy;
+                Mat t = mul(h.ops[k].W[g], Z[k][g], ct);  // stacked children locals
+                int off = 0;
+                for (int c = 0; c < 4; ++c) {
+                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
+                    Mat& zc = Z[k + 1][cg];
+                    for (int i = 0; i < zc.r; ++i)
+                        for (int j = 0; j < nrhs; ++j) zc.at(i, j) += t.at(off + i, j);
+                    off += zc.r;
+                }
+            }
+    }
+    // L2P + P2P
+    for (int iy = 0; iy < side; ++iy)
+        for (int ix = 0; ix < side; ++ix) {
+            int g = ix + side * iy;
+            Mat out = mul(h.ops[kap].W[g], Z[kap][g], ct);
+            if (!out.present()) out = Mat(h.leaf_count[g], nrhs);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int jx = ix + dx, jy = iy + dy;
+                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
+                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
+                    if (!B.present()) continue;
+                    Mat t = mul(B, xl[jx + side * jy], ct);
+                    add_into(out, t, 1.0, ct);
+                }
+            for (int a = 0; a < h.leaf_count[g]; ++a)
+                for (int j = 0; j < nrhs; ++j) y[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]] = out.present() ? out.at(a, j) : 0.0;
+        }
+}
+
+int leaf_of_tree_pos(const Handle& h, int64_t t) {
+    int side = side_of(h.depth);
+    double ux = (h.px[t] - h.prm.box[0]) / h.prm.box[2], uy = (h.py[t] - h.prm.box[1]) / h.prm.box[2];
+    int ix = std::min((int)std::floor(ux * side), side - 1);
+    int iy = std::min((int)std::floor(uy * side), side - 1);
+    return ix + side * iy;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C interface
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+void* oracle_build(const double* pts, int64_t N, const oracle_params* prm) {
+    if (!pts || !prm || N <= 0 || prm->depth < 2 || prm->depth > 12 || prm->cheb_p < 1 || prm->cheb_p > 12) return nullptr;
+    if (!(prm->box[2] > 0.0) || prm->eps < 0.0) return nullptr;
+    if (prm->kernel == ORACLE_K_EXP && !(prm->kparam[0] > 0.0)) return nullptr;
+    auto h = std::make_unique<Handle>();
+    h->prm = *prm;
+    h->N = N;
+    h->depth = prm->depth;
+    h->p = prm->cheb_p;
+    h->r0 = prm->cheb_p * prm->cheb_p;
+#ifdef _OPENMP
+    if (prm->threads > 0) omp_set_num_threads(prm->threads);
+#endif
+    if (!build(*h, pts)) return nullptr;
+    return h.release();
+}
+
+void oracle_destroy(void* hp) { delete static_cast<Handle*>(hp); }
+
+int oracle_factor(void* hp) {
+    if (!hp) return 1;
+    Handle& h = *static_cast<Handle*>(hp);
+#ifdef _OPENMP
+    if (h.prm.threads > 0) omp_set_num_threads(h.prm.threads);
+#endif
+    if (h.factored) return 0;
+    return do_factor(h);
+}
+
+int oracle_solve(void* hp, const double* b, double* x, int nrhs) {
+    if (!hp || !b || !x || nrhs <= 0) return 1;
+    return do_solve(*static_cast<Handle*>(hp), b, x, nrhs);
+}
+
+int oracle_matvec(void* hp, const double* x, double* y, int nrhs) {
+    if (!hp || !x || !y || nrhs <= 0) return 1;
+    do_matvec(*static_cast<Handle*>(hp), x, y, nrhs);
+    return 0;
+}
+
+int oracle_dense_exact(void* hp, double* A) {
+    Handle& h = *static_cast<Handle*>(hp);
+    int64_t N = h.N;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            int64_t ui = h.perm[i], uj = h.perm[j];
+            A[ui * N + uj] = (i == j) ? h.prm.diag : kernel_value(h.prm, h.px[i], h.py[i], h.px[j], h.py[j]);
+        }
+    return 0;
+}
+
+// A~ through the nested orthonormal operators: near leaves P2P; otherwise
+// B_i^(k) M2L^(k)_{IJ} B_j^(k)^T at the level k where the ancestors are in each other's
+// interaction list, B_i^(kappa) = W_i, B_i^(k) = B_i^(k+1) W_anc[rows of the child]
+int oracle_dense_tilde(void* hp, double* A) {
+    Handle& h = *static_cast<Handle*>(hp);
+    int kap = h.depth;
+    int64_t N = h.N;
+    Counter ct;
+    int side = side_of(kap);
+    // per leaf, per level: chain basis (n_i x r_anc)
+    std::vector<std::vector<Mat>> Bc(side * side, std::vector<Mat>(kap + 1));
+    for (int g = 0; g < side * side; ++g) {
+        Bc[g][kap] = h.ops[kap].W[g];
+        int ix = g % side, iy = g / side;
+        for (int k = kap - 1; k >= 2; --k) {
+            int cx = ix >> (kap - k - 1), cy = iy >> (kap - k - 1);   // ancestor at k+1
+            int px = cx >> 1, py = cy >> 1;
+            int c = (cx & 1) + 2 * (cy & 1);
+            int s = side_of(k);
+            const Mat& Wp = h.ops[k].W[px + s * py];
+            int off = 0;
+            for (int cc = 0; cc < c; ++cc) off += h.ops[k + 1].rank[(2 * px + (cc & 1)) + 2 * s * (2 * py + (cc >> 1))];
+            int rc = h.ops[k + 1].rank[cx + 2 * s * cy];
+            Mat sub(rc, Wp.c);
+            for (int i = 0; i < rc; ++i)
+                for (int j = 0; j < Wp.c; ++j) sub.at(i, j) = Wp.at(off + i, j);
+            Bc[g][k] = mul(Bc[g][k + 1], sub, ct);
+        }
+    }
+    for (int gi = 0; gi < side * side; ++gi)
+        for (int gj = 0; gj < side * side; ++gj) {
+            int ix = gi % side, iy = gi / side, jx = gj % side, jy = gj / side;
+            int ni = h.leaf_count[gi], nj = h.leaf_count[gj];
+            if (ni == 0 || nj == 0) continue;
+            Mat blkv;
+            if (cheb_dist(ix, iy, jx, jy) <= 1) {
+                blkv = h.leafP2P[(size_t)gi * 9 + d9(jx - ix, jy - iy)];
+            } else {
+                int k = kap;
+                while (k >= 2) {
+                    int sh = kap - k;
+                    if (in_interaction_list(ix >> sh, iy >> sh, jx >> sh, jy >> sh)) break;
+                    --k;
+                }
+                int sh = kap - k, s = side_of(k);
+                int I = (ix >> sh) + s * (iy >> sh);
+                int dx = (jx >> sh) - (ix >> sh), dy = (jy >> sh) - (iy >> sh);
+                const Mat& M = h.ops[k].M2L[(size_t)I * 49 + d49(dx, dy)];
+                Mat t = mul(Bc[gi][k], M, ct);
+                blkv = mul(t, transpose(Bc[gj][k]), ct);
+            }
+            for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < nj; ++b) {
+                    int64_t ua = h.perm[h.leaf_start[gi] + a], ub = h.perm[h.leaf_start[gj] + b];
+                    A[ua * N + ub] = blkv.at(a, b);
+                }
+        }
+    return 0;
+}
+
+// A~ from its definition: sum_{m,l} S^I_m(x_a) K(node^I_m, node^J_l) S^J_l(x_b) at the level
+// where the ancestors I, J are well-separated with neighbouring parents; K itself for
+// neighbouring leaves
+int oracle_dense_tilde_direct(void* hp, double* A) {
+    Handle& h = *static_cast<Handle*>(hp);
+    int kap = h.depth, r0 = h.r0;
+    int64_t N = h.N;
+    std::vector<double> si(r0), sj(r0), nix, niy, njx, njy;
+    for (int64_t a = 0; a < N; ++a)
+        for (int64_t b = 0; b < N; ++b) {
+            int la = leaf_of_tree_pos(h, a), lb = leaf_of_tree_pos(h, b);
+            int side = side_of(kap);
+            int ix = la % side, iy = la / side, jx = lb % side, jy = lb / side;
+            double v;
+            if (cheb_dist(ix, iy, jx, jy) <= 1) {
+                v = (a == b) ? h.prm.diag : kernel_value(h.prm, h.px[a], h.py[a], h.px[b], h.py[b]);
+            } else {
+                int k = kap;
+                while (k >= 2 && !in_interaction_list(ix >> (kap - k), iy >> (kap - k), jx >> (kap - k), jy >> (kap - k))) --k;
+                int sh = kap - k;
+                box_basis(h, k, ix >> sh, iy >> sh, h.px[a], h.py[a], si.data());
+                box_basis(h, k, jx >> sh, jy >> sh, h.px[b], h.py[b], sj.data());
+                box_nodes(h, k, ix >> sh, iy >> sh, nix, niy);
+                box_nodes(h, k, jx >> sh, jy >> sh, njx, njy);
+                v = 0.0;
+                for (int m = 0; m < r0; ++m)
+                    for (int l = 0; l < r0; ++l) v += si[m] * kernel_value(h.prm, nix[m], niy[m], njx[l], njy[l]) * sj[l];
+            }
+            A[h.perm[a] * N + h.perm[b]] = v;
+        }
+    return 0;
+}
+
+// The extended sparse system (Eq. "extended_sparsity", all levels) assembled densely and
+// solved by LU: unknowns x (leaf particles) then (y_i, z_i) per box per level; equations P2P
+// rows at the leaves, P2M rows W_i^T x_i - y_i = 0 and M2L rows
+// -z_i + sum_{J in I_i} M2L_iJ y_J + L2L_i z_parent = 0 at every level k >= 2.
+int oracle_extended_solve(void* hp, const double* b, double* x, int nrhs) {
+    Handle& h = *static_cast<Handle*>(hp);
+    int kap = h.depth;
+    int64_t N = h.N;
+    std::vector<std::vector<int64_t>> yoff(kap + 1), zoff(kap + 1);
+    int64_t M = N;
+    for (int k = kap; k >= 2; --k) {
+        int s = side_of(k);
+        yoff[k].resize(s * s); zoff[k].resize(s * s);
+        for (int g = 0; g < s * s; ++g) {
+            yoff[k][g] = M; M += h.ops[k].rank[g];
+            zoff[k][g] = M; M += h.ops[k].rank[g];
+        }
+    }
+    if (M > 20000) return 1;
+    std::vector<double> D((size_t)M * M, 0.0), R((size_t)M * nrhs, 0.0);
+    auto Dat = [&](int64_t i, int64_t j) -> double& { return D[(size_t)i * M + j]; };
+    int side = side_of(kap);
+    // leaf P2P rows
+    for (int g = 0; g < side * side; ++g) {
+        int ix = g % side, iy = g / side;
+        for (int a = 0; a < h.leaf_count[g]; ++a) {
+            int64_t row = h.leaf_start[g] + a;
+            for (int j = 0; j < nrhs; ++j) R[(size_t)row * nrhs + j] = b[(size_t)j * N + h.perm[row]];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int jx = ix + dx, jy = iy + dy;
+                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
+                    int q = jx + side * jy;
+                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
+                    for (int c = 0; c < h.leaf_count[q]; ++c) Dat(row, h.leaf_start[q] + c) = B.at(a, c);
+                }
+            for (int m = 0; m < h.ops[kap].rank[g]; ++m) Dat(row, zoff[kap][g] + m) = h.ops[kap].W[g].at(a, m);
+        }
+    }
+    for (int k = kap; k >= 2; --k) {
+        int s = side_of(k);
+        for (int iy = 0; iy < s; ++iy)
+            for (int ix = 0; ix < s; ++ix) {
+                int g = ix + s * iy, r = h.ops[k].rank[g];
+                const Mat& W = h.ops[k].W[g];
+                // P2M rows: W^T x_g - y_g = 0, x_g = leaf particles or the children's y
+                for (int m = 0; m < r; ++m) {
+                    int64_t row = yoff[k][g] + m;
+                    Dat(row, yoff[k][g] + m) = -1.0;
+                    if (k == kap) {
+                        for (int a = 0; a < h.leaf_count[g]; ++a) Dat(row, h.leaf_start[g] + a) = W.at(a, m);
+                    } else {
+                        int off = 0;
+                        for (int c = 0; c < 4; ++c) {
+                            int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
+                            for (int t = 0; t < h.ops[k + 1].rank[cg]; ++t) Dat(row, yoff[k + 1][cg] + t) = W.at(off + t, m);
+                            off += h.ops[k + 1].rank[cg];
+                        }
+                    }
+                }
+                // M2L rows
+                for (int m = 0; m < r; ++m) {
+                    int64_t row = zoff[k][g] + m;
+                    Dat(row, zoff[k][g] + m) = -1.0;
+                    for (int dy = -3; dy <= 3; ++dy)
+                        for (int dx = -3; dx <= 3; ++dx) {
+                            int jx = ix + dx, jy = iy + dy;
+                            if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
+                            const Mat& Mm = h.ops[k].M2L[(size_t)g * 49 + d49(dx, dy)];
+                            if (!Mm.present()) continue;
+                            int q = jx + s * jy;
+                            for (int l = 0; l < Mm.c; ++l) Dat(row, yoff[k][q] + l) = Mm.at(m, l);
+                        }
+                    if (k > 2) {  // L2L from the parent's locals
+                        int px = ix >> 1, py = iy >> 1, ps = side_of(k - 1), pg = px + ps * py;
+                        int c = (ix & 1) + 2 * (iy & 1);
+                        int off = 0;
+                        for (int cc = 0; cc < c; ++cc) off += h.ops[k].rank[(2 * px + (cc & 1)) + 2 * ps * (2 * py + (cc >> 1))];
+                        const Mat& Wp = h.ops[k - 1].W[pg];
+                        for (int l = 0; l < Wp.c; ++l) Dat(row, zoff[k - 1][pg] + l) = Wp.at(off + m, l);
+                    }
+                }
+            }
+    }
+    Mat Dm; Dm.r = (int)M; Dm.c = (int)M; Dm.a = std::move(D);
+    std::vector<int> piv;
+    Counter ct;
+    if (!lu_factor(Dm, piv, ct)) return 4;
+    Mat Rm; Rm.r = (int)M; Rm.c = nrhs; Rm.a = std::move(R);
+    lu_solve(Dm, piv, Rm, ct);
+    for (int64_t t = 0; t < N; ++t)
+        for (int j = 0; j < nrhs; ++j) x[(size_t)j * N + h.perm[t]] = Rm.at((int)t, j);
+    return 0;
+}
+
+int oracle_dense_lu_solve(const double* A, int64_t n, const double* b, double* x, int nrhs) {
+    Mat D((int)n, (int)n);
+    std::memcpy(D.a.data(), A, sizeof(double) * (size_t)n * n);
+    std::vector<int> piv;
+    Counter ct;
+    if (!lu_factor(D, piv, ct)) return 4;
+    Mat R((int)n, nrhs);
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < nrhs; ++j) R.at((int)i, j) = b[(size_t)j * n + i];
+    lu_solve(D, piv, R, ct);
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < nrhs; ++j) x[(size_t)j * n + i] = R.at((int)i, j);
+    return 0;
+}
+
+int oracle_num_boxes(void* hp, int level) {
+    (void)hp;
+    return side_of(level) * side_of(level);
+}
+
+int oracle_ranks(void* hp, int level, int* out) {
+    Handle& h = *static_cast<Handle*>(hp);
+    if (!h.factored || level < 2 || level > h.depth) return 8;
+    const ElimLevel& L = h.el[level];
+    for (int g = 0; g < L.nb; ++g) out[g] = L.r[g];
+    return 0;
+}
+
+int oracle_initial_ranks(void* hp, int level, int* out) {
+    Handle& h = *static_cast<Handle*>(hp);
+    if (level < 2 || level > h.depth) return 1;
+    const OpsLevel& L = h.ops[level];
+    for (size_t g = 0; g < L.rank.size(); ++g) out[g] = L.rank[g];
+    return 0;
+}
+
+int oracle_leaf_counts(void* hp, int* out) {
+    Handle& h = *static_cast<Handle*>(hp);
+    for (size_t g = 0; g < h.leaf_count.size(); ++g) out[g] = h.leaf_count[g];
+    return 0;
+}
+
+int oracle_perm(void* hp, int64_t* out) {
+    Handle& h = *static_cast<Handle*>(hp);
+    for (int64_t t = 0; t < h.N; ++t) out[t] = h.perm[t];
+    return 0;
+}
+
+int oracle_lists(void* hp, int level, int box, int* nbr, int* n_nbr, int* inter, int* n_inter) {
+    Handle& h = *static_cast<Handle*>(hp);
+    if (level < 1 || level > h.depth) return 1;
+    int s = side_of(level);
+    int ix = box % s, iy = box / s;
+    *n_nbr = 0; *n_inter = 0;
+    for (int jy = 0; jy < s; ++jy)
+        for (int jx = 0; jx < s; ++jx) {
+            if (cheb_dist(ix, iy, jx, jy) <= 1) nbr[(*n_nbr)++] = jx + s * jy;
+            else if (in_interaction_list(ix, iy, jx, jy)) inter[(*n_inter)++] = jx + s * jy;
+        }
+    return 0;
+}
+
+int oracle_order(void* hp, int level, int* out) {
+    Handle& h = *static_cast<Handle*>(hp);
+    std::vector<int> o = elimination_order(level, h.prm.order);
+    for (size_t t = 0; t < o.size(); ++t) out[t] = o[t];
+    return 0;
+}
+
+int oracle_stats(void* hp, double* out, int nout) {
+    Handle& h = *static_cast<Handle*>(hp);
+    double v[9] = {h.ct.flops, h.ct.bytes, h.ct.compressions, h.ct.overflows, (double)h.max_rank,
+                   h.eliminations, h.ct.added, h.factor_seconds, h.scale_A};
+    for (int i = 0; i < nout && i < 9; ++i) out[i] = v[i];
+    return 0;
+}
+
+void oracle_cheb_nodes(int p, double* t) { cheb_nodes(p, t); }
+
+void oracle_lagrange(int p, double t, double* out) {
+    std::vector<double> nodes(p);
+    cheb_nodes(p, nodes.data());
+    lagrange(p, nodes.data(), t, out);
+}
+
+int oracle_kernel_eval(const oracle_params* prm, const double* a, const double* b, double* out) {
+    *out = kernel_value(*prm, a[0], a[1], b[0], b[1]);
+    return 0;
+}
+
+}  // extern "C"

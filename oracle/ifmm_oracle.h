@@ -1,0 +1,73 @@
+/*
+ * ifmm_oracle.h -- C interface of the CPU oracle for the Inverse Fast Multipole Method
+ * (Ambikasaran & Darve, "The Inverse Fast Multipole Method", arXiv:1407.1572).
+ *
+ * TEST INFRASTRUCTURE ONLY. The oracle is a plain, slow FP64 restatement of the paper's
+ * method (Section 4.2, Algorithms 1 and 2). It is called by the tests, by the package's
+ * smoke check and by the bench's CPU-baseline leg, and by nothing in the product library.
+ * It shares no code with the CUDA path.
+ *
+ * All vectors are in the caller's point order, column-major N x nrhs.
+ * Return codes: 0 = ok, 1 = invalid argument, 4 = singular pivot, 8 = wrong call order.
+ */
+#ifndef IFMM_ORACLE_H
+#define IFMM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_POLY = 3 };
+
+typedef struct {
+    int depth;          /* leaf level kappa >= 2 of the uniform quadtree                      */
+    int cheb_p;         /* Chebyshev nodes per dimension; initial rank p^2                      */
+    int kernel;         /* ORACLE_K_*                                                           */
+    int r_cap;          /* upper bound on any box rank (<= 0: no cap besides n_i)              */
+    double eps;         /* relative compression tolerance of the fill-ins                      */
+    double diag;        /* matrix diagonal A_ii                                                 */
+    double kparam[4];   /* kernel parameters (EXP: kparam[0] = length scale)                   */
+    double box[3];      /* root box: x0, y0, side length                                       */
+    int order;          /* 0 = colour-major elimination order, 1 = Morton order                */
+    int threads;        /* OpenMP threads for same-colour boxes (<= 0: default)                */
+    int tau_ref;        /* compression threshold reference: 0 = eps * largest column norm of the
+                           fill being compressed; 1 = eps * largest column norm over the leaf
+                           diagonal blocks P2P_ii (the scale of the matrix)                      */
+} oracle_params;
+
+void* oracle_build(const double* pts, int64_t N, const oracle_params* prm);
+void  oracle_destroy(void* h);
+int   oracle_factor(void* h);
+int   oracle_solve(void* h, const double* b, double* x, int nrhs);
+int   oracle_matvec(void* h, const double* x, double* y, int nrhs);
+
+/* dense N x N matrices, row-major, caller's point order (small N only) */
+int   oracle_dense_tilde(void* h, double* A);         /* the FMM matrix via the nested operators    */
+int   oracle_dense_tilde_direct(void* h, double* A);  /* same matrix, Chebyshev formula per level  */
+int   oracle_dense_exact(void* h, double* A);         /* the kernel matrix A itself                */
+int   oracle_extended_solve(void* h, const double* b, double* x, int nrhs); /* dense extended system */
+int   oracle_dense_lu_solve(const double* A, int64_t n, const double* b, double* x, int nrhs);
+
+/* introspection for the tests */
+int   oracle_num_boxes(void* h, int level);
+int   oracle_ranks(void* h, int level, int* out);          /* final ranks, grid order ix + side*iy   */
+int   oracle_initial_ranks(void* h, int level, int* out);  /* ranks after orthonormalisation         */
+int   oracle_leaf_counts(void* h, int* out);
+int   oracle_perm(void* h, int64_t* out);                  /* tree position -> caller index           */
+int   oracle_lists(void* h, int level, int box, int* nbr, int* n_nbr, int* inter, int* n_inter);
+int   oracle_order(void* h, int level, int* out);          /* elimination order (grid indices)       */
+/* stats: [0] flops, [1] bytes, [2] compressions (augmenting events), [3] rank overflows,
+ *        [4] max rank, [5] eliminations, [6] directions added, [7] factor seconds,
+ *        [8] matrix scale s_A (largest column norm over the leaf diagonal blocks)             */
+int   oracle_stats(void* h, double* out, int nout);
+
+/* primitives used as pins */
+void  oracle_cheb_nodes(int p, double* t);
+void  oracle_lagrange(int p, double t, double* out);
+int   oracle_kernel_eval(const oracle_params* prm, const double* a, const double* b, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,257 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows. None of them retypes an oracle formula: they check
+closed forms, brute force on tiny inputs, special cases that reduce to a textbook routine,
+and the exactness invariant of the extended sparse system (Section 2.3 / 4.1: the FMM matrix
+is represented "exactly" by the extended sparse matrix).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1407_1572_gb300 import inputs
+
+
+def _oracle(O, N, depth, p, kernel=None, eps=1e-10, diag=None, seed=1407, **kw):
+    pts = inputs.uniform_points(seed, N)
+    kernel = O.K_INV_R if kernel is None else kernel
+    prm = O.make_params(depth, p, kernel, eps=eps, diag=math.sqrt(N) if diag is None else diag, **kw)
+    return O.Oracle(pts, prm), pts
+
+
+# ---- Chebyshev interpolation (Section 5: 8 Chebyshev nodes per dimension) --------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+def test_cheb_nodes_are_roots_of_T_p(oracle_mod, p):
+    t = oracle_mod.cheb_nodes(p)
+    # T_p(cos th) = cos(p th): first-kind nodes are the p roots of T_p in (-1, 1)
+    assert np.allclose(np.cos(p * np.arccos(t)), 0.0, atol=1e-14)
+    assert len(set(np.round(t, 12))) == p
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_lagrange_cardinal_and_exact_on_polynomials(oracle_mod, p):
+    t = oracle_mod.cheb_nodes(p)
+    for n in range(p):
+        assert np.allclose(oracle_mod.lagrange(p, t[n]), np.eye(p)[n], atol=1e-13)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        coeff = rng.standard_normal(p)          # degree p-1 polynomial
+        x = rng.uniform(-1, 1)
+        interp = oracle_mod.lagrange(p, x) @ np.polyval(coeff, t)
+        assert abs(interp - np.polyval(coeff, x)) < 1e-12
+        assert abs(oracle_mod.lagrange(p, x).sum() - 1.0) < 1e-13
+
+
+def test_kernel_values_closed_form(oracle_mod):
+    O = oracle_mod
+    prm = O.make_params(3, 4, O.K_INV_R)
+    assert O.kernel_eval(prm, [0.0, 0.0], [3.0, 4.0]) == pytest.approx(0.2, rel=1e-15)
+    prm = O.make_params(3, 4, O.K_EXP, kparam=(0.1, 0, 0, 0))
+    assert O.kernel_eval(prm, [0.0, 0.0], [0.3, 0.4]) == pytest.approx(math.exp(-5.0), rel=1e-14)
+
+
+# ---- tree and lists (Section 4.2, Table "table_cluster") -------------------------------------
+
+def test_lists_brute_force(oracle_mod):
+    o, _ = _oracle(oracle_mod, 512, 4, 2)
+    for k in range(1, 5):
+        s = 2 ** k
+        for box in range(s * s):
+            nb, it = o.lists(k, box)
+            ix, iy = box % s, box // s
+            want_nb, want_it = [], []
+            for jy in range(s):
+                for jx in range(s):
+                    d = max(abs(ix - jx), abs(iy - jy))
+                    pd = max(abs(ix // 2 - jx // 2), abs(iy // 2 - jy // 2))
+                    if d <= 1:
+                        want_nb.append(jx + s * jy)
+                    elif pd <= 1:
+                        want_it.append(jx + s * jy)
+            assert sorted(nb) == sorted(want_nb)
+            assert sorted(it) == sorted(want_it)
+            if 2 <= ix < s - 2 and 2 <= iy < s - 2:
+                assert len(nb) == 9 and len(it) == 27
+
+
+def test_every_leaf_pair_covered_exactly_once(oracle_mod):
+    """The near field plus the interaction lists of all levels partition the leaf pairs
+    (the FMM matrix of Section 2.2: each block is either full rank or a well-separated
+    low-rank block at exactly one level)."""
+    o, _ = _oracle(oracle_mod, 512, 4, 2)
+    kap = 4
+    s = 2 ** kap
+    cover = np.zeros((s * s, s * s), dtype=int)
+    for i in range(s * s):
+        nb, _ = o.lists(kap, i)
+        cover[i, nb] += 1
+    for k in range(2, kap + 1):
+        sk = 2 ** k
+        for I in range(sk * sk):
+            _, it = o.lists(k, I)
+            for J in it:
+                for i in range(s * s):
+                    if (i % s) >> (kap - k) != I % sk or (i // s) >> (kap - k) != I // sk:
+                        continue
+                    for j in range(s * s):
+                        if (j % s) >> (kap - k) == J % sk and (j // s) >> (kap - k) == J // sk:
+                            cover[i, j] += 1
+    assert (cover == 1).all()
+
+
+def test_colour_order_independent_sets(oracle_mod):
+    o, _ = _oracle(oracle_mod, 1024, 3, 2)
+    for k in (2, 3):
+        s = 2 ** k
+        order = o.order(k)
+        assert sorted(order) == list(range(s * s))
+        col = [(b % s) % 3 + 3 * ((b // s) % 3) for b in order]
+        assert col == sorted(col)
+        for a in order:
+            for b in order:
+                if a != b and col[list(order).index(a)] == col[list(order).index(b)]:
+                    d = max(abs(a % s - b % s), abs(a // s - b // s))
+                    assert d >= 3
+
+
+# ---- dense LU (textbook) -----------------------------------------------------------------------
+
+def test_dense_lu_solves_known_system(oracle_mod):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((60, 60))
+    x = rng.standard_normal((60, 3))
+    got = oracle_mod.dense_lu_solve(A, A @ x)
+    assert np.abs(got - x).max() < 1e-10
+    assert np.allclose(got, np.linalg.solve(A, A @ x), atol=1e-11)
+
+
+# ---- the FMM matrix A~ (Section 2.2, Table "table_FMM_operators", Section 5) -----------------
+
+def test_polynomial_kernel_is_reproduced_exactly(oracle_mod):
+    """Chebyshev interpolation with p >= 2 nodes is exact for a kernel of degree 1 in each
+    coordinate, so the FMM matrix equals the kernel matrix (nested bases, orthonormalisation
+    and M2L folding all included)."""
+    O = oracle_mod
+    for depth, p in [(3, 2), (3, 3), (4, 2)]:
+        o, _ = _oracle(O, 600, depth, p, kernel=O.K_POLY, diag=3.0)
+        A = o.dense_exact()
+        At = o.dense_tilde()
+        assert np.abs(A - At).max() < 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("kernel", ["inv_r", "exp"])
+def test_nested_operators_equal_textbook_formula(oracle_mod, kernel):
+    """A~ through P2M/M2M/M2L/L2L/L2P with orthonormalised bases equals the per-level Chebyshev
+    formula sum_{m,l} S_m(x) K(xbar_m, ybar_l) S_l(y) (nesting of polynomial interpolation)."""
+    O = oracle_mod
+    kk = O.K_INV_R if kernel == "inv_r" else O.K_EXP
+    o, _ = _oracle(O, 700, 4, 3, kernel=kk, kparam=(0.1, 0, 0, 0))
+    At = o.dense_tilde()
+    Ad = o.dense_tilde_direct()
+    assert np.abs(At - Ad).max() < 1e-12 * np.abs(Ad).max()
+    assert np.allclose(At, At.T, rtol=0, atol=1e-12 * np.abs(At).max())
+
+
+def test_interpolation_error_decreases_with_p(oracle_mod):
+    errs = []
+    for p in (2, 4, 6):
+        o, _ = _oracle(oracle_mod, 1024, 3, p)
+        A = o.dense_exact()
+        errs.append(np.linalg.norm(o.dense_tilde() - A) / np.linalg.norm(A))
+    assert errs[0] > 10 * errs[1] > 100 * errs[2]
+
+
+def test_fmm_matvec_equals_dense(oracle_mod):
+    o, _ = _oracle(oracle_mod, 1500, 3, 4)
+    x = inputs.rhs(11, 1500, 3)
+    y = o.matvec(x)
+    ref = o.dense_tilde() @ x
+    assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ---- extended sparse system (Section 4.1, Eq. "extended_sparsity") ---------------------------
+
+@pytest.mark.parametrize("depth,p", [(2, 3), (3, 2), (3, 3)])
+def test_extended_system_is_exact(oracle_mod, depth, p):
+    """The extended sparse system with multipoles and locals as unknowns has exactly the
+    solution of A~ x = b (the paper's first key idea)."""
+    N = 640
+    o, _ = _oracle(oracle_mod, N, depth, p)
+    x = inputs.rhs(5, N, 2)
+    A = o.dense_tilde()
+    b = A @ x
+    xe = o.extended_solve(b)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(xe - xd) / np.linalg.norm(xd) < 1e-9
+
+
+# ---- elimination and back substitution (Algorithms 1 and 2) ----------------------------------
+
+@pytest.mark.parametrize("depth,p,order", [(2, 3, 0), (3, 2, 0), (3, 3, 0), (3, 3, 1), (4, 2, 0)])
+def test_uncompressed_elimination_is_exact(oracle_mod, depth, p, order):
+    """eps = 0 keeps every fill direction: the elimination is then plain block LU of the
+    extended system (Remark in Section 4.1) and reproduces A~^{-1} b."""
+    N = 1024
+    o, _ = _oracle(oracle_mod, N, depth, p, eps=0.0, order=order)
+    A = o.dense_tilde()
+    x = inputs.rhs(9, N, 2)
+    b = A @ x
+    o.factor()
+    xs = o.solve(b)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) < 1e-10
+
+
+def test_compressed_error_tracks_eps(oracle_mod):
+    N = 2048
+    errs = []
+    for eps in (1e-5, 1e-8, 1e-11):
+        o, _ = _oracle(oracle_mod, N, 3, 3, eps=eps)
+        x = inputs.rhs(13, N, 1)
+        b = o.matvec(x)
+        o.factor()
+        errs.append(np.linalg.norm(o.solve(b) - x) / np.linalg.norm(x))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-6
+
+
+@pytest.mark.parametrize("tau_ref", [0, 1])
+def test_orders_agree_within_eps_bound(oracle_mod, tau_ref):
+    """The paper leaves the elimination order open; colour-major and Morton order must give
+    the same solution up to the compression error."""
+    N = 2048
+    sols = []
+    for order in (0, 1):
+        o, _ = _oracle(oracle_mod, N, 3, 3, eps=1e-9, order=order, tau_ref=tau_ref)
+        x = inputs.rhs(17, N, 1)
+        b = o.matvec(x)
+        o.factor()
+        sols.append((o.solve(b), x))
+    for xs, x in sols:
+        assert np.linalg.norm(xs - x) / np.linalg.norm(x) < 1e-4
+    assert np.linalg.norm(sols[0][0] - sols[1][0]) / np.linalg.norm(sols[0][1]) < 1e-4
+
+
+def test_multiple_rhs_consistent(oracle_mod):
+    N = 1024
+    o, _ = _oracle(oracle_mod, N, 3, 3, eps=1e-8)
+    o.factor()
+    B = inputs.rhs(19, N, 3)
+    X = o.solve(B)
+    for j in range(3):
+        assert np.allclose(o.solve(B[:, j].copy()), X[:, j], rtol=0, atol=1e-13 * np.abs(X).max())
+
+
+def test_ranks_bounded_and_work_linear(oracle_mod):
+    """Ranks of the compressed blocks stay bounded and the work per unknown stays flat as N
+    grows at fixed points per leaf (Section 5 remark; O(N) claim of Section 1)."""
+    out = []
+    for N, depth in ((1024, 2), (4096, 3), (16384, 4)):
+        o, _ = _oracle(oracle_mod, N, depth, 3, eps=1e-6, tau_ref=1)
+        o.factor()
+        st = o.stats()
+        out.append((st["max_rank"], st["flops"] / N))
+    assert out[2][0] <= 2.0 * out[1][0]
+    assert out[2][1] <= 2.5 * out[1][1]
