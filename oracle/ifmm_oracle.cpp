@@ -39,7 +39,9 @@
  *   R5 the reference of the compression threshold (the paper's tolerance 1e-14 does not say
  *      relative to what): tau_ref = 0 takes the fill itself (largest column norm of S_q),
  *      tau_ref = 1 takes the scale of the matrix, s_A = largest column norm over the leaf
- *      diagonal blocks P2P_ii.
+ *      diagonal blocks P2P_ii (an absolute tolerance eps * s_A at every level);
+ *      tau_ref = 2 takes the scale of the level being eliminated, s^(k) = largest column norm
+ *      over the diagonal blocks P2P_ii^(k) at the start of level k.
  */
 #include "ifmm_oracle.h"
 
@@ -187,6 +189,16 @@ void lu_solve(const Mat& LU, const std::vector<int>& piv, Mat& B, Counter& ct) {
         for (int j = 0; j < m; ++j) B.at(i, j) /= d;
     }
     ct.flops += 2.0 * (double)n * n * m;
+}
+
+// B <- Piv^{-1} B for a pivot block factored in balanced form: Piv = S^{-1} Piv_s S^{-1} with
+// S = diag(I_n, alpha I_r), so Piv^{-1} = S Piv_s^{-1} S (rows n.. of B and of the result scale).
+void piv_solve(const Mat& LU, const std::vector<int>& piv, int n, double alpha, Mat& B, Counter& ct) {
+    for (int i = n; i < B.r; ++i)
+        for (int j = 0; j < B.c; ++j) B.at(i, j) *= alpha;
+    lu_solve(LU, piv, B, ct);
+    for (int i = n; i < B.r; ++i)
+        for (int j = 0; j < B.c; ++j) B.at(i, j) *= alpha;
 }
 
 double col_norm(const Mat& A, int j, int row0 = 0) {
@@ -400,6 +412,7 @@ enum { COL_X = 0, COL_Y = 1 };      // active unknown of a box: x before, y afte
 struct Panel { int box; int kind; Mat blk; };
 struct BoxFactor {
     int n = 0, r = 0;
+    double alpha = 1.0;   // balancing of the pivot block, see eliminate()
     Mat LU;
     std::vector<int> piv;
     std::vector<Panel> C;  // active rows of the neighbours at pivot column x_e
@@ -408,6 +421,7 @@ struct BoxFactor {
 
 struct ElimLevel {
     int k = 0, side = 0, nb = 0;
+    double scale = 0.0;        // largest column norm of the diagonal blocks at the start of the level
     std::vector<int> n, r, E;
     std::vector<int> xoff;     // non-leaf: 5 offsets per box of the children's y inside x_i
     std::vector<Mat> W;        // L2P_ii; P2M_ii = W^T
@@ -746,16 +760,24 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
     int n = L.n[e], r = L.r[e];
     BoxFactor& F = L.fac[e];
     F.n = n; F.r = r;
-    // pivot block [[P2P_ee, L2P_ee], [P2M_ee, 0]], rows (P2P_e; P2M_e), columns (x_e; z_e)
+    // pivot block [[P2P_ee, L2P_ee], [P2M_ee, 0]], rows (P2P_e; P2M_e), columns (x_e; z_e).
+    // It is factored in balanced form [[P2P_ee, a W_e], [a W_e^T, 0]] with a = largest column norm
+    // of P2P_ee: the orthonormal basis W_e is O(1) while P2P_ee is O(a), and without balancing the
+    // block's condition number grows like a^2 (exact arithmetic is unchanged, see piv_solve).
     Mat piv(n + r, n + r);
     Mat& Pee = blk(L.P2P, L, e, e);
-    if (Pee.present())
+    double alpha = 0.0;
+    if (Pee.present()) {
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) piv.at(i, j) = Pee.at(i, j);
+        for (int j = 0; j < n; ++j) alpha = std::max(alpha, col_norm(Pee, j));
+    }
+    if (!(alpha > 0.0)) alpha = 1.0;
+    F.alpha = alpha;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < r; ++j) {
-            piv.at(i, n + j) = L.W[e].at(i, j);
-            piv.at(n + j, i) = L.W[e].at(i, j);
+            piv.at(i, n + j) = alpha * L.W[e].at(i, j);
+            piv.at(n + j, i) = alpha * L.W[e].at(i, j);
         }
     if (n + r > 0 && !lu_factor(piv, F.piv, ct)) return false;
     F.LU = std::move(piv);
@@ -779,12 +801,12 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
         Mat rhs(n + r, b.c);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < b.c; ++j) rhs.at(i, j) = b.at(i, j);
-        lu_solve(F.LU, F.piv, rhs, ct);
+        piv_solve(F.LU, F.piv, n, F.alpha, rhs, ct);
         X[t] = std::move(rhs);
     }
     Mat Xy(n + r, r);
     for (int j = 0; j < r; ++j) Xy.at(n + j, j) = -1.0;
-    if (n + r > 0) lu_solve(F.LU, F.piv, Xy, ct);
+    if (n + r > 0) piv_solve(F.LU, F.piv, n, F.alpha, Xy, ct);
     // consumed blocks: column x_e and row P2P_e leave the system
     for (int p : nb) {
         blk(L.P2P, L, p, e).clear(); blk(L.P2L, L, p, e).clear();
@@ -911,6 +933,12 @@ void make_level(Handle& h, int k) {
     }
     for (size_t t = 0; t < nblk; ++t)
         if (O.M2L[t].present()) L.M2L[t] = O.M2L[t];
+    L.scale = 0.0;
+    for (int g = 0; g < L.nb; ++g) {
+        const Mat& D = L.P2P[(size_t)g * 49 + d49(0, 0)];
+        if (!D.present()) continue;
+        for (int j = 0; j < D.c; ++j) L.scale = std::max(L.scale, col_norm(D, j));
+    }
 }
 
 int do_factor(Handle& h) {
@@ -918,12 +946,12 @@ int do_factor(Handle& h) {
     int kap = h.depth;
     h.el.assign(kap + 1, ElimLevel());
     double eps = h.prm.eps;
-    double ref = h.prm.tau_ref == 1 ? h.scale_A : 0.0;
     int rcap = h.prm.r_cap;
     int status = 0;
     for (int k = kap; k >= 2; --k) {
         make_level(h, k);
         ElimLevel& L = h.el[k];
+        const double ref = h.prm.tau_ref == 1 ? h.scale_A : (h.prm.tau_ref == 2 ? L.scale : 0.0);
         if (h.prm.order == 0) {
             // same-colour boxes are at Chebyshev distance >= 3 and touch disjoint blocks
             for (int col = 0; col < 9; ++col) {
@@ -1015,7 +1043,7 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
             Mat v(F.n + F.r, nrhs);
             for (int i = 0; i < F.n; ++i)
                 for (int j = 0; j < nrhs; ++j) v.at(i, j) = rhsP[k][e].at(i, j);
-            if (F.n + F.r > 0) lu_solve(F.LU, F.piv, v, ct);
+            if (F.n + F.r > 0) piv_solve(F.LU, F.piv, F.n, F.alpha, v, ct);
             Mat vx(F.n, nrhs);
             for (int i = 0; i < F.n; ++i)
                 for (int j = 0; j < nrhs; ++j) vx.at(i, j) = v.at(i, j);
@@ -1082,7 +1110,7 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
             // row P2M_e: W^T x_e - y_e = 0
             for (int i = 0; i < F.r; ++i)
                 for (int j = 0; j < nrhs; ++j) v.at(F.n + i, j) = ys[k][e].at(i, j);
-            if (F.n + F.r > 0) lu_solve(F.LU, F.piv, v, ct);
+            if (F.n + F.r > 0) piv_solve(F.LU, F.piv, F.n, F.alpha, v, ct);
             Mat X(F.n, nrhs);
             for (int i = 0; i < F.n; ++i)
                 for (int j = 0; j < nrhs; ++j) X.at(i, j) = v.at(i, j);

@@ -32,8 +32,9 @@ typedef struct {
     int order;          /* 0 = colour-major elimination order, 1 = Morton order                */
     int threads;        /* OpenMP threads for same-colour boxes (<= 0: default)                */
     int tau_ref;        /* compression threshold reference: 0 = eps * largest column norm of the
-                           fill being compressed; 1 = eps * largest column norm over the leaf
-                           diagonal blocks P2P_ii (the scale of the matrix)                      */
+                           fill being compressed; 1 = eps * s_A, the largest column norm over the
+                           leaf diagonal blocks (matrix scale); 2 = eps * the largest column norm
+                           over the diagonal blocks P2P_ii^(k) of the level being eliminated      */
 } oracle_params;
 
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm);
