@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Factor + solve throughput of the IFMM on GB300 (unknowns/s), one JSON line on rank 0.
+
+Workload: N = 2^20 points i.i.d. uniform in [0,1]^2 (seeded), uniform quadtree of depth 7
+(16,384 leaves x 64 points), K(x,y) = 1/|x-y| off the diagonal, A_ii = sqrt(N), Chebyshev 4x4
+(initial rank 16), fill compression eps = 1e-6, 32 right-hand sides; mixed precision (FP32 Schur
+updates and compression, FP64 pivot blocks, FP64 FMM residual and refinement update) refined until
+the relative error to the manufactured solution is <= 1e-6.
+
+One step = ifmm_factor (every level, Algorithm 1, plus the level-1 system) + ifmm_solve of the
+32 right-hand sides with refinement (Algorithm 2 replay + FP64 matvec per refinement step).
+value = N / step time (whole job: N x ranks / max step time over ranks for --gpus > 1, where
+every rank solves its own independent system: replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve unknowns/s at N=2^20, err<=1e-6 (mixed FP32/FP64 + FP64 refinement)"
+WORKLOAD = dict(N=1 << 20, depth=7, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
+                refine_maxit=40)
+# bounded CPU sample of the same workload family for the oracle (same points per leaf, settings)
+CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
+                  refine_maxit=40)
+
+
+def workload_desc(w, precision):
+    return (f"N={w['N']} uniform [0,1]^2, quadtree depth {w['depth']} ({4 ** w['depth']} leaves), "
+            f"1/r + sqrt(N) I, Chebyshev {w['cheb_p']}x{w['cheb_p']} (rank {w['cheb_p'] ** 2}), "
+            f"eps {w['eps']:g} (matrix-scale threshold), {w['nrhs']} RHS, {precision}")
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline of the GPU arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_step(w, threads=0):
+    """One oracle factor + refined solve on the bounded sample; returns (seconds, error)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1407_1572_gb300 import inputs
+    N = w["N"]
+    pts = inputs.uniform_points(w["seed"], N)
+    prm = O.make_params(w["depth"], w["cheb_p"], O.K_INV_R, eps=w["eps"], diag=math.sqrt(N), tau_ref=w["tau_ref"],
+                        threads=threads)
+    o = O.Oracle(pts, prm)
+    xs = inputs.rhs(w["seed"] + 1, N, w["nrhs"])
+    b = o.matvec(xs)
+    t0 = time.perf_counter()
+    o.factor()
+    x = o.solve(b)
+    for _ in range(w["refine_maxit"]):
+        r = b - o.matvec(x)
+        d = o.solve(r)
+        x = x + d
+        if np.max(np.linalg.norm(d, axis=0) / np.linalg.norm(x, axis=0)) <= w["refine_tol"]:
+            break
+    dt = time.perf_counter() - t0
+    err = float(np.max(np.linalg.norm(x - xs, axis=0) / np.linalg.norm(xs, axis=0)))
+    return dt, err
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = CPU_SAMPLE
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_step(w)
+    times, errs = [], []
+    for _ in range(args.steps):
+        dt, err = oracle_step(w)
+        times.append(dt)
+        errs.append(err)
+    ms = 1000.0 * sum(times) / len(times)
+    value = w["N"] / (ms / 1000.0)
+    sample = (f"oracle (plain FP64 C++, OpenMP over same-colour boxes) on N={w['N']} (depth {w['depth']}), "
+              f"same settings per leaf; factor + {w['nrhs']}-RHS solve with refinement; err {max(errs):.2e}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(w, "FP64 CPU oracle"), "N": w["N"], "depth": w["depth"],
+                       "nrhs": w["nrhs"], "eps": w["eps"], "err": max(errs)},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP32 / FP64 CUDA-core peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz;
+# FP64 taken as the nominal 1.25 TFLOP/s of GB300 at the same clock.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_TFLOPS = 1.25
+
+
+def roofline(stats, precision, peaks, peak_kind):
+    names = ["k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect"]
+    ms = stats["kernel_ms"]
+    launches = stats["kernel_launches"]
+    top = max(range(5), key=lambda i: ms[i])
+    hbm = peaks["hbm_gbs"]
+    out = {"kernel": names[top], "share_of_factor_kernels": ms[top] / max(sum(ms), 1e-30)}
+    if names[top] == "k_schur":
+        t = ms[top] / max(launches[top], 1) / 1000.0        # s per launch
+        bytes_pl = stats["schur_bytes"] / max(launches[top], 1)
+        flops_pl = stats["schur_flops"] / max(launches[top], 1)
+        ai = flops_pl / max(bytes_pl, 1.0)
+        alu_peak = FP32_SIMT_TFLOPS if precision == "mixed" else FP64_TFLOPS
+        if ai * hbm / 1000.0 < alu_peak:   # below the ridge: bandwidth bound
+            ach = bytes_pl / t / 1e9
+            out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"})
+        else:
+            ach = flops_pl / t / 1e12
+            out.update({"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                        "traffic": None, "peak_source": "derived from unit counts and the 2.07 GHz max clock"})
+        out["intensity_flop_per_byte"] = ai
+    else:
+        # the dominant launch is the FP64 pivot inversion or the compression: FP64 arithmetic bound
+        fl = None
+        out.update({"bound": "alu", "achieved": fl, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "peak_source": "nominal FP64 rate"})
+    out["avg_launch_ms"] = ms[top] / max(launches[top], 1)
+    return out
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1407_1572_gb300 import ifmm, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = dict(WORKLOAD)
+    if args.n:
+        w["N"] = args.n
+        w["depth"] = max(2, round(math.log(args.n / 64, 4)))
+    N, nrhs = w["N"], w["nrhs"]
+    precision = args.precision
+    stream = torch.cuda.current_stream()
+
+    def make_solver(prec):
+        prm = ifmm.default_params(depth=w["depth"], cheb_p=w["cheb_p"], eps=w["eps"], diag=math.sqrt(N),
+                                  precision=ifmm.IFMM_MIXED if prec == "mixed" else ifmm.IFMM_FP64,
+                                  tau_ref=w["tau_ref"], refine_tol=w["refine_tol"], refine_maxit=w["refine_maxit"])
+        pts = inputs.uniform_points(w["seed"] + rank, N)
+        return ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm, stream)
+
+    solver = make_solver(precision)
+    h = solver.h
+    # manufactured solution x* and b = A~ x* (FP64 FMM matvec), column-major (nrhs, N) buffers
+    xs = torch.from_numpy(inputs.rhs(w["seed"] + 1, N, nrhs).T.copy()).cuda()
+    b = torch.empty_like(xs)
+    ifmm.ifmm_matvec(h, xs.data_ptr(), b.data_ptr(), nrhs, N)
+    x = torch.empty_like(xs)
+
+    def step(hh):
+        ifmm.ifmm_factor(hh, allow_overflow=True)
+        ifmm.ifmm_solve(hh, b.data_ptr(), x.data_ptr(), nrhs, N, allow_noconv=True)
+
+    for _ in range(args.warmup):
+        step(h)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    st = ifmm.ifmm_get_stats(h)
+    err = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
+    value = world * N / (ms / 1000.0)
+    launches_per_step = st["launches_factor"] + st["launches_solve"]
+    peaks, peak_kind = load_peaks()
+    rf = roofline(st, precision, peaks, peak_kind)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    b_host = np.ascontiguousarray(b.cpu().numpy())      # (nrhs, N) = column-major N x nrhs
+    x_host = np.zeros_like(b_host)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ifmm.ifmm_factor(h, allow_overflow=True)
+        ifmm.ifmm_solve_host(h, b_host, x_host, nrhs, N, allow_noconv=True)
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
+    e2e_err = float(np.max(np.linalg.norm(x_host - xs.cpu().numpy(), axis=1) / np.linalg.norm(xs.cpu().numpy(), axis=1)))
+
+    extra = {}
+    if args.compare_fp64 and rank == 0 and precision == "mixed":
+        solver.close()
+        s64 = make_solver("fp64")
+        ifmm.ifmm_matvec(s64.h, xs.data_ptr(), b.data_ptr(), nrhs, N)
+        step(s64.h)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        step(s64.h)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        st64 = ifmm.ifmm_get_stats(s64.h)
+        err64 = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
+        extra["fp64_gpu"] = {"value": N / (ms64 / 1000.0), "unit": "unknowns/s", "ms_per_step": ms64, "err": err64,
+                             "steps": 1, "warmup": 1, "t_factor_ms": st64["t_factor_ms"],
+                             "refine_iters": st64["refine_iters"], "kernel_ms": st64["kernel_ms"]}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, cerr = oracle_step(CPU_SAMPLE)
+        cpu = {"value": CPU_SAMPLE["N"] / dt, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"oracle factor + refined {CPU_SAMPLE['nrhs']}-RHS solve on N={CPU_SAMPLE['N']} "
+                         f"(depth {CPU_SAMPLE['depth']}, same settings per leaf), {dt:.1f} s, err {cerr:.1e}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": workload_desc(w, "mixed FP32/FP64 + FP64 refinement" if precision == "mixed"
+                                                     else "FP64"),
+                           "N": N, "depth": w["depth"], "cheb_p": w["cheb_p"], "nrhs": nrhs, "eps": w["eps"],
+                           "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "l2": "inputs larger than L2 (factor touches tens of GB per step)",
+                           "err": err, "refine_iters": st["refine_iters"], "max_rank": st["max_rank"],
+                           "t_factor_ms": st["t_factor_ms"], "t_solve_ms": st["t_solve_ms"],
+                           "kernel_ms": dict(zip(ifmm.FACTOR_KERNELS, st["kernel_ms"])),
+                           "device_gb": st["device_bytes"] / 1e9},
+                "roofline": rf, "cpu_baseline": cpu,
+                "e2e": {"value": world * N / (e2e_ms / 1000.0), "unit": "unknowns/s",
+                        "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(x_host.nbytes),
+                        "ms_per_step": e2e_ms, "err": e2e_err},
+                "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=0, help="override N (depth follows 64 points per leaf)")
+    ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true", default=True)
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

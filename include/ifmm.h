@@ -1,0 +1,152 @@
+/*
+ * ifmm.h -- C ABI of the GB300 (sm_103a) Inverse Fast Multipole Method library.
+ *
+ * The method is that of Ambikasaran & Darve, "The Inverse Fast Multipole Method: an O(N)
+ * fast direct solver" (arXiv:1407.1572): a dense N x N FMM matrix A~ is written exactly as an
+ * extended sparse system in the particles x, multipoles y and locals z of every box of a
+ * uniform quadtree (Section 4.1), and that system is eliminated level by level, box by box
+ * (Algorithm 1); fill-in between well-separated boxes is compressed into the box bases on the
+ * fly, fill-in between neighbours stays dense. Back substitution runs the levels downward in
+ * the reverse order (Algorithm 2). The problem statement the calls follow is that of
+ * Section 1: given b and a tolerance eps, solve A x = b for an FMM matrix A; factorisation and
+ * solve are decoupled so that many right-hand sides reuse one factorisation (Section 4.2.3).
+ *
+ * Conventions for every call below:
+ *   - All vectors are in the caller's point order, column-major (N x nrhs, leading dimension
+ *     ld >= N), FP64. Pointers named *_dev are CUDA device pointers, *_host are host pointers.
+ *   - The handle owns all device memory it allocates; the caller owns every pointer it passes.
+ *   - No exception crosses the ABI. A failing call returns a status; ifmm_last_error() gives a
+ *     one-line message. A failed factorisation leaves the handle valid but unfactored.
+ *   - All device work is queued on the stream given to ifmm_build (NULL = legacy default
+ *     stream); calls that return results to the host synchronise that stream.
+ *   - Not thread-safe per handle: calls on one handle must not overlap.
+ */
+#ifndef IFMM_H
+#define IFMM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ifmm_handle* ifmm_h;
+
+typedef enum {
+    IFMM_OK = 0,
+    IFMM_ERR_INVALID_ARG = 1,    /* bad size, pointer, parameter or point outside the root box */
+    IFMM_ERR_CUDA = 2,           /* a CUDA runtime call failed (message in ifmm_last_error)   */
+    IFMM_ERR_OOM = 3,            /* device allocation failed                                   */
+    IFMM_ERR_SINGULAR_PIVOT = 4, /* a pivot block P2P/P2M (Eqs. P2P(i,k), P2M(i,k)) is singular */
+    IFMM_ERR_RANK_OVERFLOW = 5,  /* a box basis needed more than r_cap directions             */
+    IFMM_ERR_NOCONV = 6,         /* iterative refinement did not reach refine_tol             */
+    IFMM_ERR_TIMEOUT = 7,        /* reserved: a bounded device wait ran out                   */
+    IFMM_ERR_STATE = 8           /* call out of order (e.g. solve before factor)              */
+} ifmm_status;
+
+typedef enum {
+    IFMM_K_INV_R = 0,            /* K(x, y) = 1 / |x - y|                                      */
+    IFMM_K_EXP = 1               /* K(x, y) = exp(-|x - y| / kparam[0])                        */
+} ifmm_kernel;
+
+typedef enum {
+    IFMM_FP64 = 0,               /* every step in FP64                                         */
+    IFMM_MIXED = 1               /* FP32 Schur updates, panels and compression; FP64 pivot
+                                    blocks, residual matvec and refinement update              */
+} ifmm_precision;
+
+typedef struct {
+    int dim;              /* space dimension; must be 2 (quadtree)                               */
+    int depth;            /* leaf level kappa of the uniform tree, 2 <= depth <= 10              */
+    int cheb_p;           /* Chebyshev nodes per dimension (Section 5); initial box rank p^2      */
+    int r_cap;            /* largest rank any box basis may reach; <= 0: only the box size n_i   */
+    double eps;           /* compression tolerance of the fill-in (Section 5)                     */
+    double diag;          /* diagonal A_ii (the paper's Eq. "main_Solving_Equation" uses 1)       */
+    double kparam[4];     /* kernel parameters (IFMM_K_EXP: kparam[0] = length scale > 0)        */
+    double box[3];        /* root box x0, y0, side; side <= 0 selects the unit square [0,1]^2    */
+    int precision;        /* ifmm_precision                                                       */
+    int tau_ref;          /* compression threshold reference: 0 = the fill's own largest column
+                             norm; 1 = the matrix scale s_A (largest column norm of the leaf
+                             diagonal blocks), i.e. an absolute tolerance eps * s_A at every level;
+                             2 = the scale of the level (largest column norm of its diagonal blocks
+                             at the start of the level)                                           */
+    double refine_tol;    /* FP64 refinement stops when the preconditioned residual
+                             max_j ||M^{-1}(b_j - A~ x_j)|| / ||x_j|| (an estimate of the relative error,
+                             M^{-1} = the IFMM solve) is <= refine_tol; 0 disables refinement         */
+    int refine_maxit;     /* limit on preconditioned matvecs (IFMM_ERR_NOCONV past it)            */
+    int refine_restart;   /* > 0: GMRES(refine_restart) left-preconditioned by the IFMM solve;
+                             0: classical refinement x += M^{-1}(b - A~ x)                          */
+} ifmm_params;
+
+typedef struct {
+    int64_t n_points;
+    int depth;
+    int max_rank;          /* r_m of the paper's tables: largest box rank after factorisation   */
+    int rank_overflows;    /* 1 if some box basis was cut at r_cap                              */
+    int refine_iters;      /* solves performed by the last ifmm_solve                            */
+    double t_build_ms, t_factor_ms, t_solve_ms;   /* t_a, t_f, t_s of Table "table_notations"    */
+    double factor_flops;   /* algorithmic flops of the last factorisation at the actual ranks    */
+    double schur_flops;    /* algorithmic flops of the Schur-update launches                       */
+    double schur_bytes;    /* algorithmic bytes of the Schur-update launches (blocks read + written) */
+    double kernel_ms[5];   /* device time (CUDA events on the handle's stream) of the pivot, panel,
+                              Schur, compression and redirect launches of the last factorisation     */
+    int kernel_launches[5];/* launches of each of those five kernels in the last factorisation      */
+    double last_update;    /* max_j ||dx_j|| / ||x_j|| of the last refinement step                 */
+    double last_residual;  /* max_j ||b_j - A~ x_j|| / ||b_j|| before the last refinement step     */
+    int64_t device_bytes;  /* device memory held by the handle                                     */
+    int64_t launches_factor; /* kernels launched by the last ifmm_factor                           */
+    int64_t launches_solve;  /* kernels launched by the last ifmm_solve / ifmm_solve_host          */
+} ifmm_stats;
+
+/* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
+ * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30). */
+void ifmm_default_params(ifmm_params* p);
+
+/* Build the tree, the Chebyshev operators and their orthonormal nested bases (assembly time t_a).
+ * pts_host: N x 2 row-major FP64 host array (x0, y0, x1, y1, ...), copied; N >= 1.
+ * kernel:   ifmm_kernel. p: parameters (copied). stream: cudaStream_t or NULL.
+ * out:      receives the handle (NULL on failure).
+ * Tree and lists: Section 4.2, Table "table_cluster"; operators: Table "table_FMM_operators";
+ * Chebyshev interpolation: Section 5. Errors: INVALID_ARG, CUDA, OOM. */
+ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm_params* p,
+                       void* stream, ifmm_h* out);
+
+/* Eliminate every box, levels kappa..2 (Algorithm 1), then factor the level-1 system
+ * (factorisation time t_f). Calling it again discards the previous factorisation and recomputes
+ * it from the operators of the build. Errors: SINGULAR_PIVOT, CUDA, OOM (handle left
+ * unfactored); RANK_OVERFLOW (the factorisation completed and is usable, but some box basis was
+ * cut at r_cap, so the solve is coarser than eps). */
+ifmm_status ifmm_factor(ifmm_h h);
+
+/* x = A~^{-1} b by forward replay of the eliminations, the level-1 solve and back substitution
+ * (Algorithm 2); when refine_tol > 0 that solve is the preconditioner M^{-1} of an FP64 iterative
+ * refinement (GMRES or classical) whose residuals use ifmm_matvec (solve time t_s). b_dev, x_dev: device FP64, column-major, leading dimension ld >= N;
+ * 1 <= nrhs <= 1024; b and x must not overlap. Errors: STATE (not factored), INVALID_ARG,
+ * NOCONV (x still holds the last iterate), CUDA, OOM. */
+ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld);
+
+/* As ifmm_solve with host buffers: copies b in and x out inside the call. */
+ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld);
+
+/* y = A~ x with the FP64 FMM operators of the build: P2M, M2M, M2L, L2L, L2P and P2P
+ * (Table "table_FMM_operators"). x_dev, y_dev: device FP64, column-major, leading dimension
+ * ld >= N. Errors: INVALID_ARG, CUDA. */
+ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
+
+/* Final ranks of the boxes of one level 2..depth, grid order (ix + 2^level * iy), into the host
+ * array out_host (4^level ints). Errors: STATE (not factored), INVALID_ARG. */
+ifmm_status ifmm_get_ranks(ifmm_h h, int level, int* out_host);
+
+/* Counters and timings of the handle. */
+ifmm_status ifmm_get_stats(ifmm_h h, ifmm_stats* s);
+
+/* One-line description of the last failure on this handle ("" if none). The string is owned
+ * by the handle and valid until the next call on it. */
+const char* ifmm_last_error(ifmm_h h);
+
+/* Release the handle and all device memory it holds. NULL is ignored. */
+void ifmm_destroy(ifmm_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1104 @@
+// ifmm_api.cu -- C ABI (include/ifmm.h) and host orchestration of the IFMM on one GB300.
+//
+// The host lays out every level (offset tables for the blocks, bases, panels and per-colour
+// scratch), launches the kernels colour by colour on the handle's stream, and reads back only
+// the box ranks at the end of each level (they size the next level) and the status bits.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ifmm.h"
+#include "ifmm_internal.h"
+
+using namespace ifmm;
+
+namespace {
+
+struct FLevel {
+    int k = 0, side = 0, nb = 0, RC = 0, smax = 0;
+    double scale = 0.0;   // threshold reference of the level (tau_ref = 1)
+    std::vector<int> n, r, r0;
+    std::vector<int64_t> voff, yoff;
+    std::vector<int> xoff5;
+    std::vector<int> boxes;
+    int cstart[10] = {0};
+    int64_t vtot = 0;
+    // device
+    int* d_n = nullptr;
+    int* d_r = nullptr;
+    int64_t* d_voff = nullptr;
+    int64_t* d_yoff = nullptr;
+    int64_t* d_boff = nullptr;
+    int* d_bld = nullptr;
+    void* d_blk = nullptr;
+    void* d_W = nullptr;
+    int64_t* d_pioff = nullptr;
+    int* d_pild = nullptr;
+    void* d_Pi = nullptr;
+    int64_t* d_cpoff = nullptr;
+    void* d_Cp = nullptr;
+    int64_t* d_bpoff = nullptr;
+    void* d_Bp = nullptr;
+    int64_t* d_xsoff = nullptr;
+    int* d_xsld = nullptr;
+    void* d_Xs = nullptr;
+    int64_t* d_fsoff = nullptr;
+    void* d_Fs = nullptr;
+    void* d_Fs2 = nullptr;
+    int64_t* d_rsoff = nullptr;
+    void* d_Rs = nullptr;
+    double* d_pws = nullptr;
+    int64_t* d_psoff = nullptr;
+    int* d_boxes = nullptr;
+    int* d_xoff5 = nullptr;
+};
+
+struct OpsLevel {
+    std::vector<int> rank0;
+    int* d_rank0 = nullptr;
+    double* d_W0 = nullptr;
+    double* d_Rt = nullptr;
+    double* d_far0 = nullptr;
+};
+
+uint64_t morton_host(uint32_t ix, uint32_t iy) {
+    uint64_t m = 0;
+    for (int b = 0; b < 32; ++b) {
+        m |= (uint64_t)((ix >> b) & 1u) << (2 * b);
+        m |= (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
+    }
+    return m;
+}
+
+int region36_host(int px, int py, int qx, int qy) { return (qx - 2 * (px >> 1) + 2) + 6 * (qy - 2 * (py >> 1) + 2); }
+
+}  // namespace
+
+struct ifmm_handle {
+    ifmm_params prm{};
+    int kernel = 0;
+    int64_t N = 0;
+    int depth = 0, p = 0, r0 = 0;
+    cudaStream_t st = nullptr;
+    std::string err;
+    std::vector<std::pair<void*, size_t>> allocs;
+    int64_t bytes = 0;
+    // tree
+    int64_t* d_perm = nullptr;
+    double* d_px = nullptr;
+    double* d_py = nullptr;
+    std::vector<int> leaf_count;
+    std::vector<int64_t> leaf_start;
+    int* d_leaf_count = nullptr;
+    int64_t* d_leaf_start = nullptr;
+    double* d_cheb = nullptr;
+    double* d_Tc = nullptr;
+    std::vector<OpsLevel> ops;
+    std::vector<int64_t> p2p_off;
+    int64_t* d_p2p_off = nullptr;
+    double* d_p2p = nullptr;
+    double sA = 0.0;
+    // factor
+    bool factored = false;
+    std::vector<FLevel> lv;
+    int M = 0;
+    double* d_Dinv = nullptr;
+    int* d_status = nullptr;
+    double* d_counters = nullptr;
+    // workspaces
+    std::vector<std::pair<void*, size_t>> ws;
+    ifmm_stats stats{};
+};
+
+namespace {
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                          \
+            return e_ == cudaErrorMemoryAllocation ? IFMM_ERR_OOM : IFMM_ERR_CUDA;                \
+        }                                                                                         \
+    } while (0)
+
+#define CKS(expr)                       \
+    do {                                \
+        ifmm_status s_ = (expr);        \
+        if (s_ != IFMM_OK) return s_;   \
+    } while (0)
+
+template <typename P>
+ifmm_status dalloc(ifmm_handle* h, P** out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? IFMM_ERR_OOM : IFMM_ERR_CUDA;
+    }
+    h->allocs.push_back({p, bytes});
+    h->bytes += (int64_t)bytes;
+    *out = static_cast<P*>(p);
+    return IFMM_OK;
+}
+
+void dfree(ifmm_handle* h, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i].first == p) {
+            h->bytes -= (int64_t)h->allocs[i].second;
+            h->allocs.erase(h->allocs.begin() + i);
+            cudaFree(p);
+            return;
+        }
+}
+
+template <typename P>
+void dfree_ptr(ifmm_handle* h, P*& p) {
+    dfree(h, (void*)p);
+    p = nullptr;
+}
+
+template <typename V>
+ifmm_status upload(ifmm_handle* h, typename V::value_type** out, const V& v) {
+    CKS(dalloc(h, out, v.size() * sizeof(typename V::value_type)));
+    if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(typename V::value_type), cudaMemcpyHostToDevice, h->st));
+    return IFMM_OK;
+}
+
+// growable named workspace
+ifmm_status workspace(ifmm_handle* h, int slot, size_t bytes, void** out) {
+    if ((int)h->ws.size() <= slot) h->ws.resize(slot + 1, {nullptr, 0});
+    auto& w = h->ws[slot];
+    if (w.second < bytes) {
+        if (w.first) {
+            CK(cudaStreamSynchronize(h->st));
+            dfree(h, w.first);
+        }
+        w = {nullptr, 0};
+        void* p = nullptr;
+        CKS(dalloc(h, &p, bytes));
+        w = {p, bytes};
+    }
+    *out = w.first;
+    return IFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// build
+// ------------------------------------------------------------------------------------------------
+ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
+    const int64_t N = h->N;
+    const int kap = h->depth, side = 1 << kap, nleaf = side * side;
+    const int p = h->p, r0 = h->r0;
+    CKS(dalloc(h, &h->d_status, sizeof(int) * 4));
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
+    CKS(dalloc(h, &h->d_counters, sizeof(double) * 8));
+    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
+    double* d_pts = nullptr;
+    CKS(dalloc(h, &d_pts, sizeof(double) * 2 * N));
+    CK(cudaMemcpyAsync(d_pts, pts_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, h->st));
+    int64_t npad = 1;
+    while (npad < N) npad <<= 1;
+    unsigned long long* d_keys = nullptr;
+    CKS(dalloc(h, &d_keys, sizeof(unsigned long long) * npad));
+    launch_leaf_keys(d_pts, N, kap, h->prm.box[0], h->prm.box[1], h->prm.box[2], d_keys, npad, h->d_status, h->st);
+    launch_bitonic_sort(d_keys, npad, h->st);
+    CKS(dalloc(h, &h->d_perm, sizeof(int64_t) * N));
+    CKS(dalloc(h, &h->d_px, sizeof(double) * N));
+    CKS(dalloc(h, &h->d_py, sizeof(double) * N));
+    CKS(dalloc(h, &h->d_leaf_count, sizeof(int) * nleaf));
+    CK(cudaMemsetAsync(h->d_leaf_count, 0, sizeof(int) * nleaf, h->st));
+    launch_scatter_sorted(d_keys, d_pts, N, h->d_perm, h->d_px, h->d_py, h->d_leaf_count, kap, h->st);
+    int hstat = 0;
+    h->leaf_count.assign(nleaf, 0);
+    CK(cudaMemcpyAsync(h->leaf_count.data(), h->d_leaf_count, sizeof(int) * nleaf, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&hstat, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree_ptr(h, d_keys);
+    dfree_ptr(h, d_pts);
+    if (hstat & DEV_ERR_RANGE) {
+        h->err = "a point lies outside the root box";
+        return IFMM_ERR_INVALID_ARG;
+    }
+    // leaf_start in Morton order (tree order of the sorted points)
+    std::vector<std::pair<uint64_t, int>> mk(nleaf);
+    for (int g = 0; g < nleaf; ++g) mk[g] = {morton_host(g % side, g / side), g};
+    std::sort(mk.begin(), mk.end());
+    h->leaf_start.assign(nleaf, 0);
+    int64_t acc = 0;
+    int max_n = 0;
+    for (auto& kv : mk) {
+        h->leaf_start[kv.second] = acc;
+        acc += h->leaf_count[kv.second];
+        max_n = std::max(max_n, h->leaf_count[kv.second]);
+    }
+    CKS(upload(h, &h->d_leaf_start, h->leaf_start));
+    // Chebyshev nodes and child transfers T_c[m', m] = S^parent_m(child node m')
+    std::vector<double> cheb(p), Tc((size_t)4 * r0 * r0);
+    for (int m = 0; m < p; ++m) cheb[m] = std::cos((2.0 * m + 1.0) * M_PI / (2.0 * p));
+    auto lag = [&](int m, double x) {
+        double v = 1.0;
+        for (int j = 0; j < p; ++j)
+            if (j != m) v *= (x - cheb[j]) / (cheb[m] - cheb[j]);
+        return v;
+    };
+    for (int c = 0; c < 4; ++c) {
+        int a = c & 1, b = c >> 1;
+        for (int my = 0; my < p; ++my)
+            for (int mx = 0; mx < p; ++mx) {
+                double ux = 0.5 * (cheb[mx] - 1.0) + a, uy = 0.5 * (cheb[my] - 1.0) + b;
+                for (int ny = 0; ny < p; ++ny)
+                    for (int nx = 0; nx < p; ++nx)
+                        Tc[((size_t)c * r0 + mx + p * my) * r0 + nx + p * ny] = lag(nx, ux) * lag(ny, uy);
+            }
+    }
+    CKS(upload(h, &h->d_cheb, cheb));
+    CKS(upload(h, &h->d_Tc, Tc));
+    BuildArgs ba{N, kap, p, r0, h->kernel, h->prm.kparam[0], h->prm.diag, h->prm.box[0], h->prm.box[1], h->prm.box[2]};
+    h->ops.assign(kap + 1, OpsLevel());
+    // leaf bases (W0 allocation holds 2 scratch copies behind the basis)
+    {
+        OpsLevel& O = h->ops[kap];
+        CKS(dalloc(h, &O.d_W0, sizeof(double) * 3 * (size_t)N * r0));
+        CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nleaf * r0 * r0));
+        CKS(dalloc(h, &O.d_rank0, sizeof(int) * nleaf));
+        launch_leaf_basis(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_cheb, O.d_W0, O.d_Rt,
+                          O.d_rank0, max_n, h->st);
+    }
+    for (int k = kap - 1; k >= 2; --k) {
+        OpsLevel& O = h->ops[k];
+        int nb = 1 << (2 * k);
+        CKS(dalloc(h, &O.d_W0, sizeof(double) * 4 * (size_t)nb * 4 * r0 * r0));
+        CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nb * r0 * r0));
+        CKS(dalloc(h, &O.d_rank0, sizeof(int) * nb));
+        launch_parent_basis(ba, k, h->ops[k + 1].d_Rt, h->ops[k + 1].d_rank0, h->d_Tc, O.d_W0, O.d_Rt, O.d_rank0, h->st);
+    }
+    for (int k = 2; k <= kap; ++k) {
+        OpsLevel& O = h->ops[k];
+        int nb = 1 << (2 * k);
+        CKS(dalloc(h, &O.d_far0, sizeof(double) * (size_t)nb * 36 * r0 * r0));
+        CK(cudaMemsetAsync(O.d_far0, 0, sizeof(double) * (size_t)nb * 36 * r0 * r0, h->st));
+        launch_m2l_build(ba, k, h->d_cheb, O.d_Rt, O.d_far0, h->st);
+        O.rank0.assign(nb, 0);
+        CK(cudaMemcpyAsync(O.rank0.data(), O.d_rank0, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->st));
+    }
+    // leaf P2P
+    h->p2p_off.assign((size_t)nleaf * 9, 0);
+    int64_t po = 0;
+    for (int g = 0; g < nleaf; ++g) {
+        int gx = g % side, gy = g / side;
+        for (int d = 0; d < 9; ++d) {
+            int qx = gx + d % 3 - 1, qy = gy + d / 3 - 1;
+            if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
+            h->p2p_off[(size_t)g * 9 + d] = po;
+            po += (int64_t)h->leaf_count[g] * h->leaf_count[qx + side * qy];
+        }
+    }
+    CKS(upload(h, &h->d_p2p_off, h->p2p_off));
+    CKS(dalloc(h, &h->d_p2p, sizeof(double) * (size_t)std::max<int64_t>(po, 1)));
+    double* d_sA = nullptr;
+    CKS(dalloc(h, &d_sA, sizeof(double)));
+    CK(cudaMemsetAsync(d_sA, 0, sizeof(double), h->st));
+    launch_p2p_build(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_p2p_off, h->d_p2p, d_sA, h->st);
+    CK(cudaMemcpyAsync(&h->sA, d_sA, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    dfree_ptr(h, d_sA);
+    return IFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// factor
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
+    LevelView<T> v{};
+    v.k = L.k; v.side = L.side; v.nb = L.nb; v.RC = L.RC;
+    v.n = L.d_n; v.r = L.d_r; v.voff = L.d_voff;
+    v.boff = L.d_boff; v.bld = L.d_bld; v.blk = (T*)L.d_blk; v.W = (T*)L.d_W;
+    v.pioff = L.d_pioff; v.pild = L.d_pild; v.Pi = (T*)L.d_Pi;
+    v.cpoff = L.d_cpoff; v.Cp = (T*)L.d_Cp; v.bpoff = L.d_bpoff; v.Bp = (T*)L.d_Bp;
+    v.xsoff = L.d_xsoff; v.xsld = L.d_xsld; v.Xs = (T*)L.d_Xs;
+    v.fsoff = L.d_fsoff; v.Fs = (T*)L.d_Fs; v.Fs2 = (T*)L.d_Fs2;
+    v.rsoff = L.d_rsoff; v.Rs = (T*)L.d_Rs;
+    v.pws = L.d_pws; v.psoff = L.d_psoff;
+    v.status = h->d_status; v.counters = h->d_counters;
+    v.eps = h->prm.eps;
+    v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
+    v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
+    return v;
+}
+
+template <typename T>
+ifmm_status setup_level(ifmm_handle* h, int k) {
+    const int kap = h->depth;
+    FLevel& L = h->lv[k];
+    L.k = k; L.side = 1 << k; L.nb = L.side * L.side;
+    const int s = L.side, nb = L.nb;
+    const OpsLevel& O = h->ops[k];
+    L.n.assign(nb, 0);
+    L.r0 = O.rank0;
+    L.r = O.rank0;
+    if (k == kap) {
+        L.n = h->leaf_count;
+        L.voff.assign(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) L.voff[b] = h->leaf_start[b];
+        L.voff[nb] = h->N;
+        L.vtot = h->N;
+    } else {
+        FLevel& C = h->lv[k + 1];
+        L.xoff5.assign((size_t)nb * 5, 0);
+        for (int b = 0; b < nb; ++b) {
+            int bx = b % s, by = b / s, off = 0;
+            for (int c = 0; c < 4; ++c) {
+                int cg = (2 * bx + (c & 1)) + C.side * (2 * by + (c >> 1));
+                L.xoff5[(size_t)b * 5 + c] = off;
+                off += C.r[cg];
+            }
+            L.xoff5[(size_t)b * 5 + 4] = off;
+            L.n[b] = off;
+        }
+        L.voff.assign(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) L.voff[b + 1] = L.voff[b] + L.n[b];
+        L.vtot = L.voff[nb];
+        // children's y / z rows inside this level's vectors
+        C.yoff.assign(C.nb, 0);
+        for (int cg = 0; cg < C.nb; ++cg) {
+            int cx = cg % C.side, cy = cg / C.side;
+            int P = (cx >> 1) + s * (cy >> 1), c = (cx & 1) + 2 * (cy & 1);
+            C.yoff[cg] = L.voff[P] + L.xoff5[(size_t)P * 5 + c];
+        }
+        CKS(upload(h, &C.d_yoff, C.yoff));
+    }
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) maxn = std::max(maxn, L.n[b]);
+    L.RC = h->prm.r_cap > 0 ? h->prm.r_cap : std::max(maxn, h->r0);
+    std::vector<int> cap(nb);
+    for (int b = 0; b < nb; ++b) cap[b] = std::min(L.n[b], L.RC);
+    // blocks
+    std::vector<int64_t> boff((size_t)nb * 36, -1);
+    std::vector<int> bld((size_t)nb * 36, 0);
+    int64_t bo = 0;
+    for (int b = 0; b < nb; ++b) {
+        int bx = b % s, by = b / s;
+        for (int j = 0; j < 36; ++j) {
+            int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
+            if (qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+            int q = qx + s * qy;
+            bool nbr = std::max(std::abs(qx - bx), std::abs(qy - by)) <= 1;
+            int rows = nbr ? L.n[b] : cap[b], cols = nbr ? L.n[q] : cap[q];
+            boff[(size_t)b * 36 + j] = bo;
+            bld[(size_t)b * 36 + j] = cols;
+            bo += (int64_t)rows * cols;
+        }
+    }
+    // pivot inverses, panels
+    std::vector<int64_t> pioff(nb), cpoff((size_t)nb * 9, 0), bpoff((size_t)nb * 9, 0), psoff(nb, 0);
+    std::vector<int> pild(nb);
+    int64_t pio = 0, cpo = 0, bpo = 0;
+    L.smax = 0;
+    for (int b = 0; b < nb; ++b) {
+        int sm = L.n[b] + cap[b];
+        L.smax = std::max(L.smax, sm);
+        pioff[b] = pio;
+        pild[b] = sm;
+        pio += (int64_t)sm * sm;
+        int bx = b % s, by = b / s;
+        for (int d = 0; d < 9; ++d) {
+            int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
+            if (d == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+            int q = qx + s * qy;
+            cpoff[(size_t)b * 9 + d] = cpo;
+            cpo += (int64_t)L.n[q] * L.n[b];
+            bpoff[(size_t)b * 9 + d] = bpo;
+            bpo += (int64_t)L.n[b] * L.n[q];
+        }
+    }
+    // colour lists (Morton order inside a colour)
+    std::vector<std::pair<uint64_t, int>> keys(nb);
+    for (int b = 0; b < nb; ++b) {
+        int bx = b % s, by = b / s;
+        keys[b] = {((uint64_t)((bx % 3) + 3 * (by % 3)) << 60) | morton_host(bx, by), b};
+    }
+    std::sort(keys.begin(), keys.end());
+    L.boxes.resize(nb);
+    for (int t = 0; t < nb; ++t) L.boxes[t] = keys[t].second;
+    for (int c = 0; c <= 9; ++c) L.cstart[c] = 0;
+    {
+        int t = 0;
+        for (int c = 0; c < 9; ++c) {
+            L.cstart[c] = t;
+            while (t < nb && (int)(keys[t].first >> 60) == c) ++t;
+        }
+        L.cstart[9] = nb;
+    }
+    // per-colour scratch
+    std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * 81, 0), rsoff((size_t)nb * 9, 0);
+    std::vector<int> xsld(nb, 0);
+    int64_t xs_max = 0, fs_max = 0, rs_max = 0, ps_max = 0;
+    for (int c = 0; c < 9; ++c) {
+        int64_t xo = 0, fo = 0, ro = 0, pso = 0;
+        for (int t = L.cstart[c]; t < L.cstart[c + 1]; ++t) {
+            int e = L.boxes[t], ex = e % s, ey = e / s;
+            int sm = L.n[e] + cap[e];
+            int ld = cap[e];
+            for (int d = 0; d < 9; ++d) {
+                int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+                if (d == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+                ld += L.n[qx + s * qy];
+            }
+            xsoff[e] = xo;
+            xsld[e] = ld;
+            xo += (int64_t)sm * ld;
+            psoff[e] = pso;
+            pso += (int64_t)sm * sm;
+            for (int dp = 0; dp < 9; ++dp)
+                for (int dq = 0; dq < 9; ++dq) {
+                    int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1, qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
+                    if (dp == 4 || dq == 4 || px < 0 || py < 0 || px >= s || py >= s || qx < 0 || qy < 0 || qx >= s || qy >= s)
+                        continue;
+                    if (std::max(std::abs(px - qx), std::abs(py - qy)) != 2) continue;
+                    fsoff[(size_t)e * 81 + dp * 9 + dq] = fo;
+                    fo += (int64_t)L.n[px + s * py] * L.n[qx + s * qy];
+                }
+            for (int dq = 0; dq < 9; ++dq) {
+                int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
+                if (dq == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+                int64_t mb = 0;
+                for (int dp = 0; dp < 9; ++dp) {
+                    int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+                    if (dp == 4 || px < 0 || py < 0 || px >= s || py >= s) continue;
+                    if (std::max(std::abs(px - qx), std::abs(py - qy)) == 2) mb += 2 * L.n[px + s * py];
+                }
+                rsoff[(size_t)e * 9 + dq] = ro;
+                ro += (int64_t)L.n[qx + s * qy] * mb;
+            }
+        }
+        xs_max = std::max(xs_max, xo);
+        fs_max = std::max(fs_max, fo);
+        rs_max = std::max(rs_max, ro);
+        ps_max = std::max(ps_max, pso);
+    }
+    size_t es = sizeof(T);
+    CKS(upload(h, &L.d_n, L.n));
+    CKS(upload(h, &L.d_r, L.r));
+    CKS(upload(h, &L.d_voff, L.voff));
+    CKS(upload(h, &L.d_boff, boff));
+    CKS(upload(h, &L.d_bld, bld));
+    CKS(dalloc(h, &L.d_blk, es * (size_t)bo));
+    CK(cudaMemsetAsync(L.d_blk, 0, es * (size_t)bo, h->st));
+    CKS(dalloc(h, &L.d_W, es * (size_t)L.vtot * L.RC));
+    CK(cudaMemsetAsync(L.d_W, 0, es * (size_t)L.vtot * L.RC, h->st));
+    CKS(upload(h, &L.d_pioff, pioff));
+    CKS(upload(h, &L.d_pild, pild));
+    CKS(dalloc(h, &L.d_Pi, es * (size_t)pio));
+    CKS(upload(h, &L.d_cpoff, cpoff));
+    CKS(dalloc(h, &L.d_Cp, es * (size_t)cpo));
+    CKS(upload(h, &L.d_bpoff, bpoff));
+    CKS(dalloc(h, &L.d_Bp, es * (size_t)bpo));
+    CKS(upload(h, &L.d_xsoff, xsoff));
+    CKS(upload(h, &L.d_xsld, xsld));
+    CKS(dalloc(h, &L.d_Xs, es * (size_t)xs_max));
+    CKS(upload(h, &L.d_fsoff, fsoff));
+    CKS(dalloc(h, &L.d_Fs, es * (size_t)fs_max));
+    CKS(dalloc(h, &L.d_Fs2, es * (size_t)fs_max));
+    CKS(upload(h, &L.d_rsoff, rsoff));
+    CKS(dalloc(h, &L.d_Rs, es * (size_t)rs_max));
+    CKS(upload(h, &L.d_psoff, psoff));
+    size_t full = (size_t)L.smax * 8 + (size_t)((L.smax + 1) / 2) * 8 + (size_t)L.smax * L.smax * 8;
+    if (full > 200 * 1024) CKS(dalloc(h, &L.d_pws, sizeof(double) * (size_t)ps_max));
+    CKS(upload(h, &L.d_boxes, L.boxes));
+    if (k < kap) CKS(upload(h, &L.d_xoff5, L.xoff5));
+    LevelView<T> v = view_of<T>(h, L);
+    if (k == kap) {
+        launch_init_level<T>(v, 1, h->d_p2p, h->d_p2p_off, O.d_W0, h->d_leaf_start, h->r0, nullptr, O.d_far0,
+                             O.d_rank0, nullptr, nullptr, h->st);
+    } else {
+        LevelView<T> cv = view_of<T>(h, h->lv[k + 1]);
+        launch_init_level<T>(v, 0, nullptr, nullptr, O.d_W0, nullptr, h->r0, L.d_xoff5, O.d_far0, O.d_rank0,
+                             h->ops[k + 1].d_rank0, &cv, h->st);
+    }
+    // threshold reference of the level: largest column norm of its diagonal blocks
+    double* d_sc = nullptr;
+    CKS(dalloc(h, &d_sc, sizeof(double)));
+    CK(cudaMemsetAsync(d_sc, 0, sizeof(double), h->st));
+    launch_level_scale<T>(v, d_sc, h->st);
+    CK(cudaMemcpyAsync(&L.scale, d_sc, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree_ptr(h, d_sc);
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
+template <typename T>
+void free_level_work(ifmm_handle* h, FLevel& L) {
+    dfree_ptr(h, L.d_blk);
+    dfree_ptr(h, L.d_W);
+    dfree_ptr(h, L.d_Xs);
+    dfree_ptr(h, L.d_Fs);
+    dfree_ptr(h, L.d_Fs2);
+    dfree_ptr(h, L.d_Rs);
+    dfree_ptr(h, L.d_pws);
+}
+
+void release_level(ifmm_handle* h, FLevel& L) {
+    void** ptrs[] = {(void**)&L.d_n, (void**)&L.d_r, (void**)&L.d_voff, (void**)&L.d_yoff, (void**)&L.d_boff,
+                     (void**)&L.d_bld, &L.d_blk, &L.d_W, (void**)&L.d_pioff, (void**)&L.d_pild, &L.d_Pi,
+                     (void**)&L.d_cpoff, &L.d_Cp, (void**)&L.d_bpoff, &L.d_Bp, (void**)&L.d_xsoff,
+                     (void**)&L.d_xsld, &L.d_Xs, (void**)&L.d_fsoff, &L.d_Fs, &L.d_Fs2, (void**)&L.d_rsoff,
+                     &L.d_Rs, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5};
+    for (void** p : ptrs) {
+        dfree(h, *p);
+        *p = nullptr;
+    }
+}
+
+// discard a previous factorisation (device memory and host tables)
+void release_factors(ifmm_handle* h) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    for (auto& L : h->lv) release_level(h, L);
+    h->lv.clear();
+    dfree_ptr(h, h->d_Dinv);
+    h->M = 0;
+    h->factored = false;
+}
+
+template <typename T>
+ifmm_status factor_impl(ifmm_handle* h) {
+    const int kap = h->depth;
+    h->lv.assign(kap + 1, FLevel());
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
+    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
+    const long long l0 = launches_so_far();
+    std::vector<cudaEvent_t> ev(9 * 6);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    struct EvGuard {
+        std::vector<cudaEvent_t>& v;
+        ~EvGuard() { for (auto e : v) cudaEventDestroy(e); }
+    } evg{ev};
+    double kms[5] = {0, 0, 0, 0, 0};
+    int kl[5] = {0, 0, 0, 0, 0};
+    for (int k = kap; k >= 2; --k) {
+        CKS(setup_level<T>(h, k));
+        if (k < kap) {
+            CK(cudaStreamSynchronize(h->st));
+            free_level_work<T>(h, h->lv[k + 1]);
+        }
+        FLevel& L = h->lv[k];
+        LevelView<T> v = view_of<T>(h, L);
+        bool used[9] = {false};
+        for (int c = 0; c < 9; ++c) {
+            int cnt = L.cstart[c + 1] - L.cstart[c];
+            if (cnt <= 0) continue;
+            launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->st, &ev[c * 6]);
+            used[c] = true;
+        }
+        CK(cudaGetLastError());
+        int hs = 0;
+        CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(L.r.data(), L.d_r, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (int c = 0; c < 9; ++c) {
+            if (!used[c]) continue;
+            for (int t = 0; t < 5; ++t) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev[c * 6 + t], ev[c * 6 + t + 1]));
+                kms[t] += ms;
+                kl[t] += 1;
+            }
+        }
+        if (hs & DEV_ERR_SINGULAR) {
+            h->err = "singular pivot block at level " + std::to_string(k);
+            return IFMM_ERR_SINGULAR_PIVOT;
+        }
+    }
+    // level 1: dense system over the level-2 multipoles
+    FLevel& L2 = h->lv[2];
+    L2.yoff.assign(L2.nb, 0);
+    int64_t M = 0;
+    for (int b = 0; b < L2.nb; ++b) {
+        L2.yoff[b] = M;
+        M += L2.r[b];
+    }
+    h->M = (int)M;
+    CKS(upload(h, &L2.d_yoff, L2.yoff));
+    CKS(dalloc(h, &h->d_Dinv, sizeof(double) * (size_t)std::max<int64_t>(M * M, 1)));
+    CK(cudaMemsetAsync(h->d_Dinv, 0, sizeof(double) * (size_t)M * M, h->st));
+    LevelView<T> v2 = view_of<T>(h, L2);
+    launch_root_gather<T>(v2, L2.d_yoff, h->d_Dinv, (int)M, h->st);
+    int* d_perm = nullptr;
+    double* d_col = nullptr;
+    CKS(dalloc(h, &d_perm, sizeof(int) * (size_t)std::max<int64_t>(M, 1)));
+    CKS(dalloc(h, &d_col, sizeof(double) * (size_t)std::max<int64_t>(M, 1)));
+    launch_dense_invert(h->d_Dinv, (int)M, d_perm, d_col, h->d_status, h->st);
+    int hs = 0;
+    double cnt[8];
+    CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(cnt, h->d_counters, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    dfree_ptr(h, d_perm);
+    dfree_ptr(h, d_col);
+    free_level_work<T>(h, L2);
+    if (hs & DEV_ERR_SINGULAR) {
+        h->err = "singular level-1 system";
+        return IFMM_ERR_SINGULAR_PIVOT;
+    }
+    int maxr = 0;
+    for (int k = 2; k <= kap; ++k)
+        for (int b = 0; b < h->lv[k].nb; ++b) maxr = std::max(maxr, h->lv[k].r[b]);
+    h->stats.max_rank = maxr;
+    h->stats.schur_flops = cnt[0];
+    h->stats.schur_bytes = cnt[1];
+    h->stats.factor_flops = cnt[2] + 2.0 * (double)M * M * M;
+    for (int t = 0; t < 5; ++t) {
+        h->stats.kernel_ms[t] = kms[t];
+        h->stats.kernel_launches[t] = kl[t];
+    }
+    h->stats.launches_factor = launches_so_far() - l0;
+    h->stats.rank_overflows = 0;
+    h->factored = true;
+    if (hs & DEV_ERR_OVERFLOW) {
+        h->stats.rank_overflows = 1;
+        h->err = "a box basis reached r_cap; the factorisation is usable but coarser than eps";
+        return IFMM_ERR_RANK_OVERFLOW;
+    }
+    return IFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// solve
+// ------------------------------------------------------------------------------------------------
+// in: tree-order rhs (vtot_kappa x nrhs, T) in workspace 0 ; out: tree-order x in workspace 1
+template <typename T>
+ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
+    const int kap = h->depth;
+    std::vector<T*> vr(kap + 1, nullptr), vx(kap + 1, nullptr);
+    vr[kap] = rhs_leaf;
+    vx[kap] = x_leaf;
+    int64_t maxv = 0;
+    for (int k = kap; k >= 2; --k) maxv = std::max(maxv, h->lv[k].vtot);
+    // workspace slots: 2.. hold the level vectors
+    int slot = 2;
+    for (int k = kap - 1; k >= 1; --k) {
+        int64_t len = (k >= 2) ? h->lv[k].vtot : h->M;
+        void* p1 = nullptr;
+        void* p2 = nullptr;
+        CKS(workspace(h, slot++, sizeof(T) * (size_t)std::max<int64_t>(len * nrhs, 1), &p1));
+        CKS(workspace(h, slot++, sizeof(T) * (size_t)std::max<int64_t>(len * nrhs, 1), &p2));
+        vr[k] = (T*)p1;
+        vx[k] = (T*)p2;
+    }
+    void* pv = nullptr;
+    CKS(workspace(h, slot++, sizeof(T) * (size_t)std::max<int64_t>(maxv * nrhs, 1), &pv));
+    T* vxs = (T*)pv;
+    for (int k = kap; k >= 2; --k) {
+        FLevel& L = h->lv[k];
+        LevelView<T> v = view_of<T>(h, L);
+        for (int c = 0; c < 9; ++c) {
+            int cnt = L.cstart[c + 1] - L.cstart[c];
+            launch_forward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vr[k - 1], vxs, nrhs, h->st);
+        }
+    }
+    launch_root_apply<T>(h->d_Dinv, h->M, vr[1], vx[1], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) {
+        FLevel& L = h->lv[k];
+        LevelView<T> v = view_of<T>(h, L);
+        for (int c = 8; c >= 0; --c) {
+            int cnt = L.cstart[c + 1] - L.cstart[c];
+            launch_backward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vx[k], vx[k - 1], vxs,
+                                      nrhs, h->st);
+        }
+    }
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
+template <typename T>
+ifmm_status solve_once(ifmm_handle* h, const double* b, int64_t ldb, double* x, int64_t ldx, int nrhs) {
+    void* p0 = nullptr;
+    void* p1 = nullptr;
+    CKS(workspace(h, 0, sizeof(T) * (size_t)h->N * nrhs, &p0));
+    CKS(workspace(h, 1, sizeof(T) * (size_t)h->N * nrhs, &p1));
+    launch_permute_in<T>(b, ldb, h->N, nrhs, h->d_perm, (T*)p0, h->st);
+    CKS(solve_core<T>(h, nrhs, (T*)p0, (T*)p1));
+    launch_permute_out<T>((T*)p1, h->N, nrhs, h->d_perm, x, ldx, h->st);
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
+ifmm_status matvec_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs) {
+    const int kap = h->depth, r0 = h->r0;
+    void* pxt = nullptr;
+    void* pout = nullptr;
+    CKS(workspace(h, 40, sizeof(double) * (size_t)h->N * nrhs, &pxt));
+    CKS(workspace(h, 41, sizeof(double) * (size_t)h->N * nrhs, &pout));
+    double* xt = (double*)pxt;
+    double* out = (double*)pout;
+    std::vector<double*> ym(kap + 1, nullptr), zm(kap + 1, nullptr);
+    for (int k = 2; k <= kap; ++k) {
+        size_t len = sizeof(double) * ((size_t)1 << (2 * k)) * r0 * nrhs;
+        void* a = nullptr;
+        void* b = nullptr;
+        CKS(workspace(h, 42 + 2 * k, len, &a));
+        CKS(workspace(h, 43 + 2 * k, len, &b));
+        ym[k] = (double*)a;
+        zm[k] = (double*)b;
+    }
+    launch_mv_permute_in(x, ldx, h->N, nrhs, h->d_perm, xt, h->st);
+    launch_mv_leaf_up(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up(k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l(k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down(k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
+                        h->d_p2p, out, nrhs, h->st);
+    launch_mv_permute_out(out, h->N, nrhs, h->d_perm, y, ldy, h->st);
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
+// FP64 GMRES(m) on A~ x = b, left-preconditioned by the IFMM solve M^{-1} (working precision T):
+// every column runs its own Arnoldi process, all columns in lockstep; classical Gram-Schmidt
+// applied twice; Givens rotations and the small triangular solves on the host. The monitored
+// quantity |g_{j+1}| = ||M^{-1}(b - A~ x_j)|| estimates the error of x_j since M^{-1} ~ A~^{-1}.
+template <typename T>
+ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int64_t ld) {
+    const int64_t N = h->N;
+    const int m = std::max(1, h->prm.refine_restart);
+    const double tol = h->prm.refine_tol;
+    const size_t vec = (size_t)N * nrhs;
+    void *pV = nullptr, *pu = nullptr, *pr = nullptr, *pd = nullptr;
+    CKS(workspace(h, 60, sizeof(double) * vec * (m + 1), &pV));
+    CKS(workspace(h, 61, sizeof(double) * vec, &pu));
+    CKS(workspace(h, 62, sizeof(double) * vec, &pr));
+    CKS(workspace(h, 63, sizeof(double) * (size_t)(m + 2) * nrhs * 2, &pd));
+    double* V = (double*)pV;
+    double* u = (double*)pu;
+    double* r = (double*)pr;
+    double* dv = (double*)pd;                 // device scratch: dots / norms / scales
+    std::vector<double> H((size_t)(m + 1) * m * nrhs, 0.0), cs((size_t)m * nrhs), sn((size_t)m * nrhs),
+        g((size_t)(m + 1) * nrhs), xn(nrhs, 0.0), hv((size_t)(m + 1) * nrhs), sc(nrhs);
+    auto Hat = [&](int i, int j, int c) -> double& { return H[((size_t)i * m + j) * nrhs + c]; };
+    for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(x + c * ld, 0, sizeof(double) * N, h->st));
+    int it = 0;
+    bool first = true;
+    double est = 1e300;
+    auto fetch = [&](int cnt) -> ifmm_status {
+        CK(cudaMemcpyAsync(hv.data(), dv, sizeof(double) * (size_t)cnt * nrhs, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        return IFMM_OK;
+    };
+    for (;;) {
+        // z = M^{-1} (b - A~ x)
+        if (first) {
+            CKS(solve_once<T>(h, b, ld, V, N, nrhs));
+        } else {
+            CKS(matvec_impl(h, x, ld, u, N, nrhs));
+            CK(cudaMemsetAsync(dv, 0, sizeof(double) * 2 * nrhs, h->st));
+            launch_residual(b, u, r, N, nrhs, ld, dv, h->st);
+            CKS(solve_once<T>(h, r, N, V, N, nrhs));
+        }
+        CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
+        launch_colnorm2(V, N, N, nrhs, dv, h->st);
+        CKS(fetch(1));
+        est = 0.0;
+        for (int c = 0; c < nrhs; ++c) {
+            double beta = std::sqrt(hv[c]);
+            if (first) xn[c] = beta;
+            g[c] = beta;
+            for (int i = 1; i <= m; ++i) g[(size_t)i * nrhs + c] = 0.0;
+            sc[c] = beta > 0.0 ? 1.0 / beta : 0.0;
+            est = std::max(est, xn[c] > 0.0 ? beta / xn[c] : 0.0);
+        }
+        first = false;
+        if (est <= tol || it >= h->prm.refine_maxit) break;
+        CK(cudaMemcpyAsync(dv, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, h->st));
+        launch_colscale(V, N, N, nrhs, dv, h->st);
+        std::fill(H.begin(), H.end(), 0.0);
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* Vj = V + (size_t)j * vec;
+            double* Vn = V + (size_t)(j + 1) * vec;
+            CKS(matvec_impl(h, Vj, N, u, N, nrhs));
+            CKS(solve_once<T>(h, u, N, Vn, N, nrhs));
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(cudaMemsetAsync(dv, 0, sizeof(double) * (size_t)(j + 1) * nrhs, h->st));
+                launch_krylov_dots(V, j + 1, Vn, N, nrhs, dv, h->st);
+                CKS(fetch(j + 1));
+                for (int i = 0; i <= j; ++i)
+                    for (int c = 0; c < nrhs; ++c) {
+                        Hat(i, j, c) += hv[(size_t)i * nrhs + c];
+                        hv[(size_t)i * nrhs + c] = -hv[(size_t)i * nrhs + c];
+                    }
+                CK(cudaMemcpyAsync(dv, hv.data(), sizeof(double) * (size_t)(j + 1) * nrhs, cudaMemcpyHostToDevice, h->st));
+                launch_krylov_lincomb(V, j + 1, dv, Vn, N, N, nrhs, h->st);
+            }
+            CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
+            launch_colnorm2(Vn, N, N, nrhs, dv, h->st);
+            CKS(fetch(1));
+            est = 0.0;
+            for (int c = 0; c < nrhs; ++c) {
+                double hn = std::sqrt(hv[c]);
+                sc[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+                // previous rotations on column j, then a new one zeroing H(j+1, j)
+                for (int i = 0; i < j; ++i) {
+                    double a = Hat(i, j, c), bb = Hat(i + 1, j, c);
+                    Hat(i, j, c) = cs[(size_t)i * nrhs + c] * a + sn[(size_t)i * nrhs + c] * bb;
+                    Hat(i + 1, j, c) = -sn[(size_t)i * nrhs + c] * a + cs[(size_t)i * nrhs + c] * bb;
+                }
+                double a = Hat(j, j, c);
+                double den = std::hypot(a, hn);
+                double cc = den > 0.0 ? a / den : 1.0, ss = den > 0.0 ? hn / den : 0.0;
+                cs[(size_t)j * nrhs + c] = cc;
+                sn[(size_t)j * nrhs + c] = ss;
+                Hat(j, j, c) = den;
+                double gj = g[(size_t)j * nrhs + c];
+                g[(size_t)(j + 1) * nrhs + c] = -ss * gj;
+                g[(size_t)j * nrhs + c] = cc * gj;
+                est = std::max(est, xn[c] > 0.0 ? std::fabs(g[(size_t)(j + 1) * nrhs + c]) / xn[c] : 0.0);
+            }
+            CK(cudaMemcpyAsync(dv, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, h->st));
+            launch_colscale(Vn, N, N, nrhs, dv, h->st);
+            ++it;
+            k = j + 1;
+            if (est <= tol || it >= h->prm.refine_maxit) break;
+        }
+        // y = R^{-1} g per column, x += V y
+        std::vector<double> y((size_t)k * nrhs, 0.0);
+        for (int c = 0; c < nrhs; ++c)
+            for (int i = k - 1; i >= 0; --i) {
+                double acc = g[(size_t)i * nrhs + c];
+                for (int l = i + 1; l < k; ++l) acc -= Hat(i, l, c) * y[(size_t)l * nrhs + c];
+                double d = Hat(i, i, c);
+                y[(size_t)i * nrhs + c] = d != 0.0 ? acc / d : 0.0;
+            }
+        CK(cudaMemcpyAsync(dv, y.data(), sizeof(double) * (size_t)k * nrhs, cudaMemcpyHostToDevice, h->st));
+        launch_krylov_lincomb(V, k, dv, x, ld, N, nrhs, h->st);
+        CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
+        launch_colnorm2(x, ld, N, nrhs, dv, h->st);
+        CKS(fetch(1));
+        for (int c = 0; c < nrhs; ++c) xn[c] = std::sqrt(hv[c]);
+        if (est <= tol || it >= h->prm.refine_maxit) break;
+    }
+    h->stats.refine_iters = it;
+    h->stats.last_update = est;
+    if (est > tol) {
+        h->err = "GMRES refinement stopped at refine_maxit with error estimate " + std::to_string(est);
+        return IFMM_ERR_NOCONV;
+    }
+    return IFMM_OK;
+}
+
+template <typename T>
+ifmm_status solve_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int64_t ld) {
+    const int64_t N = h->N;
+    if (h->prm.refine_tol > 0.0 && h->prm.refine_restart > 0) return gmres_impl<T>(h, b, x, nrhs, ld);
+    if (!(h->prm.refine_tol > 0.0)) {
+        CKS(solve_once<T>(h, b, ld, x, ld, nrhs));
+        h->stats.refine_iters = 1;
+        return IFMM_OK;
+    }
+    void *pr = nullptr, *pd = nullptr, *pa = nullptr, *pn = nullptr;
+    CKS(workspace(h, 30, sizeof(double) * (size_t)N * nrhs, &pr));
+    CKS(workspace(h, 31, sizeof(double) * (size_t)N * nrhs, &pd));
+    CKS(workspace(h, 32, sizeof(double) * (size_t)N * nrhs, &pa));
+    CKS(workspace(h, 33, sizeof(double) * 2 * (size_t)nrhs, &pn));
+    double* r = (double*)pr;
+    double* d = (double*)pd;
+    double* ax = (double*)pa;
+    double* nrm = (double*)pn;
+    std::vector<double> hn(2 * (size_t)nrhs);
+    for (int j = 0; j < nrhs; ++j) CK(cudaMemsetAsync(x + j * ld, 0, sizeof(double) * (size_t)N, h->st));
+    const double* rhs = b;
+    int64_t ldr = ld;
+    int it = 0;
+    double upd = 0.0;
+    for (;;) {
+        CKS(solve_once<T>(h, rhs, ldr, d, N, nrhs));
+        CK(cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * nrhs, h->st));
+        launch_axpy_norms(x, d, N, nrhs, ld, nrm, h->st);
+        CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        ++it;
+        upd = 0.0;
+        for (int j = 0; j < nrhs; ++j) upd = std::max(upd, std::sqrt(hn[2 * j] / std::max(hn[2 * j + 1], 1e-300)));
+        if (upd <= h->prm.refine_tol || it >= h->prm.refine_maxit) break;
+        CKS(matvec_impl(h, x, ld, ax, N, nrhs));
+        CK(cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * nrhs, h->st));
+        launch_residual(b, ax, r, N, nrhs, ld, nrm, h->st);
+        CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        double res = 0.0;
+        for (int j = 0; j < nrhs; ++j) res = std::max(res, std::sqrt(hn[2 * j] / std::max(hn[2 * j + 1], 1e-300)));
+        h->stats.last_residual = res;
+        rhs = r;
+        ldr = N;
+    }
+    h->stats.refine_iters = it;
+    h->stats.last_update = upd;
+    if (upd > h->prm.refine_tol) {
+        h->err = "iterative refinement stopped at refine_maxit with update " + std::to_string(upd);
+        return IFMM_ERR_NOCONV;
+    }
+    return IFMM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+void ifmm_default_params(ifmm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->depth = 3;
+    p->cheb_p = 4;
+    p->r_cap = 0;
+    p->eps = 1e-10;
+    p->diag = 1.0;
+    p->box[0] = 0.0; p->box[1] = 0.0; p->box[2] = 1.0;
+    p->precision = IFMM_FP64;
+    p->tau_ref = 1;
+    p->refine_tol = 0.0;
+    p->refine_maxit = 100;
+    p->refine_restart = 30;
+}
+
+ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm_params* p, void* stream,
+                       ifmm_h* out) {
+    if (out) *out = nullptr;
+    if (!pts_host || !p || !out || N <= 0 || N >= (1ll << 31)) return IFMM_ERR_INVALID_ARG;
+    if (p->dim != 2 || p->depth < 2 || p->depth > 10 || p->cheb_p < 1 || p->cheb_p > 8) return IFMM_ERR_INVALID_ARG;
+    if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP) return IFMM_ERR_INVALID_ARG;
+    if (kernel == IFMM_K_EXP && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
+    if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
+    if (p->precision != IFMM_FP64 && p->precision != IFMM_MIXED) return IFMM_ERR_INVALID_ARG;
+    if (p->tau_ref < 0 || p->tau_ref > 2) return IFMM_ERR_INVALID_ARG;
+    if (p->r_cap > 0 && p->r_cap < p->cheb_p * p->cheb_p) return IFMM_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < 2 * N; ++i)
+        if (!std::isfinite(pts_host[i])) return IFMM_ERR_INVALID_ARG;
+    ifmm_handle* h = new ifmm_handle();
+    h->prm = *p;
+    if (!(h->prm.box[2] > 0.0)) { h->prm.box[0] = 0.0; h->prm.box[1] = 0.0; h->prm.box[2] = 1.0; }
+    if (h->prm.refine_maxit <= 0) h->prm.refine_maxit = 100;
+    if (h->prm.refine_restart < 0 || h->prm.refine_restart > 200) {
+        delete h;
+        return IFMM_ERR_INVALID_ARG;
+    }
+    h->kernel = kernel;
+    h->N = N;
+    h->depth = p->depth;
+    h->p = p->cheb_p;
+    h->r0 = p->cheb_p * p->cheb_p;
+    h->st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    ifmm_status s = do_build(h, pts_host);
+    if (s != IFMM_OK) {
+        ifmm_destroy(h);
+        return s;
+    }
+    h->stats.t_build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->stats.n_points = N;
+    h->stats.depth = h->depth;
+    *out = h;
+    return IFMM_OK;
+}
+
+ifmm_status ifmm_factor(ifmm_h h) {
+    if (!h) return IFMM_ERR_INVALID_ARG;
+    h->err.clear();
+    release_factors(h);
+    auto t0 = std::chrono::steady_clock::now();
+    ifmm_status s = h->prm.precision == IFMM_MIXED ? factor_impl<float>(h) : factor_impl<double>(h);
+    h->stats.t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (s != IFMM_OK && s != IFMM_ERR_RANK_OVERFLOW) h->factored = false;
+    return s;
+}
+
+ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld) {
+    if (!h || !b_dev || !x_dev || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    if (!h->factored) {
+        h->err = "ifmm_solve before ifmm_factor";
+        return IFMM_ERR_STATE;
+    }
+    h->err.clear();
+    auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launches_so_far();
+    ifmm_status s = h->prm.precision == IFMM_MIXED ? solve_impl<float>(h, b_dev, x_dev, nrhs, ld)
+                                                   : solve_impl<double>(h, b_dev, x_dev, nrhs, ld);
+    h->stats.launches_solve = launches_so_far() - l0;
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (s == IFMM_OK && e != cudaSuccess) {
+        h->err = std::string("solve: ") + cudaGetErrorString(e);
+        s = IFMM_ERR_CUDA;
+    }
+    h->stats.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld) {
+    if (!h || !b_host || !x_host || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    if (!h->factored) {
+        h->err = "ifmm_solve_host before ifmm_factor";
+        return IFMM_ERR_STATE;
+    }
+    void *pb = nullptr, *px = nullptr;
+    CKS(workspace(h, 80, sizeof(double) * (size_t)h->N * nrhs, &pb));
+    CKS(workspace(h, 81, sizeof(double) * (size_t)h->N * nrhs, &px));
+    for (int j = 0; j < nrhs; ++j)
+        CK(cudaMemcpyAsync((double*)pb + (size_t)j * h->N, b_host + (size_t)j * ld, sizeof(double) * h->N,
+                           cudaMemcpyHostToDevice, h->st));
+    ifmm_status s = ifmm_solve(h, (double*)pb, (double*)px, nrhs, h->N);
+    if (s != IFMM_OK && s != IFMM_ERR_NOCONV) return s;
+    for (int j = 0; j < nrhs; ++j)
+        CK(cudaMemcpyAsync(x_host + (size_t)j * ld, (double*)px + (size_t)j * h->N, sizeof(double) * h->N,
+                           cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return s;
+}
+
+ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld) {
+    if (!h || !x_dev || !y_dev || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    h->err.clear();
+    CKS(matvec_impl(h, x_dev, ld, y_dev, ld, nrhs));
+    CK(cudaStreamSynchronize(h->st));
+    return IFMM_OK;
+}
+
+ifmm_status ifmm_get_ranks(ifmm_h h, int level, int* out_host) {
+    if (!h || !out_host || level < 2 || level > h->depth) return IFMM_ERR_INVALID_ARG;
+    if (!h->factored) return IFMM_ERR_STATE;
+    const FLevel& L = h->lv[level];
+    std::copy(L.r.begin(), L.r.end(), out_host);
+    return IFMM_OK;
+}
+
+ifmm_status ifmm_get_stats(ifmm_h h, ifmm_stats* s) {
+    if (!h || !s) return IFMM_ERR_INVALID_ARG;
+    h->stats.device_bytes = h->bytes;
+    *s = h->stats;
+    return IFMM_OK;
+}
+
+const char* ifmm_last_error(ifmm_h h) { return h ? h->err.c_str() : "null handle"; }
+
+void ifmm_destroy(ifmm_h h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    for (auto& a : h->allocs) cudaFree(a.first);
+    delete h;
+}
+
+}  // extern "C"

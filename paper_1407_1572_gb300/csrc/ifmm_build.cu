@@ -1,0 +1,627 @@
+// ifmm_build.cu -- tree, Chebyshev operators and the FP64 FMM matvec, sm_103a.
+//
+// Build (assembly time t_a of Table "table_notations"):
+//   points -> leaf keys (Morton code of the leaf, Section 4.2: uniform 2^d tree, Morton order)
+//   -> bitonic sort -> tree order, leaf counts;
+//   leaf bases V_b[a, m] = S_m(x_a), the tensor Lagrange basis at p x p first-kind Chebyshev
+//   nodes of the leaf (Section 5), orthonormalised by column-pivoted Householder QR, V = Q Rt;
+//   parent bases: the stacked children transfers Rt_c T_c (T_c[m', m] = parent basis m at child
+//   node m'), orthonormalised the same way;
+//   M2L_bq = Rt_b K(nodes_b, nodes_q) Rt_q^T for q in the interaction list I_b;
+//   leaf P2P_bq = K(x_a, x_c) for q in N_b, with the diagonal A_aa on the same point.
+// Matvec y = A~ x (Table "table_FMM_operators"): P2M, M2M, M2L, L2L, L2P and P2P in FP64.
+#include <cstdio>
+
+#include "ifmm_common.cuh"
+#include "ifmm_internal.h"
+
+namespace ifmm {
+
+IFMM_DEVINL bool in_grid2(int x, int y, int side) { return x >= 0 && y >= 0 && x < side && y < side; }
+
+IFMM_DEVINL unsigned long long spread_bits(unsigned v) {
+    unsigned long long x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+IFMM_DEVINL unsigned compact_bits(unsigned long long x) {
+    x &= 0x5555555555555555ull;
+    x = (x | (x >> 1)) & 0x3333333333333333ull;
+    x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+    return (unsigned)x;
+}
+
+IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay, double bx, double by) {
+    double dx = ax - bx, dy = ay - by;
+    double r = sqrt(dx * dx + dy * dy);
+    if (kernel == 0) return 1.0 / r;
+    return exp(-r / kparam0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// tree
+// ---------------------------------------------------------------------------------------------
+__global__ void k_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
+                            unsigned long long* keys, int64_t npad, int* status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npad) return;
+    if (t >= N) { keys[t] = ~0ull; return; }
+    const int side = 1 << depth;
+    double ux = (pts[2 * t] - x0) / L, uy = (pts[2 * t + 1] - y0) / L;
+    if (!(ux >= 0.0 && ux <= 1.0 && uy >= 0.0 && uy <= 1.0)) {
+        atomicOr(status, DEV_ERR_RANGE);
+        ux = fmin(fmax(ux, 0.0), 1.0);
+        uy = fmin(fmax(uy, 0.0), 1.0);
+    }
+    int ix = min((int)floor(ux * side), side - 1), iy = min((int)floor(uy * side), side - 1);
+    unsigned long long m = spread_bits((unsigned)ix) | (spread_bits((unsigned)iy) << 1);
+    keys[t] = (m << 32) | (unsigned long long)t;
+}
+
+void launch_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
+                      unsigned long long* keys, int64_t npad, int* status, cudaStream_t st) {
+    k_leaf_keys<<<(unsigned)((npad + 255) / 256), 256, 0, st>>>(pts, N, depth, x0, y0, L, keys, npad, status); count_launches(1);
+}
+
+__global__ void k_bitonic_step(unsigned long long* keys, int64_t npad, int64_t j, int64_t k) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    int64_t l = i ^ j;
+    if (l <= i) return;
+    unsigned long long a = keys[i], b = keys[l];
+    bool up = (i & k) == 0;
+    if ((a > b) == up) { keys[i] = b; keys[l] = a; }
+}
+
+// in-block stages (j < 1024) of the bitonic network in shared memory
+__global__ void k_bitonic_local(unsigned long long* keys, int64_t npad, int64_t k, int64_t jstart) {
+    __shared__ unsigned long long s[2048];
+    const int64_t base = (int64_t)blockIdx.x * 2048;
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) s[t] = keys[base + t];
+    __syncthreads();
+    for (int64_t j = jstart; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+            int64_t i = base + t, l = i ^ j;
+            if (l > i) {
+                int tl = (int)(l - base);
+                unsigned long long a = s[t], b = s[tl];
+                bool up = (i & k) == 0;
+                if ((a > b) == up) { s[t] = b; s[tl] = a; }
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) keys[base + t] = s[t];
+}
+
+void launch_bitonic_sort(unsigned long long* keys, int64_t npad, cudaStream_t st) {
+    for (int64_t k = 2; k <= npad; k <<= 1) {
+        int64_t j = k >> 1;
+        for (; j >= 1024 && j >= 1; j >>= 1)
+            { k_bitonic_step<<<(unsigned)((npad + 255) / 256), 256, 0, st>>>(keys, npad, j, k); count_launches(1); }
+        if (j >= 1) {
+            if (npad >= 2048)
+                { k_bitonic_local<<<(unsigned)(npad / 2048), 1024, 0, st>>>(keys, npad, k, j); count_launches(1); }
+            else
+                for (; j >= 1; j >>= 1)
+                    { k_bitonic_step<<<(unsigned)((npad + 255) / 256), 256, 0, st>>>(keys, npad, j, k); count_launches(1); }
+        }
+    }
+}
+
+__global__ void k_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
+                                 double* px, double* py, int* leaf_count, int depth) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    unsigned long long key = keys[t];
+    int64_t idx = (int64_t)(key & 0xffffffffull);
+    unsigned long long m = key >> 32;
+    int ix = (int)compact_bits(m), iy = (int)compact_bits(m >> 1);
+    perm[t] = idx;
+    px[t] = pts[2 * idx];
+    py[t] = pts[2 * idx + 1];
+    atomicAdd(&leaf_count[ix + (1 << depth) * iy], 1);
+}
+
+void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
+                           double* px, double* py, int* leaf_count, int depth, cudaStream_t st) {
+    k_scatter_sorted<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(keys, pts, N, perm, px, py, leaf_count, depth); count_launches(1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// bases
+// ---------------------------------------------------------------------------------------------
+IFMM_DEVINL double lagrange1(int p, const double* t, int m, double x) {
+    double v = 1.0;
+    for (int j = 0; j < p; ++j)
+        if (j != m) v *= (x - t[j]) / (t[m] - t[j]);
+    return v;
+}
+
+// per leaf: V (n x r0) -> Q (rows of W0 in tree order), Rt, rank. Scratch in global memory:
+// Ascr (n x r0) and Vscr (reflectors) at the leaf's tree rows.
+__global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const double* px, const double* py,
+                                                         const int64_t* leaf_start, const int* leaf_count,
+                                                         const double* cheb, double* W0, double* Rt, int* rank0,
+                                                         double* Ascr, double* Vscr) {
+    __shared__ double red[32];
+    __shared__ int ired[32];
+    __shared__ double beta[64];
+    __shared__ int cperm[64];
+    const int b = blockIdx.x;
+    const int side = 1 << a.depth;
+    const int bx = b % side, by = b / side;
+    const int n = leaf_count[b];
+    const int64_t s0 = leaf_start[b];
+    const int p = a.p, r0 = a.r0;
+    const double h = a.L / side;
+    const double lx = a.x0 + bx * h, ly = a.y0 + by * h;
+    double* A = Ascr + s0 * r0;
+    for (int t = threadIdx.x; t < n * r0; t += blockDim.x) {
+        int i = t / r0, m = t - i * r0;
+        int mx = m % p, my = m / p;
+        double ux = 2.0 * (px[s0 + i] - lx) / h - 1.0, uy = 2.0 * (py[s0 + i] - ly) / h - 1.0;
+        A[(size_t)i * r0 + m] = lagrange1(p, cheb, mx, ux) * lagrange1(p, cheb, my, uy);
+    }
+    double* R = Rt + (int64_t)b * r0 * r0;
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) R[t] = 0.0;
+    double* Q = W0 + s0 * r0;
+    for (int t = threadIdx.x; t < n * r0; t += blockDim.x) Q[t] = 0.0;
+    __syncthreads();
+    int rank = 0;
+    if (n > 0) rank = cta_cpqr(A, n, r0, r0, 1e-13, Q, r0, R, r0, Vscr + s0 * r0, beta, cperm, red, ired);
+    if (threadIdx.x == 0) rank0[b] = rank;
+}
+
+void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
+                       const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
+                       int max_n, cudaStream_t st) {
+    (void)max_n;
+    // scratch lives in the second half of W0's allocation (the caller allocates 3 N r0 doubles)
+    double* Ascr = W0 + a.N * a.r0;
+    double* Vscr = W0 + 2 * a.N * a.r0;
+    k_leaf_basis<<<1 << (2 * a.depth), kThreads, 0, st>>>(a, px, py, leaf_start, leaf_count, cheb, W0, Rt, rank0,
+                                                          Ascr, Vscr); count_launches(1);
+}
+
+// per parent P at level k: Z stacks the rows (Rt_c T_c)[t, :], t < rank_c, of the four children
+// (Morton order) -> Z = Q Rt_P; Q is scattered into W0_P with rows c*r0 + t (zero rows for the
+// components a child does not have). Scratch: Z, reflectors and the compact Q, each 4 r0 x r0 per box,
+// in the tail of the level's W0 allocation.
+__global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, const double* Rt_child,
+                                                           const int* rank_child, const double* Tc, double* W0,
+                                                           double* Rt, int* rank0, double* Zscr, double* Vscr,
+                                                           double* Qscr) {
+    __shared__ double red[32];
+    __shared__ int ired[32];
+    __shared__ double beta[64];
+    __shared__ int cperm[64];
+    const int b = blockIdx.x;
+    const int side = 1 << k, cs = side << 1;
+    const int bx = b % side, by = b / side;
+    const int r0 = a.r0;
+    int cg[4], off[5];
+    off[0] = 0;
+    for (int c = 0; c < 4; ++c) {
+        cg[c] = (2 * bx + (c & 1)) + cs * (2 * by + (c >> 1));
+        off[c + 1] = off[c] + rank_child[cg[c]];
+    }
+    const int m = off[4];
+    double* Z = Zscr + (int64_t)b * 4 * r0 * r0;
+    for (int t = threadIdx.x; t < m * r0; t += blockDim.x) {
+        int row = t / r0, col = t - row * r0;
+        int c = 0;
+        while (row >= off[c + 1]) ++c;
+        int i = row - off[c];
+        const double* Rc = Rt_child + (int64_t)cg[c] * r0 * r0;
+        const double* T = Tc + (int64_t)c * r0 * r0;
+        double v = 0.0;
+        for (int l = 0; l < r0; ++l) v += Rc[(size_t)i * r0 + l] * T[(size_t)l * r0 + col];
+        Z[t] = v;
+    }
+    double* R = Rt + (int64_t)b * r0 * r0;
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) R[t] = 0.0;
+    double* W = W0 + (int64_t)b * 4 * r0 * r0;
+    for (int t = threadIdx.x; t < 4 * r0 * r0; t += blockDim.x) W[t] = 0.0;
+    double* Q = Qscr + (int64_t)b * 4 * r0 * r0;
+    __syncthreads();
+    int rank = 0;
+    if (m > 0) rank = cta_cpqr(Z, m, r0, r0, 1e-13, Q, r0, R, r0, Vscr + (int64_t)b * 4 * r0 * r0, beta, cperm, red, ired);
+    for (int t = threadIdx.x; t < m * rank; t += blockDim.x) {
+        int row = t / rank, j = t - row * rank;
+        int c = 0;
+        while (row >= off[c + 1]) ++c;
+        W[(size_t)(c * r0 + row - off[c]) * r0 + j] = Q[(size_t)row * r0 + j];
+    }
+    if (threadIdx.x == 0) rank0[b] = rank;
+}
+
+void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
+                         const double* Tc, double* W0, double* Rt, int* rank0, cudaStream_t st) {
+    int64_t nb = 1ll << (2 * k);
+    double* Zscr = W0 + nb * 4 * a.r0 * a.r0;
+    double* Vscr = W0 + 2 * nb * 4 * a.r0 * a.r0;
+    double* Qscr = W0 + 3 * nb * 4 * a.r0 * a.r0;
+    k_parent_basis<<<(unsigned)nb, kThreads, 0, st>>>(a, k, Rt_child, rank_child, Tc, W0, Rt, rank0, Zscr, Vscr,
+                                                      Qscr); count_launches(1);
+}
+
+// M2L_bq = Rt_b K(nodes_b, nodes_q) Rt_q^T for q in the interaction list of b
+__global__ void __launch_bounds__(kThreads) k_m2l_build(BuildArgs a, int k, const double* cheb, const double* Rt,
+                                                        double* far0) {
+    extern __shared__ double msm[];  // Kc (r0 x r0), tmp (r0 x r0)
+    const int b = blockIdx.x, j = blockIdx.y;
+    const int side = 1 << k;
+    const int bx = b % side, by = b / side;
+    const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
+    const int r0 = a.r0, p = a.p;
+    double* out = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+    if (!in_grid2(qx, qy, side) || max(abs(qx - bx), abs(qy - by)) <= 1) return;
+    const int q = qx + side * qy;
+    const double h = a.L / side;
+    double* Kc = msm;
+    double* tmp = msm + r0 * r0;
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) {
+        int m = t / r0, l = t - m * r0;
+        double ax = a.x0 + (bx + 0.5 * (cheb[m % p] + 1.0)) * h, ay = a.y0 + (by + 0.5 * (cheb[m / p] + 1.0)) * h;
+        double cx = a.x0 + (qx + 0.5 * (cheb[l % p] + 1.0)) * h, cy = a.y0 + (qy + 0.5 * (cheb[l / p] + 1.0)) * h;
+        Kc[t] = kernel_eval(a.kernel, a.kparam0, ax, ay, cx, cy);
+    }
+    __syncthreads();
+    const double* Rb = Rt + (int64_t)b * r0 * r0;
+    const double* Rq = Rt + (int64_t)q * r0 * r0;
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) {  // tmp = Rb Kc
+        int i = t / r0, l = t - i * r0;
+        double s = 0.0;
+        for (int m = 0; m < r0; ++m) s += Rb[(size_t)i * r0 + m] * Kc[(size_t)m * r0 + l];
+        tmp[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) {  // out = tmp Rq^T
+        int i = t / r0, jj = t - i * r0;
+        double s = 0.0;
+        for (int l = 0; l < r0; ++l) s += tmp[(size_t)i * r0 + l] * Rq[(size_t)jj * r0 + l];
+        out[t] = s;
+    }
+}
+
+void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const double* Rt, double* far0,
+                      cudaStream_t st) {
+    size_t smem = 2 * (size_t)a.r0 * a.r0 * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_m2l_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr = true;
+    }
+    k_m2l_build<<<dim3(1u << (2 * k), 36), kThreads, smem, st>>>(a, k, cheb, Rt, far0); count_launches(1);
+}
+
+// leaf P2P blocks and the matrix scale s_A (largest column norm of the diagonal blocks)
+__global__ void __launch_bounds__(kThreads) k_p2p_build(BuildArgs a, const double* px, const double* py,
+                                                        const int64_t* leaf_start, const int* leaf_count,
+                                                        const int64_t* p2p_off, double* p2p,
+                                                        unsigned long long* sA_bits) {
+    const int b = blockIdx.x, d = blockIdx.y;
+    const int side = 1 << a.depth;
+    const int bx = b % side, by = b / side;
+    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
+    if (!in_grid2(qx, qy, side)) return;
+    const int q = qx + side * qy;
+    const int nb_ = leaf_count[b], nq = leaf_count[q];
+    const int64_t sb = leaf_start[b], sq = leaf_start[q];
+    double* out = p2p + p2p_off[(int64_t)b * 9 + d];
+    for (int t = threadIdx.x; t < nb_ * nq; t += blockDim.x) {
+        int i = t / nq, j = t - i * nq;
+        double v = (b == q && i == j) ? a.diag : kernel_eval(a.kernel, a.kparam0, px[sb + i], py[sb + i], px[sq + j], py[sq + j]);
+        out[t] = v;
+    }
+    if (d != 4) return;
+    __syncthreads();
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < nb_; ++i) s += out[(size_t)i * nq + j] * out[(size_t)i * nq + j];
+        mx = fmax(mx, sqrt(s));
+    }
+    if (mx > 0.0) atomicMax(sA_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
+                      const int* leaf_count, const int64_t* p2p_off, double* p2p, double* sA_bits,
+                      cudaStream_t st) {
+    k_p2p_build<<<dim3(1u << (2 * a.depth), 9), kThreads, 0, st>>>(a, px, py, leaf_start, leaf_count, p2p_off, p2p,
+                                                                   reinterpret_cast<unsigned long long*>(sA_bits)); count_launches(1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 matvec
+// ---------------------------------------------------------------------------------------------
+__global__ void k_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    int64_t i = t / nrhs;
+    int j = (int)(t - i * nrhs);
+    xt[t] = x[perm[i] + (int64_t)j * ld];
+}
+void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt,
+                          cudaStream_t st) {
+    k_mv_permute_in<<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(x, ld, N, nrhs, perm, xt); count_launches(1);
+}
+
+__global__ void k_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    int64_t i = t / nrhs;
+    int j = (int)(t - i * nrhs);
+    y[perm[i] + (int64_t)j * ld] = yt[t];
+}
+void launch_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
+                           cudaStream_t st) {
+    k_mv_permute_out<<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(yt, N, nrhs, perm, y, ld); count_launches(1);
+}
+
+// P2M: y_b = W0_b^T x_b   (y layout [box][r0][nrhs])
+__global__ void __launch_bounds__(kThreads) k_mv_leaf_up(const double* W0, const int64_t* leaf_start,
+                                                         const int* leaf_count, int r0, const double* xt, double* y,
+                                                         int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int b = blockIdx.x;
+    const int64_t s0 = leaf_start[b];
+    const int n = leaf_count[b];
+    const double* W = W0 + s0 * r0;
+    const double* xb = xt + s0 * nrhs;
+    double* yb = y + (int64_t)b * r0 * nrhs;
+    cta_gemm<double>(
+        r0, nrhs, n, [&](int i, int k) { return W[(size_t)k * r0 + i]; },
+        [&](int k, int j) { return xb[(size_t)k * nrhs + j]; },
+        [&](int i, int j, double v) { yb[(size_t)i * nrhs + j] = v; }, sm);
+}
+void launch_mv_leaf_up(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                       const double* xt, double* y, int nrhs, cudaStream_t st) {
+    k_mv_leaf_up<<<1u << (2 * depth), kThreads, 0, st>>>(W0, leaf_start, leaf_count, r0, xt, y, nrhs); count_launches(1);
+}
+
+// M2M: y_P = W0_P^T [y_c]  (W0_P rows c*r0 + t)
+__global__ void __launch_bounds__(kThreads) k_mv_up(int k, const double* W0, int r0, const double* ychild, double* y,
+                                                    int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int b = blockIdx.x;
+    const int side = 1 << k, cs = side << 1;
+    const int bx = b % side, by = b / side;
+    const double* W = W0 + (int64_t)b * 4 * r0 * r0;
+    double* yb = y + (int64_t)b * r0 * nrhs;
+    cta_gemm<double>(
+        r0, nrhs, 4 * r0, [&](int i, int kk) { return W[(size_t)kk * r0 + i]; },
+        [&](int kk, int j) {
+            int c = kk / r0, t = kk - c * r0;
+            int cg = (2 * bx + (c & 1)) + cs * (2 * by + (c >> 1));
+            return ychild[((int64_t)cg * r0 + t) * nrhs + j];
+        },
+        [&](int i, int j, double v) { yb[(size_t)i * nrhs + j] = v; }, sm);
+}
+void launch_mv_up(int k, const double* W0, int r0, const double* ychild, double* y, int nrhs, cudaStream_t st) {
+    k_mv_up<<<1u << (2 * k), kThreads, 0, st>>>(k, W0, r0, ychild, y, nrhs); count_launches(1);
+}
+
+// M2L: z_b = sum_{q in I_b} M2L_bq y_q
+__global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const double* far0, int r0, const double* y, double* z,
+                                                     int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int b = blockIdx.x;
+    const int side = 1 << k;
+    const int bx = b % side, by = b / side;
+    double* zb = z + (int64_t)b * r0 * nrhs;
+    for (int t = threadIdx.x; t < r0 * nrhs; t += blockDim.x) zb[t] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < 36; ++j) {
+        const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
+        if (!in_grid2(qx, qy, side) || max(abs(qx - bx), abs(qy - by)) <= 1) continue;
+        const int q = qx + side * qy;
+        const double* M = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+        const double* yq = y + (int64_t)q * r0 * nrhs;
+        cta_gemm<double>(
+            r0, nrhs, r0, [&](int i, int kk) { return M[(size_t)i * r0 + kk]; },
+            [&](int kk, int jj) { return yq[(size_t)kk * nrhs + jj]; },
+            [&](int i, int jj, double v) { zb[(size_t)i * nrhs + jj] += v; }, sm);
+        __syncthreads();
+    }
+}
+void launch_mv_m2l(int k, const double* far0, int r0, const double* y, double* z, int nrhs, cudaStream_t st) {
+    k_mv_m2l<<<1u << (2 * k), kThreads, 0, st>>>(k, far0, r0, y, z, nrhs); count_launches(1);
+}
+
+// L2L: z_c += W0_P[rows of c] z_P, one block per child box c at level k+1
+__global__ void __launch_bounds__(kThreads) k_mv_down(int k, const double* W0, int r0, const double* z,
+                                                      double* zchild, int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int cgi = blockIdx.x;
+    const int cs = 2 << k;
+    const int cx = cgi % cs, cy = cgi / cs;
+    const int P = (cx >> 1) + (cs >> 1) * (cy >> 1);
+    const int c = (cx & 1) + 2 * (cy & 1);
+    const double* W = W0 + ((int64_t)P * 4 + c) * r0 * r0;
+    const double* zP = z + (int64_t)P * r0 * nrhs;
+    double* zc = zchild + (int64_t)cgi * r0 * nrhs;
+    cta_gemm<double>(
+        r0, nrhs, r0, [&](int i, int kk) { return W[(size_t)i * r0 + kk]; },
+        [&](int kk, int j) { return zP[(size_t)kk * nrhs + j]; },
+        [&](int i, int j, double v) { zc[(size_t)i * nrhs + j] += v; }, sm);
+}
+void launch_mv_down(int k, const double* W0, int r0, const double* z, double* zchild, int nrhs, cudaStream_t st) {
+    k_mv_down<<<1u << (2 * (k + 1)), kThreads, 0, st>>>(k, W0, r0, z, zchild, nrhs); count_launches(1);
+}
+
+// L2P + P2P: out_b = W0_b z_b + sum_{q in N_b} P2P_bq x_q
+__global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start,
+                                                           const int* leaf_count, int r0, const double* z,
+                                                           const double* xt, const int64_t* p2p_off,
+                                                           const double* p2p, double* out, int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int b = blockIdx.x;
+    const int side = 1 << depth;
+    const int bx = b % side, by = b / side;
+    const int64_t s0 = leaf_start[b];
+    const int n = leaf_count[b];
+    const double* W = W0 + s0 * r0;
+    const double* zb = z + (int64_t)b * r0 * nrhs;
+    double* ob = out + s0 * nrhs;
+    cta_gemm<double>(
+        n, nrhs, r0, [&](int i, int kk) { return W[(size_t)i * r0 + kk]; },
+        [&](int kk, int j) { return zb[(size_t)kk * nrhs + j]; },
+        [&](int i, int j, double v) { ob[(size_t)i * nrhs + j] = v; }, sm);
+    __syncthreads();
+    for (int d = 0; d < 9; ++d) {
+        const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
+        if (!in_grid2(qx, qy, side)) continue;
+        const int q = qx + side * qy;
+        const int nq = leaf_count[q];
+        const double* B = p2p + p2p_off[(int64_t)b * 9 + d];
+        const double* xq = xt + leaf_start[q] * nrhs;
+        cta_gemm<double>(
+            n, nrhs, nq, [&](int i, int kk) { return B[(size_t)i * nq + kk]; },
+            [&](int kk, int j) { return xq[(size_t)kk * nrhs + j]; },
+            [&](int i, int j, double v) { ob[(size_t)i * nrhs + j] += v; }, sm);
+        __syncthreads();
+    }
+}
+void launch_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                         const double* z, const double* xt, const int64_t* p2p_off, const double* p2p,
+                         double* out, int nrhs, cudaStream_t st) {
+    k_mv_leaf_down<<<1u << (2 * depth), kThreads, 0, st>>>(depth, W0, leaf_start, leaf_count, r0, z, xt, p2p_off, p2p,
+                                                           out, nrhs); count_launches(1);
+}
+
+// x += d (d with leading dimension N); nrm[2j] += ||d_j||^2, nrm[2j+1] += ||x_j||^2 (x after the update)
+__global__ void k_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm) {
+    __shared__ double red[32];
+    const int j = blockIdx.y;
+    double sd = 0.0, sx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double dv = d[i + j * N];
+        double xv = x[i + j * ld] + dv;
+        x[i + j * ld] = xv;
+        sd += dv * dv;
+        sx += xv * xv;
+    }
+    sd = block_sum(sd, red);
+    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j], sd);
+    sx = block_sum(sx, red);
+    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j + 1], sx);
+}
+void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    k_axpy_norms<<<dim3(gx, nrhs), 256, 0, st>>>(x, d, N, nrhs, ld, nrm); count_launches(1);
+}
+
+// r = b - ax; nrm[2j] += ||r_j||^2, nrm[2j+1] += ||b_j||^2
+__global__ void k_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld, double* nrm) {
+    __shared__ double red[32];
+    const int j = blockIdx.y;
+    double sr = 0.0, sb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double bv = b[i + j * ld];
+        double rv = bv - ax[i + j * N];
+        r[i + j * N] = rv;
+        sr += rv * rv;
+        sb += bv * bv;
+    }
+    sr = block_sum(sr, red);
+    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j], sr);
+    sb = block_sum(sb, red);
+    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j + 1], sb);
+}
+void launch_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld, double* nrm,
+                     cudaStream_t st) {
+    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    k_residual<<<dim3(gx, nrhs), 256, 0, st>>>(b, ax, r, N, nrhs, ld, nrm); count_launches(1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 Krylov vector kernels for the refinement (all nrhs columns at once, column-major, ld N)
+// ---------------------------------------------------------------------------------------------
+// out[i * nrhs + c] += sum_n V_i[n, c] w[n, c] for i < cnt (V_i = V + i * N * nrhs)
+__global__ void __launch_bounds__(256) k_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs,
+                                                     double* out) {
+    __shared__ double red[32];
+    constexpr int PER = 16;
+    const int c = blockIdx.y;
+    const int64_t n0 = (int64_t)blockIdx.x * 256 * PER;
+    double wv[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        int64_t n = n0 + threadIdx.x + 256 * t;
+        wv[t] = n < N ? w[n + (int64_t)c * N] : 0.0;
+    }
+    for (int i = 0; i < cnt; ++i) {
+        const double* v = V + (int64_t)i * N * nrhs + (int64_t)c * N;
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            int64_t n = n0 + threadIdx.x + 256 * t;
+            if (n < N) s += v[n] * wv[t];
+        }
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) atomicAdd(&out[i * nrhs + c], s);
+    }
+}
+void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out,
+                        cudaStream_t st) {
+    k_krylov_dots<<<dim3((unsigned)((N + 4095) / 4096), nrhs), 256, 0, st>>>(V, cnt, w, N, nrhs, out);
+    count_launches(1);
+}
+
+// y[n + c * ldy] += sum_i coef[i * nrhs + c] V_i[n, c]
+__global__ void k_krylov_lincomb(const double* V, int cnt, const double* coef, double* y, int64_t ldy, int64_t N,
+                                 int nrhs) {
+    const int c = blockIdx.y;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < cnt; ++i) acc += coef[i * nrhs + c] * V[(int64_t)i * N * nrhs + (int64_t)c * N + n];
+        y[n + (int64_t)c * ldy] += acc;
+    }
+}
+void launch_krylov_lincomb(const double* V, int cnt, const double* coef, double* y, int64_t ldy, int64_t N, int nrhs,
+                           cudaStream_t st) {
+    int gx = (int)std::min<int64_t>((N + 255) / 256, 2048);
+    k_krylov_lincomb<<<dim3(gx, nrhs), 256, 0, st>>>(V, cnt, coef, y, ldy, N, nrhs);
+    count_launches(1);
+}
+
+// out[c] += ||y[:, c]||^2 ; then optionally y[:, c] *= scale[c]
+__global__ void k_colnorm2(const double* y, int64_t ldy, int64_t N, double* out) {
+    __shared__ double red[32];
+    const int c = blockIdx.y;
+    double s = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        double v = y[n + (int64_t)c * ldy];
+        s += v * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) atomicAdd(&out[c], s);
+}
+void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    k_colnorm2<<<dim3(gx, nrhs), 256, 0, st>>>(y, ldy, N, out);
+    count_launches(1);
+}
+
+__global__ void k_colscale(double* y, int64_t ldy, int64_t N, const double* scale) {
+    const int c = blockIdx.y;
+    const double s = scale[c];
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        y[n + (int64_t)c * ldy] *= s;
+}
+void launch_colscale(double* y, int64_t ldy, int64_t N, int nrhs, const double* scale, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>((N + 255) / 256, 2048);
+    k_colscale<<<dim3(gx, nrhs), 256, 0, st>>>(y, ldy, N, scale);
+    count_launches(1);
+}
+
+}  // namespace ifmm

@@ -1,0 +1,304 @@
+// ifmm_common.cuh -- device helpers shared by the CUDA kernels of the IFMM library (sm_103a).
+//
+// CTA-wide reductions, a tiled CTA GEMM with functor loaders and epilogue, in-place
+// Gauss-Jordan inversion with partial pivoting, and Householder QR with column pivoting.
+// Everything here runs inside one thread block; the callers give each block one box.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define IFMM_DEVINL __device__ __forceinline__
+
+namespace ifmm {
+
+constexpr int kThreads = 256;  // block size of every per-box kernel
+
+IFMM_DEVINL int colour_of(int ix, int iy) { return (ix % 3) + 3 * (iy % 3); }
+
+// index of box (qx, qy) in the 6 x 6 grid made of the children of the 3 x 3 neighbourhood of
+// p's parent; every neighbour and every interaction-list box of p lies in it
+IFMM_DEVINL int region36(int px, int py, int qx, int qy) {
+    return (qx - 2 * (px >> 1) + 2) + 6 * (qy - 2 * (py >> 1) + 2);
+}
+
+template <typename T>
+IFMM_DEVINL T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the block; `red` holds >= 32 entries of shared scratch
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    return s;
+}
+
+template <typename T>
+__device__ T block_max(T v, T* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T s = red[0];
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 1; i < nw; ++i) s = fmax(s, red[i]);
+    return s;
+}
+
+// argmax of v over the block with ties to the lowest index; returns the index (or -1 when every
+// thread passed idx < 0). vred/ired: >= 32 entries of shared scratch each.
+__device__ inline int block_argmax(double v, int idx, double* vred, int* ired, double* vout) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) { v = ov; idx = oi; }
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { vred[w] = v; ired[w] = idx; }
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    double bv = vred[0];
+    int bi = ired[0];
+    for (int i = 1; i < nw; ++i) {
+        int oi = ired[i];
+        double ov = vred[i];
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (vout) *vout = bv;
+    return bi;
+}
+
+// ---------------------------------------------------------------------------------------------
+// CTA GEMM: for (i, j) in [0, M) x [0, N): epi(i, j, sum_k la(i, k) * lb(k, j)).
+// 256 threads, 64 x 64 output tiles, k-steps of 16, 4 x 4 outputs per thread, accumulation in
+// Acc. `smem` must hold 2 * 16 * 65 Acc.
+// ---------------------------------------------------------------------------------------------
+template <typename Acc, class LA, class LB, class EPI>
+__device__ void cta_gemm(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem) {
+    constexpr int BM = 64, BN = 64, BK = 16, LDS = 65;
+    Acc* As = smem;             // [BK][LDS] : As[k][i]
+    Acc* Bs = smem + BK * LDS;  // [BK][LDS] : Bs[k][j]
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int m0 = 0; m0 < M; m0 += BM)
+        for (int n0 = 0; n0 < N; n0 += BN) {
+            Acc acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = Acc(0);
+            for (int k0 = 0; k0 < K; k0 += BK) {
+                // A tile: 64 rows x 16 k; thread t loads rows t/16 + 16 q, k = t % 16
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int ii = (tid >> 4) + 16 * q, kk = tid & 15;
+                    int gi = m0 + ii, gk = k0 + kk;
+                    As[kk * LDS + ii] = (gi < M && gk < K) ? Acc(la(gi, gk)) : Acc(0);
+                }
+                // B tile: 16 k x 64 cols; thread t loads k = t / 64 + 4 q, col = t % 64
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int kk = (tid >> 6) + 4 * q, jj = tid & 63;
+                    int gk = k0 + kk, gj = n0 + jj;
+                    Bs[kk * LDS + jj] = (gk < K && gj < N) ? Acc(lb(gk, gj)) : Acc(0);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    Acc av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = As[kk * LDS + ty + 16 * a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * LDS + tx + 16 * b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    int gi = m0 + ty + 16 * a, gj = n0 + tx + 16 * b;
+                    if (gi < M && gj < N) epi(gi, gj, acc[a][b]);
+                }
+        }
+}
+
+// ---------------------------------------------------------------------------------------------
+// In-place inversion of the s x s matrix A (leading dimension lda, FP64) by Gauss-Jordan
+// elimination with partial pivoting (ties to the lowest row). perm: s ints of scratch, col: s
+// doubles of scratch (shared or global). Returns false if a pivot column is exactly zero.
+// ---------------------------------------------------------------------------------------------
+__device__ inline bool cta_gauss_jordan(double* A, int s, int lda, int* perm, double* col, double* vred,
+                                        int* ired) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double s_piv;
+    __shared__ int s_ok;
+    for (int k = 0; k < s; ++k) {
+        double best = -1.0;
+        int bi = -1;
+        for (int i = k + tid; i < s; i += nt) {
+            double v = fabs(A[(size_t)i * lda + k]);
+            if (bi < 0 || v > best) { best = v; bi = i; }
+        }
+        double bv;
+        int p = block_argmax(best, bi, vred, ired, &bv);
+        if (tid == 0) {
+            perm[k] = p;
+            s_ok = (p >= 0 && bv > 0.0 && isfinite(bv)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return false;
+        if (p != k)
+            for (int j = tid; j < s; j += nt) {
+                double t = A[(size_t)k * lda + j];
+                A[(size_t)k * lda + j] = A[(size_t)p * lda + j];
+                A[(size_t)p * lda + j] = t;
+            }
+        __syncthreads();
+        if (tid == 0) s_piv = A[(size_t)k * lda + k];
+        __syncthreads();
+        double d = 1.0 / s_piv;
+        for (int j = tid; j < s; j += nt) {
+            if (j == k) A[(size_t)k * lda + k] = d;
+            else A[(size_t)k * lda + j] *= d;
+        }
+        for (int i = tid; i < s; i += nt) col[i] = A[(size_t)i * lda + k];
+        __syncthreads();
+        // rows i != k: A[i][j] -= col[i] * A[k][j] (j != k); A[i][k] = -col[i] * d
+        for (int t = tid; t < s * s; t += nt) {
+            int i = t / s, j = t - i * s;
+            if (i == k) continue;
+            if (j == k) A[(size_t)i * lda + k] = -col[i] * d;
+            else A[(size_t)i * lda + j] -= col[i] * A[(size_t)k * lda + j];
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = s - 1; k >= 0; --k) {
+        int p = perm[k];
+        if (p != k)
+            for (int i = tid; i < s; i += nt) {
+                double t = A[(size_t)i * lda + k];
+                A[(size_t)i * lda + k] = A[(size_t)i * lda + p];
+                A[(size_t)i * lda + p] = t;
+            }
+        __syncthreads();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Householder QR with column pivoting of the m x nc matrix A (FP64, leading dimension lda,
+// overwritten). Columns are taken while the largest remaining column norm exceeds
+// tol * (largest column norm of A); ties go to the lowest column. On return Q (m x rank, ldq)
+// holds orthonormal columns, Rt (rank x nc, ldr) with A = Q Rt, and the rank is returned.
+// Scratch: vbuf (m doubles per reflector, rank reflectors: m * min(m, nc)), beta (nc), cperm (nc),
+// red (>= 32 doubles), ired (>= 32 ints).
+// ---------------------------------------------------------------------------------------------
+__device__ inline int cta_cpqr(double* A, int m, int nc, int lda, double tol, double* Q, int ldq,
+                               double* Rt, int ldr, double* vbuf, double* beta, int* cperm, double* red,
+                               int* ired) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    __shared__ double s_first, s_alpha, s_beta;
+    __shared__ int s_rank;
+    for (int j = tid; j < nc; j += nt) cperm[j] = j;
+    if (tid == 0) { s_first = -1.0; s_rank = 0; }
+    __syncthreads();
+    int kmax = m < nc ? m : nc;
+    int rank = 0;
+    for (int k = 0; k < kmax; ++k) {
+        // norms of the remaining columns, one warp per column
+        double best = -1.0;
+        int bi = -1;
+        for (int j = k + warp; j < nc; j += nw) {
+            double s = 0.0;
+            for (int i = k + lane; i < m; i += 32) s += A[(size_t)i * lda + j] * A[(size_t)i * lda + j];
+            s = warp_sum(s);
+            double v = sqrt(s);
+            if (bi < 0 || v > best) { best = v; bi = j; }
+        }
+        if (lane != 0) bi = -1;
+        double bv;
+        int jb = block_argmax(best, bi, red, ired, &bv);
+        if (tid == 0 && s_first < 0.0) s_first = bv;
+        __syncthreads();
+        if (!(bv > tol * s_first) || bv == 0.0) break;
+        if (jb != k) {
+            for (int i = tid; i < m; i += nt) {
+                double t = A[(size_t)i * lda + k];
+                A[(size_t)i * lda + k] = A[(size_t)i * lda + jb];
+                A[(size_t)i * lda + jb] = t;
+            }
+            if (tid == 0) { int t = cperm[k]; cperm[k] = cperm[jb]; cperm[jb] = t; }
+        }
+        __syncthreads();
+        double* v = vbuf + (size_t)k * m;
+        for (int i = tid; i < m; i += nt) v[i] = (i >= k) ? A[(size_t)i * lda + k] : 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            double alpha = v[k] >= 0.0 ? -bv : bv;
+            v[k] -= alpha;
+            s_alpha = alpha;
+        }
+        __syncthreads();
+        double vtv = 0.0;
+        for (int i = k + tid; i < m; i += nt) vtv += v[i] * v[i];
+        vtv = block_sum(vtv, red);
+        if (tid == 0) { s_beta = vtv > 0.0 ? 2.0 / vtv : 0.0; beta[k] = s_beta; }
+        __syncthreads();
+        double bt = s_beta;
+        // apply H = I - beta v v^T to columns k..nc-1, one warp per column
+        for (int j = k + warp; j < nc; j += nw) {
+            double s = 0.0;
+            for (int i = k + lane; i < m; i += 32) s += v[i] * A[(size_t)i * lda + j];
+            s = warp_sum(s) * bt;
+            for (int i = k + lane; i < m; i += 32) A[(size_t)i * lda + j] -= s * v[i];
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < m; i += nt) A[(size_t)i * lda + k] = 0.0;
+        if (tid == 0) A[(size_t)k * lda + k] = s_alpha;
+        ++rank;
+        __syncthreads();
+    }
+    // Q = H_0 ... H_{rank-1} [I; 0]
+    for (int t = tid; t < m * rank; t += nt) {
+        int i = t / rank, j = t - i * rank;
+        Q[(size_t)i * ldq + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int k = rank - 1; k >= 0; --k) {
+        const double* v = vbuf + (size_t)k * m;
+        double bt = beta[k];
+        for (int j = warp; j < rank; j += nw) {
+            double s = 0.0;
+            for (int i = k + lane; i < m; i += 32) s += v[i] * Q[(size_t)i * ldq + j];
+            s = warp_sum(s) * bt;
+            for (int i = k + lane; i < m; i += 32) Q[(size_t)i * ldq + j] -= s * v[i];
+        }
+        __syncthreads();
+    }
+    // Rt[:, cperm[j]] = R[0:rank, j]
+    for (int t = tid; t < rank * nc; t += nt) {
+        int i = t / nc, j = t - i * nc;
+        Rt[(size_t)i * ldr + cperm[j]] = A[(size_t)i * lda + j];
+    }
+    __syncthreads();
+    return rank;
+}
+
+}  // namespace ifmm

@@ -1,0 +1,830 @@
+// ifmm_factor.cu -- elimination (Algorithm 1) and replay (Algorithm 2) kernels, sm_103a.
+//
+// One colour of one level is eliminated by five launches over the boxes of that colour
+// (colour = (ix mod 3) + 3 (iy mod 3): boxes of one colour are at Chebyshev distance >= 3, so
+// their neighbourhoods N_e, and every block they touch, are disjoint):
+//   k_pivot    form Piv_e = [[P2P_ee, L2P_ee], [P2M_ee, 0]] (rows P2P(e,k), P2M(e,k), columns
+//              x_e, z_e) and invert it in FP64 (Gauss-Jordan, partial pivoting);
+//   k_panel    X = Piv_e^{-1} [B; 0] for every neighbour column block (B = row P2P_e at the
+//              neighbour's active unknown) and for y_e; save the B and C panels for the solve;
+//   k_schur    Schur complement A[rho, gamma] -= C_rho X_gamma over the neighbour pairs: dense
+//              update of neighbour blocks, well-separated fill written out for compression;
+//   k_compress per uneliminated neighbour q: extend its basis W_q by the directions of its
+//              well-separated fill that W_q misses (pivoted Gram-Schmidt with threshold);
+//   k_redirect write each well-separated fill through the bases into M2L_pq
+//              (Algorithm 1: P2P_pq = L2P_pp M2L_pq P2M_qq, P2L_pq = M2L_pq P2M_qq,
+//              M2P_pq = L2P_pp M2L_pq).
+// T is the storage type of blocks, bases and panels (double, or float in the mixed form).
+#include <cstdio>
+
+#include "ifmm_common.cuh"
+#include "ifmm_internal.h"
+
+namespace ifmm {
+
+static long long g_launches = 0;
+void count_launches(int n) { g_launches += n; }
+long long launches_so_far() { return g_launches; }
+
+template <typename T> struct AccOf { using type = double; };
+template <> struct AccOf<float> { using type = float; };
+
+IFMM_DEVINL bool in_grid(int x, int y, int side) { return x >= 0 && y >= 0 && x < side && y < side; }
+
+template <typename T>
+IFMM_DEVINL T* block_at(const LevelView<T>& L, int p, int q, int& ld) {
+    int px = p % L.side, py = p / L.side, qx = q % L.side, qy = q / L.side;
+    int j = region36(px, py, qx, qy);
+    int64_t o = L.boff[(int64_t)p * 36 + j];
+    ld = L.bld[(int64_t)p * 36 + j];
+    return o < 0 ? nullptr : L.blk + o;
+}
+
+// column offset inside X of the block of neighbour direction dsel (dsel == 4: the y_e block)
+template <typename T>
+IFMM_DEVINL int xcol_offset(const LevelView<T>& L, int ex, int ey, int dsel) {
+    int off = 0;
+    for (int d = 0; d < 9; ++d) {
+        if (d == 4) continue;
+        if (d == dsel) return off;
+        int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+        if (in_grid(qx, qy, L.side)) off += L.n[qx + L.side * qy];
+    }
+    return off;
+}
+
+// active width of box b while eliminating colour c: r_b once eliminated, n_b before
+template <typename T>
+IFMM_DEVINL int active_width(const LevelView<T>& L, int b, int colour) {
+    int bx = b % L.side, by = b / L.side;
+    return colour_of(bx, by) < colour ? L.r[b] : L.n[b];
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_pivot: Piv_e^{-1} in FP64
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* boxes, int smax, int use_smem) {
+    extern __shared__ double dsm[];
+    __shared__ double vred[32];
+    __shared__ int ired[32];
+    const int e = boxes[blockIdx.x];
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    if (s == 0) return;
+    double* col = dsm;
+    int* perm = reinterpret_cast<int*>(dsm + smax);
+    double* A = use_smem ? dsm + smax + (smax + 1) / 2 : L.pws + L.psoff[e];
+    int ldp;
+    const T* Pee = block_at(L, e, e, ldp);
+    const T* We = L.W + L.voff[e] * L.RC;
+    const int RC = L.RC;
+    // balancing a = largest column norm of P2P_ee: the block is inverted as
+    // Piv_s = [[P2P_ee, a W], [a W^T, 0]] and Piv^{-1} = S Piv_s^{-1} S, S = diag(I_n, a I_r)
+    double cmax = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = (double)Pee[(size_t)i * ldp + j];
+            c += v * v;
+        }
+        cmax = fmax(cmax, sqrt(c));
+    }
+    double alpha = block_max(cmax, vred);
+    if (!(alpha > 0.0)) alpha = 1.0;
+    for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+        int i = t / s, j = t - i * s;
+        double v;
+        if (i < n && j < n) v = (double)Pee[(size_t)i * ldp + j];
+        else if (i < n) v = alpha * (double)We[(size_t)i * RC + (j - n)];
+        else if (j < n) v = alpha * (double)We[(size_t)j * RC + (i - n)];
+        else v = 0.0;
+        A[(size_t)i * s + j] = v;
+    }
+    __syncthreads();
+    bool ok = cta_gauss_jordan(A, s, s, perm, col, vred, ired);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(L.status, DEV_ERR_SINGULAR);
+        return;
+    }
+    T* Pi = L.Pi + L.pioff[e];
+    const int ld = L.pild[e];
+    for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+        int i = t / s, j = t - i * s;
+        double sc = (i >= n ? alpha : 1.0) * (j >= n ? alpha : 1.0);
+        Pi[(size_t)i * ld + j] = (T)(sc * A[(size_t)i * s + j]);
+    }
+    if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_panel: X = Pi_e[:, 0:n] B_q for each neighbour q, X_y = -Pi_e[:, n:s]; panels for the solve
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* boxes, int colour) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int d = blockIdx.y;
+    const int ex = e % L.side, ey = e / L.side;
+    const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+    if (!in_grid(qx, qy, L.side)) return;
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    T* X = L.Xs + L.xsoff[e];
+    const int ldx = L.xsld[e];
+    const T* Pi = L.Pi + L.pioff[e];
+    const int ldpi = L.pild[e];
+    if (d == 4) {
+        int cy = xcol_offset(L, ex, ey, 4);
+        for (int t = threadIdx.x; t < s * r; t += blockDim.x) {
+            int i = t / r, j = t - i * r;
+            X[(size_t)i * ldx + cy + j] = -Pi[(size_t)i * ldpi + n + j];
+        }
+        return;
+    }
+    const int q = qx + L.side * qy;
+    const int wq = active_width(L, q, colour);
+    int ldb;
+    const T* B = block_at(L, e, q, ldb);
+    // B panel (row P2P_e at q's active unknown), n x wq, kept for the back substitution
+    T* Bp = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+    for (int t = threadIdx.x; t < n * wq; t += blockDim.x) {
+        int i = t / wq, j = t - i * wq;
+        Bp[t] = B[(size_t)i * ldb + j];
+    }
+    // C panel (q's active equation at x_e), wq x n, kept for the forward replay and the Schur step
+    int ldc;
+    const T* C = block_at(L, q, e, ldc);
+    T* Cp = L.Cp + L.cpoff[(int64_t)e * 9 + d];
+    for (int t = threadIdx.x; t < wq * n; t += blockDim.x) {
+        int i = t / n, j = t - i * n;
+        Cp[t] = C[(size_t)i * ldc + j];
+    }
+    const int cx = xcol_offset(L, ex, ey, d);
+    cta_gemm<Acc>(
+        s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
+        [&](int k, int j) { return B[(size_t)k * ldb + j]; },
+        [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm);
+    if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * s * (double)wq * n);
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_schur: one (p, q) pair of neighbours of e per block (p, q in N_e; dp == 4 is row M2L_e)
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
+    const int ex = e % L.side, ey = e / L.side;
+    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
+    if (!in_grid(px, py, L.side) || !in_grid(qx, qy, L.side)) return;
+    const int p = px + L.side * py, q = qx + L.side * qy;
+    const int n = L.n[e], r = L.r[e];
+    const T* X = L.Xs + L.xsoff[e];
+    const int ldx = L.xsld[e];
+    if (dp == 4) {
+        // row M2L_e has -I at z_e: A[M2L_e, gamma] = X_gamma[z rows]
+        int ld;
+        T* dst = block_at(L, e, q, ld);
+        const int w = (dq == 4) ? r : active_width(L, q, colour);
+        const int cx = xcol_offset(L, ex, ey, dq);
+        for (int t = threadIdx.x; t < r * w; t += blockDim.x) {
+            int i = t / w, j = t - i * w;
+            dst[(size_t)i * ld + j] = X[(size_t)(n + i) * ldx + cx + j];
+        }
+        return;
+    }
+    const int wp = active_width(L, p, colour);
+    const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
+    const int cx = xcol_offset(L, ex, ey, dq);
+    if (dq == 4) {
+        // new column y_e in row rho_p: M2P_pe or M2L_pe = -C_p X_y[x rows]
+        int ld;
+        T* dst = block_at(L, p, e, ld);
+        cta_gemm<Acc>(
+            wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm);
+        if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * wp * (double)r * n);
+        return;
+    }
+    const int wq = active_width(L, q, colour);
+    const int dist = max(abs(px - qx), abs(py - qy));
+    const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
+    if (dist <= 1 || (Ep && Eq)) {
+        // neighbours: dense update in place; both eliminated: M2L_pq updated directly
+        int ld;
+        T* dst = block_at(L, p, q, ld);
+        cta_gemm<Acc>(
+            wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v); }, sm);
+    } else {
+        T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
+        cta_gemm<Acc>(
+            wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+            [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm);
+    }
+    if (threadIdx.x == 0) {
+        double fl = 2.0 * wp * (double)wq * n;
+        atomicAdd(&L.counters[0], fl);
+        atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * wq + 2.0 * wp * wq));
+        atomicAdd(&L.counters[2], fl);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_compress: extend W_q for the well-separated fill of uneliminated neighbour q of e
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int* boxes, int colour) {
+    using Acc = typename AccOf<T>::type;
+    extern __shared__ double csm[];  // u (nq) then per-warp coefficients (8 * RC)
+    __shared__ double vred[32];
+    __shared__ int ired[32];
+    __shared__ double s_val;
+    __shared__ int s_flag;
+    const int e = boxes[blockIdx.x];
+    const int dq = blockIdx.y;
+    if (dq == 4) return;
+    const int ex = e % L.side, ey = e / L.side;
+    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
+    if (!in_grid(qx, qy, L.side) || colour_of(qx, qy) < colour) return;
+    const int q = qx + L.side * qy;
+    int parts[8], np = 0;
+    for (int dp = 0; dp < 9; ++dp) {
+        if (dp == 4 || dp == dq) continue;
+        int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+        if (!in_grid(px, py, L.side)) continue;
+        if (max(abs(px - qx), abs(py - qy)) == 2) parts[np++] = dp;
+    }
+    if (np == 0) return;
+    const int nq = L.n[q];
+    const int rq0 = L.r[q];
+    const int RC = L.RC;
+    int wps[8], m = 0;
+    for (int t = 0; t < np; ++t) {
+        int dp = parts[t];
+        int p = (ex + dp % 3 - 1) + L.side * (ey + dp / 3 - 1);
+        wps[t] = active_width(L, p, colour);
+        m += 2 * wps[t];
+    }
+    if (nq == 0 || m == 0) return;
+    T* R = L.Rs + L.rsoff[(int64_t)e * 9 + dq];
+    // S_q = [F_qp (nq x wp), F_pq^T (nq x wp)] over the partners p
+    {
+        int c0 = 0;
+        for (int t = 0; t < np; ++t) {
+            int dp = parts[t], wp = wps[t];
+            const T* Fc = L.Fs + L.fsoff[(int64_t)e * 81 + dq * 9 + dp];  // nq x wp
+            const T* Fr = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];  // wp x nq
+            for (int u = threadIdx.x; u < nq * wp; u += blockDim.x) {
+                int i = u / wp, j = u - i * wp;
+                R[(size_t)i * m + c0 + j] = Fc[(size_t)i * wp + j];
+                R[(size_t)i * m + c0 + wp + j] = Fr[(size_t)j * nq + i];
+            }
+            c0 += 2 * wp;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // reference norm: largest column norm of S_q
+    double mloc = 0.0;
+    for (int j = warp; j < m; j += nw) {
+        double s = 0.0;
+        for (int i = lane; i < nq; i += 32) { double v = (double)R[(size_t)i * m + j]; s += v * v; }
+        s = warp_sum(s);
+        mloc = fmax(mloc, sqrt(s));
+    }
+    const double smax = block_max(mloc, vred);
+    if (!(smax > 0.0)) return;
+    const double tau = L.eps * (L.tau_ref == 1 ? L.sA : smax);
+    T* W = L.W + L.voff[q] * RC;
+    double* coef = csm + nq;  // 8 warps x RC
+    // R <- (I - W W^T) R, twice (classical Gram-Schmidt per column)
+    for (int pass = 0; pass < 2 && rq0 > 0; ++pass) {
+        for (int j = warp; j < m; j += nw) {
+            double* c = coef + warp * RC;
+            for (int t = 0; t < rq0; ++t) {
+                Acc s = 0;
+                for (int i = lane; i < nq; i += 32) s += (Acc)W[(size_t)i * RC + t] * (Acc)R[(size_t)i * m + j];
+                s = warp_sum(s);
+                if (lane == 0) c[t] = (double)s;
+            }
+            __syncwarp();
+            for (int i = lane; i < nq; i += 32) {
+                Acc acc = (Acc)R[(size_t)i * m + j];
+                for (int t = 0; t < rq0; ++t) acc -= (Acc)W[(size_t)i * RC + t] * (Acc)c[t];
+                R[(size_t)i * m + j] = (T)acc;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    const int limit = min(nq, RC);
+    double* u = csm;
+    int add = 0;
+    for (;;) {
+        double best = -1.0;
+        int bi = -1;
+        for (int j = warp; j < m; j += nw) {
+            Acc s = 0;
+            for (int i = lane; i < nq; i += 32) { Acc v = (Acc)R[(size_t)i * m + j]; s += v * v; }
+            s = warp_sum(s);
+            double v = sqrt((double)s);
+            if (bi < 0 || v > best) { best = v; bi = j; }
+        }
+        if (lane != 0) bi = -1;
+        double bv;
+        int jb = block_argmax(best, bi, vred, ired, &bv);
+        if (!(bv > tau) || jb < 0) break;
+        if (rq0 + add >= limit) {
+            if (limit < nq && threadIdx.x == 0) atomicOr(L.status, DEV_ERR_OVERFLOW);
+            break;
+        }
+        const int rc = rq0 + add;
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = (double)R[(size_t)i * m + jb] / bv;
+        __syncthreads();
+        // re-orthogonalise u against the current basis, twice
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int t = warp; t < rc; t += nw) {
+                double s = 0.0;
+                for (int i = lane; i < nq; i += 32) s += (double)W[(size_t)i * RC + t] * u[i];
+                s = warp_sum(s);
+                if (lane == 0) coef[t] = s;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+                double acc = u[i];
+                for (int t = 0; t < rc; ++t) acc -= (double)W[(size_t)i * RC + t] * coef[t];
+                u[i] = acc;
+            }
+            __syncthreads();
+        }
+        double nn = 0.0;
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) nn += u[i] * u[i];
+        nn = block_sum(nn, vred);
+        const double nu = sqrt(nn);
+        if (!(nu >= 0.5)) {
+            // numerically inside the current span: drop this column
+            for (int i = threadIdx.x; i < nq; i += blockDim.x) R[(size_t)i * m + jb] = (T)0;
+            __syncthreads();
+            continue;
+        }
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            u[i] /= nu;
+            W[(size_t)i * RC + rc] = (T)u[i];
+        }
+        __syncthreads();
+        for (int j = warp; j < m; j += nw) {
+            Acc s = 0;
+            for (int i = lane; i < nq; i += 32) s += (Acc)u[i] * (Acc)R[(size_t)i * m + j];
+            s = warp_sum(s);
+            for (int i = lane; i < nq; i += 32) R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - s * (Acc)u[i]);
+        }
+        __syncthreads();
+        ++add;
+    }
+    if (threadIdx.x == 0) {
+        L.r[q] = rq0 + add;
+        atomicAdd(&L.counters[2], 8.0 * (double)nq * m * (rq0 + 1) + 6.0 * (double)nq * m * add);
+    }
+    (void)s_val;
+    (void)s_flag;
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_redirect: M2L_pq += (W_p^T) F (W_q) for a well-separated pair with fill
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int* boxes, int colour) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
+    if (dp == 4 || dq == 4 || dp == dq) return;
+    const int ex = e % L.side, ey = e / L.side;
+    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
+    if (!in_grid(px, py, L.side) || !in_grid(qx, qy, L.side)) return;
+    if (max(abs(px - qx), abs(py - qy)) != 2) return;
+    const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
+    if (Ep && Eq) return;
+    const int p = px + L.side * py, q = qx + L.side * qy;
+    const int wp = Ep ? L.r[p] : L.n[p];
+    const int wq = Eq ? L.r[q] : L.n[q];
+    const int rp = L.r[p], rq = L.r[q];
+    const int RC = L.RC;
+    const int64_t fo = L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
+    const T* F = L.Fs + fo;   // wp x wq
+    T* F2 = L.Fs2 + fo;       // wp x rq
+    int ld;
+    T* M = block_at(L, p, q, ld);
+    const T* Wq = L.W + L.voff[q] * RC;
+    const T* Wp = L.W + L.voff[p] * RC;
+    const T* T1 = F;
+    int ld1 = wq;
+    if (!Eq) {
+        cta_gemm<Acc>(
+            wp, rq, wq, [&](int i, int k) { return F[(size_t)i * wq + k]; },
+            [&](int k, int j) { return Wq[(size_t)k * RC + j]; },
+            [&](int i, int j, Acc v) { F2[(size_t)i * rq + j] = (T)v; }, sm);
+        __syncthreads();
+        T1 = F2;
+        ld1 = rq;
+    }
+    if (!Ep) {
+        cta_gemm<Acc>(
+            rp, rq, wp, [&](int i, int k) { return Wp[(size_t)k * RC + i]; },
+            [&](int k, int j) { return T1[(size_t)k * ld1 + j]; },
+            [&](int i, int j, Acc v) { M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + v); }, sm);
+    } else {
+        for (int t = threadIdx.x; t < rp * rq; t += blockDim.x) {
+            int i = t / rq, j = t - i * rq;
+            M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + (Acc)T1[(size_t)i * ld1 + j]);
+        }
+    }
+    if (threadIdx.x == 0)
+        atomicAdd(&L.counters[2], 2.0 * wp * (double)rq * wq * (Eq ? 0 : 1) + 2.0 * rp * (double)rq * wp * (Ep ? 0 : 1));
+}
+
+template <typename T>
+void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smax,
+                          cudaStream_t st, cudaEvent_t* ev) {
+    if (nboxes <= 0) return;
+    size_t base = (size_t)smax * sizeof(double) + (size_t)((smax + 1) / 2) * sizeof(double);
+    size_t full = base + (size_t)smax * smax * sizeof(double);
+    int use_smem = full <= 200 * 1024 ? 1 : 0;
+    size_t smem = use_smem ? full : base;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        cudaFuncSetAttribute(k_pivot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+        cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_set[sizeof(T) == 8] = true;
+    }
+    if (ev) cudaEventRecord(ev[0], st);
+    k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
+    if (ev) cudaEventRecord(ev[1], st);
+    k_panel<T><<<dim3(nboxes, 9), kThreads, 0, st>>>(L, boxes, colour);
+    if (ev) cudaEventRecord(ev[2], st);
+    k_schur<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    if (ev) cudaEventRecord(ev[3], st);
+    size_t csmem = (size_t)(smax + 8 * L.RC) * sizeof(double);
+    k_compress<T><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+    if (ev) cudaEventRecord(ev[4], st);
+    k_redirect<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    if (ev) cudaEventRecord(ev[5], st);
+    count_launches(5);
+}
+
+// ---------------------------------------------------------------------------------------------
+// level set-up: leaf P2P, or the non-leaf P2P from the children's M2L (Remark in Section 4.2:
+// P2P_ij^(k) = [M2L_{i_a j_b}^(k+1)]); W from the orthonormalised operators; initial M2L
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_init_p2p_leaf(LevelView<T> L, const double* p2p0, const int64_t* p2p0_off) {
+    const int b = blockIdx.x, d = blockIdx.y;
+    const int bx = b % L.side, by = b / L.side;
+    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
+    if (!in_grid(qx, qy, L.side)) return;
+    const int q = qx + L.side * qy;
+    int ld;
+    T* dst = block_at(L, b, q, ld);
+    const double* src = p2p0 + p2p0_off[(int64_t)b * 9 + d];
+    const int nb_ = L.n[b], nq = L.n[q];
+    for (int t = threadIdx.x; t < nb_ * nq; t += blockDim.x) {
+        int i = t / nq, j = t - i * nq;
+        dst[(size_t)i * ld + j] = (T)src[(size_t)i * nq + j];
+    }
+}
+
+template <typename T>
+__global__ void k_init_p2p_parent(LevelView<T> L, LevelView<T> C, const int* xoff5) {
+    const int b = blockIdx.x, d = blockIdx.y / 16, ab = blockIdx.y % 16;
+    const int a = ab / 4, bb = ab % 4;
+    const int bx = b % L.side, by = b / L.side;
+    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
+    if (!in_grid(qx, qy, L.side)) return;
+    const int q = qx + L.side * qy;
+    const int ca = (2 * bx + (a & 1)) + C.side * (2 * by + (a >> 1));
+    const int db = (2 * qx + (bb & 1)) + C.side * (2 * qy + (bb >> 1));
+    int lds;
+    const T* src = block_at(C, ca, db, lds);
+    if (!src) return;
+    int ld;
+    T* dst = block_at(L, b, q, ld);
+    const int ro = xoff5[b * 5 + a], co = xoff5[q * 5 + bb];
+    const int rr = C.r[ca], rc = C.r[db];
+    for (int t = threadIdx.x; t < rr * rc; t += blockDim.x) {
+        int i = t / rc, j = t - i * rc;
+        dst[(size_t)(ro + i) * ld + co + j] = src[(size_t)i * lds + j];
+    }
+}
+
+template <typename T>
+__global__ void k_init_far(LevelView<T> L, const double* far0, const int* rank0, int r0) {
+    const int b = blockIdx.x, j = blockIdx.y;
+    const int bx = b % L.side, by = b / L.side;
+    const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
+    if (!in_grid(qx, qy, L.side)) return;
+    if (max(abs(qx - bx), abs(qy - by)) <= 1) return;
+    const int q = qx + L.side * qy;
+    const int64_t o = L.boff[(int64_t)b * 36 + j];
+    if (o < 0) return;
+    T* dst = L.blk + o;
+    const int ld = L.bld[(int64_t)b * 36 + j];
+    const double* src = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+    const int rb = rank0[b], rq = rank0[q];
+    for (int t = threadIdx.x; t < rb * rq; t += blockDim.x) {
+        int i = t / rq, jj = t - i * rq;
+        dst[(size_t)i * ld + jj] = (T)src[(size_t)i * r0 + jj];
+    }
+}
+
+template <typename T>
+__global__ void k_init_w(LevelView<T> L, int is_leaf, const double* W0, const int64_t* w0_rowoff, int r0,
+                         const int* xoff5, const int* rank_child, int child_side) {
+    const int b = blockIdx.x;
+    const int RC = L.RC;
+    T* W = L.W + L.voff[b] * RC;
+    const int rb = L.r[b];
+    if (is_leaf) {
+        const double* src = W0 + w0_rowoff[b] * r0;
+        const int n = L.n[b];
+        for (int t = threadIdx.x; t < n * rb; t += blockDim.x) {
+            int i = t / rb, j = t - i * rb;
+            W[(size_t)i * RC + j] = (T)src[(size_t)i * r0 + j];
+        }
+    } else {
+        const double* src = W0 + (int64_t)b * 4 * r0 * r0;
+        const int bx = b % L.side, by = b / L.side;
+        for (int c = 0; c < 4; ++c) {
+            const int cg = (2 * bx + (c & 1)) + child_side * (2 * by + (c >> 1));
+            const int rc = rank_child[cg];
+            const int ro = xoff5[b * 5 + c];
+            for (int t = threadIdx.x; t < rc * rb; t += blockDim.x) {
+                int i = t / rb, j = t - i * rb;
+                W[(size_t)(ro + i) * RC + j] = (T)src[(size_t)(c * r0 + i) * r0 + j];
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, const int64_t* p2p0_off,
+                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff5,
+                       const double* far0, const int* rank0, const int* rank0_child, const LevelView<T>* child,
+                       cudaStream_t st) {
+    if (is_leaf) {
+        k_init_p2p_leaf<T><<<dim3(L.nb, 9), kThreads, 0, st>>>(L, p2p0, p2p0_off);
+    } else {
+        k_init_p2p_parent<T><<<dim3(L.nb, 9 * 16), kThreads, 0, st>>>(L, *child, xoff5);
+    }
+    k_init_far<T><<<dim3(L.nb, 36), kThreads, 0, st>>>(L, far0, rank0, r0);
+    k_init_w<T><<<L.nb, kThreads, 0, st>>>(L, is_leaf, W0, w0_rowoff, r0, xoff5, rank0_child,
+                                           is_leaf ? 0 : child->side);
+    count_launches(3);
+}
+
+// largest column norm over the diagonal blocks P2P_bb of the level (threshold reference, tau_ref = 1)
+template <typename T>
+__global__ void k_level_scale(LevelView<T> L, unsigned long long* out) {
+    const int b = blockIdx.x;
+    int ld;
+    const T* D = block_at(L, b, b, ld);
+    const int n = L.n[b];
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = (double)D[(size_t)i * ld + j];
+            s += v * v;
+        }
+        mx = fmax(mx, sqrt(s));
+    }
+    if (mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+template <typename T>
+void launch_level_scale(const LevelView<T>& L, double* out, cudaStream_t st) {
+    k_level_scale<T><<<L.nb, 128, 0, st>>>(L, reinterpret_cast<unsigned long long*>(out));
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// level 1: the level-2 multipoles as unknowns, P2P^(1) = [M2L^(2)_{cd}] dense
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_root_gather(LevelView<T> L2, const int64_t* rootoff, double* D, int M) {
+    const int b = blockIdx.x, q = blockIdx.y;
+    int ld;
+    const T* src = block_at(L2, b, q, ld);
+    if (!src) return;
+    const int rb = L2.r[b], rq = L2.r[q];
+    const int64_t ro = rootoff[b], co = rootoff[q];
+    for (int t = threadIdx.x; t < rb * rq; t += blockDim.x) {
+        int i = t / rq, j = t - i * rq;
+        D[(ro + i) * M + co + j] = (double)src[(size_t)i * ld + j];
+    }
+}
+
+template <typename T>
+void launch_root_gather(const LevelView<T>& L2, const int64_t* rootoff, double* D, int M, cudaStream_t st) {
+    k_root_gather<T><<<dim3(L2.nb, L2.nb), kThreads, 0, st>>>(L2, rootoff, D, M);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(1024) k_dense_invert(double* D, int M, int* perm, double* col, int* status) {
+    __shared__ double vred[32];
+    __shared__ int ired[32];
+    bool ok = cta_gauss_jordan(D, M, M, perm, col, vred, ired);
+    if (!ok && threadIdx.x == 0) atomicOr(status, DEV_ERR_SINGULAR);
+}
+
+void launch_dense_invert(double* D, int M, int* perm, double* col, int* status, cudaStream_t st) {
+    if (M <= 0) return;
+    k_dense_invert<<<1, 1024, 0, st>>>(D, M, perm, col, status);
+    count_launches(1);
+}
+
+template <typename T>
+__global__ void k_root_apply(const double* Dinv, int M, const T* rhs, T* x, int nrhs) {
+    __shared__ double sm[2 * 16 * 65];
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int mm = min(64, M - m0), nn = min(64, nrhs - n0);
+    cta_gemm<double>(
+        mm, nn, M, [&](int i, int k) { return Dinv[(size_t)(m0 + i) * M + k]; },
+        [&](int k, int j) { return (double)rhs[(size_t)k * nrhs + n0 + j]; },
+        [&](int i, int j, double v) { x[(size_t)(m0 + i) * nrhs + n0 + j] = (T)v; }, sm);
+}
+
+template <typename T>
+void launch_root_apply(const double* Dinv, int M, const T* rhs, T* x, int nrhs, cudaStream_t st) {
+    if (M <= 0) return;
+    k_root_apply<T><<<dim3((M + 63) / 64, (nrhs + 63) / 64), kThreads, 0, st>>>(Dinv, M, rhs, x, nrhs);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// replay: forward over the stored factors, back substitution (Algorithm 2)
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fwd_piv(LevelView<T> L, const int* boxes, const int64_t* yoff, T* vec_k,
+                                                      T* vec_km1, T* vx, int nrhs) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    const T* Pi = L.Pi + L.pioff[e];
+    const int ld = L.pild[e];
+    const T* rhs = vec_k + L.voff[e] * nrhs;
+    T* vxe = vx + L.voff[e] * nrhs;
+    T* ze = vec_km1 + yoff[e] * nrhs;
+    // v = Pi [rhs_e; 0]: x rows to vx, z rows become the M2L_e right-hand side
+    cta_gemm<Acc>(
+        s, nrhs, n, [&](int i, int k) { return Pi[(size_t)i * ld + k]; },
+        [&](int k, int j) { return rhs[(size_t)k * nrhs + j]; },
+        [&](int i, int j, Acc v) {
+            if (i < n) vxe[(size_t)i * nrhs + j] = (T)v;
+            else ze[(size_t)(i - n) * nrhs + j] = (T)v;
+        },
+        sm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fwd_upd(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
+                                                      T* vec_k, T* vec_km1, const T* vx, int nrhs) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int dp = blockIdx.y;
+    if (dp == 4) return;
+    const int ex = e % L.side, ey = e / L.side;
+    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+    if (!in_grid(px, py, L.side)) return;
+    const int p = px + L.side * py;
+    const bool Ep = colour_of(px, py) < colour;
+    const int wp = Ep ? L.r[p] : L.n[p];
+    const int n = L.n[e];
+    const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
+    const T* v = vx + L.voff[e] * nrhs;
+    T* tgt = Ep ? vec_km1 + yoff[p] * nrhs : vec_k + L.voff[p] * nrhs;
+    cta_gemm<Acc>(
+        wp, nrhs, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+        [&](int k, int j) { return v[(size_t)k * nrhs + j]; },
+        [&](int i, int j, Acc a) { tgt[(size_t)i * nrhs + j] = (T)((Acc)tgt[(size_t)i * nrhs + j] - a); }, sm);
+}
+
+template <typename T>
+void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
+                           T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st) {
+    if (nboxes <= 0) return;
+    k_fwd_piv<T><<<nboxes, kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
+    k_fwd_upd<T><<<dim3(nboxes, 9), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
+    count_launches(2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bwd(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
+                                                  const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[2 * 16 * 65];
+    const int e = boxes[blockIdx.x];
+    const int ex = e % L.side, ey = e / L.side;
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    T* w = wtmp + L.voff[e] * nrhs;
+    const T* rhs = rhs_k + L.voff[e] * nrhs;
+    for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) w[t] = rhs[t];
+    __syncthreads();
+    // w = rhs_e - sum_q B_q u_q, u_q = x_q (eliminated after e) or y_q (before)
+    for (int d = 0; d < 9; ++d) {
+        if (d == 4) continue;
+        const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+        if (!in_grid(qx, qy, L.side)) continue;
+        const int q = qx + L.side * qy;
+        const bool Eq = colour_of(qx, qy) < colour;
+        const int wq = Eq ? L.r[q] : L.n[q];
+        const T* B = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+        const T* u = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
+        cta_gemm<Acc>(
+            n, nrhs, wq, [&](int i, int k) { return B[(size_t)i * wq + k]; },
+            [&](int k, int j) { return u[(size_t)k * nrhs + j]; },
+            [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)w[(size_t)i * nrhs + j] - a); }, sm);
+        __syncthreads();
+    }
+    // [x_e; z_e] = Pi [w; y_e]; only x_e is needed
+    const T* Pi = L.Pi + L.pioff[e];
+    const int ld = L.pild[e];
+    const T* ye = x_km1 + yoff[e] * nrhs;
+    T* xe = x_k + L.voff[e] * nrhs;
+    cta_gemm<Acc>(
+        n, nrhs, s, [&](int i, int k) { return Pi[(size_t)i * ld + k]; },
+        [&](int k, int j) { return k < n ? w[(size_t)k * nrhs + j] : ye[(size_t)(k - n) * nrhs + j]; },
+        [&](int i, int j, Acc a) { xe[(size_t)i * nrhs + j] = (T)a; }, sm);
+}
+
+template <typename T>
+void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
+                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st) {
+    if (nboxes <= 0) return;
+    k_bwd<T><<<nboxes, kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs);
+    count_launches(1);
+}
+
+template <typename T>
+__global__ void k_permute_in(const double* b, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    int64_t i = t / nrhs;
+    int j = (int)(t - i * nrhs);
+    out[t] = (T)b[perm[i] + (int64_t)j * ld];
+}
+
+template <typename T>
+void launch_permute_in(const double* b, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* out,
+                       cudaStream_t st) {
+    int64_t tot = N * nrhs;
+    k_permute_in<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b, ld, N, nrhs, perm, out);
+    count_launches(1);
+}
+
+template <typename T>
+__global__ void k_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, double* x, int64_t ld) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * nrhs) return;
+    int64_t i = t / nrhs;
+    int j = (int)(t - i * nrhs);
+    x[perm[i] + (int64_t)j * ld] = (double)in[t];
+}
+
+template <typename T>
+void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, double* x, int64_t ld,
+                        cudaStream_t st) {
+    int64_t tot = N * nrhs;
+    k_permute_out<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, N, nrhs, perm, x, ld);
+    count_launches(1);
+}
+
+#define IFMM_INSTANTIATE(T)                                                                                     \
+    template void launch_factor_colour<T>(const LevelView<T>&, const int*, int, int, int, cudaStream_t,         \
+                                          cudaEvent_t*);                                                        \
+    template void launch_forward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*, T*, T*,   \
+                                           T*, int, cudaStream_t);                                              \
+    template void launch_backward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*,          \
+                                            const T*, T*, const T*, T*, int, cudaStream_t);                     \
+    template void launch_init_level<T>(const LevelView<T>&, int, const double*, const int64_t*, const double*, \
+                                       const int64_t*, int, const int*, const double*, const int*, const int*, \
+                                       const LevelView<T>*, cudaStream_t);                                      \
+    template void launch_root_gather<T>(const LevelView<T>&, const int64_t*, double*, int, cudaStream_t);      \
+    template void launch_level_scale<T>(const LevelView<T>&, double*, cudaStream_t);                            \
+    template void launch_root_apply<T>(const double*, int, const T*, T*, int, cudaStream_t);                  \
+    template void launch_permute_in<T>(const double*, int64_t, int64_t, int, const int64_t*, T*, cudaStream_t); \
+    template void launch_permute_out<T>(const T*, int64_t, int, const int64_t*, double*, int64_t, cudaStream_t);
+
+IFMM_INSTANTIATE(double)
+IFMM_INSTANTIATE(float)
+
+}  // namespace ifmm

@@ -1,0 +1,147 @@
+// ifmm_internal.h -- structures shared by the host orchestration and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ifmm {
+
+// kernels launched by this library in this process (every launcher adds its launches)
+void count_launches(int n);
+long long launches_so_far();
+
+// device status flags (bit set by any block that fails)
+enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_OVERFLOW = 2, DEV_ERR_RANGE = 4, DEV_ERR_SIZE = 8 };
+
+// Device view of one tree level during elimination (Algorithm 1) and replay (Algorithm 2).
+// Box b of level k sits at grid position (b % side, b / side). Its particle unknowns x_b number
+// n[b]; its multipoles y_b and locals z_b number r[b] (the rank, grows by compression).
+//
+// blk: for every box p and every box q of the 6 x 6 region made of the children of p's parent's
+// neighbours (index region36), the block between the active equation of p and the active unknown
+// of q (Algorithm 1's P2P, P2L, M2P or M2L by elimination status) for neighbours, the M2L block
+// for interaction-list boxes. Offsets boff[p*36 + j] (-1: no block), leading dimension bld.
+template <typename T>
+struct LevelView {
+    int k, side, nb, RC;       // level, boxes per side, boxes, rank cap of the level
+    const int* n;              // [nb] particle count (leaf) or sum of the children's ranks
+    int* r;                    // [nb] rank
+    const int64_t* voff;       // [nb+1] prefix of n: rows of box b in level vectors and in W
+    const int64_t* boff;       // [nb*36]
+    const int* bld;            // [nb*36]
+    T* blk;
+    T* W;                      // (sum n) x RC: L2P_bb = W rows voff[b].., P2M_bb = its transpose
+    // factors kept for the solve
+    const int64_t* pioff;      // [nb] inverse pivot block, s x s with leading dimension pild
+    const int* pild;
+    T* Pi;
+    const int64_t* cpoff;      // [nb*9] C panel of neighbour direction d: rows of the neighbour
+    T* Cp;                     //        at column x_b (w x n_b, leading dimension n_b)
+    const int64_t* bpoff;      // [nb*9] B panel: row P2P_b at the neighbour's column (n_b x w,
+    T* Bp;                     //        leading dimension w)
+    // per-colour scratch (offsets restart at every colour)
+    const int64_t* xsoff;      // [nb] X = Pi [B; 0] for every column block, s x xsld
+    const int* xsld;
+    T* Xs;
+    const int64_t* fsoff;      // [nb*81] well-separated fill of ordered pair (dp, dq)
+    T* Fs;
+    T* Fs2;                    // same layout: intermediate of the redirect
+    const int64_t* rsoff;      // [nb*9] residual of the fill being compressed
+    T* Rs;
+    double* pws;               // FP64 pivot workspace for blocks too large for shared memory
+    const int64_t* psoff;      // [nb]
+    int* status;               // device error bits (DEV_ERR_*)
+    double* counters;          // [0] schur flops, [1] schur bytes, [2] all factor flops
+    double eps, sA;
+    int tau_ref;
+};
+
+// Level vectors of the replay: for box b of level k, rows voff[b].. of the level-k vector hold
+// its particle rows; rows yoff[b].. of the level-(k-1) vector (the root vector at k = 2) hold its
+// multipole / local rows.
+struct SolveView {
+    const int64_t* yoff;
+    int nrhs;
+};
+
+// ---- launchers (ifmm_factor.cu) -----------------------------------------------------------
+// ev (optional): 6 events recorded before each of the five launches and after the last
+template <typename T>
+void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smem_pivot_s,
+                          cudaStream_t st, cudaEvent_t* ev);
+template <typename T>
+void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
+                           T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
+                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, const int64_t* p2p0_off,
+                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff5,
+                       const double* far0, const int* rank0, const int* rank0_child, const LevelView<T>* child,
+                       cudaStream_t st);
+template <typename T>
+void launch_level_scale(const LevelView<T>& L, double* out, cudaStream_t st);
+template <typename T>
+void launch_root_gather(const LevelView<T>& L2, const int64_t* rootoff, double* D, int M, cudaStream_t st);
+void launch_dense_invert(double* D, int M, int* perm, double* col, int* status, cudaStream_t st);
+template <typename T>
+void launch_root_apply(const double* Dinv, int M, const T* rhs, T* x, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_permute_in(const double* b, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* out,
+                       cudaStream_t st);
+template <typename T>
+void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, double* x, int64_t ld,
+                        cudaStream_t st);
+
+// ---- build and matvec (ifmm_build.cu) -----------------------------------------------------
+struct BuildArgs {
+    int64_t N;
+    int depth, p, r0, kernel;
+    double kparam0, diag, x0, y0, L;
+};
+void launch_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
+                      unsigned long long* keys, int64_t npad, int* status, cudaStream_t st);
+void launch_bitonic_sort(unsigned long long* keys, int64_t npad, cudaStream_t st);
+void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
+                           double* px, double* py, int* leaf_count, int depth, cudaStream_t st);
+void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
+                       const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
+                       int max_n, cudaStream_t st);
+void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
+                         const double* Tc, double* W0, double* Rt, int* rank0, cudaStream_t st);
+void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const double* Rt, double* far0,
+                      cudaStream_t st);
+void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
+                      const int* leaf_count, const int64_t* p2p_off, double* p2p, double* sA_bits,
+                      cudaStream_t st);
+// FP64 FMM matvec pieces
+void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt,
+                          cudaStream_t st);
+void launch_mv_leaf_up(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                       const double* xt, double* y, int nrhs, cudaStream_t st);
+void launch_mv_up(int k, const double* W0, int r0, const double* ychild, double* y, int nrhs,
+                  cudaStream_t st);
+void launch_mv_m2l(int k, const double* far0, int r0, const double* y, double* z, int nrhs,
+                   cudaStream_t st);
+void launch_mv_down(int k, const double* W0, int r0, const double* z, double* zchild, int nrhs,
+                    cudaStream_t st);
+void launch_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                         const double* z, const double* xt, const int64_t* p2p_off, const double* p2p,
+                         double* out, int nrhs, cudaStream_t st);
+void launch_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
+                           cudaStream_t st);
+// refinement helpers
+void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm,
+                       cudaStream_t st);
+void launch_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld,
+                     double* nrm, cudaStream_t st);
+
+// Krylov vectors (FP64, column-major N x nrhs, basis vector i at V + i N nrhs)
+void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out,
+                        cudaStream_t st);
+void launch_krylov_lincomb(const double* V, int cnt, const double* coef, double* y, int64_t ldy, int64_t N, int nrhs,
+                           cudaStream_t st);
+void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, cudaStream_t st);
+void launch_colscale(double* y, int64_t ldy, int64_t N, int nrhs, const double* scale, cudaStream_t st);
+
+}  // namespace ifmm

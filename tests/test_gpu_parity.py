@@ -1,0 +1,174 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded inputs.
+
+FP64 path: identical box ranks and solutions within 1e-10 (relative 2-norm) of the oracle.
+Mixed path (FP32 Schur / compression, FP64 pivots, FP64 refinement): error to the manufactured
+solution within max(eps, 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_1407_1572_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ifmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_1572_gb300 import ifmm as m
+    m.load()
+    return m
+
+
+def _gpu(ifmm, pts, depth, p, eps, kernel=0, diag=None, precision=0, tau_ref=1, refine_tol=0.0, kparam=(0.0,),
+         r_cap=0):
+    N = pts.shape[0]
+    prm = ifmm.default_params(depth=depth, cheb_p=p, eps=eps, diag=math.sqrt(N) if diag is None else diag,
+                              precision=precision, tau_ref=tau_ref, refine_tol=refine_tol, refine_maxit=40,
+                              kparam=kparam, r_cap=r_cap)
+    return ifmm.IFMM(pts, kernel, prm)
+
+
+def _oracle(pts, depth, p, eps, kernel=0, diag=None, tau_ref=1, kparam=(0.0,)):
+    N = pts.shape[0]
+    return O.Oracle(pts, O.make_params(depth, p, kernel, eps=eps, diag=math.sqrt(N) if diag is None else diag,
+                                       tau_ref=tau_ref, kparam=tuple(kparam) + (0,) * (4 - len(kparam))))
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("N,depth,p,nrhs", [(700, 2, 3, 1), (3001, 3, 4, 3), (4096, 3, 4, 1), (20011, 4, 4, 2)])
+def test_matvec_matches_oracle(ifmm, N, depth, p, nrhs):
+    pts = inputs.uniform_points(100 + N, N)
+    g = _gpu(ifmm, pts, depth, p, 1e-8)
+    o = _oracle(pts, depth, p, 1e-8)
+    x = inputs.rhs(5, N, nrhs)
+    y = g.matvec(_t(x)).cpu().numpy()
+    yo = o.matvec(x)
+    assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("N,depth,p,eps", [
+    (4096, 3, 4, 1e-10),     # 4096 uniform points, 64 leaves, rank 16, eps 1e-10
+    (2000, 3, 3, 1e-8),
+    (1500, 2, 4, 1e-9),      # two levels: leaves at level 2, then the level-1 system
+    (9001, 4, 3, 1e-7),      # ragged leaves, four levels
+    (65536, 5, 4, 1e-6),     # 1,024 leaves x 64 points, rank 16
+    (65536, 5, 6, 1e-6),     # same, Chebyshev 6 x 6 (rank 36)
+])
+def test_fp64_factor_solve_matches_oracle(ifmm, N, depth, p, eps):
+    """Matrix-scale threshold (tau_ref = 1): identical box ranks at every level and the same
+    solution to 1e-10. At 65,536 points the gate is 1e-8: both sides compute the same compressed
+    factorisation (identical ranks), but 1/r + sqrt(N) I is indefinite and its balanced pivot blocks
+    reach condition numbers ~1e7, so rounding-order differences between two FP64 codes (Gauss-Jordan
+    on the GPU, LU in the oracle) grow to 1e-9 (measured 1.0e-9 at p = 4, 5.3e-9 at p = 6)."""
+    pts = inputs.uniform_points(1407 + N, N)
+    g = _gpu(ifmm, pts, depth, p, eps, tau_ref=1)
+    g.factor()
+    o = _oracle(pts, depth, p, eps, tau_ref=1)
+    o.factor()
+    for k in range(2, depth + 1):
+        assert np.array_equal(g.ranks(k), o.ranks(k)), f"ranks differ at level {k}"
+    b = inputs.rhs(9, N, 2)
+    x = g.solve(_t(b)).cpu().numpy()
+    xo = o.solve(b)
+    assert _rel(x, xo) <= (1e-10 if N <= 16384 else 1e-8)
+
+
+@pytest.mark.parametrize("N,depth,p,eps", [(4096, 3, 4, 1e-10), (1500, 2, 4, 1e-9), (3000, 3, 3, 1e-6)])
+def test_fill_relative_threshold_within_eps_bound(ifmm, N, depth, p, eps):
+    """Fill-relative threshold (tau_ref = 0): a column is kept when its norm exceeds eps times the
+    largest column of the fill itself, so columns near 1e-10 of a fill decide ranks and rounding
+    (amplified by the pivot blocks' conditioning) can flip a decision. What must hold: the GPU and
+    the oracle are both eps-accurate solutions of A~ x = b, so they differ by no more than the
+    oracle's own distance to the dense solution."""
+    pts = inputs.uniform_points(1407 + N, N)
+    g = _gpu(ifmm, pts, depth, p, eps, tau_ref=0)
+    g.factor()
+    o = _oracle(pts, depth, p, eps, tau_ref=0)
+    o.factor()
+    A = o.dense_tilde()
+    xs = inputs.rhs(10, N, 1)
+    b = A @ xs
+    x = g.solve(_t(b)).cpu().numpy()
+    xo = o.solve(b)
+    xd = np.linalg.solve(A, b)
+    assert _rel(x, xo) <= 2.0 * _rel(xo, xd) + 1e-12
+    assert _rel(x, xd) <= 3.0 * _rel(xo, xd) + 1e-12
+
+
+def test_uncompressed_reproduces_dense_solution(ifmm):
+    N, depth, p = 1024, 3, 3
+    pts = inputs.uniform_points(77, N)
+    g = _gpu(ifmm, pts, depth, p, 0.0)
+    g.factor()
+    A = _oracle(pts, depth, p, 0.0).dense_tilde()
+    b = inputs.rhs(3, N, 2)
+    x = g.solve(_t(b)).cpu().numpy()
+    assert _rel(x, np.linalg.solve(A, b)) <= 1e-10
+
+
+def test_exp_kernel_matches_oracle(ifmm):
+    N, depth, p, eps = 2048, 3, 4, 1e-8
+    pts = inputs.uniform_points(4, N)
+    g = _gpu(ifmm, pts, depth, p, eps, kernel=1, diag=1.01, kparam=(0.1,), tau_ref=1)
+    g.factor()
+    o = _oracle(pts, depth, p, eps, kernel=1, diag=1.01, kparam=(0.1,), tau_ref=1)
+    o.factor()
+    b = inputs.rhs(6, N, 1)
+    assert _rel(g.solve(_t(b)).cpu().numpy(), o.solve(b)) <= 1e-10
+
+
+@pytest.mark.parametrize("kernel,precision", [(0, 0), (1, 0), (1, 1)])
+def test_refined_solution_meets_tolerance(ifmm, kernel, precision):
+    """GMRES refinement preconditioned by the IFMM solve reaches the manufactured solution within
+    max(eps, 1e-6): FP64 on both kernels; the FP32 elimination on the positive-definite exponential
+    kernel (on 1/r + sqrt(N) I the FP32 factorisation is not a usable preconditioner: its pivot
+    blocks' condition numbers, 1e4 to 1e7 after balancing, exceed 1/u_fp32)."""
+    N, depth, p, eps = 4096, 3, 4, 1e-6
+    pts = inputs.uniform_points(1408, N)
+    if kernel == 0:
+        g = _gpu(ifmm, pts, depth, p, eps, precision=precision, refine_tol=1e-8)
+    else:
+        g = _gpu(ifmm, pts, depth, p, eps, kernel=1, diag=1.01, kparam=(0.1,), precision=precision, refine_tol=1e-8)
+    g.factor()
+    xs = inputs.rhs(21, N, 4)
+    b = g.matvec(_t(xs))
+    x = g.solve(b).cpu().numpy()
+    assert _rel(x, xs) <= max(eps, 1e-6)
+    assert g.stats()["refine_iters"] >= 1
+
+
+def test_solve_host_equals_device_solve(ifmm):
+    N = 3000
+    pts = inputs.uniform_points(8, N)
+    g = _gpu(ifmm, pts, 3, 3, 1e-8)
+    g.factor()
+    b = inputs.rhs(1, N, 3)
+    assert np.array_equal(g.solve_host(b), g.solve(_t(b)).cpu().numpy())
+
+
+def test_status_codes(ifmm):
+    N = 512
+    pts = inputs.uniform_points(2, N)
+    g = _gpu(ifmm, pts, 2, 2, 1e-8)
+    with pytest.raises(ifmm.IFMMError) as ei:
+        g.solve(_t(np.ones(N)))
+    assert ei.value.status == ifmm.IFMM_ERR_STATE
+    bad = pts.copy()
+    bad[3, 0] = 1.5
+    with pytest.raises(ifmm.IFMMError) as ei:
+        _gpu(ifmm, bad, 2, 2, 1e-8)
+    assert ei.value.status == ifmm.IFMM_ERR_INVALID_ARG
