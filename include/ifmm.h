@@ -90,6 +90,8 @@ typedef struct {
     double kernel_ms[5];   /* device time (CUDA events on the handle's stream) of the pivot, panel,
                               Schur, compression and redirect launches of the last factorisation     */
     int kernel_launches[5];/* launches of each of those five kernels in the last factorisation      */
+    double kernel_flops[5];/* algorithmic flops of each of those five kernels (actual sizes)         */
+    double level_ms[16];   /* device time of the five kernels per tree level (index = level)       */
     double last_update;    /* max_j ||dx_j|| / ||x_j|| of the last refinement step                 */
     double last_residual;  /* max_j ||b_j - A~ x_j|| / ||b_j|| before the last refinement step     */
     int64_t device_bytes;  /* device memory held by the handle                                     */

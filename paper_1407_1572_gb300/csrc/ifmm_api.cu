@@ -577,6 +577,7 @@ ifmm_status factor_impl(ifmm_handle* h) {
     h->lv.assign(kap + 1, FLevel());
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
     CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
+    for (int k = 0; k < 16; ++k) h->stats.level_ms[k] = 0.0;
     const long long l0 = launches_so_far();
     std::vector<cudaEvent_t> ev(9 * 6);
     for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -606,6 +607,7 @@ ifmm_status factor_impl(ifmm_handle* h) {
         CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
         CK(cudaMemcpyAsync(L.r.data(), L.d_r, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
+        double lms = 0.0;
         for (int c = 0; c < 9; ++c) {
             if (!used[c]) continue;
             for (int t = 0; t < 5; ++t) {
@@ -613,8 +615,10 @@ ifmm_status factor_impl(ifmm_handle* h) {
                 CK(cudaEventElapsedTime(&ms, ev[c * 6 + t], ev[c * 6 + t + 1]));
                 kms[t] += ms;
                 kl[t] += 1;
+                lms += ms;
             }
         }
+        if (k < 16) h->stats.level_ms[k] = lms;
         if (hs & DEV_ERR_SINGULAR) {
             h->err = "singular pivot block at level " + std::to_string(k);
             return IFMM_ERR_SINGULAR_PIVOT;
@@ -659,9 +663,11 @@ ifmm_status factor_impl(ifmm_handle* h) {
     h->stats.schur_flops = cnt[0];
     h->stats.schur_bytes = cnt[1];
     h->stats.factor_flops = cnt[2] + 2.0 * (double)M * M * M;
+    const int fidx[5] = {3, 4, 0, 5, 6};
     for (int t = 0; t < 5; ++t) {
         h->stats.kernel_ms[t] = kms[t];
         h->stats.kernel_launches[t] = kl[t];
+        h->stats.kernel_flops[t] = cnt[fidx[t]];
     }
     h->stats.launches_factor = launches_so_far() - l0;
     h->stats.rank_overflows = 0;

@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
         double sc = (i >= n ? alpha : 1.0) * (j >= n ? alpha : 1.0);
         Pi[(size_t)i * ld + j] = (T)(sc * A[(size_t)i * s + j]);
     }
-    if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
+    if (threadIdx.x == 0) {
+        atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
+        atomicAdd(&L.counters[3], 2.0 * s * (double)s * s);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -164,7 +167,10 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
         s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
         [&](int k, int j) { return B[(size_t)k * ldb + j]; },
         [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm);
-    if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * s * (double)wq * n);
+    if (threadIdx.x == 0) {
+        atomicAdd(&L.counters[2], 2.0 * s * (double)wq * n);
+        atomicAdd(&L.counters[4], 2.0 * s * (double)wq * n);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -207,7 +213,11 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
             wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm);
-        if (threadIdx.x == 0) atomicAdd(&L.counters[2], 2.0 * wp * (double)r * n);
+        if (threadIdx.x == 0) {
+            atomicAdd(&L.counters[0], 2.0 * wp * (double)r * n);
+            atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * r + (double)wp * r));
+            atomicAdd(&L.counters[2], 2.0 * wp * (double)r * n);
+        }
         return;
     }
     const int wq = active_width(L, q, colour);
@@ -390,7 +400,9 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     }
     if (threadIdx.x == 0) {
         L.r[q] = rq0 + add;
-        atomicAdd(&L.counters[2], 8.0 * (double)nq * m * (rq0 + 1) + 6.0 * (double)nq * m * add);
+        double fl = 8.0 * (double)nq * m * rq0 + 6.0 * (double)nq * m * (add + 1);
+        atomicAdd(&L.counters[2], fl);
+        atomicAdd(&L.counters[5], fl);
     }
     (void)s_val;
     (void)s_flag;
@@ -447,8 +459,11 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
             M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + (Acc)T1[(size_t)i * ld1 + j]);
         }
     }
-    if (threadIdx.x == 0)
-        atomicAdd(&L.counters[2], 2.0 * wp * (double)rq * wq * (Eq ? 0 : 1) + 2.0 * rp * (double)rq * wp * (Ep ? 0 : 1));
+    if (threadIdx.x == 0) {
+        double fl = 2.0 * wp * (double)rq * wq * (Eq ? 0 : 1) + 2.0 * rp * (double)rq * wp * (Ep ? 0 : 1);
+        atomicAdd(&L.counters[2], fl);
+        atomicAdd(&L.counters[6], fl);
+    }
 }
 
 template <typename T>

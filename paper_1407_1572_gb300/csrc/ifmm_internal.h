@@ -50,7 +50,8 @@ struct LevelView {
     double* pws;               // FP64 pivot workspace for blocks too large for shared memory
     const int64_t* psoff;      // [nb]
     int* status;               // device error bits (DEV_ERR_*)
-    double* counters;          // [0] schur flops, [1] schur bytes, [2] all factor flops
+    double* counters;          // [0] schur flops, [1] schur bytes, [2] all factor flops,
+                               // [3] pivot, [4] panel, [5] compress, [6] redirect flops
     double eps, sA;
     int tau_ref;
 };

@@ -39,6 +39,7 @@ class ifmm_stats(ctypes.Structure):
                 ("t_solve_ms", ctypes.c_double), ("factor_flops", ctypes.c_double),
                 ("schur_flops", ctypes.c_double), ("schur_bytes", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double * 5), ("kernel_launches", ctypes.c_int * 5),
+                ("kernel_flops", ctypes.c_double * 5), ("level_ms", ctypes.c_double * 16),
                 ("last_update", ctypes.c_double), ("last_residual", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
                 ("launches_solve", ctypes.c_int64)]
@@ -158,7 +159,7 @@ def ifmm_get_stats(h) -> dict:
     out = {}
     for name, _ in ifmm_stats._fields_:
         v = getattr(s, name)
-        out[name] = list(v) if name in ("kernel_ms", "kernel_launches") else v
+        out[name] = list(v) if name in ("kernel_ms", "kernel_launches", "kernel_flops", "level_ms") else v
     return out
 
 
