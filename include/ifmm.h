@@ -134,6 +134,22 @@ ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int 
  * ld >= N. Errors: INVALID_ARG, CUDA. */
 ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
 
+/* y = A~ x exactly as ifmm_matvec, but without allocating any device memory. This call has no
+ * counterpart in the paper; it serves callers that must not allocate: an application whose
+ * device memory is owned by another allocator (a framework's caching pool, a fixed budget), or a
+ * latency-sensitive loop in which an allocation would stall the device. ifmm_matvec allocates
+ * its intermediate vectors in the handle on first use; this variant keeps them in one fixed
+ * 32 MiB array compiled into the library (every GPU that loads the library holds those 32 MiB
+ * until the process exits). Limit: 16 N nrhs + 16 nrhs p^2 (4^2 + ... + 4^depth) bytes, each
+ * piece rounded up to 256 bytes, must fit in 32 MiB; larger calls return IFMM_ERR_INVALID_ARG
+ * with the size in ifmm_last_error. The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream capture. All calls
+ * share the array and each call overwrites it: calls that overlap on the GPU (two streams, two
+ * threads, two handles on one device) race and must be serialised by the caller. Arguments,
+ * layout and the other errors are those of ifmm_matvec; the call synchronises the handle's
+ * stream. */
+ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
+
 /* Final ranks of the boxes of one level 2..depth, grid order (ix + 2^level * iy), into the host
  * array out_host (4^level ints). Errors: STATE (not factored), INVALID_ARG. */
 ifmm_status ifmm_get_ranks(ifmm_h h, int level, int* out_host);

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1107,4 +1108,85 @@ void ifmm_destroy(ifmm_h h) {
     delete h;
 }
 
+// ------------------------------------------------------------------------------------------------
+// FMM matvec without any device allocation
+// ------------------------------------------------------------------------------------------------
 }  // extern "C"
+
+namespace {
+
+// Scratch of ifmm_matvec_noalloc: a fixed 32 MiB array in the library's device image. Every GPU
+// that loads the library holds it until the process exits; all calls share it.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {nullptr};   // device address of g_noalloc_scratch, per device ordinal
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld) {
+    if (!h || !x_dev || !y_dev || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    h->err.clear();
+    const int kap = h->depth, r0 = h->r0;
+    // carve the scratch: tree-order input and output, then multipoles and locals per level
+    const size_t vec = align256(sizeof(double) * (size_t)h->N * nrhs);
+    size_t need = 2 * vec;
+    std::vector<size_t> lvl(kap + 1, 0);
+    for (int k = 2; k <= kap; ++k) {
+        lvl[k] = align256(sizeof(double) * ((size_t)1 << (2 * k)) * r0 * nrhs);
+        need += 2 * lvl[k];
+    }
+    if (need > kNoAllocScratchBytes) {
+        h->err = "ifmm_matvec_noalloc: this problem needs " + std::to_string(need) +
+                 " bytes of scratch; the fixed limit is " + std::to_string(kNoAllocScratchBytes) +
+                 " bytes (reduce N * nrhs, or use ifmm_matvec)";
+        return IFMM_ERR_INVALID_ARG;
+    }
+    // set-up, once per device, with that device current: the host-side name of the array is not
+    // a device address, so fetch the address the kernels must be given
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        h->err = "ifmm_matvec_noalloc: device ordinal out of range";
+        return IFMM_ERR_CUDA;
+    }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                h->err = std::string("ifmm_matvec_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+                return IFMM_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    }
+    double* xt = reinterpret_cast<double*>(base);
+    double* out = reinterpret_cast<double*>(base + vec);
+    std::vector<double*> ym(kap + 1, nullptr), zm(kap + 1, nullptr);
+    size_t off = 2 * vec;
+    for (int k = 2; k <= kap; ++k) {
+        ym[k] = reinterpret_cast<double*>(base + off);
+        off += lvl[k];
+        zm[k] = reinterpret_cast<double*>(base + off);
+        off += lvl[k];
+    }
+    // every scratch vector is written before it is read (the M2L launch clears the locals first)
+    launch_mv_permute_in(x_dev, ld, h->N, nrhs, h->d_perm, xt, h->st);
+    launch_mv_leaf_up(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up(k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l(k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down(k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
+                        h->d_p2p, out, nrhs, h->st);
+    launch_mv_permute_out(out, h->N, nrhs, h->d_perm, y_dev, ld, h->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    return IFMM_OK;
+}

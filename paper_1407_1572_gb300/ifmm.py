@@ -58,7 +58,8 @@ _lib = None
 
 # every symbol include/ifmm.h declares
 SYMBOLS = ["ifmm_default_params", "ifmm_build", "ifmm_factor", "ifmm_solve", "ifmm_solve_host",
-           "ifmm_matvec", "ifmm_get_ranks", "ifmm_get_stats", "ifmm_last_error", "ifmm_destroy"]
+           "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_get_ranks", "ifmm_get_stats", "ifmm_last_error",
+           "ifmm_destroy"]
 
 
 def library_path() -> str:
@@ -83,7 +84,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ifmm_build.restype = ip
     lib.ifmm_factor.argtypes = [vp]
     lib.ifmm_factor.restype = ip
-    for name in ("ifmm_solve", "ifmm_solve_host", "ifmm_matvec"):
+    for name in ("ifmm_solve", "ifmm_solve_host", "ifmm_matvec", "ifmm_matvec_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, ip, i64]
         getattr(lib, name).restype = ip
     lib.ifmm_get_ranks.argtypes = [vp, ip, vp]
@@ -145,6 +146,11 @@ def ifmm_solve_host(h, b: np.ndarray, x: np.ndarray, nrhs: int, ld: int, allow_n
 
 def ifmm_matvec(h, x_ptr: int, y_ptr: int, nrhs: int, ld: int) -> int:
     return _check(h, load().ifmm_matvec(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), nrhs, ld))
+
+
+def ifmm_matvec_noalloc(h, x_ptr: int, y_ptr: int, nrhs: int, ld: int) -> int:
+    """ifmm_matvec without device allocation (fixed 32 MiB scratch compiled into the library)."""
+    return _check(h, load().ifmm_matvec_noalloc(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), nrhs, ld))
 
 
 def ifmm_get_ranks(h, level: int) -> np.ndarray:
