@@ -322,6 +322,8 @@ template <typename T>
 LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     LevelView<T> v{};
     v.k = L.k; v.side = L.side; v.nb = L.nb; v.RC = L.RC;
+    v.nmax = 0;
+    for (int b = 0; b < (int)L.n.size(); ++b) v.nmax = std::max(v.nmax, L.n[b]);
     v.n = L.d_n; v.r = L.d_r; v.voff = L.d_voff;
     v.boff = L.d_boff; v.bld = L.d_bld; v.blk = (T*)L.d_blk; v.W = (T*)L.d_W;
     v.pioff = L.d_pioff; v.pild = L.d_pild; v.Pi = (T*)L.d_Pi;
@@ -334,6 +336,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.eps = h->prm.eps;
     v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
+    v.symmetric = 1;   // both kernels, 1/r and exp(-r/l), are symmetric
     return v;
 }
 

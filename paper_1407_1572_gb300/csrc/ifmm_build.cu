@@ -371,7 +371,7 @@ void launch_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t*
 __global__ void __launch_bounds__(kThreads) k_mv_leaf_up(const double* W0, const int64_t* leaf_start,
                                                          const int* leaf_count, int r0, const double* xt, double* y,
                                                          int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int b = blockIdx.x;
     const int64_t s0 = leaf_start[b];
     const int n = leaf_count[b];
@@ -391,7 +391,7 @@ void launch_mv_leaf_up(int depth, const double* W0, const int64_t* leaf_start, c
 // M2M: y_P = W0_P^T [y_c]  (W0_P rows c*r0 + t)
 __global__ void __launch_bounds__(kThreads) k_mv_up(int k, const double* W0, int r0, const double* ychild, double* y,
                                                     int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int b = blockIdx.x;
     const int side = 1 << k, cs = side << 1;
     const int bx = b % side, by = b / side;
@@ -413,7 +413,7 @@ void launch_mv_up(int k, const double* W0, int r0, const double* ychild, double*
 // M2L: z_b = sum_{q in I_b} M2L_bq y_q
 __global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const double* far0, int r0, const double* y, double* z,
                                                      int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int b = blockIdx.x;
     const int side = 1 << k;
     const int bx = b % side, by = b / side;
@@ -440,7 +440,7 @@ void launch_mv_m2l(int k, const double* far0, int r0, const double* y, double* z
 // L2L: z_c += W0_P[rows of c] z_P, one block per child box c at level k+1
 __global__ void __launch_bounds__(kThreads) k_mv_down(int k, const double* W0, int r0, const double* z,
                                                       double* zchild, int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int cgi = blockIdx.x;
     const int cs = 2 << k;
     const int cx = cgi % cs, cy = cgi / cs;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const doub
                                                            const int* leaf_count, int r0, const double* z,
                                                            const double* xt, const int64_t* p2p_off,
                                                            const double* p2p, double* out, int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int b = blockIdx.x;
     const int side = 1 << depth;
     const int bx = b % side, by = b / side;

@@ -80,32 +80,86 @@ __device__ inline int block_argmax(double v, int idx, double* vred, int* ired, d
 
 // ---------------------------------------------------------------------------------------------
 // CTA GEMM: for (i, j) in [0, M) x [0, N): epi(i, j, sum_k la(i, k) * lb(k, j)).
-// 256 threads, 64 x 64 output tiles, k-steps of 16, 4 x 4 outputs per thread, accumulation in
-// Acc. `smem` must hold 2 * 16 * 65 Acc.
+// Output tiles of 64 x 64; the tiles with index = tile0 (mod tstride) belong to this block (one
+// pair block can be spread over several blocks). `smem` holds gemm_smem<Acc>::value elements.
+//  - FP32: register-tiled, 4 x 4 outputs per thread, k-steps of 16 (shared-memory bandwidth is
+//    the limit at the FP32 rate).
+//  - FP64: exact extent — each thread owns the outputs tid + 256 u of the tile that exist, so no
+//    padded multiply-adds reach the FP64 pipe (the limit at the FP64 rate); k-steps of 32.
 // ---------------------------------------------------------------------------------------------
+template <typename Acc> struct gemm_smem { static constexpr int value = 2 * 16 * 65; };
+template <> struct gemm_smem<double> { static constexpr int value = 2 * 32 * 64; };
+
 template <typename Acc, class LA, class LB, class EPI>
-__device__ void cta_gemm(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem) {
-    constexpr int BM = 64, BN = 64, BK = 16, LDS = 65;
-    Acc* As = smem;             // [BK][LDS] : As[k][i]
-    Acc* Bs = smem + BK * LDS;  // [BK][LDS] : Bs[k][j]
+__device__ void cta_gemm_exact(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem, int tile0, int tstride) {
+    constexpr int TM = 64, TN = 64, KC = 32, PER = 16;
+    Acc* As = smem;             // [KC][TM] : As[k][i]
+    Acc* Bs = smem + KC * TM;   // [KC][TN] : Bs[k][j]
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int m0 = 0; m0 < M; m0 += BM)
-        for (int n0 = 0; n0 < N; n0 += BN) {
+    const int tn = (N + TN - 1) / TN, tm = (M + TM - 1) / TM;
+    for (int tile = tile0; tile < tm * tn; tile += tstride) {
+        const int m0 = (tile / tn) * TM, n0 = (tile % tn) * TN;
+        const int mm = min(TM, M - m0), nn = min(TN, N - n0), tot = mm * nn;
+        const int cnt = tot > tid ? (tot - tid + 255) / 256 : 0;
+        int oi[PER], oj[PER];
+        Acc acc[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            int o = tid + 256 * u;
+            oi[u] = o / nn;
+            oj[u] = o - oi[u] * nn;
+            acc[u] = Acc(0);
+        }
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            const int kc = min(KC, K - k0);
+            for (int t = tid; t < mm * KC; t += 256) {
+                int i = t / KC, k = t - i * KC;
+                As[k * TM + i] = k < kc ? Acc(la(m0 + i, k0 + k)) : Acc(0);
+            }
+            for (int t = tid; t < KC * nn; t += 256) {
+                int k = t / nn, j = t - k * nn;
+                Bs[k * TN + j] = k < kc ? Acc(lb(k0 + k, n0 + j)) : Acc(0);
+            }
+            __syncthreads();
+            for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+                for (int u = 0; u < PER; ++u)
+                    if (u < cnt) acc[u] = fma(As[kk * TM + oi[u]], Bs[kk * TN + oj[u]], acc[u]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            if (u < cnt) epi(m0 + oi[u], n0 + oj[u], acc[u]);
+    }
+}
+
+template <typename Acc, class LA, class LB, class EPI>
+__device__ void cta_gemm(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem, int tile0 = 0, int tstride = 1) {
+    if constexpr (sizeof(Acc) == 8) {
+        cta_gemm_exact<Acc>(M, N, K, la, lb, epi, smem, tile0, tstride);
+        return;
+    } else {
+        constexpr int BM = 64, BN = 64, BK = 16, LDS = 65;
+        Acc* As = smem;             // [BK][LDS] : As[k][i]
+        Acc* Bs = smem + BK * LDS;  // [BK][LDS] : Bs[k][j]
+        const int tid = threadIdx.x;
+        const int tx = tid & 15, ty = tid >> 4;
+        const int tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
+        for (int tile = tile0; tile < tm * tn; tile += tstride) {
+            const int m0 = (tile / tn) * BM, n0 = (tile % tn) * BN;
             Acc acc[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = Acc(0);
             for (int k0 = 0; k0 < K; k0 += BK) {
-                // A tile: 64 rows x 16 k; thread t loads rows t/16 + 16 q, k = t % 16
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     int ii = (tid >> 4) + 16 * q, kk = tid & 15;
                     int gi = m0 + ii, gk = k0 + kk;
                     As[kk * LDS + ii] = (gi < M && gk < K) ? Acc(la(gi, gk)) : Acc(0);
                 }
-                // B tile: 16 k x 64 cols; thread t loads k = t / 64 + 4 q, col = t % 64
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     int kk = (tid >> 6) + 4 * q, jj = tid & 63;
@@ -135,6 +189,7 @@ __device__ void cta_gemm(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem) 
                     if (gi < M && gj < N) epi(gi, gj, acc[a][b]);
                 }
         }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -15,6 +15,7 @@
 //              (Algorithm 1: P2P_pq = L2P_pp M2L_pq P2M_qq, P2L_pq = M2L_pq P2M_qq,
 //              M2P_pq = L2P_pp M2L_pq).
 // T is the storage type of blocks, bases and panels (double, or float in the mixed form).
+#include <algorithm>
 #include <cstdio>
 
 #include "ifmm_common.cuh"
@@ -51,6 +52,14 @@ IFMM_DEVINL int xcol_offset(const LevelView<T>& L, int ex, int ey, int dsel) {
         if (in_grid(qx, qy, L.side)) off += L.n[qx + L.side * qy];
     }
     return off;
+}
+
+// element (i, j) of the well-separated fill F_ab (wa x wb) of the eliminated box e, ordered
+// directions da, db. For a symmetric kernel only the pair with da < db is stored (F_ba = F_ab^T).
+template <typename T>
+IFMM_DEVINL T fill_at(const LevelView<T>& L, int e, int da, int db, int wa, int wb, int i, int j) {
+    if (!L.symmetric || da < db) return L.Fs[L.fsoff[(int64_t)e * 81 + da * 9 + db] + (size_t)i * wb + j];
+    return L.Fs[L.fsoff[(int64_t)e * 81 + db * 9 + da] + (size_t)j * wa + i];
 }
 
 // active width of box b while eliminating colour c: r_b once eliminated, n_b before
@@ -125,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
     const int e = boxes[blockIdx.x];
     const int d = blockIdx.y;
     const int ex = e % L.side, ey = e / L.side;
@@ -137,6 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
     const T* Pi = L.Pi + L.pioff[e];
     const int ldpi = L.pild[e];
     if (d == 4) {
+        if (blockIdx.z != 0) return;
         int cy = xcol_offset(L, ex, ey, 4);
         for (int t = threadIdx.x; t < s * r; t += blockDim.x) {
             int i = t / r, j = t - i * r;
@@ -148,26 +158,28 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
     const int wq = active_width(L, q, colour);
     int ldb;
     const T* B = block_at(L, e, q, ldb);
-    // B panel (row P2P_e at q's active unknown), n x wq, kept for the back substitution
-    T* Bp = L.Bp + L.bpoff[(int64_t)e * 9 + d];
-    for (int t = threadIdx.x; t < n * wq; t += blockDim.x) {
-        int i = t / wq, j = t - i * wq;
-        Bp[t] = B[(size_t)i * ldb + j];
-    }
-    // C panel (q's active equation at x_e), wq x n, kept for the forward replay and the Schur step
-    int ldc;
-    const T* C = block_at(L, q, e, ldc);
-    T* Cp = L.Cp + L.cpoff[(int64_t)e * 9 + d];
-    for (int t = threadIdx.x; t < wq * n; t += blockDim.x) {
-        int i = t / n, j = t - i * n;
-        Cp[t] = C[(size_t)i * ldc + j];
+    if (blockIdx.z == 0) {
+        // B panel (row P2P_e at q's active unknown), n x wq, kept for the back substitution
+        T* Bp = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+        for (int t = threadIdx.x; t < n * wq; t += blockDim.x) {
+            int i = t / wq, j = t - i * wq;
+            Bp[t] = B[(size_t)i * ldb + j];
+        }
+        // C panel (q's active equation at x_e), wq x n, kept for the forward replay and the Schur step
+        int ldc;
+        const T* C = block_at(L, q, e, ldc);
+        T* Cp = L.Cp + L.cpoff[(int64_t)e * 9 + d];
+        for (int t = threadIdx.x; t < wq * n; t += blockDim.x) {
+            int i = t / n, j = t - i * n;
+            Cp[t] = C[(size_t)i * ldc + j];
+        }
     }
     const int cx = xcol_offset(L, ex, ey, d);
     cta_gemm<Acc>(
         s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
         [&](int k, int j) { return B[(size_t)k * ldb + j]; },
-        [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm);
-    if (threadIdx.x == 0) {
+        [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm, blockIdx.z, gridDim.z);
+    if (threadIdx.x == 0 && blockIdx.z == 0) {
         atomicAdd(&L.counters[2], 2.0 * s * (double)wq * n);
         atomicAdd(&L.counters[4], 2.0 * s * (double)wq * n);
     }
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     const int ex = e % L.side, ey = e / L.side;
@@ -192,6 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
     const int ldx = L.xsld[e];
     if (dp == 4) {
         // row M2L_e has -I at z_e: A[M2L_e, gamma] = X_gamma[z rows]
+        if (blockIdx.z != 0) return;
         int ld;
         T* dst = block_at(L, e, q, ld);
         const int w = (dq == 4) ? r : active_width(L, q, colour);
@@ -202,6 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         }
         return;
     }
+    // symmetric kernel: the (q, p) block is the transpose of the (p, q) block, written by that block
+    if (L.symmetric && dq != 4 && dp > dq) return;
     const int wp = active_width(L, p, colour);
     const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
     const int cx = xcol_offset(L, ex, ey, dq);
@@ -212,8 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         cta_gemm<Acc>(
             wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm);
-        if (threadIdx.x == 0) {
+            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
+        if (threadIdx.x == 0 && blockIdx.z == 0) {
             atomicAdd(&L.counters[0], 2.0 * wp * (double)r * n);
             atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * r + (double)wp * r));
             atomicAdd(&L.counters[2], 2.0 * wp * (double)r * n);
@@ -225,23 +240,29 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
     const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
     if (dist <= 1 || (Ep && Eq)) {
         // neighbours: dense update in place; both eliminated: M2L_pq updated directly
-        int ld;
+        int ld, ld2 = 0;
         T* dst = block_at(L, p, q, ld);
+        T* dst2 = (L.symmetric && p != q) ? block_at(L, q, p, ld2) : nullptr;
         cta_gemm<Acc>(
             wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v); }, sm);
+            [&](int i, int j, Acc v) {
+                dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v);
+                if (dst2) dst2[(size_t)j * ld2 + i] = (T)((Acc)dst2[(size_t)j * ld2 + i] - v);
+            },
+            sm, blockIdx.z, gridDim.z);
     } else {
         T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
         cta_gemm<Acc>(
             wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm);
+            [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && blockIdx.z == 0) {
         double fl = 2.0 * wp * (double)wq * n;
         atomicAdd(&L.counters[0], fl);
-        atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * wq + 2.0 * wp * wq));
+        const double mirror = (L.symmetric && p != q && (dist <= 1 || (Ep && Eq))) ? 2.0 : 1.0;
+        atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * wq + 2.0 * mirror * wp * wq));
         atomicAdd(&L.counters[2], fl);
     }
 }
@@ -275,28 +296,29 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const int nq = L.n[q];
     const int rq0 = L.r[q];
     const int RC = L.RC;
+    // S_q = [F_qp (nq x wp), F_pq^T (nq x wp)] over the partners p. For a symmetric kernel the
+    // extended system stays symmetric and F_pq^T = F_qp in exact arithmetic, so with the
+    // matrix-scale threshold the column fills alone span S_q.
+    const bool half = L.symmetric && L.tau_ref == 1;
     int wps[8], m = 0;
     for (int t = 0; t < np; ++t) {
         int dp = parts[t];
         int p = (ex + dp % 3 - 1) + L.side * (ey + dp / 3 - 1);
         wps[t] = active_width(L, p, colour);
-        m += 2 * wps[t];
+        m += (half ? 1 : 2) * wps[t];
     }
     if (nq == 0 || m == 0) return;
     T* R = L.Rs + L.rsoff[(int64_t)e * 9 + dq];
-    // S_q = [F_qp (nq x wp), F_pq^T (nq x wp)] over the partners p
     {
         int c0 = 0;
         for (int t = 0; t < np; ++t) {
             int dp = parts[t], wp = wps[t];
-            const T* Fc = L.Fs + L.fsoff[(int64_t)e * 81 + dq * 9 + dp];  // nq x wp
-            const T* Fr = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];  // wp x nq
             for (int u = threadIdx.x; u < nq * wp; u += blockDim.x) {
                 int i = u / wp, j = u - i * wp;
-                R[(size_t)i * m + c0 + j] = Fc[(size_t)i * wp + j];
-                R[(size_t)i * m + c0 + wp + j] = Fr[(size_t)j * nq + i];
+                R[(size_t)i * m + c0 + j] = fill_at(L, e, dq, dp, nq, wp, i, j);                // F_qp
+                if (!half) R[(size_t)i * m + c0 + wp + j] = fill_at(L, e, dp, dq, wp, nq, j, i);  // F_pq^T
             }
-            c0 += 2 * wp;
+            c0 += (half ? 1 : 2) * wp;
         }
     }
     __syncthreads();
@@ -314,8 +336,10 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const double tau = L.eps * (L.tau_ref == 1 ? L.sA : smax);
     T* W = L.W + L.voff[q] * RC;
     double* coef = csm + nq;  // 8 warps x RC
-    // R <- (I - W W^T) R, twice (classical Gram-Schmidt per column)
-    for (int pass = 0; pass < 2 && rq0 > 0; ++pass) {
+    // R <- (I - W W^T) R by classical Gram-Schmidt per column: once in FP64 (the basis is
+    // orthonormal to working precision), twice in FP32
+    const int passes = sizeof(T) == 8 ? 1 : 2;
+    for (int pass = 0; pass < passes && rq0 > 0; ++pass) {
         for (int j = warp; j < m; j += nw) {
             double* c = coef + warp * RC;
             for (int t = 0; t < rq0; ++t) {
@@ -400,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     }
     if (threadIdx.x == 0) {
         L.r[q] = rq0 + add;
-        double fl = 8.0 * (double)nq * m * rq0 + 6.0 * (double)nq * m * (add + 1);
+        double fl = 4.0 * passes * (double)nq * m * rq0 + 6.0 * (double)nq * m * (add + 1);
         atomicAdd(&L.counters[2], fl);
         atomicAdd(&L.counters[5], fl);
     }
@@ -414,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     if (dp == 4 || dq == 4 || dp == dq) return;
@@ -425,6 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
     if (max(abs(px - qx), abs(py - qy)) != 2) return;
     const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
     if (Ep && Eq) return;
+    if (L.symmetric && dp > dq) return;   // M2L_qp += G_pq^T below
     const int p = px + L.side * py, q = qx + L.side * qy;
     const int wp = Ep ? L.r[p] : L.n[p];
     const int wq = Eq ? L.r[q] : L.n[q];
@@ -433,8 +458,9 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
     const int64_t fo = L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
     const T* F = L.Fs + fo;   // wp x wq
     T* F2 = L.Fs2 + fo;       // wp x rq
-    int ld;
+    int ld, ld2 = 0;
     T* M = block_at(L, p, q, ld);
+    T* M2 = L.symmetric ? block_at(L, q, p, ld2) : nullptr;
     const T* Wq = L.W + L.voff[q] * RC;
     const T* Wp = L.W + L.voff[p] * RC;
     const T* T1 = F;
@@ -452,11 +478,17 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
         cta_gemm<Acc>(
             rp, rq, wp, [&](int i, int k) { return Wp[(size_t)k * RC + i]; },
             [&](int k, int j) { return T1[(size_t)k * ld1 + j]; },
-            [&](int i, int j, Acc v) { M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + v); }, sm);
+            [&](int i, int j, Acc v) {
+                M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + v);
+                if (M2) M2[(size_t)j * ld2 + i] = (T)((Acc)M2[(size_t)j * ld2 + i] + v);
+            },
+            sm);
     } else {
         for (int t = threadIdx.x; t < rp * rq; t += blockDim.x) {
             int i = t / rq, j = t - i * rq;
-            M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + (Acc)T1[(size_t)i * ld1 + j]);
+            Acc v = (Acc)T1[(size_t)i * ld1 + j];
+            M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + v);
+            if (M2) M2[(size_t)j * ld2 + i] = (T)((Acc)M2[(size_t)j * ld2 + i] + v);
         }
     }
     if (threadIdx.x == 0) {
@@ -482,10 +514,14 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     }
     if (ev) cudaEventRecord(ev[0], st);
     k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
+    // spread big pair blocks over several blocks when the colour has few boxes
+    const int tiles = ((L.nmax + 63) / 64) * ((L.nmax + 63) / 64);
+    const int zs = std::max(1, std::min(tiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
+    const int zp = std::max(1, std::min(((smax + 63) / 64) * ((L.nmax + 63) / 64), (608 + nboxes * 8 - 1) / (nboxes * 8)));
     if (ev) cudaEventRecord(ev[1], st);
-    k_panel<T><<<dim3(nboxes, 9), kThreads, 0, st>>>(L, boxes, colour);
+    k_panel<T><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[2], st);
-    k_schur<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    k_schur<T><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[3], st);
     size_t csmem = (size_t)(smax + 8 * L.RC) * sizeof(double);
     k_compress<T><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
@@ -667,7 +703,7 @@ void launch_dense_invert(double* D, int M, int* perm, double* col, int* status, 
 
 template <typename T>
 __global__ void k_root_apply(const double* Dinv, int M, const T* rhs, T* x, int nrhs) {
-    __shared__ double sm[2 * 16 * 65];
+    __shared__ double sm[gemm_smem<double>::value];
     const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
     const int mm = min(64, M - m0), nn = min(64, nrhs - n0);
     cta_gemm<double>(
@@ -690,7 +726,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fwd_piv(LevelView<T> L, const int* boxes, const int64_t* yoff, T* vec_k,
                                                       T* vec_km1, T* vx, int nrhs) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
     const int e = boxes[blockIdx.x];
     const int n = L.n[e], r = L.r[e], s = n + r;
     const T* Pi = L.Pi + L.pioff[e];
@@ -706,14 +742,14 @@ __global__ void __launch_bounds__(kThreads) k_fwd_piv(LevelView<T> L, const int*
             if (i < n) vxe[(size_t)i * nrhs + j] = (T)v;
             else ze[(size_t)(i - n) * nrhs + j] = (T)v;
         },
-        sm);
+        sm, blockIdx.z, gridDim.z);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fwd_upd(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
                                                       T* vec_k, T* vec_km1, const T* vx, int nrhs) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y;
     if (dp == 4) return;
@@ -730,47 +766,89 @@ __global__ void __launch_bounds__(kThreads) k_fwd_upd(LevelView<T> L, const int*
     cta_gemm<Acc>(
         wp, nrhs, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
         [&](int k, int j) { return v[(size_t)k * nrhs + j]; },
-        [&](int i, int j, Acc a) { tgt[(size_t)i * nrhs + j] = (T)((Acc)tgt[(size_t)i * nrhs + j] - a); }, sm);
+        [&](int i, int j, Acc a) { tgt[(size_t)i * nrhs + j] = (T)((Acc)tgt[(size_t)i * nrhs + j] - a); }, sm,
+        blockIdx.z, gridDim.z);
 }
 
 template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st) {
     if (nboxes <= 0) return;
-    k_fwd_piv<T><<<nboxes, kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
-    k_fwd_upd<T><<<dim3(nboxes, 9), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
+    const int tr = (nrhs + 63) / 64;
+    const int smax = L.nmax + std::min(L.nmax, L.RC);
+    const int z1 = std::max(1, std::min(((smax + 63) / 64) * tr, (608 + nboxes - 1) / nboxes));
+    const int z2 = std::max(1, std::min(((L.nmax + 63) / 64) * tr, (608 + nboxes * 8 - 1) / (nboxes * 8)));
+    k_fwd_piv<T><<<dim3(nboxes, 1, z1), kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
+    k_fwd_upd<T><<<dim3(nboxes, 9, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
     count_launches(2);
 }
 
+// back substitution, first half: w = rhs_e - sum_q B_q u_q as one GEMM over the concatenated
+// panels, u_q = x_q (q eliminated after e) or y_q (before)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bwd(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
-                                                  const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs) {
+__global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
+                                                    const T* rhs_k, const T* x_k, const T* x_km1, T* wtmp, int nrhs) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[2 * 16 * 65];
+    __shared__ Acc sm[gemm_smem<Acc>::value];
+    __shared__ const T* sB[8];
+    __shared__ const T* sU[8];
+    __shared__ int sOff[9], sW[8];
     const int e = boxes[blockIdx.x];
     const int ex = e % L.side, ey = e / L.side;
-    const int n = L.n[e], r = L.r[e], s = n + r;
+    const int n = L.n[e];
+    if (threadIdx.x == 0) {
+        int cnt = 0, off = 0;
+        for (int d = 0; d < 9; ++d) {
+            if (d == 4) continue;
+            const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+            if (!in_grid(qx, qy, L.side)) continue;
+            const int q = qx + L.side * qy;
+            const bool Eq = colour_of(qx, qy) < colour;
+            const int wq = Eq ? L.r[q] : L.n[q];
+            sB[cnt] = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+            sU[cnt] = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
+            sW[cnt] = wq;
+            sOff[cnt] = off;
+            off += wq;
+            ++cnt;
+        }
+        for (int c = cnt; c < 9; ++c) sOff[c] = off;
+    }
+    __syncthreads();
+    const int K = sOff[8];
+    auto seg = [&](int k) {
+        int c = 0;
+        while (c < 7 && k >= sOff[c + 1]) ++c;
+        return c;
+    };
     T* w = wtmp + L.voff[e] * nrhs;
     const T* rhs = rhs_k + L.voff[e] * nrhs;
-    for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) w[t] = rhs[t];
-    __syncthreads();
-    // w = rhs_e - sum_q B_q u_q, u_q = x_q (eliminated after e) or y_q (before)
-    for (int d = 0; d < 9; ++d) {
-        if (d == 4) continue;
-        const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
-        if (!in_grid(qx, qy, L.side)) continue;
-        const int q = qx + L.side * qy;
-        const bool Eq = colour_of(qx, qy) < colour;
-        const int wq = Eq ? L.r[q] : L.n[q];
-        const T* B = L.Bp + L.bpoff[(int64_t)e * 9 + d];
-        const T* u = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
-        cta_gemm<Acc>(
-            n, nrhs, wq, [&](int i, int k) { return B[(size_t)i * wq + k]; },
-            [&](int k, int j) { return u[(size_t)k * nrhs + j]; },
-            [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)w[(size_t)i * nrhs + j] - a); }, sm);
-        __syncthreads();
+    cta_gemm<Acc>(
+        n, nrhs, K,
+        [&](int i, int k) {
+            int c = seg(k);
+            return sB[c][(size_t)i * sW[c] + (k - sOff[c])];
+        },
+        [&](int k, int j) {
+            int c = seg(k);
+            return sU[c][(size_t)(k - sOff[c]) * nrhs + j];
+        },
+        [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - a); }, sm,
+        blockIdx.z, gridDim.z);
+    if (K == 0) {
+        for (int t = threadIdx.x + blockIdx.z * blockDim.x; t < n * nrhs; t += blockDim.x * gridDim.z) w[t] = rhs[t];
     }
-    // [x_e; z_e] = Pi [w; y_e]; only x_e is needed
+}
+
+// back substitution, second half: [x_e; z_e] = Pi [w; y_e]; only x_e is kept
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bwd_x(LevelView<T> L, const int* boxes, const int64_t* yoff, T* x_k,
+                                                    const T* x_km1, const T* wtmp, int nrhs) {
+    using Acc = typename AccOf<T>::type;
+    __shared__ Acc sm[gemm_smem<Acc>::value];
+    const int e = boxes[blockIdx.x];
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    const T* w = wtmp + L.voff[e] * nrhs;
     const T* Pi = L.Pi + L.pioff[e];
     const int ld = L.pild[e];
     const T* ye = x_km1 + yoff[e] * nrhs;
@@ -778,15 +856,17 @@ __global__ void __launch_bounds__(kThreads) k_bwd(LevelView<T> L, const int* box
     cta_gemm<Acc>(
         n, nrhs, s, [&](int i, int k) { return Pi[(size_t)i * ld + k]; },
         [&](int k, int j) { return k < n ? w[(size_t)k * nrhs + j] : ye[(size_t)(k - n) * nrhs + j]; },
-        [&](int i, int j, Acc a) { xe[(size_t)i * nrhs + j] = (T)a; }, sm);
+        [&](int i, int j, Acc a) { xe[(size_t)i * nrhs + j] = (T)a; }, sm, blockIdx.z, gridDim.z);
 }
 
 template <typename T>
 void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                             const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st) {
     if (nboxes <= 0) return;
-    k_bwd<T><<<nboxes, kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs);
-    count_launches(1);
+    const int z = std::max(1, std::min(((L.nmax + 63) / 64) * ((nrhs + 63) / 64), (608 + nboxes - 1) / nboxes));
+    k_bwd_w<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs);
+    k_bwd_x<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, yoff, x_k, x_km1, wtmp, nrhs);
+    count_launches(2);
 }
 
 template <typename T>

@@ -23,6 +23,7 @@ enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_OVERFLOW = 2, DEV_ERR_RANGE = 4, DEV_
 template <typename T>
 struct LevelView {
     int k, side, nb, RC;       // level, boxes per side, boxes, rank cap of the level
+    int nmax;                  // largest n at the level (sizes the tile split of big blocks)
     const int* n;              // [nb] particle count (leaf) or sum of the children's ranks
     int* r;                    // [nb] rank
     const int64_t* voff;       // [nb+1] prefix of n: rows of box b in level vectors and in W
@@ -54,6 +55,7 @@ struct LevelView {
                                // [3] pivot, [4] panel, [5] compress, [6] redirect flops
     double eps, sA;
     int tau_ref;
+    int symmetric;             // kernel symmetric: F_pq = F_qp^T in exact arithmetic
 };
 
 // Level vectors of the replay: for box b of level k, rows voff[b].. of the level-k vector hold
