@@ -516,8 +516,9 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     CKS(upload(h, &L.d_rsoff, rsoff));
     CKS(dalloc(h, &L.d_Rs, es * (size_t)rs_max));
     CKS(upload(h, &L.d_psoff, psoff));
-    size_t full = (size_t)L.smax * 8 + (size_t)((L.smax + 1) / 2) * 8 + (size_t)L.smax * L.smax * 8;
-    if (full > 200 * 1024) CKS(dalloc(h, &L.d_pws, sizeof(double) * (size_t)ps_max));
+    // FP64 pivot workspace in global memory for blocks whose matrix does not fit in shared memory
+    // (single block per box) or whose cluster slabs do not (8-block clusters)
+    if ((size_t)L.smax * L.smax * 8 > 150 * 1024) CKS(dalloc(h, &L.d_pws, sizeof(double) * (size_t)ps_max));
     CKS(upload(h, &L.d_boxes, L.boxes));
     if (k < kap) CKS(upload(h, &L.d_xoff5, L.xoff5));
     LevelView<T> v = view_of<T>(h, L);

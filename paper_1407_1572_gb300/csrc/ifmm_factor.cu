@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "ifmm_common.cuh"
 #include "ifmm_internal.h"
 
@@ -126,6 +128,151 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
         atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
         atomicAdd(&L.counters[3], 2.0 * s * (double)s * s);
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_pivot_cluster: the same balanced FP64 Gauss-Jordan inversion for large pivot blocks, spread
+// over a cluster of C blocks (one box per cluster). Row i lives in block i mod C (local row
+// i / C). Row interchanges are implicit: at step k the pivot is the unused row p_k with the
+// largest |A[p_k][k]| (ties to the lowest row); in exchange form the tableau then holds
+// A^{-1}[k][p_j] = R[p_k][j], applied when Pi is written. Per step: candidates are exchanged
+// through distributed shared memory (cluster barrier), the owner scales the pivot row, every
+// block copies it (cluster barrier) and updates its own rows. Every block runs the same
+// number of cluster barriers (the pivot choice is computed identically in all of them).
+// Shared memory: slab (rows_loc x s, or in the box's global FP64 workspace when slab_global),
+// prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 8 (portable).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, const int* boxes, int C, int smax,
+                                                            int slab_global) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double dsm[];
+    __shared__ double vred[32];
+    __shared__ int ired[32];
+    __shared__ double s_cval;
+    __shared__ int s_cidx;
+    __shared__ double s_alpha;
+    const int c = (int)cl.block_rank();
+    const int e = boxes[blockIdx.x / C];
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    const int rows_max = (smax + C - 1) / C;
+    double* base = slab_global ? dsm : dsm + (size_t)rows_max * smax;
+    double* prow = base;                              // smax
+    double* fcol = prow + smax;                       // rows_max
+    int* perm = reinterpret_cast<int*>(fcol + rows_max);  // smax
+    int* used = perm + smax;                          // rows_max
+    const int rows_loc = s > c ? (s - c + C - 1) / C : 0;
+    // local row tl of this block is global row c + tl C: in shared memory (slab_global = 0) at
+    // dsm + tl s, in global memory at row c + tl C of the box's s x s workspace
+    double* slab = slab_global ? L.pws + L.psoff[e] + (size_t)c * s : dsm;
+    const size_t sstride = slab_global ? (size_t)C * s : (size_t)s;
+    int ldp;
+    const T* Pee = block_at(L, e, e, ldp);
+    const T* We = L.W + L.voff[e] * L.RC;
+    const int RC = L.RC;
+    // balancing a = largest column norm of P2P_ee (same in every block of the cluster)
+    double cmax = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = (double)Pee[(size_t)i * ldp + j];
+            acc += v * v;
+        }
+        cmax = fmax(cmax, sqrt(acc));
+    }
+    double alpha = block_max(cmax, vred);
+    if (!(alpha > 0.0)) alpha = 1.0;
+    if (threadIdx.x == 0) s_alpha = alpha;
+    for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
+        const int tl = t / s, j = t - tl * s;
+        const int i = c + tl * C;
+        double v;
+        if (i < n && j < n) v = (double)Pee[(size_t)i * ldp + j];
+        else if (i < n) v = alpha * (double)We[(size_t)i * RC + (j - n)];
+        else if (j < n) v = alpha * (double)We[(size_t)j * RC + (i - n)];
+        else v = 0.0;
+        slab[(size_t)tl * sstride + j] = v;
+    }
+    for (int t = threadIdx.x; t < rows_loc; t += blockDim.x) used[t] = 0;
+    __syncthreads();
+    for (int k = 0; k < s; ++k) {
+        // local candidate among unused rows
+        double best = -1.0;
+        int bi = -1;
+        for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) {
+            if (used[tl]) continue;
+            const double v = fabs(slab[(size_t)tl * sstride + k]);
+            const int gi = c + tl * C;
+            if (bi < 0 || v > best || (v == best && gi < bi)) { best = v; bi = gi; }
+        }
+        double bv;
+        const int li = block_argmax(best, bi, vred, ired, &bv);
+        if (threadIdx.x == 0) { s_cval = bv; s_cidx = li; }
+        cl.sync();
+        // global pivot: identical choice in every block
+        double gv = -1.0;
+        int p = -1;
+        for (int j = 0; j < C; ++j) {
+            const double* rv = cl.map_shared_rank(&s_cval, j);
+            const int* ri = cl.map_shared_rank(&s_cidx, j);
+            const double v = *rv;
+            const int idx = *ri;
+            if (idx >= 0 && (p < 0 || v > gv || (v == gv && idx < p))) { gv = v; p = idx; }
+        }
+        if (p < 0 || !(gv > 0.0) || !isfinite(gv)) {
+            if (threadIdx.x == 0 && c == 0) atomicOr(L.status, DEV_ERR_SINGULAR);
+            cl.sync();  // every block leaves at the same step, after all candidate reads
+            return;
+        }
+        const int owner = p % C, tp = p / C;
+        if (threadIdx.x == 0) perm[k] = p;
+        if (c == owner) {
+            // every thread reads the pivot before the thread with j == k overwrites it
+            const double d = 1.0 / slab[(size_t)tp * sstride + k];
+            __syncthreads();
+            for (int j = threadIdx.x; j < s; j += blockDim.x) {
+                const double v = (j == k) ? d : slab[(size_t)tp * sstride + j] * d;
+                slab[(size_t)tp * sstride + j] = v;
+                prow[j] = v;
+            }
+            if (threadIdx.x == 0) used[tp] = 1;
+        }
+        cl.sync();
+        if (c != owner) {
+            const double* rp = cl.map_shared_rank(prow, owner);
+            for (int j = threadIdx.x; j < s; j += blockDim.x) prow[j] = rp[j];
+        }
+        for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) fcol[tl] = slab[(size_t)tl * sstride + k];
+        __syncthreads();
+        const double d = prow[k];
+        for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
+            const int tl = t / s, j = t - tl * s;
+            if (c == owner && tl == tp) continue;
+            const double f = fcol[tl];
+            if (j == k) slab[(size_t)tl * sstride + k] = -f * d;
+            else slab[(size_t)tl * sstride + j] -= f * prow[j];
+        }
+        __syncthreads();
+    }
+    // write Pi = S A^{-1} S: A^{-1}[k][p_j] = R[p_k][j]; local row i = p_k for k = pinv(i)
+    T* Pi = L.Pi + L.pioff[e];
+    const int ld = L.pild[e];
+    alpha = s_alpha;
+    for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
+        const int tl = t / s, j = t - tl * s;
+        const int i = c + tl * C;
+        int kk = 0;
+        while (kk < s - 1 && perm[kk] != i) ++kk;
+        const int col = perm[j];
+        const double sc = (kk >= n ? alpha : 1.0) * (col >= n ? alpha : 1.0);
+        Pi[(size_t)kk * ld + col] = (T)(sc * slab[(size_t)tl * sstride + j]);
+    }
+    if (threadIdx.x == 0 && c == 0) {
+        atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
+        atomicAdd(&L.counters[3], 2.0 * s * (double)s * s);
+    }
+    cl.sync();  // no block leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -512,8 +659,51 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_set[sizeof(T) == 8] = true;
     }
+    // large pivot blocks and few boxes: one cluster of C blocks per box
+    int C = 1, slab_global = 0;
+    auto cl_bytes = [&](int cc, int glob) {
+        const size_t rows = (size_t)(smax + cc - 1) / cc;
+        return (glob ? 0 : rows * smax * sizeof(double)) + (smax + rows) * sizeof(double) + (smax + rows) * sizeof(int);
+    };
+    if (smax >= 160) {
+        while (C < 8 && nboxes * C < 2 * 152) C *= 2;
+        while (C < 8 && cl_bytes(C, 0) > 200 * 1024) C *= 2;
+        if (cl_bytes(C, 0) > 200 * 1024) slab_global = 1;   // slab rows in the FP64 workspace (L2)
+        if (slab_global && !L.pws) C = 1;
+    }
     if (ev) cudaEventRecord(ev[0], st);
-    k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
+    if (C > 1) {
+        // (falls back to C = 1 below when the cluster shape cannot be scheduled)
+        static bool cl_attr[2] = {false, false};
+        if (!cl_attr[sizeof(T) == 8]) {
+            cudaFuncSetAttribute(k_pivot_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+            cl_attr[sizeof(T) == 8] = true;
+        }
+        const size_t cbytes = cl_bytes(C, slab_global);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nboxes * C));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = cbytes;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, k_pivot_cluster<T>, &cfg) != cudaSuccess || active < 1) {
+            cudaGetLastError();
+            C = 1;   // this cluster shape cannot be scheduled: one block per box
+        } else if (cudaLaunchKernelEx(&cfg, k_pivot_cluster<T>, L, boxes, C, smax, slab_global) != cudaSuccess) {
+            cudaGetLastError();
+            C = 1;   // launch refused: one block per box instead
+        }
+    }
+    if (C == 1) {
+        k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
+    }
     // spread big pair blocks over several blocks when the colour has few boxes
     const int tiles = ((L.nmax + 63) / 64) * ((L.nmax + 63) / 64);
     const int zs = std::max(1, std::min(tiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
