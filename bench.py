@@ -7,9 +7,12 @@ Workload: N = 2^20 points i.i.d. uniform in [0,1]^2 (seeded), uniform quadtree o
 GMRES-based FP64 refinement (preconditioner = the IFMM solve) until the estimated relative error
 is <= 1e-7; the error to the manufactured solution is measured and reported.
 
-Headline precision: FP64 elimination (--precision fp64). The FP32 elimination (--precision mixed:
-FP32 Schur updates, panels and compression, FP64 pivot blocks, residuals and refinement) is timed
-alongside and reported with its error.
+Precisions (--precision): mixed_solve (default) = FP64 elimination, solve phase on the FP32 pipe in
+double-float arithmetic (replay of double-float copies of the factors and double-float FMM matvec
+inside GMRES, FP64 residual at every restart, FP64 update); fp64 = every step in FP64; mixed = FP32
+elimination (FP32 Schur updates, panels and compression, FP64 pivot blocks, residuals and
+refinement). The precisions not chosen are timed alongside (one step each) and reported with their
+errors.
 
 One step = ifmm_factor (every level, Algorithm 1, plus the level-1 system) + ifmm_solve of the
 32 right-hand sides with refinement (Algorithm 2 replay + FP64 matvec per refinement step).
@@ -34,10 +37,22 @@ if ROOT not in sys.path:
 
 METRIC = "factor+solve unknowns/s at N=2^20, err<=1e-6, mixed vs FP64 GPU; % of roofline"
 WORKLOAD = dict(N=1 << 20, depth=7, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
-                refine_maxit=120, refine_restart=30)
+                refine_maxit=120, refine_restart=30, refine_inner=1e-4)
 # bounded CPU sample of the same workload family for the oracle (same points per leaf, settings)
 CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
                   refine_maxit=40, refine_restart=0)
+
+
+PRECISION_DESC = {
+    "fp64": "FP64",
+    "mixed_solve": ("FP64 elimination, double-float (FP32-pair) solve phase on the FP32 pipe (replay + matvec in "
+                    "GMRES), FP64 restart residuals"),
+    "mixed": "FP32 elimination (FP64 pivots) + FP64 refinement",
+}
+
+
+def precision_code(ifmm, prec):
+    return {"fp64": ifmm.IFMM_FP64, "mixed": ifmm.IFMM_MIXED, "mixed_solve": ifmm.IFMM_MIXED_SOLVE}[prec]
 
 
 def workload_desc(w, precision):
@@ -233,9 +248,10 @@ def run_gpu(args):
 
     def make_solver(prec):
         prm = ifmm.default_params(depth=w["depth"], cheb_p=w["cheb_p"], eps=w["eps"], diag=math.sqrt(N),
-                                  precision=ifmm.IFMM_MIXED if prec == "mixed" else ifmm.IFMM_FP64,
-                                  tau_ref=w["tau_ref"], refine_tol=w["refine_tol"], refine_maxit=w["refine_maxit"],
-                                  refine_restart=w["refine_restart"])
+                                  precision=precision_code(ifmm, prec),
+                                  tau_ref=w["tau_ref"], refine_tol=w["refine_tol"],
+                                  refine_maxit=w["refine_maxit"] if prec != "mixed" else 30,
+                                  refine_restart=w["refine_restart"], refine_inner=w["refine_inner"])
         pts = inputs.uniform_points(w["seed"] + rank, N)
         return ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm, stream)
 
@@ -294,29 +310,33 @@ def run_gpu(args):
 
     extra = {}
     if args.compare and rank == 0:
-        other = "mixed" if precision == "fp64" else "fp64"
         solver.close()
-        so = make_solver(other)
-        ifmm.ifmm_matvec(so.h, xs.data_ptr(), b.data_ptr(), nrhs, N)
-        step(so.h)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        step(so.h)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        mso = f0.elapsed_time(f1)
-        sto = ifmm.ifmm_get_stats(so.h)
-        erro = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
-        extra[f"{other}_gpu"] = {
-            "value": N / (mso / 1000.0), "unit": "unknowns/s", "ms_per_step": mso, "err": erro,
-            "meets_err_1e-6": erro <= 1e-6, "steps": 1, "warmup": 1, "t_factor_ms": sto["t_factor_ms"],
-            "t_solve_ms": sto["t_solve_ms"], "refine_iters": sto["refine_iters"], "max_rank": sto["max_rank"],
-            "kernel_ms": dict(zip(ifmm.FACTOR_KERNELS, sto["kernel_ms"])),
-            "note": ("FP32 elimination: its pivot blocks (condition numbers 1e4..5e7 after balancing) exceed "
-                     "1/u_fp32, so the FP32 factorisation is not an accurate preconditioner on 1/r + sqrt(N) I")
-            if other == "mixed" else "plain FP64"}
-        so.close()
+        for other in [q for q in ("fp64", "mixed_solve", "mixed") if q != precision]:
+            so = make_solver(other)
+            ifmm.ifmm_matvec(so.h, xs.data_ptr(), b.data_ptr(), nrhs, N)
+            step(so.h)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            step(so.h)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            mso = f0.elapsed_time(f1)
+            sto = ifmm.ifmm_get_stats(so.h)
+            erro = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
+            extra[f"{other}_gpu"] = {
+                "value": N / (mso / 1000.0), "unit": "unknowns/s", "ms_per_step": mso, "err": erro,
+                "meets_err_1e-6": erro <= 1e-6, "steps": 1, "warmup": 1, "precision": PRECISION_DESC[other],
+                "t_factor_ms": sto["t_factor_ms"], "t_solve_ms": sto["t_solve_ms"],
+                "refine_iters": sto["refine_iters"], "max_rank": sto["max_rank"],
+                "kernel_ms": dict(zip(ifmm.FACTOR_KERNELS, sto["kernel_ms"]))}
+            if other == "mixed":
+                extra[f"{other}_gpu"]["note"] = (
+                    "FP32 elimination: its pivot blocks (condition numbers 1e4..5e7 after balancing) exceed "
+                    "1/u_fp32, so the FP32 factorisation is not an accurate preconditioner on 1/r + sqrt(N) I "
+                    "(refinement capped at 30 iterations)")
+            so.close()
+        solver = None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -328,10 +348,9 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
                 "precision": precision, "meets_err_1e-6": err <= 1e-6,
-                "config": {"workload": workload_desc(w, "mixed FP32/FP64 + FP64 refinement" if precision == "mixed"
-                                                     else "FP64"),
+                "config": {"workload": workload_desc(w, PRECISION_DESC[precision]),
                            "N": N, "depth": w["depth"], "cheb_p": w["cheb_p"], "nrhs": nrhs, "eps": w["eps"],
                            "parallelism": "replicas" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (factor touches tens of GB per step)",
@@ -348,7 +367,8 @@ def run_gpu(args):
                 "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks}
         line.update(extra)
         print(json.dumps(line), flush=True)
-    solver.close()
+    if solver is not None:
+        solver.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -360,8 +380,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"],
-                    help="headline precision (fp64 is the one that reaches err <= 1e-6 on this workload)")
+    ap.add_argument("--precision", default="mixed_solve", choices=["fp64", "mixed_solve", "mixed"],
+                    help="headline precision; the others are timed alongside (one step each)")
     ap.add_argument("--n", type=int, default=0, help="override N (depth follows 64 points per leaf)")
     ap.add_argument("--compare", dest="compare", action="store_true", default=True,
                     help="also time one step of the other precision (reported, not the headline)")

@@ -50,8 +50,13 @@ typedef enum {
 
 typedef enum {
     IFMM_FP64 = 0,               /* every step in FP64                                         */
-    IFMM_MIXED = 1               /* FP32 Schur updates, panels and compression; FP64 pivot
+    IFMM_MIXED = 1,              /* FP32 Schur updates, panels and compression; FP64 pivot
                                     blocks, residual matvec and refinement update              */
+    IFMM_MIXED_SOLVE = 2         /* FP64 elimination; the solve phase on the FP32 pipe in
+                                    double-float arithmetic (pairs of FP32, ~48-bit significand):
+                                    the replay of double-float copies of the factors and the FMM
+                                    matvec inside GMRES, with FP64 residuals at every restart and
+                                    FP64 updates                                                */
 } ifmm_precision;
 
 typedef struct {
@@ -75,6 +80,9 @@ typedef struct {
     int refine_maxit;     /* limit on preconditioned matvecs (IFMM_ERR_NOCONV past it)            */
     int refine_restart;   /* > 0: GMRES(refine_restart) left-preconditioned by the IFMM solve;
                              0: classical refinement x += M^{-1}(b - A~ x)                          */
+    double refine_inner;  /* IFMM_MIXED_SOLVE: a GMRES cycle (double-float products) ends once its error
+                             estimate has fallen by this factor, then the FP64 residual is formed
+                             again; <= 0 selects 1e-4                                             */
 } ifmm_params;
 
 typedef struct {
@@ -100,7 +108,7 @@ typedef struct {
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
- * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30). */
+ * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30, refine_inner 1e-4). */
 void ifmm_default_params(ifmm_params* p);
 
 /* Build the tree, the Chebyshev operators and their orthonormal nested bases (assembly time t_a).
@@ -125,6 +133,14 @@ ifmm_status ifmm_factor(ifmm_h h);
  * 1 <= nrhs <= 1024; b and x must not overlap. Errors: STATE (not factored), INVALID_ARG,
  * NOCONV (x still holds the last iterate), CUDA, OOM. */
 ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld);
+
+/* x = A~^{-T} b: the transposed system, as needed by an adjoint (a gradient through the solve).
+ * Every kernel of this library is symmetric and the build keeps A~ = A~^T (P2P_ji = P2P_ij^T,
+ * M2L_ji = M2L_ij^T, L2P = P2M^T, Table "table_FMM_operators"), and the elimination compresses the
+ * fill of a box with one basis for its row and its column, so the factors invert a symmetric
+ * matrix and the transposed solve replays them exactly as ifmm_solve does (Algorithm 2).
+ * Arguments, layout, refinement and errors are those of ifmm_solve. */
+ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld);
 
 /* As ifmm_solve with host buffers: copies b in and x out inside the call. */
 ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld);

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,11 @@ struct FLevel {
     int64_t* d_psoff = nullptr;
     int* d_boxes = nullptr;
     int* d_xoff5 = nullptr;
+    // double-float copies of the stored factors (precision IFMM_MIXED_SOLVE) and element counts
+    int64_t npi = 0, ncp = 0, nbp = 0;
+    dfl* d_Pi2 = nullptr;
+    dfl* d_Cp2 = nullptr;
+    dfl* d_Bp2 = nullptr;
 };
 
 struct OpsLevel {
@@ -64,6 +70,10 @@ struct OpsLevel {
     double* d_W0 = nullptr;
     double* d_Rt = nullptr;
     double* d_far0 = nullptr;
+    // double-float copies for the inner matvec of IFMM_MIXED_SOLVE: W0 (used part) and far0
+    int64_t nW0 = 0, nfar0 = 0;
+    dfl* d_W0_2 = nullptr;
+    dfl* d_far0_2 = nullptr;
 };
 
 uint64_t morton_host(uint32_t ix, uint32_t iy) {
@@ -102,6 +112,8 @@ struct ifmm_handle {
     std::vector<int64_t> p2p_off;
     int64_t* d_p2p_off = nullptr;
     double* d_p2p = nullptr;
+    int64_t np2p = 0;
+    dfl* d_p2p2 = nullptr;
     double sA = 0.0;
     // factor
     bool factored = false;
@@ -272,6 +284,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nleaf));
         launch_leaf_basis(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_cheb, O.d_W0, O.d_Rt,
                           O.d_rank0, max_n, h->st);
+        O.nW0 = (int64_t)N * r0;
     }
     for (int k = kap - 1; k >= 2; --k) {
         OpsLevel& O = h->ops[k];
@@ -280,6 +293,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nb * r0 * r0));
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nb));
         launch_parent_basis(ba, k, h->ops[k + 1].d_Rt, h->ops[k + 1].d_rank0, h->d_Tc, O.d_W0, O.d_Rt, O.d_rank0, h->st);
+        O.nW0 = (int64_t)nb * 4 * r0 * r0;
     }
     for (int k = 2; k <= kap; ++k) {
         OpsLevel& O = h->ops[k];
@@ -287,6 +301,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_far0, sizeof(double) * (size_t)nb * 36 * r0 * r0));
         CK(cudaMemsetAsync(O.d_far0, 0, sizeof(double) * (size_t)nb * 36 * r0 * r0, h->st));
         launch_m2l_build(ba, k, h->d_cheb, O.d_Rt, O.d_far0, h->st);
+        O.nfar0 = (int64_t)nb * 36 * r0 * r0;
         O.rank0.assign(nb, 0);
         CK(cudaMemcpyAsync(O.rank0.data(), O.d_rank0, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->st));
     }
@@ -309,6 +324,19 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     CK(cudaMemsetAsync(d_sA, 0, sizeof(double), h->st));
     launch_p2p_build(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_p2p_off, h->d_p2p, d_sA, h->st);
     CK(cudaMemcpyAsync(&h->sA, d_sA, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    h->np2p = po;
+    // double-float operator copies for the inner Krylov matvec of the mixed-precision solve
+    if (h->prm.precision == IFMM_MIXED_SOLVE) {
+        for (int k = 2; k <= kap; ++k) {
+            OpsLevel& O = h->ops[k];
+            CKS(dalloc(h, &O.d_W0_2, sizeof(dfl) * (size_t)O.nW0));
+            launch_split_dfl(O.d_W0, O.d_W0_2, O.nW0, h->st);
+            CKS(dalloc(h, &O.d_far0_2, sizeof(dfl) * (size_t)O.nfar0));
+            launch_split_dfl(O.d_far0, O.d_far0_2, O.nfar0, h->st);
+        }
+        CKS(dalloc(h, &h->d_p2p2, sizeof(dfl) * (size_t)std::max<int64_t>(po, 1)));
+        launch_split_dfl(h->d_p2p, h->d_p2p2, po, h->st);
+    }
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     dfree_ptr(h, d_sA);
@@ -337,6 +365,20 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
     v.symmetric = 1;   // both kernels, 1/r and exp(-r/l), are symmetric
+    return v;
+}
+
+// The level as the replay (Algorithm 2) reads it: with T = dfl, the double-float copies of the
+// FP64 factors; the replay touches only n, r, offsets and the Pi, C and B panels.
+template <typename T>
+LevelView<T> solve_view(ifmm_handle* h, FLevel& L) {
+    LevelView<T> v = view_of<T>(h, L);
+    if (std::is_same<T, dfl>::value) {
+        v.Pi = (T*)L.d_Pi2;
+        v.Cp = (T*)L.d_Cp2;
+        v.Bp = (T*)L.d_Bp2;
+        v.blk = nullptr; v.W = nullptr; v.Xs = nullptr; v.Fs = nullptr; v.Fs2 = nullptr; v.Rs = nullptr;
+    }
     return v;
 }
 
@@ -503,10 +545,13 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     CKS(upload(h, &L.d_pioff, pioff));
     CKS(upload(h, &L.d_pild, pild));
     CKS(dalloc(h, &L.d_Pi, es * (size_t)pio));
+    L.npi = pio;
     CKS(upload(h, &L.d_cpoff, cpoff));
     CKS(dalloc(h, &L.d_Cp, es * (size_t)cpo));
+    L.ncp = cpo;
     CKS(upload(h, &L.d_bpoff, bpoff));
     CKS(dalloc(h, &L.d_Bp, es * (size_t)bpo));
+    L.nbp = bpo;
     CKS(upload(h, &L.d_xsoff, xsoff));
     CKS(upload(h, &L.d_xsld, xsld));
     CKS(dalloc(h, &L.d_Xs, es * (size_t)xs_max));
@@ -558,7 +603,8 @@ void release_level(ifmm_handle* h, FLevel& L) {
                      (void**)&L.d_bld, &L.d_blk, &L.d_W, (void**)&L.d_pioff, (void**)&L.d_pild, &L.d_Pi,
                      (void**)&L.d_cpoff, &L.d_Cp, (void**)&L.d_bpoff, &L.d_Bp, (void**)&L.d_xsoff,
                      (void**)&L.d_xsld, &L.d_Xs, (void**)&L.d_fsoff, &L.d_Fs, &L.d_Fs2, (void**)&L.d_rsoff,
-                     &L.d_Rs, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5};
+                     &L.d_Rs, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5,
+                     (void**)&L.d_Pi2, (void**)&L.d_Cp2, (void**)&L.d_Bp2};
     for (void** p : ptrs) {
         dfree(h, *p);
         *p = nullptr;
@@ -574,6 +620,22 @@ void release_factors(ifmm_handle* h) {
     dfree_ptr(h, h->d_Dinv);
     h->M = 0;
     h->factored = false;
+}
+
+// double-float copies of the FP64 factors for the replay of IFMM_MIXED_SOLVE (the level-1 inverse
+// stays FP64)
+ifmm_status split_factors(ifmm_handle* h) {
+    for (int k = 2; k <= h->depth; ++k) {
+        FLevel& L = h->lv[k];
+        CKS(dalloc(h, &L.d_Pi2, sizeof(dfl) * (size_t)std::max<int64_t>(L.npi, 1)));
+        launch_split_dfl((const double*)L.d_Pi, L.d_Pi2, L.npi, h->st);
+        CKS(dalloc(h, &L.d_Cp2, sizeof(dfl) * (size_t)std::max<int64_t>(L.ncp, 1)));
+        launch_split_dfl((const double*)L.d_Cp, L.d_Cp2, L.ncp, h->st);
+        CKS(dalloc(h, &L.d_Bp2, sizeof(dfl) * (size_t)std::max<int64_t>(L.nbp, 1)));
+        launch_split_dfl((const double*)L.d_Bp, L.d_Bp2, L.nbp, h->st);
+    }
+    CK(cudaGetLastError());
+    return IFMM_OK;
 }
 
 template <typename T>
@@ -713,7 +775,7 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
     T* vxs = (T*)pv;
     for (int k = kap; k >= 2; --k) {
         FLevel& L = h->lv[k];
-        LevelView<T> v = view_of<T>(h, L);
+        LevelView<T> v = solve_view<T>(h, L);
         for (int c = 0; c < 9; ++c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             launch_forward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vr[k - 1], vxs, nrhs, h->st);
@@ -722,7 +784,7 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
     launch_root_apply<T>(h->d_Dinv, h->M, vr[1], vx[1], nrhs, h->st);
     for (int k = 2; k <= kap; ++k) {
         FLevel& L = h->lv[k];
-        LevelView<T> v = view_of<T>(h, L);
+        LevelView<T> v = solve_view<T>(h, L);
         for (int c = 8; c >= 0; --c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             launch_backward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vx[k], vx[k - 1], vxs,
@@ -759,8 +821,8 @@ ifmm_status matvec_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y,
         size_t len = sizeof(double) * ((size_t)1 << (2 * k)) * r0 * nrhs;
         void* a = nullptr;
         void* b = nullptr;
-        CKS(workspace(h, 42 + 2 * k, len, &a));
-        CKS(workspace(h, 43 + 2 * k, len, &b));
+        CKS(workspace(h, 120 + 2 * k, len, &a));
+        CKS(workspace(h, 121 + 2 * k, len, &b));
         ym[k] = (double*)a;
         zm[k] = (double*)b;
     }
@@ -776,12 +838,53 @@ ifmm_status matvec_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y,
     return IFMM_OK;
 }
 
+// y = A~ x with the double-float copies of the operators on the FP32 pipe; x and y FP64 (the inner
+// Krylov products of IFMM_MIXED_SOLVE)
+ifmm_status matvec_dfl_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y, int64_t ldy, int nrhs) {
+    const int kap = h->depth, r0 = h->r0;
+    void* pxt = nullptr;
+    void* pout = nullptr;
+    CKS(workspace(h, 90, sizeof(dfl) * (size_t)h->N * nrhs, &pxt));
+    CKS(workspace(h, 91, sizeof(dfl) * (size_t)h->N * nrhs, &pout));
+    dfl* xt = (dfl*)pxt;
+    dfl* out = (dfl*)pout;
+    std::vector<dfl*> ym(kap + 1, nullptr), zm(kap + 1, nullptr);
+    for (int k = 2; k <= kap; ++k) {
+        size_t len = sizeof(dfl) * ((size_t)1 << (2 * k)) * r0 * nrhs;
+        void* a = nullptr;
+        void* b = nullptr;
+        CKS(workspace(h, 150 + 2 * k, len, &a));
+        CKS(workspace(h, 151 + 2 * k, len, &b));
+        ym[k] = (dfl*)a;
+        zm[k] = (dfl*)b;
+    }
+    launch_mv_permute_in<dfl>(x, ldx, h->N, nrhs, h->d_perm, xt, h->st);
+    launch_mv_leaf_up<dfl>(kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up<dfl>(k, h->ops[k].d_W0_2, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l<dfl>(k, h->ops[k].d_far0_2, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down<dfl>(k, h->ops[k].d_W0_2, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down<dfl>(kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt,
+                             h->d_p2p_off, h->d_p2p2, out, nrhs, h->st);
+    launch_mv_permute_out<dfl>(out, h->N, nrhs, h->d_perm, y, ldy, h->st);
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
 // FP64 GMRES(m) on A~ x = b, left-preconditioned by the IFMM solve M^{-1} (working precision T):
 // every column runs its own Arnoldi process, all columns in lockstep; classical Gram-Schmidt
 // applied twice; Givens rotations and the small triangular solves on the host. The monitored
 // quantity |g_{j+1}| = ||M^{-1}(b - A~ x_j)|| estimates the error of x_j since M^{-1} ~ A~^{-1}.
+// With IFMM_MIXED_SOLVE the preconditioner is the double-float replay and the Arnoldi products use
+// the double-float matvec (both on the FP32 pipe), and a cycle ends once its estimate has fallen
+// by refine_inner (or after m steps): the restart recomputes b - A~ x with the FP64 matvec, so the
+// double-float rounding limits each cycle's reduction, not the final accuracy (iterative
+// refinement with a mixed-precision inner GMRES). Only the estimate taken on that FP64 residual
+// ends the solve.
+
 template <typename T>
 ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int64_t ld) {
+    const bool inner32 = h->prm.precision == IFMM_MIXED_SOLVE;
+    const double inner_red = h->prm.refine_inner > 0.0 ? h->prm.refine_inner : 1e-4;
     const int64_t N = h->N;
     const int m = std::max(1, h->prm.refine_restart);
     const double tol = h->prm.refine_tol;
@@ -831,6 +934,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         }
         first = false;
         if (est <= tol || it >= h->prm.refine_maxit) break;
+        const double est_cycle = est;
         CK(cudaMemcpyAsync(dv, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, h->st));
         launch_colscale(V, N, N, nrhs, dv, h->st);
         std::fill(H.begin(), H.end(), 0.0);
@@ -838,7 +942,8 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         for (int j = 0; j < m; ++j) {
             double* Vj = V + (size_t)j * vec;
             double* Vn = V + (size_t)(j + 1) * vec;
-            CKS(matvec_impl(h, Vj, N, u, N, nrhs));
+            if (inner32) CKS(matvec_dfl_impl(h, Vj, N, u, N, nrhs));
+            else CKS(matvec_impl(h, Vj, N, u, N, nrhs));
             CKS(solve_once<T>(h, u, N, Vn, N, nrhs));
             for (int pass = 0; pass < 2; ++pass) {
                 CK(cudaMemsetAsync(dv, 0, sizeof(double) * (size_t)(j + 1) * nrhs, h->st));
@@ -881,6 +986,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
             ++it;
             k = j + 1;
             if (est <= tol || it >= h->prm.refine_maxit) break;
+            if (inner32 && est <= inner_red * est_cycle) break;
         }
         // y = R^{-1} g per column, x += V y
         std::vector<double> y((size_t)k * nrhs, 0.0);
@@ -897,7 +1003,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         launch_colnorm2(x, ld, N, nrhs, dv, h->st);
         CKS(fetch(1));
         for (int c = 0; c < nrhs; ++c) xn[c] = std::sqrt(hv[c]);
-        if (est <= tol || it >= h->prm.refine_maxit) break;
+        if ((est <= tol && !inner32) || it >= h->prm.refine_maxit) break;
     }
     h->stats.refine_iters = it;
     h->stats.last_update = est;
@@ -984,6 +1090,7 @@ void ifmm_default_params(ifmm_params* p) {
     p->refine_tol = 0.0;
     p->refine_maxit = 100;
     p->refine_restart = 30;
+    p->refine_inner = 1e-4;
 }
 
 ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm_params* p, void* stream,
@@ -994,7 +1101,8 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP) return IFMM_ERR_INVALID_ARG;
     if (kernel == IFMM_K_EXP && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
     if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
-    if (p->precision != IFMM_FP64 && p->precision != IFMM_MIXED) return IFMM_ERR_INVALID_ARG;
+    if (p->precision != IFMM_FP64 && p->precision != IFMM_MIXED && p->precision != IFMM_MIXED_SOLVE)
+        return IFMM_ERR_INVALID_ARG;
     if (p->tau_ref < 0 || p->tau_ref > 2) return IFMM_ERR_INVALID_ARG;
     if (p->r_cap > 0 && p->r_cap < p->cheb_p * p->cheb_p) return IFMM_ERR_INVALID_ARG;
     for (int64_t i = 0; i < 2 * N; ++i)
@@ -1032,6 +1140,13 @@ ifmm_status ifmm_factor(ifmm_h h) {
     release_factors(h);
     auto t0 = std::chrono::steady_clock::now();
     ifmm_status s = h->prm.precision == IFMM_MIXED ? factor_impl<float>(h) : factor_impl<double>(h);
+    if ((s == IFMM_OK || s == IFMM_ERR_RANK_OVERFLOW) && h->prm.precision == IFMM_MIXED_SOLVE) {
+        ifmm_status s2 = split_factors(h);
+        if (s2 != IFMM_OK) {
+            h->factored = false;
+            return s2;
+        }
+    }
     h->stats.t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (s != IFMM_OK && s != IFMM_ERR_RANK_OVERFLOW) h->factored = false;
     return s;
@@ -1046,8 +1161,9 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
     h->err.clear();
     auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launches_so_far();
-    ifmm_status s = h->prm.precision == IFMM_MIXED ? solve_impl<float>(h, b_dev, x_dev, nrhs, ld)
-                                                   : solve_impl<double>(h, b_dev, x_dev, nrhs, ld);
+    ifmm_status s = h->prm.precision == IFMM_MIXED         ? solve_impl<float>(h, b_dev, x_dev, nrhs, ld)
+                    : h->prm.precision == IFMM_MIXED_SOLVE ? solve_impl<dfl>(h, b_dev, x_dev, nrhs, ld)
+                                                           : solve_impl<double>(h, b_dev, x_dev, nrhs, ld);
     h->stats.launches_solve = launches_so_far() - l0;
     cudaError_t e = cudaStreamSynchronize(h->st);
     if (s == IFMM_OK && e != cudaSuccess) {
@@ -1056,6 +1172,20 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
     }
     h->stats.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return s;
+}
+
+// Transposed solve. Both kernels of the library are symmetric, K(x, y) = K(y, x), and the build
+// keeps A~ symmetric: P2P_ji = P2P_ij^T, M2L_ji = M2L_ij^T, L2P = P2M^T; the elimination compresses
+// the fill of every box with one basis for its row and its column (F_qp = F_pq^T), so the compressed
+// matrix that the factors invert is symmetric as well. A~^T x = b is therefore the system of
+// ifmm_solve, solved by the same replay of the factors.
+ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld) {
+    if (!h) return IFMM_ERR_INVALID_ARG;
+    if (h->kernel != IFMM_K_INV_R && h->kernel != IFMM_K_EXP) {
+        h->err = "ifmm_solve_T: the transposed replay is only provided for symmetric kernels";
+        return IFMM_ERR_INVALID_ARG;
+    }
+    return ifmm_solve(h, b_dev, x_dev, nrhs, ld);
 }
 
 ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld) {

@@ -341,162 +341,198 @@ void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, co
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP64 matvec
+// FMM matvec y = A~ x (Table "table_FMM_operators"), element type T: FP64 for the residuals of the
+// refinement, double-float (operators split once into double-float copies) for the inner Krylov
+// steps of the mixed-precision solve. Vectors outside are FP64; the permutation kernels convert.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt) {
+template <typename T>
+__global__ void k_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* xt) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * nrhs) return;
     int64_t i = t / nrhs;
     int j = (int)(t - i * nrhs);
-    xt[t] = x[perm[i] + (int64_t)j * ld];
+    xt[t] = (T)x[perm[i] + (int64_t)j * ld];
 }
-void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt,
+template <typename T>
+void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* xt,
                           cudaStream_t st) {
-    k_mv_permute_in<<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(x, ld, N, nrhs, perm, xt); count_launches(1);
+    k_mv_permute_in<T><<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(x, ld, N, nrhs, perm, xt); count_launches(1);
 }
 
-__global__ void k_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld) {
+template <typename T>
+__global__ void k_mv_permute_out(const T* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * nrhs) return;
     int64_t i = t / nrhs;
     int j = (int)(t - i * nrhs);
-    y[perm[i] + (int64_t)j * ld] = yt[t];
+    y[perm[i] + (int64_t)j * ld] = (double)yt[t];
 }
-void launch_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
+template <typename T>
+void launch_mv_permute_out(const T* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
                            cudaStream_t st) {
-    k_mv_permute_out<<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(yt, N, nrhs, perm, y, ld); count_launches(1);
+    k_mv_permute_out<T><<<(unsigned)((N * nrhs + 255) / 256), 256, 0, st>>>(yt, N, nrhs, perm, y, ld); count_launches(1);
 }
 
 // P2M: y_b = W0_b^T x_b   (y layout [box][r0][nrhs])
-__global__ void __launch_bounds__(kThreads) k_mv_leaf_up(const double* W0, const int64_t* leaf_start,
-                                                         const int* leaf_count, int r0, const double* xt, double* y,
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_leaf_up(const T* W0, const int64_t* leaf_start,
+                                                         const int* leaf_count, int r0, const T* xt, T* y,
                                                          int nrhs) {
-    __shared__ double sm[gemm_smem<double>::value];
+    __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
     const int64_t s0 = leaf_start[b];
     const int n = leaf_count[b];
-    const double* W = W0 + s0 * r0;
-    const double* xb = xt + s0 * nrhs;
-    double* yb = y + (int64_t)b * r0 * nrhs;
-    cta_gemm<double>(
+    const T* W = W0 + s0 * r0;
+    const T* xb = xt + s0 * nrhs;
+    T* yb = y + (int64_t)b * r0 * nrhs;
+    cta_gemm<T>(
         r0, nrhs, n, [&](int i, int k) { return W[(size_t)k * r0 + i]; },
         [&](int k, int j) { return xb[(size_t)k * nrhs + j]; },
-        [&](int i, int j, double v) { yb[(size_t)i * nrhs + j] = v; }, sm);
+        [&](int i, int j, T v) { yb[(size_t)i * nrhs + j] = v; }, sm);
 }
-void launch_mv_leaf_up(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
-                       const double* xt, double* y, int nrhs, cudaStream_t st) {
-    k_mv_leaf_up<<<1u << (2 * depth), kThreads, 0, st>>>(W0, leaf_start, leaf_count, r0, xt, y, nrhs); count_launches(1);
+template <typename T>
+void launch_mv_leaf_up(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                       const T* xt, T* y, int nrhs, cudaStream_t st) {
+    k_mv_leaf_up<T><<<1u << (2 * depth), kThreads, 0, st>>>(W0, leaf_start, leaf_count, r0, xt, y, nrhs); count_launches(1);
 }
 
 // M2M: y_P = W0_P^T [y_c]  (W0_P rows c*r0 + t)
-__global__ void __launch_bounds__(kThreads) k_mv_up(int k, const double* W0, int r0, const double* ychild, double* y,
-                                                    int nrhs) {
-    __shared__ double sm[gemm_smem<double>::value];
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs) {
+    __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
     const int side = 1 << k, cs = side << 1;
     const int bx = b % side, by = b / side;
-    const double* W = W0 + (int64_t)b * 4 * r0 * r0;
-    double* yb = y + (int64_t)b * r0 * nrhs;
-    cta_gemm<double>(
+    const T* W = W0 + (int64_t)b * 4 * r0 * r0;
+    T* yb = y + (int64_t)b * r0 * nrhs;
+    cta_gemm<T>(
         r0, nrhs, 4 * r0, [&](int i, int kk) { return W[(size_t)kk * r0 + i]; },
         [&](int kk, int j) {
             int c = kk / r0, t = kk - c * r0;
             int cg = (2 * bx + (c & 1)) + cs * (2 * by + (c >> 1));
             return ychild[((int64_t)cg * r0 + t) * nrhs + j];
         },
-        [&](int i, int j, double v) { yb[(size_t)i * nrhs + j] = v; }, sm);
+        [&](int i, int j, T v) { yb[(size_t)i * nrhs + j] = v; }, sm);
 }
-void launch_mv_up(int k, const double* W0, int r0, const double* ychild, double* y, int nrhs, cudaStream_t st) {
-    k_mv_up<<<1u << (2 * k), kThreads, 0, st>>>(k, W0, r0, ychild, y, nrhs); count_launches(1);
+template <typename T>
+void launch_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st) {
+    k_mv_up<T><<<1u << (2 * k), kThreads, 0, st>>>(k, W0, r0, ychild, y, nrhs); count_launches(1);
 }
 
 // M2L: z_b = sum_{q in I_b} M2L_bq y_q
-__global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const double* far0, int r0, const double* y, double* z,
-                                                     int nrhs) {
-    __shared__ double sm[gemm_smem<double>::value];
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs) {
+    __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
     const int side = 1 << k;
     const int bx = b % side, by = b / side;
-    double* zb = z + (int64_t)b * r0 * nrhs;
-    for (int t = threadIdx.x; t < r0 * nrhs; t += blockDim.x) zb[t] = 0.0;
+    T* zb = z + (int64_t)b * r0 * nrhs;
+    for (int t = threadIdx.x; t < r0 * nrhs; t += blockDim.x) zb[t] = (T)0;
     __syncthreads();
     for (int j = 0; j < 36; ++j) {
         const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
         if (!in_grid2(qx, qy, side) || max(abs(qx - bx), abs(qy - by)) <= 1) continue;
         const int q = qx + side * qy;
-        const double* M = far0 + ((int64_t)b * 36 + j) * r0 * r0;
-        const double* yq = y + (int64_t)q * r0 * nrhs;
-        cta_gemm<double>(
+        const T* M = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+        const T* yq = y + (int64_t)q * r0 * nrhs;
+        cta_gemm<T>(
             r0, nrhs, r0, [&](int i, int kk) { return M[(size_t)i * r0 + kk]; },
             [&](int kk, int jj) { return yq[(size_t)kk * nrhs + jj]; },
-            [&](int i, int jj, double v) { zb[(size_t)i * nrhs + jj] += v; }, sm);
+            [&](int i, int jj, T v) { zb[(size_t)i * nrhs + jj] += v; }, sm);
         __syncthreads();
     }
 }
-void launch_mv_m2l(int k, const double* far0, int r0, const double* y, double* z, int nrhs, cudaStream_t st) {
-    k_mv_m2l<<<1u << (2 * k), kThreads, 0, st>>>(k, far0, r0, y, z, nrhs); count_launches(1);
+template <typename T>
+void launch_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st) {
+    k_mv_m2l<T><<<1u << (2 * k), kThreads, 0, st>>>(k, far0, r0, y, z, nrhs); count_launches(1);
 }
 
 // L2L: z_c += W0_P[rows of c] z_P, one block per child box c at level k+1
-__global__ void __launch_bounds__(kThreads) k_mv_down(int k, const double* W0, int r0, const double* z,
-                                                      double* zchild, int nrhs) {
-    __shared__ double sm[gemm_smem<double>::value];
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs) {
+    __shared__ T sm[gemm_smem<T>::value];
     const int cgi = blockIdx.x;
     const int cs = 2 << k;
     const int cx = cgi % cs, cy = cgi / cs;
     const int P = (cx >> 1) + (cs >> 1) * (cy >> 1);
     const int c = (cx & 1) + 2 * (cy & 1);
-    const double* W = W0 + ((int64_t)P * 4 + c) * r0 * r0;
-    const double* zP = z + (int64_t)P * r0 * nrhs;
-    double* zc = zchild + (int64_t)cgi * r0 * nrhs;
-    cta_gemm<double>(
+    const T* W = W0 + ((int64_t)P * 4 + c) * r0 * r0;
+    const T* zP = z + (int64_t)P * r0 * nrhs;
+    T* zc = zchild + (int64_t)cgi * r0 * nrhs;
+    cta_gemm<T>(
         r0, nrhs, r0, [&](int i, int kk) { return W[(size_t)i * r0 + kk]; },
         [&](int kk, int j) { return zP[(size_t)kk * nrhs + j]; },
-        [&](int i, int j, double v) { zc[(size_t)i * nrhs + j] += v; }, sm);
+        [&](int i, int j, T v) { zc[(size_t)i * nrhs + j] += v; }, sm);
 }
-void launch_mv_down(int k, const double* W0, int r0, const double* z, double* zchild, int nrhs, cudaStream_t st) {
-    k_mv_down<<<1u << (2 * (k + 1)), kThreads, 0, st>>>(k, W0, r0, z, zchild, nrhs); count_launches(1);
+template <typename T>
+void launch_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st) {
+    k_mv_down<T><<<1u << (2 * (k + 1)), kThreads, 0, st>>>(k, W0, r0, z, zchild, nrhs); count_launches(1);
 }
 
 // L2P + P2P: out_b = W0_b z_b + sum_{q in N_b} P2P_bq x_q
-__global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start,
-                                                           const int* leaf_count, int r0, const double* z,
-                                                           const double* xt, const int64_t* p2p_off,
-                                                           const double* p2p, double* out, int nrhs) {
-    __shared__ double sm[gemm_smem<double>::value];
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start,
+                                                           const int* leaf_count, int r0, const T* z, const T* xt,
+                                                           const int64_t* p2p_off, const T* p2p, T* out, int nrhs) {
+    __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
     const int side = 1 << depth;
     const int bx = b % side, by = b / side;
     const int64_t s0 = leaf_start[b];
     const int n = leaf_count[b];
-    const double* W = W0 + s0 * r0;
-    const double* zb = z + (int64_t)b * r0 * nrhs;
-    double* ob = out + s0 * nrhs;
-    cta_gemm<double>(
+    const T* W = W0 + s0 * r0;
+    const T* zb = z + (int64_t)b * r0 * nrhs;
+    T* ob = out + s0 * nrhs;
+    cta_gemm<T>(
         n, nrhs, r0, [&](int i, int kk) { return W[(size_t)i * r0 + kk]; },
         [&](int kk, int j) { return zb[(size_t)kk * nrhs + j]; },
-        [&](int i, int j, double v) { ob[(size_t)i * nrhs + j] = v; }, sm);
+        [&](int i, int j, T v) { ob[(size_t)i * nrhs + j] = v; }, sm);
     __syncthreads();
     for (int d = 0; d < 9; ++d) {
         const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
         if (!in_grid2(qx, qy, side)) continue;
         const int q = qx + side * qy;
         const int nq = leaf_count[q];
-        const double* B = p2p + p2p_off[(int64_t)b * 9 + d];
-        const double* xq = xt + leaf_start[q] * nrhs;
-        cta_gemm<double>(
+        const T* B = p2p + p2p_off[(int64_t)b * 9 + d];
+        const T* xq = xt + leaf_start[q] * nrhs;
+        cta_gemm<T>(
             n, nrhs, nq, [&](int i, int kk) { return B[(size_t)i * nq + kk]; },
             [&](int kk, int j) { return xq[(size_t)kk * nrhs + j]; },
-            [&](int i, int j, double v) { ob[(size_t)i * nrhs + j] += v; }, sm);
+            [&](int i, int j, T v) { ob[(size_t)i * nrhs + j] += v; }, sm);
         __syncthreads();
     }
 }
-void launch_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
-                         const double* z, const double* xt, const int64_t* p2p_off, const double* p2p,
-                         double* out, int nrhs, cudaStream_t st) {
-    k_mv_leaf_down<<<1u << (2 * depth), kThreads, 0, st>>>(depth, W0, leaf_start, leaf_count, r0, z, xt, p2p_off, p2p,
-                                                           out, nrhs); count_launches(1);
+template <typename T>
+void launch_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                         const T* z, const T* xt, const int64_t* p2p_off, const T* p2p, T* out, int nrhs,
+                         cudaStream_t st) {
+    k_mv_leaf_down<T><<<1u << (2 * depth), kThreads, 0, st>>>(depth, W0, leaf_start, leaf_count, r0, z, xt, p2p_off,
+                                                              p2p, out, nrhs); count_launches(1);
 }
+
+// split of an FP64 array into double-float pairs
+__global__ void k_split_dfl(const double* a, dfl* b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = dfl(a[i]);
+}
+void launch_split_dfl(const double* a, dfl* b, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    k_split_dfl<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(a, b, n); count_launches(1);
+}
+
+#define IFMM_MV_INSTANTIATE(T)                                                                                    \
+    template void launch_mv_permute_in<T>(const double*, int64_t, int64_t, int, const int64_t*, T*, cudaStream_t); \
+    template void launch_mv_permute_out<T>(const T*, int64_t, int, const int64_t*, double*, int64_t, cudaStream_t); \
+    template void launch_mv_leaf_up<T>(int, const T*, const int64_t*, const int*, int, const T*, T*, int,         \
+                                       cudaStream_t);                                                            \
+    template void launch_mv_up<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                           \
+    template void launch_mv_m2l<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                          \
+    template void launch_mv_down<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                         \
+    template void launch_mv_leaf_down<T>(int, const T*, const int64_t*, const int*, int, const T*, const T*,      \
+                                         const int64_t*, const T*, T*, int, cudaStream_t);
+IFMM_MV_INSTANTIATE(double)
+IFMM_MV_INSTANTIATE(dfl)
+#undef IFMM_MV_INSTANTIATE
 
 // x += d (d with leading dimension N); nrm[2j] += ||d_j||^2, nrm[2j+1] += ||x_j||^2 (x after the update)
 __global__ void k_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm) {

@@ -7,6 +7,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "ifmm_internal.h"
+
 #define IFMM_DEVINL __device__ __forceinline__
 
 namespace ifmm {
@@ -89,6 +93,95 @@ __device__ inline int block_argmax(double v, int idx, double* vred, int* ired, d
 // ---------------------------------------------------------------------------------------------
 template <typename Acc> struct gemm_smem { static constexpr int value = 2 * 16 * 65; };
 template <> struct gemm_smem<double> { static constexpr int value = 2 * 32 * 64; };
+template <> struct gemm_smem<dfl> { static constexpr int value = 2 * 32 * 33; };
+
+// ---------------------------------------------------------------------------------------------
+// double-float arithmetic (the type is declared in ifmm_internal.h). The intrinsics keep the
+// compiler from contracting the error-free transformations.
+// ---------------------------------------------------------------------------------------------
+// s += a * b: the exact product a.hi b.hi = p + e (FMA), the cross terms a.hi b.lo + a.lo b.hi added
+// to e (a.lo b.lo dropped), p added to s.hi exactly (TwoSum), the rounding errors gathered in s.lo
+IFMM_DEVINL void dfl_fma_acc(dfl& s, dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float t = __fadd_rn(s.hi, p);
+    const float z = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
+// renormalise: hi = fl(hi + lo), lo = the exact remainder (TwoSum)
+IFMM_DEVINL dfl dfl_norm(dfl a) {
+    const float t = __fadd_rn(a.hi, a.lo);
+    const float z = __fsub_rn(t, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, z)), __fsub_rn(a.lo, z));
+    return dfl(t, err);
+}
+IFMM_DEVINL dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float z = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return dfl_norm(dfl(s, e));
+}
+IFMM_DEVINL dfl operator-(dfl a, dfl b) { return a + dfl(-b.hi, -b.lo); }
+IFMM_DEVINL dfl& operator+=(dfl& a, dfl b) {
+    a = a + b;
+    return a;
+}
+
+// CTA GEMM in double-float: output tiles of 32 x 32, each of the 256 threads owns 2 x 2 outputs
+// (rows ty, ty + 16, columns tx, tx + 16), k-steps of 32 staged in padded shared tiles. About 11
+// FP32 operations per multiply-add and 4 shared loads per 4 multiply-adds: FP32-pipe bound.
+template <class LA, class LB, class EPI>
+__device__ void cta_gemm_dfl(int M, int N, int K, LA la, LB lb, EPI epi, dfl* smem, int tile0, int tstride) {
+    constexpr int TM = 32, TN = 32, KC = 32, LDA = TM + 1, LDB = TN + 1;
+    dfl* As = smem;              // [KC][LDA] : As[k][i]
+    dfl* Bs = smem + KC * LDA;   // [KC][LDB] : Bs[k][j]
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int tn = (N + TN - 1) / TN, tm = (M + TM - 1) / TM;
+    for (int tile = tile0; tile < tm * tn; tile += tstride) {
+        const int m0 = (tile / tn) * TM, n0 = (tile % tn) * TN;
+        dfl acc[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) acc[a][b] = dfl(0.0f, 0.0f);
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            for (int t = tid; t < TM * KC; t += 256) {
+                const int i = t / KC, k = t - i * KC;
+                const int gi = m0 + i, gk = k0 + k;
+                As[k * LDA + i] = (gi < M && gk < K) ? dfl(la(gi, gk)) : dfl(0.0f, 0.0f);
+            }
+            for (int t = tid; t < KC * TN; t += 256) {
+                const int k = t / TN, j = t - k * TN;
+                const int gk = k0 + k, gj = n0 + j;
+                Bs[k * LDB + j] = (gk < K && gj < N) ? dfl(lb(gk, gj)) : dfl(0.0f, 0.0f);
+            }
+            __syncthreads();
+            const int kc = min(KC, K - k0);
+            for (int kk = 0; kk < kc; ++kk) {
+                const dfl a0 = As[kk * LDA + ty], a1 = As[kk * LDA + ty + 16];
+                const dfl b0 = Bs[kk * LDB + tx], b1 = Bs[kk * LDB + tx + 16];
+                dfl_fma_acc(acc[0][0], a0, b0);
+                dfl_fma_acc(acc[0][1], a0, b1);
+                dfl_fma_acc(acc[1][0], a1, b0);
+                dfl_fma_acc(acc[1][1], a1, b1);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int gi = m0 + ty + 16 * a, gj = n0 + tx + 16 * b;
+                if (gi < M && gj < N) epi(gi, gj, dfl_norm(acc[a][b]));
+            }
+    }
+}
 
 template <typename Acc, class LA, class LB, class EPI>
 __device__ void cta_gemm_exact(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem, int tile0, int tstride) {
@@ -136,7 +229,10 @@ __device__ void cta_gemm_exact(int M, int N, int K, LA la, LB lb, EPI epi, Acc* 
 
 template <typename Acc, class LA, class LB, class EPI>
 __device__ void cta_gemm(int M, int N, int K, LA la, LB lb, EPI epi, Acc* smem, int tile0 = 0, int tstride = 1) {
-    if constexpr (sizeof(Acc) == 8) {
+    if constexpr (std::is_same<Acc, dfl>::value) {
+        cta_gemm_dfl(M, N, K, la, lb, epi, smem, tile0, tstride);
+        return;
+    } else if constexpr (sizeof(Acc) == 8) {
         cta_gemm_exact<Acc>(M, N, K, la, lb, epi, smem, tile0, tstride);
         return;
     } else {

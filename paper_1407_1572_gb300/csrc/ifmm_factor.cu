@@ -31,6 +31,7 @@ long long launches_so_far() { return g_launches; }
 
 template <typename T> struct AccOf { using type = double; };
 template <> struct AccOf<float> { using type = float; };
+template <> struct AccOf<dfl> { using type = dfl; };
 
 IFMM_DEVINL bool in_grid(int x, int y, int side) { return x >= 0 && y >= 0 && x < side && y < side; }
 
@@ -1111,5 +1112,14 @@ void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, d
 
 IFMM_INSTANTIATE(double)
 IFMM_INSTANTIATE(float)
+
+// the replay (Algorithm 2) also runs on double-float copies of FP64 factors
+template void launch_forward_colour<dfl>(const LevelView<dfl>&, const int*, int, int, const int64_t*, dfl*, dfl*,
+                                         dfl*, int, cudaStream_t);
+template void launch_backward_colour<dfl>(const LevelView<dfl>&, const int*, int, int, const int64_t*, const dfl*,
+                                          dfl*, const dfl*, dfl*, int, cudaStream_t);
+template void launch_root_apply<dfl>(const double*, int, const dfl*, dfl*, int, cudaStream_t);
+template void launch_permute_in<dfl>(const double*, int64_t, int64_t, int, const int64_t*, dfl*, cudaStream_t);
+template void launch_permute_out<dfl>(const dfl*, int64_t, int, const int64_t*, double*, int64_t, cudaStream_t);
 
 }  // namespace ifmm

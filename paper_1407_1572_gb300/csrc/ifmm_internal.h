@@ -5,6 +5,20 @@
 
 namespace ifmm {
 
+// Double-float number hi + lo (two FP32 values, |lo| <= ulp(hi) / 2 when normalised): about 48
+// significand bits with FP32's exponent range. GB300 runs FP32 at 64 times its FP64 rate, so the
+// replay and the FMM matvec of the mixed-precision solve keep their operands in this form and run
+// on the FP32 pipe (multiply-adds by the exact-product and exact-sum transformations of Dekker and
+// Knuth); FP64 values split as hi = fl32(d), lo = fl32(d - hi).
+struct dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit dfl(int v) : hi((float)v), lo(0.0f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
 // kernels launched by this library in this process (every launcher adds its launches)
 void count_launches(int n);
 long long launches_so_far();
@@ -117,22 +131,28 @@ void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const doubl
 void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
                       const int* leaf_count, const int64_t* p2p_off, double* p2p, double* sA_bits,
                       cudaStream_t st);
-// FP64 FMM matvec pieces
-void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, double* xt,
+// FMM matvec pieces, element type T = double (residuals) or dfl (inner Krylov steps)
+template <typename T>
+void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* xt,
                           cudaStream_t st);
-void launch_mv_leaf_up(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
-                       const double* xt, double* y, int nrhs, cudaStream_t st);
-void launch_mv_up(int k, const double* W0, int r0, const double* ychild, double* y, int nrhs,
-                  cudaStream_t st);
-void launch_mv_m2l(int k, const double* far0, int r0, const double* y, double* z, int nrhs,
-                   cudaStream_t st);
-void launch_mv_down(int k, const double* W0, int r0, const double* z, double* zchild, int nrhs,
-                    cudaStream_t st);
-void launch_mv_leaf_down(int depth, const double* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
-                         const double* z, const double* xt, const int64_t* p2p_off, const double* p2p,
-                         double* out, int nrhs, cudaStream_t st);
-void launch_mv_permute_out(const double* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
+template <typename T>
+void launch_mv_leaf_up(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                       const T* xt, T* y, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+                         const T* z, const T* xt, const int64_t* p2p_off, const T* p2p, T* out, int nrhs,
+                         cudaStream_t st);
+template <typename T>
+void launch_mv_permute_out(const T* yt, int64_t N, int nrhs, const int64_t* perm, double* y, int64_t ld,
                            cudaStream_t st);
+// b = a split into double-float pairs, n elements
+void launch_split_dfl(const double* a, dfl* b, int64_t n, cudaStream_t st);
 // refinement helpers
 void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm,
                        cudaStream_t st);

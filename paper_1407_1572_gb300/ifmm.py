@@ -17,7 +17,7 @@ IFMM_OK, IFMM_ERR_INVALID_ARG, IFMM_ERR_CUDA, IFMM_ERR_OOM = 0, 1, 2, 3
 IFMM_ERR_SINGULAR_PIVOT, IFMM_ERR_RANK_OVERFLOW, IFMM_ERR_NOCONV = 4, 5, 6
 IFMM_ERR_TIMEOUT, IFMM_ERR_STATE = 7, 8
 IFMM_K_INV_R, IFMM_K_EXP = 0, 1
-IFMM_FP64, IFMM_MIXED = 0, 1
+IFMM_FP64, IFMM_MIXED, IFMM_MIXED_SOLVE = 0, 1, 2
 _NAMES = {0: "IFMM_OK", 1: "IFMM_ERR_INVALID_ARG", 2: "IFMM_ERR_CUDA", 3: "IFMM_ERR_OOM",
           4: "IFMM_ERR_SINGULAR_PIVOT", 5: "IFMM_ERR_RANK_OVERFLOW", 6: "IFMM_ERR_NOCONV",
           7: "IFMM_ERR_TIMEOUT", 8: "IFMM_ERR_STATE"}
@@ -29,7 +29,8 @@ class ifmm_params(ctypes.Structure):
                 ("kparam", ctypes.c_double * 4), ("box", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("tau_ref", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
-                ("refine_restart", ctypes.c_int)]
+                ("refine_restart", ctypes.c_int),
+                ("refine_inner", ctypes.c_double)]
 
 
 class ifmm_stats(ctypes.Structure):
@@ -57,7 +58,7 @@ class IFMMError(RuntimeError):
 _lib = None
 
 # every symbol include/ifmm.h declares
-SYMBOLS = ["ifmm_default_params", "ifmm_build", "ifmm_factor", "ifmm_solve", "ifmm_solve_host",
+SYMBOLS = ["ifmm_default_params", "ifmm_build", "ifmm_factor", "ifmm_solve", "ifmm_solve_T", "ifmm_solve_host",
            "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_get_ranks", "ifmm_get_stats", "ifmm_last_error",
            "ifmm_destroy"]
 
@@ -84,7 +85,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ifmm_build.restype = ip
     lib.ifmm_factor.argtypes = [vp]
     lib.ifmm_factor.restype = ip
-    for name in ("ifmm_solve", "ifmm_solve_host", "ifmm_matvec", "ifmm_matvec_noalloc"):
+    for name in ("ifmm_solve", "ifmm_solve_T", "ifmm_solve_host", "ifmm_matvec", "ifmm_matvec_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, ip, i64]
         getattr(lib, name).restype = ip
     lib.ifmm_get_ranks.argtypes = [vp, ip, vp]
@@ -136,6 +137,11 @@ def ifmm_factor(h, allow_overflow: bool = False) -> int:
 
 def ifmm_solve(h, b_ptr: int, x_ptr: int, nrhs: int, ld: int, allow_noconv: bool = False) -> int:
     return _check(h, load().ifmm_solve(h, ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr), nrhs, ld),
+                  allow=(IFMM_ERR_NOCONV,) if allow_noconv else ())
+
+
+def ifmm_solve_T(h, b_ptr: int, x_ptr: int, nrhs: int, ld: int, allow_noconv: bool = False) -> int:
+    return _check(h, load().ifmm_solve_T(h, ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr), nrhs, ld),
                   allow=(IFMM_ERR_NOCONV,) if allow_noconv else ())
 
 
@@ -222,6 +228,13 @@ class IFMM:
         bt = self._colmajor(b)
         xt = self._torch.empty_like(bt)
         ifmm_solve(self.h, bt.data_ptr(), xt.data_ptr(), bt.shape[0], self.N, allow_noconv)
+        x = xt.t()
+        return x[:, 0] if b.dim() == 1 else x
+
+    def solve_T(self, b, allow_noconv: bool = False):
+        bt = self._colmajor(b)
+        xt = self._torch.empty_like(bt)
+        ifmm_solve_T(self.h, bt.data_ptr(), xt.data_ptr(), bt.shape[0], self.N, allow_noconv)
         x = xt.t()
         return x[:, 0] if b.dim() == 1 else x
 

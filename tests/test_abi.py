@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     txt = open(os.path.join(ROOT, "include", "ifmm.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(ifmm_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(ifmm_[A-Za-z_]+)\s*\(", txt)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -27,6 +27,7 @@ def test_default_params_and_struct_layout():
     p = ifmm.default_params()
     assert (p.dim, p.depth, p.cheb_p, p.precision, p.tau_ref) == (2, 3, 4, 0, 1)
     assert p.box[2] == 1.0 and p.eps == 1e-10 and p.refine_maxit == 100 and p.refine_restart == 30
+    assert p.refine_inner == 1e-4
     # host-side argument checks reject bad input without touching a device
     h = ctypes.c_void_p()
     lib = ifmm.load()

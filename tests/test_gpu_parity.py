@@ -133,10 +133,11 @@ def test_exp_kernel_matches_oracle(ifmm):
     assert _rel(g.solve(_t(b)).cpu().numpy(), o.solve(b)) <= 1e-10
 
 
-@pytest.mark.parametrize("kernel,precision", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("kernel,precision", [(0, 0), (1, 0), (1, 1), (0, 2), (1, 2)])
 def test_refined_solution_meets_tolerance(ifmm, kernel, precision):
     """GMRES refinement preconditioned by the IFMM solve reaches the manufactured solution within
-    max(eps, 1e-6) with the FP64 elimination on both kernels. The FP32 elimination is checked on
+    max(eps, 1e-6) with the FP64 elimination on both kernels, with the solve phase in FP64
+    (precision 0) or in FP32 with FP64 restart residuals (precision 2). The FP32 elimination is checked on
     the positive-definite exponential kernel only, to 1e-3: the refinement's Krylov recurrence is
     FP64 but the preconditioner is applied in FP32, so the error it can certify stops near
     u_fp32 times the pivot blocks' condition numbers (measured 1.5e-4 here); on 1/r + sqrt(N) I the
@@ -152,9 +153,72 @@ def test_refined_solution_meets_tolerance(ifmm, kernel, precision):
     xs = inputs.rhs(21, N, 4)
     b = g.matvec(_t(xs))
     x = g.solve(b, allow_noconv=True).cpu().numpy()
-    bar = max(eps, 1e-6) if precision == 0 else 1e-3
+    bar = max(eps, 1e-6) if precision != 1 else 1e-3
     assert _rel(x, xs) <= bar
     assert g.stats()["refine_iters"] >= 1
+
+
+def test_double_float_replay_of_fp64_factors(ifmm):
+    """IFMM_MIXED_SOLVE factors in FP64 exactly as IFMM_FP64 (same ranks) and replays double-float
+    copies of the factors (hi + lo FP32 pairs, unit roundoff about 2^-48) on the FP32 pipe: the
+    unrefined solve matches the FP64 replay to 1e-9 relative. (A plain FP32 replay differs by
+    8e-5 here, by 1.0 at N = 65,536 and by 1.5e3 at N = 2^20: the pivot blocks amplify rounding.)"""
+    N, depth, p, eps = 4096, 3, 4, 1e-6
+    pts = inputs.uniform_points(1407, N)
+    g64 = _gpu(ifmm, pts, depth, p, eps, precision=0)
+    g32 = _gpu(ifmm, pts, depth, p, eps, precision=2)
+    g64.factor()
+    g32.factor()
+    for k in range(2, depth + 1):
+        assert np.array_equal(g64.ranks(k), g32.ranks(k))
+    b = inputs.rhs(7, N, 4)
+    x64 = g64.solve(_t(b)).cpu().numpy()
+    x32 = g32.solve(_t(b)).cpu().numpy()
+    d = _rel(x32, x64)
+    print(f"double-float replay vs FP64 replay: {d:.2e}")
+    assert d <= 1e-9
+
+
+def test_mixed_solve_config_65536(ifmm):
+    """N = 65,536, depth 5, rank 16, eps 1e-6, 8 right-hand sides: the FP64 and the mixed-precision
+    solve phase both reach the manufactured solution within 1e-6."""
+    N, depth, p, eps = 65536, 5, 4, 1e-6
+    pts = inputs.uniform_points(1409, N)
+    xs = inputs.rhs(1410, N, 8)
+    errs = {}
+    for prec in (0, 2):
+        prm = ifmm.default_params(depth=depth, cheb_p=p, eps=eps, diag=math.sqrt(N), precision=prec, tau_ref=1,
+                                  refine_tol=1e-7, refine_maxit=120, refine_restart=30)
+        g = ifmm.IFMM(pts, 0, prm)
+        g.factor()
+        b = g.matvec(_t(xs))
+        x = g.solve(b).cpu().numpy()
+        errs[prec] = (_rel(x, xs), g.stats()["refine_iters"])
+        g.close()
+    print("errors / iterations", errs)
+    assert errs[0][0] <= 1e-6 and errs[2][0] <= 1e-6
+
+
+def test_transposed_solve(ifmm):
+    """ifmm_solve_T solves A~^T x = b: with no compression it reproduces the dense solve of the
+    transposed FMM matrix, and with compression the factors it replays define a symmetric
+    operator, <u, M^{-1} v> = <M^{-T} u, v> to rounding."""
+    N, depth, p = 1024, 3, 3
+    pts = inputs.uniform_points(78, N)
+    g = _gpu(ifmm, pts, depth, p, 0.0)
+    g.factor()
+    A = _oracle(pts, depth, p, 0.0).dense_tilde()
+    b = inputs.rhs(5, N, 2)
+    assert _rel(g.solve_T(_t(b)).cpu().numpy(), np.linalg.solve(A.T, b)) <= 1e-10
+    N, depth, p, eps = 4096, 3, 4, 1e-6
+    pts = inputs.uniform_points(79, N)
+    g = _gpu(ifmm, pts, depth, p, eps)
+    g.factor()
+    u, v = inputs.rhs(11, N, 1)[:, 0], inputs.rhs(12, N, 1)[:, 0]
+    mv = g.solve(_t(v)).cpu().numpy()
+    mtu = g.solve_T(_t(u)).cpu().numpy()
+    lhs, rhs = float(u @ mv), float(mtu @ v)
+    assert abs(lhs - rhs) <= 1e-9 * np.linalg.norm(u) * np.linalg.norm(mv)
 
 
 def test_solve_host_equals_device_solve(ifmm):
