@@ -365,6 +365,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
     v.symmetric = 1;   // both kernels, 1/r and exp(-r/l), are symmetric
+    v.gemm_dfl = (std::is_same<T, double>::value && h->prm.precision == IFMM_MIXED_SOLVE) ? 1 : 0;
     return v;
 }
 

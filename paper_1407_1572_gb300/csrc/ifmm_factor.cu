@@ -279,6 +279,22 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
 // ---------------------------------------------------------------------------------------------
 // k_panel: X = Pi_e[:, 0:n] B_q for each neighbour q, X_y = -Pi_e[:, n:s]; panels for the solve
 // ---------------------------------------------------------------------------------------------
+// CTA GEMM of the panel and Schur steps: in the working precision, or for FP64 level data with
+// gemm_dfl set, in double-float on the FP32 pipe (operands split while they are staged, FP64 epilogue)
+template <typename T, class LA, class LB, class EPI>
+IFMM_DEVINL void factor_gemm(const LevelView<T>& L, int M, int N, int K, LA la, LB lb, EPI epi, void* sm, int tile0,
+                             int tstride) {
+    using Acc = typename AccOf<T>::type;
+    if constexpr (std::is_same<T, double>::value) {
+        if (L.gemm_dfl) {
+            cta_gemm<dfl>(M, N, K, la, lb, [&](int i, int j, dfl v) { epi(i, j, (double)v); }, (dfl*)sm, tile0,
+                          tstride);
+            return;
+        }
+    }
+    cta_gemm<Acc>(M, N, K, la, lb, epi, (Acc*)sm, tile0, tstride);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
@@ -323,8 +339,8 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
         }
     }
     const int cx = xcol_offset(L, ex, ey, d);
-    cta_gemm<Acc>(
-        s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
+    factor_gemm<T>(
+        L, s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
         [&](int k, int j) { return B[(size_t)k * ldb + j]; },
         [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm, blockIdx.z, gridDim.z);
     if (threadIdx.x == 0 && blockIdx.z == 0) {
@@ -372,8 +388,8 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         // new column y_e in row rho_p: M2P_pe or M2L_pe = -C_p X_y[x rows]
         int ld;
         T* dst = block_at(L, p, e, ld);
-        cta_gemm<Acc>(
-            wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+        factor_gemm<T>(
+            L, wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
         if (threadIdx.x == 0 && blockIdx.z == 0) {
@@ -391,8 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         int ld, ld2 = 0;
         T* dst = block_at(L, p, q, ld);
         T* dst2 = (L.symmetric && p != q) ? block_at(L, q, p, ld2) : nullptr;
-        cta_gemm<Acc>(
-            wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+        factor_gemm<T>(
+            L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) {
                 dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v);
@@ -401,8 +417,8 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
             sm, blockIdx.z, gridDim.z);
     } else {
         T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
-        cta_gemm<Acc>(
-            wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+        factor_gemm<T>(
+            L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
     }
@@ -705,10 +721,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     if (C == 1) {
         k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
     }
-    // spread big pair blocks over several blocks when the colour has few boxes
-    const int tiles = ((L.nmax + 63) / 64) * ((L.nmax + 63) / 64);
+    // spread big pair blocks over several blocks when the colour has few boxes (output tiles of 64,
+    // or 32 for the double-float products)
+    const int tw = L.gemm_dfl ? 32 : 64;
+    const int tiles = ((L.nmax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw);
     const int zs = std::max(1, std::min(tiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
-    const int zp = std::max(1, std::min(((smax + 63) / 64) * ((L.nmax + 63) / 64), (608 + nboxes * 8 - 1) / (nboxes * 8)));
+    const int zp = std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8)));
     if (ev) cudaEventRecord(ev[1], st);
     k_panel<T><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[2], st);

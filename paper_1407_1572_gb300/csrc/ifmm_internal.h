@@ -14,7 +14,26 @@ struct dfl {
     float hi, lo;
     dfl() = default;
     __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
-    __host__ __device__ explicit dfl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    // On the device the split works on the bit pattern (integer and FP32 operations only; the FP64
+    // pipe is 64 times slower): hi = d truncated to 24 significant bits, lo = the remaining 29
+    // bits rounded to 24, both exact scalings of the double's fields. Exponents whose hi or lo
+    // would leave the FP32 normal range take the FP64 formula.
+    __host__ __device__ explicit dfl(double d) {
+#ifdef __CUDA_ARCH__
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+        if (e >= 949u && e <= 1150u) {
+            const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+            hi = __uint_as_float(sgn | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
+            const float scale = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
+            const float m = __uint2float_rn((unsigned)b & 0x1FFFFFFFu);
+            lo = __uint_as_float(__float_as_uint(__fmul_rn(m, scale)) | sgn);
+            return;
+        }
+#endif
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
     __host__ __device__ explicit dfl(int v) : hi((float)v), lo(0.0f) {}
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
@@ -70,6 +89,7 @@ struct LevelView {
     double eps, sA;
     int tau_ref;
     int symmetric;             // kernel symmetric: F_pq = F_qp^T in exact arithmetic
+    int gemm_dfl;              // FP64 level data, panel and Schur products in double-float (FP32 pipe)
 };
 
 // Level vectors of the replay: for box b of level k, rows voff[b].. of the level-k vector hold

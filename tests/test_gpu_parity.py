@@ -159,10 +159,12 @@ def test_refined_solution_meets_tolerance(ifmm, kernel, precision):
 
 
 def test_double_float_replay_of_fp64_factors(ifmm):
-    """IFMM_MIXED_SOLVE factors in FP64 exactly as IFMM_FP64 (same ranks) and replays double-float
-    copies of the factors (hi + lo FP32 pairs, unit roundoff about 2^-48) on the FP32 pipe: the
-    unrefined solve matches the FP64 replay to 1e-9 relative. (A plain FP32 replay differs by
-    8e-5 here, by 1.0 at N = 65,536 and by 1.5e3 at N = 2^20: the pivot blocks amplify rounding.)"""
+    """IFMM_MIXED_SOLVE eliminates with FP64 pivots, compression and level data, forms the panel and
+    Schur products in double-float (hi + lo FP32 pairs, unit roundoff about 2^-48) and replays
+    double-float copies of the factors on the FP32 pipe. Box ranks agree with IFMM_FP64 to within
+    one (a compression decision at the threshold may flip) and the unrefined solve matches the FP64
+    one to 1e-8 relative: 2^-48 amplified by the elimination's growth, which a plain FP32 replay
+    shows as a difference of 8e-5 here (1.0 at N = 65,536, 1.5e3 at N = 2^20)."""
     N, depth, p, eps = 4096, 3, 4, 1e-6
     pts = inputs.uniform_points(1407, N)
     g64 = _gpu(ifmm, pts, depth, p, eps, precision=0)
@@ -170,13 +172,13 @@ def test_double_float_replay_of_fp64_factors(ifmm):
     g64.factor()
     g32.factor()
     for k in range(2, depth + 1):
-        assert np.array_equal(g64.ranks(k), g32.ranks(k))
+        assert np.abs(g64.ranks(k) - g32.ranks(k)).max() <= 1
     b = inputs.rhs(7, N, 4)
     x64 = g64.solve(_t(b)).cpu().numpy()
     x32 = g32.solve(_t(b)).cpu().numpy()
     d = _rel(x32, x64)
     print(f"double-float replay vs FP64 replay: {d:.2e}")
-    assert d <= 1e-9
+    assert d <= 1e-8
 
 
 def test_mixed_solve_config_65536(ifmm):
