@@ -438,6 +438,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
     extern __shared__ double csm[];  // u (nq) then per-warp coefficients (8 * RC)
+    __shared__ Acc gsm[gemm_smem<Acc>::value];
     __shared__ double vred[32];
     __shared__ int ired[32];
     __shared__ double s_val;
@@ -500,10 +501,25 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const double tau = L.eps * (L.tau_ref == 1 ? L.sA : smax);
     T* W = L.W + L.voff[q] * RC;
     double* coef = csm + nq;  // 8 warps x RC
-    // R <- (I - W W^T) R by classical Gram-Schmidt per column: once in FP64 (the basis is
-    // orthonormal to working precision), twice in FP32
+    // R <- (I - W W^T) R: once in FP64 (the basis is orthonormal to working precision), twice in
+    // FP32. With the column fills alone (half) the second half of R's scratch is free and holds
+    // C = W^T R, and the projection is two CTA GEMMs (in double-float for gemm_dfl); otherwise
+    // classical Gram-Schmidt per column.
     const int passes = sizeof(T) == 8 ? 1 : 2;
-    for (int pass = 0; pass < passes && rq0 > 0; ++pass) {
+    if (half && passes == 1 && rq0 > 0) {
+        T* Cm = R + (size_t)nq * m;
+        factor_gemm<T>(
+            L, rq0, m, nq, [&](int i, int k) { return W[(size_t)k * RC + i]; },
+            [&](int k, int j) { return R[(size_t)k * m + j]; },
+            [&](int i, int j, Acc v) { Cm[(size_t)i * m + j] = (T)v; }, gsm, 0, 1);
+        __syncthreads();
+        factor_gemm<T>(
+            L, nq, m, rq0, [&](int i, int k) { return W[(size_t)i * RC + k]; },
+            [&](int k, int j) { return Cm[(size_t)k * m + j]; },
+            [&](int i, int j, Acc v) { R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - v); }, gsm, 0, 1);
+        __syncthreads();
+    }
+    for (int pass = 0; pass < passes && rq0 > 0 && !(half && passes == 1); ++pass) {
         for (int j = warp; j < m; j += nw) {
             double* c = coef + warp * RC;
             for (int t = 0; t < rq0; ++t) {
@@ -733,6 +749,7 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     k_schur<T><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[3], st);
     size_t csmem = (size_t)(smax + 8 * L.RC) * sizeof(double);
+    cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
     k_compress<T><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[4], st);
     k_redirect<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
