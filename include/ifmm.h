@@ -45,7 +45,11 @@ typedef enum {
 
 typedef enum {
     IFMM_K_INV_R = 0,            /* K(x, y) = 1 / |x - y|                                      */
-    IFMM_K_EXP = 1               /* K(x, y) = exp(-|x - y| / kparam[0])                        */
+    IFMM_K_EXP = 1,              /* K(x, y) = exp(-|x - y| / kparam[0])                        */
+    IFMM_K_DEXP_DELL = 2         /* K(x, y) = d/dl exp(-r / l) = (r / l^2) exp(-r / l), l = kparam[0],
+                                    r = |x - y|: with diag = 0 its FMM matvec is dA~/dl of the
+                                    IFMM_K_EXP matrix (the Chebyshev nodes and bases do not depend
+                                    on l), the parameter derivative an adjoint gradient needs    */
 } ifmm_kernel;
 
 typedef enum {

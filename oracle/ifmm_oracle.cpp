@@ -363,6 +363,8 @@ double kernel_value(const oracle_params& p, double ax, double ay, double bx, dou
     switch (p.kernel) {
         case ORACLE_K_INV_R: return 1.0 / r;
         case ORACLE_K_EXP: return std::exp(-r / p.kparam[0]);
+        // derivative of exp(-r / l) with respect to the length scale l
+        case ORACLE_K_DEXP_DELL: return r / (p.kparam[0] * p.kparam[0]) * std::exp(-r / p.kparam[0]);
         case ORACLE_K_POLY: return (1.0 + ax * bx) * (1.0 + ay * by);
         default: return 0.0;
     }
@@ -1250,7 +1252,7 @@ extern "C" {
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm) {
     if (!pts || !prm || N <= 0 || prm->depth < 2 || prm->depth > 12 || prm->cheb_p < 1 || prm->cheb_p > 12) return nullptr;
     if (!(prm->box[2] > 0.0) || prm->eps < 0.0) return nullptr;
-    if (prm->kernel == ORACLE_K_EXP && !(prm->kparam[0] > 0.0)) return nullptr;
+    if ((prm->kernel == ORACLE_K_EXP || prm->kernel == ORACLE_K_DEXP_DELL) && !(prm->kparam[0] > 0.0)) return nullptr;
     auto h = std::make_unique<Handle>();
     h->prm = *prm;
     h->N = N;

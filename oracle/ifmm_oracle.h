@@ -18,7 +18,7 @@
 extern "C" {
 #endif
 
-enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_POLY = 3 };
+enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_DEXP_DELL = 2, ORACLE_K_POLY = 3 };
 
 typedef struct {
     int depth;          /* leaf level kappa >= 2 of the uniform quadtree                      */

@@ -24,7 +24,7 @@ _LIB = os.path.join(_LIB_DIR, "libifmm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-K_INV_R, K_EXP, K_POLY = 0, 1, 3
+K_INV_R, K_EXP, K_DEXP_DELL, K_POLY = 0, 1, 2, 3
 
 
 def compile_oracle(force: bool = False) -> str:

@@ -364,7 +364,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.eps = h->prm.eps;
     v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
-    v.symmetric = 1;   // both kernels, 1/r and exp(-r/l), are symmetric
+    v.symmetric = 1;   // every kernel of the library (1/r, exp(-r/l), its l-derivative) is symmetric
     v.gemm_dfl = (std::is_same<T, double>::value && h->prm.precision == IFMM_MIXED_SOLVE) ? 1 : 0;
     return v;
 }
@@ -1099,8 +1099,8 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     if (out) *out = nullptr;
     if (!pts_host || !p || !out || N <= 0 || N >= (1ll << 31)) return IFMM_ERR_INVALID_ARG;
     if (p->dim != 2 || p->depth < 2 || p->depth > 10 || p->cheb_p < 1 || p->cheb_p > 8) return IFMM_ERR_INVALID_ARG;
-    if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP) return IFMM_ERR_INVALID_ARG;
-    if (kernel == IFMM_K_EXP && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
+    if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP && kernel != IFMM_K_DEXP_DELL) return IFMM_ERR_INVALID_ARG;
+    if ((kernel == IFMM_K_EXP || kernel == IFMM_K_DEXP_DELL) && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
     if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
     if (p->precision != IFMM_FP64 && p->precision != IFMM_MIXED && p->precision != IFMM_MIXED_SOLVE)
         return IFMM_ERR_INVALID_ARG;
@@ -1175,14 +1175,14 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
     return s;
 }
 
-// Transposed solve. Both kernels of the library are symmetric, K(x, y) = K(y, x), and the build
+// Transposed solve. Every kernel of the library is symmetric, K(x, y) = K(y, x), and the build
 // keeps A~ symmetric: P2P_ji = P2P_ij^T, M2L_ji = M2L_ij^T, L2P = P2M^T; the elimination compresses
 // the fill of every box with one basis for its row and its column (F_qp = F_pq^T), so the compressed
 // matrix that the factors invert is symmetric as well. A~^T x = b is therefore the system of
 // ifmm_solve, solved by the same replay of the factors.
 ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld) {
     if (!h) return IFMM_ERR_INVALID_ARG;
-    if (h->kernel != IFMM_K_INV_R && h->kernel != IFMM_K_EXP) {
+    if (h->kernel != IFMM_K_INV_R && h->kernel != IFMM_K_EXP && h->kernel != IFMM_K_DEXP_DELL) {
         h->err = "ifmm_solve_T: the transposed replay is only provided for symmetric kernels";
         return IFMM_ERR_INVALID_ARG;
     }

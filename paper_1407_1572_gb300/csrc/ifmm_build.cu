@@ -42,6 +42,7 @@ IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay,
     double dx = ax - bx, dy = ay - by;
     double r = sqrt(dx * dx + dy * dy);
     if (kernel == 0) return 1.0 / r;
+    if (kernel == 2) return r / (kparam0 * kparam0) * exp(-r / kparam0);  // d/dl of exp(-r / l)
     return exp(-r / kparam0);
 }
 

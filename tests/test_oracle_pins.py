@@ -52,6 +52,24 @@ def test_kernel_values_closed_form(oracle_mod):
     assert O.kernel_eval(prm, [0.0, 0.0], [0.3, 0.4]) == pytest.approx(math.exp(-5.0), rel=1e-14)
 
 
+def test_length_scale_derivative_kernel(oracle_mod):
+    """K_DEXP_DELL is d/dl exp(-r/l) = (r/l^2) exp(-r/l): closed form at r = 0.5, l = 0.1, and the
+    central difference of K_EXP in l at other points."""
+    O = oracle_mod
+    prm = O.make_params(3, 4, O.K_DEXP_DELL, kparam=(0.1, 0, 0, 0))
+    assert O.kernel_eval(prm, [0.0, 0.0], [0.3, 0.4]) == pytest.approx(0.5 / 0.01 * math.exp(-5.0), rel=1e-14)
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        a, b = rng.uniform(0, 1, 2), rng.uniform(0, 1, 2)
+        ell = rng.uniform(0.05, 0.3)
+        h = 1e-4 * ell   # central difference: truncation O((h/l)^2) ~ 1e-8 relative
+        kp = O.make_params(3, 4, O.K_EXP, kparam=(ell + h, 0, 0, 0))
+        km = O.make_params(3, 4, O.K_EXP, kparam=(ell - h, 0, 0, 0))
+        fd = (O.kernel_eval(kp, a, b) - O.kernel_eval(km, a, b)) / (2 * h)
+        d = O.kernel_eval(O.make_params(3, 4, O.K_DEXP_DELL, kparam=(ell, 0, 0, 0)), a, b)
+        assert d == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
 # ---- tree and lists (Section 4.2, Table "table_cluster") -------------------------------------
 
 def test_lists_brute_force(oracle_mod):
@@ -152,6 +170,23 @@ def test_nested_operators_equal_textbook_formula(oracle_mod, kernel):
     Ad = o.dense_tilde_direct()
     assert np.abs(At - Ad).max() < 1e-12 * np.abs(Ad).max()
     assert np.allclose(At, At.T, rtol=0, atol=1e-12 * np.abs(At).max())
+
+
+def test_fmm_of_length_derivative_is_derivative_of_fmm(oracle_mod):
+    """The Chebyshev nodes, the orthonormal bases and the tree do not depend on l, so the FMM matrix
+    of K_DEXP_DELL (zero diagonal) is d/dl of the FMM matrix of K_EXP (diagonal 1 + sigma^2): checked
+    against the central difference of the assembled A~(l)."""
+    O = oracle_mod
+    pts = inputs.uniform_points(31, 600)
+    ell, h, sig2 = 0.1, 1e-5, 1e-2
+    mk = lambda kernel, l, diag: O.Oracle(pts, O.make_params(3, 4, kernel, diag=diag, kparam=(l, 0, 0, 0)))
+    Ap = mk(O.K_EXP, ell + h, 1.0 + sig2).dense_tilde()
+    Am = mk(O.K_EXP, ell - h, 1.0 + sig2).dense_tilde()
+    D = mk(O.K_DEXP_DELL, ell, 0.0).dense_tilde()
+    fd = (Ap - Am) / (2 * h)
+    assert np.abs(D - fd).max() <= 1e-7 * np.abs(D).max()
+    assert np.allclose(D, D.T, rtol=0, atol=1e-12 * np.abs(D).max())
+    assert np.abs(np.diag(D)).max() == 0.0
 
 
 def test_interpolation_error_decreases_with_p(oracle_mod):
