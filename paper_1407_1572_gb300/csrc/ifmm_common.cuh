@@ -329,12 +329,19 @@ __device__ inline bool cta_gauss_jordan(double* A, int s, int lda, int* perm, do
         }
         for (int i = tid; i < s; i += nt) col[i] = A[(size_t)i * lda + k];
         __syncthreads();
-        // rows i != k: A[i][j] -= col[i] * A[k][j] (j != k); A[i][k] = -col[i] * d
-        for (int t = tid; t < s * s; t += nt) {
-            int i = t / s, j = t - i * s;
-            if (i == k) continue;
-            if (j == k) A[(size_t)i * lda + k] = -col[i] * d;
-            else A[(size_t)i * lda + j] -= col[i] * A[(size_t)k * lda + j];
+        // rows i != k: A[i][j] -= col[i] * A[k][j] (j != k); A[i][k] = -col[i] * d. Element
+        // t = i s + j walked in steps of nt = dr s + dc (no division per element).
+        {
+            const int dr = nt / s, dc = nt - dr * s;
+            for (int i = tid / s, j = tid - (tid / s) * s; i < s;) {
+                if (i != k) {
+                    if (j == k) A[(size_t)i * lda + k] = -col[i] * d;
+                    else A[(size_t)i * lda + j] -= col[i] * A[(size_t)k * lda + j];
+                }
+                i += dr;
+                j += dc;
+                if (j >= s) { j -= s; ++i; }
+            }
         }
         __syncthreads();
     }

@@ -185,8 +185,12 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
     double alpha = block_max(cmax, vred);
     if (!(alpha > 0.0)) alpha = 1.0;
     if (threadIdx.x == 0) s_alpha = alpha;
-    for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
-        const int tl = t / s, j = t - tl * s;
+    // element t = tl s + j of the local rows, walked in steps of the block size without a division
+    // per element: (tl, j) advances by (dr, dc) with blockDim = dr s + dc
+    const int sd = s > 0 ? s : 1;   // an empty box (s = 0) has no local rows
+    const int dr = (int)blockDim.x / sd, dc = (int)blockDim.x - dr * sd;
+    const int tl0 = (int)threadIdx.x / sd, j0 = (int)threadIdx.x - tl0 * sd;
+    for (int tl = tl0, j = j0; tl < rows_loc;) {
         const int i = c + tl * C;
         double v;
         if (i < n && j < n) v = (double)Pee[(size_t)i * ldp + j];
@@ -194,6 +198,9 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         else if (j < n) v = alpha * (double)We[(size_t)j * RC + (i - n)];
         else v = 0.0;
         slab[(size_t)tl * sstride + j] = v;
+        tl += dr;
+        j += dc;
+        if (j >= s) { j -= s; ++tl; }
     }
     for (int t = threadIdx.x; t < rows_loc; t += blockDim.x) used[t] = 0;
     __syncthreads();
@@ -247,27 +254,38 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) fcol[tl] = slab[(size_t)tl * sstride + k];
         __syncthreads();
         const double d = prow[k];
-        for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
-            const int tl = t / s, j = t - tl * s;
-            if (c == owner && tl == tp) continue;
-            const double f = fcol[tl];
-            if (j == k) slab[(size_t)tl * sstride + k] = -f * d;
-            else slab[(size_t)tl * sstride + j] -= f * prow[j];
+        for (int tl = tl0, j = j0; tl < rows_loc;) {
+            if (!(c == owner && tl == tp)) {
+                const double f = fcol[tl];
+                if (j == k) slab[(size_t)tl * sstride + k] = -f * d;
+                else slab[(size_t)tl * sstride + j] -= f * prow[j];
+            }
+            tl += dr;
+            j += dc;
+            if (j >= s) { j -= s; ++tl; }
         }
         __syncthreads();
     }
-    // write Pi = S A^{-1} S: A^{-1}[k][p_j] = R[p_k][j]; local row i = p_k for k = pinv(i)
+    // write Pi = S A^{-1} S: A^{-1}[k][p_j] = R[p_k][j]; local row i = p_k for k = pinv(i), found
+    // once per row (into `used`, free after the elimination)
     T* Pi = L.Pi + L.pioff[e];
     const int ld = L.pild[e];
     alpha = s_alpha;
-    for (int t = threadIdx.x; t < rows_loc * s; t += blockDim.x) {
-        const int tl = t / s, j = t - tl * s;
+    for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) {
         const int i = c + tl * C;
         int kk = 0;
         while (kk < s - 1 && perm[kk] != i) ++kk;
+        used[tl] = kk;
+    }
+    __syncthreads();
+    for (int tl = tl0, j = j0; tl < rows_loc;) {
+        const int kk = used[tl];
         const int col = perm[j];
         const double sc = (kk >= n ? alpha : 1.0) * (col >= n ? alpha : 1.0);
         Pi[(size_t)kk * ld + col] = (T)(sc * slab[(size_t)tl * sstride + j]);
+        tl += dr;
+        j += dc;
+        if (j >= s) { j -= s; ++tl; }
     }
     if (threadIdx.x == 0 && c == 0) {
         atomicAdd(&L.counters[2], 2.0 * s * (double)s * s);
@@ -678,10 +696,32 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
     }
 }
 
+// largest pivot size s = n + r over the boxes of a colour at the time of their elimination (the
+// ranks grow on the device), into *out
 template <typename T>
-void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smax,
+__global__ void k_colour_smax(LevelView<T> L, const int* boxes, int nboxes, int* out) {
+    __shared__ double vred[32];
+    double m = 0.0;
+    for (int b = threadIdx.x; b < nboxes; b += blockDim.x) m = fmax(m, (double)(L.n[boxes[b]] + L.r[boxes[b]]));
+    m = block_max(m, vred);
+    if (threadIdx.x == 0) *out = (int)m;
+}
+
+template <typename T>
+void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smax_bound,
                           cudaStream_t st, cudaEvent_t* ev) {
     if (nboxes <= 0) return;
+    // size the pivot launch by the colour's actual largest pivot (the level bound nmax + min(nmax,
+    // RC) is reached only when a basis fills up); status[2] is the scratch word
+    int smax = smax_bound;
+    {
+        k_colour_smax<T><<<1, 256, 0, st>>>(L, boxes, nboxes, L.status + 2);
+        count_launches(1);
+        int hs = 0;
+        if (cudaMemcpyAsync(&hs, L.status + 2, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess && hs > 0 && hs <= smax_bound)
+            smax = hs;
+    }
     size_t base = (size_t)smax * sizeof(double) + (size_t)((smax + 1) / 2) * sizeof(double);
     size_t full = base + (size_t)smax * smax * sizeof(double);
     int use_smem = full <= 200 * 1024 ? 1 : 0;
@@ -698,9 +738,11 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         const size_t rows = (size_t)(smax + cc - 1) / cc;
         return (glob ? 0 : rows * smax * sizeof(double)) + (smax + rows) * sizeof(double) + (smax + rows) * sizeof(int);
     };
-    if (smax >= 160) {
+    if (smax >= 96) {
+        // few boxes: spread each over several SMs; many boxes: keep a CTA within 72 KB so that
+        // three share an SM (a pivot is a chain of s dependent steps; resident CTAs hide it)
         while (C < 8 && nboxes * C < 2 * 152) C *= 2;
-        while (C < 8 && cl_bytes(C, 0) > 200 * 1024) C *= 2;
+        while (C < 8 && cl_bytes(C, 0) > 72 * 1024) C *= 2;
         if (cl_bytes(C, 0) > 200 * 1024) slab_global = 1;   // slab rows in the FP64 workspace (L2)
         if (slab_global && !L.pws) C = 1;
     }
@@ -748,7 +790,8 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     if (ev) cudaEventRecord(ev[2], st);
     k_schur<T><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[3], st);
-    size_t csmem = (size_t)(smax + 8 * L.RC) * sizeof(double);
+    // u holds a neighbour's n_q rows: sized by the level bound, not by this colour's pivots
+    size_t csmem = (size_t)(smax_bound + 8 * L.RC) * sizeof(double);
     cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
     k_compress<T><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[4], st);
