@@ -297,26 +297,27 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
 // ---------------------------------------------------------------------------------------------
 // k_panel: X = Pi_e[:, 0:n] B_q for each neighbour q, X_y = -Pi_e[:, n:s]; panels for the solve
 // ---------------------------------------------------------------------------------------------
-// CTA GEMM of the panel and Schur steps: in the working precision, or for FP64 level data with
-// gemm_dfl set, in double-float on the FP32 pipe (operands split while they are staged, FP64 epilogue)
-template <typename T, class LA, class LB, class EPI>
+// CTA GEMM of the panel, Schur and compression steps: in the working precision (DF = false), or,
+// for FP64 level data with gemm_dfl set (DF = true), in double-float on the FP32 pipe (operands
+// split while they are staged, FP64 epilogue). DF is a template parameter so that each kernel
+// instantiation carries one GEMM only (registers, hence occupancy).
+template <typename T, bool DF, class LA, class LB, class EPI>
 IFMM_DEVINL void factor_gemm(const LevelView<T>& L, int M, int N, int K, LA la, LB lb, EPI epi, void* sm, int tile0,
                              int tstride) {
     using Acc = typename AccOf<T>::type;
-    if constexpr (std::is_same<T, double>::value) {
-        if (L.gemm_dfl) {
-            cta_gemm<dfl>(M, N, K, la, lb, [&](int i, int j, dfl v) { epi(i, j, (double)v); }, (dfl*)sm, tile0,
-                          tstride);
-            return;
-        }
+    (void)L;
+    if constexpr (DF && std::is_same<T, double>::value) {
+        cta_gemm<dfl>(M, N, K, la, lb, [&](int i, int j, dfl v) { epi(i, j, (double)v); }, (dfl*)sm, tile0, tstride);
+    } else {
+        cta_gemm<Acc>(M, N, K, la, lb, epi, (Acc*)sm, tile0, tstride);
     }
-    cta_gemm<Acc>(M, N, K, la, lb, epi, (Acc*)sm, tile0, tstride);
 }
 
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
+    __shared__ GS sm[gemm_smem<GS>::value];
     const int e = boxes[blockIdx.x];
     const int d = blockIdx.y;
     const int ex = e % L.side, ey = e / L.side;
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
         }
     }
     const int cx = xcol_offset(L, ex, ey, d);
-    factor_gemm<T>(
+    factor_gemm<T, DF>(
         L, s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
         [&](int k, int j) { return B[(size_t)k * ldb + j]; },
         [&](int i, int j, Acc v) { X[(size_t)i * ldx + cx + j] = (T)v; }, sm, blockIdx.z, gridDim.z);
@@ -370,10 +371,11 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
 // ---------------------------------------------------------------------------------------------
 // k_schur: one (p, q) pair of neighbours of e per block (p, q in N_e; dp == 4 is row M2L_e)
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
+    __shared__ GS sm[gemm_smem<GS>::value];
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     const int ex = e % L.side, ey = e / L.side;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         // new column y_e in row rho_p: M2P_pe or M2L_pe = -C_p X_y[x rows]
         int ld;
         T* dst = block_at(L, p, e, ld);
-        factor_gemm<T>(
+        factor_gemm<T, DF>(
             L, wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         int ld, ld2 = 0;
         T* dst = block_at(L, p, q, ld);
         T* dst2 = (L.symmetric && p != q) ? block_at(L, q, p, ld2) : nullptr;
-        factor_gemm<T>(
+        factor_gemm<T, DF>(
             L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) {
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
             sm, blockIdx.z, gridDim.z);
     } else {
         T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
-        factor_gemm<T>(
+        factor_gemm<T, DF>(
             L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
             [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
@@ -452,11 +454,12 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
 // ---------------------------------------------------------------------------------------------
 // k_compress: extend W_q for the well-separated fill of uneliminated neighbour q of e
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
     extern __shared__ double csm[];  // u (nq) then per-warp coefficients (8 * RC)
-    __shared__ Acc gsm[gemm_smem<Acc>::value];
+    using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
+    __shared__ GS gsm[gemm_smem<GS>::value];
     __shared__ double vred[32];
     __shared__ int ired[32];
     __shared__ double s_val;
@@ -526,12 +529,12 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const int passes = sizeof(T) == 8 ? 1 : 2;
     if (half && passes == 1 && rq0 > 0) {
         T* Cm = R + (size_t)nq * m;
-        factor_gemm<T>(
+        factor_gemm<T, DF>(
             L, rq0, m, nq, [&](int i, int k) { return W[(size_t)k * RC + i]; },
             [&](int k, int j) { return R[(size_t)k * m + j]; },
             [&](int i, int j, Acc v) { Cm[(size_t)i * m + j] = (T)v; }, gsm, 0, 1);
         __syncthreads();
-        factor_gemm<T>(
+        factor_gemm<T, DF>(
             L, nq, m, rq0, [&](int i, int k) { return W[(size_t)i * RC + k]; },
             [&](int k, int j) { return Cm[(size_t)k * m + j]; },
             [&](int i, int j, Acc v) { R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - v); }, gsm, 0, 1);
@@ -729,7 +732,8 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     static bool attr_set[2] = {false, false};
     if (!attr_set[sizeof(T) == 8]) {
         cudaFuncSetAttribute(k_pivot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-        cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_set[sizeof(T) == 8] = true;
     }
     // large pivot blocks and few boxes: one cluster of C blocks per box
@@ -786,14 +790,22 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     const int zs = std::max(1, std::min(tiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
     const int zp = std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8)));
     if (ev) cudaEventRecord(ev[1], st);
-    k_panel<T><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
+    const bool df = std::is_same<T, double>::value && L.gemm_dfl;
+    if (df) k_panel<T, true><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
+    else k_panel<T, false><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[2], st);
-    k_schur<T><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+    if (df) k_schur<T, true><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+    else k_schur<T, false><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[3], st);
     // u holds a neighbour's n_q rows: sized by the level bound, not by this colour's pivots
     size_t csmem = (size_t)(smax_bound + 8 * L.RC) * sizeof(double);
-    cudaFuncSetAttribute(k_compress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
-    k_compress<T><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+    if (df) {
+        cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        k_compress<T, true><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+    } else {
+        cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        k_compress<T, false><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+    }
     if (ev) cudaEventRecord(ev[4], st);
     k_redirect<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[5], st);
