@@ -636,10 +636,11 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
 // ---------------------------------------------------------------------------------------------
 // k_redirect: M2L_pq += (W_p^T) F (W_q) for a well-separated pair with fill
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
+    __shared__ GS sm[gemm_smem<GS>::value];
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     if (dp == 4 || dq == 4 || dp == dq) return;
@@ -667,23 +668,23 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
     const T* T1 = F;
     int ld1 = wq;
     if (!Eq) {
-        cta_gemm<Acc>(
-            wp, rq, wq, [&](int i, int k) { return F[(size_t)i * wq + k]; },
+        factor_gemm<T, DF>(
+            L, wp, rq, wq, [&](int i, int k) { return F[(size_t)i * wq + k]; },
             [&](int k, int j) { return Wq[(size_t)k * RC + j]; },
-            [&](int i, int j, Acc v) { F2[(size_t)i * rq + j] = (T)v; }, sm);
+            [&](int i, int j, Acc v) { F2[(size_t)i * rq + j] = (T)v; }, sm, 0, 1);
         __syncthreads();
         T1 = F2;
         ld1 = rq;
     }
     if (!Ep) {
-        cta_gemm<Acc>(
-            rp, rq, wp, [&](int i, int k) { return Wp[(size_t)k * RC + i]; },
+        factor_gemm<T, DF>(
+            L, rp, rq, wp, [&](int i, int k) { return Wp[(size_t)k * RC + i]; },
             [&](int k, int j) { return T1[(size_t)k * ld1 + j]; },
             [&](int i, int j, Acc v) {
                 M[(size_t)i * ld + j] = (T)((Acc)M[(size_t)i * ld + j] + v);
                 if (M2) M2[(size_t)j * ld2 + i] = (T)((Acc)M2[(size_t)j * ld2 + i] + v);
             },
-            sm);
+            sm, 0, 1);
     } else {
         for (int t = threadIdx.x; t < rp * rq; t += blockDim.x) {
             int i = t / rq, j = t - i * rq;
@@ -807,7 +808,8 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         k_compress<T, false><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    k_redirect<T><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    if (df) k_redirect<T, true><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    else k_redirect<T, false><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[5], st);
     count_launches(5);
 }
@@ -1055,10 +1057,11 @@ template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st) {
     if (nboxes <= 0) return;
-    const int tr = (nrhs + 63) / 64;
+    const int tw = std::is_same<T, dfl>::value ? 32 : 64;   // output tile of the CTA GEMM
+    const int tr = (nrhs + tw - 1) / tw;
     const int smax = L.nmax + std::min(L.nmax, L.RC);
-    const int z1 = std::max(1, std::min(((smax + 63) / 64) * tr, (608 + nboxes - 1) / nboxes));
-    const int z2 = std::max(1, std::min(((L.nmax + 63) / 64) * tr, (608 + nboxes * 8 - 1) / (nboxes * 8)));
+    const int z1 = std::max(1, std::min(((smax + tw - 1) / tw) * tr, (608 + nboxes - 1) / nboxes));
+    const int z2 = std::max(1, std::min(((L.nmax + tw - 1) / tw) * tr, (608 + nboxes * 8 - 1) / (nboxes * 8)));
     k_fwd_piv<T><<<dim3(nboxes, 1, z1), kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
     k_fwd_upd<T><<<dim3(nboxes, 9, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
     count_launches(2);
@@ -1144,7 +1147,8 @@ template <typename T>
 void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                             const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st) {
     if (nboxes <= 0) return;
-    const int z = std::max(1, std::min(((L.nmax + 63) / 64) * ((nrhs + 63) / 64), (608 + nboxes - 1) / nboxes));
+    const int tw = std::is_same<T, dfl>::value ? 32 : 64;   // output tile of the CTA GEMM
+    const int z = std::max(1, std::min(((L.nmax + tw - 1) / tw) * ((nrhs + tw - 1) / tw), (608 + nboxes - 1) / nboxes));
     k_bwd_w<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs);
     k_bwd_x<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, yoff, x_k, x_km1, wtmp, nrhs);
     count_launches(2);
