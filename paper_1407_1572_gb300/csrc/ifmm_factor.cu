@@ -561,35 +561,69 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     }
     const int limit = min(nq, RC);
     double* u = csm;
+    double* nrm2 = coef + 8 * RC;   // squared column norms of R, downdated after each direction
+    // g threads per column (a power of two dividing 32; more when the columns are few), ngr
+    // groups; every warp runs the same number of column rounds so the group shuffles converge
+    int g = 1;
+    while (g < 8 && g * 2 * m <= (int)blockDim.x) g *= 2;
+    const int ngr = (int)blockDim.x / g, gid = (int)threadIdx.x / g, gl = (int)threadIdx.x % g;
+    const int rounds = (m + ngr - 1) / ngr;
+    auto group_sum = [&](Acc v) {
+        for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    auto all_norms = [&]() {
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int j = gid + rd * ngr;
+            Acc sq = 0;
+            if (j < m)
+                for (int i = gl; i < nq; i += g) { const Acc v = (Acc)R[(size_t)i * m + j]; sq += v * v; }
+            sq = group_sum(sq);
+            if (j < m && gl == 0) nrm2[j] = (double)sq;
+        }
+        __syncthreads();
+    };
+    all_norms();
+    bool fresh = true;   // nrm2 exact: recomputed since the last downdate
     int add = 0;
     for (;;) {
+        // largest remaining column norm (estimate), ties to the lowest column
         double best = -1.0;
         int bi = -1;
-        for (int j = warp; j < m; j += nw) {
-            Acc s = 0;
-            for (int i = lane; i < nq; i += 32) { Acc v = (Acc)R[(size_t)i * m + j]; s += v * v; }
-            s = warp_sum(s);
-            double v = sqrt((double)s);
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const double v = nrm2[j];
             if (bi < 0 || v > best) { best = v; bi = j; }
         }
-        if (lane != 0) bi = -1;
-        double bv;
-        int jb = block_argmax(best, bi, vred, ired, &bv);
-        if (!(bv > tau) || jb < 0) break;
+        double est2;
+        const int jb = block_argmax(best, bi, vred, ired, &est2);
+        if (jb < 0) break;
+        double ex2 = 0.0;
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) { const double v = (double)R[(size_t)i * m + jb]; ex2 += v * v; }
+        ex2 = block_sum(ex2, vred);
+        // a downdated estimate that is off, or a stop decided on estimates: recompute exactly
+        // (the loop ends only on exact norms, as the column-pivoted Gram-Schmidt of reading R2)
+        if (!fresh && (fabs(ex2 - est2) > 0.02 * fmax(ex2, est2) || !(sqrt(ex2) > tau))) {
+            all_norms();
+            fresh = true;
+            continue;
+        }
+        const double bv = sqrt(ex2);
+        if (!(bv > tau)) break;
         if (rq0 + add >= limit) {
             if (limit < nq && threadIdx.x == 0) atomicOr(L.status, DEV_ERR_OVERFLOW);
             break;
         }
         const int rc = rq0 + add;
-        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = (double)R[(size_t)i * m + jb] / bv;
+        const double ib = 1.0 / bv;
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = (double)R[(size_t)i * m + jb] * ib;
         __syncthreads();
-        // re-orthogonalise u against the current basis, twice
+        // re-orthogonalise u against the current basis, twice (one thread per basis vector for the
+        // coefficients, one per row for the update)
         for (int pass = 0; pass < 2; ++pass) {
-            for (int t = warp; t < rc; t += nw) {
-                double s = 0.0;
-                for (int i = lane; i < nq; i += 32) s += (double)W[(size_t)i * RC + t] * u[i];
-                s = warp_sum(s);
-                if (lane == 0) coef[t] = s;
+            for (int t = threadIdx.x; t < rc; t += blockDim.x) {
+                double sc = 0.0;
+                for (int i = 0; i < nq; ++i) sc += (double)W[(size_t)i * RC + t] * u[i];
+                coef[t] = sc;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < nq; i += blockDim.x) {
@@ -606,21 +640,30 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
         if (!(nu >= 0.5)) {
             // numerically inside the current span: drop this column
             for (int i = threadIdx.x; i < nq; i += blockDim.x) R[(size_t)i * m + jb] = (T)0;
+            if (threadIdx.x == 0) nrm2[jb] = 0.0;
             __syncthreads();
             continue;
         }
+        const double inu = 1.0 / nu;
         for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-            u[i] /= nu;
+            u[i] *= inu;
             W[(size_t)i * RC + rc] = (T)u[i];
         }
         __syncthreads();
-        for (int j = warp; j < m; j += nw) {
-            Acc s = 0;
-            for (int i = lane; i < nq; i += 32) s += (Acc)u[i] * (Acc)R[(size_t)i * m + j];
-            s = warp_sum(s);
-            for (int i = lane; i < nq; i += 32) R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - s * (Acc)u[i]);
+        // remove u from every column and downdate its norm
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int j = gid + rd * ngr;
+            Acc sp = 0;
+            if (j < m)
+                for (int i = gl; i < nq; i += g) sp += (Acc)u[i] * (Acc)R[(size_t)i * m + j];
+            sp = group_sum(sp);
+            if (j < m) {
+                for (int i = gl; i < nq; i += g) R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - sp * (Acc)u[i]);
+                if (gl == 0) nrm2[j] = fmax(0.0, nrm2[j] - (double)sp * (double)sp);
+            }
         }
         __syncthreads();
+        fresh = false;
         ++add;
     }
     if (threadIdx.x == 0) {
@@ -798,8 +841,9 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     if (df) k_schur<T, true><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     else k_schur<T, false><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[3], st);
-    // u holds a neighbour's n_q rows: sized by the level bound, not by this colour's pivots
-    size_t csmem = (size_t)(smax_bound + 8 * L.RC) * sizeof(double);
+    // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
+    // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax)
+    size_t csmem = (size_t)(smax_bound + 8 * L.RC + 10 * L.nmax) * sizeof(double);
     if (df) {
         cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
         k_compress<T, true><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
