@@ -774,6 +774,13 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
     void* pv = nullptr;
     CKS(workspace(h, slot++, sizeof(T) * (size_t)std::max<int64_t>(maxv * nrhs, 1), &pv));
     T* vxs = (T*)pv;
+    // split-K scratch of the back substitution at the upper levels (partials and tile counters)
+    const int64_t part_cap = (int64_t)4 << 20;
+    const int cnt_cap = 4096;
+    void *pp = nullptr, *pc = nullptr;
+    CKS(workspace(h, 26, sizeof(T) * (size_t)part_cap, &pp));
+    CKS(workspace(h, 27, sizeof(int) * (size_t)cnt_cap, &pc));
+    CK(cudaMemsetAsync(pc, 0, sizeof(int) * (size_t)cnt_cap, h->st));
     for (int k = kap; k >= 2; --k) {
         FLevel& L = h->lv[k];
         LevelView<T> v = solve_view<T>(h, L);
@@ -789,7 +796,7 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
         for (int c = 8; c >= 0; --c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             launch_backward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vx[k], vx[k - 1], vxs,
-                                      nrhs, h->st);
+                                      nrhs, (T*)pp, part_cap, (int*)pc, cnt_cap, h->st);
         }
     }
     CK(cudaGetLastError());

@@ -1113,19 +1113,35 @@ void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, 
 
 // back substitution, first half: w = rhs_e - sum_q B_q u_q as one GEMM over the concatenated
 // panels, u_q = x_q (q eliminated after e) or y_q (before)
+// L2-coherent load (the partial sums of split-K are written by other CTAs of the same launch)
+IFMM_DEVINL double ldcg_v(const double* p) { return __ldcg(p); }
+IFMM_DEVINL float ldcg_v(const float* p) { return __ldcg(p); }
+IFMM_DEVINL dfl ldcg_v(const dfl* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return dfl(v.x, v.y);
+}
+
+// back substitution, first half: w = rhs_e - sum_q B_q u_q as one GEMM over the concatenated
+// panels, u_q = x_q (q eliminated after e) or y_q (before). blockIdx.z = tile group tg (of zt) +
+// zt * K-split kz (of ks). With ks > 1 each CTA writes the partial product over its slice of K to
+// `part`; the last CTA of a tile group (atomic counter) adds the partials in split order, so the
+// result does not depend on the CTAs' timing, and resets the counter.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
-                                                    const T* rhs_k, const T* x_k, const T* x_km1, T* wtmp, int nrhs) {
+                                                    const T* rhs_k, const T* x_k, const T* x_km1, T* wtmp, int nrhs,
+                                                    int zt, int ks, T* part, int* cnt, int64_t pstride) {
     using Acc = typename AccOf<T>::type;
     __shared__ Acc sm[gemm_smem<Acc>::value];
     __shared__ const T* sB[8];
     __shared__ const T* sU[8];
     __shared__ int sOff[9], sW[8];
+    __shared__ int s_last;
     const int e = boxes[blockIdx.x];
     const int ex = e % L.side, ey = e / L.side;
     const int n = L.n[e];
+    const int tg = blockIdx.z % zt, kz = blockIdx.z / zt;
     if (threadIdx.x == 0) {
-        int cnt = 0, off = 0;
+        int cnt_ = 0, off = 0;
         for (int d = 0; d < 9; ++d) {
             if (d == 4) continue;
             const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
@@ -1133,14 +1149,14 @@ __global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* b
             const int q = qx + L.side * qy;
             const bool Eq = colour_of(qx, qy) < colour;
             const int wq = Eq ? L.r[q] : L.n[q];
-            sB[cnt] = L.Bp + L.bpoff[(int64_t)e * 9 + d];
-            sU[cnt] = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
-            sW[cnt] = wq;
-            sOff[cnt] = off;
+            sB[cnt_] = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+            sU[cnt_] = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
+            sW[cnt_] = wq;
+            sOff[cnt_] = off;
             off += wq;
-            ++cnt;
+            ++cnt_;
         }
-        for (int c = cnt; c < 9; ++c) sOff[c] = off;
+        for (int c = cnt_; c < 9; ++c) sOff[c] = off;
     }
     __syncthreads();
     const int K = sOff[8];
@@ -1149,23 +1165,52 @@ __global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* b
         while (c < 7 && k >= sOff[c + 1]) ++c;
         return c;
     };
+    auto la = [&](int i, int k) {
+        const int c = seg(k);
+        return sB[c][(size_t)i * sW[c] + (k - sOff[c])];
+    };
+    auto lb = [&](int k, int j) {
+        const int c = seg(k);
+        return sU[c][(size_t)(k - sOff[c]) * nrhs + j];
+    };
     T* w = wtmp + L.voff[e] * nrhs;
     const T* rhs = rhs_k + L.voff[e] * nrhs;
-    cta_gemm<Acc>(
-        n, nrhs, K,
-        [&](int i, int k) {
-            int c = seg(k);
-            return sB[c][(size_t)i * sW[c] + (k - sOff[c])];
-        },
-        [&](int k, int j) {
-            int c = seg(k);
-            return sU[c][(size_t)(k - sOff[c]) * nrhs + j];
-        },
-        [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - a); }, sm,
-        blockIdx.z, gridDim.z);
-    if (K == 0) {
-        for (int t = threadIdx.x + blockIdx.z * blockDim.x; t < n * nrhs; t += blockDim.x * gridDim.z) w[t] = rhs[t];
+    if (ks == 1) {
+        cta_gemm<Acc>(
+            n, nrhs, K, la, lb,
+            [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - a); }, sm, tg,
+            zt);
+        if (K == 0) {
+            for (int t = threadIdx.x + tg * blockDim.x; t < n * nrhs; t += blockDim.x * zt) w[t] = rhs[t];
+        }
+        return;
     }
+    // this split's slice of K (a multiple of 32 long; possibly empty)
+    const int chunk = (((K + ks - 1) / ks) + 31) & ~31;
+    const int k_lo = min(K, kz * chunk), k_hi = min(K, k_lo + chunk);
+    T* P = part + ((int64_t)kz * gridDim.x + blockIdx.x) * pstride;
+    cta_gemm<Acc>(
+        n, nrhs, k_hi - k_lo, [&](int i, int k) { return la(i, k_lo + k); },
+        [&](int k, int j) { return lb(k_lo + k, j); }, [&](int i, int j, Acc a) { P[(size_t)i * nrhs + j] = (T)a; },
+        sm, tg, zt);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cnt[blockIdx.x * zt + tg], 1) == ks - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // outputs of this tile group (the CTA GEMM's tiles: 32 x 32 in double-float, else 64 x 64)
+    constexpr int TW = std::is_same<Acc, dfl>::value ? 32 : 64;
+    const int tn = (nrhs + TW - 1) / TW;
+    for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
+        const int i = t / nrhs, j = t - i * nrhs;
+        if (((i / TW) * tn + j / TW) % zt != tg) continue;
+        Acc acc = (Acc)0;
+        for (int z = 0; z < ks; ++z)
+            acc = acc + (Acc)ldcg_v(part + ((int64_t)z * gridDim.x + blockIdx.x) * pstride + (size_t)i * nrhs + j);
+        w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - acc);
+    }
+    if (threadIdx.x == 0) cnt[blockIdx.x * zt + tg] = 0;
 }
 
 // back substitution, second half: [x_e; z_e] = Pi [w; y_e]; only x_e is kept
@@ -1189,11 +1234,21 @@ __global__ void __launch_bounds__(kThreads) k_bwd_x(LevelView<T> L, const int* b
 
 template <typename T>
 void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
-                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st) {
+                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, T* part, int64_t part_cap,
+                            int* cnt, int cnt_cap, cudaStream_t st) {
     if (nboxes <= 0) return;
     const int tw = std::is_same<T, dfl>::value ? 32 : 64;   // output tile of the CTA GEMM
     const int z = std::max(1, std::min(((L.nmax + tw - 1) / tw) * ((nrhs + tw - 1) / tw), (608 + nboxes - 1) / nboxes));
-    k_bwd_w<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs);
+    // few CTAs (upper levels): split K = sum of the neighbours' widths (<= 8 nmax) over more CTAs
+    int ks = 1;
+    const int64_t pstride = (int64_t)std::max(L.nmax, 1) * nrhs;
+    if (part && cnt && nboxes * z < 304 && nboxes * z <= cnt_cap) {
+        ks = std::min(16, (304 + nboxes * z - 1) / (nboxes * z));
+        ks = std::min(ks, std::max(1, 8 * L.nmax / 64));
+        while (ks > 1 && (int64_t)ks * nboxes * pstride > part_cap) --ks;
+    }
+    k_bwd_w<T><<<dim3(nboxes, 1, z * ks), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs, z,
+                                                              ks, part, cnt, pstride);
     k_bwd_x<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, yoff, x_k, x_km1, wtmp, nrhs);
     count_launches(2);
 }
@@ -1238,7 +1293,8 @@ void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, d
     template void launch_forward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*, T*, T*,   \
                                            T*, int, cudaStream_t);                                              \
     template void launch_backward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*,          \
-                                            const T*, T*, const T*, T*, int, cudaStream_t);                     \
+                                            const T*, T*, const T*, T*, int, T*, int64_t, int*, int,            \
+                                            cudaStream_t);                                                      \
     template void launch_init_level<T>(const LevelView<T>&, int, const double*, const int64_t*, const double*, \
                                        const int64_t*, int, const int*, const double*, const int*, const int*, \
                                        const LevelView<T>*, cudaStream_t);                                      \
@@ -1255,7 +1311,7 @@ IFMM_INSTANTIATE(float)
 template void launch_forward_colour<dfl>(const LevelView<dfl>&, const int*, int, int, const int64_t*, dfl*, dfl*,
                                          dfl*, int, cudaStream_t);
 template void launch_backward_colour<dfl>(const LevelView<dfl>&, const int*, int, int, const int64_t*, const dfl*,
-                                          dfl*, const dfl*, dfl*, int, cudaStream_t);
+                                          dfl*, const dfl*, dfl*, int, dfl*, int64_t, int*, int, cudaStream_t);
 template void launch_root_apply<dfl>(const double*, int, const dfl*, dfl*, int, cudaStream_t);
 template void launch_permute_in<dfl>(const double*, int64_t, int64_t, int, const int64_t*, dfl*, cudaStream_t);
 template void launch_permute_out<dfl>(const dfl*, int64_t, int, const int64_t*, double*, int64_t, cudaStream_t);

@@ -108,9 +108,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
 template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st);
+// part (part_cap elements) and cnt (cnt_cap ints, zero on entry and on return): split-K scratch
+// for colours with few boxes; NULL disables the split
 template <typename T>
 void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
-                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, cudaStream_t st);
+                            const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, T* part, int64_t part_cap,
+                            int* cnt, int cnt_cap, cudaStream_t st);
 template <typename T>
 void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, const int64_t* p2p0_off,
                        const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff5,
