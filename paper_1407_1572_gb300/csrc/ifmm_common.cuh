@@ -133,8 +133,10 @@ IFMM_DEVINL dfl& operator+=(dfl& a, dfl b) {
 }
 
 // CTA GEMM in double-float: output tiles of 32 x 32, each of the 256 threads owns 2 x 2 outputs
-// (rows ty, ty + 16, columns tx, tx + 16), k-steps of 32 staged in padded shared tiles. About 11
-// FP32 operations per multiply-add and 4 shared loads per 4 multiply-adds: FP32-pipe bound.
+// (rows ty, ty + 16, columns tx, tx + 16), k-steps of 32 staged in padded shared tiles; the next
+// k-step's operands (4 of A and 4 of B per thread) are loaded into registers while the current one
+// is multiplied. About 11 FP32 operations per multiply-add and 4 shared loads per 4 multiply-adds:
+// FP32-pipe bound.
 template <class LA, class LB, class EPI>
 __device__ void cta_gemm_dfl(int M, int N, int K, LA la, LB lb, EPI epi, dfl* smem, int tile0, int tstride) {
     constexpr int TM = 32, TN = 32, KC = 32, LDA = TM + 1, LDB = TN + 1;
@@ -143,6 +145,8 @@ __device__ void cta_gemm_dfl(int M, int N, int K, LA la, LB lb, EPI epi, dfl* sm
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int tn = (N + TN - 1) / TN, tm = (M + TM - 1) / TM;
+    // staging: element u of this thread is tid + 256 u (u < 4) of the 32 x 32 chunk; A as (i, k) =
+    // (t / KC, t % KC), B as (k, j) = (t / TN, t % TN)
     for (int tile = tile0; tile < tm * tn; tile += tstride) {
         const int m0 = (tile / tn) * TM, n0 = (tile % tn) * TN;
         dfl acc[2][2];
@@ -150,18 +154,61 @@ __device__ void cta_gemm_dfl(int M, int N, int K, LA la, LB lb, EPI epi, dfl* sm
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) acc[a][b] = dfl(0.0f, 0.0f);
-        for (int k0 = 0; k0 < K; k0 += KC) {
-            for (int t = tid; t < TM * KC; t += 256) {
+        // operands that are double-float already (the replay, the matvec) are prefetched into
+        // registers one k-step ahead; FP64 operands (split while staged) are staged directly,
+        // where the extra registers would cost more occupancy than the overlap gains
+        constexpr bool kPrefetch = std::is_same<std::decay_t<decltype(la(0, 0))>, dfl>::value &&
+                                   std::is_same<std::decay_t<decltype(lb(0, 0))>, dfl>::value;
+        if constexpr (!kPrefetch) {
+            for (int k0 = 0; k0 < K; k0 += KC) {
+                for (int t = tid; t < TM * KC; t += 256) {
+                    const int i = t / KC, k = t - i * KC;
+                    const int gi = m0 + i, gk = k0 + k;
+                    As[k * LDA + i] = (gi < M && gk < K) ? dfl(la(gi, gk)) : dfl(0.0f, 0.0f);
+                }
+                for (int t = tid; t < KC * TN; t += 256) {
+                    const int k = t / TN, j = t - k * TN;
+                    const int gk = k0 + k, gj = n0 + j;
+                    Bs[k * LDB + j] = (gk < K && gj < N) ? dfl(lb(gk, gj)) : dfl(0.0f, 0.0f);
+                }
+                __syncthreads();
+                const int kc = min(KC, K - k0);
+                for (int kk = 0; kk < kc; ++kk) {
+                    const dfl a0 = As[kk * LDA + ty], a1 = As[kk * LDA + ty + 16];
+                    const dfl b0 = Bs[kk * LDB + tx], b1 = Bs[kk * LDB + tx + 16];
+                    dfl_fma_acc(acc[0][0], a0, b0);
+                    dfl_fma_acc(acc[0][1], a0, b1);
+                    dfl_fma_acc(acc[1][0], a1, b0);
+                    dfl_fma_acc(acc[1][1], a1, b1);
+                }
+                __syncthreads();
+            }
+        } else {
+        dfl ra[4], rb[4];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = tid + 256 * u;
                 const int i = t / KC, k = t - i * KC;
                 const int gi = m0 + i, gk = k0 + k;
-                As[k * LDA + i] = (gi < M && gk < K) ? dfl(la(gi, gk)) : dfl(0.0f, 0.0f);
+                ra[u] = (gi < M && gk < K) ? dfl(la(gi, gk)) : dfl(0.0f, 0.0f);
+                const int kb = t / TN, jb = t - kb * TN;
+                const int gkb = k0 + kb, gj = n0 + jb;
+                rb[u] = (gkb < K && gj < N) ? dfl(lb(gkb, gj)) : dfl(0.0f, 0.0f);
             }
-            for (int t = tid; t < KC * TN; t += 256) {
-                const int k = t / TN, j = t - k * TN;
-                const int gk = k0 + k, gj = n0 + j;
-                Bs[k * LDB + j] = (gk < K && gj < N) ? dfl(lb(gk, gj)) : dfl(0.0f, 0.0f);
+        };
+        if (K > 0) fetch(0);
+        for (int k0 = 0; k0 < K; k0 += KC) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = tid + 256 * u;
+                const int i = t / KC, k = t - i * KC;
+                As[k * LDA + i] = ra[u];
+                const int kb = t / TN, jb = t - kb * TN;
+                Bs[kb * LDB + jb] = rb[u];
             }
             __syncthreads();
+            if (k0 + KC < K) fetch(k0 + KC);
             const int kc = min(KC, K - k0);
             for (int kk = 0; kk < kc; ++kk) {
                 const dfl a0 = As[kk * LDA + ty], a1 = As[kk * LDA + ty + 16];
@@ -172,6 +219,7 @@ __device__ void cta_gemm_dfl(int M, int N, int K, LA la, LB lb, EPI epi, dfl* sm
                 dfl_fma_acc(acc[1][1], a1, b1);
             }
             __syncthreads();
+        }
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
