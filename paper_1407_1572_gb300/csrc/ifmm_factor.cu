@@ -143,9 +143,12 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
 // Shared memory: slab (rows_loc x s, or in the box's global FP64 workspace when slab_global),
 // prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 8 (portable).
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, const int* boxes, int C, int smax,
                                                             int slab_global) {
+    // element type of the elimination: FP64, or double-float (DF, the mixed mode) with the pivot
+    // reciprocal taken in FP64 and the row operations on the FP32 pipe
+    using S = std::conditional_t<DF, dfl, double>;
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double dsm[];
@@ -159,14 +162,14 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
     const int n = L.n[e], r = L.r[e], s = n + r;
     const int rows_max = (smax + C - 1) / C;
     double* base = slab_global ? dsm : dsm + (size_t)rows_max * smax;
-    double* prow = base;                              // smax
-    double* fcol = prow + smax;                       // rows_max
+    S* prow = reinterpret_cast<S*>(base);             // smax
+    S* fcol = prow + smax;                            // rows_max
     int* perm = reinterpret_cast<int*>(fcol + rows_max);  // smax
     int* used = perm + smax;                          // rows_max
     const int rows_loc = s > c ? (s - c + C - 1) / C : 0;
     // local row tl of this block is global row c + tl C: in shared memory (slab_global = 0) at
     // dsm + tl s, in global memory at row c + tl C of the box's s x s workspace
-    double* slab = slab_global ? L.pws + L.psoff[e] + (size_t)c * s : dsm;
+    S* slab = reinterpret_cast<S*>(slab_global ? L.pws + L.psoff[e] + (size_t)c * s : dsm);
     const size_t sstride = slab_global ? (size_t)C * s : (size_t)s;
     int ldp;
     const T* Pee = block_at(L, e, e, ldp);
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         else if (i < n) v = alpha * (double)We[(size_t)i * RC + (j - n)];
         else if (j < n) v = alpha * (double)We[(size_t)j * RC + (i - n)];
         else v = 0.0;
-        slab[(size_t)tl * sstride + j] = v;
+        slab[(size_t)tl * sstride + j] = S(v);
         tl += dr;
         j += dc;
         if (j >= s) { j -= s; ++tl; }
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         int bi = -1;
         for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) {
             if (used[tl]) continue;
-            const double v = fabs(slab[(size_t)tl * sstride + k]);
+            const double v = sc_mag(slab[(size_t)tl * sstride + k]);
             const int gi = c + tl * C;
             if (bi < 0 || v > best || (v == best && gi < bi)) { best = v; bi = gi; }
         }
@@ -237,10 +240,10 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         if (threadIdx.x == 0) perm[k] = p;
         if (c == owner) {
             // every thread reads the pivot before the thread with j == k overwrites it
-            const double d = 1.0 / slab[(size_t)tp * sstride + k];
+            const S d = S(1.0 / (double)slab[(size_t)tp * sstride + k]);
             __syncthreads();
             for (int j = threadIdx.x; j < s; j += blockDim.x) {
-                const double v = (j == k) ? d : slab[(size_t)tp * sstride + j] * d;
+                const S v = (j == k) ? d : sc_mul(slab[(size_t)tp * sstride + j], d);
                 slab[(size_t)tp * sstride + j] = v;
                 prow[j] = v;
             }
@@ -248,17 +251,17 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         }
         cl.sync();
         if (c != owner) {
-            const double* rp = cl.map_shared_rank(prow, owner);
+            const S* rp = cl.map_shared_rank(prow, owner);
             for (int j = threadIdx.x; j < s; j += blockDim.x) prow[j] = rp[j];
         }
         for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) fcol[tl] = slab[(size_t)tl * sstride + k];
         __syncthreads();
-        const double d = prow[k];
+        const S d = prow[k];
         for (int tl = tl0, j = j0; tl < rows_loc;) {
             if (!(c == owner && tl == tp)) {
-                const double f = fcol[tl];
-                if (j == k) slab[(size_t)tl * sstride + k] = -f * d;
-                else slab[(size_t)tl * sstride + j] -= f * prow[j];
+                const S f = fcol[tl];
+                if (j == k) slab[(size_t)tl * sstride + k] = sc_neg(sc_mul(f, d));
+                else slab[(size_t)tl * sstride + j] = sc_fms(slab[(size_t)tl * sstride + j], f, prow[j]);
             }
             tl += dr;
             j += dc;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
         const int kk = used[tl];
         const int col = perm[j];
         const double sc = (kk >= n ? alpha : 1.0) * (col >= n ? alpha : 1.0);
-        Pi[(size_t)kk * ld + col] = (T)(sc * slab[(size_t)tl * sstride + j]);
+        Pi[(size_t)kk * ld + col] = (T)(sc * (double)slab[(size_t)tl * sstride + j]);
         tl += dr;
         j += dc;
         if (j >= s) { j -= s; ++tl; }
@@ -799,9 +802,11 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         // (falls back to C = 1 below when the cluster shape cannot be scheduled)
         static bool cl_attr[2] = {false, false};
         if (!cl_attr[sizeof(T) == 8]) {
-            cudaFuncSetAttribute(k_pivot_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+            cudaFuncSetAttribute(k_pivot_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+            cudaFuncSetAttribute(k_pivot_cluster<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
             cl_attr[sizeof(T) == 8] = true;
         }
+        auto kfn = (std::is_same<T, double>::value && L.gemm_dfl) ? k_pivot_cluster<T, true> : k_pivot_cluster<T, false>;
         const size_t cbytes = cl_bytes(C, slab_global);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nboxes * C));
@@ -816,10 +821,10 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, k_pivot_cluster<T>, &cfg) != cudaSuccess || active < 1) {
+        if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess || active < 1) {
             cudaGetLastError();
             C = 1;   // this cluster shape cannot be scheduled: one block per box
-        } else if (cudaLaunchKernelEx(&cfg, k_pivot_cluster<T>, L, boxes, C, smax, slab_global) != cudaSuccess) {
+        } else if (cudaLaunchKernelEx(&cfg, kfn, L, boxes, C, smax, slab_global) != cudaSuccess) {
             cudaGetLastError();
             C = 1;   // launch refused: one block per box instead
         }
