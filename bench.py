@@ -189,38 +189,59 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# Arithmetic peaks of the CUDA cores: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz (unit counts and
-# the maximum clock); FP64 = the nominal 1.25 TFLOP/s of GB300.
+# Arithmetic peaks of the CUDA cores from unit counts and the maximum clock: FP32 = 152 SMs x 128 lanes
+# x 2 flops x 2.07 GHz; FP64 = the nominal 1.25 TFLOP/s of GB300 (304 DFMA per clock); double-float =
+# the FP32 lanes at 11 FP32 instructions per multiply-add (exact product, cross terms, exact sum),
+# counted as 2 FP64-equivalent flops per multiply-add.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_TFLOPS = 1.25
+DFL_TFLOPS = 152 * 128 * 2.07e9 / 11 * 2 / 1e12
+
+# arithmetic of each factor kernel per precision
+ARITH = {
+    "fp64": {k: "FP64" for k in ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")},
+    "mixed_solve": {"k_pivot": "double-float row operations (cluster) / FP64 (small pivots)",
+                    "k_panel": "double-float GEMM", "k_schur": "double-float GEMM",
+                    "k_compress": "double-float projection GEMMs + FP64 Gram-Schmidt",
+                    "k_redirect": "double-float GEMM"},
+    "mixed": {k: "FP32" for k in ("k_panel", "k_schur", "k_compress", "k_redirect")} | {"k_pivot": "FP64"},
+}
+
+
+def _kernel_roofline(stats, precision, i):
+    from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
+    ms, launches, flops = stats["kernel_ms"], stats["kernel_launches"], stats["kernel_flops"]
+    name = FACTOR_KERNELS[i]
+    nl = max(launches[i], 1)
+    t = ms[i] / nl / 1000.0                       # seconds per launch (CUDA events, handle's stream)
+    flops_pl = flops[i] / nl
+    arith = ARITH[precision][name]
+    if arith.startswith("double-float GEMM"):
+        peak, src = DFL_TFLOPS, "double-float rate of the FP32 CUDA cores (unit counts at 2.07 GHz, 11 instructions per multiply-add)"
+    elif arith == "FP32":
+        peak, src = FP32_SIMT_TFLOPS, "FP32 CUDA cores from unit counts at 2.07 GHz"
+    else:
+        peak, src = FP64_TFLOPS, "nominal FP64 rate of GB300"
+    ach = flops_pl / t / 1e12
+    return {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
+            "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
+            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src}
 
 
 def roofline(stats, precision, peaks, peak_kind):
-    from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
-    ms, launches, flops = stats["kernel_ms"], stats["kernel_launches"], stats["kernel_flops"]
+    """Dominant factor kernel (CUDA-event time); `schur` adds the Schur-update kernel, the dense
+    contraction of the elimination, against the peak of its own arithmetic."""
+    ms = stats["kernel_ms"]
     top = max(range(5), key=lambda i: ms[i])
-    name = FACTOR_KERNELS[top]
-    nl = max(launches[top], 1)
-    t = ms[top] / nl / 1000.0                     # seconds per launch (CUDA events, handle's stream)
-    flops_pl = flops[top] / nl
-    fp32 = precision == "mixed" and name != "k_pivot"
-    alu_peak = FP32_SIMT_TFLOPS if fp32 else FP64_TFLOPS
-    out = {"kernel": name, "share_of_factor_kernels": ms[top] / max(sum(ms), 1e-30), "avg_launch_ms": ms[top] / nl,
-           "launches": launches[top], "flops_per_launch": flops_pl}
-    hbm = peaks["hbm_gbs"]
-    if name == "k_schur":
-        bytes_pl = stats["schur_bytes"] / nl
-        ai = flops_pl / max(bytes_pl, 1.0)
-        out["intensity_flop_per_byte"] = ai
-        if ai * hbm / 1000.0 < alu_peak:
-            ach = bytes_pl / t / 1e9
-            out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                        "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"})
-            return out
-    ach = flops_pl / t / 1e12
-    out.update({"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                "traffic": None,
-                "peak_source": ("FP32 CUDA cores from unit counts at 2.07 GHz" if fp32 else "nominal FP64 rate of GB300")})
+    out = _kernel_roofline(stats, precision, top)
+    out["schur"] = _kernel_roofline(stats, precision, 2)
+    # the Schur step's algorithmic bytes, for the intensity against HBM
+    nl = max(stats["kernel_launches"][2], 1)
+    bytes_pl = stats["schur_bytes"] / nl
+    out["schur"]["intensity_flop_per_byte"] = (stats["kernel_flops"][2] / nl) / max(bytes_pl, 1.0)
+    out["schur"]["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    out["schur"]["hbm_peak_source"] = f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
     return out
 
 
