@@ -65,7 +65,8 @@ typedef enum {
 
 typedef struct {
     int dim;              /* space dimension; must be 2 (quadtree)                               */
-    int depth;            /* leaf level kappa of the uniform tree, 2 <= depth <= 10              */
+    int depth;            /* leaf level kappa of the uniform tree, 2 <= depth <= 10; 0 = automatic
+                             (see leaf_max)                                                       */
     int cheb_p;           /* Chebyshev nodes per dimension (Section 5); initial box rank p^2      */
     int r_cap;            /* largest rank any box basis may reach; <= 0: only the box size n_i   */
     double eps;           /* compression tolerance of the fill-in (Section 5)                     */
@@ -87,6 +88,8 @@ typedef struct {
     double refine_inner;  /* IFMM_MIXED_SOLVE: a GMRES cycle (double-float products) ends once its error
                              estimate has fallen by this factor, then the FP64 residual is formed
                              again; <= 0 selects 1e-4                                             */
+    int leaf_max;         /* depth = 0: the build takes the smallest depth whose fullest leaf holds
+                             at most leaf_max points (ifmm_auto_depth)                           */
 } ifmm_params;
 
 typedef struct {
@@ -112,8 +115,15 @@ typedef struct {
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
- * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30, refine_inner 1e-4). */
+ * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30, refine_inner 1e-4),
+ * leaf_max 64. */
 void ifmm_default_params(ifmm_params* p);
+
+/* Smallest depth 2..10 of the uniform quadtree (Section 4.2: boxes of level k form a 2^k x 2^k
+ * grid of the root box) whose fullest leaf holds at most leaf_max points; 10 if none. pts_host:
+ * N x 2 row-major host array; box: {x0, y0, side} or NULL for the unit square (side <= 0 also
+ * selects it). Host only (no device call). Returns -1 for invalid arguments. */
+int ifmm_auto_depth(const double* pts_host, int64_t N, const double* box, int leaf_max);
 
 /* Build the tree, the Chebyshev operators and their orthonormal nested bases (assembly time t_a).
  * pts_host: N x 2 row-major FP64 host array (x0, y0, x1, y1, ...), copied; N >= 1.
@@ -145,6 +155,21 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
  * matrix and the transposed solve replays them exactly as ifmm_solve does (Algorithm 2).
  * Arguments, layout, refinement and errors are those of ifmm_solve. */
 ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld);
+
+/* Batched factorisation of n independent systems (no counterpart in the paper, which solves one
+ * system; the batched workload of many uneven systems). A native scheduler gives the systems,
+ * largest N first, to `workers` host threads (<= 0: min(n, 16)), each to the thread with the least
+ * work so far; a thread factors its systems one after another on their own handles' streams, so
+ * handles built on distinct streams run concurrently on the GPU. status_out (n entries, may be
+ * NULL) receives each ifmm_factor status; the call returns the first non-OK one (IFMM_OK when all
+ * succeeded). Handles must be distinct; no other call may use them meanwhile. */
+ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* status_out);
+
+/* Batched ifmm_solve of n factored systems: system i solves nrhs[i] right-hand sides b_dev[i] into
+ * x_dev[i] (device, column-major, leading dimension ld[i]); scheduling (by N x nrhs), streams,
+ * statuses and return value as in ifmm_factor_batch. */
+ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
+                             const int64_t* ld, int workers, ifmm_status* status_out);
 
 /* As ifmm_solve with host buffers: copies b in and x out inside the call. */
 ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld);

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -92,11 +94,13 @@ int region36_host(int px, int py, int qx, int qy) { return (qx - 2 * (px >> 1) +
 struct ifmm_handle {
     ifmm_params prm{};
     int kernel = 0;
+    int device = 0;
     int64_t N = 0;
     int depth = 0, p = 0, r0 = 0;
     cudaStream_t st = nullptr;
     std::string err;
     std::vector<std::pair<void*, size_t>> allocs;
+    cudaMemPool_t pool = nullptr;   // stream-ordered allocations on st (NULL: cudaMalloc / cudaFree)
     int64_t bytes = 0;
     // tree
     int64_t* d_perm = nullptr;
@@ -144,12 +148,39 @@ namespace {
         if (s_ != IFMM_OK) return s_;   \
     } while (0)
 
+// Device memory of the handles comes from one library-owned, stream-ordered pool per device: buffers
+// are allocated and freed in order on the handle's stream, so a free never synchronises the device
+// (handles factored concurrently on separate streams keep overlapping), and the pool keeps freed
+// memory for the next level or factorisation (release threshold unbounded; ifmm_destroy trims it).
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t library_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pools[dev] = pool;
+    return pool;
+}
+
 template <typename P>
 ifmm_status dalloc(ifmm_handle* h, P** out, size_t bytes) {
     *out = nullptr;
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = h->pool ? cudaMallocFromPoolAsync(&p, bytes, h->pool, h->st) : cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         h->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
@@ -167,7 +198,8 @@ void dfree(ifmm_handle* h, void* p) {
         if (h->allocs[i].first == p) {
             h->bytes -= (int64_t)h->allocs[i].second;
             h->allocs.erase(h->allocs.begin() + i);
-            cudaFree(p);
+            if (h->pool) cudaFreeAsync(p, h->st);
+            else cudaFree(p);
             return;
         }
 }
@@ -1081,6 +1113,48 @@ ifmm_status solve_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
 // ------------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------------
+// Batched calls: a native scheduler runs independent systems concurrently. Systems are taken in
+// order of decreasing work (N x nrhs) and each goes to the worker with the least work so far
+// (longest-processing-time-first); a worker runs its systems in that order on their own streams.
+namespace {
+template <class F>
+ifmm_status run_batch(ifmm_h* hs, int n, int workers, const std::vector<double>& work, ifmm_status* status_out,
+                      F one) {
+    if (!hs || n <= 0) return IFMM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i]) return IFMM_ERR_INVALID_ARG;
+    if (workers <= 0) workers = std::min(n, 16);
+    workers = std::min(workers, n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<std::vector<int>> lists(workers);
+    std::vector<double> load(workers, 0.0);
+    for (int i : order) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[w].push_back(i);
+        load[w] += work[i];
+    }
+    std::vector<ifmm_status> st(n, IFMM_OK);
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w)
+        pool.emplace_back([&, w]() {
+            for (int i : lists[w]) {
+                cudaSetDevice(hs[i]->device);
+                st[i] = one(i);
+            }
+        });
+    for (auto& t : pool) t.join();
+    ifmm_status first = IFMM_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status_out) status_out[i] = st[i];
+        if (first == IFMM_OK && st[i] != IFMM_OK) first = st[i];
+    }
+    return first;
+}
+}  // namespace
+
+
 extern "C" {
 
 void ifmm_default_params(ifmm_params* p) {
@@ -1099,13 +1173,39 @@ void ifmm_default_params(ifmm_params* p) {
     p->refine_maxit = 100;
     p->refine_restart = 30;
     p->refine_inner = 1e-4;
+    p->leaf_max = 64;
+}
+
+// Smallest depth 2..10 of the uniform tree whose fullest leaf holds at most leaf_max points, with the
+// build's leaf rule (floor of the box-relative coordinate times 2^depth, the upper edge clamped into
+// the last box); 10 if none. Host only.
+int ifmm_auto_depth(const double* pts_host, int64_t N, const double* box, int leaf_max) {
+    if (!pts_host || N <= 0 || leaf_max <= 0) return -1;
+    double x0 = 0.0, y0 = 0.0, L = 1.0;
+    if (box && box[2] > 0.0) { x0 = box[0]; y0 = box[1]; L = box[2]; }
+    for (int depth = 2; depth <= 10; ++depth) {
+        const int side = 1 << depth;
+        std::vector<int> cnt((size_t)side * side, 0);
+        int mx = 0;
+        for (int64_t t = 0; t < N; ++t) {
+            const double ux = std::fmin(std::fmax((pts_host[2 * t] - x0) / L, 0.0), 1.0);
+            const double uy = std::fmin(std::fmax((pts_host[2 * t + 1] - y0) / L, 0.0), 1.0);
+            const int ix = std::min((int)std::floor(ux * side), side - 1);
+            const int iy = std::min((int)std::floor(uy * side), side - 1);
+            mx = std::max(mx, ++cnt[(size_t)iy * side + ix]);
+        }
+        if (mx <= leaf_max) return depth;
+    }
+    return 10;
 }
 
 ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm_params* p, void* stream,
                        ifmm_h* out) {
     if (out) *out = nullptr;
     if (!pts_host || !p || !out || N <= 0 || N >= (1ll << 31)) return IFMM_ERR_INVALID_ARG;
-    if (p->dim != 2 || p->depth < 2 || p->depth > 10 || p->cheb_p < 1 || p->cheb_p > 8) return IFMM_ERR_INVALID_ARG;
+    if (p->dim != 2 || (p->depth != 0 && (p->depth < 2 || p->depth > 10)) || p->cheb_p < 1 || p->cheb_p > 8)
+        return IFMM_ERR_INVALID_ARG;
+    if (p->depth == 0 && p->leaf_max <= 0) return IFMM_ERR_INVALID_ARG;
     if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP && kernel != IFMM_K_DEXP_DELL) return IFMM_ERR_INVALID_ARG;
     if ((kernel == IFMM_K_EXP || kernel == IFMM_K_DEXP_DELL) && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
     if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
@@ -1125,7 +1225,10 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     }
     h->kernel = kernel;
     h->N = N;
-    h->depth = p->depth;
+    if (h->prm.depth == 0) h->prm.depth = ifmm_auto_depth(pts_host, N, h->prm.box, h->prm.leaf_max);
+    h->depth = h->prm.depth;
+    cudaGetDevice(&h->device);
+    h->pool = library_pool(h->device);
     h->p = p->cheb_p;
     h->r0 = p->cheb_p * p->cheb_p;
     h->st = (cudaStream_t)stream;
@@ -1196,6 +1299,22 @@ ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs,
     return ifmm_solve(h, b_dev, x_dev, nrhs, ld);
 }
 
+ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* status_out) {
+    if (!hs || n <= 0) return IFMM_ERR_INVALID_ARG;
+    std::vector<double> work(n);
+    for (int i = 0; i < n; ++i) work[i] = hs[i] ? (double)hs[i]->N : 0.0;
+    return run_batch(hs, n, workers, work, status_out, [&](int i) { return ifmm_factor(hs[i]); });
+}
+
+ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
+                             const int64_t* ld, int workers, ifmm_status* status_out) {
+    if (!hs || n <= 0 || !b_dev || !x_dev || !nrhs || !ld) return IFMM_ERR_INVALID_ARG;
+    std::vector<double> work(n);
+    for (int i = 0; i < n; ++i) work[i] = hs[i] ? (double)hs[i]->N * std::max(nrhs[i], 1) : 0.0;
+    return run_batch(hs, n, workers, work, status_out,
+                     [&](int i) { return ifmm_solve(hs[i], b_dev[i], x_dev[i], nrhs[i], ld[i]); });
+}
+
 ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld) {
     if (!h || !b_host || !x_host || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
     if (!h->factored) {
@@ -1244,9 +1363,18 @@ const char* ifmm_last_error(ifmm_h h) { return h ? h->err.c_str() : "null handle
 
 void ifmm_destroy(ifmm_h h) {
     if (!h) return;
+    cudaSetDevice(h->device);
     if (h->st) cudaStreamSynchronize(h->st);
     else cudaDeviceSynchronize();
-    for (auto& a : h->allocs) cudaFree(a.first);
+    for (auto& a : h->allocs) {
+        if (h->pool) cudaFreeAsync(a.first, h->st);
+        else cudaFree(a.first);
+    }
+    if (h->pool) {
+        if (h->st) cudaStreamSynchronize(h->st);
+        else cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(h->pool, 0);
+    }
     delete h;
 }
 

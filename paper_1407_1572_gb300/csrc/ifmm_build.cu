@@ -10,6 +10,7 @@
 //   M2L_bq = Rt_b K(nodes_b, nodes_q) Rt_q^T for q in the interaction list I_b;
 //   leaf P2P_bq = K(x_a, x_c) for q in N_b, with the diagonal A_aa on the same point.
 // Matvec y = A~ x (Table "table_FMM_operators"): P2M, M2M, M2L, L2L, L2P and P2P in FP64.
+#include <atomic>
 #include <cstdio>
 
 #include "ifmm_common.cuh"
@@ -296,10 +297,10 @@ __global__ void __launch_bounds__(kThreads) k_m2l_build(BuildArgs a, int k, cons
 void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const double* Rt, double* far0,
                       cudaStream_t st) {
     size_t smem = 2 * (size_t)a.r0 * a.r0 * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
         cudaFuncSetAttribute(k_m2l_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr = true;
+        attr.store(true);
     }
     k_m2l_build<<<dim3(1u << (2 * k), 36), kThreads, smem, st>>>(a, k, cheb, Rt, far0); count_launches(1);
 }

@@ -16,6 +16,7 @@
 //              M2P_pq = L2P_pp M2L_pq).
 // T is the storage type of blocks, bases and panels (double, or float in the mixed form).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include <cooperative_groups.h>
@@ -25,7 +26,9 @@
 
 namespace ifmm {
 
-static long long g_launches = 0;
+// per host thread, so that handles factored or solved concurrently by different threads each count
+// their own launches
+static thread_local long long g_launches = 0;
 void count_launches(int n) { g_launches += n; }
 long long launches_so_far() { return g_launches; }
 
@@ -776,12 +779,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     size_t full = base + (size_t)smax * smax * sizeof(double);
     int use_smem = full <= 200 * 1024 ? 1 : 0;
     size_t smem = use_smem ? full : base;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
+    static std::atomic<bool> attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8].load()) {
         cudaFuncSetAttribute(k_pivot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
         cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_set[sizeof(T) == 8] = true;
+        attr_set[sizeof(T) == 8].store(true);
     }
     // large pivot blocks and few boxes: one cluster of C blocks per box
     int C = 1, slab_global = 0;
@@ -800,11 +803,11 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     if (ev) cudaEventRecord(ev[0], st);
     if (C > 1) {
         // (falls back to C = 1 below when the cluster shape cannot be scheduled)
-        static bool cl_attr[2] = {false, false};
-        if (!cl_attr[sizeof(T) == 8]) {
+        static std::atomic<bool> cl_attr[2] = {false, false};
+        if (!cl_attr[sizeof(T) == 8].load()) {
             cudaFuncSetAttribute(k_pivot_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
             cudaFuncSetAttribute(k_pivot_cluster<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-            cl_attr[sizeof(T) == 8] = true;
+            cl_attr[sizeof(T) == 8].store(true);
         }
         auto kfn = (std::is_same<T, double>::value && L.gemm_dfl) ? k_pivot_cluster<T, true> : k_pivot_cluster<T, false>;
         const size_t cbytes = cl_bytes(C, slab_global);

@@ -30,7 +30,8 @@ class ifmm_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("tau_ref", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
                 ("refine_restart", ctypes.c_int),
-                ("refine_inner", ctypes.c_double)]
+                ("refine_inner", ctypes.c_double),
+                ("leaf_max", ctypes.c_int)]
 
 
 class ifmm_stats(ctypes.Structure):
@@ -58,7 +59,8 @@ class IFMMError(RuntimeError):
 _lib = None
 
 # every symbol include/ifmm.h declares
-SYMBOLS = ["ifmm_default_params", "ifmm_build", "ifmm_factor", "ifmm_solve", "ifmm_solve_T", "ifmm_solve_host",
+SYMBOLS = ["ifmm_default_params", "ifmm_auto_depth", "ifmm_build", "ifmm_factor", "ifmm_factor_batch",
+           "ifmm_solve", "ifmm_solve_T", "ifmm_solve_batch", "ifmm_solve_host",
            "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_get_ranks", "ifmm_get_stats", "ifmm_last_error",
            "ifmm_destroy"]
 
@@ -96,6 +98,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ifmm_last_error.restype = ctypes.c_char_p
     lib.ifmm_destroy.argtypes = [vp]
     lib.ifmm_destroy.restype = None
+    lib.ifmm_auto_depth.argtypes = [vp, i64, vp, ip]
+    lib.ifmm_auto_depth.restype = ip
+    lib.ifmm_factor_batch.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ip)]
+    lib.ifmm_factor_batch.restype = ip
+    lib.ifmm_solve_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(ip), ctypes.POINTER(i64), ip, ctypes.POINTER(ip)]
+    lib.ifmm_solve_batch.restype = ip
     _lib = lib
     return lib
 
@@ -129,6 +138,43 @@ def ifmm_build(points: np.ndarray, kernel: int, params: ifmm_params, stream: int
                            ctypes.c_void_p(stream), ctypes.byref(h))
     _check(None, st)
     return h
+
+
+def ifmm_auto_depth(points: np.ndarray, leaf_max: int = 64, box=None) -> int:
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    return load().ifmm_auto_depth(pts.ctypes.data_as(ctypes.c_void_p), pts.shape[0],
+                                  None if bx is None else bx.ctypes.data_as(ctypes.c_void_p), leaf_max)
+
+
+def ifmm_factor_batch(handles, workers: int = 0, allow_overflow: bool = False):
+    """Factor the systems of `handles` concurrently; returns the per-system statuses."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    st = (ctypes.c_int * n)()
+    load().ifmm_factor_batch(hs, n, workers, st)
+    out = list(st)
+    bad = [i for i, v in enumerate(out) if v not in ((IFMM_OK, IFMM_ERR_RANK_OVERFLOW) if allow_overflow else (IFMM_OK,))]
+    if bad:
+        raise IFMMError(out[bad[0]], f"system {bad[0]}: " + load().ifmm_last_error(handles[bad[0]]).decode())
+    return out
+
+
+def ifmm_solve_batch(handles, b_ptrs, x_ptrs, nrhs, lds, workers: int = 0, allow_noconv: bool = False):
+    """Solve the factored systems of `handles` concurrently (device pointers, column-major)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    bp = (ctypes.c_void_p * n)(*b_ptrs)
+    xp = (ctypes.c_void_p * n)(*x_ptrs)
+    nr = (ctypes.c_int * n)(*nrhs)
+    ld = (ctypes.c_int64 * n)(*lds)
+    st = (ctypes.c_int * n)()
+    load().ifmm_solve_batch(hs, n, bp, xp, nr, ld, workers, st)
+    out = list(st)
+    bad = [i for i, v in enumerate(out) if v not in ((IFMM_OK, IFMM_ERR_NOCONV) if allow_noconv else (IFMM_OK,))]
+    if bad:
+        raise IFMMError(out[bad[0]], f"system {bad[0]}: " + load().ifmm_last_error(handles[bad[0]]).decode())
+    return out
 
 
 def ifmm_factor(h, allow_overflow: bool = False) -> int:

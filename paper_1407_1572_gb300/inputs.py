@@ -51,6 +51,43 @@ def uniform_points(seed: int, n: int, lo: float = 0.0, side: float = 1.0) -> np.
     return lo + side * u
 
 
+def gaussian_blobs(seed: int, n: int, k: int = 8, sigma: float = 0.05, lo: float = 0.15, hi: float = 0.85) -> np.ndarray:
+    """n points from an equal-weight mixture of k isotropic Gaussians of standard deviation sigma whose
+    centres are uniform in [lo, hi]^2; a draw outside [0, 1)^2 is drawn again. Shape (n, 2)."""
+    centres = lo + (hi - lo) * uniform(seed, 2 * k).reshape(k, 2)
+    out = np.empty((n, 2))
+    filled, attempt = 0, 0
+    while filled < n:
+        m = 2 * (n - filled) + 16
+        s = seed + 7919 * (attempt + 1)
+        comp = np.minimum((uniform(s, m) * k).astype(np.int64), k - 1)
+        cand = centres[comp] + sigma * normal(s + 1, 2 * m).reshape(m, 2)
+        ok = (cand >= 0.0).all(axis=1) & (cand < 1.0).all(axis=1)
+        take = cand[ok][: n - filled]
+        out[filled: filled + len(take)] = take
+        filled += len(take)
+        attempt += 1
+    return out
+
+
+def batch_systems(seed: int = 1409, count: int = 256, nmin: int = 2048, nmax: int = 32768, rhs_min: int = 1,
+                  rhs_max: int = 16) -> list:
+    """The batched workload: `count` independent systems with N log-uniform in [nmin, nmax]; the first
+    half of the systems are uniform point clouds, the second half Gaussian blobs (8 centres, sigma
+    0.05); nrhs uniform in [rhs_min, rhs_max]. System i draws its points and right-hand sides from
+    seed * 1000 + i. Returns dicts with keys points, nrhs, kind, seed."""
+    u = uniform(seed, 2 * count)
+    out = []
+    for i in range(count):
+        n = int(round(float(np.exp(np.log(nmin) + (np.log(nmax) - np.log(nmin)) * u[2 * i]))))
+        nrhs = rhs_min + min(int(u[2 * i + 1] * (rhs_max - rhs_min + 1)), rhs_max - rhs_min)
+        si = seed * 1000 + i
+        kind = "uniform" if i < count // 2 else "blobs"
+        pts = uniform_points(si, n) if kind == "uniform" else gaussian_blobs(si, n)
+        out.append(dict(points=pts, nrhs=nrhs, kind=kind, seed=si))
+    return out
+
+
 def rhs(seed: int, n: int, nrhs: int) -> np.ndarray:
     """n x nrhs right-hand sides i.i.d. N(0, 1), column-major (Fortran) float64."""
     return np.asfortranarray(normal(seed, n * nrhs).reshape(nrhs, n).T)
