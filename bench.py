@@ -246,7 +246,7 @@ def roofline(stats, precision, peaks, peak_kind):
 
 
 BATCH = dict(count=256, seed=1409, nmin=2048, nmax=32768, rhs_min=1, rhs_max=16, cheb_p=4, eps=1e-6, leaf_max=64,
-             refine_tol=1e-7, wave=64, workers=16)
+             refine_tol=1e-7, wave=64, workers=48)
 
 
 def run_batched(precision: str):

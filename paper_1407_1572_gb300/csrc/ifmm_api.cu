@@ -95,6 +95,7 @@ struct ifmm_handle {
     ifmm_params prm{};
     int kernel = 0;
     int device = 0;
+    bool in_batch = false;   // factored by ifmm_factor_batch: pivot launches sized without a readback
     int64_t N = 0;
     int depth = 0, p = 0, r0 = 0;
     cudaStream_t st = nullptr;
@@ -500,23 +501,28 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
             bpo += (int64_t)L.n[b] * L.n[q];
         }
     }
-    // colour lists (Morton order inside a colour)
-    std::vector<std::pair<uint64_t, int>> keys(nb);
+    // colour lists (Morton order inside a colour). An empty box (n = 0, hence r = 0) has nothing
+    // to eliminate: its pivot, panels and Schur, compression and redirect contributions are all of
+    // size zero, so it is left out of the lists (uniform trees of clustered clouds are mostly empty)
+    std::vector<std::pair<uint64_t, int>> keys;
+    keys.reserve(nb);
     for (int b = 0; b < nb; ++b) {
+        if (L.n[b] == 0) continue;
         int bx = b % s, by = b / s;
-        keys[b] = {((uint64_t)((bx % 3) + 3 * (by % 3)) << 60) | morton_host(bx, by), b};
+        keys.push_back({((uint64_t)((bx % 3) + 3 * (by % 3)) << 60) | morton_host(bx, by), b});
     }
     std::sort(keys.begin(), keys.end());
-    L.boxes.resize(nb);
-    for (int t = 0; t < nb; ++t) L.boxes[t] = keys[t].second;
+    const int nact = (int)keys.size();
+    L.boxes.resize(nact);
+    for (int t = 0; t < nact; ++t) L.boxes[t] = keys[t].second;
     for (int c = 0; c <= 9; ++c) L.cstart[c] = 0;
     {
         int t = 0;
         for (int c = 0; c < 9; ++c) {
             L.cstart[c] = t;
-            while (t < nb && (int)(keys[t].first >> 60) == c) ++t;
+            while (t < nact && (int)(keys[t].first >> 60) == c) ++t;
         }
-        L.cstart[9] = nb;
+        L.cstart[9] = nact;
     }
     // per-colour scratch
     std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * 81, 0), rsoff((size_t)nb * 9, 0);
@@ -699,7 +705,8 @@ ifmm_status factor_impl(ifmm_handle* h) {
         for (int c = 0; c < 9; ++c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             if (cnt <= 0) continue;
-            launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->st, &ev[c * 6]);
+            launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->in_batch ? 0 : 1, h->st,
+                                    &ev[c * 6]);
             used[c] = true;
         }
         CK(cudaGetLastError());
@@ -722,6 +729,11 @@ ifmm_status factor_impl(ifmm_handle* h) {
         if (hs & DEV_ERR_SINGULAR) {
             h->err = "singular pivot block at level " + std::to_string(k);
             return IFMM_ERR_SINGULAR_PIVOT;
+        }
+        if (hs & DEV_ERR_SIZE) {
+            h->err = "the well-separated fill at level " + std::to_string(k) +
+                     " is wider than the compression's shared-memory arrays";
+            return IFMM_ERR_INVALID_ARG;
         }
     }
     // level 1: dense system over the level-2 multipoles
@@ -1303,7 +1315,12 @@ ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* statu
     if (!hs || n <= 0) return IFMM_ERR_INVALID_ARG;
     std::vector<double> work(n);
     for (int i = 0; i < n; ++i) work[i] = hs[i] ? (double)hs[i]->N : 0.0;
-    return run_batch(hs, n, workers, work, status_out, [&](int i) { return ifmm_factor(hs[i]); });
+    return run_batch(hs, n, workers, work, status_out, [&](int i) {
+        hs[i]->in_batch = true;
+        const ifmm_status s = ifmm_factor(hs[i]);
+        hs[i]->in_batch = false;
+        return s;
+    });
 }
 
 ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,

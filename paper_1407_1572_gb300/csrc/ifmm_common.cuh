@@ -127,30 +127,11 @@ IFMM_DEVINL dfl operator+(dfl a, dfl b) {
     return dfl_norm(dfl(s, e));
 }
 IFMM_DEVINL dfl operator-(dfl a, dfl b) { return a + dfl(-b.hi, -b.lo); }
-// a * b: exact product of the hi parts plus the cross terms, renormalised
-IFMM_DEVINL dfl dfl_mul(dfl a, dfl b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const float h = __fadd_rn(p, e);
-    return dfl(h, __fsub_rn(e, __fsub_rn(h, p)));
-}
-
-// scalar helpers shared by FP64 and double-float elimination code: magnitude for pivot search,
-// product, and s - f p
+// scalar helpers of the pivot elimination (FP64): magnitude for the pivot search, product, s - f p
 IFMM_DEVINL double sc_mag(double v) { return fabs(v); }
-IFMM_DEVINL double sc_mag(dfl v) { return (double)fabsf(v.hi); }
 IFMM_DEVINL double sc_mul(double a, double b) { return a * b; }
-IFMM_DEVINL dfl sc_mul(dfl a, dfl b) { return dfl_mul(a, b); }
 IFMM_DEVINL double sc_fms(double s, double f, double p) { return s - f * p; }
-IFMM_DEVINL dfl sc_fms(dfl s, dfl f, dfl p) {
-    dfl acc = s;
-    dfl_fma_acc(acc, dfl(-f.hi, -f.lo), p);
-    return dfl_norm(acc);
-}
 IFMM_DEVINL double sc_neg(double v) { return -v; }
-IFMM_DEVINL dfl sc_neg(dfl v) { return dfl(-v.hi, -v.lo); }
 IFMM_DEVINL dfl& operator+=(dfl& a, dfl b) {
     a = a + b;
     return a;

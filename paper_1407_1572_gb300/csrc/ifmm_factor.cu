@@ -18,6 +18,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -146,12 +149,13 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
 // Shared memory: slab (rows_loc x s, or in the box's global FP64 workspace when slab_global),
 // prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 8 (portable).
 // ---------------------------------------------------------------------------------------------
-template <typename T, bool DF>
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, const int* boxes, int C, int smax,
                                                             int slab_global) {
-    // element type of the elimination: FP64, or double-float (DF, the mixed mode) with the pivot
-    // reciprocal taken in FP64 and the row operations on the FP32 pipe
-    using S = std::conditional_t<DF, dfl, double>;
+    // pivot blocks are inverted in FP64 in every precision mode: they are the ill-conditioned part
+    // of the elimination (balanced condition numbers up to 5e7 on uniform clouds, worse on
+    // clustered ones), where a 48-bit double-float inversion broke GMRES on Gaussian-blob systems
+    using S = double;
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double dsm[];
@@ -749,6 +753,29 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int
     }
 }
 
+// Largest dynamic shared memory a launch of `fn` may use: the device's opt-in limit per block less
+// the kernel's static shared memory (queried once per kernel and device).
+int dynamic_smem_limit(const void* fn) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> lim;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = lim.find({fn, dev});
+    if (it != lim.end()) return it->second;
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    int v = 48 * 1024;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+        v = optin - (int)fa.sharedSizeBytes;
+    cudaGetLastError();
+    lim[{fn, dev}] = v;
+    return v;
+}
+
+__global__ void k_set_flag(int* status, int flag) { atomicOr(status, flag); }
+
 // largest pivot size s = n + r over the boxes of a colour at the time of their elimination (the
 // ranks grow on the device), into *out
 template <typename T>
@@ -762,12 +789,14 @@ __global__ void k_colour_smax(LevelView<T> L, const int* boxes, int nboxes, int*
 
 template <typename T>
 void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smax_bound,
-                          cudaStream_t st, cudaEvent_t* ev) {
+                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev) {
     if (nboxes <= 0) return;
     // size the pivot launch by the colour's actual largest pivot (the level bound nmax + min(nmax,
     // RC) is reached only when a basis fills up); status[2] is the scratch word
     int smax = smax_bound;
-    {
+    // (the readback waits for the stream: with exact_sizing = 0, as when many systems share the GPU
+    // and the pause would idle this system's stream, the level bound is used)
+    if (exact_sizing && smax_bound >= 96) {
         k_colour_smax<T><<<1, 256, 0, st>>>(L, boxes, nboxes, L.status + 2);
         count_launches(1);
         int hs = 0;
@@ -782,8 +811,13 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     static std::atomic<bool> attr_set[2] = {false, false};
     if (!attr_set[sizeof(T) == 8].load()) {
         cudaFuncSetAttribute(k_pivot<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-        cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        // set once to the largest size any launch may use: host threads factoring different systems
+        // launch concurrently, so a per-launch setting could be lowered under another's launch
+        cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dynamic_smem_limit((const void*)k_compress<T, false>));
+        cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dynamic_smem_limit((const void*)k_compress<T, true>));
+        cudaGetLastError();
         attr_set[sizeof(T) == 8].store(true);
     }
     // large pivot blocks and few boxes: one cluster of C blocks per box
@@ -805,11 +839,10 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         // (falls back to C = 1 below when the cluster shape cannot be scheduled)
         static std::atomic<bool> cl_attr[2] = {false, false};
         if (!cl_attr[sizeof(T) == 8].load()) {
-            cudaFuncSetAttribute(k_pivot_cluster<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-            cudaFuncSetAttribute(k_pivot_cluster<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+            cudaFuncSetAttribute(k_pivot_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
             cl_attr[sizeof(T) == 8].store(true);
         }
-        auto kfn = (std::is_same<T, double>::value && L.gemm_dfl) ? k_pivot_cluster<T, true> : k_pivot_cluster<T, false>;
+        auto kfn = k_pivot_cluster<T>;
         const size_t cbytes = cl_bytes(C, slab_global);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nboxes * C));
@@ -823,8 +856,24 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
+        // schedulability of the cluster shape, cached per (instantiation, C, shared memory)
+        static std::mutex occ_mu;
+        static std::map<std::tuple<const void*, int, size_t>, int> occ;
         int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess || active < 1) {
+        {
+            std::lock_guard<std::mutex> lk(occ_mu);
+            const auto key = std::make_tuple((const void*)kfn, C, cbytes);
+            auto it = occ.find(key);
+            if (it != occ.end()) active = it->second;
+            else {
+                if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess) {
+                    cudaGetLastError();
+                    active = 0;
+                }
+                occ[key] = active;
+            }
+        }
+        if (active < 1) {
             cudaGetLastError();
             C = 1;   // this cluster shape cannot be scheduled: one block per box
         } else if (cudaLaunchKernelEx(&cfg, kfn, L, boxes, C, smax, slab_global) != cudaSuccess) {
@@ -852,11 +901,14 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
     // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax)
     size_t csmem = (size_t)(smax_bound + 8 * L.RC + 10 * L.nmax) * sizeof(double);
-    if (df) {
-        cudaFuncSetAttribute(k_compress<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+    const void* kc = df ? (const void*)k_compress<T, true> : (const void*)k_compress<T, false>;
+    if (csmem > (size_t)dynamic_smem_limit(kc)) {
+        // the level's fills are too wide for the compression's shared arrays: report, do not launch
+        k_set_flag<<<1, 1, 0, st>>>(L.status, DEV_ERR_SIZE);
+        count_launches(1);
+    } else if (df) {
         k_compress<T, true><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
     } else {
-        cudaFuncSetAttribute(k_compress<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
         k_compress<T, false><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
     }
     if (ev) cudaEventRecord(ev[4], st);
@@ -1296,7 +1348,7 @@ void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, d
 }
 
 #define IFMM_INSTANTIATE(T)                                                                                     \
-    template void launch_factor_colour<T>(const LevelView<T>&, const int*, int, int, int, cudaStream_t,         \
+    template void launch_factor_colour<T>(const LevelView<T>&, const int*, int, int, int, int, cudaStream_t,    \
                                           cudaEvent_t*);                                                        \
     template void launch_forward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*, T*, T*,   \
                                            T*, int, cudaStream_t);                                              \

@@ -103,8 +103,10 @@ struct SolveView {
 // ---- launchers (ifmm_factor.cu) -----------------------------------------------------------
 // ev (optional): 6 events recorded before each of the five launches and after the last
 template <typename T>
+// smem_pivot_s: the level's bound on a pivot's size; exact_sizing: read the colour's actual largest
+// pivot back (a stream synchronisation) to size the pivot launch
 void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smem_pivot_s,
-                          cudaStream_t st, cudaEvent_t* ev);
+                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev);
 template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st);

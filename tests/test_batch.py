@@ -73,3 +73,30 @@ def test_blob_cloud_with_empty_leaves_matches_oracle(ifmm):
     rel = float(np.linalg.norm(x - xo) / np.linalg.norm(xo))
     print(f"blob cloud N={N} depth {depth}: GPU vs oracle {rel:.2e}")
     assert rel <= 1e-10
+
+
+def test_mixed_mode_blob_systems_reach_tolerance(ifmm):
+    """Gaussian-blob systems of the batched workload (clustered points: more ill-conditioned pivot
+    blocks than uniform clouds) solved in the mixed mode through the batch API reach the
+    manufactured solutions within 1e-6."""
+    sy = [s for i, s in enumerate(inputs.batch_systems(count=256)) if i in (128, 160, 192, 224, 250, 255)]
+    streams = [torch.cuda.Stream() for _ in sy]
+    hs, xs_l, bs_l, xo_l = [], [], [], []
+    for s, st in zip(sy, streams):
+        n = s["points"].shape[0]
+        prm = ifmm.default_params(depth=0, cheb_p=4, eps=1e-6, diag=math.sqrt(n), tau_ref=1,
+                                  precision=ifmm.IFMM_MIXED_SOLVE, refine_tol=1e-7, refine_maxit=120)
+        g = ifmm.IFMM(s["points"], 0, prm, st)
+        xs = torch.from_numpy(inputs.rhs(s["seed"], n, s["nrhs"]).T.copy()).cuda()
+        b = torch.empty_like(xs)
+        ifmm.ifmm_matvec(g.h, xs.data_ptr(), b.data_ptr(), s["nrhs"], n)
+        hs.append(g); xs_l.append(xs); bs_l.append(b); xo_l.append(torch.empty_like(xs))
+    torch.cuda.synchronize()
+    ifmm.ifmm_factor_batch([g.h for g in hs], workers=6, allow_overflow=True)
+    ifmm.ifmm_solve_batch([g.h for g in hs], [b.data_ptr() for b in bs_l], [x.data_ptr() for x in xo_l],
+                          [s["nrhs"] for s in sy], [s["points"].shape[0] for s in sy], workers=6)
+    torch.cuda.synchronize()
+    for x, xs in zip(xo_l, xs_l):
+        assert float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max()) <= 1e-6
+    for g in hs:
+        g.close()
