@@ -930,8 +930,10 @@ ifmm_status matvec_dfl_impl(ifmm_handle* h, const double* x, int64_t ldx, double
 // the double-float matvec (both on the FP32 pipe), and a cycle ends once its estimate has fallen
 // by refine_inner (or after m steps): the restart recomputes b - A~ x with the FP64 matvec, so the
 // double-float rounding limits each cycle's reduction, not the final accuracy (iterative
-// refinement with a mixed-precision inner GMRES). Only the estimate taken on that FP64 residual
-// ends the solve.
+// refinement with a mixed-precision inner GMRES). In every mode only an estimate taken on a freshly
+// computed FP64 residual ends the solve: the recurrence's own estimate |g_{j+1}| drifts from the
+// true preconditioned residual on ill-conditioned systems (measured 30x optimistic on a clustered
+// cloud), so reaching refine_tol inside a cycle triggers a restart that checks it.
 
 template <typename T>
 ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int64_t ld) {
@@ -1055,7 +1057,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         launch_colnorm2(x, ld, N, nrhs, dv, h->st);
         CKS(fetch(1));
         for (int c = 0; c < nrhs; ++c) xn[c] = std::sqrt(hv[c]);
-        if ((est <= tol && !inner32) || it >= h->prm.refine_maxit) break;
+        if (it >= h->prm.refine_maxit) break;
     }
     h->stats.refine_iters = it;
     h->stats.last_update = est;
