@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 
 METRIC = "factor+solve unknowns/s at N=2^20, err<=1e-6, mixed vs FP64 GPU; % of roofline"
 WORKLOAD = dict(N=1 << 20, depth=7, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
-                refine_maxit=120, refine_restart=30, refine_inner=1e-4)
+                refine_maxit=120, refine_restart=60, refine_inner=1e-4)
 # bounded CPU sample of the same workload family for the oracle (same points per leaf, settings)
 CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
                   refine_maxit=40, refine_restart=0)
@@ -270,7 +270,7 @@ def run_batched(precision: str):
             n = s["points"].shape[0]
             prm = ifmm.default_params(depth=0, leaf_max=c["leaf_max"], cheb_p=c["cheb_p"], eps=c["eps"],
                                       diag=math.sqrt(n), tau_ref=1, precision=precision_code(ifmm, precision),
-                                      refine_tol=c["refine_tol"], refine_maxit=120, refine_restart=30)
+                                      refine_tol=c["refine_tol"], refine_maxit=120, refine_restart=60)
             g = ifmm.IFMM(s["points"], ifmm.IFMM_K_INV_R, prm, torch.cuda.Stream())
             xs = torch.from_numpy(inputs.rhs(s["seed"], n, s["nrhs"]).T.copy()).cuda()
             b = torch.empty_like(xs)

@@ -115,7 +115,7 @@ typedef struct {
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
- * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 30, refine_inner 1e-4),
+ * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 60, refine_inner 1e-4),
  * leaf_max 64. */
 void ifmm_default_params(ifmm_params* p);
 

@@ -1185,7 +1185,7 @@ void ifmm_default_params(ifmm_params* p) {
     p->tau_ref = 1;
     p->refine_tol = 0.0;
     p->refine_maxit = 100;
-    p->refine_restart = 30;
+    p->refine_restart = 60;
     p->refine_inner = 1e-4;
     p->leaf_max = 64;
 }

@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 def test_default_params_and_struct_layout():
     p = ifmm.default_params()
     assert (p.dim, p.depth, p.cheb_p, p.precision, p.tau_ref) == (2, 3, 4, 0, 1)
-    assert p.box[2] == 1.0 and p.eps == 1e-10 and p.refine_maxit == 100 and p.refine_restart == 30
+    assert p.box[2] == 1.0 and p.eps == 1e-10 and p.refine_maxit == 100 and p.refine_restart == 60
     assert p.refine_inner == 1e-4 and p.leaf_max == 64
     # host-side argument checks reject bad input without touching a device
     h = ctypes.c_void_p()
