@@ -46,10 +46,16 @@ typedef enum {
 typedef enum {
     IFMM_K_INV_R = 0,            /* K(x, y) = 1 / |x - y|                                      */
     IFMM_K_EXP = 1,              /* K(x, y) = exp(-|x - y| / kparam[0])                        */
-    IFMM_K_DEXP_DELL = 2         /* K(x, y) = d/dl exp(-r / l) = (r / l^2) exp(-r / l), l = kparam[0],
+    IFMM_K_DEXP_DELL = 2,        /* K(x, y) = d/dl exp(-r / l) = (r / l^2) exp(-r / l), l = kparam[0],
                                     r = |x - y|: with diag = 0 its FMM matvec is dA~/dl of the
                                     IFMM_K_EXP matrix (the Chebyshev nodes and bases do not depend
                                     on l), the parameter derivative an adjoint gradient needs    */
+    /* the regularised kernels of the numerical benchmarks (Section 5), a = kparam[0] (0.001 there),
+       used with diag = 1 (Eq. "main_Solving_Equation"); each is 0 at r = 0                      */
+    IFMM_K_LOG_REG = 3,          /* r (log r - 1) / (a (log a - 1)) for r < a, ln r / ln a beyond  */
+    IFMM_K_INV_REG = 4,          /* r / a for r < a, a / r beyond                                  */
+    IFMM_K_R2LOG_REG = 5         /* r^3 (3 log r - 1) / (a^3 (3 log a - 1)) for r < a,
+                                    r^2 ln r / (a^2 ln a) beyond                                   */
 } ifmm_kernel;
 
 typedef enum {

@@ -366,6 +366,24 @@ double kernel_value(const oracle_params& p, double ax, double ay, double bx, dou
         // derivative of exp(-r / l) with respect to the length scale l
         case ORACLE_K_DEXP_DELL: return r / (p.kparam[0] * p.kparam[0]) * std::exp(-r / p.kparam[0]);
         case ORACLE_K_POLY: return (1.0 + ax * bx) * (1.0 + ay * by);
+        // the three regularised kernels of the numerical benchmarks (Section 5), a = kparam[0]:
+        // (i) r (log r - 1) / (a (log a - 1)) for r < a, ln r / ln a beyond; (ii) r / a, a / r;
+        // (iii) r^3 (3 log r - 1) / (a^3 (3 log a - 1)), r^2 ln r / (a^2 ln a); each tends to 0 at r = 0
+        case ORACLE_K_LOG_REG: {
+            const double a = p.kparam[0];
+            if (r == 0.0) return 0.0;
+            return r < a ? r * (std::log(r) - 1.0) / (a * (std::log(a) - 1.0)) : std::log(r) / std::log(a);
+        }
+        case ORACLE_K_INV_REG: {
+            const double a = p.kparam[0];
+            return r < a ? r / a : a / r;
+        }
+        case ORACLE_K_R2LOG_REG: {
+            const double a = p.kparam[0];
+            if (r == 0.0) return 0.0;
+            return r < a ? r * r * r * (3.0 * std::log(r) - 1.0) / (a * a * a * (3.0 * std::log(a) - 1.0))
+                         : r * r * std::log(r) / (a * a * std::log(a));
+        }
         default: return 0.0;
     }
 }
@@ -1252,7 +1270,9 @@ extern "C" {
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm) {
     if (!pts || !prm || N <= 0 || prm->depth < 2 || prm->depth > 12 || prm->cheb_p < 1 || prm->cheb_p > 12) return nullptr;
     if (!(prm->box[2] > 0.0) || prm->eps < 0.0) return nullptr;
-    if ((prm->kernel == ORACLE_K_EXP || prm->kernel == ORACLE_K_DEXP_DELL) && !(prm->kparam[0] > 0.0)) return nullptr;
+    if ((prm->kernel == ORACLE_K_EXP || prm->kernel == ORACLE_K_DEXP_DELL || prm->kernel >= ORACLE_K_LOG_REG) &&
+        !(prm->kparam[0] > 0.0))
+        return nullptr;
     auto h = std::make_unique<Handle>();
     h->prm = *prm;
     h->N = N;

@@ -18,7 +18,8 @@
 extern "C" {
 #endif
 
-enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_DEXP_DELL = 2, ORACLE_K_POLY = 3 };
+enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_DEXP_DELL = 2, ORACLE_K_POLY = 3,
+       ORACLE_K_LOG_REG = 4, ORACLE_K_INV_REG = 5, ORACLE_K_R2LOG_REG = 6 };
 
 typedef struct {
     int depth;          /* leaf level kappa >= 2 of the uniform quadtree                      */

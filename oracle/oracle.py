@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 K_INV_R, K_EXP, K_DEXP_DELL, K_POLY = 0, 1, 2, 3
+K_LOG_REG, K_INV_REG, K_R2LOG_REG = 4, 5, 6   # the numerical benchmarks of Section 5
 
 
 def compile_oracle(force: bool = False) -> str:

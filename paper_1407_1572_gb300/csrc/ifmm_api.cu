@@ -397,7 +397,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.eps = h->prm.eps;
     v.sA = h->prm.tau_ref == 2 ? L.scale : h->sA;
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
-    v.symmetric = 1;   // every kernel of the library (1/r, exp(-r/l), its l-derivative) is symmetric
+    v.symmetric = 1;   // every kernel of the library is radial, hence symmetric
     v.gemm_dfl = (std::is_same<T, double>::value && h->prm.precision == IFMM_MIXED_SOLVE) ? 1 : 0;
     return v;
 }
@@ -1220,8 +1220,8 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     if (p->dim != 2 || (p->depth != 0 && (p->depth < 2 || p->depth > 10)) || p->cheb_p < 1 || p->cheb_p > 8)
         return IFMM_ERR_INVALID_ARG;
     if (p->depth == 0 && p->leaf_max <= 0) return IFMM_ERR_INVALID_ARG;
-    if (kernel != IFMM_K_INV_R && kernel != IFMM_K_EXP && kernel != IFMM_K_DEXP_DELL) return IFMM_ERR_INVALID_ARG;
-    if ((kernel == IFMM_K_EXP || kernel == IFMM_K_DEXP_DELL) && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
+    if (kernel < IFMM_K_INV_R || kernel > IFMM_K_R2LOG_REG) return IFMM_ERR_INVALID_ARG;
+    if (kernel != IFMM_K_INV_R && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
     if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
     if (p->precision != IFMM_FP64 && p->precision != IFMM_MIXED && p->precision != IFMM_MIXED_SOLVE)
         return IFMM_ERR_INVALID_ARG;
@@ -1306,7 +1306,7 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
 // ifmm_solve, solved by the same replay of the factors.
 ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld) {
     if (!h) return IFMM_ERR_INVALID_ARG;
-    if (h->kernel != IFMM_K_INV_R && h->kernel != IFMM_K_EXP && h->kernel != IFMM_K_DEXP_DELL) {
+    if (h->kernel < IFMM_K_INV_R || h->kernel > IFMM_K_R2LOG_REG) {
         h->err = "ifmm_solve_T: the transposed replay is only provided for symmetric kernels";
         return IFMM_ERR_INVALID_ARG;
     }

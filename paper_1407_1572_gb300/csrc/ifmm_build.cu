@@ -44,6 +44,15 @@ IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay,
     double r = sqrt(dx * dx + dy * dy);
     if (kernel == 0) return 1.0 / r;
     if (kernel == 2) return r / (kparam0 * kparam0) * exp(-r / kparam0);  // d/dl of exp(-r / l)
+    if (kernel >= 3) {
+        // the regularised benchmark kernels of Section 5 (a = kparam0), each 0 at r = 0
+        const double a = kparam0;
+        if (kernel == 4) return r < a ? r / a : a / r;
+        if (r == 0.0) return 0.0;
+        if (kernel == 3) return r < a ? r * (log(r) - 1.0) / (a * (log(a) - 1.0)) : log(r) / log(a);
+        return r < a ? r * r * r * (3.0 * log(r) - 1.0) / (a * a * a * (3.0 * log(a) - 1.0))
+                     : r * r * log(r) / (a * a * log(a));
+    }
     return exp(-r / kparam0);
 }
 

@@ -17,6 +17,7 @@ IFMM_OK, IFMM_ERR_INVALID_ARG, IFMM_ERR_CUDA, IFMM_ERR_OOM = 0, 1, 2, 3
 IFMM_ERR_SINGULAR_PIVOT, IFMM_ERR_RANK_OVERFLOW, IFMM_ERR_NOCONV = 4, 5, 6
 IFMM_ERR_TIMEOUT, IFMM_ERR_STATE = 7, 8
 IFMM_K_INV_R, IFMM_K_EXP, IFMM_K_DEXP_DELL = 0, 1, 2
+IFMM_K_LOG_REG, IFMM_K_INV_REG, IFMM_K_R2LOG_REG = 3, 4, 5   # Section 5 benchmark kernels
 IFMM_FP64, IFMM_MIXED, IFMM_MIXED_SOLVE = 0, 1, 2
 _NAMES = {0: "IFMM_OK", 1: "IFMM_ERR_INVALID_ARG", 2: "IFMM_ERR_CUDA", 3: "IFMM_ERR_OOM",
           4: "IFMM_ERR_SINGULAR_PIVOT", 5: "IFMM_ERR_RANK_OVERFLOW", 6: "IFMM_ERR_NOCONV",

@@ -70,6 +70,30 @@ def test_length_scale_derivative_kernel(oracle_mod):
         assert d == pytest.approx(fd, rel=1e-6, abs=1e-12)
 
 
+def test_benchmark_kernels_closed_form_and_continuity(oracle_mod):
+    """The three regularised kernels of Section 5 (a = 0.001): values on both branches and
+    continuity at r = a, where both branches equal 1."""
+    O = oracle_mod
+    a = 1e-3
+    mk = lambda k: O.make_params(3, 4, k, kparam=(a, 0, 0, 0))
+    r_small, r_big = 4e-4, 0.3
+    pts = lambda r: ([0.0, 0.0], [r, 0.0])
+    la = math.log(a)
+    assert O.kernel_eval(mk(O.K_LOG_REG), *pts(r_big)) == pytest.approx(math.log(r_big) / la, rel=1e-14)
+    assert O.kernel_eval(mk(O.K_LOG_REG), *pts(r_small)) == pytest.approx(
+        r_small * (math.log(r_small) - 1) / (a * (la - 1)), rel=1e-14)
+    assert O.kernel_eval(mk(O.K_INV_REG), *pts(r_big)) == pytest.approx(a / r_big, rel=1e-15)
+    assert O.kernel_eval(mk(O.K_INV_REG), *pts(r_small)) == pytest.approx(r_small / a, rel=1e-15)
+    assert O.kernel_eval(mk(O.K_R2LOG_REG), *pts(r_big)) == pytest.approx(r_big ** 2 * math.log(r_big) / (a * a * la), rel=1e-14)
+    assert O.kernel_eval(mk(O.K_R2LOG_REG), *pts(r_small)) == pytest.approx(
+        r_small ** 3 * (3 * math.log(r_small) - 1) / (a ** 3 * (3 * la - 1)), rel=1e-14)
+    for k in (O.K_LOG_REG, O.K_INV_REG, O.K_R2LOG_REG):
+        lo = O.kernel_eval(mk(k), *pts(a * (1 - 1e-9)))
+        hi = O.kernel_eval(mk(k), *pts(a * (1 + 1e-9)))
+        assert lo == pytest.approx(1.0, abs=1e-7) and hi == pytest.approx(1.0, abs=1e-7)
+        assert O.kernel_eval(mk(k), [0.2, 0.3], [0.2, 0.3]) == 0.0
+
+
 # ---- tree and lists (Section 4.2, Table "table_cluster") -------------------------------------
 
 def test_lists_brute_force(oracle_mod):
@@ -159,13 +183,15 @@ def test_polynomial_kernel_is_reproduced_exactly(oracle_mod):
         assert np.abs(A - At).max() < 1e-12 * np.abs(A).max()
 
 
-@pytest.mark.parametrize("kernel", ["inv_r", "exp"])
+@pytest.mark.parametrize("kernel", ["inv_r", "exp", "log_reg", "inv_reg", "r2log_reg"])
 def test_nested_operators_equal_textbook_formula(oracle_mod, kernel):
     """A~ through P2M/M2M/M2L/L2L/L2P with orthonormalised bases equals the per-level Chebyshev
     formula sum_{m,l} S_m(x) K(xbar_m, ybar_l) S_l(y) (nesting of polynomial interpolation)."""
     O = oracle_mod
-    kk = O.K_INV_R if kernel == "inv_r" else O.K_EXP
-    o, _ = _oracle(O, 700, 4, 3, kernel=kk, kparam=(0.1, 0, 0, 0))
+    kk = {"inv_r": O.K_INV_R, "exp": O.K_EXP, "log_reg": O.K_LOG_REG, "inv_reg": O.K_INV_REG,
+          "r2log_reg": O.K_R2LOG_REG}[kernel]
+    kp = (0.1, 0, 0, 0) if kernel == "exp" else (1e-3, 0, 0, 0)
+    o, _ = _oracle(O, 700, 4, 3, kernel=kk, kparam=kp)
     At = o.dense_tilde()
     Ad = o.dense_tilde_direct()
     assert np.abs(At - Ad).max() < 1e-12 * np.abs(Ad).max()
