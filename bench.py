@@ -200,7 +200,7 @@ DFL_TFLOPS = 152 * 128 * 2.07e9 / 11 * 2 / 1e12
 # arithmetic of each factor kernel per precision
 ARITH = {
     "fp64": {k: "FP64" for k in ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")},
-    "mixed_solve": {"k_pivot": "double-float row operations (cluster) / FP64 (small pivots)",
+    "mixed_solve": {"k_pivot": "FP64",
                     "k_panel": "double-float GEMM", "k_schur": "double-float GEMM",
                     "k_compress": "double-float projection GEMMs + FP64 Gram-Schmidt",
                     "k_redirect": "double-float GEMM"},
@@ -208,7 +208,29 @@ ARITH = {
 }
 
 
-def _kernel_roofline(stats, precision, i):
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over the kernel's
+# launches) from one ncu capture of this bench's own command at N = 2^20 (summary in
+# profiles/launches_bench_n1048576_mixed.md), with the SHA-256 of the kernel sources it was taken on:
+# once a source differs the figure no longer describes the kernel and is reported as null.
+TRAFFIC = {("mixed_solve", 1048576): {"k_compress": 2640.8e6, "k_schur": 1868.9e6}}
+TRAFFIC_SRC = {
+    "ifmm_factor.cu": "f7a7bc100fe13fb36acf5fda1a027c5d425fd425c71b7d222698652919b2a273",
+    "ifmm_common.cuh": "f7c96910ada3ff910b1b5cb6387b1bb1e9610e28d75e5ee46c6aa3c7b3da150d",
+    "ifmm_internal.h": "3f839e10601708fc2629c8d77922411acf52db74616146a7280989523c0537cc",
+}
+
+
+def _traffic(precision, n, name):
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1407_1572_gb300", "csrc")
+    for f, h in TRAFFIC_SRC.items():
+        with open(os.path.join(csrc, f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != h:
+                return None
+    return TRAFFIC.get((precision, n), {}).get(name)
+
+
+def _kernel_roofline(stats, precision, i, n=0):
     from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
     ms, launches, flops = stats["kernel_ms"], stats["kernel_launches"], stats["kernel_flops"]
     name = FACTOR_KERNELS[i]
@@ -226,16 +248,16 @@ def _kernel_roofline(stats, precision, i):
     return {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
             "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
             "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_source": src}
+            "traffic": _traffic(precision, n, name), "traffic_unit": "bytes per launch", "peak_source": src}
 
 
-def roofline(stats, precision, peaks, peak_kind):
+def roofline(stats, precision, peaks, peak_kind, n=0):
     """Dominant factor kernel (CUDA-event time); `schur` adds the Schur-update kernel, the dense
     contraction of the elimination, against the peak of its own arithmetic."""
     ms = stats["kernel_ms"]
     top = max(range(5), key=lambda i: ms[i])
-    out = _kernel_roofline(stats, precision, top)
-    out["schur"] = _kernel_roofline(stats, precision, 2)
+    out = _kernel_roofline(stats, precision, top, n)
+    out["schur"] = _kernel_roofline(stats, precision, 2, n)
     # the Schur step's algorithmic bytes, for the intensity against HBM
     nl = max(stats["kernel_launches"][2], 1)
     bytes_pl = stats["schur_bytes"] / nl
@@ -386,7 +408,7 @@ def run_gpu(args):
     value = world * N / (ms / 1000.0)
     launches_per_step = st["launches_factor"] + st["launches_solve"]
     peaks, peak_kind = load_peaks()
-    rf = roofline(st, precision, peaks, peak_kind)
+    rf = roofline(st, precision, peaks, peak_kind, N)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     b_host = np.ascontiguousarray(b.cpu().numpy())      # (nrhs, N) = column-major N x nrhs
