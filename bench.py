@@ -46,7 +46,7 @@ CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, ta
 PRECISION_DESC = {
     "fp64": "FP64",
     "mixed_solve": ("FP64 elimination, double-float (FP32-pair) solve phase on the FP32 pipe (replay + matvec in "
-                    "GMRES), FP64 restart residuals"),
+                    "GMRES), FP64 final residual and update"),
     "mixed": "FP32 elimination (FP64 pivots) + FP64 refinement",
 }
 

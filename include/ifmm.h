@@ -65,8 +65,9 @@ typedef enum {
     IFMM_MIXED_SOLVE = 2         /* FP64 elimination; the solve phase on the FP32 pipe in
                                     double-float arithmetic (pairs of FP32, ~48-bit significand):
                                     the replay of double-float copies of the factors and the FMM
-                                    matvec inside GMRES, with FP64 residuals at every restart and
-                                    FP64 updates                                                */
+                                    matvec inside GMRES; the residual that may end the solve
+                                    is an FP64 matvec (restarts that only seed the next cycle
+                                    take the double-float one), updates are FP64              */
 } ifmm_precision;
 
 typedef struct {

@@ -928,12 +928,16 @@ ifmm_status matvec_dfl_impl(ifmm_handle* h, const double* x, int64_t ldx, double
 // quantity |g_{j+1}| = ||M^{-1}(b - A~ x_j)|| estimates the error of x_j since M^{-1} ~ A~^{-1}.
 // With IFMM_MIXED_SOLVE the preconditioner is the double-float replay and the Arnoldi products use
 // the double-float matvec (both on the FP32 pipe), and a cycle ends once its estimate has fallen
-// by refine_inner (or after m steps): the restart recomputes b - A~ x with the FP64 matvec, so the
-// double-float rounding limits each cycle's reduction, not the final accuracy (iterative
-// refinement with a mixed-precision inner GMRES). In every mode only an estimate taken on a freshly
-// computed FP64 residual ends the solve: the recurrence's own estimate |g_{j+1}| drifts from the
-// true preconditioned residual on ill-conditioned systems (measured 30x optimistic on a clustered
-// cloud), so reaching refine_tol inside a cycle triggers a restart that checks it.
+// by refine_inner (or after m steps): the restart recomputes b - A~ x, so the double-float
+// rounding limits each cycle's reduction, not the final accuracy (iterative refinement with a
+// mixed-precision inner GMRES). In every mode only an estimate taken on a freshly computed FP64
+// residual ends the solve: the recurrence's own estimate |g_{j+1}| drifts from the true
+// preconditioned residual on ill-conditioned systems (measured 30x optimistic on a clustered
+// cloud), so reaching refine_tol inside a cycle triggers a restart that checks it in FP64. A restart
+// after a cycle that ended on refine_inner only seeds the next cycle; with IFMM_MIXED_SOLVE it
+// takes the residual with the double-float matvec (rounding 2^-48 relative, far below the 0.1-0.4
+// accuracy of the preconditioner it feeds), and should that residual already meet refine_tol the
+// next restart recomputes it in FP64 before the solve may end.
 
 template <typename T>
 ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int64_t ld) {
@@ -958,6 +962,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
     for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(x + c * ld, 0, sizeof(double) * N, h->st));
     int it = 0;
     bool first = true;
+    bool res64 = true;                        // the next restart residual in FP64
     double est = 1e300;
     auto fetch = [&](int cnt) -> ifmm_status {
         CK(cudaMemcpyAsync(hv.data(), dv, sizeof(double) * (size_t)cnt * nrhs, cudaMemcpyDeviceToHost, h->st));
@@ -965,11 +970,13 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         return IFMM_OK;
     };
     for (;;) {
-        // z = M^{-1} (b - A~ x)
+        // z = M^{-1} (b - A~ x); fresh64: the residual is exact (x = 0) or an FP64 product
+        const bool fresh64 = first || !inner32 || res64;
         if (first) {
             CKS(solve_once<T>(h, b, ld, V, N, nrhs));
         } else {
-            CKS(matvec_impl(h, x, ld, u, N, nrhs));
+            if (fresh64) CKS(matvec_impl(h, x, ld, u, N, nrhs));
+            else CKS(matvec_dfl_impl(h, x, ld, u, N, nrhs));
             CK(cudaMemsetAsync(dv, 0, sizeof(double) * 2 * nrhs, h->st));
             launch_residual(b, u, r, N, nrhs, ld, dv, h->st);
             CKS(solve_once<T>(h, r, N, V, N, nrhs));
@@ -987,7 +994,12 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
             est = std::max(est, xn[c] > 0.0 ? beta / xn[c] : 0.0);
         }
         first = false;
-        if (est <= tol || it >= h->prm.refine_maxit) break;
+        if (it >= h->prm.refine_maxit) break;
+        if (est <= tol) {
+            if (fresh64) break;
+            res64 = true;                     // confirm on an FP64 residual before ending
+            continue;
+        }
         const double est_cycle = est;
         CK(cudaMemcpyAsync(dv, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, h->st));
         launch_colscale(V, N, N, nrhs, dv, h->st);
@@ -1039,6 +1051,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
             launch_colscale(Vn, N, N, nrhs, dv, h->st);
             ++it;
             k = j + 1;
+            res64 = est <= tol;               // this cycle's restart may end the solve
             if (est <= tol || it >= h->prm.refine_maxit) break;
             if (inner32 && est <= inner_red * est_cycle) break;
         }

@@ -137,7 +137,7 @@ def test_exp_kernel_matches_oracle(ifmm):
 def test_refined_solution_meets_tolerance(ifmm, kernel, precision):
     """GMRES refinement preconditioned by the IFMM solve reaches the manufactured solution within
     max(eps, 1e-6) with the FP64 elimination on both kernels, with the solve phase in FP64
-    (precision 0) or in FP32 with FP64 restart residuals (precision 2). The FP32 elimination is checked on
+    (precision 0) or in double-float with the FP64 final residual (precision 2). The FP32 elimination is checked on
     the positive-definite exponential kernel only, to 1e-3: the refinement's Krylov recurrence is
     FP64 but the preconditioner is applied in FP32, so the error it can certify stops near
     u_fp32 times the pivot blocks' condition numbers (measured 1.5e-4 here); on 1/r + sqrt(N) I the
