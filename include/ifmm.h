@@ -178,7 +178,9 @@ ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* statu
 ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
                              const int64_t* ld, int workers, ifmm_status* status_out);
 
-/* As ifmm_solve with host buffers: copies b in and x out inside the call. */
+/* As ifmm_solve with host buffers: copies b in and x out inside the call (one copy per column, or
+ * one for the block when ld = N). Page-locked host buffers (cudaHostAlloc or pinned tensors) copy
+ * at the link's rate; pageable ones are staged by the driver, several times slower. */
 ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int nrhs, int64_t ld);
 
 /* y = A~ x with the FP64 FMM operators of the build: P2M, M2M, M2L, L2L, L2P and P2P

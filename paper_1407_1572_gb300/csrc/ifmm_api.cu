@@ -1356,14 +1356,19 @@ ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int 
     void *pb = nullptr, *px = nullptr;
     CKS(workspace(h, 80, sizeof(double) * (size_t)h->N * nrhs, &pb));
     CKS(workspace(h, 81, sizeof(double) * (size_t)h->N * nrhs, &px));
-    for (int j = 0; j < nrhs; ++j)
-        CK(cudaMemcpyAsync((double*)pb + (size_t)j * h->N, b_host + (size_t)j * ld, sizeof(double) * h->N,
-                           cudaMemcpyHostToDevice, h->st));
+    // one copy per column, or one for the whole block when the columns are contiguous (ld = N);
+    // from page-locked host memory the copies run at the link's rate, from pageable memory the
+    // driver stages them
+    const int ncopy = ld == h->N ? 1 : nrhs;
+    const size_t cbytes = sizeof(double) * h->N * (ld == h->N ? (size_t)nrhs : 1);
+    for (int j = 0; j < ncopy; ++j)
+        CK(cudaMemcpyAsync((double*)pb + (size_t)j * h->N, b_host + (size_t)j * ld, cbytes, cudaMemcpyHostToDevice,
+                           h->st));
     ifmm_status s = ifmm_solve(h, (double*)pb, (double*)px, nrhs, h->N);
     if (s != IFMM_OK && s != IFMM_ERR_NOCONV) return s;
-    for (int j = 0; j < nrhs; ++j)
-        CK(cudaMemcpyAsync(x_host + (size_t)j * ld, (double*)px + (size_t)j * h->N, sizeof(double) * h->N,
-                           cudaMemcpyDeviceToHost, h->st));
+    for (int j = 0; j < ncopy; ++j)
+        CK(cudaMemcpyAsync(x_host + (size_t)j * ld, (double*)px + (size_t)j * h->N, cbytes, cudaMemcpyDeviceToHost,
+                           h->st));
     CK(cudaStreamSynchronize(h->st));
     return s;
 }

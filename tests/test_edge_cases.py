@@ -1,6 +1,7 @@
-"""Edge cases of the CUDA path through the C ABI: leading dimensions larger than N, columns solved
-alone against a block of right-hand sides, the largest number of right-hand sides, tiny systems whose
-tree is mostly empty, and points on the upper edges of the root box (clamped into the last box)."""
+"""Edge cases of the CUDA path through the C ABI: leading dimensions larger than N (device and host
+buffers), columns solved alone against a block of right-hand sides, the largest number of
+right-hand sides, tiny systems whose tree is mostly empty, and points on the upper edges of the
+root box (clamped into the last box)."""
 import math
 
 import numpy as np
@@ -50,6 +51,16 @@ def test_leading_dimension_larger_than_n(ifmm):
     ifmm.ifmm_matvec(g.h, bp.data_ptr(), yp.data_ptr(), nrhs, n + pad)
     torch.cuda.synchronize()
     assert torch.equal(yp[:, :n], y_tight)
+    # host buffers: one copy per column when ld > N, one block copy when ld = N
+    bh = np.full((nrhs, n + pad), np.nan)
+    bh[:, :n] = b.T
+    xh = np.full_like(bh, 7.0)
+    ifmm.ifmm_solve_host(g.h, bh, xh, nrhs, n + pad)
+    assert np.array_equal(xh[:, :n], x_tight.cpu().numpy())
+    assert bool((xh[:, n:] == 7.0).all()), "the padding of the host x must not be written"
+    xt = np.zeros((nrhs, n))
+    ifmm.ifmm_solve_host(g.h, np.ascontiguousarray(b.T), xt, nrhs, n)
+    assert np.array_equal(xt, x_tight.cpu().numpy())
     g.close()
 
 
