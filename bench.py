@@ -245,10 +245,12 @@ def _kernel_roofline(stats, precision, i, n=0):
     else:
         peak, src = FP64_TFLOPS, "nominal FP64 rate of GB300"
     ach = flops_pl / t / 1e12
+    traffic = _traffic(precision, n, name)
     return {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
             "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
             "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _traffic(precision, n, name), "traffic_unit": "bytes per launch", "peak_source": src}
+            "traffic": traffic, "traffic_unit": "bytes per launch",
+            "achieved_dram_gbs": traffic / t / 1e9 if traffic else None, "peak_source": src}
 
 
 def roofline(stats, precision, peaks, peak_kind, n=0):
@@ -261,9 +263,15 @@ def roofline(stats, precision, peaks, peak_kind, n=0):
     # the Schur step's algorithmic bytes, for the intensity against HBM
     nl = max(stats["kernel_launches"][2], 1)
     bytes_pl = stats["schur_bytes"] / nl
-    out["schur"]["intensity_flop_per_byte"] = (stats["kernel_flops"][2] / nl) / max(bytes_pl, 1.0)
-    out["schur"]["hbm_peak_gbs"] = peaks["hbm_gbs"]
-    out["schur"]["hbm_peak_source"] = f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+    sc = out["schur"]
+    sc["intensity_flop_per_byte"] = (stats["kernel_flops"][2] / nl) / max(bytes_pl, 1.0)
+    sc["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    sc["hbm_peak_source"] = f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+    # attainable = min(arithmetic peak, intensity x HBM bandwidth); the Schur update's intensity
+    # puts its ridge far above the double-float and FP64 peaks, so the two agree
+    sc["attainable"] = min(sc["peak"], sc["intensity_flop_per_byte"] * peaks["hbm_gbs"] / 1000.0)
+    sc["frac_attainable"] = sc["achieved"] / sc["attainable"]
+    sc["algorithmic_gbs"] = bytes_pl / (sc["avg_launch_ms"] / 1000.0) / 1e9
     return out
 
 
@@ -338,6 +346,29 @@ def run_batched(precision: str):
                          "rank 16, eps 1e-6, refined to 1e-7")}
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s point set: every replica solves its own independent system."""
+    return base + rank
+
+
+def reduce_max_ms(ms: float, dist, device) -> float:
+    """The step time of the whole job: the maximum over ranks (all-reduce MAX, then a barrier so
+    that no rank starts the next phase early); `dist` None for one process."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_value(world: int, n: int, ms: float) -> float:
+    """Unknowns per second over all ranks: every rank factors and solves n unknowns per step."""
+    return world * n / (ms / 1000.0)
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -366,7 +397,7 @@ def run_gpu(args):
                                   tau_ref=w["tau_ref"], refine_tol=w["refine_tol"],
                                   refine_maxit=w["refine_maxit"] if prec != "mixed" else 30,
                                   refine_restart=w["refine_restart"], refine_inner=w["refine_inner"])
-        pts = inputs.uniform_points(w["seed"] + rank, N)
+        pts = inputs.uniform_points(replica_seed(w["seed"], rank), N)
         return ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm, stream)
 
     solver = make_solver(precision)
@@ -397,15 +428,10 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     st = ifmm.ifmm_get_stats(h)
     err = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
-    value = world * N / (ms / 1000.0)
+    value = whole_job_value(world, N, ms)
     launches_per_step = st["launches_factor"] + st["launches_solve"]
     peaks, peak_kind = load_peaks()
     rf = roofline(st, precision, peaks, peak_kind, N)
@@ -417,11 +443,13 @@ def run_gpu(args):
     b_host, x_host = b_pin.numpy(), x_pin.numpy()       # (nrhs, N) = column-major N x nrhs
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ifmm.ifmm_factor(h, allow_overflow=True)
         ifmm.ifmm_solve_host(h, b_host, x_host, nrhs, N, allow_noconv=True)
-    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
+    e2e_ms = reduce_max_ms(1000.0 * (time.perf_counter() - t0) / e2e_steps, dist, "cuda")
     e2e_err = float(np.max(np.linalg.norm(x_host - xs.cpu().numpy(), axis=1) / np.linalg.norm(xs.cpu().numpy(), axis=1)))
 
     extra = {}
@@ -478,12 +506,13 @@ def run_gpu(args):
                            "l2": "inputs larger than L2 (factor touches tens of GB per step)",
                            "err": err, "refine_iters": st["refine_iters"], "max_rank": st["max_rank"],
                            "t_factor_ms": st["t_factor_ms"], "t_solve_ms": st["t_solve_ms"],
+                           "solve_rhs_unknowns_per_s": N * nrhs / (st["t_solve_ms"] / 1000.0),
                            "kernel_ms": dict(zip(ifmm.FACTOR_KERNELS, st["kernel_ms"])),
                            "level_ms": {str(k): round(st["level_ms"][k], 2) for k in range(2, w["depth"] + 1)},
                            "factor_tflop": st["factor_flops"] / 1e12,
                            "device_gb": st["device_bytes"] / 1e9},
                 "roofline": rf, "cpu_baseline": cpu,
-                "e2e": {"value": world * N / (e2e_ms / 1000.0), "unit": "unknowns/s",
+                "e2e": {"value": whole_job_value(world, N, e2e_ms), "unit": "unknowns/s",
                         "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(x_host.nbytes),
                         "host_buffers": "pinned", "ms_per_step": e2e_ms, "err": e2e_err},
                 "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks}

@@ -1,0 +1,98 @@
+"""Host logic of bench.py without a GPU: the roofline arithmetic on given kernel statistics, the
+source check that retires a stale DRAM-traffic figure, and the multi-rank timing of the replicas
+mode (every rank solves its own system; the job's step time is the maximum over ranks) with two
+gloo ranks on the CPU."""
+import hashlib
+import math
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+PEAKS = {"hbm_gbs": 6785.9}
+
+
+def _stats():
+    # five factor kernels in the order k_pivot, k_panel, k_schur, k_compress, k_redirect
+    return {"kernel_ms": [100.0, 50.0, 180.0, 250.0, 40.0], "kernel_launches": [54, 54, 54, 54, 54],
+            "kernel_flops": [1e11, 2e11, 3.9e11, 1.6e11, 5e10], "schur_bytes": 1.0e11}
+
+
+def test_roofline_picks_the_dominant_kernel_and_divides_by_its_own_peak():
+    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", n=4096)
+    assert rf["kernel"] == "k_compress"
+    t = 250.0 / 54 / 1000.0
+    assert math.isclose(rf["achieved"], 1.6e11 / 54 / t / 1e12, rel_tol=1e-12)
+    assert rf["peak"] == bench.FP64_TFLOPS and math.isclose(rf["frac"], rf["achieved"] / rf["peak"])
+    sc = rf["schur"]
+    assert sc["kernel"] == "k_schur" and sc["peak"] == bench.DFL_TFLOPS
+    ai = 3.9e11 / 1.0e11
+    assert math.isclose(sc["intensity_flop_per_byte"], ai)
+    assert math.isclose(sc["attainable"], min(bench.DFL_TFLOPS, ai * PEAKS["hbm_gbs"] / 1000.0))
+    assert math.isclose(sc["frac_attainable"], sc["achieved"] / sc["attainable"])
+    assert math.isclose(sc["algorithmic_gbs"], 1.0e11 / 54 / (180.0 / 54 / 1000.0) / 1e9)
+    # no capture was taken at this size: no traffic
+    assert rf["traffic"] is None and rf["achieved_dram_gbs"] is None
+
+
+def test_roofline_in_fp64_uses_the_fp64_peak_everywhere():
+    rf = bench.roofline(_stats(), "fp64", PEAKS, "measured", n=4096)
+    assert rf["peak"] == bench.FP64_TFLOPS and rf["schur"]["peak"] == bench.FP64_TFLOPS
+    # the Schur update's ridge lies above the FP64 peak, so the attainable roofline is that peak
+    assert rf["schur"]["attainable"] == bench.FP64_TFLOPS
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    csrc = os.path.join(ROOT, "paper_1407_1572_gb300", "csrc")
+    now = {f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() for f in bench.TRAFFIC_SRC}
+    monkeypatch.setattr(bench, "TRAFFIC_SRC", now)
+    key = next(iter(bench.TRAFFIC))
+    name = next(iter(bench.TRAFFIC[key]))
+    assert bench._traffic(key[0], key[1], name) == bench.TRAFFIC[key][name]
+    assert bench._traffic(key[0], key[1] // 4, name) is None            # another size
+    stale = dict(now)
+    stale[next(iter(stale))] = "0" * 64
+    monkeypatch.setattr(bench, "TRAFFIC_SRC", stale)
+    assert bench._traffic(key[0], key[1], name) is None                 # the kernel changed
+
+
+def test_replica_seeds_differ_per_rank_and_the_value_counts_every_rank():
+    assert len({bench.replica_seed(1411, r) for r in range(8)}) == 8
+    assert math.isclose(bench.whole_job_value(4, 1 << 20, 2000.0), 4 * (1 << 20) / 2.0)
+    assert bench.reduce_max_ms(12.5, None, "cpu") == 12.5
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        ms = bench.reduce_max_ms(10.0 + 5.0 * rank, dist, "cpu")
+        q.put((rank, ms, bench.whole_job_value(world, 4096, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_the_slowest_step_time():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [15.0, 15.0]
+    assert all(math.isclose(o[2], 2 * 4096 / 0.015) for o in out)
