@@ -1598,4 +1598,12 @@ int oracle_kernel_eval(const oracle_params* prm, const double* a, const double* 
     return 0;
 }
 
+int oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
+                         double* out) {
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            out[i * n + j] = kernel_value(*prm, P[2 * i], P[2 * i + 1], Q[2 * j], Q[2 * j + 1]);
+    return 0;
+}
+
 }  // extern "C"

@@ -68,6 +68,9 @@ int   oracle_stats(void* h, double* out, int nout);
 void  oracle_cheb_nodes(int p, double* t);
 void  oracle_lagrange(int p, double t, double* out);
 int   oracle_kernel_eval(const oracle_params* prm, const double* a, const double* b, double* out);
+/* out[i * n + j] = K(P_i, Q_j) for m points P and n points Q (row-major x, y pairs), no diagonal */
+int   oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
+                           double* out);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,7 @@ def _load():
             lib.oracle_cheb_nodes.argtypes = [ctypes.c_int, dp]
             lib.oracle_lagrange.argtypes = [ctypes.c_int, ctypes.c_double, dp]
             lib.oracle_kernel_eval.argtypes = [ctypes.POINTER(Params), dp, dp, dp]
+            lib.oracle_kernel_matrix.argtypes = [ctypes.POINTER(Params), dp, i64, dp, i64, dp]
             _lib = lib
     return _lib
 
@@ -113,6 +114,15 @@ def kernel_eval(params: Params, a, b) -> float:
     out = np.zeros(1)
     _load().oracle_kernel_eval(ctypes.byref(params), _ptr(a), _ptr(b), _ptr(out))
     return float(out[0])
+
+
+def kernel_matrix(params: Params, P, Q) -> np.ndarray:
+    """K(P_i, Q_j) for point sets P (m x 2) and Q (n x 2): the kernel alone, no diagonal term."""
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, 2)
+    Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros((P.shape[0], Q.shape[0]))
+    _load().oracle_kernel_matrix(ctypes.byref(params), _ptr(P), P.shape[0], _ptr(Q), Q.shape[0], _ptr(out))
+    return out
 
 
 def dense_lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
