@@ -41,6 +41,8 @@ WORKLOAD = dict(N=1 << 20, depth=7, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_
 # bounded CPU sample of the same workload family for the oracle (same points per leaf, settings)
 CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
                   refine_maxit=40, refine_restart=0)
+# the same on one thread, smaller (about 10 s)
+CPU_SAMPLE_1T = dict(CPU_SAMPLE, N=1 << 14, depth=4)
 
 
 PRECISION_DESC = {
@@ -121,8 +123,29 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # CPU oracle (the reference arm and the cpu_baseline of the GPU arm)
 # ------------------------------------------------------------------------------------------------
-def oracle_step(w, threads=0):
-    """One oracle factor + refined solve on the bounded sample; returns (seconds, error)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_step(w, threads=0, parts=None):
+    """One oracle factor + refined solve on the bounded sample; returns (seconds, error). `parts`
+    (a dict), if given, receives the build, factor and solve (with refinement) seconds."""
     import numpy as np
 
     from oracle import oracle as O
@@ -131,11 +154,14 @@ def oracle_step(w, threads=0):
     pts = inputs.uniform_points(w["seed"], N)
     prm = O.make_params(w["depth"], w["cheb_p"], O.K_INV_R, eps=w["eps"], diag=math.sqrt(N), tau_ref=w["tau_ref"],
                         threads=threads)
+    tb = time.perf_counter()
     o = O.Oracle(pts, prm)
+    tb = time.perf_counter() - tb
     xs = inputs.rhs(w["seed"] + 1, N, w["nrhs"])
     b = o.matvec(xs)
     t0 = time.perf_counter()
     o.factor()
+    tf = time.perf_counter() - t0
     x = o.solve(b)
     for _ in range(w["refine_maxit"]):
         r = b - o.matvec(x)
@@ -145,7 +171,25 @@ def oracle_step(w, threads=0):
             break
     dt = time.perf_counter() - t0
     err = float(np.max(np.linalg.norm(x - xs, axis=0) / np.linalg.norm(xs, axis=0)))
+    if parts is not None:
+        parts.update(t_build_s=tb, t_factor_s=tf, t_solve_s=dt - tf)
     return dt, err
+
+
+def cpu_baseline_entry():
+    """The oracle timed on this host: all cores on CPU_SAMPLE, one thread on CPU_SAMPLE_1T."""
+    parts = {}
+    dt, err = oracle_step(CPU_SAMPLE, parts=parts)
+    dt1, err1 = oracle_step(CPU_SAMPLE_1T, threads=1)
+    w, w1 = CPU_SAMPLE, CPU_SAMPLE_1T
+    return {"value": w["N"] / dt, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"oracle factor + refined {w['nrhs']}-RHS solve on N={w['N']} (depth {w['depth']}, same "
+                      f"settings per leaf), {dt:.1f} s, err {err:.1e}",
+            **{k: round(v, 3) for k, v in parts.items()},
+            "single_thread": {"value": w1["N"] / dt1, "unit": "unknowns/s", "cores": 1,
+                              "sample": f"the same on N={w1['N']} (depth {w1['depth']}), one thread, {dt1:.1f} s, "
+                                        f"err {err1:.1e}"}}
 
 
 def run_reference(args):
@@ -170,7 +214,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(w, "FP64 CPU oracle"), "N": w["N"], "depth": w["depth"],
                        "nrhs": w["nrhs"], "eps": w["eps"], "err": max(errs)},
-            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -490,10 +535,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, cerr = oracle_step(CPU_SAMPLE)
-        cpu = {"value": CPU_SAMPLE["N"] / dt, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
-               "sample": f"oracle factor + refined {CPU_SAMPLE['nrhs']}-RHS solve on N={CPU_SAMPLE['N']} "
-                         f"(depth {CPU_SAMPLE['depth']}, same settings per leaf), {dt:.1f} s, err {cerr:.1e}"}
+        cpu = cpu_baseline_entry()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,

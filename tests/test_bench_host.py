@@ -96,3 +96,12 @@ def test_two_gloo_ranks_agree_on_the_slowest_step_time():
         assert p.exitcode == 0
     assert [o[1] for o in out] == [15.0, 15.0]
     assert all(math.isclose(o[2], 2 * 4096 / 0.015) for o in out)
+
+
+def test_oracle_step_reports_its_phases_and_the_host_cpu():
+    w = dict(bench.CPU_SAMPLE, N=1024, depth=2, nrhs=2)
+    parts = {}
+    dt, err = bench.oracle_step(w, threads=1, parts=parts)
+    assert err < 1e-6 and set(parts) == {"t_build_s", "t_factor_s", "t_solve_s"}
+    assert math.isclose(parts["t_factor_s"] + parts["t_solve_s"], dt, rel_tol=1e-9)
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
