@@ -259,7 +259,7 @@ ARITH = {
 # once a source differs the figure no longer describes the kernel and is reported as null.
 TRAFFIC = {("mixed_solve", 1048576): {"k_compress": 2640.8e6, "k_schur": 1868.9e6}}
 TRAFFIC_SRC = {
-    "ifmm_factor.cu": "f7a7bc100fe13fb36acf5fda1a027c5d425fd425c71b7d222698652919b2a273",
+    "ifmm_factor.cu": "89d58850fd32c25981a5c606db9909aabd8e4be699c8293b9d659b075db0c302",
     "ifmm_common.cuh": "f7c96910ada3ff910b1b5cb6387b1bb1e9610e28d75e5ee46c6aa3c7b3da150d",
     "ifmm_internal.h": "3f839e10601708fc2629c8d77922411acf52db74616146a7280989523c0537cc",
 }

@@ -752,8 +752,8 @@ ifmm_status factor_impl(ifmm_handle* h) {
     launch_root_gather<T>(v2, L2.d_yoff, h->d_Dinv, (int)M, h->st);
     int* d_perm = nullptr;
     double* d_col = nullptr;
-    CKS(dalloc(h, &d_perm, sizeof(int) * (size_t)std::max<int64_t>(M, 1)));
-    CKS(dalloc(h, &d_col, sizeof(double) * (size_t)std::max<int64_t>(M, 1)));
+    CKS(dalloc(h, &d_perm, sizeof(int) * (size_t)(M + 1)));
+    CKS(dalloc(h, &d_col, sizeof(double) * (size_t)(M + 1)));
     launch_dense_invert(h->d_Dinv, (int)M, d_perm, d_col, h->d_status, h->st);
     int hs = 0;
     double cnt[8];

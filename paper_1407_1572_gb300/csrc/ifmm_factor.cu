@@ -1082,10 +1082,97 @@ __global__ void __launch_bounds__(1024) k_dense_invert(double* D, int M, int* pe
     if (!ok && threadIdx.x == 0) atomicOr(status, DEV_ERR_SINGULAR);
 }
 
+// The same Gauss-Jordan elimination spread over the GPU for large M, two launches per column: the
+// pivot step (one block: partial pivoting with ties to the lowest row, row interchange, scaling of
+// the pivot row, copy of the pivot column) and the update of every other row (one block per row
+// and 256 columns). Every element sees the operations of cta_gauss_jordan in the same order.
+// perm[M] is the failure flag (set on a zero or non-finite pivot; later launches then return),
+// col[M] keeps 1 / pivot for the update.
+__global__ void __launch_bounds__(1024) k_gj_pivot(double* A, int M, int k, int* perm, double* col, int* status) {
+    __shared__ double vred[32];
+    __shared__ int ired[32];
+    __shared__ int s_ok;
+    __shared__ double s_piv;
+    if (perm[M]) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double best = -1.0;
+    int bi = -1;
+    for (int i = k + tid; i < M; i += nt) {
+        const double v = fabs(A[(size_t)i * M + k]);
+        if (bi < 0 || v > best) { best = v; bi = i; }
+    }
+    double bv;
+    const int p = block_argmax(best, bi, vred, ired, &bv);
+    if (tid == 0) {
+        perm[k] = p;
+        s_ok = (p >= 0 && bv > 0.0 && isfinite(bv)) ? 1 : 0;
+        if (!s_ok) {
+            perm[M] = 1;
+            atomicOr(status, DEV_ERR_SINGULAR);
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    if (p != k)
+        for (int j = tid; j < M; j += nt) {
+            const double t = A[(size_t)k * M + j];
+            A[(size_t)k * M + j] = A[(size_t)p * M + j];
+            A[(size_t)p * M + j] = t;
+        }
+    __syncthreads();
+    if (tid == 0) s_piv = A[(size_t)k * M + k];
+    __syncthreads();
+    const double d = 1.0 / s_piv;
+    for (int j = tid; j < M; j += nt) {
+        if (j == k) A[(size_t)k * M + k] = d;
+        else A[(size_t)k * M + j] *= d;
+    }
+    for (int i = tid; i < M; i += nt) col[i] = i == k ? d : A[(size_t)i * M + k];
+    if (tid == 0) col[M] = d;
+}
+
+__global__ void __launch_bounds__(256) k_gj_update(double* A, int M, int k, const int* perm, const double* col) {
+    if (perm[M]) return;
+    const int i = blockIdx.y, j = blockIdx.x * 256 + threadIdx.x;
+    if (i == k || j >= M) return;
+    const double c = col[i];
+    if (j == k) A[(size_t)i * M + k] = -c * col[M];
+    else A[(size_t)i * M + j] -= c * A[(size_t)k * M + j];
+}
+
+// undo the row interchanges as column interchanges, last first: row-local, one thread per row
+__global__ void __launch_bounds__(256) k_gj_unswap(double* A, int M, const int* perm) {
+    if (perm[M]) return;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= M) return;
+    double* row = A + (size_t)i * M;
+    for (int k = M - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k) {
+            const double t = row[k];
+            row[k] = row[p];
+            row[p] = t;
+        }
+    }
+}
+
+// perm: M + 1 ints, col: M + 1 doubles of scratch
 void launch_dense_invert(double* D, int M, int* perm, double* col, int* status, cudaStream_t st) {
     if (M <= 0) return;
-    k_dense_invert<<<1, 1024, 0, st>>>(D, M, perm, col, status);
-    count_launches(1);
+    if (M < 256 || M > 65535) {   // one block: fewer launches than the per-column steps cost (or
+                                   // more rows than a grid dimension holds)
+        k_dense_invert<<<1, 1024, 0, st>>>(D, M, perm, col, status);
+        count_launches(1);
+        return;
+    }
+    cudaMemsetAsync(perm + M, 0, sizeof(int), st);
+    const dim3 ug((M + 255) / 256, M);
+    for (int k = 0; k < M; ++k) {
+        k_gj_pivot<<<1, 1024, 0, st>>>(D, M, k, perm, col, status);
+        k_gj_update<<<ug, 256, 0, st>>>(D, M, k, perm, col);
+    }
+    k_gj_unswap<<<(M + 255) / 256, 256, 0, st>>>(D, M, perm);
+    count_launches(2 * M + 1);
 }
 
 template <typename T>
