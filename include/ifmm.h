@@ -74,11 +74,14 @@ typedef struct {
     int dim;              /* space dimension; must be 2 (quadtree)                               */
     int depth;            /* leaf level kappa of the uniform tree, 2 <= depth <= 10; 0 = automatic
                              (see leaf_max)                                                       */
-    int cheb_p;           /* Chebyshev nodes per dimension (Section 5); initial box rank p^2      */
-    int r_cap;            /* largest rank any box basis may reach; <= 0: only the box size n_i   */
-    double eps;           /* compression tolerance of the fill-in (Section 5)                     */
-    double diag;          /* diagonal A_ii (the paper's Eq. "main_Solving_Equation" uses 1)       */
-    double kparam[4];     /* kernel parameters (IFMM_K_EXP: kparam[0] = length scale > 0)        */
+    int cheb_p;           /* Chebyshev nodes per dimension (Section 5), 1..8; initial box rank p^2 */
+    int r_cap;            /* largest rank any box basis may reach (if > 0, at least cheb_p^2);
+                             <= 0: only the box size n_i                                          */
+    double eps;           /* compression tolerance of the fill-in (Section 5), >= 0              */
+    double diag;          /* diagonal A_ii, finite (the paper's Eq. "main_Solving_Equation" uses 1) */
+    double kparam[4];     /* kernel parameters: kparam[0] > 0 for every kernel but IFMM_K_INV_R
+                             (the length scale l of IFMM_K_EXP / IFMM_K_DEXP_DELL, the a of the
+                             benchmark kernels)                                                   */
     double box[3];        /* root box x0, y0, side; side <= 0 selects the unit square [0,1]^2    */
     int precision;        /* ifmm_precision                                                       */
     int tau_ref;          /* compression threshold reference: 0 = the fill's own largest column
@@ -90,11 +93,12 @@ typedef struct {
                              max_j ||M^{-1}(b_j - A~ x_j)|| / ||x_j|| (an estimate of the relative error,
                              M^{-1} = the IFMM solve) is <= refine_tol; 0 disables refinement         */
     int refine_maxit;     /* limit on preconditioned matvecs (IFMM_ERR_NOCONV past it)            */
-    int refine_restart;   /* > 0: GMRES(refine_restart) left-preconditioned by the IFMM solve;
+    int refine_restart;   /* 1..200: GMRES(refine_restart) left-preconditioned by the IFMM solve;
                              0: classical refinement x += M^{-1}(b - A~ x)                          */
     double refine_inner;  /* IFMM_MIXED_SOLVE: a GMRES cycle (double-float products) ends once its error
-                             estimate has fallen by this factor, then the FP64 residual is formed
-                             again; <= 0 selects 1e-4                                             */
+                             estimate has fallen by this factor, and the next cycle starts from a
+                             recomputed residual (double-float; FP64 once the estimate has reached
+                             refine_tol, and only an FP64 one ends the solve); <= 0 selects 1e-4    */
     int leaf_max;         /* depth = 0: the build takes the smallest depth whose fullest leaf holds
                              at most leaf_max points (ifmm_auto_depth)                           */
 } ifmm_params;
@@ -137,7 +141,8 @@ int ifmm_auto_depth(const double* pts_host, int64_t N, const double* box, int le
  * kernel:   ifmm_kernel. p: parameters (copied). stream: cudaStream_t or NULL.
  * out:      receives the handle (NULL on failure).
  * Tree and lists: Section 4.2, Table "table_cluster"; operators: Table "table_FMM_operators";
- * Chebyshev interpolation: Section 5. Errors: INVALID_ARG, CUDA, OOM. */
+ * Chebyshev interpolation: Section 5. Errors: INVALID_ARG (N outside 1..2^31-1, a non-finite
+ * coordinate or a point outside the root box, a parameter outside the ranges above), CUDA, OOM. */
 ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm_params* p,
                        void* stream, ifmm_h* out);
 
@@ -149,9 +154,10 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
 ifmm_status ifmm_factor(ifmm_h h);
 
 /* x = A~^{-1} b by forward replay of the eliminations, the level-1 solve and back substitution
- * (Algorithm 2); when refine_tol > 0 that solve is the preconditioner M^{-1} of an FP64 iterative
- * refinement (GMRES or classical) whose residuals use ifmm_matvec (solve time t_s). b_dev, x_dev: device FP64, column-major, leading dimension ld >= N;
- * 1 <= nrhs <= 1024; b and x must not overlap. Errors: STATE (not factored), INVALID_ARG,
+ * (Algorithm 2); when refine_tol > 0 that solve is the preconditioner M^{-1} of an iterative
+ * refinement (GMRES or classical) on A~ x = b whose residuals use the FMM matvec (solve time t_s).
+ * b_dev, x_dev: device FP64, column-major, leading dimension ld >= N; 1 <= nrhs <= 1024; b and x
+ * must not overlap; rows N..ld-1 of x are not written. Errors: STATE (not factored), INVALID_ARG,
  * NOCONV (x still holds the last iterate), CUDA, OOM. */
 ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, int64_t ld);
 
@@ -208,7 +214,7 @@ ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, in
  * array out_host (4^level ints). Errors: STATE (not factored), INVALID_ARG. */
 ifmm_status ifmm_get_ranks(ifmm_h h, int level, int* out_host);
 
-/* Counters and timings of the handle. */
+/* Counters and timings of the handle into *s. Errors: INVALID_ARG (NULL argument). */
 ifmm_status ifmm_get_stats(ifmm_h h, ifmm_stats* s);
 
 /* One-line description of the last failure on this handle ("" if none). The string is owned
