@@ -3,6 +3,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_1407_1572_gb300 import ifmm
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -42,3 +44,24 @@ def test_default_params_and_struct_layout():
     assert lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), 4, 0, ctypes.byref(ok), None, ctypes.byref(h)) == 1
     assert lib.ifmm_factor(None) == 1
     assert lib.ifmm_solve(None, None, None, 1, 1) == 1
+
+
+@pytest.mark.parametrize("change,kernel,n", [
+    (dict(depth=11), 0, 4), (dict(cheb_p=0), 0, 4), (dict(cheb_p=9), 0, 4),
+    (dict(depth=0, leaf_max=0), 0, 4), (dict(), 6, 4), (dict(), -1, 4),
+    (dict(kparam=(0.0,)), 1, 4), (dict(kparam=(-1.0,)), 3, 4), (dict(kparam=(0.0,)), 5, 4),
+    (dict(eps=-1e-6), 0, 4), (dict(diag=float("inf")), 0, 4), (dict(precision=3), 0, 4),
+    (dict(tau_ref=3), 0, 4), (dict(r_cap=8), 0, 4), (dict(refine_restart=201), 0, 4),
+    (dict(refine_restart=-1), 0, 4), (dict(), 0, 0),
+])
+def test_build_rejects_each_out_of_range_argument_on_the_host(change, kernel, n):
+    """Every range ifmm.h states for ifmm_build is checked before any device call: the call returns
+    IFMM_ERR_INVALID_ARG and leaves the output handle NULL."""
+    import numpy as np
+    lib = ifmm.load()
+    pts = np.full((max(n, 1), 2), 0.5)
+    prm = ifmm.default_params(**change)
+    h = ctypes.c_void_p(1)
+    st = lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), n, kernel, ctypes.byref(prm), None, ctypes.byref(h))
+    assert st == ifmm.IFMM_ERR_INVALID_ARG
+    assert not h.value
