@@ -21,6 +21,20 @@
  *     box bases (Table "table_IFMM_operators");
  *   - dense solve at level 1, then Algorithm 2 (back substitution / downward pass).
  *
+ * Kernels (kernel_value): 1/r; exp(-r/l) and its derivative in l, (r/l^2) exp(-r/l); the
+ * polynomial (1 + x1 y1)(1 + x2 y2), which Chebyshev interpolation of order >= 2 reproduces exactly
+ * (a pin); the three regularised kernels of the numerical benchmarks (Section 5), K(0) = 0.
+ *
+ * Pins, i.e. checks against something other than this file (tests/test_oracle_pins.py,
+ * tests/test_paper_ranks.py): Chebyshev nodes = roots of T_p, Lagrange cardinality and polynomial
+ * exactness; interaction lists against brute force; kernels against closed forms; the nested
+ * operators against the per-level textbook interpolation formula; the matvec against the dense
+ * A~; the dense extended system and the eps = 0 elimination against A~^{-1} b (the paper's
+ * exactness of the extended sparse representation); the compressed solve's error against eps;
+ * both elimination orders within the eps bound; the paper's rank table (Table
+ * "table_numerical_ranks_2D") in order of magnitude and trend. Rank decisions at the exact
+ * threshold boundary with the fill-relative reference (R5, tau_ref = 0) are parity unpinned.
+ *
  * Readings where the paper is silent (each is stated again where it is used):
  *   R1 elimination order inside a level: colour-major, colour = (ix mod 3) + 3 (iy mod 3),
  *      Morton order inside a colour (order = 0); or plain Morton order (order = 1).
