@@ -324,13 +324,35 @@ BATCH = dict(count=256, seed=1409, nmin=2048, nmax=32768, rhs_min=1, rhs_max=16,
              refine_tol=1e-7, wave=64, workers=48)
 
 
-def run_batched(precision: str):
+def partition_work(work, world: int):
+    """Independent systems over `world` ranks: largest work first, each to the rank with the least
+    work so far (ties to the lower rank, then the lower index). Returns each rank's indices, sorted."""
+    parts = [[] for _ in range(world)]
+    load = [0.0] * world
+    for i in sorted(range(len(work)), key=lambda i: (-work[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        parts[r].append(i)
+        load[r] += work[i]
+    return [sorted(p) for p in parts]
+
+
+def aggregate_batched(tf: float, ts: float, err: float, dmin: int, dmax: int, dist, device):
+    """A rank's batched results combined over ranks: the job's time is the slowest rank's factor +
+    solve time; error and depth range over all systems. Returns (t_total, tf, ts, err, dmin, dmax)."""
+    t = reduce_max(tf + ts, dist, device)
+    return (t, reduce_max(tf, dist, device), reduce_max(ts, dist, device), reduce_max(err, dist, device),
+            -reduce_max(-dmin, dist, device), reduce_max(dmax, dist, device))
+
+
+def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
     """The batched workload (independent uneven systems): 256 systems, N log-uniform in [2048, 32768],
     half uniform clouds and half Gaussian blobs (8 centres, sigma 0.05), automatic depth (fullest
     leaf <= 64 points, empty leaves kept), 1-16 right-hand sides each, 1/r + sqrt(N) I, rank 16,
     eps 1e-6, refined to 1e-7. Systems are built, factored (ifmm_factor_batch) and solved
     (ifmm_solve_batch) in waves of 64, half uniform and half blobs per wave, each system on its own
-    stream; one untimed warm-up wave of 16 first. Timed: the batched factor + solve calls."""
+    stream; one untimed warm-up wave of 16 first. Timed: the batched factor + solve calls. Over
+    several ranks every rank runs its share (partition_work on N x nrhs) and the job's time is the
+    slowest rank's (strong scaling: the 256 systems are fixed)."""
     import torch
 
     from paper_1407_1572_gb300 import ifmm, inputs
@@ -338,6 +360,10 @@ def run_batched(precision: str):
     c = BATCH
     systems = inputs.batch_systems(seed=c["seed"], count=c["count"], nmin=c["nmin"], nmax=c["nmax"],
                                    rhs_min=c["rhs_min"], rhs_max=c["rhs_max"])
+    half = c["count"] // 2
+    mine = partition_work([s["points"].shape[0] * s["nrhs"] for s in systems], world)[rank]
+    uni = [systems[i] for i in mine if i < half]
+    blob = [systems[i] for i in mine if i >= half]
 
     def wave(sy):
         handles, xs_l, bs_l, xo_l = [], [], [], []
@@ -369,22 +395,26 @@ def run_batched(precision: str):
             g.close()
         return t2 - t1, t3 - t2, err, depths
 
-    half = c["count"] // 2
-    wave(systems[:8] + systems[half:half + 8])
+    if uni or blob:
+        wave(uni[:8] + blob[:8])
+    if dist:
+        dist.barrier()
     tf = ts = err = 0.0
     depths = []
     per = c["wave"] // 2
-    for w in range(half // per):
-        f_, s_, e_, d_ = wave(systems[w * per:(w + 1) * per] + systems[half + w * per:half + (w + 1) * per])
+    for w in range(max(-(-len(uni) // per), -(-len(blob) // per))):
+        f_, s_, e_, d_ = wave(uni[w * per:(w + 1) * per] + blob[w * per:(w + 1) * per])
         tf += f_
         ts += s_
         err = max(err, e_)
         depths += d_
+    t, tf, ts, err, dmin, dmax = aggregate_batched(tf, ts, err, min(depths, default=99), max(depths, default=0),
+                                                   dist, "cuda")
     n_tot = sum(s["points"].shape[0] for s in systems)
     unk = sum(s["points"].shape[0] * s["nrhs"] for s in systems)
-    return {"value": n_tot / (tf + ts), "unit": "unknowns/s", "systems": c["count"], "N_total": n_tot,
-            "rhs_columns_x_N": unk, "t_factor_s": tf, "t_solve_s": ts, "err": err, "meets_err_1e-6": err <= 1e-6,
-            "depth_range": [min(depths), max(depths)], "precision": PRECISION_DESC[precision],
+    return {"value": n_tot / t, "unit": "unknowns/s", "systems": c["count"], "N_total": n_tot, "ranks": world,
+            "scaling": "strong", "rhs_columns_x_N": unk, "t_factor_s": tf, "t_solve_s": ts, "err": err,
+            "meets_err_1e-6": err <= 1e-6, "depth_range": [int(dmin), int(dmax)], "precision": PRECISION_DESC[precision],
             "workers": c["workers"], "timing": "host clock around the blocking batched calls (device synchronised)",
             "workload": ("256 systems, N log-uniform in [2048, 32768], half uniform / half Gaussian blobs "
                          "(8 centres, sigma 0.05), automatic depth (leaf <= 64), 1-16 RHS, 1/r + sqrt(N) I, "
@@ -396,17 +426,22 @@ def replica_seed(base: int, rank: int) -> int:
     return base + rank
 
 
-def reduce_max_ms(ms: float, dist, device) -> float:
-    """The step time of the whole job: the maximum over ranks (all-reduce MAX, then a barrier so
-    that no rank starts the next phase early); `dist` None for one process."""
+def reduce_max(v: float, dist, device) -> float:
+    """The maximum of v over ranks (all-reduce MAX, then a barrier so that no rank starts the next
+    phase early); `dist` None for one process."""
     if dist is None:
-        return ms
+        return v
     import torch
 
-    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    t = torch.tensor([v], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.barrier()
     return float(t.item())
+
+
+def reduce_max_ms(ms: float, dist, device) -> float:
+    """The step time of the whole job: the maximum over ranks."""
+    return reduce_max(ms, dist, device)
 
 
 def whole_job_value(world: int, n: int, ms: float) -> float:
@@ -527,11 +562,11 @@ def run_gpu(args):
             so.close()
         solver = None
 
-    if args.batch and rank == 0:
+    if args.batch:   # every rank runs its share of the independent systems
         if solver is not None:
             solver.close()
             solver = None
-        extra["batched_gpu"] = run_batched(precision)
+        extra["batched_gpu"] = run_batched(precision, rank, world, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

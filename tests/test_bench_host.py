@@ -105,3 +105,49 @@ def test_oracle_step_reports_its_phases_and_the_host_cpu():
     assert err < 1e-6 and set(parts) == {"t_build_s", "t_factor_s", "t_solve_s"}
     assert math.isclose(parts["t_factor_s"] + parts["t_solve_s"], dt, rel_tol=1e-9)
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+
+
+def test_partition_of_independent_systems_is_complete_and_balanced():
+    import random
+    rng = random.Random(5)
+    work = [rng.randint(2048, 32768) * rng.randint(1, 16) for _ in range(256)]
+    assert bench.partition_work(work, 1) == [list(range(256))]     # one rank: every system, in order
+    for world in (2, 3, 4, 8):
+        parts = bench.partition_work(work, world)
+        assert sorted(i for p in parts for i in p) == list(range(256))
+        loads = [sum(work[i] for i in p) for p in parts]
+        # largest-first greedy: no rank exceeds the least loaded by more than the largest system
+        assert max(loads) - min(loads) <= max(work)
+        assert bench.partition_work(work, world) == parts            # deterministic
+
+
+def _batched_rank(rank, world, port, q):
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        # rank 0: fast, shallow trees; rank 1: slow, a larger error and deeper trees
+        res = bench.aggregate_batched(1.0 + rank, 0.5 + 2 * rank, 1e-8 * (1 + 9 * rank), 3 + rank, 5 + 2 * rank,
+                                      dist, "cpu")
+        q.put((rank, res))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batched_results_combine_over_two_gloo_ranks():
+    assert bench.aggregate_batched(1.0, 2.0, 1e-8, 3, 7, None, "cpu") == (3.0, 1.0, 2.0, 1e-8, 3, 7)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_batched_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, (t, tf, ts, err, dmin, dmax) in out:
+        assert (t, tf, ts, dmin, dmax) == (4.5, 2.0, 2.5, 3.0, 7.0)   # slowest rank: 2.0 + 2.5
+        assert math.isclose(err, 1e-7)
