@@ -65,3 +65,20 @@ def test_build_rejects_each_out_of_range_argument_on_the_host(change, kernel, n)
     st = lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), n, kernel, ctypes.byref(prm), None, ctypes.byref(h))
     assert st == ifmm.IFMM_ERR_INVALID_ARG
     assert not h.value
+
+
+def test_no_cpu_fallback_without_a_device():
+    """With valid arguments and no CUDA device the library fails with IFMM_ERR_CUDA and a message;
+    nothing on the product path computes on the host instead."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+    lib = ifmm.load()
+    pts = np.random.default_rng(0).random((256, 2))
+    prm = ifmm.default_params(depth=2)
+    h = ctypes.c_void_p(1)
+    st = lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), 256, 0, ctypes.byref(prm), None, ctypes.byref(h))
+    assert st == ifmm.IFMM_ERR_CUDA and not h.value
+    with pytest.raises(RuntimeError):   # the wrapper fails before the build (no CUDA stream)
+        ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm)
