@@ -265,6 +265,30 @@ def test_uncompressed_elimination_is_exact(oracle_mod, depth, p, order):
     assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) < 1e-10
 
 
+@pytest.mark.parametrize("kernel", ["log_reg", "inv_reg", "r2log_reg"])
+def test_uncompressed_elimination_is_exact_for_the_benchmark_kernels(oracle_mod, kernel):
+    """The same exactness for the paper's benchmark kernels (Section 5: a = 0.001, unit diagonal,
+    points in [-1, 1]^2): the eps = 0 solve is backward stable on A~ (normwise backward error at
+    roundoff) and, where A~ is well conditioned (log: kappa 1e3, a / r: 4e1), equals the dense
+    solution to 1e-12; r^2 ln r (kappa 2e8) is held to the backward error alone."""
+    O = oracle_mod
+    kid = {"log_reg": O.K_LOG_REG, "inv_reg": O.K_INV_REG, "r2log_reg": O.K_R2LOG_REG}[kernel]
+    N = 1024
+    pts = inputs.uniform_points(71, N, lo=-1.0, side=2.0)
+    o = O.Oracle(pts, O.make_params(3, 3, kid, eps=0.0, diag=1.0, kparam=(1e-3, 0, 0, 0), box=(-1.0, -1.0, 2.0)))
+    A = o.dense_tilde()
+    x = inputs.rhs(9, N, 2)
+    b = A @ x
+    o.factor()
+    xs = o.solve(b)
+    an = np.linalg.norm(A, 1)
+    eta = float((np.abs(A @ xs - b).sum(0) / (an * np.abs(xs).sum(0) + np.abs(b).sum(0))).max())
+    assert eta < 1e-14
+    if kernel != "r2log_reg":
+        xd = np.linalg.solve(A, b)
+        assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) < 1e-12
+
+
 def test_compressed_error_tracks_eps(oracle_mod):
     N = 2048
     errs = []
