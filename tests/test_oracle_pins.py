@@ -118,6 +118,41 @@ def test_lists_brute_force(oracle_mod):
                 assert len(nb) == 9 and len(it) == 27
 
 
+@pytest.mark.parametrize("box", [(0.0, 0.0, 1.0), (-1.0, -1.0, 2.0)])
+def test_leaf_assignment_is_the_floor_rule(oracle_mod, box):
+    """Each point falls in the leaf floor((coordinate - origin) 2^depth / side), a point on the upper
+    edge of the root box in the last leaf of its row or column (Section 4.2's uniform tree); the
+    tree order lists the leaves in Z-order (Morton) and each leaf's points by index."""
+    O = oracle_mod
+    depth, n = 3, 700
+    x0, y0, side = box
+    pts = x0 + side * inputs.uniform_points(29, n)
+    pts[:20, 0] = x0 + side            # right edge
+    pts[20:40, 1] = y0 + side          # top edge
+    pts[40] = (x0 + side, y0 + side)   # corner
+    pts[41] = (x0, y0)                 # origin
+    pts[42, 0] = x0 + side / 2         # on an inner box boundary
+    o = O.Oracle(pts, O.make_params(depth, 2, O.K_INV_R, box=box))
+    m = 1 << depth
+    cx = np.minimum(np.floor((pts[:, 0] - x0) / side * m).astype(int), m - 1)
+    cy = np.minimum(np.floor((pts[:, 1] - y0) / side * m).astype(int), m - 1)
+    cell = cy * m + cx
+    # leaf counts by grid index g = ix + 2^depth iy
+    assert np.array_equal(o.leaf_counts(), np.bincount(cell, minlength=m * m))
+    # tree order: points sorted by the Z-order (bit-interleaved) index of their leaf, ties by
+    # point index; either interleaving convention is a Z-order
+    perm = o.perm()
+    assert np.array_equal(np.sort(perm), np.arange(n))
+
+    def interleave(a, b):
+        return sum((((a >> k) & 1) << (2 * k)) | (((b >> k) & 1) << (2 * k + 1)) for k in range(depth))
+
+    got = [(int(cell[i]), int(i)) for i in perm]
+    want = [sorted(((int(cell[i]), int(i)) for i in range(n)), key=lambda t: (z(t[0] % m, t[0] // m), t[1]))
+            for z in (interleave, lambda a, b: interleave(b, a))]
+    assert got in want
+
+
 def test_every_leaf_pair_covered_exactly_once(oracle_mod):
     """The near field plus the interaction lists of all levels partition the leaf pairs
     (the FMM matrix of Section 2.2: each block is either full rank or a well-separated
