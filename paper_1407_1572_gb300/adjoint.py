@@ -11,7 +11,8 @@ the FMM matrix of the differentiated kernel (Table "table_FMM_operators"; the fa
 U K(xbar_i, ybar_j) V^T with U, V and the nodes fixed). The gradient is therefore the gradient of
 the computed solution, to the accuracy of the refined solves.
 
-All arithmetic runs in the library's CUDA kernels; this module only marshals tensors.
+The solves and the matvecs run in the library's CUDA kernels; the two inner products that turn
+lambda into dL/dl and dL/dsigma2 are plain torch reductions on the device tensors.
 """
 from __future__ import annotations
 
@@ -94,8 +95,10 @@ def solve_exp(points: np.ndarray, b, ell, sigma2, system: ExpKernelSystem | None
     global _FN
     if _FN is None:
         _FN = _function()
+    ell_v = float(ell.detach()) if hasattr(ell, "detach") else float(ell)
+    sig_v = float(sigma2.detach()) if hasattr(sigma2, "detach") else float(sigma2)
     if system is None:
-        system = ExpKernelSystem(points, float(ell), float(sigma2), **params)
-    elif system.ell != float(ell) or system.sigma2 != float(sigma2):
+        system = ExpKernelSystem(points, ell_v, sig_v, **params)
+    elif system.ell != ell_v or system.sigma2 != sig_v:
         raise ValueError("the system was built for other parameter values")
     return _FN.apply(b, ell, sigma2, system)
