@@ -19,6 +19,8 @@
  *     one-line message. A failed factorisation leaves the handle valid but unfactored.
  *   - All device work is queued on the stream given to ifmm_build (NULL = legacy default
  *     stream); calls that return results to the host synchronise that stream.
+ *   - A handle belongs to the device that was current at ifmm_build. Every call on it makes that
+ *     device current for its duration and gives the caller's current device back on return.
  *   - Not thread-safe per handle: calls on one handle must not overlap.
  */
 #ifndef IFMM_H
@@ -123,6 +125,9 @@ typedef struct {
     int64_t device_bytes;  /* device memory held by the handle                                     */
     int64_t launches_factor; /* kernels launched by the last ifmm_factor                           */
     int64_t launches_solve;  /* kernels launched by the last ifmm_solve / ifmm_solve_host          */
+    double compress_proj_flops; /* the part of kernel_flops[3] spent projecting the fill onto the
+                              complement of the old basis (products; double-float in
+                              IFMM_MIXED_SOLVE); the rest is the FP64 pivoted Gram-Schmidt        */
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
@@ -202,8 +207,9 @@ ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, 
  * 32 MiB array compiled into the library (every GPU that loads the library holds those 32 MiB
  * until the process exits). Limit: 16 N nrhs + 16 nrhs p^2 (4^2 + ... + 4^depth) bytes, each
  * piece rounded up to 256 bytes, must fit in 32 MiB; larger calls return IFMM_ERR_INVALID_ARG
- * with the size in ifmm_last_error. The first call on a device looks up the array's device
- * address (with that device current); make that first call before any stream capture. All calls
+ * with the size in ifmm_last_error. The first call for a device (the handle's device, made current
+ * by the call) looks up the array's device address on that device; make that first call before
+ * any stream capture. All calls
  * share the array and each call overwrites it: calls that overlap on the GPU (two streams, two
  * threads, two handles on one device) race and must be serialised by the caller. Arguments,
  * layout and the other errors are those of ifmm_matvec; the call synchronises the handle's

@@ -149,6 +149,21 @@ namespace {
         if (s_ != IFMM_OK) return s_;   \
     } while (0)
 
+// Every call on a handle runs with the handle's device current (the device that was current at
+// ifmm_build) and gives the caller back the device it had: a caller that switched devices between
+// calls must not have the kernels run on another GPU than the handle's memory.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) switched = cudaSetDevice(dev) == cudaSuccess;
+        cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
 // Device memory of the handles comes from one library-owned, stream-ordered pool per device: buffers
 // are allocated and freed in order on the handle's stream, so a free never synchronises the device
 // (handles factored concurrently on separate streams keep overlapping), and the pool keeps freed
@@ -781,6 +796,7 @@ ifmm_status factor_impl(ifmm_handle* h) {
         h->stats.kernel_launches[t] = kl[t];
         h->stats.kernel_flops[t] = cnt[fidx[t]];
     }
+    h->stats.compress_proj_flops = cnt[7];
     h->stats.launches_factor = launches_so_far() - l0;
     h->stats.rank_overflows = 0;
     h->factored = true;
@@ -1274,6 +1290,7 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
 
 ifmm_status ifmm_factor(ifmm_h h) {
     if (!h) return IFMM_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
     h->err.clear();
     release_factors(h);
     auto t0 = std::chrono::steady_clock::now();
@@ -1296,6 +1313,7 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
         h->err = "ifmm_solve before ifmm_factor";
         return IFMM_ERR_STATE;
     }
+    DeviceGuard dg(h->device);
     h->err.clear();
     auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launches_so_far();
@@ -1353,6 +1371,7 @@ ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int 
         h->err = "ifmm_solve_host before ifmm_factor";
         return IFMM_ERR_STATE;
     }
+    DeviceGuard dg(h->device);
     void *pb = nullptr, *px = nullptr;
     CKS(workspace(h, 80, sizeof(double) * (size_t)h->N * nrhs, &pb));
     CKS(workspace(h, 81, sizeof(double) * (size_t)h->N * nrhs, &px));
@@ -1375,6 +1394,7 @@ ifmm_status ifmm_solve_host(ifmm_h h, const double* b_host, double* x_host, int 
 
 ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld) {
     if (!h || !x_dev || !y_dev || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
     h->err.clear();
     CKS(matvec_impl(h, x_dev, ld, y_dev, ld, nrhs));
     CK(cudaStreamSynchronize(h->st));
@@ -1400,7 +1420,7 @@ const char* ifmm_last_error(ifmm_h h) { return h ? h->err.c_str() : "null handle
 
 void ifmm_destroy(ifmm_h h) {
     if (!h) return;
-    cudaSetDevice(h->device);
+    DeviceGuard dg(h->device);
     if (h->st) cudaStreamSynchronize(h->st);
     else cudaDeviceSynchronize();
     for (auto& a : h->allocs) {
@@ -1436,6 +1456,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 extern "C" ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld) {
     if (!h || !x_dev || !y_dev || nrhs < 1 || nrhs > 1024 || ld < h->N) return IFMM_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);   // the handle's device is current from here on
     h->err.clear();
     const int kap = h->depth, r0 = h->r0;
     // carve the scratch: tree-order input and output, then multipoles and locals per level
@@ -1452,10 +1473,9 @@ extern "C" ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double
                  " bytes (reduce N * nrhs, or use ifmm_matvec)";
         return IFMM_ERR_INVALID_ARG;
     }
-    // set-up, once per device, with that device current: the host-side name of the array is not
-    // a device address, so fetch the address the kernels must be given
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
+    // set-up, once per device, with that device (the handle's) current: the host-side name of the
+    // array is not a device address, so fetch the address the kernels must be given
+    const int dev = h->device;
     if (dev < 0 || dev >= 256) {
         h->err = "ifmm_matvec_noalloc: device ordinal out of range";
         return IFMM_ERR_CUDA;

@@ -85,7 +85,8 @@ struct LevelView {
     const int64_t* psoff;      // [nb]
     int* status;               // device error bits (DEV_ERR_*)
     double* counters;          // [0] schur flops, [1] schur bytes, [2] all factor flops,
-                               // [3] pivot, [4] panel, [5] compress, [6] redirect flops
+                               // [3] pivot, [4] panel, [5] compress, [6] redirect flops,
+                               // [7] the projection part of [5]
     double eps, sA;
     int tau_ref;
     int symmetric;             // kernel symmetric: F_pq = F_qp^T in exact arithmetic

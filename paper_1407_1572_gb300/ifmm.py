@@ -45,7 +45,7 @@ class ifmm_stats(ctypes.Structure):
                 ("kernel_flops", ctypes.c_double * 5), ("level_ms", ctypes.c_double * 16),
                 ("last_update", ctypes.c_double), ("last_residual", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
-                ("launches_solve", ctypes.c_int64)]
+                ("launches_solve", ctypes.c_int64), ("compress_proj_flops", ctypes.c_double)]
 
 
 FACTOR_KERNELS = ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")
