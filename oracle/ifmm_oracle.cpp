@@ -42,7 +42,12 @@
  *      Here: the old basis W_q is kept; the stacked well-separated fill S_q of box q is
  *      projected onto the complement of W_q and a column-pivoted QR (pivoted Gram-Schmidt)
  *      of the remainder appends directions while the largest remaining column norm exceeds
- *      eps * (largest column norm of S_q). One basis serves both L2P_qq and P2M_qq^T.
+ *      eps * (largest column norm of S_q). One basis serves both L2P_qq and P2M_qq^T. Every
+ *      kernel here is symmetric, so the elimination keeps the extended system exactly
+ *      symmetric: Algorithm 1's paired fill-ins (P2P_pq and P2P_qp, P2L_pq and M2P_qp, M2L_pq
+ *      and M2L_qp) are formed once per unordered pair (p <= q in grid order) and written as a
+ *      block and its transpose, S_q stacks the row fills only (the column fills are their
+ *      transposes), and the pivot column of each Gram-Schmidt step is chosen on exact norms.
  *   R3 orthonormalisation ("Chebyshev interpolation followed by SVD", Section 5): a
  *      column-pivoted Householder QR of each leaf basis and of each stacked parent transfer,
  *      with the R factors folded into M2L and the parent transfers; rank cut at 1e-13
@@ -70,8 +75,16 @@
 #include <omp.h>
 #endif
 
+// Planted mistakes: tests/test_planted_mistakes.py compiles this file with -DORACLE_PLANT=k
+// (k = 1..9) to check that the pins catch each one; every real build has ORACLE_PLANT = 0 and the
+// branches below fold away.
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+
 namespace {
 
+constexpr int kPlant = ORACLE_PLANT;
 const double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------------------------------
@@ -297,15 +310,16 @@ int augment_basis(Mat& W, const Mat& S, double eps, double ref, int cap, Counter
     double smax = 0.0;
     for (int j = 0; j < m; ++j) smax = std::max(smax, col_norm(S, j));
     if (smax == 0.0) return 0;
-    double tau = eps * (ref > 0.0 ? ref : smax);
-    // R = (I - W W^T) S, applied twice
+    double tau = eps * (ref > 0.0 && kPlant != 7 ? ref : smax);
+    // R = (I - W W^T) S, applied once: what it leaves inside span(W) is of the order of
+    // u ||S_j|| per column, far below the threshold for any fill below tau / u; a candidate is
+    // re-orthogonalised twice below before it enters the basis, so the basis stays orthonormal
     Mat R = S;
-    if (r > 0)
-        for (int pass = 0; pass < 2; ++pass) {
-            Mat T = mul_tn(W, R, ct);  // r x m
-            Mat WT = mul(W, T, ct);
-            for (size_t t = 0; t < R.a.size(); ++t) R.a[t] -= WT.a[t];
-        }
+    if (r > 0) {
+        Mat T = mul_tn(W, R, ct);  // r x m
+        Mat WT = mul(W, T, ct);
+        for (size_t t = 0; t < R.a.size(); ++t) R.a[t] -= WT.a[t];
+    }
     int limit = std::min(n, cap > 0 ? cap : n);
     std::vector<std::vector<double>> U;
     std::vector<double> norms(m);
@@ -325,7 +339,7 @@ int augment_basis(Mat& W, const Mat& S, double eps, double ref, int cap, Counter
         std::vector<double> u(n);
         for (int i = 0; i < n; ++i) u[i] = R.at(i, jb) / best;
         // re-orthogonalise against W and the directions already taken, twice
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < (kPlant == 8 ? 0 : 2); ++pass) {
             for (int j = 0; j < r; ++j) {
                 double s = 0.0;
                 for (int i = 0; i < n; ++i) s += W.at(i, j) * u[i];
@@ -356,6 +370,7 @@ int augment_basis(Mat& W, const Mat& S, double eps, double ref, int cap, Counter
         ct.flops += 4.0 * n * m + 8.0 * n * (r + U.size());
         U.push_back(std::move(u));
     }
+    if (kPlant == 9 && !U.empty()) U.pop_back();
     int add = (int)U.size();
     if (add > 0) {
         Mat Wn(n, r + add);
@@ -729,31 +744,25 @@ void compress_fill(ElimLevel& L, int e, double eps, double ref, int rcap, Counte
     std::vector<int> nb = neighbours(L, e);
     for (int q : nb) {
         if (q == e || L.E[q]) continue;
-        // S_q: well-separated fill in q's P2P row (P2P_qp / M2P_qp) and in q's column x_q
-        // (P2P_pq / P2L_pq, transposed)
-        std::vector<const Mat*> cols, rows;
+        // S_q: well-separated fill in q's P2P row (P2P_qp / M2P_qp). The fill in q's column x_q
+        // (P2P_pq / P2L_pq) is its exact transpose (the Schur update above writes both blocks of a
+        // pair), so the one basis W_q = L2P_qq = P2M_qq^T that spans the row fill spans the column
+        // fill as well
+        std::vector<const Mat*> cols;
         for (int p : nb) {
             if (p == q || !well_separated(L, p, q)) continue;
             Mat& f1 = active_block(L, q, p);
             if (f1.present()) cols.push_back(&f1);
-            Mat& f2 = active_block(L, p, q);
-            if (f2.present()) rows.push_back(&f2);
         }
-        if (cols.empty() && rows.empty()) continue;
+        if (cols.empty()) continue;
         int nq = L.n[q], m = 0;
         for (auto* f : cols) m += f->c;
-        for (auto* f : rows) m += f->r;
         Mat S(nq, m);
         int off = 0;
         for (auto* f : cols) {
             for (int i = 0; i < nq; ++i)
                 for (int j = 0; j < f->c; ++j) S.at(i, off + j) = f->at(i, j);
             off += f->c;
-        }
-        for (auto* f : rows) {
-            for (int i = 0; i < nq; ++i)
-                for (int j = 0; j < f->r; ++j) S.at(i, off + j) = f->at(j, i);
-            off += f->r;
         }
         bool over = false;
         int add = augment_basis(L.W[q], S, eps, ref, rcap, ct, over);
@@ -763,11 +772,12 @@ void compress_fill(ElimLevel& L, int e, double eps, double ref, int rcap, Counte
         ct.added += add;
         if (over) ct.overflows += 1.0;
     }
-    // redirect each well-separated fill through the bases into M2L_pq
+    // redirect each well-separated fill through the bases into M2L_pq; the pair (q, p) receives
+    // the transpose (its fill is the transpose of F_pq)
     for (int p : nb) {
         if (p == e) continue;
         for (int q : nb) {
-            if (q == e || p == q || !well_separated(L, p, q)) continue;
+            if (q == e || q <= p || !well_separated(L, p, q)) continue;
             if (L.E[p] && L.E[q]) continue;  // M2L_pq was updated directly
             Mat& F = active_block(L, p, q);
             if (!F.present()) continue;
@@ -777,13 +787,19 @@ void compress_fill(ElimLevel& L, int e, double eps, double ref, int rcap, Counte
                 G = mul(t, L.W[q], ct);
             } else if (L.E[p] && !L.E[q]) {  // P2L_pq = M2L_pq P2M_qq
                 G = mul(F, L.W[q], ct);
+                if (kPlant == 2)
+                    for (double& t : G.a) t *= 1.0 + 1e-6;
             } else {                         // M2P_pq = L2P_pp M2L_pq
                 G = mul_tn(L.W[p], F, ct);
             }
             Mat& M = blk(L.M2L, L, p, q);
             pad_to(M, L.r[p], L.r[q]);
             add_into(M, G, 1.0, ct);
+            Mat& M2 = blk(L.M2L, L, q, p);
+            pad_to(M2, L.r[q], L.r[p]);
+            add_into(M2, transpose(G), 1.0, ct);
             F.clear();
+            active_block(L, q, p).clear();
         }
     }
 }
@@ -839,18 +855,33 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
         X[t] = std::move(rhs);
     }
     Mat Xy(n + r, r);
-    for (int j = 0; j < r; ++j) Xy.at(n + j, j) = -1.0;
+    for (int j = 0; j < r; ++j) Xy.at(n + j, j) = kPlant == 4 ? 1.0 : -1.0;
     if (n + r > 0) piv_solve(F.LU, F.piv, n, F.alpha, Xy, ct);
     // consumed blocks: column x_e and row P2P_e leave the system
     for (int p : nb) {
         blk(L.P2P, L, p, e).clear(); blk(L.P2L, L, p, e).clear();
         blk(L.P2P, L, e, p).clear(); blk(L.M2P, L, e, p).clear();
     }
-    // Schur complement A[rho, gamma] -= C_rho X_gamma (rows of the neighbours)
+    // Schur complement A[rho, gamma] -= C_rho X_gamma (rows of the neighbours). Every kernel of
+    // this oracle is symmetric, and so is the extended system (P2M = L2P^T, M2L_qp = M2L_pq^T):
+    // the update of block (q, p) is the transpose of that of (p, q). Algorithm 1 names the fill-ins
+    // in exactly such pairs (P2P_pq and P2P_qp, P2L_pq and M2P_qp, M2L_pq and M2L_qp), so each
+    // unordered pair is formed once, for p <= q in grid order, and written to both blocks; the
+    // system stays exactly symmetric (reading R2).
+    auto has_row = [&](int b) {
+        for (const Panel& c : F.C) if (c.box == b) return true;
+        return false;
+    };
+    auto has_col = [&](int b) {
+        for (const Panel& c : F.B) if (c.box == b) return true;
+        return false;
+    };
     for (const Panel& cp : F.C) {
         int p = cp.box;
         for (size_t t = 0; t < F.B.size(); ++t) {
             int q = F.B[t].box;
+            const bool mirrored = q != p && has_row(q) && has_col(p);
+            if (mirrored && q < p) continue;   // written as the transpose of the pair (q, p)
             Mat Xx(n, X[t].c);
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < X[t].c; ++j) Xx.at(i, j) = X[t].at(i, j);
@@ -859,6 +890,12 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
             if (L.E[p] && L.E[q]) pad_to(tgt, L.r[p], L.r[q]);
             add_into(tgt, upd, -1.0, ct);
             ct.bytes += 8.0 * ((double)cp.blk.r * cp.blk.c + (double)Xx.r * Xx.c + 2.0 * upd.r * upd.c);
+            if (mirrored) {
+                Mat& tgt2 = active_block(L, q, p);
+                if (L.E[p] && L.E[q]) pad_to(tgt2, L.r[q], L.r[p]);
+                add_into(tgt2, transpose(upd), -1.0, ct);
+                ct.bytes += 16.0 * upd.r * upd.c;
+            }
         }
         // new column y_e in row rho: M2P_pe (p not eliminated) or M2L_pe (p eliminated)
         Mat Xx(n, r);
@@ -876,7 +913,7 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
             for (int j = 0; j < X[t].c; ++j) Xz.at(i, j) = X[t].at(n + i, j);
         Mat& tgt = L.E[q] ? blk(L.M2L, L, e, q) : blk(L.P2L, L, e, q);
         if (L.E[q]) pad_to(tgt, r, L.r[q]);
-        add_into(tgt, Xz, 1.0, ct);
+        add_into(tgt, Xz, kPlant == 1 ? -1.0 : 1.0, ct);
     }
     {
         Mat Xz(r, r);
@@ -940,7 +977,8 @@ void make_level(Handle& h, int k) {
                 Mat W(off, O.rank[g]);
                 for (int c = 0; c < 4; ++c)
                     for (int t = 0; t < OC.rank[cg[c]]; ++t)
-                        for (int j = 0; j < O.rank[g]; ++j) W.at(offs[c] + t, j) = O.W[g].at(ooffs[c] + t, j);
+                        for (int j = 0; j < O.rank[g]; ++j)
+                            W.at(offs[c] + t, j) = (kPlant == 3 && c == 3) ? 0.0 : O.W[g].at(ooffs[c] + t, j);
                 L.W[g] = std::move(W);
             }
         // P2P_PQ = [M2L_{c d}] over the children of neighbours P, Q
@@ -1085,7 +1123,7 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
                 Mat upd = mul(cp.blk, vx, ct);
                 Mat& tgt = cp.kind == ROW_P2P ? rhsP[k][cp.box] : rhsZ[k][cp.box];
                 for (int i = 0; i < upd.r; ++i)
-                    for (int j = 0; j < nrhs; ++j) tgt.at(i, j) -= upd.at(i, j);
+                    for (int j = 0; j < nrhs; ++j) tgt.at(i, j) -= (kPlant == 5 ? 1.0 + 1e-6 : 1.0) * upd.at(i, j);
             }
             for (int i = 0; i < F.r; ++i)
                 for (int j = 0; j < nrhs; ++j) rhsZ[k][e].at(i, j) += v.at(F.n + i, j);
@@ -1097,7 +1135,9 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
                 int ix = g % U.side, iy = g / U.side;
                 Mat R(U.n[g], nrhs);
                 for (int c = 0; c < 4; ++c) {
-                    int cg = (2 * ix + (c & 1)) + L.side * (2 * iy + (c >> 1));
+                    // (plant 6: the children's x and y offsets swapped)
+                    const int cx = kPlant == 6 ? (c >> 1) : (c & 1), cy = kPlant == 6 ? (c & 1) : (c >> 1);
+                    int cg = (2 * ix + cx) + L.side * (2 * iy + cy);
                     int off = U.xoff[(size_t)g * 5 + c];
                     for (int i = 0; i < L.r[cg]; ++i)
                         for (int j = 0; j < nrhs; ++j) R.at(off + i, j) = rhsZ[k][cg].at(i, j);
@@ -1618,6 +1658,27 @@ int oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, c
         for (int64_t j = 0; j < n; ++j)
             out[i * n + j] = kernel_value(*prm, P[2 * i], P[2 * i + 1], Q[2 * j], Q[2 * j + 1]);
     return 0;
+}
+
+/* Reading R2's basis augmentation on its own (a pin of the compression step). */
+int oracle_augment_basis(const double* W, int n, int r, const double* S, int m, double eps, double ref, int cap,
+                         double* Wout, int* overflow) {
+    if (!S || !Wout || n <= 0 || r < 0 || r > n || m < 0 || (r > 0 && !W) || !(eps >= 0.0)) return -1;
+    Mat Wm;
+    if (r > 0) {
+        Wm = Mat(n, r);
+        std::copy(W, W + (size_t)n * r, Wm.a.begin());
+    }
+    Mat Sm(n, m);
+    std::copy(S, S + (size_t)n * m, Sm.a.begin());
+    Counter ct;
+    bool over = false;
+    int add = augment_basis(Wm, Sm, eps, ref, cap, ct, over);
+    const int rr = Wm.present() ? Wm.c : 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < rr; ++j) Wout[(size_t)i * rr + j] = Wm.at(i, j);
+    if (overflow) *overflow = over ? 1 : 0;
+    return add;
 }
 
 }  // extern "C"

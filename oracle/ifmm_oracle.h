@@ -72,6 +72,15 @@ int   oracle_kernel_eval(const oracle_params* prm, const double* a, const double
 int   oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
                            double* out);
 
+/* The compression step of reading R2 alone: append to W (n x r, row-major, orthonormal columns;
+ * NULL when r = 0) the directions of S (n x m, row-major) that W misses, by pivoted Gram-Schmidt
+ * on (I - W W^T) S with threshold eps * ref (ref > 0) or eps * (largest column norm of S)
+ * (ref <= 0), at most cap columns in all (cap <= 0: n). Wout receives the extended basis
+ * (n x (r + added), row-major; room for n x n). Returns the number of appended directions (-1 on
+ * bad arguments); *overflow = 1 if the cap cut it. */
+int   oracle_augment_basis(const double* W, int n, int r, const double* S, int m, double eps, double ref, int cap,
+                           double* Wout, int* overflow);
+
 #ifdef __cplusplus
 }
 #endif

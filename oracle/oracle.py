@@ -75,6 +75,8 @@ def _load():
             lib.oracle_lagrange.argtypes = [ctypes.c_int, ctypes.c_double, dp]
             lib.oracle_kernel_eval.argtypes = [ctypes.POINTER(Params), dp, dp, dp]
             lib.oracle_kernel_matrix.argtypes = [ctypes.POINTER(Params), dp, i64, dp, i64, dp]
+            lib.oracle_augment_basis.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, dp, dp]
             _lib = lib
     return _lib
 
@@ -123,6 +125,23 @@ def kernel_matrix(params: Params, P, Q) -> np.ndarray:
     out = np.zeros((P.shape[0], Q.shape[0]))
     _load().oracle_kernel_matrix(ctypes.byref(params), _ptr(P), P.shape[0], _ptr(Q), Q.shape[0], _ptr(out))
     return out
+
+
+def augment_basis(W: np.ndarray, S: np.ndarray, eps: float, ref: float = 0.0, cap: int = 0):
+    """Reading R2's compression step alone: returns (extended basis, appended count, overflow).
+    W: n x r with orthonormal columns (r may be 0), S: n x m fill; threshold eps * ref (ref > 0) or
+    eps * the largest column norm of S."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    n, m = S.shape
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(n, -1))
+    r = W.shape[1]
+    out = np.zeros(n * n)
+    ov = np.zeros(1, dtype=np.int32)
+    add = _load().oracle_augment_basis(_ptr(W) if r else None, n, r, _ptr(S), m, float(eps), float(ref), int(cap),
+                                       _ptr(out), _ptr(ov))
+    if add < 0:
+        raise ValueError("oracle_augment_basis rejected its arguments")
+    return out[: n * (r + add)].reshape(n, r + add), int(add), bool(ov[0])
 
 
 def dense_lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:

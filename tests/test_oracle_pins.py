@@ -375,3 +375,89 @@ def test_ranks_bounded_and_work_linear(oracle_mod):
         out.append((st["max_rank"], st["flops"] / N))
     assert out[2][0] <= 2.0 * out[1][0]
     assert out[2][1] <= 2.5 * out[1][1]
+
+
+# ---- the compression step alone (Algorithm 1's compression of well-separated fill; reading R2) --
+
+def _fill_with_known_rank(n=64, r=16, seed=5):
+    """An orthonormal basis W (n x r) and a fill S whose part outside span(W) is known exactly:
+    seven columns sigma_j q_j with q_j orthonormal and orthogonal to W, sigma_j = 10^-a_j with
+    a = (2, 3, 4.5, 5.5, 7.5, 9, 10); three columns of norm 100 inside span(W); every column plus
+    noise of norm 1e-9. The threshold eps = 1e-6 is never within a factor 3 of a sigma_j."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, r + 7)))
+    W, Qp = Q[:, :r].copy(), Q[:, r:]
+    sig = 10.0 ** -np.array([2.0, 3.0, 4.5, 5.5, 7.5, 9.0, 10.0])
+    cols = [sig[j] * Qp[:, j] for j in range(7)]
+    for _ in range(3):
+        g = rng.standard_normal(r)
+        cols.append(100.0 * W @ (g / np.linalg.norm(g)))
+    S = np.stack(cols, axis=1)
+    noise = rng.standard_normal(S.shape)
+    S += 1e-9 * noise / np.linalg.norm(noise, axis=0)
+    return W, S, Qp, sig
+
+
+def test_compression_appends_exactly_the_directions_above_the_threshold(oracle_mod):
+    """Reading R2/R5: with the matrix-scale reference (threshold eps * s_A, here s_A = 1) the four
+    directions whose size exceeds 1e-6 are appended and nothing else; with the fill-relative
+    reference (eps times the largest column of S, which is 100) only the two above 1e-4 are. The
+    old basis is kept bit for bit (so the operators' update is a zero-padding), the new columns are
+    orthonormal to it, and they span the expected directions. A wrong reference, an off-by-one in
+    the kept count or a lost old basis fails here."""
+    O = oracle_mod
+    W, S, Qp, sig = _fill_with_known_rank()
+    for ref, want in ((1.0, 4), (0.0, 2)):
+        W2, add, over = O.augment_basis(W, S, 1e-6, ref=ref)
+        assert (add, over) == (want, False), (ref, add)
+        assert np.array_equal(W2[:, :16], W)
+        assert np.abs(W2.T @ W2 - np.eye(16 + add)).max() < 1e-14
+        # the appended columns span q_0 .. q_{want-1} up to the noise and the dropped directions
+        P = Qp[:, :want] @ Qp[:, :want].T
+        # (the noise, 1e-9, against the smallest kept direction, 3.2e-6: 3e-4)
+        assert np.linalg.norm(W2[:, 16:] - P @ W2[:, 16:]) < 1e-3
+    # the cap: at most 18 columns in all
+    W3, add, over = O.augment_basis(W, S, 1e-6, ref=1.0, cap=18)
+    assert (add, over) == (2, True)
+
+
+def test_compression_stays_orthonormal_on_nearly_parallel_fill(oracle_mod):
+    """Columns a, a + 1e-7 b, a + 2e-7 c (threshold 1e-12): three directions, and the basis stays
+    orthonormal to rounding. Gram-Schmidt without the re-orthogonalisation of reading R2 loses
+    orthogonality in proportion to u / 1e-7 (about 1e-9) on such columns."""
+    O = oracle_mod
+    rng = np.random.default_rng(11)
+    n, r = 64, 16
+    Q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    a, b, c = (rng.standard_normal(n) for _ in range(3))
+    S = np.stack([a, a + 1e-7 * b, a + 2e-7 * c], axis=1)
+    W2, add, _ = O.augment_basis(Q, S, 1e-12, ref=1.0)
+    assert add == 3
+    assert np.abs(W2.T @ W2 - np.eye(r + 3)).max() < 1e-14
+
+
+def test_compressed_solve_within_c_eps_of_dense_lu(oracle_mod):
+    """4,096 uniform points, depth 3, rank 16, eps 1e-10, matrix-scale threshold: the compressed
+    factorisation solves a perturbed matrix A~ + E, and every remainder the compression drops has
+    columns below eps * s_A, so to first order ||x - x_dense|| / ||x_dense|| <= C eps with
+    C = s_A ||A~^{-1}||_2 (8.9e4 here; s_A = 3954, ||A~^{-1}||_2 = 22.4 = 1 / min |lambda(A~)|, A~
+    being symmetric). The measured error, 5.5e-8, is 0.6% of that bound, and it scales with eps.
+    The dense reference is LAPACK's solve of the oracle's assembled A~."""
+    O = oracle_mod
+    N = 4096
+    errs = {}
+    for eps in (1e-10, 1e-8):
+        o, _ = _oracle(O, N, 3, 4, eps=eps, seed=1407 + N, tau_ref=1)
+        o.factor()
+        if eps == 1e-10:
+            A = o.dense_tilde()
+            assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+            sA = o.stats()["scale_A"]
+            C = sA / np.abs(np.linalg.eigvalsh(A)).min()
+            b = inputs.rhs(9, N, 2)
+            xd = np.linalg.solve(A, b)
+        errs[eps] = np.linalg.norm(o.solve(b) - xd) / np.linalg.norm(xd)
+    assert 5e4 < C < 2e5
+    assert errs[1e-10] <= C * 1e-10
+    assert errs[1e-8] <= C * 1e-8
+    assert 10.0 < errs[1e-8] / errs[1e-10] < 1000.0
