@@ -60,22 +60,39 @@ def test_matvec_matches_oracle(ifmm, N, depth, p, nrhs):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
 
 
-@pytest.mark.parametrize("N,depth,p,eps", [
-    (4096, 3, 4, 1e-10),     # 4096 uniform points, 64 leaves, rank 16, eps 1e-10
-    (2000, 3, 3, 1e-8),
-    (1500, 2, 4, 1e-9),      # two levels: leaves at level 2, then the level-1 system
-    (9001, 4, 3, 1e-7),      # ragged leaves, four levels
-    (65536, 5, 4, 1e-6),     # 1,024 leaves x 64 points, rank 16
-    (65536, 5, 6, 1e-6),     # same, Chebyshev 6 x 6 (rank 36)
+def _maxrel(a, b):
+    """Largest element-wise difference relative to the largest element of the reference."""
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("N,depth,p,eps,bar", [
+    (4096, 3, 4, 1e-10, 1e-10),     # 4096 uniform points, 64 leaves, rank 16, eps 1e-10
+    (4096, 3, 6, 1e-6, 1e-10),      # rank 36
+    (2000, 3, 3, 1e-8, 1e-10),
+    (1500, 2, 4, 1e-9, 1e-10),      # two levels: leaves at level 2, then the level-1 system
+    (9001, 4, 3, 1e-7, 1e-10),      # ragged leaves, four levels
+    (16384, 4, 4, 1e-6, 1e-8),
+    (16384, 4, 6, 1e-6, 1e-8),
+    (65536, 5, 4, 1e-6, 1e-8),      # 1,024 leaves x 64 points, rank 16
+    (65536, 5, 6, 1e-6, 1e-7),      # same, Chebyshev 6 x 6 (rank 36)
+    (65536, 5, 6, 1e-8, 1e-8),
 ])
-def test_fp64_factor_solve_matches_oracle(ifmm, N, depth, p, eps):
-    """Matrix-scale threshold (tau_ref = 1): identical box ranks at every level and the same
-    solution to 1e-10. At 65,536 points the gate is 1e-6: both sides compute the same compressed
-    factorisation (identical ranks, asserted), but 1/r + sqrt(N) I is indefinite and its balanced
-    pivot blocks reach condition numbers ~1e7, so rounding-order differences between two FP64 codes
-    (Gauss-Jordan, one projection pass by CTA GEMMs with sequential accumulation and mirrored
-    symmetric updates on the GPU; LU, two projection passes and both halves in the oracle) grow
-    to 1e-9 .. 1e-6 (measured 1.0e-9 at p = 4, 4.9e-7 at p = 6)."""
+def test_fp64_factor_solve_matches_oracle(ifmm, N, depth, p, eps, bar):
+    """Matrix-scale threshold (tau_ref = 1): identical box ranks at every level, and every element
+    of the solution within `bar` of the oracle's, relative to the solution's largest element.
+
+    The bars come from what rounding alone does to this method (tests/test_oracle_sensitivity.py):
+    the oracle run on the same points with the last bit of every coordinate flipped differs from
+    itself by 5.7e-11 (4,096 points, eps 1e-10), 1.8e-10 / 2.6e-10 (16,384, rank 16 / 36),
+    1.2e-9 / 1.5e-8 (65,536, rank 16 / 36), with identical ranks. 1/r + sqrt(N) I is indefinite,
+    its pivot blocks reach condition numbers near 1e7, and the pivoted Gram-Schmidt of the
+    compression compares column norms, so where two candidates are within the rounding noise a
+    different one is kept. The GPU (Gauss-Jordan inverses, CTA-tiled sums) and the oracle (LU
+    solves, sequential sums) round differently and differ by a few times that much (measured
+    1e-11 at 4,096, 1.2e-9 / 5.9e-10 at 16,384, 1.9e-9 / 4.8e-8 / 4.6e-9 at 65,536); each bar
+    leaves a margin of 2 to 10 over the measurement. Both sides make the same algorithmic choices:
+    each symmetric pair of fill-ins formed once and its transpose written, the same fill columns
+    stacked and projected once, every Gram-Schmidt pivot chosen on exact column norms."""
     pts = inputs.uniform_points(1407 + N, N)
     g = _gpu(ifmm, pts, depth, p, eps, tau_ref=1)
     g.factor()
@@ -86,7 +103,35 @@ def test_fp64_factor_solve_matches_oracle(ifmm, N, depth, p, eps):
     b = inputs.rhs(9, N, 2)
     x = g.solve(_t(b)).cpu().numpy()
     xo = o.solve(b)
-    assert _rel(x, xo) <= (1e-10 if N <= 16384 else 1e-6)
+    d = _maxrel(x, xo)
+    print(f"N={N} p={p} eps={eps:g}: GPU vs oracle {d:.2e} (2-norm {_rel(x, xo):.2e})")
+    assert d <= bar
+
+
+@pytest.mark.parametrize("N,depth,bar", [(262144, 6, 1e-8), (1048576, 7, 1e-5)])
+def test_fp64_matches_oracle_at_scale(ifmm, N, depth, bar):
+    """The headline's tree (64 points per leaf, rank 16, eps 1e-6, 1/r + sqrt(N) I) at 2^18 and
+    2^20 points against the oracle (which factors 2^20 points in under a minute on 16 cores):
+    identical ranks at every level and the solution element-wise within `bar`. At 2^20 the oracle
+    on points moved by one unit in the last place differs from itself by 2.6e-7 (identical ranks):
+    the pivoted Gram-Schmidt meets more near-ties among some 10^6 pivot choices; the GPU differs
+    from it by 2.6e-6. Both are far below the compressed solve's own distance to A~^{-1} b at this
+    size (about 0.1, which the refinement removes)."""
+    p, eps = 4, 1e-6
+    pts = inputs.uniform_points(1407 + N, N)
+    g = _gpu(ifmm, pts, depth, p, eps, tau_ref=1)
+    g.factor()
+    o = _oracle(pts, depth, p, eps, tau_ref=1)
+    o.factor()
+    for k in range(2, depth + 1):
+        assert np.array_equal(g.ranks(k), o.ranks(k)), f"ranks differ at level {k}"
+    b = inputs.rhs(9, N, 1)
+    x = g.solve(_t(b)).cpu().numpy()
+    xo = o.solve(b)
+    d = _maxrel(x, xo)
+    print(f"N={N}: GPU vs oracle {d:.2e}")
+    assert d <= bar
+    g.close()
 
 
 @pytest.mark.parametrize("N,depth,p,eps", [(4096, 3, 4, 1e-10), (1500, 2, 4, 1e-9), (3000, 3, 3, 1e-6)])
@@ -165,8 +210,10 @@ def test_benchmark_kernels_match_oracle(ifmm, kernel):
     oracle, plus the normwise backward error on the interpolated matrix A~ (the oracle's is 1e-16
     to 1e-14 here).
 
-    log and a / r (kappa(A~) = 1.7e5 and 1.1e3): identical box ranks at every level, the oracle's
-    solution to 1e-10 and a backward error within ten times the oracle's. r^2 ln r has kappa(A~) =
+    log and a / r (kappa(A~) = 1.7e5 and 1.1e3): box ranks identical but in at most two boxes per
+    level, which may differ by at most two (at eps 1e-12 a direction can sit on the threshold: the
+    oracle on points moved by one unit in the last place already changes one level-2 rank of the
+    log kernel), the oracle's solution to 1e-10 and a backward error within ten times the oracle's. r^2 ln r has kappa(A~) =
     2.0e10 (far values reach 1.2e6 against the unit diagonal): the oracle's elimination and a dense LU of the same matrix already differ by 6.5e-9.
     The GPU applies explicit pivot inverses (Gauss-Jordan) where the oracle solves with the LU
     factors; on pivots this ill-conditioned the two roundings differ enough to move fill directions
@@ -192,7 +239,7 @@ def test_benchmark_kernels_match_oracle(ifmm, kernel):
         if ill:
             assert np.all(np.abs(gr - orr) <= 0.15 * orr + 2), f"level {k}: {gr} vs {orr}"
         else:
-            assert np.array_equal(gr, orr), f"ranks differ at level {k}: {int((gr != orr).sum())} boxes"
+            assert int((gr != orr).sum()) <= 2 and np.abs(gr - orr).max() <= 2, f"level {k}: {gr} vs {orr}"
     b = inputs.rhs(61, N, 2)
     x = g.solve(_t(b)).cpu().numpy()
     xo = o.solve(b)
@@ -208,7 +255,7 @@ def test_benchmark_kernels_match_oracle(ifmm, kernel):
         assert d <= 1e-7
         assert eta(x) <= eps, (eta(x), eta(xo))
     else:
-        assert d <= 1e-10
+        assert _maxrel(x, xo) <= 1e-10
         assert eta(x) <= 10.0 * eta(xo) + 1e-15, (eta(x), eta(xo))
 
 
@@ -235,24 +282,47 @@ def test_double_float_replay_of_fp64_factors(ifmm):
     assert d <= 1e-8
 
 
+def _oracle_refined(o, b, tol=1e-12, maxit=60):
+    """Classical iterative refinement with the oracle's own solve and FP64 FMM matvec: x converges
+    to A~^{-1} b when the compressed solve is a contraction for this system."""
+    x = o.solve(b)
+    for _ in range(maxit):
+        d = o.solve(b - o.matvec(x))
+        x = x + d
+        if np.linalg.norm(d) <= tol * np.linalg.norm(x):
+            break
+    return x
+
+
 def test_mixed_solve_config_65536(ifmm):
-    """N = 65,536, depth 5, rank 16, eps 1e-6, 8 right-hand sides: the FP64 and the mixed-precision
-    solve phase both reach the manufactured solution within 1e-6."""
+    """N = 65,536, depth 5, rank 16, eps 1e-6, 8 right-hand sides (b ~ N(0, 1)): the FP64 and the
+    mixed-precision solve (FP64 elimination, double-float products and replay, FP64 residuals)
+    both agree with the oracle's refined solution of the same A~ x = b within max(eps, 1e-6),
+    element-wise relative to the largest element, and reach the manufactured solution of
+    b = A~ x* within 1e-6."""
     N, depth, p, eps = 65536, 5, 4, 1e-6
     pts = inputs.uniform_points(1409, N)
+    o = _oracle(pts, depth, p, eps, tau_ref=1)
+    o.factor()
+    b8 = inputs.rhs(1411, N, 8)
+    xo = _oracle_refined(o, b8)
     xs = inputs.rhs(1410, N, 8)
-    errs = {}
+    res = {}
     for prec in (0, 2):
         prm = ifmm.default_params(depth=depth, cheb_p=p, eps=eps, diag=math.sqrt(N), precision=prec, tau_ref=1,
                                   refine_tol=1e-7, refine_maxit=120, refine_restart=30)
         g = ifmm.IFMM(pts, 0, prm)
         g.factor()
+        x8 = g.solve(_t(b8)).cpu().numpy()
+        d_oracle = _maxrel(x8, xo)
         b = g.matvec(_t(xs))
         x = g.solve(b).cpu().numpy()
-        errs[prec] = (_rel(x, xs), g.stats()["refine_iters"])
+        res[prec] = (d_oracle, _rel(x, xs), g.stats()["refine_iters"])
         g.close()
-    print("errors / iterations", errs)
-    assert errs[0][0] <= 1e-6 and errs[2][0] <= 1e-6
+    print("vs oracle / vs x* / iterations", res)
+    for prec in (0, 2):
+        assert res[prec][0] <= max(eps, 1e-6)
+        assert res[prec][1] <= 1e-6
 
 
 def test_transposed_solve(ifmm):
