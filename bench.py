@@ -40,7 +40,7 @@ WORKLOAD = dict(N=1 << 20, depth=7, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_
                 refine_maxit=120, refine_restart=60, refine_inner=1e-4)
 # bounded CPU sample of the same workload family for the oracle (same points per leaf, settings)
 CPU_SAMPLE = dict(N=1 << 16, depth=5, cheb_p=4, eps=1e-6, nrhs=32, seed=1411, tau_ref=1, refine_tol=1e-7,
-                  refine_maxit=40, refine_restart=0)
+                  refine_maxit=120, refine_restart=60)
 # the same on one thread, smaller (about 10 s)
 CPU_SAMPLE_1T = dict(CPU_SAMPLE, N=1 << 14, depth=4)
 
@@ -143,9 +143,75 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def oracle_gmres(o, b, tol, restart, maxit):
+    """Left-preconditioned GMRES(restart) on A~ x = b with the oracle's FMM matvec as A~ and its
+    IFMM solve as M^{-1}: the refinement the library runs (same recurrence: classical Gram-Schmidt
+    twice, Givens rotations, one independent Krylov space per right-hand side sharing every operator
+    application), stopped when max_j ||M^{-1}(b_j - A~ x_j)|| / ||x_j|| <= tol. Returns (x, inner
+    iterations, preconditioner applications)."""
+    import numpy as np
+
+    N, nrhs = b.shape
+    x = np.zeros_like(b)
+    it = applications = 0
+    xn = None
+    while True:
+        r = b if it == 0 and xn is None else b - o.matvec(x)
+        z = o.solve(r)
+        applications += 1
+        beta = np.linalg.norm(z, axis=0)
+        if xn is None:
+            xn = beta.copy()
+        est = float(np.max(np.where(xn > 0, beta / np.maximum(xn, 1e-300), 0.0)))
+        if est <= tol or it >= maxit:
+            break
+        V = [z / np.where(beta > 0, beta, 1.0)]
+        H = np.zeros((restart + 1, restart, nrhs))
+        cs, sn = np.zeros((restart, nrhs)), np.zeros((restart, nrhs))
+        g = np.zeros((restart + 1, nrhs))
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            w = o.solve(o.matvec(V[j]))
+            applications += 1
+            for _ in range(2):
+                for i in range(j + 1):
+                    hij = np.sum(V[i] * w, axis=0)
+                    H[i, j] += hij
+                    w = w - V[i] * hij
+            hn = np.linalg.norm(w, axis=0)
+            for i in range(j):
+                a, bb = H[i, j].copy(), H[i + 1, j].copy()
+                H[i, j] = cs[i] * a + sn[i] * bb
+                H[i + 1, j] = -sn[i] * a + cs[i] * bb
+            den = np.hypot(H[j, j], hn)
+            cs[j] = np.where(den > 0, H[j, j] / np.where(den > 0, den, 1.0), 1.0)
+            sn[j] = np.where(den > 0, hn / np.where(den > 0, den, 1.0), 0.0)
+            H[j, j] = den
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            V.append(w / np.where(hn > 0, hn, 1.0))
+            it += 1
+            k = j + 1
+            est = float(np.max(np.abs(g[j + 1]) / np.maximum(xn, 1e-300)))
+            if est <= tol or it >= maxit:
+                break
+        y = np.zeros((k, nrhs))
+        for i in range(k - 1, -1, -1):
+            acc = g[i] - np.sum(H[i, i + 1:k] * y[i + 1:k], axis=0)
+            y[i] = np.where(H[i, i] != 0, acc / np.where(H[i, i] != 0, H[i, i], 1.0), 0.0)
+        for i in range(k):
+            x = x + V[i] * y[i]
+        xn = np.linalg.norm(x, axis=0)
+        if it >= maxit:
+            break
+    return x, it, applications
+
+
 def oracle_step(w, threads=0, parts=None):
-    """One oracle factor + refined solve on the bounded sample; returns (seconds, error). `parts`
-    (a dict), if given, receives the build, factor and solve (with refinement) seconds."""
+    """One oracle factor + refined solve (GMRES, as the library refines) on the bounded sample;
+    returns (seconds, error). `parts` (a dict), if given, receives the build, factor and solve
+    seconds and the GMRES iteration count."""
     import numpy as np
 
     from oracle import oracle as O
@@ -162,34 +228,72 @@ def oracle_step(w, threads=0, parts=None):
     t0 = time.perf_counter()
     o.factor()
     tf = time.perf_counter() - t0
-    x = o.solve(b)
-    for _ in range(w["refine_maxit"]):
-        r = b - o.matvec(x)
-        d = o.solve(r)
-        x = x + d
-        if np.max(np.linalg.norm(d, axis=0) / np.linalg.norm(x, axis=0)) <= w["refine_tol"]:
-            break
+    x, its, _ = oracle_gmres(o, b, w["refine_tol"], w["refine_restart"], w["refine_maxit"])
     dt = time.perf_counter() - t0
     err = float(np.max(np.linalg.norm(x - xs, axis=0) / np.linalg.norm(xs, axis=0)))
     if parts is not None:
-        parts.update(t_build_s=tb, t_factor_s=tf, t_solve_s=dt - tf)
+        parts.update(t_build_s=tb, t_factor_s=tf, t_solve_s=dt - tf, gmres_iters=its)
     return dt, err
 
 
-def cpu_baseline_entry():
-    """The oracle timed on this host: all cores on CPU_SAMPLE, one thread on CPU_SAMPLE_1T."""
-    parts = {}
-    dt, err = oracle_step(CPU_SAMPLE, parts=parts)
-    dt1, err1 = oracle_step(CPU_SAMPLE_1T, threads=1)
-    w, w1 = CPU_SAMPLE, CPU_SAMPLE_1T
-    return {"value": w["N"] / dt, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+def oracle_headline_sample(w, gpu_iters):
+    """The oracle on the headline workload itself (same N, points and settings): its factorisation
+    timed in full, one 32-column IFMM solve and one FMM matvec timed once, and the solve phase taken
+    as the GPU step's number of preconditioned matvecs times (solve + matvec) plus one solve. Returns
+    a dict of seconds."""
+    from oracle import oracle as O
+    from paper_1407_1572_gb300 import inputs
+    N = w["N"]
+    pts = inputs.uniform_points(w["seed"], N)
+    o = O.Oracle(pts, O.make_params(w["depth"], w["cheb_p"], O.K_INV_R, eps=w["eps"], diag=math.sqrt(N),
+                                    tau_ref=w["tau_ref"]))
+    b = inputs.rhs(w["seed"] + 1, N, w["nrhs"])
+    t0 = time.perf_counter()
+    o.factor()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x = o.solve(b)
+    ts1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.matvec(x)
+    tm1 = time.perf_counter() - t0
+    return {"t_factor_s": tf, "t_solve_once_s": ts1, "t_matvec_once_s": tm1,
+            "t_solve_modelled_s": (gpu_iters + 1) * ts1 + gpu_iters * tm1}
+
+
+def cpu_baseline_entry(gpu_iters=None):
+    """The oracle timed on this host. At the headline size (gpu_iters given): the oracle on the bench's
+    own workload (2^20 points, same points and settings), factor timed in full and the refined solve
+    sampled (one solve and one FMM matvec, scaled by the GPU step's GMRES iteration count), so the
+    ratio compares the same factorisation and the same number of operator applications. Otherwise
+    the complete factor + GMRES-refined solve on the 65,536-point sample. Both add one thread on
+    16,384 points."""
+    w1 = CPU_SAMPLE_1T
+    dt1, err1 = oracle_step(w1, threads=1)
+    single = {"value": w1["N"] / dt1, "unit": "unknowns/s", "cores": 1,
+              "sample": f"factor + GMRES-refined solve on N={w1['N']} (depth {w1['depth']}), one thread, {dt1:.1f} s, "
+                        f"err {err1:.1e}"}
+    if gpu_iters is None:
+        parts = {}
+        w = CPU_SAMPLE
+        dt, err = oracle_step(w, parts=parts)
+        return {"value": w["N"] / dt, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                "cpu_model": cpu_model(),
+                "sample": f"oracle factor + GMRES-refined {w['nrhs']}-RHS solve on N={w['N']} (depth {w['depth']}, "
+                          f"same settings per leaf), {dt:.1f} s, err {err:.1e}",
+                **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in parts.items()},
+                "single_thread": single}
+    hs = oracle_headline_sample(WORKLOAD, gpu_iters)
+    n = WORKLOAD["N"]
+    total = hs["t_factor_s"] + hs["t_solve_modelled_s"]
+    return {"value": n / total, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
             "cpu_model": cpu_model(),
-            "sample": f"oracle factor + refined {w['nrhs']}-RHS solve on N={w['N']} (depth {w['depth']}, same "
-                      f"settings per leaf), {dt:.1f} s, err {err:.1e}",
-            **{k: round(v, 3) for k, v in parts.items()},
-            "single_thread": {"value": w1["N"] / dt1, "unit": "unknowns/s", "cores": 1,
-                              "sample": f"the same on N={w1['N']} (depth {w1['depth']}), one thread, {dt1:.1f} s, "
-                                        f"err {err1:.1e}"}}
+            "sample": (f"oracle on the headline workload (N={n}, same points and settings): factor timed in full "
+                       f"({hs['t_factor_s']:.1f} s), one {WORKLOAD['nrhs']}-RHS solve ({hs['t_solve_once_s']:.1f} s) "
+                       f"and one FMM matvec ({hs['t_matvec_once_s']:.1f} s) timed and scaled to the GPU step's "
+                       f"{gpu_iters} preconditioned matvecs: {total:.0f} s per step"),
+            "factor_only_value": n / hs["t_factor_s"], "seconds": {k: round(v, 3) for k, v in hs.items()},
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -208,7 +312,8 @@ def run_reference(args):
     ms = 1000.0 * sum(times) / len(times)
     value = w["N"] / (ms / 1000.0)
     sample = (f"oracle (plain FP64 C++, OpenMP over same-colour boxes) on N={w['N']} (depth {w['depth']}), "
-              f"same settings per leaf; factor + {w['nrhs']}-RHS solve with refinement; err {max(errs):.2e}")
+              f"same settings per leaf; factor + {w['nrhs']}-RHS solve refined by GMRES({w['refine_restart']}) "
+              f"as the library refines; err {max(errs):.2e}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -234,13 +339,36 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# Arithmetic peaks of the CUDA cores from unit counts and the maximum clock: FP32 = 152 SMs x 128 lanes
-# x 2 flops x 2.07 GHz; FP64 = the nominal 1.25 TFLOP/s of GB300 (304 DFMA per clock); double-float =
-# the FP32 lanes at 11 FP32 instructions per multiply-add (exact product, cross terms, exact sum),
-# counted as 2 FP64-equivalent flops per multiply-add.
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_TFLOPS = 1.25
-DFL_TFLOPS = 152 * 128 * 2.07e9 / 11 * 2 / 1e12
+# Arithmetic peaks of the CUDA cores. Measured at run time by the pipe probe (measure/pipe_peaks.cu:
+# chains of independent FMAs over 8 blocks per SM, CUDA events), else the unit-count figures at
+# 2.07 GHz: FP32 = 152 SMs x 128 lanes x 2 flops; FP64 = 304 DFMA per clock (1.26 TFLOP/s). The
+# double-float rate is the FP32 rate at 11 FP32 instructions per multiply-add (exact product, two
+# cross terms, exact sum), counted as 2 FP64-equivalent flops per multiply-add.
+NOMINAL_PIPES = {"fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64_tflops": 304 * 2 * 2.07e9 / 1e12}
+
+
+def measure_pipes():
+    """FP64 and FP32 FMA rates of this GPU (TFLOP/s) from the pipe probe; None if it cannot run."""
+    import ctypes
+
+    try:
+        from paper_1407_1572_gb300 import build as _b
+        lib = ctypes.CDLL(_b.build_peaks())
+        out = (ctypes.c_double * 4)()
+        if lib.ifmm_pipe_peaks(out) != 0:
+            return None
+        return {"fp64_tflops": out[0], "fp32_tflops": out[1], "sms": int(out[2]),
+                "how": "measure/pipe_peaks.cu: 8 independent FMA chains per thread, 8 blocks of 256 threads per "
+                       "SM, CUDA events, one launch after a warm-up"}
+    except (OSError, RuntimeError):
+        return None
+
+
+def pipe_peaks(measured):
+    src = "measured (pipe probe)" if measured else "nominal unit counts at 2.07 GHz"
+    m = measured or NOMINAL_PIPES
+    return {"fp64": m["fp64_tflops"], "fp32": m["fp32_tflops"], "dfl": m["fp32_tflops"] / 11.0, "source": src}
+
 
 # arithmetic of each factor kernel per precision
 ARITH = {
@@ -253,29 +381,30 @@ ARITH = {
 }
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over the kernel's
-# launches) from one ncu capture of this bench's own command at N = 2^20 (summary in
-# profiles/launches_bench_n1048576_mixed.md), with the SHA-256 of the kernel sources it was taken on:
-# once a source differs the figure no longer describes the kernel and is reported as null.
-TRAFFIC = {("mixed_solve", 1048576): {"k_compress": 2640.8e6, "k_schur": 1868.9e6}}
-TRAFFIC_SRC = {
-    "ifmm_factor.cu": "89d58850fd32c25981a5c606db9909aabd8e4be699c8293b9d659b075db0c302",
-    "ifmm_common.cuh": "f7c96910ada3ff910b1b5cb6387b1bb1e9610e28d75e5ee46c6aa3c7b3da150d",
-    "ifmm_internal.h": "3f839e10601708fc2629c8d77922411acf52db74616146a7280989523c0537cc",
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel, from a bounded
+# ncu capture (one kernel, two launches, 65,536 points; profiles/), scaled to the bench's N by the
+# kernel's algorithmic flops per launch; keyed by the SHA-256 of the kernel sources it was taken on,
+# so that it reads null once a source differs. Empty: no capture of the current sources.
+TRAFFIC = {}
+TRAFFIC_SRC = {}
 
 
-def _traffic(precision, n, name):
+def _traffic(precision, n, name, flops_pl):
     import hashlib
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1407_1572_gb300", "csrc")
+    if not TRAFFIC_SRC:
+        return None
     for f, h in TRAFFIC_SRC.items():
         with open(os.path.join(csrc, f), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest() != h:
                 return None
-    return TRAFFIC.get((precision, n), {}).get(name)
+    rec = TRAFFIC.get((precision, name))
+    if not rec:
+        return None
+    return rec["bytes_per_launch"] * flops_pl / rec["flops_per_launch"]
 
 
-def _kernel_roofline(stats, precision, i, n=0):
+def _kernel_roofline(stats, precision, i, pipes, n=0):
     from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
     ms, launches, flops = stats["kernel_ms"], stats["kernel_launches"], stats["kernel_flops"]
     name = FACTOR_KERNELS[i]
@@ -283,28 +412,45 @@ def _kernel_roofline(stats, precision, i, n=0):
     t = ms[i] / nl / 1000.0                       # seconds per launch (CUDA events, handle's stream)
     flops_pl = flops[i] / nl
     arith = ARITH[precision][name]
-    if arith.startswith("double-float GEMM"):
-        peak, src = DFL_TFLOPS, "double-float rate of the FP32 CUDA cores (unit counts at 2.07 GHz, 11 instructions per multiply-add)"
+    parts = None
+    if name == "k_compress" and precision == "mixed_solve":
+        # two pipes in one kernel: the projection products in double-float on the FP32 pipe, the
+        # pivoted Gram-Schmidt in FP64; the peak is the rate at which the kernel's own mix of the
+        # two would run if each part ran at its pipe's peak (time-weighted)
+        proj = stats["compress_proj_flops"] / nl
+        gs = flops_pl - proj
+        t_ideal = proj / (pipes["dfl"] * 1e12) + gs / (pipes["fp64"] * 1e12)
+        peak = flops_pl / t_ideal / 1e12 if t_ideal > 0 else pipes["fp64"]
+        src = f"time-weighted blend of the double-float ({pipes['dfl']:.2f}) and FP64 ({pipes['fp64']:.2f}) peaks, {pipes['source']}"
+        parts = {"projection_flops_per_launch": proj, "gram_schmidt_flops_per_launch": gs,
+                 "projection_share_of_flops": proj / max(flops_pl, 1.0)}
+    elif name == "k_compress" and precision == "fp64":
+        peak, src = pipes["fp64"], f"FP64 pipe, {pipes['source']}"
+    elif arith.startswith("double-float GEMM"):
+        peak, src = pipes["dfl"], f"double-float rate of the FP32 pipe (11 instructions per multiply-add), {pipes['source']}"
     elif arith == "FP32":
-        peak, src = FP32_SIMT_TFLOPS, "FP32 CUDA cores from unit counts at 2.07 GHz"
+        peak, src = pipes["fp32"], f"FP32 pipe, {pipes['source']}"
     else:
-        peak, src = FP64_TFLOPS, "nominal FP64 rate of GB300"
+        peak, src = pipes["fp64"], f"FP64 pipe, {pipes['source']}"
     ach = flops_pl / t / 1e12
-    traffic = _traffic(precision, n, name)
-    return {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
-            "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
-            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": traffic, "traffic_unit": "bytes per launch",
-            "achieved_dram_gbs": traffic / t / 1e9 if traffic else None, "peak_source": src}
+    traffic = _traffic(precision, n, name, flops_pl)
+    out = {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
+           "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
+           "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+           "traffic": traffic, "traffic_unit": "bytes per launch",
+           "achieved_dram_gbs": traffic / t / 1e9 if traffic else None, "peak_source": src}
+    if parts:
+        out.update(parts)
+    return out
 
 
-def roofline(stats, precision, peaks, peak_kind, n=0):
+def roofline(stats, precision, peaks, peak_kind, pipes, n=0):
     """Dominant factor kernel (CUDA-event time); `schur` adds the Schur-update kernel, the dense
     contraction of the elimination, against the peak of its own arithmetic."""
     ms = stats["kernel_ms"]
     top = max(range(5), key=lambda i: ms[i])
-    out = _kernel_roofline(stats, precision, top, n)
-    out["schur"] = _kernel_roofline(stats, precision, 2, n)
+    out = _kernel_roofline(stats, precision, top, pipes, n)
+    out["schur"] = _kernel_roofline(stats, precision, 2, pipes, n)
     # the Schur step's algorithmic bytes, for the intensity against HBM
     nl = max(stats["kernel_launches"][2], 1)
     bytes_pl = stats["schur_bytes"] / nl
@@ -312,11 +458,11 @@ def roofline(stats, precision, peaks, peak_kind, n=0):
     sc["intensity_flop_per_byte"] = (stats["kernel_flops"][2] / nl) / max(bytes_pl, 1.0)
     sc["hbm_peak_gbs"] = peaks["hbm_gbs"]
     sc["hbm_peak_source"] = f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
-    # attainable = min(arithmetic peak, intensity x HBM bandwidth); the Schur update's intensity
-    # puts its ridge far above the double-float and FP64 peaks, so the two agree
+    # attainable = min(arithmetic peak, intensity x HBM bandwidth)
     sc["attainable"] = min(sc["peak"], sc["intensity_flop_per_byte"] * peaks["hbm_gbs"] / 1000.0)
     sc["frac_attainable"] = sc["achieved"] / sc["attainable"]
     sc["algorithmic_gbs"] = bytes_pl / (sc["avg_launch_ms"] / 1000.0) / 1e9
+    out["pipes"] = pipes
     return out
 
 
@@ -476,10 +622,12 @@ def run_gpu(args):
                                   precision=precision_code(ifmm, prec),
                                   tau_ref=w["tau_ref"], refine_tol=w["refine_tol"],
                                   refine_maxit=w["refine_maxit"] if prec != "mixed" else 30,
-                                  refine_restart=w["refine_restart"], refine_inner=w["refine_inner"])
+                                  refine_restart=w["refine_restart"], refine_inner=w["refine_inner"],
+                                  tc_products=args.tc_products)
         pts = inputs.uniform_points(replica_seed(w["seed"], rank), N)
         return ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm, stream)
 
+    pipes_measured = measure_pipes()   # before any solver work: the probe runs alone on the GPU
     solver = make_solver(precision)
     h = solver.h
     # manufactured solution x* and b = A~ x* (FP64 FMM matvec), column-major (nrhs, N) buffers
@@ -514,7 +662,7 @@ def run_gpu(args):
     value = whole_job_value(world, N, ms)
     launches_per_step = st["launches_factor"] + st["launches_solve"]
     peaks, peak_kind = load_peaks()
-    rf = roofline(st, precision, peaks, peak_kind, N)
+    rf = roofline(st, precision, peaks, peak_kind, pipe_peaks(pipes_measured), N)
 
     # end to end through the C ABI with host buffers in pinned memory (copies inside the timed region)
     b_pin = torch.empty((nrhs, N), dtype=torch.float64, pin_memory=True)
@@ -570,7 +718,10 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_entry()
+        cpu = cpu_baseline_entry(st["refine_iters"] if N == WORKLOAD["N"] else None)
+        cpu["gpu_over_oracle"] = value / cpu["value"]
+        if "factor_only_value" in cpu:
+            cpu["gpu_factor_over_oracle_factor"] = (N / (st["t_factor_ms"] / 1000.0)) / cpu["factor_only_value"]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
@@ -615,6 +766,9 @@ def main():
                     help="also time one step of the other precision (reported, not the headline)")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-products", type=int, default=0, choices=[0, 1, 2],
+                    help="mixed_solve: tensor-core products in the replay (1), the replay and the Schur "
+                         "update (2), or double-float on the FP32 pipe (0)")
     ap.add_argument("--batch", dest="batch", action="store_true", default=True,
                     help="also time the batched workload of 256 uneven systems (default)")
     ap.add_argument("--no-batch", dest="batch", action="store_false")

@@ -41,7 +41,7 @@ typedef enum {
     IFMM_ERR_SINGULAR_PIVOT = 4, /* a pivot block P2P/P2M (Eqs. P2P(i,k), P2M(i,k)) is singular */
     IFMM_ERR_RANK_OVERFLOW = 5,  /* a box basis needed more than r_cap directions             */
     IFMM_ERR_NOCONV = 6,         /* iterative refinement did not reach refine_tol             */
-    IFMM_ERR_TIMEOUT = 7,        /* reserved: a bounded device wait ran out                   */
+    IFMM_ERR_TIMEOUT = 7,        /* a bounded device wait (on the tensor cores) ran out       */
     IFMM_ERR_STATE = 8           /* call out of order (e.g. solve before factor)              */
 } ifmm_status;
 
@@ -103,6 +103,12 @@ typedef struct {
                              refine_tol, and only an FP64 one ends the solve); <= 0 selects 1e-4    */
     int leaf_max;         /* depth = 0: the build takes the smallest depth whose fullest leaf holds
                              at most leaf_max points (ifmm_auto_depth)                           */
+    int tc_products;      /* IFMM_MIXED_SOLVE, products in FP64 accuracy on the tensor cores (the
+                             digit-split product of ifmm_tc_dgemm): 1 = the replay of the solve
+                             (FP64 vectors; the factors split into digits once, after the
+                             factorisation); 2 = the replay and the Schur-update products of the
+                             elimination; 0 (default) = neither: double-float replay and products
+                             on the FP32 pipe. Range 0..2                                        */
 } ifmm_params;
 
 typedef struct {
@@ -132,7 +138,7 @@ typedef struct {
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
  * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 60, refine_inner 1e-4),
- * leaf_max 64. */
+ * leaf_max 64, tc_products 0. */
 void ifmm_default_params(ifmm_params* p);
 
 /* Smallest depth 2..10 of the uniform quadtree (Section 4.2: boxes of level k form a 2^k x 2^k
@@ -215,6 +221,19 @@ ifmm_status ifmm_matvec(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, 
  * layout and the other errors are those of ifmm_matvec; the call synchronises the handle's
  * stream. */
 ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
+
+/* C = A B in FP64 accuracy on the tensor cores: the product kernel of the Schur-complement update
+ * A[rho, gamma] -= C_rho X_gamma of Algorithm 1 on its own. Each row of A and column of B is scaled
+ * by a power of two and cut into eight 7-bit digits; the 36 digit products of weight <= 7 run as
+ * bf16 tcgen05 MMAs whose FP32 accumulators hold exact integers, combined in 64-bit integer
+ * arithmetic (relative error about 2^-52 of |A| |B|; exact when every entry has at most 53
+ * significant bits within 56 bits of its row's or column's largest entry and the exact products and
+ * sums fit in FP64). A (M x K, leading dimension lda >= K), B (K x N, ldb >= N), C (M x N, ldc >= N): device
+ * pointers, row-major, FP64; C must not overlap A or B. stream: cudaStream_t or NULL; the call
+ * synchronises it. Entries below 2^-1022 are flushed to zero. Errors: INVALID_ARG, CUDA, TIMEOUT
+ * (a bounded wait on the tensor cores ran out; C is then undefined). */
+ifmm_status ifmm_tc_dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                          int M, int N, int K, void* stream);
 
 /* Final ranks of the boxes of one level 2..depth, grid order (ix + 2^level * iy), into the host
  * array out_host (4^level ints). Errors: STATE (not factored), INVALID_ARG. */

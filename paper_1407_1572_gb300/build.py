@@ -67,5 +67,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+MEASURE = os.path.join(HERE, "measure")
+PEAKS_LIB = os.path.join(BUILD, "libifmm_peaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile the pipe-peak probe (measure/pipe_peaks.cu, the roofline denominators of the FP64 and
+    FP32 pipes) into its own library, apart from the solver."""
+    src = os.path.join(MEASURE, "pipe_peaks.cu")
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(src):
+        return PEAKS_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, src]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_peaks(force=True))

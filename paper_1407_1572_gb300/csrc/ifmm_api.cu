@@ -17,6 +17,7 @@
 
 #include "ifmm.h"
 #include "ifmm_internal.h"
+#include "ifmm_tc.cuh"
 
 using namespace ifmm;
 
@@ -62,6 +63,11 @@ struct FLevel {
     // double-float copies of the stored factors (precision IFMM_MIXED_SOLVE) and element counts
     int64_t npi = 0, ncp = 0, nbp = 0;
     dfl* d_Pi2 = nullptr;
+    // digit slabs of the factors for the tensor-core replay (IFMM_MIXED_SOLVE with tc_products)
+    uint8_t* d_slab = nullptr;
+    int* d_srexp = nullptr;
+    int64_t* d_soff = nullptr;
+    int64_t* d_seoff = nullptr;
     dfl* d_Cp2 = nullptr;
     dfl* d_Bp2 = nullptr;
 };
@@ -414,6 +420,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.tau_ref = h->prm.tau_ref == 0 ? 0 : 1;
     v.symmetric = 1;   // every kernel of the library is radial, hence symmetric
     v.gemm_dfl = (std::is_same<T, double>::value && h->prm.precision == IFMM_MIXED_SOLVE) ? 1 : 0;
+    v.gemm_tc = (v.gemm_dfl && h->prm.tc_products >= 2) ? 1 : 0;
     return v;
 }
 
@@ -422,6 +429,12 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
 template <typename T>
 LevelView<T> solve_view(ifmm_handle* h, FLevel& L) {
     LevelView<T> v = view_of<T>(h, L);
+    if (std::is_same<T, double>::value && L.d_slab) {
+        v.sl.slab = L.d_slab;
+        v.sl.rexp = L.d_srexp;
+        v.sl.soff = L.d_soff;
+        v.sl.eoff = L.d_seoff;
+    }
     if (std::is_same<T, dfl>::value) {
         v.Pi = (T*)L.d_Pi2;
         v.Cp = (T*)L.d_Cp2;
@@ -658,7 +671,8 @@ void release_level(ifmm_handle* h, FLevel& L) {
                      (void**)&L.d_cpoff, &L.d_Cp, (void**)&L.d_bpoff, &L.d_Bp, (void**)&L.d_xsoff,
                      (void**)&L.d_xsld, &L.d_Xs, (void**)&L.d_fsoff, &L.d_Fs, &L.d_Fs2, (void**)&L.d_rsoff,
                      &L.d_Rs, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5,
-                     (void**)&L.d_Pi2, (void**)&L.d_Cp2, (void**)&L.d_Bp2};
+                     (void**)&L.d_Pi2, (void**)&L.d_Cp2, (void**)&L.d_Bp2, (void**)&L.d_slab, (void**)&L.d_srexp,
+                     (void**)&L.d_soff, (void**)&L.d_seoff};
     for (void** p : ptrs) {
         dfree(h, *p);
         *p = nullptr;
@@ -687,6 +701,53 @@ ifmm_status split_factors(ifmm_handle* h) {
         launch_split_dfl((const double*)L.d_Cp, L.d_Cp2, L.ncp, h->st);
         CKS(dalloc(h, &L.d_Bp2, sizeof(dfl) * (size_t)std::max<int64_t>(L.nbp, 1)));
         launch_split_dfl((const double*)L.d_Bp, L.d_Bp2, L.nbp, h->st);
+    }
+    CK(cudaGetLastError());
+    return IFMM_OK;
+}
+
+// Digit slabs of every level's factors for the tensor-core replay (IFMM_MIXED_SOLVE, tc_products): the
+// operands of the replay's products split once (ifmm_tc.cuh), twelve per box (kSlabRecs): Pi with
+// rows s and K = n, Pi with rows n and K = s, the C panel of each neighbour direction (rows = the
+// neighbour's width at the elimination, K = n) and the B panels side by side (rows n, K = the sum of
+// the widths). Record sizes follow tc::slab_bytes; the host lays the records out per level.
+ifmm_status presplit_factors(ifmm_handle* h) {
+    for (int k = 2; k <= h->depth; ++k) {
+        FLevel& L = h->lv[k];
+        const int s = L.side;
+        std::vector<int64_t> soff((size_t)L.nb * kSlabRecs, -1), eoff((size_t)L.nb * kSlabRecs, 0);
+        int64_t bytes = 0, exps = 0;
+        auto add = [&](int e, int rec, int rows, int K) {
+            if (rows <= 0 || K <= 0) return;
+            soff[(size_t)e * kSlabRecs + rec] = bytes;
+            eoff[(size_t)e * kSlabRecs + rec] = exps;
+            bytes += tc::slab_bytes(rows, K);
+            exps += (int64_t)((rows + 7) / 8) * 8;
+        };
+        for (int e : L.boxes) {
+            const int n = L.n[e], r = L.r[e], ex = e % s, ey = e / s, ce = (ex % 3) + 3 * (ey % 3);
+            add(e, 0, n + r, n);
+            add(e, 1, n, n + r);
+            int ksum = 0;
+            for (int d = 0; d < 9; ++d) {
+                const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+                if (d == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+                const int q = qx + s * qy, cq = (qx % 3) + 3 * (qy % 3);
+                const int w = cq < ce ? L.r[q] : L.n[q];
+                add(e, 2 + d, w, n);
+                ksum += w;
+            }
+            add(e, 11, n, ksum);
+        }
+        CKS(dalloc(h, &L.d_slab, (size_t)std::max<int64_t>(bytes, 16)));
+        CKS(dalloc(h, &L.d_srexp, sizeof(int) * (size_t)std::max<int64_t>(exps, 1)));
+        CKS(upload(h, &L.d_soff, soff));
+        CKS(upload(h, &L.d_seoff, eoff));
+        LevelView<double> v = view_of<double>(h, L);
+        v.sl.soff = L.d_soff;
+        v.sl.eoff = L.d_seoff;
+        for (int c = 0; c < 9; ++c)
+            launch_presplit(v, L.d_slab, L.d_srexp, L.d_boxes + L.cstart[c], L.cstart[c + 1] - L.cstart[c], c, h->st);
     }
     CK(cudaGetLastError());
     return IFMM_OK;
@@ -744,6 +805,10 @@ ifmm_status factor_impl(ifmm_handle* h) {
         if (hs & DEV_ERR_SINGULAR) {
             h->err = "singular pivot block at level " + std::to_string(k);
             return IFMM_ERR_SINGULAR_PIVOT;
+        }
+        if (hs & DEV_ERR_TIMEOUT) {
+            h->err = "a bounded wait on the tensor cores ran out at level " + std::to_string(k);
+            return IFMM_ERR_TIMEOUT;
         }
         if (hs & DEV_ERR_SIZE) {
             h->err = "the well-separated fill at level " + std::to_string(k) +
@@ -1217,6 +1282,7 @@ void ifmm_default_params(ifmm_params* p) {
     p->refine_restart = 60;
     p->refine_inner = 1e-4;
     p->leaf_max = 64;
+    p->tc_products = 0;
 }
 
 // Smallest depth 2..10 of the uniform tree whose fullest leaf holds at most leaf_max points, with the
@@ -1256,6 +1322,7 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
         return IFMM_ERR_INVALID_ARG;
     if (p->tau_ref < 0 || p->tau_ref > 2) return IFMM_ERR_INVALID_ARG;
     if (p->r_cap > 0 && p->r_cap < p->cheb_p * p->cheb_p) return IFMM_ERR_INVALID_ARG;
+    if (p->tc_products < 0 || p->tc_products > 2) return IFMM_ERR_INVALID_ARG;
     for (int64_t i = 0; i < 2 * N; ++i)
         if (!std::isfinite(pts_host[i])) return IFMM_ERR_INVALID_ARG;
     ifmm_handle* h = new ifmm_handle();
@@ -1295,7 +1362,16 @@ ifmm_status ifmm_factor(ifmm_h h) {
     release_factors(h);
     auto t0 = std::chrono::steady_clock::now();
     ifmm_status s = h->prm.precision == IFMM_MIXED ? factor_impl<float>(h) : factor_impl<double>(h);
-    if ((s == IFMM_OK || s == IFMM_ERR_RANK_OVERFLOW) && h->prm.precision == IFMM_MIXED_SOLVE) {
+    // the double-float replay reads double-float copies of the factors; the tensor-core replay
+    // reads digit slabs of the FP64 factors
+    if ((s == IFMM_OK || s == IFMM_ERR_RANK_OVERFLOW) && h->prm.precision == IFMM_MIXED_SOLVE && h->prm.tc_products) {
+        ifmm_status s2 = presplit_factors(h);
+        if (s2 != IFMM_OK) {
+            h->factored = false;
+            return s2;
+        }
+    }
+    if ((s == IFMM_OK || s == IFMM_ERR_RANK_OVERFLOW) && h->prm.precision == IFMM_MIXED_SOLVE && !h->prm.tc_products) {
         ifmm_status s2 = split_factors(h);
         if (s2 != IFMM_OK) {
             h->factored = false;
@@ -1317,9 +1393,12 @@ ifmm_status ifmm_solve(ifmm_h h, const double* b_dev, double* x_dev, int nrhs, i
     h->err.clear();
     auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launches_so_far();
-    ifmm_status s = h->prm.precision == IFMM_MIXED         ? solve_impl<float>(h, b_dev, x_dev, nrhs, ld)
-                    : h->prm.precision == IFMM_MIXED_SOLVE ? solve_impl<dfl>(h, b_dev, x_dev, nrhs, ld)
-                                                           : solve_impl<double>(h, b_dev, x_dev, nrhs, ld);
+    // IFMM_MIXED_SOLVE replays in double-float on the FP32 pipe, or with FP64 vectors and the replay
+    // products on the tensor cores (tc_products)
+    const bool dfl_replay = h->prm.precision == IFMM_MIXED_SOLVE && !h->prm.tc_products;
+    ifmm_status s = h->prm.precision == IFMM_MIXED ? solve_impl<float>(h, b_dev, x_dev, nrhs, ld)
+                    : dfl_replay                   ? solve_impl<dfl>(h, b_dev, x_dev, nrhs, ld)
+                                                   : solve_impl<double>(h, b_dev, x_dev, nrhs, ld);
     h->stats.launches_solve = launches_so_far() - l0;
     cudaError_t e = cudaStreamSynchronize(h->st);
     if (s == IFMM_OK && e != cudaSuccess) {

@@ -26,6 +26,7 @@
 
 #include "ifmm_common.cuh"
 #include "ifmm_internal.h"
+#include "ifmm_tc.cuh"
 
 namespace ifmm {
 
@@ -381,11 +382,25 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
 // ---------------------------------------------------------------------------------------------
 // k_schur: one (p, q) pair of neighbours of e per block (p, q in N_e; dp == 4 is row M2L_e)
 // ---------------------------------------------------------------------------------------------
-template <typename T, bool DF>
-__global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
+// GM selects the product: 0 = the working precision (FP64 exact extent, or FP32), 1 = double-float
+// on the FP32 pipe, 2 = the tensor cores (ifmm_tc.cuh: digit-split bf16 MMAs, 128 threads, dynamic
+// shared memory and tensor memory taken only by the blocks that multiply)
+template <typename T, int GM>
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
     using Acc = typename AccOf<T>::type;
-    using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
-    __shared__ GS sm[gemm_smem<GS>::value];
+    using GS = std::conditional_t<GM == 1 && std::is_same<T, double>::value, dfl, Acc>;
+    __shared__ GS sm[GM == 2 ? 1 : gemm_smem<GS>::value];
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    auto gemm = [&](int M, int N, int K, auto la, auto lb, auto epi) {
+        if constexpr (GM == 2) {
+            tc::Ctx c;
+            tc::ctx_init(c, tc_smem, L.status);
+            tc::tc_gemm(c, M, N, K, la, lb, epi, blockIdx.z, gridDim.z);
+            tc::ctx_release(c);
+        } else {
+            factor_gemm<T, GM == 1>(L, M, N, K, la, lb, epi, sm, blockIdx.z, gridDim.z);
+        }
+    };
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     const int ex = e % L.side, ey = e / L.side;
@@ -418,10 +433,9 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         // new column y_e in row rho_p: M2P_pe or M2L_pe = -C_p X_y[x rows]
         int ld;
         T* dst = block_at(L, p, e, ld);
-        factor_gemm<T, DF>(
-            L, wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
-            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
+        gemm(wp, r, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+             [&](int i, int j, Acc v) { dst[(size_t)i * ld + j] = (T)(-v); });
         if (threadIdx.x == 0 && blockIdx.z == 0) {
             atomicAdd(&L.counters[0], 2.0 * wp * (double)r * n);
             atomicAdd(&L.counters[1], (double)sizeof(T) * ((double)wp * n + (double)n * r + (double)wp * r));
@@ -437,20 +451,17 @@ __global__ void __launch_bounds__(kThreads) k_schur(LevelView<T> L, const int* b
         int ld, ld2 = 0;
         T* dst = block_at(L, p, q, ld);
         T* dst2 = (L.symmetric && p != q) ? block_at(L, q, p, ld2) : nullptr;
-        factor_gemm<T, DF>(
-            L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
-            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) {
-                dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v);
-                if (dst2) dst2[(size_t)j * ld2 + i] = (T)((Acc)dst2[(size_t)j * ld2 + i] - v);
-            },
-            sm, blockIdx.z, gridDim.z);
+        gemm(wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+             [&](int i, int j, Acc v) {
+                 dst[(size_t)i * ld + j] = (T)((Acc)dst[(size_t)i * ld + j] - v);
+                 if (dst2) dst2[(size_t)j * ld2 + i] = (T)((Acc)dst2[(size_t)j * ld2 + i] - v);
+             });
     } else {
         T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
-        factor_gemm<T, DF>(
-            L, wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
-            [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
-            [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); }, sm, blockIdx.z, gridDim.z);
+        gemm(wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
+             [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
+             [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); });
     }
     if (threadIdx.x == 0 && blockIdx.z == 0) {
         double fl = 2.0 * wp * (double)wq * n;
@@ -895,8 +906,21 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     if (df) k_panel<T, true><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
     else k_panel<T, false><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
     if (ev) cudaEventRecord(ev[2], st);
-    if (df) k_schur<T, true><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
-    else k_schur<T, false><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+    if (df && L.gemm_tc) {
+        // tensor-core products: output tiles of 128 x 32, 82.6 KB of dynamic shared memory
+        static std::atomic<bool> tc_attr{false};
+        if (!tc_attr.load()) {
+            cudaFuncSetAttribute(k_schur<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+            tc_attr.store(true);
+        }
+        const int ttiles = ((L.nmax + tc::kTM - 1) / tc::kTM) * ((L.nmax + tc::kTN - 1) / tc::kTN);
+        const int zt = std::max(1, std::min(ttiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
+        k_schur<T, 2><<<dim3(nboxes, 81, zt), tc::kThreads, tc::kSmemBytes, st>>>(L, boxes, colour);
+    } else if (df) {
+        k_schur<T, 1><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+    } else {
+        k_schur<T, 0><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
     // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax)
@@ -1196,11 +1220,309 @@ void launch_root_apply(const double* Dinv, int M, const T* rhs, T* x, int nrhs, 
 // ---------------------------------------------------------------------------------------------
 // replay: forward over the stored factors, back substitution (Algorithm 2)
 // ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fwd_piv(LevelView<T> L, const int* boxes, const int64_t* yoff, T* vec_k,
-                                                      T* vec_km1, T* vx, int nrhs) {
+// The replay's products in the working precision (a CTA GEMM); the tensor-core replay (FP64
+// vectors, factors split once into digit slabs) is the k_*_slab family below
+template <int GM>
+struct ReplayGemm;
+template <>
+struct ReplayGemm<0> {
+    template <typename T, class LA, class LB, class EPI>
+    static IFMM_DEVINL void run(int M, int N, int K, LA la, LB lb, EPI epi, void* sm, int* status, int tile0,
+                                int tstride) {
+        using Acc = typename AccOf<T>::type;
+        (void)status;
+        cta_gemm<Acc>(M, N, K, la, lb, epi, (Acc*)sm, tile0, tstride);
+    }
+};
+// shared memory of a replay CTA: the CTA GEMM's tiles (GM = 0) or the dynamic tensor-core tiles
+template <typename T, int GM>
+struct ReplaySmem {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    static constexpr int elems = GM == 2 ? 1 : gemm_smem<Acc>::value;
+};
+#define IFMM_REPLAY_SMEM(T, GM)                                                            \
+    __shared__ typename AccOf<T>::type rsm_static[ReplaySmem<T, GM>::elems];               \
+    extern __shared__ __align__(1024) uint8_t rsm_dyn[];                                   \
+    void* rsm = GM == 2 ? (void*)rsm_dyn : (void*)rsm_static;
+// output tile of the replay GEMM (rows x columns) for the split-K reduction
+template <typename T, int GM>
+struct ReplayTile {
+    static constexpr int M = GM == 2 ? tc::kTM : (std::is_same<T, dfl>::value ? 32 : 64);
+    static constexpr int N = GM == 2 ? tc::kTN : (std::is_same<T, dfl>::value ? 32 : 64);
+};
+
+// ---- the tensor-core replay: factors from their digit slabs, vectors split per block -------------
+IFMM_DEVINL int active_width_at(const int* n, const int* r, int side, int q, int colour_e) {
+    const int qx = q % side, qy = q / side;
+    return colour_of(qx, qy) < colour_e ? r[q] : n[q];
+}
+
+// one record's slab and row exponents
+IFMM_DEVINL const uint8_t* slab_of(const SlabSet& S, int e, int rec) {
+    return S.slab + S.soff[(int64_t)e * kSlabRecs + rec];
+}
+IFMM_DEVINL const int* rexp_of(const SlabSet& S, int e, int rec) { return S.rexp + S.eoff[(int64_t)e * kSlabRecs + rec]; }
+
+__global__ void __launch_bounds__(tc::kSlabThreads) k_presplit(LevelView<double> L, uint8_t* slab, int* rexp,
+                                                               const int* boxes, int colour) {
+    const int e = boxes[blockIdx.x];
+    const int rec = blockIdx.y;
+    const int64_t so = L.sl.soff[(int64_t)e * kSlabRecs + rec];
+    if (so < 0) return;
+    uint8_t* sp = slab + so;
+    int* ep = rexp + L.sl.eoff[(int64_t)e * kSlabRecs + rec];
+    const int n = L.n[e], r = L.r[e], s = n + r;
+    const int ex = e % L.side, ey = e / L.side;
+    const double* Pi = L.Pi + L.pioff[e];
+    const int ld = L.pild[e];
+    if (rec == 0) {
+        tc::split_to_slab(s, n, [&](int i, int k) { return Pi[(size_t)i * ld + k]; }, sp, ep);
+    } else if (rec == 1) {
+        tc::split_to_slab(n, s, [&](int i, int k) { return Pi[(size_t)i * ld + k]; }, sp, ep);
+    } else if (rec < 11) {
+        const int d = rec - 2;
+        const int q = (ex + d % 3 - 1) + L.side * (ey + d / 3 - 1);
+        const int w = active_width_at(L.n, L.r, L.side, q, colour);
+        const double* C = L.Cp + L.cpoff[(int64_t)e * 9 + d];
+        tc::split_to_slab(w, n, [&](int i, int k) { return C[(size_t)i * n + k]; }, sp, ep);
+    } else {
+        __shared__ const double* sB[8];
+        __shared__ int sOff[9], sW[8];
+        if (threadIdx.x == 0) {
+            int c = 0, off = 0;
+            for (int d = 0; d < 9; ++d) {
+                if (d == 4) continue;
+                const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+                if (!in_grid(qx, qy, L.side)) continue;
+                const int q = qx + L.side * qy;
+                sB[c] = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+                sW[c] = active_width_at(L.n, L.r, L.side, q, colour);
+                sOff[c] = off;
+                off += sW[c];
+                ++c;
+            }
+            for (int t = c; t < 9; ++t) sOff[t] = off;
+        }
+        __syncthreads();
+        const int K = sOff[8];
+        tc::split_to_slab(n, K, [&](int i, int k) {
+            int c = 0;
+            while (c < 7 && k >= sOff[c + 1]) ++c;
+            return sB[c][(size_t)i * sW[c] + (k - sOff[c])];
+        }, sp, ep);
+    }
+}
+
+void launch_presplit(const LevelView<double>& L, uint8_t* slab, int* rexp, const int* boxes, int nboxes, int colour,
+                     cudaStream_t st) {
+    if (nboxes <= 0) return;
+    k_presplit<<<dim3(nboxes, kSlabRecs), tc::kSlabThreads, 0, st>>>(L, slab, rexp, boxes, colour);
+    count_launches(1);
+}
+
+IFMM_DEVINL int slab_rg(int rows) { return (rows + 7) / 8; }
+
+// The slab kernels are persistent: a grid of at most two blocks per SM walks the items (box, tile
+// group) of the launch, with tensor memory and the mbarrier set up once per block.
+__global__ void __launch_bounds__(tc::kSlabThreads, 2) k_fwd_piv_slab(LevelView<double> L, const int* boxes,
+                                                                     int nboxes, int Z, const int64_t* yoff,
+                                                                     double* vec_k, double* vec_km1, double* vx,
+                                                                     int nrhs) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    tc::Ctx c;
+    tc::ctx_init(c, tsm, L.status);
+    for (int item = blockIdx.x; item < nboxes * Z; item += gridDim.x) {
+        const int e = boxes[item / Z], z = item % Z;
+        const int n = L.n[e], r = L.r[e], s = n + r;
+        if (s == 0) continue;
+        const double* rhs = vec_k + L.voff[e] * nrhs;
+        double* vxe = vx + L.voff[e] * nrhs;
+        double* ze = vec_km1 + yoff[e] * nrhs;
+        // v = Pi [rhs_e; 0]: x rows to vx, z rows become the M2L_e right-hand side
+        tc::tc_gemm_slab(
+            c, slab_of(L.sl, e, 0), rexp_of(L.sl, e, 0), slab_rg(s), 0, s, nrhs, n,
+            [&](int k, int j) { return rhs[(size_t)k * nrhs + j]; },
+            [&](int i, int j, double v) {
+                if (i < n) vxe[(size_t)i * nrhs + j] = v;
+                else ze[(size_t)(i - n) * nrhs + j] = v;
+            },
+            z, Z);
+    }
+    tc::ctx_release(c);
+}
+
+__global__ void __launch_bounds__(tc::kSlabThreads, 2) k_fwd_upd_slab(LevelView<double> L, const int* boxes,
+                                                                     int nboxes, int Z, int colour,
+                                                                     const int64_t* yoff, double* vec_k,
+                                                                     double* vec_km1, const double* vx, int nrhs) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    tc::Ctx c;
+    tc::ctx_init(c, tsm, L.status);
+    for (int item = blockIdx.x; item < nboxes * 8 * Z; item += gridDim.x) {
+        const int e = boxes[item / (8 * Z)];
+        const int dd = (item / Z) % 8, z = item % Z;
+        const int dp = dd < 4 ? dd : dd + 1;      // neighbour directions without 4 (e itself)
+        const int ex = e % L.side, ey = e / L.side;
+        const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
+        if (!in_grid(px, py, L.side)) continue;
+        const int p = px + L.side * py;
+        const bool Ep = colour_of(px, py) < colour;
+        const int wp = Ep ? L.r[p] : L.n[p];
+        const int n = L.n[e];
+        if (wp == 0 || n == 0) continue;
+        const double* v = vx + L.voff[e] * nrhs;
+        double* tgt = Ep ? vec_km1 + yoff[p] * nrhs : vec_k + L.voff[p] * nrhs;
+        tc::tc_gemm_slab(
+            c, slab_of(L.sl, e, 2 + dp), rexp_of(L.sl, e, 2 + dp), slab_rg(wp), 0, wp, nrhs, n,
+            [&](int k, int j) { return v[(size_t)k * nrhs + j]; },
+            [&](int i, int j, double a) { tgt[(size_t)i * nrhs + j] -= a; }, z, Z);
+    }
+    tc::ctx_release(c);
+}
+
+// back substitution, first half, from the slab of the side-by-side B panels; split-K as k_bwd_w
+// (item = box x (tile group tg of zt + zt x K split kz of ks))
+__global__ void __launch_bounds__(tc::kSlabThreads, 2) k_bwd_w_slab(LevelView<double> L, const int* boxes,
+                                                                   int nboxes, int colour, const int64_t* yoff,
+                                                                   const double* rhs_k, const double* x_k,
+                                                                   const double* x_km1, double* wtmp, int nrhs,
+                                                                   int zt, int ks, double* part, int* cnt,
+                                                                   int64_t pstride) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    __shared__ const double* sU[8];
+    __shared__ int sOff[9];
+    __shared__ int s_last;
+    tc::Ctx c;
+    tc::ctx_init(c, tsm, L.status);
+    const int per = zt * ks;
+    constexpr int TM = tc::kTM, TN = tc::kTN;
+    const int tn = (nrhs + TN - 1) / TN;
+    for (int item = blockIdx.x; item < nboxes * per; item += gridDim.x) {
+        const int bi = item / per, zz = item % per;
+        const int e = boxes[bi];
+        const int ex = e % L.side, ey = e / L.side;
+        const int n = L.n[e];
+        const int tg = zz % zt, kz = zz / zt;
+        __syncthreads();   // the previous item's readers of sU / sOff are done
+        if (threadIdx.x == 0) {
+            int cc = 0, off = 0;
+            for (int d = 0; d < 9; ++d) {
+                if (d == 4) continue;
+                const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
+                if (!in_grid(qx, qy, L.side)) continue;
+                const int q = qx + L.side * qy;
+                const bool Eq = colour_of(qx, qy) < colour;
+                sU[cc] = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
+                sOff[cc] = off;
+                off += Eq ? L.r[q] : L.n[q];
+                ++cc;
+            }
+            for (int t = cc; t < 9; ++t) sOff[t] = off;
+        }
+        __syncthreads();
+        if (n == 0) continue;
+        const int K = sOff[8];
+        auto lb = [&](int k, int j) {
+            int cc = 0;
+            while (cc < 7 && k >= sOff[cc + 1]) ++cc;
+            return sU[cc][(size_t)(k - sOff[cc]) * nrhs + j];
+        };
+        double* w = wtmp + L.voff[e] * nrhs;
+        const double* rhs = rhs_k + L.voff[e] * nrhs;
+        const uint8_t* sp = slab_of(L.sl, e, 11);
+        const int* ep = rexp_of(L.sl, e, 11);
+        if (ks == 1) {
+            if (K == 0) {
+                for (int t = threadIdx.x + tg * blockDim.x; t < n * nrhs; t += blockDim.x * zt) w[t] = rhs[t];
+                continue;
+            }
+            tc::tc_gemm_slab(c, sp, ep, slab_rg(n), 0, n, nrhs, K, lb,
+                             [&](int i, int j, double a) { w[(size_t)i * nrhs + j] = rhs[(size_t)i * nrhs + j] - a; },
+                             tg, zt);
+            continue;
+        }
+        const int chunk = (((K + ks - 1) / ks) + 31) & ~31;
+        const int k_lo = min(K, kz * chunk), k_hi = min(K, k_lo + chunk);
+        double* P = part + ((int64_t)kz * nboxes + bi) * pstride;
+        if (k_hi > k_lo) {
+            tc::tc_gemm_slab(c, sp, ep, slab_rg(n), k_lo / tc::kKC, n, nrhs, k_hi - k_lo,
+                             [&](int k, int j) { return lb(k_lo + k, j); },
+                             [&](int i, int j, double a) { P[(size_t)i * nrhs + j] = a; }, tg, zt);
+        } else {
+            for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
+                const int i = t / nrhs, j = t - i * nrhs;
+                if (((i / TM) * tn + j / TN) % zt == tg) P[(size_t)i * nrhs + j] = 0.0;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(&cnt[bi * zt + tg], 1) == ks - 1) ? 1 : 0;
+        __syncthreads();
+        if (!s_last) continue;
+        __threadfence();
+        for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
+            const int i = t / nrhs, j = t - i * nrhs;
+            if (((i / TM) * tn + j / TN) % zt != tg) continue;
+            double a = 0.0;
+            for (int z = 0; z < ks; ++z) a += __ldcg(part + ((int64_t)z * nboxes + bi) * pstride + (size_t)i * nrhs + j);
+            w[(size_t)i * nrhs + j] = rhs[(size_t)i * nrhs + j] - a;
+        }
+        if (threadIdx.x == 0) cnt[bi * zt + tg] = 0;
+    }
+    tc::ctx_release(c);
+}
+
+// back substitution, second half: [x_e; z_e] = Pi [w; y_e] from the slab of Pi's first n rows
+__global__ void __launch_bounds__(tc::kSlabThreads, 2) k_bwd_x_slab(LevelView<double> L, const int* boxes,
+                                                                   int nboxes, int Z, const int64_t* yoff,
+                                                                   double* x_k, const double* x_km1,
+                                                                   const double* wtmp, int nrhs) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    tc::Ctx c;
+    tc::ctx_init(c, tsm, L.status);
+    for (int item = blockIdx.x; item < nboxes * Z; item += gridDim.x) {
+        const int e = boxes[item / Z], z = item % Z;
+        const int n = L.n[e], r = L.r[e], s = n + r;
+        if (n == 0) continue;
+        const double* w = wtmp + L.voff[e] * nrhs;
+        const double* ye = x_km1 + yoff[e] * nrhs;
+        double* xe = x_k + L.voff[e] * nrhs;
+        tc::tc_gemm_slab(
+            c, slab_of(L.sl, e, 1), rexp_of(L.sl, e, 1), slab_rg(n), 0, n, nrhs, s,
+            [&](int k, int j) { return k < n ? w[(size_t)k * nrhs + j] : ye[(size_t)(k - n) * nrhs + j]; },
+            [&](int i, int j, double a) { xe[(size_t)i * nrhs + j] = a; }, z, Z);
+    }
+    tc::ctx_release(c);
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cudaGetLastError();
+        sms = v;
+    }
+    return sms;
+}
+
+void set_slab_smem() {
+    static std::atomic<bool> done{false};
+    if (done.load()) return;
+    cudaFuncSetAttribute(k_fwd_piv_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    cudaFuncSetAttribute(k_fwd_upd_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    cudaFuncSetAttribute(k_bwd_w_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    cudaFuncSetAttribute(k_bwd_x_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    done.store(true);
+}
+
+template <typename T, int GM>
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_fwd_piv(LevelView<T> L, const int* boxes,
+                                                                              const int64_t* yoff, T* vec_k,
+                                                                              T* vec_km1, T* vx, int nrhs) {
+    using Acc = typename AccOf<T>::type;
+    IFMM_REPLAY_SMEM(T, GM)
     const int e = boxes[blockIdx.x];
     const int n = L.n[e], r = L.r[e], s = n + r;
     const T* Pi = L.Pi + L.pioff[e];
@@ -1208,22 +1530,25 @@ __global__ void __launch_bounds__(kThreads) k_fwd_piv(LevelView<T> L, const int*
     const T* rhs = vec_k + L.voff[e] * nrhs;
     T* vxe = vx + L.voff[e] * nrhs;
     T* ze = vec_km1 + yoff[e] * nrhs;
+    if (s == 0) return;
     // v = Pi [rhs_e; 0]: x rows to vx, z rows become the M2L_e right-hand side
-    cta_gemm<Acc>(
+    ReplayGemm<GM>::template run<T>(
         s, nrhs, n, [&](int i, int k) { return Pi[(size_t)i * ld + k]; },
         [&](int k, int j) { return rhs[(size_t)k * nrhs + j]; },
         [&](int i, int j, Acc v) {
             if (i < n) vxe[(size_t)i * nrhs + j] = (T)v;
             else ze[(size_t)(i - n) * nrhs + j] = (T)v;
         },
-        sm, blockIdx.z, gridDim.z);
+        rsm, L.status, blockIdx.z, gridDim.z);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fwd_upd(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
-                                                      T* vec_k, T* vec_km1, const T* vx, int nrhs) {
+template <typename T, int GM>
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_fwd_upd(LevelView<T> L, const int* boxes,
+                                                                              int colour, const int64_t* yoff,
+                                                                              T* vec_k, T* vec_km1, const T* vx,
+                                                                              int nrhs) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    IFMM_REPLAY_SMEM(T, GM)
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y;
     if (dp == 4) return;
@@ -1234,28 +1559,44 @@ __global__ void __launch_bounds__(kThreads) k_fwd_upd(LevelView<T> L, const int*
     const bool Ep = colour_of(px, py) < colour;
     const int wp = Ep ? L.r[p] : L.n[p];
     const int n = L.n[e];
+    if (wp == 0) return;
     const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
     const T* v = vx + L.voff[e] * nrhs;
     T* tgt = Ep ? vec_km1 + yoff[p] * nrhs : vec_k + L.voff[p] * nrhs;
-    cta_gemm<Acc>(
+    ReplayGemm<GM>::template run<T>(
         wp, nrhs, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
         [&](int k, int j) { return v[(size_t)k * nrhs + j]; },
-        [&](int i, int j, Acc a) { tgt[(size_t)i * nrhs + j] = (T)((Acc)tgt[(size_t)i * nrhs + j] - a); }, sm,
-        blockIdx.z, gridDim.z);
+        [&](int i, int j, Acc a) { tgt[(size_t)i * nrhs + j] = (T)((Acc)tgt[(size_t)i * nrhs + j] - a); }, rsm,
+        L.status, blockIdx.z, gridDim.z);
 }
 
 template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st) {
     if (nboxes <= 0) return;
-    const int tw = std::is_same<T, dfl>::value ? 32 : 64;   // output tile of the CTA GEMM
-    const int tr = (nrhs + tw - 1) / tw;
     const int smax = L.nmax + std::min(L.nmax, L.RC);
+    count_launches(2);
+    if constexpr (std::is_same<T, double>::value) {
+        if (L.sl.slab) {
+            constexpr int TM = tc::kTM, TN = tc::kTN;
+            const int tr = (nrhs + TN - 1) / TN;
+            const int z1 = std::max(1, std::min(((smax + TM - 1) / TM) * tr, (304 + nboxes - 1) / nboxes));
+            const int z2 = std::max(1, std::min(((L.nmax + TM - 1) / TM) * tr, (304 + nboxes * 8 - 1) / (nboxes * 8)));
+            set_slab_smem();
+            const int cap = 2 * num_sms();
+            k_fwd_piv_slab<<<std::min(nboxes * z1, cap), tc::kSlabThreads, tc::kSmemBytes, st>>>(
+                L, boxes, nboxes, z1, yoff, vec_k, vec_km1, vx, nrhs);
+            k_fwd_upd_slab<<<std::min(nboxes * 8 * z2, cap), tc::kSlabThreads, tc::kSmemBytes, st>>>(
+                L, boxes, nboxes, z2, colour, yoff, vec_k, vec_km1, vx, nrhs);
+            return;
+        }
+    }
+    const int tw = ReplayTile<T, 0>::M;   // output tile of the CTA GEMM
+    const int tr = (nrhs + tw - 1) / tw;
     const int z1 = std::max(1, std::min(((smax + tw - 1) / tw) * tr, (608 + nboxes - 1) / nboxes));
     const int z2 = std::max(1, std::min(((L.nmax + tw - 1) / tw) * tr, (608 + nboxes * 8 - 1) / (nboxes * 8)));
-    k_fwd_piv<T><<<dim3(nboxes, 1, z1), kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
-    k_fwd_upd<T><<<dim3(nboxes, 9, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
-    count_launches(2);
+    k_fwd_piv<T, 0><<<dim3(nboxes, 1, z1), kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
+    k_fwd_upd<T, 0><<<dim3(nboxes, 9, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
 }
 
 // back substitution, first half: w = rhs_e - sum_q B_q u_q as one GEMM over the concatenated
@@ -1273,12 +1614,15 @@ IFMM_DEVINL dfl ldcg_v(const dfl* p) {
 // zt * K-split kz (of ks). With ks > 1 each CTA writes the partial product over its slice of K to
 // `part`; the last CTA of a tile group (atomic counter) adds the partials in split order, so the
 // result does not depend on the CTAs' timing, and resets the counter.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* boxes, int colour, const int64_t* yoff,
-                                                    const T* rhs_k, const T* x_k, const T* x_km1, T* wtmp, int nrhs,
-                                                    int zt, int ks, T* part, int* cnt, int64_t pstride) {
+template <typename T, int GM>
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_bwd_w(LevelView<T> L, const int* boxes,
+                                                                            int colour, const int64_t* yoff,
+                                                                            const T* rhs_k, const T* x_k,
+                                                                            const T* x_km1, T* wtmp, int nrhs, int zt,
+                                                                            int ks, T* part, int* cnt,
+                                                                            int64_t pstride) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    IFMM_REPLAY_SMEM(T, GM)
     __shared__ const T* sB[8];
     __shared__ const T* sU[8];
     __shared__ int sOff[9], sW[8];
@@ -1322,36 +1666,48 @@ __global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* b
     };
     T* w = wtmp + L.voff[e] * nrhs;
     const T* rhs = rhs_k + L.voff[e] * nrhs;
+    if (n == 0) return;
     if (ks == 1) {
-        cta_gemm<Acc>(
-            n, nrhs, K, la, lb,
-            [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - a); }, sm, tg,
-            zt);
         if (K == 0) {
             for (int t = threadIdx.x + tg * blockDim.x; t < n * nrhs; t += blockDim.x * zt) w[t] = rhs[t];
+            return;
         }
+        ReplayGemm<GM>::template run<T>(
+            n, nrhs, K, la, lb,
+            [&](int i, int j, Acc a) { w[(size_t)i * nrhs + j] = (T)((Acc)rhs[(size_t)i * nrhs + j] - a); }, rsm,
+            L.status, tg, zt);
         return;
     }
     // this split's slice of K (a multiple of 32 long; possibly empty)
     const int chunk = (((K + ks - 1) / ks) + 31) & ~31;
     const int k_lo = min(K, kz * chunk), k_hi = min(K, k_lo + chunk);
     T* P = part + ((int64_t)kz * gridDim.x + blockIdx.x) * pstride;
-    cta_gemm<Acc>(
-        n, nrhs, k_hi - k_lo, [&](int i, int k) { return la(i, k_lo + k); },
-        [&](int k, int j) { return lb(k_lo + k, j); }, [&](int i, int j, Acc a) { P[(size_t)i * nrhs + j] = (T)a; },
-        sm, tg, zt);
+    if (k_hi > k_lo) {
+        ReplayGemm<GM>::template run<T>(
+            n, nrhs, k_hi - k_lo, [&](int i, int k) { return la(i, k_lo + k); },
+            [&](int k, int j) { return lb(k_lo + k, j); },
+            [&](int i, int j, Acc a) { P[(size_t)i * nrhs + j] = (T)a; }, rsm, L.status, tg, zt);
+    } else {
+        // an empty slice contributes zeros to the outputs of this tile group
+        constexpr int TM = ReplayTile<T, GM>::M, TN = ReplayTile<T, GM>::N;
+        const int tn = (nrhs + TN - 1) / TN;
+        for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
+            const int i = t / nrhs, j = t - i * nrhs;
+            if (((i / TM) * tn + j / TN) % zt == tg) P[(size_t)i * nrhs + j] = (T)0;
+        }
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(&cnt[blockIdx.x * zt + tg], 1) == ks - 1) ? 1 : 0;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // outputs of this tile group (the CTA GEMM's tiles: 32 x 32 in double-float, else 64 x 64)
-    constexpr int TW = std::is_same<Acc, dfl>::value ? 32 : 64;
-    const int tn = (nrhs + TW - 1) / TW;
+    // outputs of this tile group (the tiles of the product above)
+    constexpr int TM = ReplayTile<T, GM>::M, TN = ReplayTile<T, GM>::N;
+    const int tn = (nrhs + TN - 1) / TN;
     for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
         const int i = t / nrhs, j = t - i * nrhs;
-        if (((i / TW) * tn + j / TW) % zt != tg) continue;
+        if (((i / TM) * tn + j / TN) % zt != tg) continue;
         Acc acc = (Acc)0;
         for (int z = 0; z < ks; ++z)
             acc = acc + (Acc)ldcg_v(part + ((int64_t)z * gridDim.x + blockIdx.x) * pstride + (size_t)i * nrhs + j);
@@ -1361,11 +1717,13 @@ __global__ void __launch_bounds__(kThreads) k_bwd_w(LevelView<T> L, const int* b
 }
 
 // back substitution, second half: [x_e; z_e] = Pi [w; y_e]; only x_e is kept
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_bwd_x(LevelView<T> L, const int* boxes, const int64_t* yoff, T* x_k,
-                                                    const T* x_km1, const T* wtmp, int nrhs) {
+template <typename T, int GM>
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_bwd_x(LevelView<T> L, const int* boxes,
+                                                                            const int64_t* yoff, T* x_k,
+                                                                            const T* x_km1, const T* wtmp,
+                                                                            int nrhs) {
     using Acc = typename AccOf<T>::type;
-    __shared__ Acc sm[gemm_smem<Acc>::value];
+    IFMM_REPLAY_SMEM(T, GM)
     const int e = boxes[blockIdx.x];
     const int n = L.n[e], r = L.r[e], s = n + r;
     const T* w = wtmp + L.voff[e] * nrhs;
@@ -1373,10 +1731,11 @@ __global__ void __launch_bounds__(kThreads) k_bwd_x(LevelView<T> L, const int* b
     const int ld = L.pild[e];
     const T* ye = x_km1 + yoff[e] * nrhs;
     T* xe = x_k + L.voff[e] * nrhs;
-    cta_gemm<Acc>(
+    if (n == 0) return;
+    ReplayGemm<GM>::template run<T>(
         n, nrhs, s, [&](int i, int k) { return Pi[(size_t)i * ld + k]; },
         [&](int k, int j) { return k < n ? w[(size_t)k * nrhs + j] : ye[(size_t)(k - n) * nrhs + j]; },
-        [&](int i, int j, Acc a) { xe[(size_t)i * nrhs + j] = (T)a; }, sm, blockIdx.z, gridDim.z);
+        [&](int i, int j, Acc a) { xe[(size_t)i * nrhs + j] = (T)a; }, rsm, L.status, blockIdx.z, gridDim.z);
 }
 
 template <typename T>
@@ -1384,8 +1743,11 @@ void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes,
                             const T* rhs_k, T* x_k, const T* x_km1, T* wtmp, int nrhs, T* part, int64_t part_cap,
                             int* cnt, int cnt_cap, cudaStream_t st) {
     if (nboxes <= 0) return;
-    const int tw = std::is_same<T, dfl>::value ? 32 : 64;   // output tile of the CTA GEMM
-    const int z = std::max(1, std::min(((L.nmax + tw - 1) / tw) * ((nrhs + tw - 1) / tw), (608 + nboxes - 1) / nboxes));
+    const bool tcm = std::is_same<T, double>::value && L.sl.slab != nullptr;
+    const int TM = tcm ? ReplayTile<T, 2>::M : ReplayTile<T, 0>::M;
+    const int TN = tcm ? ReplayTile<T, 2>::N : ReplayTile<T, 0>::N;
+    const int cap_ctas = tcm ? 304 : 608;
+    const int z = std::max(1, std::min(((L.nmax + TM - 1) / TM) * ((nrhs + TN - 1) / TN), (cap_ctas + nboxes - 1) / nboxes));
     // few CTAs (upper levels): split K = sum of the neighbours' widths (<= 8 nmax) over more CTAs
     int ks = 1;
     const int64_t pstride = (int64_t)std::max(L.nmax, 1) * nrhs;
@@ -1394,10 +1756,21 @@ void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes,
         ks = std::min(ks, std::max(1, 8 * L.nmax / 64));
         while (ks > 1 && (int64_t)ks * nboxes * pstride > part_cap) --ks;
     }
-    k_bwd_w<T><<<dim3(nboxes, 1, z * ks), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs, z,
-                                                              ks, part, cnt, pstride);
-    k_bwd_x<T><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, yoff, x_k, x_km1, wtmp, nrhs);
     count_launches(2);
+    if constexpr (std::is_same<T, double>::value) {
+        if (tcm) {
+            set_slab_smem();
+            const int cap = 2 * num_sms();
+            k_bwd_w_slab<<<std::min(nboxes * z * ks, cap), tc::kSlabThreads, tc::kSmemBytes, st>>>(
+                L, boxes, nboxes, colour, yoff, rhs_k, x_k, x_km1, wtmp, nrhs, z, ks, part, cnt, pstride);
+            k_bwd_x_slab<<<std::min(nboxes * z, cap), tc::kSlabThreads, tc::kSmemBytes, st>>>(
+                L, boxes, nboxes, z, yoff, x_k, x_km1, wtmp, nrhs);
+            return;
+        }
+    }
+    k_bwd_w<T, 0><<<dim3(nboxes, 1, z * ks), kThreads, 0, st>>>(L, boxes, colour, yoff, rhs_k, x_k, x_km1, wtmp,
+                                                                 nrhs, z, ks, part, cnt, pstride);
+    k_bwd_x<T, 0><<<dim3(nboxes, 1, z), kThreads, 0, st>>>(L, boxes, yoff, x_k, x_km1, wtmp, nrhs);
 }
 
 template <typename T>

@@ -43,7 +43,20 @@ void count_launches(int n);
 long long launches_so_far();
 
 // device status flags (bit set by any block that fails)
-enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_OVERFLOW = 2, DEV_ERR_RANGE = 4, DEV_ERR_SIZE = 8 };
+enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_OVERFLOW = 2, DEV_ERR_RANGE = 4, DEV_ERR_SIZE = 8, DEV_ERR_TIMEOUT = 16 };
+
+// Digit slabs of the stored factors for the tensor-core replay (ifmm_tc.cuh: operands split once,
+// multiplied by every replay), twelve operands per box e: 0 = Pi_e with rows s, K = n (forward
+// replay), 1 = Pi_e with rows n, K = s (back substitution), 2 + d = the C panel of neighbour
+// direction d (rows w_q, K = n), 11 = the B panels of all directions side by side (rows n, K = the
+// sum of the widths). slab == nullptr: no slabs (the replay splits nothing and multiplies as before).
+constexpr int kSlabRecs = 12;
+struct SlabSet {
+    const uint8_t* slab;
+    const int* rexp;
+    const int64_t* soff;   // [nb * kSlabRecs] byte offset of the operand's slab (-1: none)
+    const int64_t* eoff;   // [nb * kSlabRecs] offset of its row exponents
+};
 
 // Device view of one tree level during elimination (Algorithm 1) and replay (Algorithm 2).
 // Box b of level k sits at grid position (b % side, b / side). Its particle unknowns x_b number
@@ -91,6 +104,8 @@ struct LevelView {
     int tau_ref;
     int symmetric;             // kernel symmetric: F_pq = F_qp^T in exact arithmetic
     int gemm_dfl;              // FP64 level data, panel and Schur products in double-float (FP32 pipe)
+    int gemm_tc;               // with gemm_dfl: the Schur products on the tensor cores (ifmm_tc.cuh)
+    SlabSet sl;                // digit slabs of the factors for the tensor-core replay
 };
 
 // Level vectors of the replay: for box b of level k, rows voff[b].. of the level-k vector hold
@@ -124,6 +139,9 @@ void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, c
                        cudaStream_t st);
 template <typename T>
 void launch_level_scale(const LevelView<T>& L, double* out, cudaStream_t st);
+// split the stored factors of the boxes of one colour into digit slabs (L.sl, written)
+void launch_presplit(const LevelView<double>& L, uint8_t* slab, int* rexp, const int* boxes, int nboxes, int colour,
+                     cudaStream_t st);
 template <typename T>
 void launch_root_gather(const LevelView<T>& L2, const int64_t* rootoff, double* D, int M, cudaStream_t st);
 void launch_dense_invert(double* D, int M, int* perm, double* col, int* status, cudaStream_t st);

@@ -32,7 +32,7 @@ class ifmm_params(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
                 ("refine_restart", ctypes.c_int),
                 ("refine_inner", ctypes.c_double),
-                ("leaf_max", ctypes.c_int)]
+                ("leaf_max", ctypes.c_int), ("tc_products", ctypes.c_int)]
 
 
 class ifmm_stats(ctypes.Structure):
@@ -62,8 +62,8 @@ _lib = None
 # every symbol include/ifmm.h declares
 SYMBOLS = ["ifmm_default_params", "ifmm_auto_depth", "ifmm_build", "ifmm_factor", "ifmm_factor_batch",
            "ifmm_solve", "ifmm_solve_T", "ifmm_solve_batch", "ifmm_solve_host",
-           "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_get_ranks", "ifmm_get_stats", "ifmm_last_error",
-           "ifmm_destroy"]
+           "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_tc_dgemm", "ifmm_get_ranks", "ifmm_get_stats",
+           "ifmm_last_error", "ifmm_destroy"]
 
 
 def library_path() -> str:
@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     for name in ("ifmm_solve", "ifmm_solve_T", "ifmm_solve_host", "ifmm_matvec", "ifmm_matvec_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, ip, i64]
         getattr(lib, name).restype = ip
+    lib.ifmm_tc_dgemm.argtypes = [vp, i64, vp, i64, vp, i64, ip, ip, ip, vp]
+    lib.ifmm_tc_dgemm.restype = ip
     lib.ifmm_get_ranks.argtypes = [vp, ip, vp]
     lib.ifmm_get_ranks.restype = ip
     lib.ifmm_get_stats.argtypes = [vp, ctypes.POINTER(ifmm_stats)]
@@ -204,6 +206,12 @@ def ifmm_matvec(h, x_ptr: int, y_ptr: int, nrhs: int, ld: int) -> int:
 def ifmm_matvec_noalloc(h, x_ptr: int, y_ptr: int, nrhs: int, ld: int) -> int:
     """ifmm_matvec without device allocation (fixed 32 MiB scratch compiled into the library)."""
     return _check(h, load().ifmm_matvec_noalloc(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), nrhs, ld))
+
+
+def ifmm_tc_dgemm(a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, M: int, N: int, K: int,
+                  stream: int = 0) -> int:
+    """C = A B (row-major FP64 device arrays) on the tensor cores in FP64 accuracy."""
+    return _check(None, load().ifmm_tc_dgemm(a_ptr, lda, b_ptr, ldb, c_ptr, ldc, M, N, K, stream))
 
 
 def ifmm_get_ranks(h, level: int) -> np.ndarray:

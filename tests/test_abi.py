@@ -29,7 +29,7 @@ def test_default_params_and_struct_layout():
     p = ifmm.default_params()
     assert (p.dim, p.depth, p.cheb_p, p.precision, p.tau_ref) == (2, 3, 4, 0, 1)
     assert p.box[2] == 1.0 and p.eps == 1e-10 and p.refine_maxit == 100 and p.refine_restart == 60
-    assert p.refine_inner == 1e-4 and p.leaf_max == 64
+    assert p.refine_inner == 1e-4 and p.leaf_max == 64 and p.tc_products == 0
     # host-side argument checks reject bad input without touching a device
     h = ctypes.c_void_p()
     lib = ifmm.load()
@@ -52,7 +52,7 @@ def test_default_params_and_struct_layout():
     (dict(kparam=(0.0,)), 1, 4), (dict(kparam=(-1.0,)), 3, 4), (dict(kparam=(0.0,)), 5, 4),
     (dict(eps=-1e-6), 0, 4), (dict(diag=float("inf")), 0, 4), (dict(precision=3), 0, 4),
     (dict(tau_ref=3), 0, 4), (dict(r_cap=8), 0, 4), (dict(refine_restart=201), 0, 4),
-    (dict(refine_restart=-1), 0, 4), (dict(), 0, 0),
+    (dict(refine_restart=-1), 0, 4), (dict(tc_products=3), 0, 4), (dict(tc_products=-1), 0, 4), (dict(), 0, 0),
 ])
 def test_build_rejects_each_out_of_range_argument_on_the_host(change, kernel, n):
     """Every range ifmm.h states for ifmm_build is checked before any device call: the call returns

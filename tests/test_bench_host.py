@@ -18,50 +18,64 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 PEAKS = {"hbm_gbs": 6785.9}
+PIPES = bench.pipe_peaks({"fp64_tflops": 1.25, "fp32_tflops": 78.3})
 
 
 def _stats():
     # five factor kernels in the order k_pivot, k_panel, k_schur, k_compress, k_redirect
     return {"kernel_ms": [100.0, 50.0, 180.0, 250.0, 40.0], "kernel_launches": [54, 54, 54, 54, 54],
-            "kernel_flops": [1e11, 2e11, 3.9e11, 1.6e11, 5e10], "schur_bytes": 1.0e11}
+            "kernel_flops": [1e11, 2e11, 3.9e11, 1.6e11, 5e10], "schur_bytes": 1.0e11,
+            "compress_proj_flops": 1.2e11}
+
+
+def test_pipe_peaks_derive_the_double_float_rate_from_the_fp32_rate():
+    assert PIPES["dfl"] == 78.3 / 11.0 and PIPES["fp64"] == 1.25 and PIPES["source"].startswith("measured")
+    nominal = bench.pipe_peaks(None)
+    assert nominal["source"].startswith("nominal") and math.isclose(nominal["fp32"], 152 * 128 * 2 * 2.07e-3)
 
 
 def test_roofline_picks_the_dominant_kernel_and_divides_by_its_own_peak():
-    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", n=4096)
+    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", PIPES, n=4096)
     assert rf["kernel"] == "k_compress"
     t = 250.0 / 54 / 1000.0
     assert math.isclose(rf["achieved"], 1.6e11 / 54 / t / 1e12, rel_tol=1e-12)
-    assert rf["peak"] == bench.FP64_TFLOPS and math.isclose(rf["frac"], rf["achieved"] / rf["peak"])
+    # two pipes: the projection (1.2e11 flops) in double-float, the Gram-Schmidt (4e10) in FP64;
+    # the peak is the rate of that mix with each part at its own pipe's peak
+    t_ideal = 1.2e11 / 54 / (PIPES["dfl"] * 1e12) + 0.4e11 / 54 / (PIPES["fp64"] * 1e12)
+    assert math.isclose(rf["peak"], 1.6e11 / 54 / t_ideal / 1e12, rel_tol=1e-12)
+    assert math.isclose(rf["frac"], rf["achieved"] / rf["peak"])
+    assert math.isclose(rf["projection_share_of_flops"], 0.75)
     sc = rf["schur"]
-    assert sc["kernel"] == "k_schur" and sc["peak"] == bench.DFL_TFLOPS
+    assert sc["kernel"] == "k_schur" and sc["peak"] == PIPES["dfl"]
     ai = 3.9e11 / 1.0e11
     assert math.isclose(sc["intensity_flop_per_byte"], ai)
-    assert math.isclose(sc["attainable"], min(bench.DFL_TFLOPS, ai * PEAKS["hbm_gbs"] / 1000.0))
+    assert math.isclose(sc["attainable"], min(PIPES["dfl"], ai * PEAKS["hbm_gbs"] / 1000.0))
     assert math.isclose(sc["frac_attainable"], sc["achieved"] / sc["attainable"])
     assert math.isclose(sc["algorithmic_gbs"], 1.0e11 / 54 / (180.0 / 54 / 1000.0) / 1e9)
-    # no capture was taken at this size: no traffic
+    # no capture of the current sources: no traffic
     assert rf["traffic"] is None and rf["achieved_dram_gbs"] is None
 
 
 def test_roofline_in_fp64_uses_the_fp64_peak_everywhere():
-    rf = bench.roofline(_stats(), "fp64", PEAKS, "measured", n=4096)
-    assert rf["peak"] == bench.FP64_TFLOPS and rf["schur"]["peak"] == bench.FP64_TFLOPS
+    rf = bench.roofline(_stats(), "fp64", PEAKS, "measured", PIPES, n=4096)
+    assert rf["peak"] == PIPES["fp64"] and rf["schur"]["peak"] == PIPES["fp64"]
     # the Schur update's ridge lies above the FP64 peak, so the attainable roofline is that peak
-    assert rf["schur"]["attainable"] == bench.FP64_TFLOPS
+    assert rf["schur"]["attainable"] == PIPES["fp64"]
 
 
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    """A bounded capture's DRAM bytes per launch, scaled by the kernel's flops per launch, while the
+    kernel sources hash as they did when it was taken; null once a source differs."""
     csrc = os.path.join(ROOT, "paper_1407_1572_gb300", "csrc")
-    now = {f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() for f in bench.TRAFFIC_SRC}
+    files = ["ifmm_factor.cu", "ifmm_common.cuh"]
+    now = {f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() for f in files}
     monkeypatch.setattr(bench, "TRAFFIC_SRC", now)
-    key = next(iter(bench.TRAFFIC))
-    name = next(iter(bench.TRAFFIC[key]))
-    assert bench._traffic(key[0], key[1], name) == bench.TRAFFIC[key][name]
-    assert bench._traffic(key[0], key[1] // 4, name) is None            # another size
-    stale = dict(now)
-    stale[next(iter(stale))] = "0" * 64
-    monkeypatch.setattr(bench, "TRAFFIC_SRC", stale)
-    assert bench._traffic(key[0], key[1], name) is None                 # the kernel changed
+    monkeypatch.setattr(bench, "TRAFFIC", {("mixed_solve", "k_compress"): {"bytes_per_launch": 2.0e8,
+                                                                           "flops_per_launch": 1.0e9}})
+    assert bench._traffic("mixed_solve", 0, "k_compress", 4.0e9) == 8.0e8
+    assert bench._traffic("fp64", 0, "k_compress", 4.0e9) is None
+    monkeypatch.setattr(bench, "TRAFFIC_SRC", {f: "0" * 64 for f in files})
+    assert bench._traffic("mixed_solve", 0, "k_compress", 4.0e9) is None
 
 
 def test_replica_seeds_differ_per_rank_and_the_value_counts_every_rank():
@@ -102,7 +116,8 @@ def test_oracle_step_reports_its_phases_and_the_host_cpu():
     w = dict(bench.CPU_SAMPLE, N=1024, depth=2, nrhs=2)
     parts = {}
     dt, err = bench.oracle_step(w, threads=1, parts=parts)
-    assert err < 1e-6 and set(parts) == {"t_build_s", "t_factor_s", "t_solve_s"}
+    assert err < 1e-6 and set(parts) == {"t_build_s", "t_factor_s", "t_solve_s", "gmres_iters"}
+    assert parts["gmres_iters"] >= 1
     assert math.isclose(parts["t_factor_s"] + parts["t_solve_s"], dt, rel_tol=1e-9)
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
 

@@ -27,11 +27,11 @@ def ifmm():
 
 
 def _gpu(ifmm, pts, depth, p, eps, kernel=0, diag=None, precision=0, tau_ref=1, refine_tol=0.0, kparam=(0.0,),
-         r_cap=0):
+         r_cap=0, tc_products=0):
     N = pts.shape[0]
     prm = ifmm.default_params(depth=depth, cheb_p=p, eps=eps, diag=math.sqrt(N) if diag is None else diag,
                               precision=precision, tau_ref=tau_ref, refine_tol=refine_tol, refine_maxit=40,
-                              kparam=kparam, r_cap=r_cap)
+                              kparam=kparam, r_cap=r_cap, tc_products=tc_products)
     return ifmm.IFMM(pts, kernel, prm)
 
 
@@ -269,7 +269,7 @@ def test_double_float_replay_of_fp64_factors(ifmm):
     N, depth, p, eps = 4096, 3, 4, 1e-6
     pts = inputs.uniform_points(1407, N)
     g64 = _gpu(ifmm, pts, depth, p, eps, precision=0)
-    g32 = _gpu(ifmm, pts, depth, p, eps, precision=2)
+    g32 = _gpu(ifmm, pts, depth, p, eps, precision=2, tc_products=0)
     g64.factor()
     g32.factor()
     for k in range(2, depth + 1):
@@ -280,6 +280,31 @@ def test_double_float_replay_of_fp64_factors(ifmm):
     d = _rel(x32, x64)
     print(f"double-float replay vs FP64 replay: {d:.2e}")
     assert d <= 1e-8
+
+
+def test_tensor_core_products_match_double_float(ifmm):
+    """IFMM_MIXED_SOLVE with the replay and the Schur products on the tensor cores (digit-split bf16
+    MMAs, about 2^-52 of |C| |X|; tc_products 2) against the same mode with double-float products
+    and replay (about 2^-48; tc_products 0) and against IFMM_FP64: all are FP64-accurate products of
+    the same elimination, so box ranks agree to within one (a direction at the threshold may flip)
+    and the unrefined solves agree to 1e-8, as the double-float replay agrees with the FP64 one."""
+    N, depth, p, eps = 16384, 4, 4, 1e-6
+    pts = inputs.uniform_points(1413, N)
+    b = inputs.rhs(71, N, 4)
+    xs = {}
+    for tag, prec, tcp in (("tc", 2, 2), ("tc_replay", 2, 1), ("dfl", 2, 0), ("fp64", 0, 1)):
+        prm = ifmm.default_params(depth=depth, cheb_p=p, eps=eps, diag=math.sqrt(N), precision=prec, tau_ref=1,
+                                  tc_products=tcp)
+        g = ifmm.IFMM(pts, 0, prm)
+        g.factor()
+        xs[tag] = (g.solve(_t(b)).cpu().numpy(), [g.ranks(k) for k in range(2, depth + 1)])
+        g.close()
+    for other in ("tc_replay", "dfl", "fp64"):
+        for ra, rb in zip(xs["tc"][1], xs[other][1]):
+            assert np.abs(ra - rb).max() <= 1
+        d = _maxrel(xs["tc"][0], xs[other][0])
+        print(f"tensor-core products vs {other}: {d:.2e}")
+        assert d <= 1e-8
 
 
 def _oracle_refined(o, b, tol=1e-12, maxit=60):
