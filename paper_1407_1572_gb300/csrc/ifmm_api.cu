@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <atomic>
 #include <thread>
 #include <type_traits>
 #include <string>
@@ -56,6 +57,9 @@ struct FLevel {
     void* d_Fs2 = nullptr;
     int64_t* d_rsoff = nullptr;
     void* d_Rs = nullptr;
+    int64_t* d_cwsoff = nullptr;
+    double* d_Cws = nullptr;
+    int64_t ps_max = 0;   // largest per-colour sum of s^2 (the FP64 pivot workspace's size)
     double* d_pws = nullptr;
     int64_t* d_psoff = nullptr;
     int* d_boxes = nullptr;
@@ -413,6 +417,7 @@ LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     v.xsoff = L.d_xsoff; v.xsld = L.d_xsld; v.Xs = (T*)L.d_Xs;
     v.fsoff = L.d_fsoff; v.Fs = (T*)L.d_Fs; v.Fs2 = (T*)L.d_Fs2;
     v.rsoff = L.d_rsoff; v.Rs = (T*)L.d_Rs;
+    v.cwsoff = L.d_cwsoff; v.Cws = L.d_Cws;
     v.pws = L.d_pws; v.psoff = L.d_psoff;
     v.status = h->d_status; v.counters = h->d_counters;
     v.eps = h->prm.eps;
@@ -553,11 +558,11 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
         L.cstart[9] = nact;
     }
     // per-colour scratch
-    std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * 81, 0), rsoff((size_t)nb * 9, 0);
+    std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * 81, 0), rsoff((size_t)nb * 9, 0), cwsoff((size_t)nb * 9, 0);
     std::vector<int> xsld(nb, 0);
-    int64_t xs_max = 0, fs_max = 0, rs_max = 0, ps_max = 0;
+    int64_t xs_max = 0, fs_max = 0, rs_max = 0, ps_max = 0, cw_max = 0;
     for (int c = 0; c < 9; ++c) {
-        int64_t xo = 0, fo = 0, ro = 0, pso = 0;
+        int64_t xo = 0, fo = 0, ro = 0, pso = 0, cwo = 0;
         for (int t = L.cstart[c]; t < L.cstart[c + 1]; ++t) {
             int e = L.boxes[t], ex = e % s, ey = e / s;
             int sm = L.n[e] + cap[e];
@@ -592,11 +597,16 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
                 }
                 rsoff[(size_t)e * 9 + dq] = ro;
                 ro += (int64_t)L.n[qx + s * qy] * mb;
+                // the compression's work arrays: the basis vector (n_q), 8 x RC coefficients, m norms,
+                // the basis vector again in the column arithmetic's type (n_q)
+                cwsoff[(size_t)e * 9 + dq] = cwo;
+                cwo += 2 * (int64_t)L.n[qx + s * qy] + 8 * (int64_t)L.RC + mb;
             }
         }
         xs_max = std::max(xs_max, xo);
         fs_max = std::max(fs_max, fo);
         rs_max = std::max(rs_max, ro);
+        cw_max = std::max(cw_max, cwo);
         ps_max = std::max(ps_max, pso);
     }
     size_t es = sizeof(T);
@@ -627,9 +637,12 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     CKS(dalloc(h, &L.d_Fs2, es * (size_t)fs_max));
     CKS(upload(h, &L.d_rsoff, rsoff));
     CKS(dalloc(h, &L.d_Rs, es * (size_t)rs_max));
+    CKS(upload(h, &L.d_cwsoff, cwsoff));
+    CKS(dalloc(h, &L.d_Cws, sizeof(double) * (size_t)std::max<int64_t>(cw_max, 1)));
     CKS(upload(h, &L.d_psoff, psoff));
     // FP64 pivot workspace in global memory for blocks whose matrix does not fit in shared memory
     // (single block per box) or whose cluster slabs do not (8-block clusters)
+    L.ps_max = ps_max;
     if ((size_t)L.smax * L.smax * 8 > 150 * 1024) CKS(dalloc(h, &L.d_pws, sizeof(double) * (size_t)ps_max));
     CKS(upload(h, &L.d_boxes, L.boxes));
     if (k < kap) CKS(upload(h, &L.d_xoff5, L.xoff5));
@@ -662,6 +675,7 @@ void free_level_work(ifmm_handle* h, FLevel& L) {
     dfree_ptr(h, L.d_Fs);
     dfree_ptr(h, L.d_Fs2);
     dfree_ptr(h, L.d_Rs);
+    dfree_ptr(h, L.d_Cws);
     dfree_ptr(h, L.d_pws);
 }
 
@@ -670,7 +684,7 @@ void release_level(ifmm_handle* h, FLevel& L) {
                      (void**)&L.d_bld, &L.d_blk, &L.d_W, (void**)&L.d_pioff, (void**)&L.d_pild, &L.d_Pi,
                      (void**)&L.d_cpoff, &L.d_Cp, (void**)&L.d_bpoff, &L.d_Bp, (void**)&L.d_xsoff,
                      (void**)&L.d_xsld, &L.d_Xs, (void**)&L.d_fsoff, &L.d_Fs, &L.d_Fs2, (void**)&L.d_rsoff,
-                     &L.d_Rs, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5,
+                     &L.d_Rs, (void**)&L.d_cwsoff, (void**)&L.d_Cws, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5,
                      (void**)&L.d_Pi2, (void**)&L.d_Cp2, (void**)&L.d_Bp2, (void**)&L.d_slab, (void**)&L.d_srexp,
                      (void**)&L.d_soff, (void**)&L.d_seoff};
     for (void** p : ptrs) {
@@ -753,69 +767,59 @@ ifmm_status presplit_factors(ifmm_handle* h) {
     return IFMM_OK;
 }
 
+// A factorisation in phases, so that a batch of systems can run its levels in lockstep (factor_fused):
+// factor_begin; per level k = depth..2: factor_level_setup, the colours' launches, factor_level_end;
+// factor_finish (the level-1 system). factor_impl runs them for one system.
 template <typename T>
-ifmm_status factor_impl(ifmm_handle* h) {
-    const int kap = h->depth;
-    h->lv.assign(kap + 1, FLevel());
+ifmm_status factor_begin(ifmm_handle* h) {
+    h->lv.assign(h->depth + 1, FLevel());
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
     CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
     for (int k = 0; k < 16; ++k) h->stats.level_ms[k] = 0.0;
-    const long long l0 = launches_so_far();
-    std::vector<cudaEvent_t> ev(9 * 6);
-    for (auto& e : ev) CK(cudaEventCreate(&e));
-    struct EvGuard {
-        std::vector<cudaEvent_t>& v;
-        ~EvGuard() { for (auto e : v) cudaEventDestroy(e); }
-    } evg{ev};
-    double kms[5] = {0, 0, 0, 0, 0};
-    int kl[5] = {0, 0, 0, 0, 0};
-    for (int k = kap; k >= 2; --k) {
-        CKS(setup_level<T>(h, k));
-        if (k < kap) {
-            CK(cudaStreamSynchronize(h->st));
-            free_level_work<T>(h, h->lv[k + 1]);
-        }
-        FLevel& L = h->lv[k];
-        LevelView<T> v = view_of<T>(h, L);
-        bool used[9] = {false};
-        for (int c = 0; c < 9; ++c) {
-            int cnt = L.cstart[c + 1] - L.cstart[c];
-            if (cnt <= 0) continue;
-            launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->in_batch ? 0 : 1, h->st,
-                                    &ev[c * 6]);
-            used[c] = true;
-        }
-        CK(cudaGetLastError());
-        int hs = 0;
-        CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaMemcpyAsync(L.r.data(), L.d_r, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        double lms = 0.0;
-        for (int c = 0; c < 9; ++c) {
-            if (!used[c]) continue;
-            for (int t = 0; t < 5; ++t) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, ev[c * 6 + t], ev[c * 6 + t + 1]));
-                kms[t] += ms;
-                kl[t] += 1;
-                lms += ms;
-            }
-        }
-        if (k < 16) h->stats.level_ms[k] = lms;
-        if (hs & DEV_ERR_SINGULAR) {
-            h->err = "singular pivot block at level " + std::to_string(k);
-            return IFMM_ERR_SINGULAR_PIVOT;
-        }
-        if (hs & DEV_ERR_TIMEOUT) {
-            h->err = "a bounded wait on the tensor cores ran out at level " + std::to_string(k);
-            return IFMM_ERR_TIMEOUT;
-        }
-        if (hs & DEV_ERR_SIZE) {
-            h->err = "the well-separated fill at level " + std::to_string(k) +
-                     " is wider than the compression's shared-memory arrays";
-            return IFMM_ERR_INVALID_ARG;
-        }
+    for (int t = 0; t < 5; ++t) {
+        h->stats.kernel_ms[t] = 0.0;
+        h->stats.kernel_launches[t] = 0;
     }
+    return IFMM_OK;
+}
+
+template <typename T>
+ifmm_status factor_level_setup(ifmm_handle* h, int k) {
+    CKS(setup_level<T>(h, k));
+    if (k < h->depth) {
+        CK(cudaStreamSynchronize(h->st));
+        free_level_work<T>(h, h->lv[k + 1]);
+    }
+    return IFMM_OK;
+}
+
+// status and ranks of level k after its colours ran (a stream synchronisation)
+template <typename T>
+ifmm_status factor_level_end(ifmm_handle* h, int k) {
+    FLevel& L = h->lv[k];
+    CK(cudaGetLastError());
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(L.r.data(), L.d_r, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (hs & DEV_ERR_SINGULAR) {
+        h->err = "singular pivot block at level " + std::to_string(k);
+        return IFMM_ERR_SINGULAR_PIVOT;
+    }
+    if (hs & DEV_ERR_TIMEOUT) {
+        h->err = "a bounded wait on the tensor cores ran out at level " + std::to_string(k);
+        return IFMM_ERR_TIMEOUT;
+    }
+    if (hs & DEV_ERR_SIZE) {
+        h->err = "the well-separated fill at level " + std::to_string(k) +
+                 " is wider than the compression's shared-memory arrays";
+        return IFMM_ERR_INVALID_ARG;
+    }
+    return IFMM_OK;
+}
+
+template <typename T>
+ifmm_status factor_finish(ifmm_handle* h, long long l0) {
     // level 1: dense system over the level-2 multipoles
     FLevel& L2 = h->lv[2];
     L2.yoff.assign(L2.nb, 0);
@@ -849,18 +853,14 @@ ifmm_status factor_impl(ifmm_handle* h) {
         return IFMM_ERR_SINGULAR_PIVOT;
     }
     int maxr = 0;
-    for (int k = 2; k <= kap; ++k)
+    for (int k = 2; k <= h->depth; ++k)
         for (int b = 0; b < h->lv[k].nb; ++b) maxr = std::max(maxr, h->lv[k].r[b]);
     h->stats.max_rank = maxr;
     h->stats.schur_flops = cnt[0];
     h->stats.schur_bytes = cnt[1];
     h->stats.factor_flops = cnt[2] + 2.0 * (double)M * M * M;
     const int fidx[5] = {3, 4, 0, 5, 6};
-    for (int t = 0; t < 5; ++t) {
-        h->stats.kernel_ms[t] = kms[t];
-        h->stats.kernel_launches[t] = kl[t];
-        h->stats.kernel_flops[t] = cnt[fidx[t]];
-    }
+    for (int t = 0; t < 5; ++t) h->stats.kernel_flops[t] = cnt[fidx[t]];
     h->stats.compress_proj_flops = cnt[7];
     h->stats.launches_factor = launches_so_far() - l0;
     h->stats.rank_overflows = 0;
@@ -871,6 +871,187 @@ ifmm_status factor_impl(ifmm_handle* h) {
         return IFMM_ERR_RANK_OVERFLOW;
     }
     return IFMM_OK;
+}
+
+template <typename T>
+ifmm_status factor_impl(ifmm_handle* h) {
+    const int kap = h->depth;
+    CKS(factor_begin<T>(h));
+    const long long l0 = launches_so_far();
+    std::vector<cudaEvent_t> ev(9 * 6);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    struct EvGuard {
+        std::vector<cudaEvent_t>& v;
+        ~EvGuard() { for (auto e : v) cudaEventDestroy(e); }
+    } evg{ev};
+    for (int k = kap; k >= 2; --k) {
+        CKS(factor_level_setup<T>(h, k));
+        FLevel& L = h->lv[k];
+        LevelView<T> v = view_of<T>(h, L);
+        bool used[9] = {false};
+        for (int c = 0; c < 9; ++c) {
+            int cnt = L.cstart[c + 1] - L.cstart[c];
+            if (cnt <= 0) continue;
+            launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->in_batch ? 0 : 1, h->st,
+                                    &ev[c * 6]);
+            used[c] = true;
+        }
+        CKS(factor_level_end<T>(h, k));
+        double lms = 0.0;
+        for (int c = 0; c < 9; ++c) {
+            if (!used[c]) continue;
+            for (int t = 0; t < 5; ++t) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev[c * 6 + t], ev[c * 6 + t + 1]));
+                h->stats.kernel_ms[t] += ms;
+                h->stats.kernel_launches[t] += 1;
+                lms += ms;
+            }
+        }
+        if (k < 16) h->stats.level_ms[k] = lms;
+    }
+    return factor_finish<T>(h, l0);
+}
+
+// Worker threads run one function per system (index i of `idx`); returns after all finished.
+template <class F>
+void for_each_system(const std::vector<int>& idx, int workers, F fn) {
+    if (idx.empty()) return;
+    workers = std::max(1, std::min<int>(workers, (int)idx.size()));
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w)
+        pool.emplace_back([&]() {
+            for (int t; (t = next.fetch_add(1)) < (int)idx.size();) fn(idx[t]);
+        });
+    for (auto& t : pool) t.join();
+}
+
+// Batched factorisation in lockstep (no counterpart in the paper, which eliminates one system):
+// step t eliminates level depth_s - t of every system s that has it, and every colour of that step is
+// one launch of each factor kernel over the boxes of all those systems together (a global list of
+// (system, box) items; each block reads its system's level view from device memory), on the
+// batch's own stream. Per-system work (level set-up, status and rank read-back, the level-1 system)
+// runs on the systems' streams in worker threads. Same device and precision for every handle.
+template <typename T>
+ifmm_status factor_fused(ifmm_h* hs, int n, int workers, ifmm_status* st_out) {
+    std::vector<ifmm_status> st(n, IFMM_OK);
+    const int dev = hs[0]->device;
+    cudaStream_t B = nullptr;
+    if (cudaStreamCreateWithFlags(&B, cudaStreamNonBlocking) != cudaSuccess) return IFMM_ERR_CUDA;
+    std::vector<cudaEvent_t> evs(n, nullptr);
+    cudaEvent_t evB = nullptr;
+    cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
+    for (auto& e : evs) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    const long long l0 = launches_so_far();
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    auto on_dev = [&](auto fn) { return [&, fn](int i) { cudaSetDevice(dev); fn(i); }; };
+    for_each_system(all, workers, on_dev([&](int i) {
+        hs[i]->err.clear();
+        release_factors(hs[i]);
+        st[i] = factor_begin<T>(hs[i]);
+    }));
+    int maxd = 0;
+    for (int i = 0; i < n; ++i) maxd = std::max(maxd, hs[i]->depth);
+    ifmm_handle* h0 = hs[0];
+    for (int t = 0; maxd - t >= 2; ++t) {
+        std::vector<int> act;
+        for (int i = 0; i < n; ++i)
+            if (st[i] == IFMM_OK && hs[i]->depth - t >= 2) act.push_back(i);
+        if (act.empty()) break;
+        for_each_system(act, workers, on_dev([&](int i) {
+            ifmm_handle* h = hs[i];
+            st[i] = factor_level_setup<T>(h, h->depth - t);
+            if (st[i] == IFMM_OK) cudaEventRecord(evs[i], h->st);
+        }));
+        std::vector<int> ok;
+        for (int i : act)
+            if (st[i] == IFMM_OK) ok.push_back(i);
+        if (ok.empty()) continue;
+        // launch sizes over the batch: the largest pivot, box and rank cap
+        int smax = 0, nmax = 0, rc = 0, rep = ok[0];
+        for (int i : ok) {
+            const FLevel& L = hs[i]->lv[hs[i]->depth - t];
+            if (L.smax > smax) { smax = L.smax; rep = i; }
+            for (int b : L.boxes) nmax = std::max(nmax, L.n[b]);
+            rc = std::max(rc, L.RC);
+        }
+        // blocks whose pivot slab lives in the FP64 workspace need it in every system of the launch
+        if ((size_t)smax * smax * 8 > 150 * 1024)
+            for (int i : ok) {
+                FLevel& L = hs[i]->lv[hs[i]->depth - t];
+                if (!L.d_pws && dalloc(hs[i], &L.d_pws, sizeof(double) * (size_t)std::max<int64_t>(L.ps_max, 1)) != IFMM_OK)
+                    st[i] = IFMM_ERR_OOM;
+                cudaEventRecord(evs[i], hs[i]->st);
+            }
+        std::vector<LevelView<T>> views;
+        std::vector<int> vi(n, -1);
+        for (int i : ok) {
+            if (st[i] != IFMM_OK) continue;
+            vi[i] = (int)views.size();
+            views.push_back(view_of<T>(hs[i], hs[i]->lv[hs[i]->depth - t]));
+        }
+        if (views.empty()) continue;
+        std::vector<int2> items;
+        int cstart[10];
+        for (int c = 0; c < 9; ++c) {
+            cstart[c] = (int)items.size();
+            for (int i : ok) {
+                if (vi[i] < 0) continue;
+                const FLevel& L = hs[i]->lv[hs[i]->depth - t];
+                for (int q = L.cstart[c]; q < L.cstart[c + 1]; ++q) items.push_back(make_int2(vi[i], L.boxes[q]));
+            }
+        }
+        cstart[9] = (int)items.size();
+        for (int i : ok)
+            if (vi[i] >= 0) cudaStreamWaitEvent(B, evs[i], 0);
+        LevelView<T>* d_views = nullptr;
+        int2* d_items = nullptr;
+        ifmm_status s0 = IFMM_OK;
+        if (cudaMallocAsync((void**)&d_views, sizeof(LevelView<T>) * views.size(), B) != cudaSuccess ||
+            cudaMallocAsync((void**)&d_items, sizeof(int2) * std::max<size_t>(items.size(), 1), B) != cudaSuccess)
+            s0 = IFMM_ERR_OOM;
+        if (s0 == IFMM_OK) {
+            cudaMemcpyAsync(d_views, views.data(), sizeof(LevelView<T>) * views.size(), cudaMemcpyHostToDevice, B);
+            cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, B);
+            LevelView<T> Lr = views[vi[rep] >= 0 ? vi[rep] : 0];
+            Lr.nmax = nmax;
+            Lr.RC = rc;
+            for (int c = 0; c < 9; ++c) {
+                const int cnt = cstart[c + 1] - cstart[c];
+                if (cnt > 0)
+                    launch_factor_colour<T>(Lr, nullptr, cnt, c, smax, 0, B, nullptr, d_items + cstart[c], d_views);
+            }
+            cudaFreeAsync(d_views, B);
+            cudaFreeAsync(d_items, B);
+        }
+        cudaEventRecord(evB, B);
+        for_each_system(ok, workers, on_dev([&](int i) {
+            if (st[i] != IFMM_OK) return;
+            ifmm_handle* h = hs[i];
+            if (s0 != IFMM_OK) {
+                st[i] = s0;
+                return;
+            }
+            cudaStreamWaitEvent(h->st, evB, 0);
+            st[i] = factor_level_end<T>(h, h->depth - t);
+        }));
+    }
+    for_each_system(all, workers, on_dev([&](int i) {
+        if (st[i] == IFMM_OK) st[i] = factor_finish<T>(hs[i], l0);
+        if (st[i] != IFMM_OK && st[i] != IFMM_ERR_RANK_OVERFLOW) hs[i]->factored = false;
+    }));
+    cudaStreamSynchronize(B);
+    cudaStreamDestroy(B);
+    cudaEventDestroy(evB);
+    for (auto& e : evs) cudaEventDestroy(e);
+    ifmm_status first = IFMM_OK;
+    for (int i = 0; i < n; ++i) {
+        if (st_out) st_out[i] = st[i];
+        if (first == IFMM_OK && st[i] != IFMM_OK) first = st[i];
+    }
+    return first;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1425,6 +1606,46 @@ ifmm_status ifmm_solve_T(ifmm_h h, const double* b_dev, double* x_dev, int nrhs,
 
 ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* status_out) {
     if (!hs || n <= 0) return IFMM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i]) return IFMM_ERR_INVALID_ARG;
+    // one device and one precision: the systems' levels run in lockstep, each colour one launch per
+    // kernel over all of them
+    bool fused = true;
+    for (int i = 1; i < n; ++i)
+        fused = fused && hs[i]->device == hs[0]->device && hs[i]->prm.precision == hs[0]->prm.precision &&
+                hs[i]->prm.tc_products == hs[0]->prm.tc_products;
+    if (fused) {
+        DeviceGuard dg(hs[0]->device);
+        if (workers <= 0) workers = std::min(n, 16);
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<ifmm_status> st(n, IFMM_OK);
+        ifmm_status s = hs[0]->prm.precision == IFMM_MIXED ? factor_fused<float>(hs, n, workers, st.data())
+                                                           : factor_fused<double>(hs, n, workers, st.data());
+        (void)s;
+        // the solve's copies of the factors (IFMM_MIXED_SOLVE), per system
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i)
+            if ((st[i] == IFMM_OK || st[i] == IFMM_ERR_RANK_OVERFLOW) && hs[i]->prm.precision == IFMM_MIXED_SOLVE)
+                idx.push_back(i);
+        const int dev = hs[0]->device;
+        for_each_system(idx, workers, [&](int i) {
+            cudaSetDevice(dev);
+            ifmm_status s2 = hs[i]->prm.tc_products ? presplit_factors(hs[i]) : split_factors(hs[i]);
+            if (s2 == IFMM_OK) s2 = cudaStreamSynchronize(hs[i]->st) == cudaSuccess ? IFMM_OK : IFMM_ERR_CUDA;
+            if (s2 != IFMM_OK) {
+                hs[i]->factored = false;
+                st[i] = s2;
+            }
+        });
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ifmm_status first = IFMM_OK;
+        for (int i = 0; i < n; ++i) {
+            hs[i]->stats.t_factor_ms = ms;   // the whole batch's time
+            if (status_out) status_out[i] = st[i];
+            if (first == IFMM_OK && st[i] != IFMM_OK) first = st[i];
+        }
+        return first;
+    }
     std::vector<double> work(n);
     for (int i = 0; i < n; ++i) work[i] = hs[i] ? (double)hs[i]->N : 0.0;
     return run_batch(hs, n, workers, work, status_out, [&](int i) {

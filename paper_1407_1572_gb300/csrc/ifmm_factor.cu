@@ -83,11 +83,12 @@ IFMM_DEVINL int active_width(const LevelView<T>& L, int b, int colour) {
 // k_pivot: Piv_e^{-1} in FP64
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* boxes, int smax, int use_smem) {
+__global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L0, BoxList<T> bl, int smax, int use_smem) {
+    const LevelView<T>& L = bl.view(L0, blockIdx.x);
     extern __shared__ double dsm[];
     __shared__ double vred[32];
     __shared__ int ired[32];
-    const int e = boxes[blockIdx.x];
+    const int e = bl.box(blockIdx.x);
     const int n = L.n[e], r = L.r[e], s = n + r;
     if (s == 0) return;
     double* col = dsm;
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L, const int* b
 // prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 8 (portable).
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, const int* boxes, int C, int smax,
+__global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, BoxList<T> bl, int C, int smax,
                                                             int slab_global) {
     // pivot blocks are inverted in FP64 in every precision mode: they are the ill-conditioned part
     // of the elimination (balanced condition numbers up to 5e7 on uniform clouds, worse on
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L, cons
     __shared__ int s_cidx;
     __shared__ double s_alpha;
     const int c = (int)cl.block_rank();
-    const int e = boxes[blockIdx.x / C];
+    const LevelView<T>& L = bl.view(L0, blockIdx.x / C);
+    const int e = bl.box(blockIdx.x / C);
     const int n = L.n[e], r = L.r[e], s = n + r;
     const int rows_max = (smax + C - 1) / C;
     double* base = slab_global ? dsm : dsm + (size_t)rows_max * smax;
@@ -325,11 +327,12 @@ IFMM_DEVINL void factor_gemm(const LevelView<T>& L, int M, int N, int K, LA la, 
 }
 
 template <typename T, bool DF>
-__global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* boxes, int colour) {
+__global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L0, BoxList<T> bl, int colour) {
+    const LevelView<T>& L = bl.view(L0, blockIdx.x);
     using Acc = typename AccOf<T>::type;
     using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS sm[gemm_smem<GS>::value];
-    const int e = boxes[blockIdx.x];
+    const int e = bl.box(blockIdx.x);
     const int d = blockIdx.y;
     const int ex = e % L.side, ey = e / L.side;
     const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
@@ -386,7 +389,8 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L, const int* b
 // on the FP32 pipe, 2 = the tensor cores (ifmm_tc.cuh: digit-split bf16 MMAs, 128 threads, dynamic
 // shared memory and tensor memory taken only by the blocks that multiply)
 template <typename T, int GM>
-__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(LevelView<T> L, const int* boxes, int colour) {
+__global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(LevelView<T> L0, BoxList<T> bl, int colour) {
+    const LevelView<T>& L = bl.view(L0, blockIdx.x);
     using Acc = typename AccOf<T>::type;
     using GS = std::conditional_t<GM == 1 && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS sm[GM == 2 ? 1 : gemm_smem<GS>::value];
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
             factor_gemm<T, GM == 1>(L, M, N, K, la, lb, epi, sm, blockIdx.z, gridDim.z);
         }
     };
-    const int e = boxes[blockIdx.x];
+    const int e = bl.box(blockIdx.x);
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     const int ex = e % L.side, ey = e / L.side;
     const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
@@ -475,17 +479,40 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
 // ---------------------------------------------------------------------------------------------
 // k_compress: extend W_q for the well-separated fill of uneliminated neighbour q of e
 // ---------------------------------------------------------------------------------------------
+// element operations of the compression's Gram-Schmidt, in FP64 (or FP32) or double-float
+IFMM_DEVINL void gs_fma(double& s, double a, double b) { s = fma(a, b, s); }
+IFMM_DEVINL void gs_fma(float& s, float a, float b) { s = fmaf(a, b, s); }
+IFMM_DEVINL void gs_fma(dfl& s, dfl a, dfl b) { dfl_fma_acc(s, a, b); s = dfl_norm(s); }
+IFMM_DEVINL double gs_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+IFMM_DEVINL float gs_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+IFMM_DEVINL dfl gs_shfl(dfl v, int o) {
+    return dfl(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+IFMM_DEVINL double gs_d(double v) { return v; }
+IFMM_DEVINL double gs_d(float v) { return (double)v; }
+IFMM_DEVINL double gs_d(dfl v) { return (double)v; }
+// r - s u
+IFMM_DEVINL double gs_axpy(double r, double s, double u) { return fma(-s, u, r); }
+IFMM_DEVINL float gs_axpy(float r, float s, float u) { return fmaf(-s, u, r); }
+IFMM_DEVINL dfl gs_axpy(dfl r, dfl s, dfl u) {
+    dfl_fma_acc(r, dfl(-s.hi, -s.lo), u);
+    return dfl_norm(r);
+}
+
+// gscr: the FP64 work arrays live in the colour's global scratch (L.Cws) instead of shared memory
+// (wide fills, whose arrays exceed the shared-memory budget of the launch)
 template <typename T, bool DF>
-__global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int* boxes, int colour) {
+__global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<T> bl, int colour, int gscr) {
+    const LevelView<T>& L = bl.view(L0, blockIdx.x);
     using Acc = typename AccOf<T>::type;
-    extern __shared__ double csm[];  // u (nq) then per-warp coefficients (8 * RC)
+    extern __shared__ double csm_dyn[];  // u (nq), per-warp coefficients (8 * RC), column norms (m)
     using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS gsm[gemm_smem<GS>::value];
     __shared__ double vred[32];
     __shared__ int ired[32];
     __shared__ double s_val;
     __shared__ int s_flag;
-    const int e = boxes[blockIdx.x];
+    const int e = bl.box(blockIdx.x);
     const int dq = blockIdx.y;
     if (dq == 4) return;
     const int ex = e % L.side, ey = e / L.side;
@@ -503,10 +530,10 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const int nq = L.n[q];
     const int rq0 = L.r[q];
     const int RC = L.RC;
-    // S_q = [F_qp (nq x wp), F_pq^T (nq x wp)] over the partners p. For a symmetric kernel the
-    // extended system stays symmetric and F_pq^T = F_qp in exact arithmetic, so with the
-    // matrix-scale threshold the column fills alone span S_q.
-    const bool half = L.symmetric && L.tau_ref == 1;
+    // S_q = [F_qp (nq x wp), F_pq^T (nq x wp)] over the partners p. For a symmetric kernel the Schur
+    // update writes each fill pair as a block and its transpose (F_pq^T = F_qp bit for bit), so the
+    // row fills F_qp alone make up S_q (reading R2)
+    const bool half = L.symmetric != 0;
     int wps[8], m = 0;
     for (int t = 0; t < np; ++t) {
         int dp = parts[t];
@@ -516,6 +543,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     }
     if (nq == 0 || m == 0) return;
     T* R = L.Rs + L.rsoff[(int64_t)e * 9 + dq];
+    double* csm = gscr ? L.Cws + L.cwsoff[(int64_t)e * 9 + dq] : csm_dyn;
     {
         int c0 = 0;
         for (int t = 0; t < np; ++t) {
@@ -583,23 +611,34 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
     const int limit = min(nq, RC);
     double* u = csm;
     double* nrm2 = coef + 8 * RC;   // squared column norms of R, exact after every step
+    // the column work of the Gram-Schmidt: FP64, or double-float on the FP32 pipe when the products
+    // are double-float (the basis, the re-orthogonalisation, the norms that decide the pivots and the
+    // ranks, and the threshold test stay FP64)
+    using E = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
+    E* Re = reinterpret_cast<E*>(R);
+    E* ue = reinterpret_cast<E*>(nrm2 + m);   // u in E (nq entries)
+    if constexpr (std::is_same<E, dfl>::value) {
+        // R to double-float in place (the split works on the bit pattern: no FP64 arithmetic)
+        for (int t = threadIdx.x; t < nq * m; t += blockDim.x) Re[t] = dfl((double)R[t]);
+        __syncthreads();
+    }
     // g threads per column (a power of two dividing 32; more when the columns are few), ngr
     // groups; every warp runs the same number of column rounds so the group shuffles converge
     int g = 1;
     while (g < 8 && g * 2 * m <= (int)blockDim.x) g *= 2;
     const int ngr = (int)blockDim.x / g, gid = (int)threadIdx.x / g, gl = (int)threadIdx.x % g;
     const int rounds = (m + ngr - 1) / ngr;
-    auto group_sum = [&](Acc v) {
-        for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    auto group_sum = [&](E v) {
+        for (int o = g >> 1; o > 0; o >>= 1) v = v + gs_shfl(v, o);
         return v;
     };
     for (int rd = 0; rd < rounds; ++rd) {
         const int j = gid + rd * ngr;
-        Acc sq = 0;
+        E sq = E(0);
         if (j < m)
-            for (int i = gl; i < nq; i += g) { const Acc v = (Acc)R[(size_t)i * m + j]; sq += v * v; }
+            for (int i = gl; i < nq; i += g) { const E v = Re[(size_t)i * m + j]; gs_fma(sq, v, v); }
         sq = group_sum(sq);
-        if (j < m && gl == 0) nrm2[j] = (double)sq;
+        if (j < m && gl == 0) nrm2[j] = gs_d(sq);
     }
     __syncthreads();
     int add = 0;
@@ -625,7 +664,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
         }
         const int rc = rq0 + add;
         const double ib = 1.0 / bv;
-        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = (double)R[(size_t)i * m + jb] * ib;
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = gs_d(Re[(size_t)i * m + jb]) * ib;
         __syncthreads();
         // re-orthogonalise u against the current basis, twice (one thread per basis vector for the
         // coefficients, one per row for the update)
@@ -649,7 +688,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
         const double nu = sqrt(nn);
         if (!(nu >= 0.5)) {
             // numerically inside the current span: drop this column
-            for (int i = threadIdx.x; i < nq; i += blockDim.x) R[(size_t)i * m + jb] = (T)0;
+            for (int i = threadIdx.x; i < nq; i += blockDim.x) Re[(size_t)i * m + jb] = E(0);
             if (threadIdx.x == 0) nrm2[jb] = 0.0;
             __syncthreads();
             continue;
@@ -658,25 +697,26 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
         for (int i = threadIdx.x; i < nq; i += blockDim.x) {
             u[i] *= inu;
             W[(size_t)i * RC + rc] = (T)u[i];
+            ue[i] = E(u[i]);
         }
         __syncthreads();
         // remove u from every column; the squared norm of the updated column is summed in the same
         // pass (one more multiply-add per element, no extra memory traffic)
         for (int rd = 0; rd < rounds; ++rd) {
             const int j = gid + rd * ngr;
-            Acc sp = 0;
+            E sp = E(0);
             if (j < m)
-                for (int i = gl; i < nq; i += g) sp += (Acc)u[i] * (Acc)R[(size_t)i * m + j];
+                for (int i = gl; i < nq; i += g) gs_fma(sp, ue[i], Re[(size_t)i * m + j]);
             sp = group_sum(sp);
-            Acc sq = 0;
+            E sq = E(0);
             if (j < m)
                 for (int i = gl; i < nq; i += g) {
-                    const Acc v = (Acc)R[(size_t)i * m + j] - sp * (Acc)u[i];
-                    R[(size_t)i * m + j] = (T)v;
-                    sq += (Acc)(T)v * (Acc)(T)v;
+                    const E v = gs_axpy(Re[(size_t)i * m + j], sp, ue[i]);   // R_ij - sp u_i
+                    Re[(size_t)i * m + j] = v;
+                    gs_fma(sq, v, v);
                 }
             sq = group_sum(sq);
-            if (j < m && gl == 0) nrm2[j] = (double)sq;
+            if (j < m && gl == 0) nrm2[j] = gs_d(sq);
         }
         __syncthreads();
         ++add;
@@ -701,11 +741,12 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L, const int
 // k_redirect: M2L_pq += (W_p^T) F (W_q) for a well-separated pair with fill
 // ---------------------------------------------------------------------------------------------
 template <typename T, bool DF>
-__global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L, const int* boxes, int colour) {
+__global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L0, BoxList<T> bl, int colour) {
+    const LevelView<T>& L = bl.view(L0, blockIdx.x);
     using Acc = typename AccOf<T>::type;
     using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS sm[gemm_smem<GS>::value];
-    const int e = boxes[blockIdx.x];
+    const int e = bl.box(blockIdx.x);
     const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
     if (dp == 4 || dq == 4 || dp == dq) return;
     const int ex = e % L.side, ey = e / L.side;
@@ -800,8 +841,12 @@ __global__ void k_colour_smax(LevelView<T> L, const int* boxes, int nboxes, int*
 
 template <typename T>
 void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smax_bound,
-                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev) {
+                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev, const int2* items,
+                          const LevelView<T>* views) {
     if (nboxes <= 0) return;
+    // the blocks' boxes: one level of one system, or the items of a batch of systems (then L carries
+    // the launch sizes: the largest smax, nmax and RC over the batch)
+    const BoxList<T> bl{boxes, items, views};
     // size the pivot launch by the colour's actual largest pivot (the level bound nmax + min(nmax,
     // RC) is reached only when a basis fills up); status[2] is the scratch word
     int smax = smax_bound;
@@ -887,13 +932,13 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         if (active < 1) {
             cudaGetLastError();
             C = 1;   // this cluster shape cannot be scheduled: one block per box
-        } else if (cudaLaunchKernelEx(&cfg, kfn, L, boxes, C, smax, slab_global) != cudaSuccess) {
+        } else if (cudaLaunchKernelEx(&cfg, kfn, L, bl, C, smax, slab_global) != cudaSuccess) {
             cudaGetLastError();
             C = 1;   // launch refused: one block per box instead
         }
     }
     if (C == 1) {
-        k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, boxes, smax, use_smem);
+        k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, bl, smax, use_smem);
     }
     // spread big pair blocks over several blocks when the colour has few boxes (output tiles of 64,
     // or 32 for the double-float products)
@@ -903,8 +948,8 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     const int zp = std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8)));
     if (ev) cudaEventRecord(ev[1], st);
     const bool df = std::is_same<T, double>::value && L.gemm_dfl;
-    if (df) k_panel<T, true><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
-    else k_panel<T, false><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, boxes, colour);
+    if (df) k_panel<T, true><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, bl, colour);
+    else k_panel<T, false><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, bl, colour);
     if (ev) cudaEventRecord(ev[2], st);
     if (df && L.gemm_tc) {
         // tensor-core products: output tiles of 128 x 32, 82.6 KB of dynamic shared memory
@@ -915,29 +960,30 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         }
         const int ttiles = ((L.nmax + tc::kTM - 1) / tc::kTM) * ((L.nmax + tc::kTN - 1) / tc::kTN);
         const int zt = std::max(1, std::min(ttiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
-        k_schur<T, 2><<<dim3(nboxes, 81, zt), tc::kThreads, tc::kSmemBytes, st>>>(L, boxes, colour);
+        k_schur<T, 2><<<dim3(nboxes, 81, zt), tc::kThreads, tc::kSmemBytes, st>>>(L, bl, colour);
     } else if (df) {
-        k_schur<T, 1><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+        k_schur<T, 1><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, bl, colour);
     } else {
-        k_schur<T, 0><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, boxes, colour);
+        k_schur<T, 0><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, bl, colour);
     }
     if (ev) cudaEventRecord(ev[3], st);
     // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
     // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax)
+    // arrays above 64 KB go to the colour's global scratch (read through L1 / L2) so that wide fills
+    // neither fail nor cut the number of resident blocks
     size_t csmem = (size_t)(smax_bound + 8 * L.RC + 10 * L.nmax) * sizeof(double);
-    const void* kc = df ? (const void*)k_compress<T, true> : (const void*)k_compress<T, false>;
-    if (csmem > (size_t)dynamic_smem_limit(kc)) {
-        // the level's fills are too wide for the compression's shared arrays: report, do not launch
-        k_set_flag<<<1, 1, 0, st>>>(L.status, DEV_ERR_SIZE);
+    const int gscr = (csmem > (size_t)64 * 1024 || !L.Cws) ? 1 : 0;
+    if (gscr && !L.Cws) {
+        k_set_flag<<<1, 1, 0, st>>>(L.status, DEV_ERR_SIZE);   // no scratch was provided: refuse
         count_launches(1);
     } else if (df) {
-        k_compress<T, true><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+        k_compress<T, true><<<dim3(nboxes, 9), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
     } else {
-        k_compress<T, false><<<dim3(nboxes, 9), kThreads, csmem, st>>>(L, boxes, colour);
+        k_compress<T, false><<<dim3(nboxes, 9), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (df) k_redirect<T, true><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
-    else k_redirect<T, false><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, boxes, colour);
+    if (df) k_redirect<T, true><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, bl, colour);
+    else k_redirect<T, false><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, bl, colour);
     if (ev) cudaEventRecord(ev[5], st);
     count_launches(5);
 }
@@ -1809,7 +1855,7 @@ void launch_permute_out(const T* in, int64_t N, int nrhs, const int64_t* perm, d
 
 #define IFMM_INSTANTIATE(T)                                                                                     \
     template void launch_factor_colour<T>(const LevelView<T>&, const int*, int, int, int, int, cudaStream_t,    \
-                                          cudaEvent_t*);                                                        \
+                                          cudaEvent_t*, const int2*, const LevelView<T>*);                      \
     template void launch_forward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*, T*, T*,   \
                                            T*, int, cudaStream_t);                                              \
     template void launch_backward_colour<T>(const LevelView<T>&, const int*, int, int, const int64_t*,          \

@@ -94,6 +94,8 @@ struct LevelView {
     T* Fs2;                    // same layout: intermediate of the redirect
     const int64_t* rsoff;      // [nb*9] residual of the fill being compressed
     T* Rs;
+    const int64_t* cwsoff;     // [nb*9] the compression's FP64 work arrays (basis vector, coefficients,
+    double* Cws;               //        column norms) when they do not fit in shared memory
     double* pws;               // FP64 pivot workspace for blocks too large for shared memory
     const int64_t* psoff;      // [nb]
     int* status;               // device error bits (DEV_ERR_*)
@@ -106,6 +108,22 @@ struct LevelView {
     int gemm_dfl;              // FP64 level data, panel and Schur products in double-float (FP32 pipe)
     int gemm_tc;               // with gemm_dfl: the Schur products on the tensor cores (ifmm_tc.cuh)
     SlabSet sl;                // digit slabs of the factors for the tensor-core replay
+};
+
+// The boxes one launch of a factor kernel eliminates: the boxes of one colour of one level of one
+// system (`boxes`, the level view passed to the kernel by value), or the work items of a batch of
+// systems eliminated together (items[i] = (index of the system's level view in `views`, box)).
+template <typename T>
+struct BoxList {
+    const int* boxes;
+    const int2* items;
+    const LevelView<T>* views;
+#ifdef __CUDACC__
+    __device__ __forceinline__ const LevelView<T>& view(const LevelView<T>& L0, int i) const {
+        return items ? views[items[i].x] : L0;
+    }
+    __device__ __forceinline__ int box(int i) const { return items ? items[i].y : boxes[i]; }
+#endif
 };
 
 // Level vectors of the replay: for box b of level k, rows voff[b].. of the level-k vector hold
@@ -121,8 +139,10 @@ struct SolveView {
 template <typename T>
 // smem_pivot_s: the level's bound on a pivot's size; exact_sizing: read the colour's actual largest
 // pivot back (a stream synchronisation) to size the pivot launch
+// items / views (nullptr for one system): the blocks of a batch of systems (BoxList)
 void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, int smem_pivot_s,
-                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev);
+                          int exact_sizing, cudaStream_t st, cudaEvent_t* ev, const int2* items = nullptr,
+                          const LevelView<T>* views = nullptr);
 template <typename T>
 void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, int colour, const int64_t* yoff,
                            T* vec_k, T* vec_km1, T* vx, int nrhs, cudaStream_t st);

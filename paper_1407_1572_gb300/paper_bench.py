@@ -5,8 +5,8 @@ Equation "main_Solving_Equation" (unit diagonal) with the three regularised kern
 tolerance 1e-14 (here the matrix-scale threshold eps * s_A), a known x and b = A~ x, solved once
 without refinement (the paper's direct solve). For each kernel and N the module prints the paper's
 columns: t_a (build), t_f (factor), t_s (solve), r_m (largest box rank) and the relative error of x.
-A size whose factorisation this build refuses (a fill wider than the compression's shared-memory
-arrays) prints a "failed" record and ends that kernel's sweep.
+A size whose factorisation fails (a device allocation, say) prints a "failed" record and ends that
+kernel's sweep.
 
     python -m paper_1407_1572_gb300.paper_bench [--nmax 1000000] [--kernels log,r2log,inv]
 """
@@ -44,12 +44,12 @@ def run(nmax: int = 1000000, kernels=("log", "r2log", "inv"), a: float = 1e-3, e
             e[2].record(st)
             try:
                 ifmm.ifmm_factor(g.h, allow_overflow=True)
-            except ifmm.IFMMError as err:   # a limit of this build (e.g. fill wider than shared memory)
+            except ifmm.IFMMError as err:   # e.g. out of device memory
                 rec = dict(kernel=name, N=n, depth=g.stats()["depth"], failed=str(err))
                 print(json.dumps(rec), flush=True)
                 out.append(rec)
                 g.close()
-                break                       # larger N only widens the fill further
+                break                       # larger N needs more
             e[3].record(st)
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(st)
