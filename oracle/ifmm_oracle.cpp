@@ -395,6 +395,7 @@ double kernel_value(const oracle_params& p, double ax, double ay, double bx, dou
         // derivative of exp(-r / l) with respect to the length scale l
         case ORACLE_K_DEXP_DELL: return r / (p.kparam[0] * p.kparam[0]) * std::exp(-r / p.kparam[0]);
         case ORACLE_K_POLY: return (1.0 + ax * bx) * (1.0 + ay * by);
+        case ORACLE_K_R2: return r * r;
         // the three regularised kernels of the numerical benchmarks (Section 5), a = kparam[0]:
         // (i) r (log r - 1) / (a (log a - 1)) for r < a, ln r / ln a beyond; (ii) r / a, a / r;
         // (iii) r^3 (3 log r - 1) / (a^3 (3 log a - 1)), r^2 ln r / (a^2 ln a); each tends to 0 at r = 0
@@ -452,6 +453,7 @@ struct OpsLevel {              // operators after orthonormalisation, level k
     std::vector<int> rank;     // r_i
     std::vector<Mat> W;        // leaf: n_i x r_i; non-leaf: (sum_c r_c) x r_i, children in Morton order
     std::vector<Mat> Rt;       // r_i x p^2, the factor folded into M2L
+    Mat U;                     // svd_eps > 0: p^2 x r_k, the level's leading singular vectors
     std::vector<Mat> M2L;      // [box*49 + d49], interaction-list pairs only, r_i x r_j
 };
 
@@ -555,6 +557,133 @@ std::vector<int> elimination_order(int k, int order_kind) {
     return out;
 }
 
+// transfer T_c[m', m] = S^parent_m(child node m'), child c = a + 2b: S^parent(x) = S^child(x) T_c
+// for the polynomials of degree < p in each coordinate, which the parent's basis functions are
+std::vector<Mat> transfer_mats(int p) {
+    int r0 = p * p;
+    std::vector<Mat> T(4, Mat(r0, r0));
+    std::vector<double> t(p), lx(p), ly(p);
+    cheb_nodes(p, t.data());
+    for (int c = 0; c < 4; ++c) {
+        int a = c & 1, b = c >> 1;
+        for (int my = 0; my < p; ++my)
+            for (int mx = 0; mx < p; ++mx) {
+                double ux = 0.5 * (t[mx] - 1.0) + a, uy = 0.5 * (t[my] - 1.0) + b;
+                lagrange(p, t.data(), ux, lx.data());
+                lagrange(p, t.data(), uy, ly.data());
+                for (int ny = 0; ny < p; ++ny)
+                    for (int nx = 0; nx < p; ++nx) T[c].at(mx + p * my, nx + p * ny) = lx[nx] * ly[ny];
+            }
+    }
+    return T;
+}
+
+// The SVD compression of the Chebyshev interpolation (Section 5: Chebyshev interpolation followed
+// by SVD). At level k (box side h) the M2L kernel matrices K_d[m, l] = K(node_m, node_l + h d)
+// between a box's Chebyshev nodes and those of the box at offset d, over the 40 offsets d of an
+// interaction list (2 <= max(|d_x|, |d_y|) <= 3), form K_fat = [K_d]_d (p^2 x 40 p^2). Below the
+// top level the bases are nested: a box's coefficients also carry its ancestors' far fields, so
+// K_fat gains the parent's kept directions seen from each child position, T_c U_{k-1} Sigma_{k-1}
+// (reading R3b: without them a kept parent direction can lean on a child direction that the
+// child's own interactions rank below the cut, and the far field at the coarser level loses it).
+// The left singular vectors come from a one-sided (Hestenes) Jacobi SVD of G = K_fat^T: plane
+// rotations of column pairs of G until every pair is orthogonal to 1e-15, accumulated in V; then
+// sigma_j = ||G_j|| and U = V, columns sorted by sigma descending, each column's entry of largest
+// magnitude made positive. Returns the number of sigma_j > svd_eps * sigma_1. Up (p^2 x rp) and
+// sp are the parent level's kept vectors and singular values (rp = 0 at the top level).
+int svd_level(const Handle& h, int k, double svd_eps, const Mat& Up, const std::vector<double>& sp, Mat& U,
+              std::vector<double>& sigma) {
+    const int p = h.p, r0 = h.r0;
+    const double hh = box_h(h, k);
+    std::vector<double> t(p);
+    cheb_nodes(p, t.data());
+    std::vector<double> nx(r0), ny(r0);
+    for (int my = 0; my < p; ++my)
+        for (int mx = 0; mx < p; ++mx) {
+            nx[mx + p * my] = 0.5 * (t[mx] + 1.0) * hh;
+            ny[mx + p * my] = 0.5 * (t[my] + 1.0) * hh;
+        }
+    std::vector<std::pair<int, int>> offs;
+    for (int dy = -3; dy <= 3; ++dy)
+        for (int dx = -3; dx <= 3; ++dx)
+            if (std::max(std::abs(dx), std::abs(dy)) >= 2) offs.push_back({dx, dy});
+    const int rp = Up.c;
+    const int m = (int)offs.size() * r0 + 4 * rp;
+    Mat G(m, r0);
+    for (size_t o = 0; o < offs.size(); ++o)
+        for (int l = 0; l < r0; ++l)
+            for (int mm = 0; mm < r0; ++mm)
+                G.at((int)o * r0 + l, mm) = kernel_value(h.prm, nx[mm], ny[mm], nx[l] + hh * offs[o].first,
+                                                         ny[l] + hh * offs[o].second);
+    if (rp > 0) {
+        const std::vector<Mat> T = transfer_mats(p);
+        Counter ct;
+        for (int c = 0; c < 4; ++c) {
+            const Mat TU = mul(T[c], Up, ct);   // p^2 x rp
+            for (int j = 0; j < rp; ++j)
+                for (int mm = 0; mm < r0; ++mm)
+                    G.at((int)offs.size() * r0 + c * rp + j, mm) = TU.at(mm, j) * sp[j];
+        }
+    }
+    Mat V(r0, r0);
+    for (int j = 0; j < r0; ++j) V.at(j, j) = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        bool rotated = false;
+        for (int i = 0; i < r0 - 1; ++i)
+            for (int j = i + 1; j < r0; ++j) {
+                double a = 0.0, b = 0.0, c = 0.0;
+                for (int q = 0; q < m; ++q) {
+                    a += G.at(q, i) * G.at(q, i);
+                    b += G.at(q, j) * G.at(q, j);
+                    c += G.at(q, i) * G.at(q, j);
+                }
+                if (c == 0.0 || std::fabs(c) <= 1e-15 * std::sqrt(a * b)) continue;
+                rotated = true;
+                const double zeta = (b - a) / (2.0 * c);
+                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / std::sqrt(1.0 + tt * tt), sn = cs * tt;
+                for (int q = 0; q < m; ++q) {
+                    const double gi = G.at(q, i), gj = G.at(q, j);
+                    G.at(q, i) = cs * gi - sn * gj;
+                    G.at(q, j) = sn * gi + cs * gj;
+                }
+                for (int q = 0; q < r0; ++q) {
+                    const double vi = V.at(q, i), vj = V.at(q, j);
+                    V.at(q, i) = cs * vi - sn * vj;
+                    V.at(q, j) = sn * vi + cs * vj;
+                }
+            }
+        if (!rotated) break;
+    }
+    std::vector<double> sv(r0);
+    std::vector<int> idx(r0);
+    for (int j = 0; j < r0; ++j) { sv[j] = col_norm(G, j); idx[j] = j; }
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return sv[x] > sv[y]; });
+    U = Mat(r0, r0);
+    sigma.assign(r0, 0.0);
+    for (int j = 0; j < r0; ++j) {
+        const int src = idx[j];
+        sigma[j] = sv[src];
+        int imax = 0;
+        for (int q = 1; q < r0; ++q)
+            if (std::fabs(V.at(q, src)) > std::fabs(V.at(imax, src))) imax = q;
+        const double sg = V.at(imax, src) < 0.0 ? -1.0 : 1.0;
+        for (int q = 0; q < r0; ++q) U.at(q, j) = sg * V.at(q, src);
+    }
+    if (!(svd_eps > 0.0)) return r0;
+    int r = 0;
+    while (r < r0 && sigma[r] > svd_eps * sigma[0]) ++r;
+    return std::max(r, 1);
+}
+
+// the first r columns of U
+Mat leading_cols(const Mat& U, int r) {
+    Mat out(U.r, r);
+    for (int i = 0; i < U.r; ++i)
+        for (int j = 0; j < r; ++j) out.at(i, j) = U.at(i, j);
+    return out;
+}
+
 // ------------------------------------------------------------------------------------------
 // build: tree, operators, orthonormalisation
 // ------------------------------------------------------------------------------------------
@@ -594,6 +723,20 @@ bool build(Handle& h, const double* pts) {
     const double rank_tol = 1e-13;
     h.ops.assign(kap + 1, OpsLevel());
     Counter ct;
+    // svd_eps > 0: every level's Chebyshev coefficients are projected onto U_k (p^2 x r_k); the
+    // orthonormalisation below then works in those r_k coordinates, and Rt maps back to the p^2
+    // node values through U_k^T, so that M2L = Rt_i K(nodes_i, nodes_j) Rt_j^T keeps its form
+    const bool svd = P.svd_eps > 0.0;
+    if (svd) {
+        std::vector<double> sp;
+        for (int k = 2; k <= kap; ++k) {
+            Mat U;
+            std::vector<double> sg;
+            const int r = svd_level(h, k, P.svd_eps, k > 2 ? h.ops[k - 1].U : Mat(), sp, U, sg);
+            h.ops[k].U = leading_cols(U, r);
+            sp.assign(sg.begin(), sg.begin() + r);
+        }
+    }
     // leaf bases V_i[a, m] = S_m(x_a), orthonormalised
     {
         OpsLevel& L = h.ops[kap];
@@ -607,27 +750,17 @@ bool build(Handle& h, const double* pts) {
                     int64_t t = h.leaf_start[g] + a;
                     box_basis(h, kap, ix, iy, h.px[t], h.py[t], &V.a[(size_t)a * r0]);
                 }
-                cpqr(V, rank_tol, L.W[g], L.Rt[g], ct);
+                if (svd) {
+                    cpqr(mul(V, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
+                    L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
+                } else {
+                    cpqr(V, rank_tol, L.W[g], L.Rt[g], ct);
+                }
                 L.rank[g] = L.W[g].c;
             }
     }
-    // transfer T_c[m', m] = S^parent_m(child node m'), child c = a + 2b
-    std::vector<Mat> T(4, Mat(r0, r0));
-    {
-        std::vector<double> t(p), lx(p), ly(p);
-        cheb_nodes(p, t.data());
-        for (int c = 0; c < 4; ++c) {
-            int a = c & 1, b = c >> 1;
-            for (int my = 0; my < p; ++my)
-                for (int mx = 0; mx < p; ++mx) {
-                    double ux = 0.5 * (t[mx] - 1.0) + a, uy = 0.5 * (t[my] - 1.0) + b;
-                    lagrange(p, t.data(), ux, lx.data());
-                    lagrange(p, t.data(), uy, ly.data());
-                    for (int ny = 0; ny < p; ++ny)
-                        for (int nx = 0; nx < p; ++nx) T[c].at(mx + p * my, nx + p * ny) = lx[nx] * ly[ny];
-                }
-        }
-    }
+    (void)p;
+    const std::vector<Mat> T = transfer_mats(h.p);
     for (int k = kap - 1; k >= 2; --k) {
         OpsLevel& L = h.ops[k];
         const OpsLevel& Cl = h.ops[k + 1];
@@ -651,7 +784,12 @@ bool build(Handle& h, const double* pts) {
                     off += parts[c].r;
                 }
                 int g = ix + s * iy;
-                cpqr(Z, rank_tol, L.W[g], L.Rt[g], ct);
+                if (svd) {
+                    cpqr(mul(Z, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
+                    L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
+                } else {
+                    cpqr(Z, rank_tol, L.W[g], L.Rt[g], ct);
+                }
                 L.rank[g] = L.W[g].c;
             }
     }
@@ -1324,9 +1462,11 @@ extern "C" {
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm) {
     if (!pts || !prm || N <= 0 || prm->depth < 2 || prm->depth > 12 || prm->cheb_p < 1 || prm->cheb_p > 12) return nullptr;
     if (!(prm->box[2] > 0.0) || prm->eps < 0.0) return nullptr;
-    if ((prm->kernel == ORACLE_K_EXP || prm->kernel == ORACLE_K_DEXP_DELL || prm->kernel >= ORACLE_K_LOG_REG) &&
+    if ((prm->kernel == ORACLE_K_EXP || prm->kernel == ORACLE_K_DEXP_DELL || prm->kernel == ORACLE_K_LOG_REG ||
+         prm->kernel == ORACLE_K_INV_REG || prm->kernel == ORACLE_K_R2LOG_REG) &&
         !(prm->kparam[0] > 0.0))
         return nullptr;
+    if (!(prm->svd_eps >= 0.0) || !std::isfinite(prm->svd_eps)) return nullptr;
     auto h = std::make_unique<Handle>();
     h->prm = *prm;
     h->N = N;
@@ -1442,6 +1582,34 @@ int oracle_dense_tilde_direct(void* hp, double* A) {
     int kap = h.depth, r0 = h.r0;
     int64_t N = h.N;
     std::vector<double> si(r0), sj(r0), nix, niy, njx, njy;
+    // with the SVD compression the interpolation from level k's nodes to a particle passes through
+    // every level between: s = S^leaf(x) Pi_kappa, then s <- s T_c Pi_k' going up, where
+    // Pi_k = U_k U_k^T projects onto the kept singular vectors (T_c: the transfer of the ancestor's
+    // child position c)
+    const bool svd = h.prm.svd_eps > 0.0;
+    const std::vector<Mat> T = transfer_mats(h.p);
+    auto project = [&](int k, std::vector<double>& s) {
+        const Mat& U = h.ops[k].U;
+        std::vector<double> c(U.c, 0.0), out(r0, 0.0);
+        for (int j = 0; j < U.c; ++j)
+            for (int m = 0; m < r0; ++m) c[j] += s[m] * U.at(m, j);
+        for (int m = 0; m < r0; ++m)
+            for (int j = 0; j < U.c; ++j) out[m] += U.at(m, j) * c[j];
+        s = out;
+    };
+    auto chain = [&](int64_t t, int lx, int ly, int k, std::vector<double>& s) {
+        box_basis(h, kap, lx, ly, h.px[t], h.py[t], s.data());
+        project(kap, s);
+        for (int kk = kap - 1; kk >= k; --kk) {
+            const int cx = lx >> (kap - kk - 1), cy = ly >> (kap - kk - 1);   // ancestor at kk + 1
+            const Mat& Tc = T[(cx & 1) + 2 * (cy & 1)];
+            std::vector<double> out(r0, 0.0);
+            for (int m = 0; m < r0; ++m)
+                for (int l = 0; l < r0; ++l) out[l] += s[m] * Tc.at(m, l);
+            s = out;
+            project(kk, s);
+        }
+    };
     for (int64_t a = 0; a < N; ++a)
         for (int64_t b = 0; b < N; ++b) {
             int la = leaf_of_tree_pos(h, a), lb = leaf_of_tree_pos(h, b);
@@ -1454,8 +1622,13 @@ int oracle_dense_tilde_direct(void* hp, double* A) {
                 int k = kap;
                 while (k >= 2 && !in_interaction_list(ix >> (kap - k), iy >> (kap - k), jx >> (kap - k), jy >> (kap - k))) --k;
                 int sh = kap - k;
-                box_basis(h, k, ix >> sh, iy >> sh, h.px[a], h.py[a], si.data());
-                box_basis(h, k, jx >> sh, jy >> sh, h.px[b], h.py[b], sj.data());
+                if (svd) {
+                    chain(a, ix, iy, k, si);
+                    chain(b, jx, jy, k, sj);
+                } else {
+                    box_basis(h, k, ix >> sh, iy >> sh, h.px[a], h.py[a], si.data());
+                    box_basis(h, k, jx >> sh, jy >> sh, h.px[b], h.py[b], sj.data());
+                }
                 box_nodes(h, k, ix >> sh, iy >> sh, nix, niy);
                 box_nodes(h, k, jx >> sh, jy >> sh, njx, njy);
                 v = 0.0;
@@ -1596,6 +1769,25 @@ int oracle_initial_ranks(void* hp, int level, int* out) {
     const OpsLevel& L = h.ops[level];
     for (size_t g = 0; g < L.rank.size(); ++g) out[g] = L.rank[g];
     return 0;
+}
+
+int oracle_svd_basis(void* hp, int level, double* U, double* sigma) {
+    if (!hp || !U || !sigma) return -1;
+    Handle& h = *static_cast<Handle*>(hp);
+    if (level < 2 || level > h.depth) return -1;
+    Mat Uf, Up;
+    std::vector<double> sg, sp;
+    int r = 0;
+    for (int k = 2; k <= level; ++k) {
+        r = svd_level(h, k, h.prm.svd_eps, Up, sp, Uf, sg);
+        Up = leading_cols(Uf, r);
+        sp.assign(sg.begin(), sg.begin() + r);
+    }
+    for (int i = 0; i < h.r0; ++i) {
+        sigma[i] = sg[i];
+        for (int j = 0; j < h.r0; ++j) U[(size_t)i * h.r0 + j] = Uf.at(i, j);
+    }
+    return r;
 }
 
 int oracle_leaf_counts(void* hp, int* out) {

@@ -19,7 +19,9 @@ extern "C" {
 #endif
 
 enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_DEXP_DELL = 2, ORACLE_K_POLY = 3,
-       ORACLE_K_LOG_REG = 4, ORACLE_K_INV_REG = 5, ORACLE_K_R2LOG_REG = 6 };
+       ORACLE_K_LOG_REG = 4, ORACLE_K_INV_REG = 5, ORACLE_K_R2LOG_REG = 6,
+       ORACLE_K_R2 = 7 /* |x - y|^2: translation invariant, of exact separable rank 4 in 2D (a pin
+                          of the SVD truncation) */ };
 
 typedef struct {
     int depth;          /* leaf level kappa >= 2 of the uniform quadtree                      */
@@ -36,6 +38,12 @@ typedef struct {
                            fill being compressed; 1 = eps * s_A, the largest column norm over the
                            leaf diagonal blocks (matrix scale); 2 = eps * the largest column norm
                            over the diagonal blocks P2P_ii^(k) of the level being eliminated      */
+    double svd_eps;     /* > 0: Chebyshev interpolation followed by SVD compression (Section 5):
+                           at every level k the p^2 Chebyshev coefficients are projected onto the
+                           leading left singular vectors U_k of the level's M2L kernel matrices
+                           [K(nodes_0, nodes_0 + h_k d)] over the 40 interaction offsets d, keeping
+                           those with sigma_j > svd_eps * sigma_1 (translation-invariant kernels);
+                           0: no truncation                                                       */
 } oracle_params;
 
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm);
@@ -71,6 +79,13 @@ int   oracle_kernel_eval(const oracle_params* prm, const double* a, const double
 /* out[i * n + j] = K(P_i, Q_j) for m points P and n points Q (row-major x, y pairs), no diagonal */
 int   oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
                            double* out);
+
+/* The SVD of level k's M2L kernel matrices (the svd_eps truncation above), computed whatever the
+ * handle's svd_eps: sigma (p^2, descending) and U (p^2 x p^2, row-major, column j = the left
+ * singular vector of sigma_j, its entry of largest magnitude positive). Returns the number of
+ * singular values above svd_eps * sigma_1 for the handle's svd_eps (p^2 when it is 0), -1 on bad
+ * arguments. */
+int   oracle_svd_basis(void* h, int level, double* U, double* sigma);
 
 /* The compression step of reading R2 alone: append to W (n x r, row-major, orthonormal columns;
  * NULL when r = 0) the directions of S (n x m, row-major) that W misses, by pivoted Gram-Schmidt

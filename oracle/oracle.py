@@ -26,6 +26,7 @@ _lib = None
 
 K_INV_R, K_EXP, K_DEXP_DELL, K_POLY = 0, 1, 2, 3
 K_LOG_REG, K_INV_REG, K_R2LOG_REG = 4, 5, 6   # the numerical benchmarks of Section 5
+K_R2 = 7                                       # |x - y|^2 (separable rank 4 in 2D: an SVD pin)
 
 
 def compile_oracle(force: bool = False) -> str:
@@ -44,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("cheb_p", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("r_cap", ctypes.c_int), ("eps", ctypes.c_double), ("diag", ctypes.c_double),
                 ("kparam", ctypes.c_double * 4), ("box", ctypes.c_double * 3),
-                ("order", ctypes.c_int), ("threads", ctypes.c_int), ("tau_ref", ctypes.c_int)]
+                ("order", ctypes.c_int), ("threads", ctypes.c_int), ("tau_ref", ctypes.c_int),
+                ("svd_eps", ctypes.c_double)]
 
 
 def _load():
@@ -75,6 +77,7 @@ def _load():
             lib.oracle_lagrange.argtypes = [ctypes.c_int, ctypes.c_double, dp]
             lib.oracle_kernel_eval.argtypes = [ctypes.POINTER(Params), dp, dp, dp]
             lib.oracle_kernel_matrix.argtypes = [ctypes.POINTER(Params), dp, i64, dp, i64, dp]
+            lib.oracle_svd_basis.argtypes = [vp, ctypes.c_int, dp, dp]
             lib.oracle_augment_basis.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int, dp, dp]
             _lib = lib
@@ -86,7 +89,7 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(depth, cheb_p, kernel=K_INV_R, eps=1e-10, diag=1.0, r_cap=0, kparam=(0, 0, 0, 0),
-                box=(0.0, 0.0, 1.0), order=0, threads=0, tau_ref=0) -> Params:
+                box=(0.0, 0.0, 1.0), order=0, threads=0, tau_ref=0, svd_eps=0.0) -> Params:
     p = Params()
     p.depth, p.cheb_p, p.kernel, p.r_cap = depth, cheb_p, kernel, r_cap
     p.eps, p.diag = eps, diag
@@ -95,6 +98,7 @@ def make_params(depth, cheb_p, kernel=K_INV_R, eps=1e-10, diag=1.0, r_cap=0, kpa
     for i in range(3):
         p.box[i] = float(box[i])
     p.order, p.threads, p.tau_ref = order, threads, tau_ref
+    p.svd_eps = svd_eps
     return p
 
 
@@ -224,6 +228,17 @@ class Oracle:
         out = np.zeros(4 ** level, dtype=np.int32)
         self._lib.oracle_initial_ranks(self._h, level, _ptr(out))
         return out
+
+    def svd_basis(self, level: int):
+        """(U, sigma, r): the SVD of the level's M2L kernel matrices (Section 5's compression of the
+        Chebyshev interpolation) and the number of singular values the handle's svd_eps keeps."""
+        r0 = self.params.cheb_p ** 2
+        U = np.zeros((r0, r0))
+        sg = np.zeros(r0)
+        r = self._lib.oracle_svd_basis(self._h, level, _ptr(U), _ptr(sg))
+        if r < 0:
+            raise ValueError("oracle_svd_basis: bad level")
+        return U, sg, int(r)
 
     def leaf_counts(self) -> np.ndarray:
         out = np.zeros(4 ** self.depth, dtype=np.int32)

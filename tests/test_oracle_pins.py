@@ -461,3 +461,117 @@ def test_compressed_solve_within_c_eps_of_dense_lu(oracle_mod):
     assert errs[1e-10] <= C * 1e-10
     assert errs[1e-8] <= C * 1e-8
     assert 10.0 < errs[1e-8] / errs[1e-10] < 1000.0
+
+
+# ---- SVD compression of the Chebyshev interpolation (Section 5: "followed by SVD") ------------
+
+def _kfat_by_definition(O, prm, level, p, parent=None):
+    """K_fat of a level from its definition, in numpy: the M2L kernel matrices between a box's
+    Chebyshev nodes and those of the 40 interaction offsets (box side 2^-level of the root), plus,
+    below the top level, the parent's kept directions restricted to each child position (T_c U S).
+    T_c is built from the Lagrange basis (S^parent evaluated at the child's nodes)."""
+    t = O.cheb_nodes(p)
+    h = prm.box[2] / 2 ** level
+    nodes = np.array([[0.5 * (t[mx] + 1) * h, 0.5 * (t[my] + 1) * h] for my in range(p) for mx in range(p)])
+    blocks = []
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            if max(abs(dx), abs(dy)) >= 2:
+                blocks.append(O.kernel_matrix(prm, nodes, nodes + h * np.array([dx, dy])))
+    K = np.hstack(blocks)
+    if parent is not None:
+        Up, sp = parent
+        for c in range(4):
+            a, b = c & 1, c >> 1
+            T = np.array([np.outer(O.lagrange(p, 0.5 * (t[my] - 1) + b), O.lagrange(p, 0.5 * (t[mx] - 1) + a)).ravel()
+                          for my in range(p) for mx in range(p)])
+            K = np.hstack([K, (T @ Up) * sp])
+    return K
+
+
+@pytest.mark.parametrize("kernel,kp", [("K_INV_R", 0.0), ("K_LOG_REG", 0.001), ("K_EXP", 0.3)])
+def test_svd_basis_is_the_svd_of_the_m2l_matrices(oracle_mod, kernel, kp):
+    """The oracle's one-sided Jacobi SVD against LAPACK's (numpy) on K_fat built from the definition:
+    singular values to 1e-13 sigma_1 at the top level and the nested one below it, and the kept
+    projector U_r U_r^T, with r where the spectrum has a gap."""
+    O = oracle_mod
+    p = 5
+    o, _ = _oracle(O, 500, 3, p, getattr(O, kernel), kparam=(kp, 0, 0, 0), svd_eps=1e-7)
+    parent = None
+    for level in (2, 3):
+        U, sg, r = o.svd_basis(level)
+        K = _kfat_by_definition(O, o.params, level, p, parent)
+        Un, sn, _ = np.linalg.svd(K)
+        assert np.allclose(sg, sn[: p * p], rtol=0, atol=1e-13 * sn[0])
+        assert np.allclose(U.T @ U, np.eye(p * p), atol=1e-12)
+        assert r == max(1, int(np.sum(sn[: p * p] > 1e-7 * sn[0])))
+        gaps = [j for j in range(1, p * p) if sn[j] < 0.5 * sn[j - 1] and sn[j - 1] > 1e-9 * sn[0]]
+        for j in gaps[:3]:
+            assert np.allclose(U[:, :j] @ U[:, :j].T, Un[:, :j] @ Un[:, :j].T, atol=1e-9)
+        # sign convention: the largest entry of every column is positive
+        assert np.all(U[np.abs(U).argmax(0), np.arange(p * p)] > 0)
+        parent = (U[:, :r], sg[:r])
+
+
+def test_svd_keeps_the_exact_rank_of_a_separable_kernel(oracle_mod):
+    """|x - y|^2 = |x|^2 - 2 x.y + |y|^2 has separable rank 4 (functions 1, x_1, x_2, |x|^2 of one
+    point); Chebyshev interpolation with p >= 3 reproduces it exactly, so the truncated bases keep
+    4 directions at every level and the FMM matrix still equals the kernel matrix."""
+    O = oracle_mod
+    for p in (3, 5):
+        o, _ = _oracle(O, 400, 4, p, O.K_R2, diag=0.0, svd_eps=1e-10)
+        assert [o.svd_basis(k)[2] for k in (2, 3, 4)] == [4, 4, 4]
+        assert o.initial_ranks(4).max() <= 4
+        A, Ae = o.dense_tilde(), o.dense_exact()
+        assert np.abs(A - Ae).max() <= 1e-12 * np.abs(Ae).max()
+
+
+@pytest.mark.parametrize("kernel,kp", [("K_INV_R", 0.0), ("K_LOG_REG", 0.001)])
+def test_svd_nested_operators_equal_the_projected_formula(oracle_mod, kernel, kp):
+    """With the truncation, the nested operators (orthonormalised bases, transfers, M2L) give the
+    same FMM matrix as the definition: S^leaf(x) Pi_kappa T_c Pi_(kappa-1) ... Pi_k between the
+    interpolation at each level, K at level k's nodes."""
+    O = oracle_mod
+    o, _ = _oracle(O, 500, 4, 5, getattr(O, kernel), kparam=(kp, 0, 0, 0), svd_eps=1e-6)
+    assert min(o.svd_basis(k)[2] for k in (2, 3, 4)) < 25
+    A, Ad = o.dense_tilde(), o.dense_tilde_direct()
+    off = A - np.diag(np.diag(A))
+    assert np.abs(A - Ad).max() <= 1e-13 * np.abs(off).max()
+
+
+@pytest.mark.parametrize("kernel,kp", [("K_INV_R", 0.0), ("K_LOG_REG", 0.001), ("K_EXP", 0.5)])
+def test_svd_truncation_error_tracks_svd_eps(oracle_mod, kernel, kp):
+    """Dropping singular values below svd_eps sigma_1 changes the far field by a small multiple of
+    svd_eps (bound 100 svd_eps of the largest far entry over three levels), and by nothing once no
+    value falls below the cut."""
+    O = oracle_mod
+    o0, _ = _oracle(O, 600, 4, 6, getattr(O, kernel), kparam=(kp, 0, 0, 0))
+    A0 = o0.dense_tilde()
+    scale = np.abs(A0 - np.diag(np.diag(A0))).max()
+    prev = None
+    for se in (1e-5, 1e-7, 1e-9, 1e-11):
+        o, _ = _oracle(O, 600, 4, 6, getattr(O, kernel), kparam=(kp, 0, 0, 0), svd_eps=se)
+        err = np.abs(o.dense_tilde() - A0).max() / scale
+        ranks = [o.svd_basis(k)[2] for k in (2, 3, 4)]
+        assert err <= 100 * se, (se, err, ranks)
+        if min(ranks) == 36:
+            assert err <= 1e-13
+        if prev is not None:
+            assert sum(ranks) >= prev
+        prev = sum(ranks)
+
+
+def test_svd_compressed_solve_matches_dense_lu(oracle_mod):
+    """Factor and solve with the truncated bases: the solution of A~ x = b (A~ the truncated FMM
+    matrix, assembled densely) within C eps of its dense LU solution, C = 1e3 as in the uncompressed
+    case."""
+    O = oracle_mod
+    N = 700
+    o, pts = _oracle(O, N, 3, 5, O.K_LOG_REG, kparam=(0.001, 0, 0, 0), diag=1.0, eps=1e-10, tau_ref=1,
+                     svd_eps=1e-8)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(N)
+    o.factor()
+    x = o.solve(b)
+    xd = np.linalg.solve(o.dense_tilde(), b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e3 * 1e-10
