@@ -109,6 +109,13 @@ typedef struct {
                              factorisation); 2 = the replay and the Schur-update products of the
                              elimination; 0 (default) = neither: double-float replay and products
                              on the FP32 pipe. Range 0..2                                        */
+    double svd_eps;       /* Chebyshev interpolation followed by SVD compression (Section 5): > 0
+                             projects every level's p^2 Chebyshev coefficients onto the leading
+                             left singular vectors of the level's M2L kernel matrices over the 40
+                             interaction offsets (with the parent level's kept directions, so the
+                             bases stay nested), keeping sigma_j > svd_eps * sigma_1; the kept
+                             counts are ifmm_stats.svd_ranks. Meant for kernels of x - y alone
+                             (all of ifmm_kernel). 0 (default): no truncation. Range [0, 1)   */
 } ifmm_params;
 
 typedef struct {
@@ -134,11 +141,13 @@ typedef struct {
     double compress_proj_flops; /* the part of kernel_flops[3] spent projecting the fill onto the
                               complement of the old basis (products; double-float in
                               IFMM_MIXED_SOLVE); the rest is the FP64 pivoted Gram-Schmidt        */
+    int svd_ranks[16];     /* singular vectors kept per level (index = level) with svd_eps > 0;
+                              0 otherwise                                                           */
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
  * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 60, refine_inner 1e-4),
- * leaf_max 64, tc_products 0. */
+ * leaf_max 64, tc_products 0, svd_eps 0. */
 void ifmm_default_params(ifmm_params* p);
 
 /* Smallest depth 2..10 of the uniform quadtree (Section 4.2: boxes of level k form a 2^k x 2^k

@@ -8,8 +8,9 @@
  * Plain FP64, no BLAS: every linear-algebra step (matrix products, LU with partial pivoting,
  * Householder QR with column pivoting, the pivoted Gram-Schmidt range finder) is written out
  * below. The method follows the paper's order and notation:
- *   - uniform 2^d tree (d = 2), lists N_i (neighbours incl. self) and I_i (interaction list),
- *     Section 4.2, Table "table_cluster";
+ *   - uniform 2^d tree, d = 2 (quadtree) or d = 3 (octree: Section 4.2 extends the method to any
+ *     dimension), lists N_i (neighbours incl. self, up to 3^d) and I_i (interaction list, up to
+ *     6^d - 3^d), Section 4.2, Table "table_cluster";
  *   - FMM operators P2P, P2M, L2P, M2L (Table "table_FMM_operators") from Chebyshev
  *     interpolation (Section 5), orthonormalised by a QR of the nested bases;
  *   - the extended sparse system of particles x, multipoles y and locals z
@@ -36,8 +37,9 @@
  * threshold boundary with the fill-relative reference (R5, tau_ref = 0) are parity unpinned.
  *
  * Readings where the paper is silent (each is stated again where it is used):
- *   R1 elimination order inside a level: colour-major, colour = (ix mod 3) + 3 (iy mod 3),
- *      Morton order inside a colour (order = 0); or plain Morton order (order = 1).
+ *   R1 elimination order inside a level: colour-major, colour = (ix mod 3) + 3 (iy mod 3)
+ *      (+ 9 (iz mod 3) in 3D), Morton order inside a colour (order = 0); or plain Morton order
+ *      (order = 1).
  *   R2 fill compression: the paper names a "tweaked ACA" at tolerance 1e-14 without details.
  *      Here: the old basis W_q is kept; the stacked well-separated fill S_q of box q is
  *      projected onto the complement of W_q and a column-pivoted QR (pivoted Gram-Schmidt)
@@ -386,15 +388,16 @@ int augment_basis(Mat& W, const Mat& S, double eps, double ref, int cap, Counter
 // ------------------------------------------------------------------------------------------
 // kernels, Chebyshev interpolation
 // ------------------------------------------------------------------------------------------
-double kernel_value(const oracle_params& p, double ax, double ay, double bx, double by) {
-    double dx = ax - bx, dy = ay - by;
-    double r = std::sqrt(dx * dx + dy * dy);
+// a, b: three coordinates each (the third is 0 in 2D)
+double kernel_value(const oracle_params& p, const double* a, const double* b) {
+    const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
     switch (p.kernel) {
         case ORACLE_K_INV_R: return 1.0 / r;
         case ORACLE_K_EXP: return std::exp(-r / p.kparam[0]);
         // derivative of exp(-r / l) with respect to the length scale l
         case ORACLE_K_DEXP_DELL: return r / (p.kparam[0] * p.kparam[0]) * std::exp(-r / p.kparam[0]);
-        case ORACLE_K_POLY: return (1.0 + ax * bx) * (1.0 + ay * by);
+        case ORACLE_K_POLY: return (1.0 + a[0] * b[0]) * (1.0 + a[1] * b[1]) * (1.0 + a[2] * b[2]);
         case ORACLE_K_R2: return r * r;
         // the three regularised kernels of the numerical benchmarks (Section 5), a = kparam[0]:
         // (i) r (log r - 1) / (a (log a - 1)) for r < a, ln r / ln a beyond; (ii) r / a, a / r;
@@ -433,15 +436,74 @@ void lagrange(int p, const double* t, double x, double* out) {
     }
 }
 
-inline int d49(int dx, int dy) { return (dx + 3) + 7 * (dy + 3); }
-inline int d9(int dx, int dy) { return (dx + 1) + 3 * (dy + 1); }
+// ------------------------------------------------------------------------------------------
+// geometry of the uniform tree: level k holds a 2^k x ... x 2^k grid of boxes (Section 4.2), in
+// d = 2 (quadtree) or d = 3 (octree, the paper's extension to three dimensions). A box is
+// addressed by its grid coordinates c (c[2] = 0 in 2D) or its grid index c0 + s (c1 + s c2).
+// ------------------------------------------------------------------------------------------
+struct Box { int c[3] = {0, 0, 0}; };
+inline int side_of(int k) { return 1 << k; }
+inline int nboxes(int d, int k) { return 1 << (d * k); }
+inline Box box_at(int g, int side, int d) {
+    Box b;
+    b.c[0] = g % side;
+    b.c[1] = (g / side) % side;
+    b.c[2] = d == 3 ? g / (side * side) : 0;
+    return b;
+}
+inline int box_index(const Box& b, int side) { return b.c[0] + side * (b.c[1] + side * b.c[2]); }
+inline bool in_grid(const Box& b, int side, int d) {
+    for (int i = 0; i < d; ++i)
+        if (b.c[i] < 0 || b.c[i] >= side) return false;
+    return true;
+}
+inline int cheb_dist(const Box& a, const Box& b) {
+    return std::max(std::abs(a.c[0] - b.c[0]), std::max(std::abs(a.c[1] - b.c[1]), std::abs(a.c[2] - b.c[2])));
+}
+inline Box parent_of(const Box& b) {
+    Box p;
+    for (int i = 0; i < 3; ++i) p.c[i] = b.c[i] >> 1;
+    return p;
+}
+// child position c = a + 2 b (+ 4 e in 3D): the child's coordinates are 2 x + a, 2 y + b, 2 z + e
+inline Box child_of(const Box& b, int c) {
+    Box o;
+    for (int i = 0; i < 3; ++i) o.c[i] = 2 * b.c[i] + ((c >> i) & 1);
+    return o;
+}
+inline int child_pos(const Box& b) { return (b.c[0] & 1) + 2 * (b.c[1] & 1) + 4 * (b.c[2] & 1); }
+inline Box shifted(const Box& b, int sh) {
+    Box o;
+    for (int i = 0; i < 3; ++i) o.c[i] = b.c[i] >> sh;
+    return o;
+}
+// interaction list at level k >= 1: Chebyshev distance >= 2 and parents are neighbours
+inline bool in_interaction_list(const Box& a, const Box& b) {
+    return cheb_dist(a, b) >= 2 && cheb_dist(parent_of(a), parent_of(b)) <= 1;
+}
+// colour (reading R1): boxes of one colour are 3 apart along every axis
+inline int colour_of(const Box& b) { return (b.c[0] % 3) + 3 * (b.c[1] % 3) + 9 * (b.c[2] % 3); }
+inline int ncolours(int d) { return d == 3 ? 27 : 9; }
+// offsets of radius R (each coordinate in -R..R; 0 in the third one in 2D), x fastest: 3^d of them
+// for the neighbours (R = 1) and 7^d for the interaction lists (R = 3)
+inline int n_off(int d, int R) { return d == 3 ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1) : (2 * R + 1) * (2 * R + 1); }
+inline int off_index(const Box& a, const Box& b, int d, int R) {
+    const int w = 2 * R + 1;
+    return (b.c[0] - a.c[0] + R) + w * (b.c[1] - a.c[1] + R) + (d == 3 ? w * w * (b.c[2] - a.c[2] + R) : 0);
+}
+inline Box offset_box(const Box& a, int o, int d, int R) {
+    const int w = 2 * R + 1;
+    Box b;
+    b.c[0] = a.c[0] + o % w - R;
+    b.c[1] = a.c[1] + (o / w) % w - R;
+    b.c[2] = d == 3 ? a.c[2] + o / (w * w) - R : 0;
+    return b;
+}
 
-uint64_t morton(uint32_t ix, uint32_t iy) {
+uint64_t morton(const Box& b, int d) {
     uint64_t m = 0;
-    for (int b = 0; b < 32; ++b) {
-        m |= (uint64_t)((ix >> b) & 1u) << (2 * b);
-        m |= (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
-    }
+    for (int bit = 0; bit < 20; ++bit)
+        for (int i = 0; i < d; ++i) m |= (uint64_t)((b.c[i] >> bit) & 1) << (d * bit + i);
     return m;
 }
 
@@ -454,7 +516,7 @@ struct OpsLevel {              // operators after orthonormalisation, level k
     std::vector<Mat> W;        // leaf: n_i x r_i; non-leaf: (sum_c r_c) x r_i, children in Morton order
     std::vector<Mat> Rt;       // r_i x p^2, the factor folded into M2L
     Mat U;                     // svd_eps > 0: p^2 x r_k, the level's leading singular vectors
-    std::vector<Mat> M2L;      // [box*49 + d49], interaction-list pairs only, r_i x r_j
+    std::vector<Mat> M2L;      // [box * 7^d + offset index (R = 3)], interaction-list pairs only, r_i x r_j
 };
 
 enum { ROW_P2P = 0, ROW_M2L = 1 };  // active equation of a box: P2P(i,k) before, M2L after
@@ -471,12 +533,12 @@ struct BoxFactor {
 };
 
 struct ElimLevel {
-    int k = 0, side = 0, nb = 0;
+    int k = 0, side = 0, nb = 0, d = 2;
     double scale = 0.0;        // largest column norm of the diagonal blocks at the start of the level
     std::vector<int> n, r, E;
-    std::vector<int> xoff;     // non-leaf: 5 offsets per box of the children's y inside x_i
+    std::vector<int> xoff;     // non-leaf: 2^d + 1 offsets per box of the children's y inside x_i
     std::vector<Mat> W;        // L2P_ii; P2M_ii = W^T
-    std::vector<Mat> P2P, M2P, P2L, M2L;  // [box*49 + d49]
+    std::vector<Mat> P2P, M2P, P2L, M2L;  // [box * 7^d + offset index (R = 3)]
     std::vector<int> order;
     std::vector<BoxFactor> fac;
 };
@@ -484,13 +546,14 @@ struct ElimLevel {
 struct Handle {
     oracle_params prm{};
     int64_t N = 0;
-    int depth = 0, p = 0, r0 = 0;
-    std::vector<double> px, py;         // tree order
+    int depth = 0, p = 0, r0 = 0, d = 2;   // r0 = p^d
+    double org[3] = {0.0, 0.0, 0.0}, Lside = 1.0;   // root box: lower corner and side
+    std::vector<double> pt;             // tree order, three coordinates per point (z = 0 in 2D)
     std::vector<int64_t> perm;          // tree position -> caller index
     std::vector<int64_t> leaf_start;    // per leaf (grid index)
     std::vector<int> leaf_count;
     std::vector<OpsLevel> ops;          // by level, valid for k >= 2
-    std::vector<Mat> leafP2P;           // [leaf*9 + d9]
+    std::vector<Mat> leafP2P;           // [leaf * 3^d + offset index (R = 1)]
     bool factored = false;
     std::vector<ElimLevel> el;          // by level
     Mat rootLU;
@@ -501,87 +564,94 @@ struct Handle {
     double scale_A = 0.0;   // largest column norm over the leaf diagonal blocks
 };
 
-int side_of(int k) { return 1 << k; }
-double box_h(const Handle& h, int k) { return h.prm.box[2] / (double)side_of(k); }
+double box_h(const Handle& h, int k) { return h.Lside / (double)side_of(k); }
 
-// Chebyshev nodes of box (ix, iy) at level k, index m = mx + p*my
-void box_nodes(const Handle& h, int k, int ix, int iy, std::vector<double>& nx, std::vector<double>& ny) {
-    int p = h.p;
+// Chebyshev nodes of box b at level k, three coordinates each, index m = mx + p (my + p mz)
+void box_nodes(const Handle& h, int k, const Box& b, std::vector<double>& nodes) {
+    const int p = h.p, d = h.d;
     std::vector<double> t(p);
     cheb_nodes(p, t.data());
-    double hh = box_h(h, k);
-    double lx = h.prm.box[0] + ix * hh, ly = h.prm.box[1] + iy * hh;
-    nx.resize(p * p); ny.resize(p * p);
-    for (int my = 0; my < p; ++my)
-        for (int mx = 0; mx < p; ++mx) {
-            nx[mx + p * my] = lx + 0.5 * (t[mx] + 1.0) * hh;
-            ny[mx + p * my] = ly + 0.5 * (t[my] + 1.0) * hh;
+    const double hh = box_h(h, k);
+    nodes.assign((size_t)3 * h.r0, 0.0);
+    for (int m = 0; m < h.r0; ++m) {
+        int mm = m;
+        for (int i = 0; i < d; ++i) {
+            nodes[3 * m + i] = h.org[i] + (b.c[i] + 0.5 * (t[mm % p] + 1.0)) * hh;
+            mm /= p;
         }
+    }
 }
 
-// S_m(x, y) for box (ix, iy) at level k: tensor Lagrange basis, out[p^2]
-void box_basis(const Handle& h, int k, int ix, int iy, double x, double y, double* out) {
-    int p = h.p;
-    std::vector<double> t(p), lx(p), ly(p);
+// S_m(x) for box b at level k: the tensor Lagrange basis, out[p^d]
+void box_basis(const Handle& h, int k, const Box& b, const double* x, double* out) {
+    const int p = h.p, d = h.d;
+    std::vector<double> t(p), l((size_t)3 * p, 1.0);
     cheb_nodes(p, t.data());
-    double hh = box_h(h, k);
-    double ux = 2.0 * (x - (h.prm.box[0] + ix * hh)) / hh - 1.0;
-    double uy = 2.0 * (y - (h.prm.box[1] + iy * hh)) / hh - 1.0;
-    lagrange(p, t.data(), ux, lx.data());
-    lagrange(p, t.data(), uy, ly.data());
-    for (int my = 0; my < p; ++my)
-        for (int mx = 0; mx < p; ++mx) out[mx + p * my] = lx[mx] * ly[my];
-}
-
-int cheb_dist(int ax, int ay, int bx, int by) { return std::max(std::abs(ax - bx), std::abs(ay - by)); }
-
-// interaction list at level k >= 1: Chebyshev distance >= 2 and parents are neighbours
-bool in_interaction_list(int ax, int ay, int bx, int by) {
-    return cheb_dist(ax, ay, bx, by) >= 2 && cheb_dist(ax >> 1, ay >> 1, bx >> 1, by >> 1) <= 1;
-}
-
-int colour_of(int ix, int iy) { return (ix % 3) + 3 * (iy % 3); }
-
-std::vector<int> elimination_order(int k, int order_kind) {
-    int side = side_of(k);
-    std::vector<std::pair<uint64_t, int>> keys;
-    for (int iy = 0; iy < side; ++iy)
-        for (int ix = 0; ix < side; ++ix) {
-            uint64_t key = morton(ix, iy);
-            if (order_kind == 0) key |= (uint64_t)colour_of(ix, iy) << 60;
-            keys.push_back({key, ix + side * iy});
+    const double hh = box_h(h, k);
+    for (int i = 0; i < d; ++i) {
+        const double u = 2.0 * (x[i] - (h.org[i] + b.c[i] * hh)) / hh - 1.0;
+        lagrange(p, t.data(), u, &l[(size_t)i * p]);
+    }
+    for (int m = 0; m < h.r0; ++m) {
+        int mm = m;
+        double v = 1.0;
+        for (int i = 0; i < d; ++i) {
+            v *= l[(size_t)i * p + mm % p];
+            mm /= p;
         }
+        out[m] = v;
+    }
+}
+
+std::vector<int> elimination_order(int k, int d, int order_kind) {
+    const int side = side_of(k), nb = nboxes(d, k);
+    std::vector<std::pair<uint64_t, int>> keys;
+    for (int g = 0; g < nb; ++g) {
+        const Box b = box_at(g, side, d);
+        uint64_t key = morton(b, d);
+        if (order_kind == 0) key |= (uint64_t)colour_of(b) << 59;
+        keys.push_back({key, g});
+    }
     std::sort(keys.begin(), keys.end());
     std::vector<int> out;
     for (auto& kv : keys) out.push_back(kv.second);
     return out;
 }
 
-// transfer T_c[m', m] = S^parent_m(child node m'), child c = a + 2b: S^parent(x) = S^child(x) T_c
-// for the polynomials of degree < p in each coordinate, which the parent's basis functions are
-std::vector<Mat> transfer_mats(int p) {
-    int r0 = p * p;
-    std::vector<Mat> T(4, Mat(r0, r0));
-    std::vector<double> t(p), lx(p), ly(p);
+// transfer T_c[m', m] = S^parent_m(child node m'), child position c (child_of): S^parent(x) =
+// S^child(x) T_c for the polynomials of degree < p in each coordinate, which the parent's basis
+// functions are. 2^d of them, p^d x p^d each.
+std::vector<Mat> transfer_mats(int p, int d) {
+    int r0 = 1;
+    for (int i = 0; i < d; ++i) r0 *= p;
+    std::vector<Mat> T(1 << d, Mat(r0, r0));
+    std::vector<double> t(p), l((size_t)3 * p);
     cheb_nodes(p, t.data());
-    for (int c = 0; c < 4; ++c) {
-        int a = c & 1, b = c >> 1;
-        for (int my = 0; my < p; ++my)
-            for (int mx = 0; mx < p; ++mx) {
-                double ux = 0.5 * (t[mx] - 1.0) + a, uy = 0.5 * (t[my] - 1.0) + b;
-                lagrange(p, t.data(), ux, lx.data());
-                lagrange(p, t.data(), uy, ly.data());
-                for (int ny = 0; ny < p; ++ny)
-                    for (int nx = 0; nx < p; ++nx) T[c].at(mx + p * my, nx + p * ny) = lx[nx] * ly[ny];
+    for (int c = 0; c < (1 << d); ++c)
+        for (int mc = 0; mc < r0; ++mc) {   // child node
+            int mm = mc;
+            for (int i = 0; i < d; ++i) {
+                lagrange(p, t.data(), 0.5 * (t[mm % p] - 1.0) + ((c >> i) & 1), &l[(size_t)i * p]);
+                mm /= p;
             }
-    }
+            for (int m = 0; m < r0; ++m) {   // parent basis function
+                int q = m;
+                double v = 1.0;
+                for (int i = 0; i < d; ++i) {
+                    v *= l[(size_t)i * p + q % p];
+                    q /= p;
+                }
+                T[c].at(mc, m) = v;
+            }
+        }
     return T;
 }
 
 // The SVD compression of the Chebyshev interpolation (Section 5: Chebyshev interpolation followed
 // by SVD). At level k (box side h) the M2L kernel matrices K_d[m, l] = K(node_m, node_l + h d)
-// between a box's Chebyshev nodes and those of the box at offset d, over the 40 offsets d of an
-// interaction list (2 <= max(|d_x|, |d_y|) <= 3), form K_fat = [K_d]_d (p^2 x 40 p^2). Below the
+// between a box's Chebyshev nodes and those of the box at offset d, over the offsets d of an
+// interaction list (2 <= max_i |d_i| <= 3: 40 in 2D, 316 in 3D), form K_fat = [K_d]_d
+// (p^d x #offsets p^d). Below the
 // top level the bases are nested: a box's coefficients also carry its ancestors' far fields, so
 // K_fat gains the parent's kept directions seen from each child position, T_c U_{k-1} Sigma_{k-1}
 // (reading R3b: without them a kept parent direction can lean on a child direction that the
@@ -593,33 +663,38 @@ std::vector<Mat> transfer_mats(int p) {
 // sp are the parent level's kept vectors and singular values (rp = 0 at the top level).
 int svd_level(const Handle& h, int k, double svd_eps, const Mat& Up, const std::vector<double>& sp, Mat& U,
               std::vector<double>& sigma) {
-    const int p = h.p, r0 = h.r0;
+    const int p = h.p, r0 = h.r0, d = h.d;
     const double hh = box_h(h, k);
     std::vector<double> t(p);
     cheb_nodes(p, t.data());
-    std::vector<double> nx(r0), ny(r0);
-    for (int my = 0; my < p; ++my)
-        for (int mx = 0; mx < p; ++mx) {
-            nx[mx + p * my] = 0.5 * (t[mx] + 1.0) * hh;
-            ny[mx + p * my] = 0.5 * (t[my] + 1.0) * hh;
+    std::vector<double> nd((size_t)3 * r0, 0.0);   // nodes of the box at the origin
+    for (int m = 0; m < r0; ++m) {
+        int mm = m;
+        for (int i = 0; i < d; ++i) {
+            nd[3 * m + i] = 0.5 * (t[mm % p] + 1.0) * hh;
+            mm /= p;
         }
-    std::vector<std::pair<int, int>> offs;
-    for (int dy = -3; dy <= 3; ++dy)
-        for (int dx = -3; dx <= 3; ++dx)
-            if (std::max(std::abs(dx), std::abs(dy)) >= 2) offs.push_back({dx, dy});
+    }
+    std::vector<Box> offs;
+    const Box o0;
+    for (int o = 0; o < n_off(d, 3); ++o) {
+        const Box b = offset_box(o0, o, d, 3);
+        if (cheb_dist(o0, b) >= 2) offs.push_back(b);
+    }
     const int rp = Up.c;
-    const int m = (int)offs.size() * r0 + 4 * rp;
+    const int m = (int)offs.size() * r0 + (1 << d) * rp;
     Mat G(m, r0);
     for (size_t o = 0; o < offs.size(); ++o)
-        for (int l = 0; l < r0; ++l)
-            for (int mm = 0; mm < r0; ++mm)
-                G.at((int)o * r0 + l, mm) = kernel_value(h.prm, nx[mm], ny[mm], nx[l] + hh * offs[o].first,
-                                                         ny[l] + hh * offs[o].second);
+        for (int l = 0; l < r0; ++l) {
+            double y[3];
+            for (int i = 0; i < 3; ++i) y[i] = nd[3 * l + i] + hh * offs[o].c[i];
+            for (int mm = 0; mm < r0; ++mm) G.at((int)o * r0 + l, mm) = kernel_value(h.prm, &nd[3 * mm], y);
+        }
     if (rp > 0) {
-        const std::vector<Mat> T = transfer_mats(p);
+        const std::vector<Mat> T = transfer_mats(p, d);
         Counter ct;
-        for (int c = 0; c < 4; ++c) {
-            const Mat TU = mul(T[c], Up, ct);   // p^2 x rp
+        for (int c = 0; c < (1 << d); ++c) {
+            const Mat TU = mul(T[c], Up, ct);   // p^d x rp
             for (int j = 0; j < rp; ++j)
                 for (int mm = 0; mm < r0; ++mm)
                     G.at((int)offs.size() * r0 + c * rp + j, mm) = TU.at(mm, j) * sp[j];
@@ -687,35 +762,44 @@ Mat leading_cols(const Mat& U, int r) {
 // ------------------------------------------------------------------------------------------
 // build: tree, operators, orthonormalisation
 // ------------------------------------------------------------------------------------------
+// leaf of a point (tree position t): the floor rule per coordinate, the upper face in the last box
+Box leaf_box(const Handle& h, const double* x) {
+    const int side = side_of(h.depth);
+    Box b;
+    for (int i = 0; i < h.d; ++i) {
+        const double u = (x[i] - h.org[i]) / h.Lside;
+        b.c[i] = std::min((int)std::floor(u * side), side - 1);
+    }
+    return b;
+}
+
 bool build(Handle& h, const double* pts) {
     const oracle_params& P = h.prm;
-    int kap = h.depth, side = side_of(kap);
+    const int kap = h.depth, side = side_of(kap), d = h.d, nleaf = nboxes(d, kap);
     int64_t N = h.N;
     std::vector<std::pair<uint64_t, int64_t>> keys(N);
-    std::vector<int> lix(N), liy(N);
     for (int64_t a = 0; a < N; ++a) {
-        double x = pts[2 * a], y = pts[2 * a + 1];
-        if (!std::isfinite(x) || !std::isfinite(y)) return false;
-        double ux = (x - P.box[0]) / P.box[2], uy = (y - P.box[1]) / P.box[2];
-        if (ux < 0.0 || ux > 1.0 || uy < 0.0 || uy > 1.0) return false;
-        int ix = std::min((int)std::floor(ux * side), side - 1);
-        int iy = std::min((int)std::floor(uy * side), side - 1);
-        keys[a] = {morton(ix, iy), a};
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < d; ++i) {
+            x[i] = pts[(size_t)d * a + i];
+            if (!std::isfinite(x[i])) return false;
+            const double u = (x[i] - h.org[i]) / h.Lside;
+            if (u < 0.0 || u > 1.0) return false;
+        }
+        keys[a] = {morton(leaf_box(h, x), d), a};
     }
     std::sort(keys.begin(), keys.end());
-    h.perm.resize(N); h.px.resize(N); h.py.resize(N);
-    h.leaf_start.assign(side * side, 0);
-    h.leaf_count.assign(side * side, 0);
+    h.perm.resize(N);
+    h.pt.assign((size_t)3 * N, 0.0);
+    h.leaf_start.assign(nleaf, 0);
+    h.leaf_count.assign(nleaf, 0);
     for (int64_t t = 0; t < N; ++t) {
         int64_t a = keys[t].second;
         h.perm[t] = a;
-        h.px[t] = pts[2 * a]; h.py[t] = pts[2 * a + 1];
+        for (int i = 0; i < d; ++i) h.pt[3 * t + i] = pts[(size_t)d * a + i];
     }
     for (int64_t t = N - 1; t >= 0; --t) {
-        double ux = (h.px[t] - P.box[0]) / P.box[2], uy = (h.py[t] - P.box[1]) / P.box[2];
-        int ix = std::min((int)std::floor(ux * side), side - 1);
-        int iy = std::min((int)std::floor(uy * side), side - 1);
-        int g = ix + side * iy;
+        const int g = box_index(leaf_box(h, &h.pt[3 * t]), side);
         h.leaf_start[g] = t;
         h.leaf_count[g]++;
     }
@@ -723,8 +807,8 @@ bool build(Handle& h, const double* pts) {
     const double rank_tol = 1e-13;
     h.ops.assign(kap + 1, OpsLevel());
     Counter ct;
-    // svd_eps > 0: every level's Chebyshev coefficients are projected onto U_k (p^2 x r_k); the
-    // orthonormalisation below then works in those r_k coordinates, and Rt maps back to the p^2
+    // svd_eps > 0: every level's Chebyshev coefficients are projected onto U_k (p^d x r_k); the
+    // orthonormalisation below then works in those r_k coordinates, and Rt maps back to the p^d
     // node values through U_k^T, so that M2L = Rt_i K(nodes_i, nodes_j) Rt_j^T keeps its form
     const bool svd = P.svd_eps > 0.0;
     if (svd) {
@@ -741,102 +825,100 @@ bool build(Handle& h, const double* pts) {
     {
         OpsLevel& L = h.ops[kap];
         L.k = kap; L.side = side;
-        L.rank.assign(side * side, 0); L.W.resize(side * side); L.Rt.resize(side * side);
-        for (int iy = 0; iy < side; ++iy)
-            for (int ix = 0; ix < side; ++ix) {
-                int g = ix + side * iy, n = h.leaf_count[g];
-                Mat V(n, r0);
-                for (int a = 0; a < n; ++a) {
-                    int64_t t = h.leaf_start[g] + a;
-                    box_basis(h, kap, ix, iy, h.px[t], h.py[t], &V.a[(size_t)a * r0]);
-                }
-                if (svd) {
-                    cpqr(mul(V, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
-                    L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
-                } else {
-                    cpqr(V, rank_tol, L.W[g], L.Rt[g], ct);
-                }
-                L.rank[g] = L.W[g].c;
+        L.rank.assign(nleaf, 0); L.W.resize(nleaf); L.Rt.resize(nleaf);
+        for (int g = 0; g < nleaf; ++g) {
+            const Box bx = box_at(g, side, d);
+            const int n = h.leaf_count[g];
+            Mat V(n, r0);
+            for (int a = 0; a < n; ++a) {
+                int64_t t = h.leaf_start[g] + a;
+                box_basis(h, kap, bx, &h.pt[3 * t], &V.a[(size_t)a * r0]);
             }
+            if (svd) {
+                cpqr(mul(V, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
+                L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
+            } else {
+                cpqr(V, rank_tol, L.W[g], L.Rt[g], ct);
+            }
+            L.rank[g] = L.W[g].c;
+        }
     }
     (void)p;
-    const std::vector<Mat> T = transfer_mats(h.p);
+    const std::vector<Mat> T = transfer_mats(h.p, d);
+    const int nkid = 1 << d;
     for (int k = kap - 1; k >= 2; --k) {
         OpsLevel& L = h.ops[k];
         const OpsLevel& Cl = h.ops[k + 1];
-        int s = side_of(k);
+        const int s = side_of(k), nb = nboxes(d, k);
         L.k = k; L.side = s;
-        L.rank.assign(s * s, 0); L.W.resize(s * s); L.Rt.resize(s * s);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int rows = 0;
-                std::vector<Mat> parts;
-                for (int c = 0; c < 4; ++c) {
-                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
-                    parts.push_back(mul(Cl.Rt[cg], T[c], ct));   // r_c x p^2
-                    rows += parts.back().r;
-                }
-                Mat Z(rows, r0);
-                int off = 0;
-                for (int c = 0; c < 4; ++c) {
-                    for (int i = 0; i < parts[c].r; ++i)
-                        for (int j = 0; j < r0; ++j) Z.at(off + i, j) = parts[c].at(i, j);
-                    off += parts[c].r;
-                }
-                int g = ix + s * iy;
-                if (svd) {
-                    cpqr(mul(Z, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
-                    L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
-                } else {
-                    cpqr(Z, rank_tol, L.W[g], L.Rt[g], ct);
-                }
-                L.rank[g] = L.W[g].c;
+        L.rank.assign(nb, 0); L.W.resize(nb); L.Rt.resize(nb);
+        for (int g = 0; g < nb; ++g) {
+            const Box bx = box_at(g, s, d);
+            int rows = 0;
+            std::vector<Mat> parts;
+            for (int c = 0; c < nkid; ++c) {
+                const int cg = box_index(child_of(bx, c), 2 * s);
+                parts.push_back(mul(Cl.Rt[cg], T[c], ct));   // r_c x p^d
+                rows += parts.back().r;
             }
+            Mat Z(rows, r0);
+            int off = 0;
+            for (int c = 0; c < nkid; ++c) {
+                for (int i = 0; i < parts[c].r; ++i)
+                    for (int j = 0; j < r0; ++j) Z.at(off + i, j) = parts[c].at(i, j);
+                off += parts[c].r;
+            }
+            if (svd) {
+                cpqr(mul(Z, L.U, ct), rank_tol, L.W[g], L.Rt[g], ct);
+                L.Rt[g] = mul(L.Rt[g], transpose(L.U), ct);
+            } else {
+                cpqr(Z, rank_tol, L.W[g], L.Rt[g], ct);
+            }
+            L.rank[g] = L.W[g].c;
+        }
     }
     // M2L_ij = Rt_i K(nodes_i, nodes_j) Rt_j^T for j in I_i
+    const int n7 = n_off(d, 3), n3 = n_off(d, 1);
     for (int k = 2; k <= kap; ++k) {
         OpsLevel& L = h.ops[k];
-        int s = side_of(k);
-        L.M2L.assign((size_t)s * s * 49, Mat());
-        std::vector<std::vector<double>> NX(s * s), NY(s * s);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) box_nodes(h, k, ix, iy, NX[ix + s * iy], NY[ix + s * iy]);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix)
-                for (int dy = -3; dy <= 3; ++dy)
-                    for (int dx = -3; dx <= 3; ++dx) {
-                        int jx = ix + dx, jy = iy + dy;
-                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
-                        if (!in_interaction_list(ix, iy, jx, jy)) continue;
-                        int gi = ix + s * iy, gj = jx + s * jy;
-                        Mat Kc(r0, r0);
-                        for (int m = 0; m < r0; ++m)
-                            for (int l = 0; l < r0; ++l)
-                                Kc.at(m, l) = kernel_value(P, NX[gi][m], NY[gi][m], NX[gj][l], NY[gj][l]);
-                        Mat t1 = mul(L.Rt[gi], Kc, ct);
-                        L.M2L[(size_t)gi * 49 + d49(dx, dy)] = mul(t1, transpose(L.Rt[gj]), ct);
-                    }
+        const int s = side_of(k), nb = nboxes(d, k);
+        L.M2L.assign((size_t)nb * n7, Mat());
+        std::vector<std::vector<double>> ND(nb);
+        for (int g = 0; g < nb; ++g) box_nodes(h, k, box_at(g, s, d), ND[g]);
+        for (int gi = 0; gi < nb; ++gi) {
+            const Box bi = box_at(gi, s, d);
+            for (int o = 0; o < n7; ++o) {
+                const Box bj = offset_box(bi, o, d, 3);
+                if (!in_grid(bj, s, d) || !in_interaction_list(bi, bj)) continue;
+                const int gj = box_index(bj, s);
+                Mat Kc(r0, r0);
+                for (int m = 0; m < r0; ++m)
+                    for (int l = 0; l < r0; ++l) Kc.at(m, l) = kernel_value(P, &ND[gi][3 * m], &ND[gj][3 * l]);
+                Mat t1 = mul(L.Rt[gi], Kc, ct);
+                L.M2L[(size_t)gi * n7 + o] = mul(t1, transpose(L.Rt[gj]), ct);
+            }
+        }
     }
     // leaf P2P_ij[a, b] = K(x_a, x_b), diagonal A_aa = diag (reading R4)
-    h.leafP2P.assign((size_t)side * side * 9, Mat());
-    for (int iy = 0; iy < side; ++iy)
-        for (int ix = 0; ix < side; ++ix)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int jx = ix + dx, jy = iy + dy;
-                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-                    int gi = ix + side * iy, gj = jx + side * jy;
-                    int ni = h.leaf_count[gi], nj = h.leaf_count[gj];
-                    Mat B(ni, nj);
-                    for (int a = 0; a < ni; ++a)
-                        for (int b = 0; b < nj; ++b) {
-                            int64_t ta = h.leaf_start[gi] + a, tb = h.leaf_start[gj] + b;
-                            B.at(a, b) = (ta == tb) ? P.diag : kernel_value(P, h.px[ta], h.py[ta], h.px[tb], h.py[tb]);
-                        }
-                    if (dx == 0 && dy == 0)
-                        for (int j = 0; j < B.c; ++j) h.scale_A = std::max(h.scale_A, col_norm(B, j));
-                    h.leafP2P[(size_t)gi * 9 + d9(dx, dy)] = std::move(B);
+    h.leafP2P.assign((size_t)nleaf * n3, Mat());
+    for (int gi = 0; gi < nleaf; ++gi) {
+        const Box bi = box_at(gi, side, d);
+        for (int o = 0; o < n3; ++o) {
+            const Box bj = offset_box(bi, o, d, 1);
+            if (!in_grid(bj, side, d)) continue;
+            const int gj = box_index(bj, side);
+            const int ni = h.leaf_count[gi], nj = h.leaf_count[gj];
+            Mat B(ni, nj);
+            for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < nj; ++b) {
+                    int64_t ta = h.leaf_start[gi] + a, tb = h.leaf_start[gj] + b;
+                    B.at(a, b) = (ta == tb) ? P.diag : kernel_value(P, &h.pt[3 * ta], &h.pt[3 * tb]);
                 }
+            if (gj == gi)
+                for (int j = 0; j < B.c; ++j) h.scale_A = std::max(h.scale_A, col_norm(B, j));
+            h.leafP2P[(size_t)gi * n3 + o] = std::move(B);
+        }
+    }
     h.ct.add(ct);
     return true;
 }
@@ -846,23 +928,18 @@ bool build(Handle& h, const double* pts) {
 // ------------------------------------------------------------------------------------------
 struct Ctx { Handle* h; ElimLevel* L; };
 
-inline int gx(const ElimLevel& L, int g) { return g % L.side; }
-inline int gy(const ElimLevel& L, int g) { return g / L.side; }
+inline Box gbox(const ElimLevel& L, int g) { return box_at(g, L.side, L.d); }
 inline Mat& blk(std::vector<Mat>& v, const ElimLevel& L, int p, int q) {
-    return v[(size_t)p * 49 + d49(gx(L, q) - gx(L, p), gy(L, q) - gy(L, p))];
+    return v[(size_t)p * n_off(L.d, 3) + off_index(gbox(L, p), gbox(L, q), L.d, 3)];
 }
-bool well_separated(const ElimLevel& L, int p, int q) {
-    return cheb_dist(gx(L, p), gy(L, p), gx(L, q), gy(L, q)) >= 2;
-}
+bool well_separated(const ElimLevel& L, int p, int q) { return cheb_dist(gbox(L, p), gbox(L, q)) >= 2; }
 std::vector<int> neighbours(const ElimLevel& L, int g) {  // N_g, grid order, self included
     std::vector<int> out;
-    int ix = gx(L, g), iy = gy(L, g);
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            int jx = ix + dx, jy = iy + dy;
-            if (jx < 0 || jy < 0 || jx >= L.side || jy >= L.side) continue;
-            out.push_back(jx + L.side * jy);
-        }
+    const Box b = gbox(L, g);
+    for (int o = 0; o < n_off(L.d, 1); ++o) {
+        const Box q = offset_box(b, o, L.d, 1);
+        if (in_grid(q, L.side, L.d)) out.push_back(box_index(q, L.side));
+    }
     return out;
 }
 
@@ -1071,14 +1148,14 @@ bool eliminate(ElimLevel& L, int e, double eps, double ref, int rcap, Counter& c
 void make_level(Handle& h, int k) {
     ElimLevel& L = h.el[k];
     const OpsLevel& O = h.ops[k];
-    int s = side_of(k);
-    L.k = k; L.side = s; L.nb = s * s;
+    const int s = side_of(k), d = h.d, n7 = n_off(d, 3), n3 = n_off(d, 1), nkid = 1 << d;
+    L.k = k; L.side = s; L.d = d; L.nb = nboxes(d, k);
     L.n.assign(L.nb, 0); L.r.assign(L.nb, 0); L.E.assign(L.nb, 0);
     L.W.assign(L.nb, Mat());
-    size_t nblk = (size_t)L.nb * 49;
+    size_t nblk = (size_t)L.nb * n7;
     L.P2P.assign(nblk, Mat()); L.M2P.assign(nblk, Mat()); L.P2L.assign(nblk, Mat()); L.M2L.assign(nblk, Mat());
     L.fac.assign(L.nb, BoxFactor());
-    L.order = elimination_order(k, h.prm.order);
+    L.order = elimination_order(k, d, h.prm.order);
     for (int g = 0; g < L.nb; ++g) L.r[g] = O.rank[g];
     if (k == h.depth) {
         for (int g = 0; g < L.nb; ++g) {
@@ -1086,66 +1163,66 @@ void make_level(Handle& h, int k) {
             L.W[g] = O.W[g];
             if (!L.W[g].present()) L.W[g] = Mat(L.n[g], 0);
         }
-        for (int g = 0; g < L.nb; ++g)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
-                    if (B.present()) L.P2P[(size_t)g * 49 + d49(dx, dy)] = B;
-                }
+        for (int g = 0; g < L.nb; ++g) {
+            const Box b = gbox(L, g);
+            for (int o = 0; o < n3; ++o) {
+                const Box q = offset_box(b, o, d, 1);
+                const Mat& B = h.leafP2P[(size_t)g * n3 + o];
+                if (B.present()) L.P2P[(size_t)g * n7 + off_index(b, q, d, 3)] = B;
+            }
+        }
     } else {
         ElimLevel& C = h.el[k + 1];
         const OpsLevel& OC = h.ops[k + 1];
-        L.xoff.assign((size_t)L.nb * 5, 0);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int g = ix + s * iy;
-                int off = 0, ooff = 0;
-                std::vector<int> offs(4), ooffs(4), cg(4);
-                for (int c = 0; c < 4; ++c) {
-                    cg[c] = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
-                    offs[c] = off; ooffs[c] = ooff;
-                    L.xoff[(size_t)g * 5 + c] = off;
-                    off += C.r[cg[c]];
-                    ooff += OC.rank[cg[c]];
-                }
-                L.xoff[(size_t)g * 5 + 4] = off;
-                L.n[g] = off;
-                // L2P of the parent = stacked children L2L; augmented child components get
-                // zero rows
-                Mat W(off, O.rank[g]);
-                for (int c = 0; c < 4; ++c)
-                    for (int t = 0; t < OC.rank[cg[c]]; ++t)
-                        for (int j = 0; j < O.rank[g]; ++j)
-                            W.at(offs[c] + t, j) = (kPlant == 3 && c == 3) ? 0.0 : O.W[g].at(ooffs[c] + t, j);
-                L.W[g] = std::move(W);
+        L.xoff.assign((size_t)L.nb * (nkid + 1), 0);
+        for (int g = 0; g < L.nb; ++g) {
+            const Box b = gbox(L, g);
+            int off = 0, ooff = 0;
+            std::vector<int> offs(nkid), ooffs(nkid), cg(nkid);
+            for (int c = 0; c < nkid; ++c) {
+                cg[c] = box_index(child_of(b, c), 2 * s);
+                offs[c] = off; ooffs[c] = ooff;
+                L.xoff[(size_t)g * (nkid + 1) + c] = off;
+                off += C.r[cg[c]];
+                ooff += OC.rank[cg[c]];
             }
+            L.xoff[(size_t)g * (nkid + 1) + nkid] = off;
+            L.n[g] = off;
+            // L2P of the parent = stacked children L2L; augmented child components get
+            // zero rows
+            Mat W(off, O.rank[g]);
+            for (int c = 0; c < nkid; ++c)
+                for (int t = 0; t < OC.rank[cg[c]]; ++t)
+                    for (int j = 0; j < O.rank[g]; ++j)
+                        W.at(offs[c] + t, j) = (kPlant == 3 && c == 3) ? 0.0 : O.W[g].at(ooffs[c] + t, j);
+            L.W[g] = std::move(W);
+        }
         // P2P_PQ = [M2L_{c d}] over the children of neighbours P, Q
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int jx = ix + dx, jy = iy + dy;
-                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
-                        int g = ix + s * iy, q = jx + s * jy;
-                        Mat B(L.n[g], L.n[q]);
-                        for (int a = 0; a < 4; ++a)
-                            for (int b = 0; b < 4; ++b) {
-                                int ca = (2 * ix + (a & 1)) + 2 * s * (2 * iy + (a >> 1));
-                                int db = (2 * jx + (b & 1)) + 2 * s * (2 * jy + (b >> 1));
-                                const Mat& M = blk(C.M2L, C, ca, db);
-                                if (!M.present()) continue;
-                                int ro = L.xoff[(size_t)g * 5 + a], co = L.xoff[(size_t)q * 5 + b];
-                                for (int i = 0; i < M.r; ++i)
-                                    for (int j = 0; j < M.c; ++j) B.at(ro + i, co + j) = M.at(i, j);
-                            }
-                        L.P2P[(size_t)g * 49 + d49(dx, dy)] = std::move(B);
+        for (int g = 0; g < L.nb; ++g) {
+            const Box b = gbox(L, g);
+            for (int o = 0; o < n3; ++o) {
+                const Box qb = offset_box(b, o, d, 1);
+                if (!in_grid(qb, s, d)) continue;
+                const int q = box_index(qb, s);
+                Mat B(L.n[g], L.n[q]);
+                for (int a = 0; a < nkid; ++a)
+                    for (int c2 = 0; c2 < nkid; ++c2) {
+                        const int ca = box_index(child_of(b, a), 2 * s), db = box_index(child_of(qb, c2), 2 * s);
+                        const Mat& M = blk(C.M2L, C, ca, db);
+                        if (!M.present()) continue;
+                        const int ro = L.xoff[(size_t)g * (nkid + 1) + a], co = L.xoff[(size_t)q * (nkid + 1) + c2];
+                        for (int i = 0; i < M.r; ++i)
+                            for (int j = 0; j < M.c; ++j) B.at(ro + i, co + j) = M.at(i, j);
                     }
+                L.P2P[(size_t)g * n7 + off_index(b, qb, d, 3)] = std::move(B);
+            }
+        }
     }
     for (size_t t = 0; t < nblk; ++t)
         if (O.M2L[t].present()) L.M2L[t] = O.M2L[t];
     L.scale = 0.0;
     for (int g = 0; g < L.nb; ++g) {
-        const Mat& D = L.P2P[(size_t)g * 49 + d49(0, 0)];
+        const Mat& D = blk(L.P2P, L, g, g);
         if (!D.present()) continue;
         for (int j = 0; j < D.c; ++j) L.scale = std::max(L.scale, col_norm(D, j));
     }
@@ -1164,10 +1241,10 @@ int do_factor(Handle& h) {
         const double ref = h.prm.tau_ref == 1 ? h.scale_A : (h.prm.tau_ref == 2 ? L.scale : 0.0);
         if (h.prm.order == 0) {
             // same-colour boxes are at Chebyshev distance >= 3 and touch disjoint blocks
-            for (int col = 0; col < 9; ++col) {
+            for (int col = 0; col < ncolours(h.d); ++col) {
                 std::vector<int> boxes;
                 for (int g : L.order)
-                    if (colour_of(gx(L, g), gy(L, g)) == col) boxes.push_back(g);
+                    if (colour_of(gbox(L, g)) == col) boxes.push_back(g);
                 int bad = 0;
                 Counter tot;
 #pragma omp parallel
@@ -1269,14 +1346,15 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
         if (k > 2) {
             ElimLevel& U = h.el[k - 1];
             rhsP[k - 1].assign(U.nb, Mat());
+            const int nkid = 1 << h.d;
             for (int g = 0; g < U.nb; ++g) {
-                int ix = g % U.side, iy = g / U.side;
+                const Box b = gbox(U, g);
                 Mat R(U.n[g], nrhs);
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < nkid; ++c) {
                     // (plant 6: the children's x and y offsets swapped)
-                    const int cx = kPlant == 6 ? (c >> 1) : (c & 1), cy = kPlant == 6 ? (c & 1) : (c >> 1);
-                    int cg = (2 * ix + cx) + L.side * (2 * iy + cy);
-                    int off = U.xoff[(size_t)g * 5 + c];
+                    const int cc = kPlant == 6 ? (((c & 1) << 1) | ((c >> 1) & 1) | (c & 4)) : c;
+                    int cg = box_index(child_of(b, cc), L.side);
+                    int off = U.xoff[(size_t)g * (nkid + 1) + c];
                     for (int i = 0; i < L.r[cg]; ++i)
                         for (int j = 0; j < nrhs; ++j) R.at(off + i, j) = rhsZ[k][cg].at(i, j);
                 }
@@ -1331,11 +1409,12 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
         if (k < kap) {  // the children's multipoles are the particles of this level
             ElimLevel& C = h.el[k + 1];
             ys[k + 1].assign(C.nb, Mat());
+            const int nkid = 1 << h.d;
             for (int g = 0; g < L.nb; ++g) {
-                int ix = g % L.side, iy = g / L.side;
-                for (int c = 0; c < 4; ++c) {
-                    int cg = (2 * ix + (c & 1)) + C.side * (2 * iy + (c >> 1));
-                    int off = L.xoff[(size_t)g * 5 + c];
+                const Box b = gbox(L, g);
+                for (int c = 0; c < nkid; ++c) {
+                    int cg = box_index(child_of(b, c), C.side);
+                    int off = L.xoff[(size_t)g * (nkid + 1) + c];
                     Mat Y(C.r[cg], nrhs);
                     for (int i = 0; i < C.r[cg]; ++i)
                         for (int j = 0; j < nrhs; ++j) Y.at(i, j) = xs[k][g].at(off + i, j);
@@ -1354,103 +1433,90 @@ int do_solve(Handle& h, const double* b, double* x, int nrhs) {
 
 // FMM matvec with the operators of the build: y = A~ x
 void do_matvec(Handle& h, const double* x, double* y, int nrhs) {
-    int kap = h.depth;
+    const int kap = h.depth, d = h.d, nkid = 1 << d, n7 = n_off(d, 3), n3 = n_off(d, 1);
     Counter ct;
     std::vector<std::vector<Mat>> Y(kap + 1), Z(kap + 1);
-    int side = side_of(kap);
-    std::vector<Mat> xl(side * side);
-    for (int g = 0; g < side * side; ++g) {
+    const int side = side_of(kap), nleaf = nboxes(d, kap);
+    std::vector<Mat> xl(nleaf);
+    for (int g = 0; g < nleaf; ++g) {
         Mat X(h.leaf_count[g], nrhs);
         for (int a = 0; a < X.r; ++a)
             for (int j = 0; j < nrhs; ++j) X.at(a, j) = x[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]];
         xl[g] = std::move(X);
     }
     // upward pass: P2M, M2M
-    Y[kap].resize(side * side);
-    for (int g = 0; g < side * side; ++g) Y[kap][g] = mul_tn(h.ops[kap].W[g], xl[g], ct);
+    Y[kap].resize(nleaf);
+    for (int g = 0; g < nleaf; ++g) Y[kap][g] = mul_tn(h.ops[kap].W[g], xl[g], ct);
     for (int k = kap - 1; k >= 2; --k) {
-        int s = side_of(k);
-        Y[k].resize(s * s);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int g = ix + s * iy;
-                int rows = 0;
-                for (int c = 0; c < 4; ++c) rows += h.ops[k + 1].rank[(2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1))];
-                Mat X(rows, nrhs);
-                int off = 0;
-                for (int c = 0; c < 4; ++c) {
-                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
-                    for (int i = 0; i < Y[k + 1][cg].r; ++i)
-                        for (int j = 0; j < nrhs; ++j) X.at(off + i, j) = Y[k + 1][cg].at(i, j);
-                    off += Y[k + 1][cg].r;
-                }
-                Y[k][g] = mul_tn(h.ops[k].W[g], X, ct);
+        const int s = side_of(k), nb = nboxes(d, k);
+        Y[k].resize(nb);
+        for (int g = 0; g < nb; ++g) {
+            const Box b = box_at(g, s, d);
+            int rows = 0;
+            for (int c = 0; c < nkid; ++c) rows += h.ops[k + 1].rank[box_index(child_of(b, c), 2 * s)];
+            Mat X(rows, nrhs);
+            int off = 0;
+            for (int c = 0; c < nkid; ++c) {
+                const int cg = box_index(child_of(b, c), 2 * s);
+                for (int i = 0; i < Y[k + 1][cg].r; ++i)
+                    for (int j = 0; j < nrhs; ++j) X.at(off + i, j) = Y[k + 1][cg].at(i, j);
+                off += Y[k + 1][cg].r;
             }
+            Y[k][g] = mul_tn(h.ops[k].W[g], X, ct);
+        }
     }
     // M2L
     for (int k = 2; k <= kap; ++k) {
-        int s = side_of(k);
-        Z[k].resize(s * s);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int g = ix + s * iy;
-                Mat acc(h.ops[k].rank[g], nrhs);
-                for (int dy = -3; dy <= 3; ++dy)
-                    for (int dx = -3; dx <= 3; ++dx) {
-                        int jx = ix + dx, jy = iy + dy;
-                        if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
-                        const Mat& M = h.ops[k].M2L[(size_t)g * 49 + d49(dx, dy)];
-                        if (!M.present()) continue;
-                        Mat t = mul(M, Y[k][jx + s * jy], ct);
-                        add_into(acc, t, 1.0, ct);
-                    }
-                Z[k][g] = std::move(acc);
+        const int s = side_of(k), nb = nboxes(d, k);
+        Z[k].resize(nb);
+        for (int g = 0; g < nb; ++g) {
+            const Box b = box_at(g, s, d);
+            Mat acc(h.ops[k].rank[g], nrhs);
+            for (int o = 0; o < n7; ++o) {
+                const Box q = offset_box(b, o, d, 3);
+                if (!in_grid(q, s, d)) continue;
+                const Mat& M = h.ops[k].M2L[(size_t)g * n7 + o];
+                if (!M.present()) continue;
+                Mat t = mul(M, Y[k][box_index(q, s)], ct);
+                add_into(acc, t, 1.0, ct);
             }
+            Z[k][g] = std::move(acc);
+        }
     }
     // downward pass: L2L
     for (int k = 2; k < kap; ++k) {
-        int s = side_of(k);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int g = ix + s * iy;
-                Mat t = mul(h.ops[k].W[g], Z[k][g], ct);  // stacked children locals
-                int off = 0;
-                for (int c = 0; c < 4; ++c) {
-                    int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
-                    Mat& zc = Z[k + 1][cg];
-                    for (int i = 0; i < zc.r; ++i)
-                        for (int j = 0; j < nrhs; ++j) zc.at(i, j) += t.at(off + i, j);
-                    off += zc.r;
-                }
+        const int s = side_of(k), nb = nboxes(d, k);
+        for (int g = 0; g < nb; ++g) {
+            const Box b = box_at(g, s, d);
+            Mat t = mul(h.ops[k].W[g], Z[k][g], ct);  // stacked children locals
+            int off = 0;
+            for (int c = 0; c < nkid; ++c) {
+                Mat& zc = Z[k + 1][box_index(child_of(b, c), 2 * s)];
+                for (int i = 0; i < zc.r; ++i)
+                    for (int j = 0; j < nrhs; ++j) zc.at(i, j) += t.at(off + i, j);
+                off += zc.r;
             }
+        }
     }
     // L2P + P2P
-    for (int iy = 0; iy < side; ++iy)
-        for (int ix = 0; ix < side; ++ix) {
-            int g = ix + side * iy;
-            Mat out = mul(h.ops[kap].W[g], Z[kap][g], ct);
-            if (!out.present()) out = Mat(h.leaf_count[g], nrhs);
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int jx = ix + dx, jy = iy + dy;
-                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
-                    if (!B.present()) continue;
-                    Mat t = mul(B, xl[jx + side * jy], ct);
-                    add_into(out, t, 1.0, ct);
-                }
-            for (int a = 0; a < h.leaf_count[g]; ++a)
-                for (int j = 0; j < nrhs; ++j) y[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]] = out.present() ? out.at(a, j) : 0.0;
+    for (int g = 0; g < nleaf; ++g) {
+        const Box b = box_at(g, side, d);
+        Mat out = mul(h.ops[kap].W[g], Z[kap][g], ct);
+        if (!out.present()) out = Mat(h.leaf_count[g], nrhs);
+        for (int o = 0; o < n3; ++o) {
+            const Box q = offset_box(b, o, d, 1);
+            if (!in_grid(q, side, d)) continue;
+            const Mat& B = h.leafP2P[(size_t)g * n3 + o];
+            if (!B.present()) continue;
+            Mat t = mul(B, xl[box_index(q, side)], ct);
+            add_into(out, t, 1.0, ct);
         }
+        for (int a = 0; a < h.leaf_count[g]; ++a)
+            for (int j = 0; j < nrhs; ++j) y[(size_t)j * h.N + h.perm[h.leaf_start[g] + a]] = out.present() ? out.at(a, j) : 0.0;
+    }
 }
 
-int leaf_of_tree_pos(const Handle& h, int64_t t) {
-    int side = side_of(h.depth);
-    double ux = (h.px[t] - h.prm.box[0]) / h.prm.box[2], uy = (h.py[t] - h.prm.box[1]) / h.prm.box[2];
-    int ix = std::min((int)std::floor(ux * side), side - 1);
-    int iy = std::min((int)std::floor(uy * side), side - 1);
-    return ix + side * iy;
-}
+int leaf_of_tree_pos(const Handle& h, int64_t t) { return box_index(leaf_box(h, &h.pt[3 * t]), side_of(h.depth)); }
 
 }  // namespace
 
@@ -1467,12 +1533,20 @@ void* oracle_build(const double* pts, int64_t N, const oracle_params* prm) {
         !(prm->kparam[0] > 0.0))
         return nullptr;
     if (!(prm->svd_eps >= 0.0) || !std::isfinite(prm->svd_eps)) return nullptr;
+    const int d = prm->dim == 0 ? 2 : prm->dim;
+    if (d != 2 && d != 3) return nullptr;
+    if (d == 3 && (prm->depth > 7 || prm->cheb_p > 6)) return nullptr;
     auto h = std::make_unique<Handle>();
     h->prm = *prm;
     h->N = N;
     h->depth = prm->depth;
     h->p = prm->cheb_p;
-    h->r0 = prm->cheb_p * prm->cheb_p;
+    h->d = d;
+    h->r0 = d == 3 ? prm->cheb_p * prm->cheb_p * prm->cheb_p : prm->cheb_p * prm->cheb_p;
+    h->org[0] = prm->box[0];
+    h->org[1] = prm->box[1];
+    h->org[2] = d == 3 ? prm->z0 : 0.0;
+    h->Lside = prm->box[2];
 #ifdef _OPENMP
     if (prm->threads > 0) omp_set_num_threads(prm->threads);
 #endif
@@ -1509,7 +1583,7 @@ int oracle_dense_exact(void* hp, double* A) {
     for (int64_t i = 0; i < N; ++i)
         for (int64_t j = 0; j < N; ++j) {
             int64_t ui = h.perm[i], uj = h.perm[j];
-            A[ui * N + uj] = (i == j) ? h.prm.diag : kernel_value(h.prm, h.px[i], h.py[i], h.px[j], h.py[j]);
+            A[ui * N + uj] = (i == j) ? h.prm.diag : kernel_value(h.prm, &h.pt[3 * i], &h.pt[3 * j]);
         }
     return 0;
 }
@@ -1519,49 +1593,48 @@ int oracle_dense_exact(void* hp, double* A) {
 // interaction list, B_i^(kappa) = W_i, B_i^(k) = B_i^(k+1) W_anc[rows of the child]
 int oracle_dense_tilde(void* hp, double* A) {
     Handle& h = *static_cast<Handle*>(hp);
-    int kap = h.depth;
+    const int kap = h.depth, d = h.d, n7 = n_off(d, 3), n3 = n_off(d, 1);
     int64_t N = h.N;
     Counter ct;
-    int side = side_of(kap);
+    const int side = side_of(kap), nleaf = nboxes(d, kap);
     // per leaf, per level: chain basis (n_i x r_anc)
-    std::vector<std::vector<Mat>> Bc(side * side, std::vector<Mat>(kap + 1));
-    for (int g = 0; g < side * side; ++g) {
+    std::vector<std::vector<Mat>> Bc(nleaf, std::vector<Mat>(kap + 1));
+    for (int g = 0; g < nleaf; ++g) {
         Bc[g][kap] = h.ops[kap].W[g];
-        int ix = g % side, iy = g / side;
+        const Box lb = box_at(g, side, d);
         for (int k = kap - 1; k >= 2; --k) {
-            int cx = ix >> (kap - k - 1), cy = iy >> (kap - k - 1);   // ancestor at k+1
-            int px = cx >> 1, py = cy >> 1;
-            int c = (cx & 1) + 2 * (cy & 1);
-            int s = side_of(k);
-            const Mat& Wp = h.ops[k].W[px + s * py];
+            const Box cb = shifted(lb, kap - k - 1);   // ancestor at k+1
+            const Box pb = parent_of(cb);
+            const int c = child_pos(cb);
+            const int s = side_of(k);
+            const Mat& Wp = h.ops[k].W[box_index(pb, s)];
             int off = 0;
-            for (int cc = 0; cc < c; ++cc) off += h.ops[k + 1].rank[(2 * px + (cc & 1)) + 2 * s * (2 * py + (cc >> 1))];
-            int rc = h.ops[k + 1].rank[cx + 2 * s * cy];
+            for (int cc = 0; cc < c; ++cc) off += h.ops[k + 1].rank[box_index(child_of(pb, cc), 2 * s)];
+            int rc = h.ops[k + 1].rank[box_index(cb, 2 * s)];
             Mat sub(rc, Wp.c);
             for (int i = 0; i < rc; ++i)
                 for (int j = 0; j < Wp.c; ++j) sub.at(i, j) = Wp.at(off + i, j);
             Bc[g][k] = mul(Bc[g][k + 1], sub, ct);
         }
     }
-    for (int gi = 0; gi < side * side; ++gi)
-        for (int gj = 0; gj < side * side; ++gj) {
-            int ix = gi % side, iy = gi / side, jx = gj % side, jy = gj / side;
+    for (int gi = 0; gi < nleaf; ++gi)
+        for (int gj = 0; gj < nleaf; ++gj) {
+            const Box bi = box_at(gi, side, d), bj = box_at(gj, side, d);
             int ni = h.leaf_count[gi], nj = h.leaf_count[gj];
             if (ni == 0 || nj == 0) continue;
             Mat blkv;
-            if (cheb_dist(ix, iy, jx, jy) <= 1) {
-                blkv = h.leafP2P[(size_t)gi * 9 + d9(jx - ix, jy - iy)];
+            if (cheb_dist(bi, bj) <= 1) {
+                blkv = h.leafP2P[(size_t)gi * n3 + off_index(bi, bj, d, 1)];
             } else {
                 int k = kap;
                 while (k >= 2) {
                     int sh = kap - k;
-                    if (in_interaction_list(ix >> sh, iy >> sh, jx >> sh, jy >> sh)) break;
+                    if (in_interaction_list(shifted(bi, sh), shifted(bj, sh))) break;
                     --k;
                 }
-                int sh = kap - k, s = side_of(k);
-                int I = (ix >> sh) + s * (iy >> sh);
-                int dx = (jx >> sh) - (ix >> sh), dy = (jy >> sh) - (iy >> sh);
-                const Mat& M = h.ops[k].M2L[(size_t)I * 49 + d49(dx, dy)];
+                const int sh = kap - k, s = side_of(k);
+                const Box I = shifted(bi, sh), J = shifted(bj, sh);
+                const Mat& M = h.ops[k].M2L[(size_t)box_index(I, s) * n7 + off_index(I, J, d, 3)];
                 Mat t = mul(Bc[gi][k], M, ct);
                 blkv = mul(t, transpose(Bc[gj][k]), ct);
             }
@@ -1579,15 +1652,15 @@ int oracle_dense_tilde(void* hp, double* A) {
 // neighbouring leaves
 int oracle_dense_tilde_direct(void* hp, double* A) {
     Handle& h = *static_cast<Handle*>(hp);
-    int kap = h.depth, r0 = h.r0;
+    const int kap = h.depth, r0 = h.r0, d = h.d;
     int64_t N = h.N;
-    std::vector<double> si(r0), sj(r0), nix, niy, njx, njy;
+    std::vector<double> si(r0), sj(r0), ndi, ndj;
     // with the SVD compression the interpolation from level k's nodes to a particle passes through
     // every level between: s = S^leaf(x) Pi_kappa, then s <- s T_c Pi_k' going up, where
     // Pi_k = U_k U_k^T projects onto the kept singular vectors (T_c: the transfer of the ancestor's
     // child position c)
     const bool svd = h.prm.svd_eps > 0.0;
-    const std::vector<Mat> T = transfer_mats(h.p);
+    const std::vector<Mat> T = transfer_mats(h.p, d);
     auto project = [&](int k, std::vector<double>& s) {
         const Mat& U = h.ops[k].U;
         std::vector<double> c(U.c, 0.0), out(r0, 0.0);
@@ -1597,12 +1670,12 @@ int oracle_dense_tilde_direct(void* hp, double* A) {
             for (int j = 0; j < U.c; ++j) out[m] += U.at(m, j) * c[j];
         s = out;
     };
-    auto chain = [&](int64_t t, int lx, int ly, int k, std::vector<double>& s) {
-        box_basis(h, kap, lx, ly, h.px[t], h.py[t], s.data());
+    auto chain = [&](int64_t t, const Box& lb, int k, std::vector<double>& s) {
+        box_basis(h, kap, lb, &h.pt[3 * t], s.data());
         project(kap, s);
         for (int kk = kap - 1; kk >= k; --kk) {
-            const int cx = lx >> (kap - kk - 1), cy = ly >> (kap - kk - 1);   // ancestor at kk + 1
-            const Mat& Tc = T[(cx & 1) + 2 * (cy & 1)];
+            const Box cb = shifted(lb, kap - kk - 1);   // ancestor at kk + 1
+            const Mat& Tc = T[child_pos(cb)];
             std::vector<double> out(r0, 0.0);
             for (int m = 0; m < r0; ++m)
                 for (int l = 0; l < r0; ++l) out[l] += s[m] * Tc.at(m, l);
@@ -1610,30 +1683,29 @@ int oracle_dense_tilde_direct(void* hp, double* A) {
             project(kk, s);
         }
     };
+    const int side = side_of(kap);
     for (int64_t a = 0; a < N; ++a)
         for (int64_t b = 0; b < N; ++b) {
-            int la = leaf_of_tree_pos(h, a), lb = leaf_of_tree_pos(h, b);
-            int side = side_of(kap);
-            int ix = la % side, iy = la / side, jx = lb % side, jy = lb / side;
+            const Box bi = box_at(leaf_of_tree_pos(h, a), side, d), bj = box_at(leaf_of_tree_pos(h, b), side, d);
             double v;
-            if (cheb_dist(ix, iy, jx, jy) <= 1) {
-                v = (a == b) ? h.prm.diag : kernel_value(h.prm, h.px[a], h.py[a], h.px[b], h.py[b]);
+            if (cheb_dist(bi, bj) <= 1) {
+                v = (a == b) ? h.prm.diag : kernel_value(h.prm, &h.pt[3 * a], &h.pt[3 * b]);
             } else {
                 int k = kap;
-                while (k >= 2 && !in_interaction_list(ix >> (kap - k), iy >> (kap - k), jx >> (kap - k), jy >> (kap - k))) --k;
-                int sh = kap - k;
+                while (k >= 2 && !in_interaction_list(shifted(bi, kap - k), shifted(bj, kap - k))) --k;
+                const int sh = kap - k;
                 if (svd) {
-                    chain(a, ix, iy, k, si);
-                    chain(b, jx, jy, k, sj);
+                    chain(a, bi, k, si);
+                    chain(b, bj, k, sj);
                 } else {
-                    box_basis(h, k, ix >> sh, iy >> sh, h.px[a], h.py[a], si.data());
-                    box_basis(h, k, jx >> sh, jy >> sh, h.px[b], h.py[b], sj.data());
+                    box_basis(h, k, shifted(bi, sh), &h.pt[3 * a], si.data());
+                    box_basis(h, k, shifted(bj, sh), &h.pt[3 * b], sj.data());
                 }
-                box_nodes(h, k, ix >> sh, iy >> sh, nix, niy);
-                box_nodes(h, k, jx >> sh, jy >> sh, njx, njy);
+                box_nodes(h, k, shifted(bi, sh), ndi);
+                box_nodes(h, k, shifted(bj, sh), ndj);
                 v = 0.0;
                 for (int m = 0; m < r0; ++m)
-                    for (int l = 0; l < r0; ++l) v += si[m] * kernel_value(h.prm, nix[m], niy[m], njx[l], njy[l]) * sj[l];
+                    for (int l = 0; l < r0; ++l) v += si[m] * kernel_value(h.prm, &ndi[3 * m], &ndj[3 * l]) * sj[l];
             }
             A[h.perm[a] * N + h.perm[b]] = v;
         }
@@ -1646,14 +1718,14 @@ int oracle_dense_tilde_direct(void* hp, double* A) {
 // -z_i + sum_{J in I_i} M2L_iJ y_J + L2L_i z_parent = 0 at every level k >= 2.
 int oracle_extended_solve(void* hp, const double* b, double* x, int nrhs) {
     Handle& h = *static_cast<Handle*>(hp);
-    int kap = h.depth;
+    const int kap = h.depth, d = h.d, nkid = 1 << d, n7 = n_off(d, 3), n3 = n_off(d, 1);
     int64_t N = h.N;
     std::vector<std::vector<int64_t>> yoff(kap + 1), zoff(kap + 1);
     int64_t M = N;
     for (int k = kap; k >= 2; --k) {
-        int s = side_of(k);
-        yoff[k].resize(s * s); zoff[k].resize(s * s);
-        for (int g = 0; g < s * s; ++g) {
+        const int nb = nboxes(d, k);
+        yoff[k].resize(nb); zoff[k].resize(nb);
+        for (int g = 0; g < nb; ++g) {
             yoff[k][g] = M; M += h.ops[k].rank[g];
             zoff[k][g] = M; M += h.ops[k].rank[g];
         }
@@ -1661,68 +1733,67 @@ int oracle_extended_solve(void* hp, const double* b, double* x, int nrhs) {
     if (M > 20000) return 1;
     std::vector<double> D((size_t)M * M, 0.0), R((size_t)M * nrhs, 0.0);
     auto Dat = [&](int64_t i, int64_t j) -> double& { return D[(size_t)i * M + j]; };
-    int side = side_of(kap);
+    const int side = side_of(kap), nleaf = nboxes(d, kap);
     // leaf P2P rows
-    for (int g = 0; g < side * side; ++g) {
-        int ix = g % side, iy = g / side;
+    for (int g = 0; g < nleaf; ++g) {
+        const Box bg = box_at(g, side, d);
         for (int a = 0; a < h.leaf_count[g]; ++a) {
             int64_t row = h.leaf_start[g] + a;
             for (int j = 0; j < nrhs; ++j) R[(size_t)row * nrhs + j] = b[(size_t)j * N + h.perm[row]];
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int jx = ix + dx, jy = iy + dy;
-                    if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-                    int q = jx + side * jy;
-                    const Mat& B = h.leafP2P[(size_t)g * 9 + d9(dx, dy)];
-                    for (int c = 0; c < h.leaf_count[q]; ++c) Dat(row, h.leaf_start[q] + c) = B.at(a, c);
-                }
+            for (int o = 0; o < n3; ++o) {
+                const Box qb = offset_box(bg, o, d, 1);
+                if (!in_grid(qb, side, d)) continue;
+                const int q = box_index(qb, side);
+                const Mat& B = h.leafP2P[(size_t)g * n3 + o];
+                for (int c = 0; c < h.leaf_count[q]; ++c) Dat(row, h.leaf_start[q] + c) = B.at(a, c);
+            }
             for (int m = 0; m < h.ops[kap].rank[g]; ++m) Dat(row, zoff[kap][g] + m) = h.ops[kap].W[g].at(a, m);
         }
     }
     for (int k = kap; k >= 2; --k) {
-        int s = side_of(k);
-        for (int iy = 0; iy < s; ++iy)
-            for (int ix = 0; ix < s; ++ix) {
-                int g = ix + s * iy, r = h.ops[k].rank[g];
-                const Mat& W = h.ops[k].W[g];
-                // P2M rows: W^T x_g - y_g = 0, x_g = leaf particles or the children's y
-                for (int m = 0; m < r; ++m) {
-                    int64_t row = yoff[k][g] + m;
-                    Dat(row, yoff[k][g] + m) = -1.0;
-                    if (k == kap) {
-                        for (int a = 0; a < h.leaf_count[g]; ++a) Dat(row, h.leaf_start[g] + a) = W.at(a, m);
-                    } else {
-                        int off = 0;
-                        for (int c = 0; c < 4; ++c) {
-                            int cg = (2 * ix + (c & 1)) + 2 * s * (2 * iy + (c >> 1));
-                            for (int t = 0; t < h.ops[k + 1].rank[cg]; ++t) Dat(row, yoff[k + 1][cg] + t) = W.at(off + t, m);
-                            off += h.ops[k + 1].rank[cg];
-                        }
-                    }
-                }
-                // M2L rows
-                for (int m = 0; m < r; ++m) {
-                    int64_t row = zoff[k][g] + m;
-                    Dat(row, zoff[k][g] + m) = -1.0;
-                    for (int dy = -3; dy <= 3; ++dy)
-                        for (int dx = -3; dx <= 3; ++dx) {
-                            int jx = ix + dx, jy = iy + dy;
-                            if (jx < 0 || jy < 0 || jx >= s || jy >= s) continue;
-                            const Mat& Mm = h.ops[k].M2L[(size_t)g * 49 + d49(dx, dy)];
-                            if (!Mm.present()) continue;
-                            int q = jx + s * jy;
-                            for (int l = 0; l < Mm.c; ++l) Dat(row, yoff[k][q] + l) = Mm.at(m, l);
-                        }
-                    if (k > 2) {  // L2L from the parent's locals
-                        int px = ix >> 1, py = iy >> 1, ps = side_of(k - 1), pg = px + ps * py;
-                        int c = (ix & 1) + 2 * (iy & 1);
-                        int off = 0;
-                        for (int cc = 0; cc < c; ++cc) off += h.ops[k].rank[(2 * px + (cc & 1)) + 2 * ps * (2 * py + (cc >> 1))];
-                        const Mat& Wp = h.ops[k - 1].W[pg];
-                        for (int l = 0; l < Wp.c; ++l) Dat(row, zoff[k - 1][pg] + l) = Wp.at(off + m, l);
+        const int s = side_of(k), nb = nboxes(d, k);
+        for (int g = 0; g < nb; ++g) {
+            const Box bg = box_at(g, s, d);
+            const int r = h.ops[k].rank[g];
+            const Mat& W = h.ops[k].W[g];
+            // P2M rows: W^T x_g - y_g = 0, x_g = leaf particles or the children's y
+            for (int m = 0; m < r; ++m) {
+                int64_t row = yoff[k][g] + m;
+                Dat(row, yoff[k][g] + m) = -1.0;
+                if (k == kap) {
+                    for (int a = 0; a < h.leaf_count[g]; ++a) Dat(row, h.leaf_start[g] + a) = W.at(a, m);
+                } else {
+                    int off = 0;
+                    for (int c = 0; c < nkid; ++c) {
+                        const int cg = box_index(child_of(bg, c), 2 * s);
+                        for (int t = 0; t < h.ops[k + 1].rank[cg]; ++t) Dat(row, yoff[k + 1][cg] + t) = W.at(off + t, m);
+                        off += h.ops[k + 1].rank[cg];
                     }
                 }
             }
+            // M2L rows
+            for (int m = 0; m < r; ++m) {
+                int64_t row = zoff[k][g] + m;
+                Dat(row, zoff[k][g] + m) = -1.0;
+                for (int o = 0; o < n7; ++o) {
+                    const Box qb = offset_box(bg, o, d, 3);
+                    if (!in_grid(qb, s, d)) continue;
+                    const Mat& Mm = h.ops[k].M2L[(size_t)g * n7 + o];
+                    if (!Mm.present()) continue;
+                    const int q = box_index(qb, s);
+                    for (int l = 0; l < Mm.c; ++l) Dat(row, yoff[k][q] + l) = Mm.at(m, l);
+                }
+                if (k > 2) {  // L2L from the parent's locals
+                    const Box pb = parent_of(bg);
+                    const int ps = side_of(k - 1), pg = box_index(pb, ps);
+                    const int c = child_pos(bg);
+                    int off = 0;
+                    for (int cc = 0; cc < c; ++cc) off += h.ops[k].rank[box_index(child_of(pb, cc), s)];
+                    const Mat& Wp = h.ops[k - 1].W[pg];
+                    for (int l = 0; l < Wp.c; ++l) Dat(row, zoff[k - 1][pg] + l) = Wp.at(off + m, l);
+                }
+            }
+        }
     }
     Mat Dm; Dm.r = (int)M; Dm.c = (int)M; Dm.a = std::move(D);
     std::vector<int> piv;
@@ -1751,8 +1822,7 @@ int oracle_dense_lu_solve(const double* A, int64_t n, const double* b, double* x
 }
 
 int oracle_num_boxes(void* hp, int level) {
-    (void)hp;
-    return side_of(level) * side_of(level);
+    return nboxes(static_cast<Handle*>(hp)->d, level);
 }
 
 int oracle_ranks(void* hp, int level, int* out) {
@@ -1805,20 +1875,20 @@ int oracle_perm(void* hp, int64_t* out) {
 int oracle_lists(void* hp, int level, int box, int* nbr, int* n_nbr, int* inter, int* n_inter) {
     Handle& h = *static_cast<Handle*>(hp);
     if (level < 1 || level > h.depth) return 1;
-    int s = side_of(level);
-    int ix = box % s, iy = box / s;
+    const int s = side_of(level), nb = nboxes(h.d, level);
+    const Box bi = box_at(box, s, h.d);
     *n_nbr = 0; *n_inter = 0;
-    for (int jy = 0; jy < s; ++jy)
-        for (int jx = 0; jx < s; ++jx) {
-            if (cheb_dist(ix, iy, jx, jy) <= 1) nbr[(*n_nbr)++] = jx + s * jy;
-            else if (in_interaction_list(ix, iy, jx, jy)) inter[(*n_inter)++] = jx + s * jy;
-        }
+    for (int g = 0; g < nb; ++g) {
+        const Box bj = box_at(g, s, h.d);
+        if (cheb_dist(bi, bj) <= 1) nbr[(*n_nbr)++] = g;
+        else if (in_interaction_list(bi, bj)) inter[(*n_inter)++] = g;
+    }
     return 0;
 }
 
 int oracle_order(void* hp, int level, int* out) {
     Handle& h = *static_cast<Handle*>(hp);
-    std::vector<int> o = elimination_order(level, h.prm.order);
+    std::vector<int> o = elimination_order(level, h.d, h.prm.order);
     for (size_t t = 0; t < o.size(); ++t) out[t] = o[t];
     return 0;
 }
@@ -1840,15 +1910,22 @@ void oracle_lagrange(int p, double t, double* out) {
 }
 
 int oracle_kernel_eval(const oracle_params* prm, const double* a, const double* b, double* out) {
-    *out = kernel_value(*prm, a[0], a[1], b[0], b[1]);
+    const int d = prm->dim == 3 ? 3 : 2;
+    double x[3] = {0.0, 0.0, 0.0}, y[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < d; ++i) { x[i] = a[i]; y[i] = b[i]; }
+    *out = kernel_value(*prm, x, y);
     return 0;
 }
 
 int oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
                          double* out) {
+    const int d = prm->dim == 3 ? 3 : 2;
     for (int64_t i = 0; i < m; ++i)
-        for (int64_t j = 0; j < n; ++j)
-            out[i * n + j] = kernel_value(*prm, P[2 * i], P[2 * i + 1], Q[2 * j], Q[2 * j + 1]);
+        for (int64_t j = 0; j < n; ++j) {
+            double x[3] = {0.0, 0.0, 0.0}, y[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < d; ++c) { x[c] = P[d * i + c]; y[c] = Q[d * j + c]; }
+            out[i * n + j] = kernel_value(*prm, x, y);
+        }
     return 0;
 }
 

@@ -7,7 +7,7 @@
  * smoke check and by the bench's CPU-baseline leg, and by nothing in the product library.
  * It shares no code with the CUDA path.
  *
- * All vectors are in the caller's point order, column-major N x nrhs.
+ * All vectors are in the caller's point order, column-major N x nrhs. Points are N x dim, row-major.
  * Return codes: 0 = ok, 1 = invalid argument, 4 = singular pivot, 8 = wrong call order.
  */
 #ifndef IFMM_ORACLE_H
@@ -24,8 +24,8 @@ enum { ORACLE_K_INV_R = 0, ORACLE_K_EXP = 1, ORACLE_K_DEXP_DELL = 2, ORACLE_K_PO
                           of the SVD truncation) */ };
 
 typedef struct {
-    int depth;          /* leaf level kappa >= 2 of the uniform quadtree                      */
-    int cheb_p;         /* Chebyshev nodes per dimension; initial rank p^2                      */
+    int depth;          /* leaf level kappa >= 2 of the uniform tree (<= 7 in 3D)              */
+    int cheb_p;         /* Chebyshev nodes per dimension; initial rank p^dim (p <= 6 in 3D)     */
     int kernel;         /* ORACLE_K_*                                                           */
     int r_cap;          /* upper bound on any box rank (<= 0: no cap besides n_i)              */
     double eps;         /* relative compression tolerance of the fill-ins                      */
@@ -44,6 +44,11 @@ typedef struct {
                            [K(nodes_0, nodes_0 + h_k d)] over the 40 interaction offsets d, keeping
                            those with sigma_j > svd_eps * sigma_1 (translation-invariant kernels);
                            0: no truncation                                                       */
+    int dim;            /* space dimension: 2 (quadtree; 0 means 2) or 3 (octree, Section 4.2's
+                           extension to 3D: 27 neighbours, up to 189 interaction-list boxes, 27
+                           colours, p^3 Chebyshev nodes); points are N x dim, row-major          */
+    double z0;          /* dim 3: lower z of the root cube [box[0], +box[2]] x [box[1], +box[2]] x
+                           [z0, z0 + box[2]]                                                      */
 } oracle_params;
 
 void* oracle_build(const double* pts, int64_t N, const oracle_params* prm);
@@ -61,7 +66,7 @@ int   oracle_dense_lu_solve(const double* A, int64_t n, const double* b, double*
 
 /* introspection for the tests */
 int   oracle_num_boxes(void* h, int level);
-int   oracle_ranks(void* h, int level, int* out);          /* final ranks, grid order ix + side*iy   */
+int   oracle_ranks(void* h, int level, int* out);          /* final ranks, grid order ix + s (iy + s iz) */
 int   oracle_initial_ranks(void* h, int level, int* out);  /* ranks after orthonormalisation         */
 int   oracle_leaf_counts(void* h, int* out);
 int   oracle_perm(void* h, int64_t* out);                  /* tree position -> caller index           */
@@ -76,7 +81,8 @@ int   oracle_stats(void* h, double* out, int nout);
 void  oracle_cheb_nodes(int p, double* t);
 void  oracle_lagrange(int p, double t, double* out);
 int   oracle_kernel_eval(const oracle_params* prm, const double* a, const double* b, double* out);
-/* out[i * n + j] = K(P_i, Q_j) for m points P and n points Q (row-major x, y pairs), no diagonal */
+/* out[i * n + j] = K(P_i, Q_j) for m points P and n points Q (row-major, dim coordinates each),
+ * no diagonal; a and b of oracle_kernel_eval likewise hold dim coordinates */
 int   oracle_kernel_matrix(const oracle_params* prm, const double* P, int64_t m, const double* Q, int64_t n,
                            double* out);
 

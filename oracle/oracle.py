@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("r_cap", ctypes.c_int), ("eps", ctypes.c_double), ("diag", ctypes.c_double),
                 ("kparam", ctypes.c_double * 4), ("box", ctypes.c_double * 3),
                 ("order", ctypes.c_int), ("threads", ctypes.c_int), ("tau_ref", ctypes.c_int),
-                ("svd_eps", ctypes.c_double)]
+                ("svd_eps", ctypes.c_double), ("dim", ctypes.c_int), ("z0", ctypes.c_double)]
 
 
 def _load():
@@ -89,7 +89,8 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(depth, cheb_p, kernel=K_INV_R, eps=1e-10, diag=1.0, r_cap=0, kparam=(0, 0, 0, 0),
-                box=(0.0, 0.0, 1.0), order=0, threads=0, tau_ref=0, svd_eps=0.0) -> Params:
+                box=(0.0, 0.0, 1.0), order=0, threads=0, tau_ref=0, svd_eps=0.0, dim=2, z0=0.0) -> Params:
+    """box = (x0, y0, side); in 3D (dim = 3) the root cube also starts at z0."""
     p = Params()
     p.depth, p.cheb_p, p.kernel, p.r_cap = depth, cheb_p, kernel, r_cap
     p.eps, p.diag = eps, diag
@@ -99,6 +100,7 @@ def make_params(depth, cheb_p, kernel=K_INV_R, eps=1e-10, diag=1.0, r_cap=0, kpa
         p.box[i] = float(box[i])
     p.order, p.threads, p.tau_ref = order, threads, tau_ref
     p.svd_eps = svd_eps
+    p.dim, p.z0 = dim, z0
     return p
 
 
@@ -123,9 +125,10 @@ def kernel_eval(params: Params, a, b) -> float:
 
 
 def kernel_matrix(params: Params, P, Q) -> np.ndarray:
-    """K(P_i, Q_j) for point sets P (m x 2) and Q (n x 2): the kernel alone, no diagonal term."""
-    P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, 2)
-    Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(-1, 2)
+    """K(P_i, Q_j) for point sets P (m x dim) and Q (n x dim): the kernel alone, no diagonal term."""
+    d = params.dim if params.dim else 2
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, d)
+    Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(-1, d)
     out = np.zeros((P.shape[0], Q.shape[0]))
     _load().oracle_kernel_matrix(ctypes.byref(params), _ptr(P), P.shape[0], _ptr(Q), Q.shape[0], _ptr(out))
     return out
@@ -164,7 +167,8 @@ class Oracle:
 
     def __init__(self, points: np.ndarray, params: Params):
         self._lib = _load()
-        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+        self.dim = params.dim if params.dim else 2
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, self.dim)
         self.N = pts.shape[0]
         self.params = params
         self.depth = params.depth
@@ -217,15 +221,19 @@ class Oracle:
     def dense_exact(self) -> np.ndarray:
         return self._dense(self._lib.oracle_dense_exact)
 
+    def num_boxes(self, level: int) -> int:
+        """Boxes of a level: 2^(dim level)."""
+        return 1 << (self.dim * level)
+
     def ranks(self, level: int) -> np.ndarray:
-        out = np.zeros(4 ** level, dtype=np.int32)
+        out = np.zeros(self.num_boxes(level), dtype=np.int32)
         rc = self._lib.oracle_ranks(self._h, level, _ptr(out))
         if rc:
             raise RuntimeError("oracle_ranks: not factored")
         return out
 
     def initial_ranks(self, level: int) -> np.ndarray:
-        out = np.zeros(4 ** level, dtype=np.int32)
+        out = np.zeros(self.num_boxes(level), dtype=np.int32)
         self._lib.oracle_initial_ranks(self._h, level, _ptr(out))
         return out
 
@@ -241,7 +249,7 @@ class Oracle:
         return U, sg, int(r)
 
     def leaf_counts(self) -> np.ndarray:
-        out = np.zeros(4 ** self.depth, dtype=np.int32)
+        out = np.zeros(self.num_boxes(self.depth), dtype=np.int32)
         self._lib.oracle_leaf_counts(self._h, _ptr(out))
         return out
 
@@ -251,15 +259,15 @@ class Oracle:
         return out
 
     def lists(self, level: int, box: int):
-        nb = np.zeros(4 ** level, dtype=np.int32)
-        it = np.zeros(4 ** level, dtype=np.int32)
+        nb = np.zeros(self.num_boxes(level), dtype=np.int32)
+        it = np.zeros(self.num_boxes(level), dtype=np.int32)
         nn = np.zeros(1, dtype=np.int32)
         ni = np.zeros(1, dtype=np.int32)
         self._lib.oracle_lists(self._h, level, box, _ptr(nb), _ptr(nn), _ptr(it), _ptr(ni))
         return nb[: nn[0]].copy(), it[: ni[0]].copy()
 
     def order(self, level: int) -> np.ndarray:
-        out = np.zeros(4 ** level, dtype=np.int32)
+        out = np.zeros(self.num_boxes(level), dtype=np.int32)
         self._lib.oracle_order(self._h, level, _ptr(out))
         return out
 

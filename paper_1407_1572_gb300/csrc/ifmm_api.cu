@@ -334,6 +334,31 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     CKS(upload(h, &h->d_Tc, Tc));
     BuildArgs ba{N, kap, p, r0, h->kernel, h->prm.kparam[0], h->prm.diag, h->prm.box[0], h->prm.box[1], h->prm.box[2]};
     h->ops.assign(kap + 1, OpsLevel());
+    // SVD compression of the Chebyshev interpolation (svd_eps > 0): per level, top first, the kept
+    // singular vectors U_k (r0 x r0 arrays, the first rsvd[k] columns used), freed after the build
+    double* d_U = nullptr;
+    double* d_sig = nullptr;
+    int* d_rsvd = nullptr;
+    double* d_svd_scr = nullptr;
+    for (int k = 0; k < 16; ++k) h->stats.svd_ranks[k] = 0;
+    if (h->prm.svd_eps > 0.0) {
+        CKS(dalloc(h, &d_U, sizeof(double) * (size_t)(kap + 1) * r0 * r0));
+        CKS(dalloc(h, &d_sig, sizeof(double) * (size_t)(kap + 1) * r0));
+        CKS(dalloc(h, &d_rsvd, sizeof(int) * (size_t)(kap + 1)));
+        CKS(dalloc(h, &d_svd_scr, sizeof(double) * svd_scratch_doubles(r0)));
+        for (int k = 2; k <= kap; ++k) {
+            const bool top = k == 2;
+            launch_svd_level(ba, k, h->prm.svd_eps, h->d_cheb, h->d_Tc, top ? nullptr : d_U + (size_t)(k - 1) * r0 * r0,
+                             top ? nullptr : d_sig + (size_t)(k - 1) * r0, top ? nullptr : d_rsvd + (k - 1),
+                             d_U + (size_t)k * r0 * r0, d_sig + (size_t)k * r0, d_rsvd + k, d_svd_scr, h->st);
+        }
+        std::vector<int> rs(kap + 1, 0);
+        CK(cudaMemcpyAsync(rs.data(), d_rsvd, sizeof(int) * (kap + 1), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (int k = 2; k <= kap && k < 16; ++k) h->stats.svd_ranks[k] = rs[k];
+    }
+    auto Uk = [&](int k) -> const double* { return d_U ? d_U + (size_t)k * r0 * r0 : nullptr; };
+    auto rk = [&](int k) -> const int* { return d_rsvd ? d_rsvd + k : nullptr; };
     // leaf bases (W0 allocation holds 2 scratch copies behind the basis)
     {
         OpsLevel& O = h->ops[kap];
@@ -341,7 +366,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nleaf * r0 * r0));
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nleaf));
         launch_leaf_basis(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_cheb, O.d_W0, O.d_Rt,
-                          O.d_rank0, max_n, h->st);
+                          O.d_rank0, max_n, Uk(kap), rk(kap), h->st);
         O.nW0 = (int64_t)N * r0;
     }
     for (int k = kap - 1; k >= 2; --k) {
@@ -350,7 +375,8 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_W0, sizeof(double) * 4 * (size_t)nb * 4 * r0 * r0));
         CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nb * r0 * r0));
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nb));
-        launch_parent_basis(ba, k, h->ops[k + 1].d_Rt, h->ops[k + 1].d_rank0, h->d_Tc, O.d_W0, O.d_Rt, O.d_rank0, h->st);
+        launch_parent_basis(ba, k, h->ops[k + 1].d_Rt, h->ops[k + 1].d_rank0, h->d_Tc, O.d_W0, O.d_Rt, O.d_rank0,
+                            Uk(k), rk(k), h->st);
         O.nW0 = (int64_t)nb * 4 * r0 * r0;
     }
     for (int k = 2; k <= kap; ++k) {
@@ -363,6 +389,10 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         O.rank0.assign(nb, 0);
         CK(cudaMemcpyAsync(O.rank0.data(), O.d_rank0, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->st));
     }
+    dfree_ptr(h, d_U);
+    dfree_ptr(h, d_sig);
+    dfree_ptr(h, d_rsvd);
+    dfree_ptr(h, d_svd_scr);
     // leaf P2P
     h->p2p_off.assign((size_t)nleaf * 9, 0);
     int64_t po = 0;
@@ -1464,6 +1494,7 @@ void ifmm_default_params(ifmm_params* p) {
     p->refine_inner = 1e-4;
     p->leaf_max = 64;
     p->tc_products = 0;
+    p->svd_eps = 0.0;
 }
 
 // Smallest depth 2..10 of the uniform tree whose fullest leaf holds at most leaf_max points, with the
@@ -1504,6 +1535,7 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     if (p->tau_ref < 0 || p->tau_ref > 2) return IFMM_ERR_INVALID_ARG;
     if (p->r_cap > 0 && p->r_cap < p->cheb_p * p->cheb_p) return IFMM_ERR_INVALID_ARG;
     if (p->tc_products < 0 || p->tc_products > 2) return IFMM_ERR_INVALID_ARG;
+    if (!(p->svd_eps >= 0.0 && p->svd_eps < 1.0)) return IFMM_ERR_INVALID_ARG;
     for (int64_t i = 0; i < 2 * N; ++i)
         if (!std::isfinite(pts_host[i])) return IFMM_ERR_INVALID_ARG;
     ifmm_handle* h = new ifmm_handle();

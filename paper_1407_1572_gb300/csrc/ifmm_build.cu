@@ -157,11 +157,14 @@ IFMM_DEVINL double lagrange1(int p, const double* t, int m, double x) {
 }
 
 // per leaf: V (n x r0) -> Q (rows of W0 in tree order), Rt, rank. Scratch in global memory:
-// Ascr (n x r0) and Vscr (reflectors) at the leaf's tree rows.
+// Ascr (n x r0) and Vscr (reflectors) at the leaf's tree rows. With the SVD compression (U, the
+// leaf level's kept singular vectors, p^2 x rk in a p^2 x p^2 array, rk = *rsvd) the
+// orthonormalised matrix is V U and Rt is mapped back to node values: Rt <- Rt U^T.
 __global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const double* px, const double* py,
                                                          const int64_t* leaf_start, const int* leaf_count,
                                                          const double* cheb, double* W0, double* Rt, int* rank0,
-                                                         double* Ascr, double* Vscr) {
+                                                         double* Ascr, double* Vscr, const double* U,
+                                                         const int* rsvd) {
     __shared__ double red[32];
     __shared__ int ired[32];
     __shared__ double beta[64];
@@ -175,41 +178,66 @@ __global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const doub
     const double h = a.L / side;
     const double lx = a.x0 + bx * h, ly = a.y0 + by * h;
     double* A = Ascr + s0 * r0;
+    double* Q = W0 + s0 * r0;
+    const int rk = U ? *rsvd : r0;
+    double* S = U ? Q : A;   // the interpolation matrix; with U it is projected into A below
     for (int t = threadIdx.x; t < n * r0; t += blockDim.x) {
         int i = t / r0, m = t - i * r0;
         int mx = m % p, my = m / p;
         double ux = 2.0 * (px[s0 + i] - lx) / h - 1.0, uy = 2.0 * (py[s0 + i] - ly) / h - 1.0;
-        A[(size_t)i * r0 + m] = lagrange1(p, cheb, mx, ux) * lagrange1(p, cheb, my, uy);
+        S[(size_t)i * r0 + m] = lagrange1(p, cheb, mx, ux) * lagrange1(p, cheb, my, uy);
+    }
+    if (U) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * r0; t += blockDim.x) {
+            int i = t / r0, j = t - i * r0;
+            double v = 0.0;
+            if (j < rk)
+                for (int m = 0; m < r0; ++m) v += S[(size_t)i * r0 + m] * U[(size_t)m * r0 + j];
+            A[t] = v;
+        }
+        __syncthreads();
     }
     double* R = Rt + (int64_t)b * r0 * r0;
     for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) R[t] = 0.0;
-    double* Q = W0 + s0 * r0;
     for (int t = threadIdx.x; t < n * r0; t += blockDim.x) Q[t] = 0.0;
     __syncthreads();
     int rank = 0;
-    if (n > 0) rank = cta_cpqr(A, n, r0, r0, 1e-13, Q, r0, R, r0, Vscr + s0 * r0, beta, cperm, red, ired);
+    if (n > 0) rank = cta_cpqr(A, n, rk, r0, 1e-13, Q, r0, R, r0, Vscr + s0 * r0, beta, cperm, red, ired);
+    if (U && rank > 0) {
+        // Rt U^T (rank x r0) through A, which the factorisation no longer needs (rank <= n)
+        for (int t = threadIdx.x; t < rank * r0; t += blockDim.x) {
+            int i = t / r0, m = t - i * r0;
+            double v = 0.0;
+            for (int j = 0; j < rk; ++j) v += R[(size_t)i * r0 + j] * U[(size_t)m * r0 + j];
+            A[t] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < rank * r0; t += blockDim.x) R[t] = A[t];
+    }
     if (threadIdx.x == 0) rank0[b] = rank;
 }
 
 void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
                        const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
-                       int max_n, cudaStream_t st) {
+                       int max_n, const double* U, const int* rsvd, cudaStream_t st) {
     (void)max_n;
     // scratch lives in the second half of W0's allocation (the caller allocates 3 N r0 doubles)
     double* Ascr = W0 + a.N * a.r0;
     double* Vscr = W0 + 2 * a.N * a.r0;
     k_leaf_basis<<<1 << (2 * a.depth), kThreads, 0, st>>>(a, px, py, leaf_start, leaf_count, cheb, W0, Rt, rank0,
-                                                          Ascr, Vscr); count_launches(1);
+                                                          Ascr, Vscr, U, rsvd); count_launches(1);
 }
 
 // per parent P at level k: Z stacks the rows (Rt_c T_c)[t, :], t < rank_c, of the four children
 // (Morton order) -> Z = Q Rt_P; Q is scattered into W0_P with rows c*r0 + t (zero rows for the
 // components a child does not have). Scratch: Z, reflectors and the compact Q, each 4 r0 x r0 per box,
-// in the tail of the level's W0 allocation.
+// in the tail of the level's W0 allocation. With the SVD compression (U, rsvd of this level, as in
+// k_leaf_basis) Z is orthonormalised in U's coordinates, Z U, and Rt mapped back, Rt U^T.
 __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, const double* Rt_child,
                                                            const int* rank_child, const double* Tc, double* W0,
                                                            double* Rt, int* rank0, double* Zscr, double* Vscr,
-                                                           double* Qscr) {
+                                                           double* Qscr, const double* U, const int* rsvd) {
     __shared__ double red[32];
     __shared__ int ired[32];
     __shared__ double beta[64];
@@ -225,7 +253,10 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
         off[c + 1] = off[c] + rank_child[cg[c]];
     }
     const int m = off[4];
+    const int rk = U ? *rsvd : r0;
     double* Z = Zscr + (int64_t)b * 4 * r0 * r0;
+    double* Q = Qscr + (int64_t)b * 4 * r0 * r0;
+    double* Z0 = U ? Q : Z;   // the stacked rows; with U projected into Z below
     for (int t = threadIdx.x; t < m * r0; t += blockDim.x) {
         int row = t / r0, col = t - row * r0;
         int c = 0;
@@ -235,16 +266,35 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
         const double* T = Tc + (int64_t)c * r0 * r0;
         double v = 0.0;
         for (int l = 0; l < r0; ++l) v += Rc[(size_t)i * r0 + l] * T[(size_t)l * r0 + col];
-        Z[t] = v;
+        Z0[t] = v;
+    }
+    if (U) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * r0; t += blockDim.x) {
+            int row = t / r0, j = t - row * r0;
+            double v = 0.0;
+            if (j < rk)
+                for (int l = 0; l < r0; ++l) v += Z0[(size_t)row * r0 + l] * U[(size_t)l * r0 + j];
+            Z[t] = v;
+        }
     }
     double* R = Rt + (int64_t)b * r0 * r0;
     for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) R[t] = 0.0;
     double* W = W0 + (int64_t)b * 4 * r0 * r0;
     for (int t = threadIdx.x; t < 4 * r0 * r0; t += blockDim.x) W[t] = 0.0;
-    double* Q = Qscr + (int64_t)b * 4 * r0 * r0;
     __syncthreads();
     int rank = 0;
-    if (m > 0) rank = cta_cpqr(Z, m, r0, r0, 1e-13, Q, r0, R, r0, Vscr + (int64_t)b * 4 * r0 * r0, beta, cperm, red, ired);
+    if (m > 0) rank = cta_cpqr(Z, m, rk, r0, 1e-13, Q, r0, R, r0, Vscr + (int64_t)b * 4 * r0 * r0, beta, cperm, red, ired);
+    if (U && rank > 0) {
+        for (int t = threadIdx.x; t < rank * r0; t += blockDim.x) {   // Rt U^T through Z (rank <= m)
+            int i = t / r0, l = t - i * r0;
+            double v = 0.0;
+            for (int j = 0; j < rk; ++j) v += R[(size_t)i * r0 + j] * U[(size_t)l * r0 + j];
+            Z[t] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < rank * r0; t += blockDim.x) R[t] = Z[t];
+    }
     for (int t = threadIdx.x; t < m * rank; t += blockDim.x) {
         int row = t / rank, j = t - row * rank;
         int c = 0;
@@ -255,14 +305,156 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
 }
 
 void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
-                         const double* Tc, double* W0, double* Rt, int* rank0, cudaStream_t st) {
+                         const double* Tc, double* W0, double* Rt, int* rank0, const double* U, const int* rsvd,
+                         cudaStream_t st) {
     int64_t nb = 1ll << (2 * k);
     double* Zscr = W0 + nb * 4 * a.r0 * a.r0;
     double* Vscr = W0 + 2 * nb * 4 * a.r0 * a.r0;
     double* Qscr = W0 + 3 * nb * 4 * a.r0 * a.r0;
     k_parent_basis<<<(unsigned)nb, kThreads, 0, st>>>(a, k, Rt_child, rank_child, Tc, W0, Rt, rank0, Zscr, Vscr,
-                                                      Qscr); count_launches(1);
+                                                      Qscr, U, rsvd); count_launches(1);
 }
+
+// The SVD compression of the Chebyshev interpolation (Section 5, "Chebyshev interpolation followed by
+// SVD"), one level per launch, one CTA, top level first. G (m x r0, global scratch) stacks
+// K_d^T for the 40 interaction offsets d of a box (K_d[i, l] = K(node_i, node_l + h d), h the box side
+// of level k) and, below the top level, the parent's kept directions seen from each child position,
+// (T_c U_{k-1} Sigma_{k-1})^T, so that the kept bases stay nested. G = Q R by Householder QR
+// (cta_cpqr, no cut), then a one-sided Jacobi SVD of R in shared memory: in each round the r0
+// columns form r0/2 disjoint pairs (a round-robin tournament), one warp per pair rotates its two
+// columns (and those of V) orthogonal; sweeps repeat until no pair has |r_i . r_j| > 1e-15 |r_i| |r_j|
+// (at most 60). sigma_j = |r_j|; U = V with columns sorted by sigma descending (ties by index),
+// each column's entry of largest magnitude made positive; *rk = #{sigma_j > svd_eps sigma_1}, >= 1.
+// U: r0 x r0 row-major; sig: r0. Up, sp, rp: the parent level's U, sigma and kept count (null at
+// the top level). Shared memory: R and V, 2 r0^2 doubles.
+__global__ void __launch_bounds__(kThreads) k_svd_level(BuildArgs a, int k, double svd_eps, const double* cheb,
+                                                        const double* Tc, const double* Up, const double* sp,
+                                                        const int* rp_dev, double* U, double* sig, int* rk,
+                                                        double* G, double* Qs, double* Vs) {
+    extern __shared__ double ssm[];
+    __shared__ double red[32];
+    __shared__ int ired[32];
+    __shared__ double beta[64];
+    __shared__ int cperm[64];
+    __shared__ int offs[40];
+    __shared__ double snorm[64];
+    __shared__ int s_rot;
+    const int r0 = a.r0, p = a.p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double h = a.L / (double)(1 << k);
+    const int rp = Up ? *rp_dev : 0;
+    const int m = 40 * r0 + 4 * rp;
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx)
+                if (max(abs(dx), abs(dy)) >= 2) offs[o++] = (dx + 3) + 7 * (dy + 3);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 40 * r0 * r0; t += blockDim.x) {
+        const int o = t / (r0 * r0), l = (t / r0) % r0, i = t % r0;
+        const int dx = offs[o] % 7 - 3, dy = offs[o] / 7 - 3;
+        const double ax = 0.5 * (cheb[i % p] + 1.0) * h, ay = 0.5 * (cheb[i / p] + 1.0) * h;
+        const double cx = (0.5 * (cheb[l % p] + 1.0) + dx) * h, cy = (0.5 * (cheb[l / p] + 1.0) + dy) * h;
+        G[t] = kernel_eval(a.kernel, a.kparam0, ax, ay, cx, cy);
+    }
+    for (int t = threadIdx.x; t < 4 * rp * r0; t += blockDim.x) {
+        const int c = t / (rp * r0), j = (t / r0) % rp, i = t % r0;
+        const double* T = Tc + (size_t)c * r0 * r0;
+        double v = 0.0;
+        for (int l = 0; l < r0; ++l) v += T[(size_t)i * r0 + l] * Up[(size_t)l * r0 + j];
+        G[(size_t)40 * r0 * r0 + t] = v * sp[j];
+    }
+    double* R = ssm;             // r0 x r0
+    double* V = ssm + r0 * r0;   // r0 x r0
+    for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) {
+        R[t] = 0.0;
+        V[t] = (t / r0 == t % r0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int rank = cta_cpqr(G, m, r0, r0, 0.0, Qs, r0, R, r0, Vs, beta, cperm, red, ired);
+    const int ne = r0 + (r0 & 1);   // players of the tournament; player r0 (odd r0) sits out
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        if (threadIdx.x == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < ne - 1; ++round) {
+            for (int slot = warp; slot < ne / 2; slot += nw) {
+                const int pa = slot, pb = ne - 1 - slot;   // positions; position 0 holds player 0
+                const int i = pa == 0 ? 0 : (pa - 1 + round) % (ne - 1) + 1;
+                const int j = (pb - 1 + round) % (ne - 1) + 1;
+                if (i >= r0 || j >= r0) continue;
+                double aa = 0.0, bb = 0.0, cc = 0.0;
+                for (int q = lane; q < rank; q += 32) {
+                    const double ri = R[q * r0 + i], rj = R[q * r0 + j];
+                    aa += ri * ri; bb += rj * rj; cc += ri * rj;
+                }
+                aa = warp_sum(aa); bb = warp_sum(bb); cc = warp_sum(cc);
+                if (cc == 0.0 || fabs(cc) <= 1e-15 * sqrt(aa * bb)) continue;
+                const double zeta = (bb - aa) / (2.0 * cc);
+                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+                for (int q = lane; q < r0; q += 32) {
+                    const double ri = R[q * r0 + i], rj = R[q * r0 + j];
+                    R[q * r0 + i] = cs * ri - sn * rj;
+                    R[q * r0 + j] = sn * ri + cs * rj;
+                    const double vi = V[q * r0 + i], vj = V[q * r0 + j];
+                    V[q * r0 + i] = cs * vi - sn * vj;
+                    V[q * r0 + j] = sn * vi + cs * vj;
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            __syncthreads();
+        }
+        const int rot = s_rot;
+        __syncthreads();
+        if (!rot) break;
+    }
+    for (int j = warp; j < r0; j += nw) {
+        double ss = 0.0;
+        for (int q = lane; q < r0; q += 32) ss += R[q * r0 + j] * R[q * r0 + j];
+        ss = warp_sum(ss);
+        if (lane == 0) snorm[j] = sqrt(ss);
+    }
+    __syncthreads();
+    for (int j = warp; j < r0; j += nw) {
+        int pos = 0;
+        for (int i = 0; i < r0; ++i) pos += (snorm[i] > snorm[j] || (snorm[i] == snorm[j] && i < j)) ? 1 : 0;
+        double best = -1.0;
+        int bi = 0;
+        for (int q = 0; q < r0; ++q)
+            if (fabs(V[q * r0 + j]) > best) { best = fabs(V[q * r0 + j]); bi = q; }
+        const double sg = V[bi * r0 + j] < 0.0 ? -1.0 : 1.0;
+        for (int q = lane; q < r0; q += 32) U[(size_t)q * r0 + pos] = sg * V[q * r0 + j];
+        if (lane == 0) sig[pos] = snorm[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double smax = 0.0;
+        for (int j = 0; j < r0; ++j) smax = fmax(smax, snorm[j]);
+        int cnt = 0;
+        for (int j = 0; j < r0; ++j) cnt += snorm[j] > svd_eps * smax ? 1 : 0;
+        *rk = cnt > 0 ? cnt : 1;
+    }
+}
+
+void launch_svd_level(const BuildArgs& a, int k, double svd_eps, const double* cheb, const double* Tc,
+                      const double* Up, const double* sp, const int* rp, double* U, double* sig, int* rk,
+                      double* scratch, cudaStream_t st) {
+    const size_t mmax = (size_t)44 * a.r0;
+    double* G = scratch;
+    double* Qs = G + mmax * a.r0;
+    double* Vs = Qs + mmax * a.r0;
+    const size_t smem = 2 * (size_t)a.r0 * a.r0 * sizeof(double);
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        cudaFuncSetAttribute(k_svd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr.store(true);
+    }
+    k_svd_level<<<1, kThreads, smem, st>>>(a, k, svd_eps, cheb, Tc, Up, sp, rp, U, sig, rk, G, Qs, Vs);
+    count_launches(1);
+}
+
+size_t svd_scratch_doubles(int r0) { return (size_t)3 * 44 * r0 * r0; }
 
 // M2L_bq = Rt_b K(nodes_b, nodes_q) Rt_q^T for q in the interaction list of b
 __global__ void __launch_bounds__(kThreads) k_m2l_build(BuildArgs a, int k, const double* cheb, const double* Rt,

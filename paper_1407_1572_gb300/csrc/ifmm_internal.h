@@ -187,9 +187,14 @@ void launch_scatter_sorted(const unsigned long long* keys, const double* pts, in
                            double* px, double* py, int* leaf_count, int depth, cudaStream_t st);
 void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
                        const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
-                       int max_n, cudaStream_t st);
+                       int max_n, const double* U, const int* rsvd, cudaStream_t st);
+void launch_svd_level(const BuildArgs& a, int k, double svd_eps, const double* cheb, const double* Tc,
+                      const double* Up, const double* sp, const int* rp, double* U, double* sig, int* rk,
+                      double* scratch, cudaStream_t st);
+size_t svd_scratch_doubles(int r0);
 void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
-                         const double* Tc, double* W0, double* Rt, int* rank0, cudaStream_t st);
+                         const double* Tc, double* W0, double* Rt, int* rank0, const double* U, const int* rsvd,
+                         cudaStream_t st);
 void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const double* Rt, double* far0,
                       cudaStream_t st);
 void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,

@@ -32,7 +32,7 @@ class ifmm_params(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
                 ("refine_restart", ctypes.c_int),
                 ("refine_inner", ctypes.c_double),
-                ("leaf_max", ctypes.c_int), ("tc_products", ctypes.c_int)]
+                ("leaf_max", ctypes.c_int), ("tc_products", ctypes.c_int), ("svd_eps", ctypes.c_double)]
 
 
 class ifmm_stats(ctypes.Structure):
@@ -45,7 +45,8 @@ class ifmm_stats(ctypes.Structure):
                 ("kernel_flops", ctypes.c_double * 5), ("level_ms", ctypes.c_double * 16),
                 ("last_update", ctypes.c_double), ("last_residual", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
-                ("launches_solve", ctypes.c_int64), ("compress_proj_flops", ctypes.c_double)]
+                ("launches_solve", ctypes.c_int64), ("compress_proj_flops", ctypes.c_double),
+                ("svd_ranks", ctypes.c_int * 16)]
 
 
 FACTOR_KERNELS = ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")
@@ -226,7 +227,7 @@ def ifmm_get_stats(h) -> dict:
     out = {}
     for name, _ in ifmm_stats._fields_:
         v = getattr(s, name)
-        out[name] = list(v) if name in ("kernel_ms", "kernel_launches", "kernel_flops", "level_ms") else v
+        out[name] = list(v) if name in ("kernel_ms", "kernel_launches", "kernel_flops", "level_ms", "svd_ranks") else v
     return out
 
 
