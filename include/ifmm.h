@@ -73,10 +73,13 @@ typedef enum {
 } ifmm_precision;
 
 typedef struct {
-    int dim;              /* space dimension; must be 2 (quadtree)                               */
+    int dim;              /* space dimension: 2 (quadtree) or 3 (octree: Section 4.2 extends the
+                             method to any dimension; 27 neighbours and up to 189 interaction-list
+                             boxes per box, 27 colours). 3 requires cheb_p <= 4, an explicit
+                             depth <= 6 and tc_products = 0                                        */
     int depth;            /* leaf level kappa of the uniform tree, 2 <= depth <= 10; 0 = automatic
-                             (see leaf_max)                                                       */
-    int cheb_p;           /* Chebyshev nodes per dimension (Section 5), 1..8; initial box rank p^2 */
+                             (see leaf_max; 2D only)                                              */
+    int cheb_p;           /* Chebyshev nodes per dimension (Section 5), 1..8; initial box rank p^dim */
     int r_cap;            /* largest rank any box basis may reach (if > 0, at least cheb_p^2);
                              <= 0: only the box size n_i                                          */
     double eps;           /* compression tolerance of the fill-in (Section 5), >= 0              */
@@ -84,7 +87,9 @@ typedef struct {
     double kparam[4];     /* kernel parameters: kparam[0] > 0 for every kernel but IFMM_K_INV_R
                              (the length scale l of IFMM_K_EXP / IFMM_K_DEXP_DELL, the a of the
                              benchmark kernels)                                                   */
-    double box[3];        /* root box x0, y0, side; side <= 0 selects the unit square [0,1]^2    */
+    double box[3];        /* root box x0, y0, side; side <= 0 selects the unit square (cube) with
+                             its corner at the origin. 3D: the cube [x0, x0 + side] x [y0, y0 + side]
+                             x [z0, z0 + side]                                                    */
     int precision;        /* ifmm_precision                                                       */
     int tau_ref;          /* compression threshold reference: 0 = the fill's own largest column
                              norm; 1 = the matrix scale s_A (largest column norm of the leaf
@@ -116,6 +121,7 @@ typedef struct {
                              bases stay nested), keeping sigma_j > svd_eps * sigma_1; the kept
                              counts are ifmm_stats.svd_ranks. Meant for kernels of x - y alone
                              (all of ifmm_kernel). 0 (default): no truncation. Range [0, 1)   */
+    double z0;            /* dim 3: lower z of the root cube (0 by default)                      */
 } ifmm_params;
 
 typedef struct {
@@ -147,7 +153,7 @@ typedef struct {
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
  * FP64, tau_ref 1, no refinement (refine_maxit 100, refine_restart 60, refine_inner 1e-4),
- * leaf_max 64, tc_products 0, svd_eps 0. */
+ * leaf_max 64, tc_products 0, svd_eps 0, z0 0. */
 void ifmm_default_params(ifmm_params* p);
 
 /* Smallest depth 2..10 of the uniform quadtree (Section 4.2: boxes of level k form a 2^k x 2^k
@@ -157,7 +163,7 @@ void ifmm_default_params(ifmm_params* p);
 int ifmm_auto_depth(const double* pts_host, int64_t N, const double* box, int leaf_max);
 
 /* Build the tree, the Chebyshev operators and their orthonormal nested bases (assembly time t_a).
- * pts_host: N x 2 row-major FP64 host array (x0, y0, x1, y1, ...), copied; N >= 1.
+ * pts_host: N x dim row-major FP64 host array (x0, y0[, z0], x1, y1[, z1], ...), copied; N >= 1.
  * kernel:   ifmm_kernel. p: parameters (copied). stream: cudaStream_t or NULL.
  * out:      receives the handle (NULL on failure).
  * Tree and lists: Section 4.2, Table "table_cluster"; operators: Table "table_FMM_operators";
@@ -244,8 +250,8 @@ ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double* y_dev, in
 ifmm_status ifmm_tc_dgemm(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
                           int M, int N, int K, void* stream);
 
-/* Final ranks of the boxes of one level 2..depth, grid order (ix + 2^level * iy), into the host
- * array out_host (4^level ints). Errors: STATE (not factored), INVALID_ARG. */
+/* Final ranks of the boxes of one level 2..depth, grid order (ix + s (iy + s iz), s = 2^level), into
+ * the host array out_host (2^(dim level) ints). Errors: STATE (not factored), INVALID_ARG. */
 ifmm_status ifmm_get_ranks(ifmm_h h, int level, int* out_host);
 
 /* Counters and timings of the handle into *s. Errors: INVALID_ARG (NULL argument). */

@@ -25,13 +25,13 @@ using namespace ifmm;
 namespace {
 
 struct FLevel {
-    int k = 0, side = 0, nb = 0, RC = 0, smax = 0;
+    int k = 0, side = 0, nb = 0, RC = 0, smax = 0, dim = 2;
     double scale = 0.0;   // threshold reference of the level (tau_ref = 1)
     std::vector<int> n, r, r0;
     std::vector<int64_t> voff, yoff;
-    std::vector<int> xoff5;
+    std::vector<int> xoffs;   // non-leaf: 2^d + 1 offsets per box of the children's rows in x_b
     std::vector<int> boxes;
-    int cstart[10] = {0};
+    int cstart[28] = {0};     // colour c's boxes: boxes[cstart[c] .. cstart[c + 1])
     int64_t vtot = 0;
     // device
     int* d_n = nullptr;
@@ -63,7 +63,7 @@ struct FLevel {
     double* d_pws = nullptr;
     int64_t* d_psoff = nullptr;
     int* d_boxes = nullptr;
-    int* d_xoff5 = nullptr;
+    int* d_xoffs = nullptr;
     // double-float copies of the stored factors (precision IFMM_MIXED_SOLVE) and element counts
     int64_t npi = 0, ncp = 0, nbp = 0;
     dfl* d_Pi2 = nullptr;
@@ -88,16 +88,15 @@ struct OpsLevel {
     dfl* d_far0_2 = nullptr;
 };
 
-uint64_t morton_host(uint32_t ix, uint32_t iy) {
+uint64_t morton_host(Cell c, int dim) {
     uint64_t m = 0;
-    for (int b = 0; b < 32; ++b) {
-        m |= (uint64_t)((ix >> b) & 1u) << (2 * b);
-        m |= (uint64_t)((iy >> b) & 1u) << (2 * b + 1);
+    for (int b = 0; b < 20; ++b) {
+        m |= (uint64_t)((c.x >> b) & 1) << (dim * b);
+        m |= (uint64_t)((c.y >> b) & 1) << (dim * b + 1);
+        if (dim == 3) m |= (uint64_t)((c.z >> b) & 1) << (dim * b + 2);
     }
     return m;
 }
-
-int region36_host(int px, int py, int qx, int qy) { return (qx - 2 * (px >> 1) + 2) + 6 * (qy - 2 * (py >> 1) + 2); }
 
 }  // namespace
 
@@ -107,7 +106,7 @@ struct ifmm_handle {
     int device = 0;
     bool in_batch = false;   // factored by ifmm_factor_batch: pivot launches sized without a readback
     int64_t N = 0;
-    int depth = 0, p = 0, r0 = 0;
+    int depth = 0, p = 0, r0 = 0, dim = 2;   // r0 = p^dim
     cudaStream_t st = nullptr;
     std::string err;
     std::vector<std::pair<void*, size_t>> allocs;
@@ -117,6 +116,7 @@ struct ifmm_handle {
     int64_t* d_perm = nullptr;
     double* d_px = nullptr;
     double* d_py = nullptr;
+    double* d_pz = nullptr;   // zeros in 2D
     std::vector<int> leaf_count;
     std::vector<int64_t> leaf_start;
     int* d_leaf_count = nullptr;
@@ -266,27 +266,30 @@ ifmm_status workspace(ifmm_handle* h, int slot, size_t bytes, void** out) {
 // ------------------------------------------------------------------------------------------------
 ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     const int64_t N = h->N;
-    const int kap = h->depth, side = 1 << kap, nleaf = side * side;
+    const int dim = h->dim, nd = ndirs(dim), nk = 1 << dim;
+    const int kap = h->depth, side = 1 << kap, nleaf = 1 << (dim * kap);
     const int p = h->p, r0 = h->r0;
     CKS(dalloc(h, &h->d_status, sizeof(int) * 4));
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
     CKS(dalloc(h, &h->d_counters, sizeof(double) * 8));
     CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
     double* d_pts = nullptr;
-    CKS(dalloc(h, &d_pts, sizeof(double) * 2 * N));
-    CK(cudaMemcpyAsync(d_pts, pts_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, h->st));
+    CKS(dalloc(h, &d_pts, sizeof(double) * dim * N));
+    CK(cudaMemcpyAsync(d_pts, pts_host, sizeof(double) * dim * N, cudaMemcpyHostToDevice, h->st));
     int64_t npad = 1;
     while (npad < N) npad <<= 1;
     unsigned long long* d_keys = nullptr;
     CKS(dalloc(h, &d_keys, sizeof(unsigned long long) * npad));
-    launch_leaf_keys(d_pts, N, kap, h->prm.box[0], h->prm.box[1], h->prm.box[2], d_keys, npad, h->d_status, h->st);
+    launch_leaf_keys(d_pts, N, kap, dim, h->prm.box[0], h->prm.box[1], h->prm.z0, h->prm.box[2], d_keys, npad,
+                     h->d_status, h->st);
     launch_bitonic_sort(d_keys, npad, h->st);
     CKS(dalloc(h, &h->d_perm, sizeof(int64_t) * N));
     CKS(dalloc(h, &h->d_px, sizeof(double) * N));
     CKS(dalloc(h, &h->d_py, sizeof(double) * N));
+    CKS(dalloc(h, &h->d_pz, sizeof(double) * N));
     CKS(dalloc(h, &h->d_leaf_count, sizeof(int) * nleaf));
     CK(cudaMemsetAsync(h->d_leaf_count, 0, sizeof(int) * nleaf, h->st));
-    launch_scatter_sorted(d_keys, d_pts, N, h->d_perm, h->d_px, h->d_py, h->d_leaf_count, kap, h->st);
+    launch_scatter_sorted(d_keys, d_pts, N, dim, h->d_perm, h->d_px, h->d_py, h->d_pz, h->d_leaf_count, kap, h->st);
     int hstat = 0;
     h->leaf_count.assign(nleaf, 0);
     CK(cudaMemcpyAsync(h->leaf_count.data(), h->d_leaf_count, sizeof(int) * nleaf, cudaMemcpyDeviceToHost, h->st));
@@ -300,7 +303,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     }
     // leaf_start in Morton order (tree order of the sorted points)
     std::vector<std::pair<uint64_t, int>> mk(nleaf);
-    for (int g = 0; g < nleaf; ++g) mk[g] = {morton_host(g % side, g / side), g};
+    for (int g = 0; g < nleaf; ++g) mk[g] = {morton_host(cell_of(g, side, dim), dim), g};
     std::sort(mk.begin(), mk.end());
     h->leaf_start.assign(nleaf, 0);
     int64_t acc = 0;
@@ -311,8 +314,8 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         max_n = std::max(max_n, h->leaf_count[kv.second]);
     }
     CKS(upload(h, &h->d_leaf_start, h->leaf_start));
-    // Chebyshev nodes and child transfers T_c[m', m] = S^parent_m(child node m')
-    std::vector<double> cheb(p), Tc((size_t)4 * r0 * r0);
+    // Chebyshev nodes and child transfers T_c[m', m] = S^parent_m(child node m'), 2^d of them
+    std::vector<double> cheb(p), Tc((size_t)nk * r0 * r0);
     for (int m = 0; m < p; ++m) cheb[m] = std::cos((2.0 * m + 1.0) * M_PI / (2.0 * p));
     auto lag = [&](int m, double x) {
         double v = 1.0;
@@ -320,19 +323,20 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
             if (j != m) v *= (x - cheb[j]) / (cheb[m] - cheb[j]);
         return v;
     };
-    for (int c = 0; c < 4; ++c) {
-        int a = c & 1, b = c >> 1;
-        for (int my = 0; my < p; ++my)
-            for (int mx = 0; mx < p; ++mx) {
-                double ux = 0.5 * (cheb[mx] - 1.0) + a, uy = 0.5 * (cheb[my] - 1.0) + b;
-                for (int ny = 0; ny < p; ++ny)
-                    for (int nx = 0; nx < p; ++nx)
-                        Tc[((size_t)c * r0 + mx + p * my) * r0 + nx + p * ny] = lag(nx, ux) * lag(ny, uy);
+    for (int c = 0; c < nk; ++c)
+        for (int mc = 0; mc < r0; ++mc) {      // child node (mx, my, mz)
+            const int mxyz[3] = {mc % p, (mc / p) % p, mc / (p * p)};
+            for (int m = 0; m < r0; ++m) {     // parent basis function (nx, ny, nz)
+                const int nxyz[3] = {m % p, (m / p) % p, m / (p * p)};
+                double v = 1.0;
+                for (int i = 0; i < dim; ++i) v *= lag(nxyz[i], 0.5 * (cheb[mxyz[i]] - 1.0) + ((c >> i) & 1));
+                Tc[((size_t)c * r0 + mc) * r0 + m] = v;
             }
-    }
+        }
     CKS(upload(h, &h->d_cheb, cheb));
     CKS(upload(h, &h->d_Tc, Tc));
-    BuildArgs ba{N, kap, p, r0, h->kernel, h->prm.kparam[0], h->prm.diag, h->prm.box[0], h->prm.box[1], h->prm.box[2]};
+    BuildArgs ba{N, kap, p, r0, h->kernel, h->prm.kparam[0], h->prm.diag, h->prm.box[0], h->prm.box[1], h->prm.box[2],
+                 dim, h->prm.z0};
     h->ops.assign(kap + 1, OpsLevel());
     // SVD compression of the Chebyshev interpolation (svd_eps > 0): per level, top first, the kept
     // singular vectors U_k (r0 x r0 arrays, the first rsvd[k] columns used), freed after the build
@@ -345,7 +349,7 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &d_U, sizeof(double) * (size_t)(kap + 1) * r0 * r0));
         CKS(dalloc(h, &d_sig, sizeof(double) * (size_t)(kap + 1) * r0));
         CKS(dalloc(h, &d_rsvd, sizeof(int) * (size_t)(kap + 1)));
-        CKS(dalloc(h, &d_svd_scr, sizeof(double) * svd_scratch_doubles(r0)));
+        CKS(dalloc(h, &d_svd_scr, sizeof(double) * svd_scratch_doubles(r0, dim)));
         for (int k = 2; k <= kap; ++k) {
             const bool top = k == 2;
             launch_svd_level(ba, k, h->prm.svd_eps, h->d_cheb, h->d_Tc, top ? nullptr : d_U + (size_t)(k - 1) * r0 * r0,
@@ -365,27 +369,28 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
         CKS(dalloc(h, &O.d_W0, sizeof(double) * 3 * (size_t)N * r0));
         CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nleaf * r0 * r0));
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nleaf));
-        launch_leaf_basis(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_cheb, O.d_W0, O.d_Rt,
+        launch_leaf_basis(ba, h->d_px, h->d_py, h->d_pz, h->d_leaf_start, h->d_leaf_count, h->d_cheb, O.d_W0, O.d_Rt,
                           O.d_rank0, max_n, Uk(kap), rk(kap), h->st);
         O.nW0 = (int64_t)N * r0;
     }
     for (int k = kap - 1; k >= 2; --k) {
         OpsLevel& O = h->ops[k];
-        int nb = 1 << (2 * k);
-        CKS(dalloc(h, &O.d_W0, sizeof(double) * 4 * (size_t)nb * 4 * r0 * r0));
+        int nb = 1 << (dim * k);
+        CKS(dalloc(h, &O.d_W0, sizeof(double) * 4 * (size_t)nb * nk * r0 * r0));
         CKS(dalloc(h, &O.d_Rt, sizeof(double) * (size_t)nb * r0 * r0));
         CKS(dalloc(h, &O.d_rank0, sizeof(int) * nb));
         launch_parent_basis(ba, k, h->ops[k + 1].d_Rt, h->ops[k + 1].d_rank0, h->d_Tc, O.d_W0, O.d_Rt, O.d_rank0,
                             Uk(k), rk(k), h->st);
-        O.nW0 = (int64_t)nb * 4 * r0 * r0;
+        O.nW0 = (int64_t)nb * nk * r0 * r0;
     }
     for (int k = 2; k <= kap; ++k) {
         OpsLevel& O = h->ops[k];
-        int nb = 1 << (2 * k);
-        CKS(dalloc(h, &O.d_far0, sizeof(double) * (size_t)nb * 36 * r0 * r0));
-        CK(cudaMemsetAsync(O.d_far0, 0, sizeof(double) * (size_t)nb * 36 * r0 * r0, h->st));
+        int nb = 1 << (dim * k);
+        const int nreg = nregion(dim);
+        CKS(dalloc(h, &O.d_far0, sizeof(double) * (size_t)nb * nreg * r0 * r0));
+        CK(cudaMemsetAsync(O.d_far0, 0, sizeof(double) * (size_t)nb * nreg * r0 * r0, h->st));
         launch_m2l_build(ba, k, h->d_cheb, O.d_Rt, O.d_far0, h->st);
-        O.nfar0 = (int64_t)nb * 36 * r0 * r0;
+        O.nfar0 = (int64_t)nb * nreg * r0 * r0;
         O.rank0.assign(nb, 0);
         CK(cudaMemcpyAsync(O.rank0.data(), O.d_rank0, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->st));
     }
@@ -394,15 +399,15 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     dfree_ptr(h, d_rsvd);
     dfree_ptr(h, d_svd_scr);
     // leaf P2P
-    h->p2p_off.assign((size_t)nleaf * 9, 0);
+    h->p2p_off.assign((size_t)nleaf * nd, 0);
     int64_t po = 0;
     for (int g = 0; g < nleaf; ++g) {
-        int gx = g % side, gy = g / side;
-        for (int d = 0; d < 9; ++d) {
-            int qx = gx + d % 3 - 1, qy = gy + d / 3 - 1;
-            if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
-            h->p2p_off[(size_t)g * 9 + d] = po;
-            po += (int64_t)h->leaf_count[g] * h->leaf_count[qx + side * qy];
+        const Cell cg = cell_of(g, side, dim);
+        for (int d = 0; d < nd; ++d) {
+            const Cell cq = cell_dir(cg, d, dim);
+            if (!cell_in(cq, side)) continue;
+            h->p2p_off[(size_t)g * nd + d] = po;
+            po += (int64_t)h->leaf_count[g] * h->leaf_count[cell_index(cq, side)];
         }
     }
     CKS(upload(h, &h->d_p2p_off, h->p2p_off));
@@ -410,7 +415,8 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     double* d_sA = nullptr;
     CKS(dalloc(h, &d_sA, sizeof(double)));
     CK(cudaMemsetAsync(d_sA, 0, sizeof(double), h->st));
-    launch_p2p_build(ba, h->d_px, h->d_py, h->d_leaf_start, h->d_leaf_count, h->d_p2p_off, h->d_p2p, d_sA, h->st);
+    launch_p2p_build(ba, h->d_px, h->d_py, h->d_pz, h->d_leaf_start, h->d_leaf_count, h->d_p2p_off, h->d_p2p, d_sA,
+                     h->st);
     CK(cudaMemcpyAsync(&h->sA, d_sA, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     h->np2p = po;
     // double-float operator copies for the inner Krylov matvec of the mixed-precision solve
@@ -438,6 +444,7 @@ template <typename T>
 LevelView<T> view_of(ifmm_handle* h, FLevel& L) {
     LevelView<T> v{};
     v.k = L.k; v.side = L.side; v.nb = L.nb; v.RC = L.RC;
+    v.dim = L.dim; v.nd = ndirs(L.dim); v.ctr = ndirs(L.dim) / 2; v.nreg = nregion(L.dim);
     v.nmax = 0;
     for (int b = 0; b < (int)L.n.size(); ++b) v.nmax = std::max(v.nmax, L.n[b]);
     v.n = L.d_n; v.r = L.d_r; v.voff = L.d_voff;
@@ -481,9 +488,10 @@ LevelView<T> solve_view(ifmm_handle* h, FLevel& L) {
 
 template <typename T>
 ifmm_status setup_level(ifmm_handle* h, int k) {
-    const int kap = h->depth;
+    const int kap = h->depth, dim = h->dim, nd = ndirs(dim), ctr = nd / 2, nreg = nregion(dim), nk = 1 << dim;
+    const int ncol = ncolours(dim);
     FLevel& L = h->lv[k];
-    L.k = k; L.side = 1 << k; L.nb = L.side * L.side;
+    L.k = k; L.side = 1 << k; L.nb = 1 << (dim * k); L.dim = dim;
     const int s = L.side, nb = L.nb;
     const OpsLevel& O = h->ops[k];
     L.n.assign(nb, 0);
@@ -497,15 +505,16 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
         L.vtot = h->N;
     } else {
         FLevel& C = h->lv[k + 1];
-        L.xoff5.assign((size_t)nb * 5, 0);
+        L.xoffs.assign((size_t)nb * (nk + 1), 0);
         for (int b = 0; b < nb; ++b) {
-            int bx = b % s, by = b / s, off = 0;
-            for (int c = 0; c < 4; ++c) {
-                int cg = (2 * bx + (c & 1)) + C.side * (2 * by + (c >> 1));
-                L.xoff5[(size_t)b * 5 + c] = off;
+            const Cell cb = cell_of(b, s, dim);
+            int off = 0;
+            for (int c = 0; c < nk; ++c) {
+                const int cg = cell_index(child_cell(cb, c), C.side);
+                L.xoffs[(size_t)b * (nk + 1) + c] = off;
                 off += C.r[cg];
             }
-            L.xoff5[(size_t)b * 5 + 4] = off;
+            L.xoffs[(size_t)b * (nk + 1) + nk] = off;
             L.n[b] = off;
         }
         L.voff.assign(nb + 1, 0);
@@ -514,9 +523,10 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
         // children's y / z rows inside this level's vectors
         C.yoff.assign(C.nb, 0);
         for (int cg = 0; cg < C.nb; ++cg) {
-            int cx = cg % C.side, cy = cg / C.side;
-            int P = (cx >> 1) + s * (cy >> 1), c = (cx & 1) + 2 * (cy & 1);
-            C.yoff[cg] = L.voff[P] + L.xoff5[(size_t)P * 5 + c];
+            const Cell cc = cell_of(cg, C.side, dim);
+            const int P = cell_index(Cell{cc.x >> 1, cc.y >> 1, cc.z >> 1}, s);
+            const int c = (cc.x & 1) + 2 * (cc.y & 1) + 4 * (cc.z & 1);
+            C.yoff[cg] = L.voff[P] + L.xoffs[(size_t)P * (nk + 1) + c];
         }
         CKS(upload(h, &C.d_yoff, C.yoff));
     }
@@ -526,24 +536,24 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     std::vector<int> cap(nb);
     for (int b = 0; b < nb; ++b) cap[b] = std::min(L.n[b], L.RC);
     // blocks
-    std::vector<int64_t> boff((size_t)nb * 36, -1);
-    std::vector<int> bld((size_t)nb * 36, 0);
+    std::vector<int64_t> boff((size_t)nb * nreg, -1);
+    std::vector<int> bld((size_t)nb * nreg, 0);
     int64_t bo = 0;
     for (int b = 0; b < nb; ++b) {
-        int bx = b % s, by = b / s;
-        for (int j = 0; j < 36; ++j) {
-            int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
-            if (qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
-            int q = qx + s * qy;
-            bool nbr = std::max(std::abs(qx - bx), std::abs(qy - by)) <= 1;
+        const Cell cb = cell_of(b, s, dim);
+        for (int j = 0; j < nreg; ++j) {
+            const Cell cq = region_cell(cb, j, dim);
+            if (!cell_in(cq, s)) continue;
+            const int q = cell_index(cq, s);
+            const bool nbr = cheb_dist(cq, cb) <= 1;
             int rows = nbr ? L.n[b] : cap[b], cols = nbr ? L.n[q] : cap[q];
-            boff[(size_t)b * 36 + j] = bo;
-            bld[(size_t)b * 36 + j] = cols;
+            boff[(size_t)b * nreg + j] = bo;
+            bld[(size_t)b * nreg + j] = cols;
             bo += (int64_t)rows * cols;
         }
     }
     // pivot inverses, panels
-    std::vector<int64_t> pioff(nb), cpoff((size_t)nb * 9, 0), bpoff((size_t)nb * 9, 0), psoff(nb, 0);
+    std::vector<int64_t> pioff(nb), cpoff((size_t)nb * nd, 0), bpoff((size_t)nb * nd, 0), psoff(nb, 0);
     std::vector<int> pild(nb);
     int64_t pio = 0, cpo = 0, bpo = 0;
     L.smax = 0;
@@ -553,14 +563,14 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
         pioff[b] = pio;
         pild[b] = sm;
         pio += (int64_t)sm * sm;
-        int bx = b % s, by = b / s;
-        for (int d = 0; d < 9; ++d) {
-            int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
-            if (d == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
-            int q = qx + s * qy;
-            cpoff[(size_t)b * 9 + d] = cpo;
+        const Cell cb = cell_of(b, s, dim);
+        for (int d = 0; d < nd; ++d) {
+            const Cell cq = cell_dir(cb, d, dim);
+            if (d == ctr || !cell_in(cq, s)) continue;
+            const int q = cell_index(cq, s);
+            cpoff[(size_t)b * nd + d] = cpo;
             cpo += (int64_t)L.n[q] * L.n[b];
-            bpoff[(size_t)b * 9 + d] = bpo;
+            bpoff[(size_t)b * nd + d] = bpo;
             bpo += (int64_t)L.n[b] * L.n[q];
         }
     }
@@ -571,66 +581,68 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     keys.reserve(nb);
     for (int b = 0; b < nb; ++b) {
         if (L.n[b] == 0) continue;
-        int bx = b % s, by = b / s;
-        keys.push_back({((uint64_t)((bx % 3) + 3 * (by % 3)) << 60) | morton_host(bx, by), b});
+        const Cell cb = cell_of(b, s, dim);
+        keys.push_back({((uint64_t)cell_colour(cb) << 58) | morton_host(cb, dim), b});
     }
     std::sort(keys.begin(), keys.end());
     const int nact = (int)keys.size();
     L.boxes.resize(nact);
     for (int t = 0; t < nact; ++t) L.boxes[t] = keys[t].second;
-    for (int c = 0; c <= 9; ++c) L.cstart[c] = 0;
+    for (int c = 0; c <= ncol; ++c) L.cstart[c] = 0;
     {
         int t = 0;
-        for (int c = 0; c < 9; ++c) {
+        for (int c = 0; c < ncol; ++c) {
             L.cstart[c] = t;
-            while (t < nact && (int)(keys[t].first >> 60) == c) ++t;
+            while (t < nact && (int)(keys[t].first >> 58) == c) ++t;
         }
-        L.cstart[9] = nact;
+        L.cstart[ncol] = nact;
     }
     // per-colour scratch
-    std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * 81, 0), rsoff((size_t)nb * 9, 0), cwsoff((size_t)nb * 9, 0);
+    std::vector<int64_t> xsoff(nb, 0), fsoff((size_t)nb * nd * nd, 0), rsoff((size_t)nb * nd, 0),
+        cwsoff((size_t)nb * nd, 0);
     std::vector<int> xsld(nb, 0);
     int64_t xs_max = 0, fs_max = 0, rs_max = 0, ps_max = 0, cw_max = 0;
-    for (int c = 0; c < 9; ++c) {
+    for (int c = 0; c < ncol; ++c) {
         int64_t xo = 0, fo = 0, ro = 0, pso = 0, cwo = 0;
         for (int t = L.cstart[c]; t < L.cstart[c + 1]; ++t) {
-            int e = L.boxes[t], ex = e % s, ey = e / s;
+            const int e = L.boxes[t];
+            const Cell ce = cell_of(e, s, dim);
             int sm = L.n[e] + cap[e];
             int ld = cap[e];
-            for (int d = 0; d < 9; ++d) {
-                int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
-                if (d == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
-                ld += L.n[qx + s * qy];
+            for (int d = 0; d < nd; ++d) {
+                const Cell cq = cell_dir(ce, d, dim);
+                if (d == ctr || !cell_in(cq, s)) continue;
+                ld += L.n[cell_index(cq, s)];
             }
             xsoff[e] = xo;
             xsld[e] = ld;
             xo += (int64_t)sm * ld;
             psoff[e] = pso;
             pso += (int64_t)sm * sm;
-            for (int dp = 0; dp < 9; ++dp)
-                for (int dq = 0; dq < 9; ++dq) {
-                    int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1, qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
-                    if (dp == 4 || dq == 4 || px < 0 || py < 0 || px >= s || py >= s || qx < 0 || qy < 0 || qx >= s || qy >= s)
-                        continue;
-                    if (std::max(std::abs(px - qx), std::abs(py - qy)) != 2) continue;
-                    fsoff[(size_t)e * 81 + dp * 9 + dq] = fo;
-                    fo += (int64_t)L.n[px + s * py] * L.n[qx + s * qy];
+            for (int dp = 0; dp < nd; ++dp)
+                for (int dq = 0; dq < nd; ++dq) {
+                    const Cell cp = cell_dir(ce, dp, dim), cq = cell_dir(ce, dq, dim);
+                    if (dp == ctr || dq == ctr || !cell_in(cp, s) || !cell_in(cq, s)) continue;
+                    if (cheb_dist(cp, cq) != 2) continue;
+                    fsoff[((size_t)e * nd + dp) * nd + dq] = fo;
+                    fo += (int64_t)L.n[cell_index(cp, s)] * L.n[cell_index(cq, s)];
                 }
-            for (int dq = 0; dq < 9; ++dq) {
-                int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
-                if (dq == 4 || qx < 0 || qy < 0 || qx >= s || qy >= s) continue;
+            for (int dq = 0; dq < nd; ++dq) {
+                const Cell cq = cell_dir(ce, dq, dim);
+                if (dq == ctr || !cell_in(cq, s)) continue;
                 int64_t mb = 0;
-                for (int dp = 0; dp < 9; ++dp) {
-                    int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
-                    if (dp == 4 || px < 0 || py < 0 || px >= s || py >= s) continue;
-                    if (std::max(std::abs(px - qx), std::abs(py - qy)) == 2) mb += 2 * L.n[px + s * py];
+                for (int dp = 0; dp < nd; ++dp) {
+                    const Cell cp = cell_dir(ce, dp, dim);
+                    if (dp == ctr || !cell_in(cp, s)) continue;
+                    if (cheb_dist(cp, cq) == 2) mb += 2 * L.n[cell_index(cp, s)];
                 }
-                rsoff[(size_t)e * 9 + dq] = ro;
-                ro += (int64_t)L.n[qx + s * qy] * mb;
+                const int nq = L.n[cell_index(cq, s)];
+                rsoff[(size_t)e * nd + dq] = ro;
+                ro += (int64_t)nq * mb;
                 // the compression's work arrays: the basis vector (n_q), 8 x RC coefficients, m norms,
                 // the basis vector again in the column arithmetic's type (n_q)
-                cwsoff[(size_t)e * 9 + dq] = cwo;
-                cwo += 2 * (int64_t)L.n[qx + s * qy] + 8 * (int64_t)L.RC + mb;
+                cwsoff[(size_t)e * nd + dq] = cwo;
+                cwo += 2 * (int64_t)nq + 8 * (int64_t)L.RC + mb;
             }
         }
         xs_max = std::max(xs_max, xo);
@@ -675,14 +687,14 @@ ifmm_status setup_level(ifmm_handle* h, int k) {
     L.ps_max = ps_max;
     if ((size_t)L.smax * L.smax * 8 > 150 * 1024) CKS(dalloc(h, &L.d_pws, sizeof(double) * (size_t)ps_max));
     CKS(upload(h, &L.d_boxes, L.boxes));
-    if (k < kap) CKS(upload(h, &L.d_xoff5, L.xoff5));
+    if (k < kap) CKS(upload(h, &L.d_xoffs, L.xoffs));
     LevelView<T> v = view_of<T>(h, L);
     if (k == kap) {
         launch_init_level<T>(v, 1, h->d_p2p, h->d_p2p_off, O.d_W0, h->d_leaf_start, h->r0, nullptr, O.d_far0,
                              O.d_rank0, nullptr, nullptr, h->st);
     } else {
         LevelView<T> cv = view_of<T>(h, h->lv[k + 1]);
-        launch_init_level<T>(v, 0, nullptr, nullptr, O.d_W0, nullptr, h->r0, L.d_xoff5, O.d_far0, O.d_rank0,
+        launch_init_level<T>(v, 0, nullptr, nullptr, O.d_W0, nullptr, h->r0, L.d_xoffs, O.d_far0, O.d_rank0,
                              h->ops[k + 1].d_rank0, &cv, h->st);
     }
     // threshold reference of the level: largest column norm of its diagonal blocks
@@ -714,7 +726,7 @@ void release_level(ifmm_handle* h, FLevel& L) {
                      (void**)&L.d_bld, &L.d_blk, &L.d_W, (void**)&L.d_pioff, (void**)&L.d_pild, &L.d_Pi,
                      (void**)&L.d_cpoff, &L.d_Cp, (void**)&L.d_bpoff, &L.d_Bp, (void**)&L.d_xsoff,
                      (void**)&L.d_xsld, &L.d_Xs, (void**)&L.d_fsoff, &L.d_Fs, &L.d_Fs2, (void**)&L.d_rsoff,
-                     &L.d_Rs, (void**)&L.d_cwsoff, (void**)&L.d_Cws, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoff5,
+                     &L.d_Rs, (void**)&L.d_cwsoff, (void**)&L.d_Cws, (void**)&L.d_pws, (void**)&L.d_psoff, (void**)&L.d_boxes, (void**)&L.d_xoffs,
                      (void**)&L.d_Pi2, (void**)&L.d_Cp2, (void**)&L.d_Bp2, (void**)&L.d_slab, (void**)&L.d_srexp,
                      (void**)&L.d_soff, (void**)&L.d_seoff};
     for (void** p : ptrs) {
@@ -908,7 +920,8 @@ ifmm_status factor_impl(ifmm_handle* h) {
     const int kap = h->depth;
     CKS(factor_begin<T>(h));
     const long long l0 = launches_so_far();
-    std::vector<cudaEvent_t> ev(9 * 6);
+    const int ncol = ncolours(h->dim);
+    std::vector<cudaEvent_t> ev(ncol * 6);
     for (auto& e : ev) CK(cudaEventCreate(&e));
     struct EvGuard {
         std::vector<cudaEvent_t>& v;
@@ -918,8 +931,8 @@ ifmm_status factor_impl(ifmm_handle* h) {
         CKS(factor_level_setup<T>(h, k));
         FLevel& L = h->lv[k];
         LevelView<T> v = view_of<T>(h, L);
-        bool used[9] = {false};
-        for (int c = 0; c < 9; ++c) {
+        bool used[27] = {false};
+        for (int c = 0; c < ncol; ++c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             if (cnt <= 0) continue;
             launch_factor_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.smax, h->in_batch ? 0 : 1, h->st,
@@ -928,7 +941,7 @@ ifmm_status factor_impl(ifmm_handle* h) {
         }
         CKS(factor_level_end<T>(h, k));
         double lms = 0.0;
-        for (int c = 0; c < 9; ++c) {
+        for (int c = 0; c < ncol; ++c) {
             if (!used[c]) continue;
             for (int t = 0; t < 5; ++t) {
                 float ms = 0.f;
@@ -1024,8 +1037,9 @@ ifmm_status factor_fused(ifmm_h* hs, int n, int workers, ifmm_status* st_out) {
         }
         if (views.empty()) continue;
         std::vector<int2> items;
-        int cstart[10];
-        for (int c = 0; c < 9; ++c) {
+        const int ncol = ncolours(hs[0]->dim);
+        int cstart[28];
+        for (int c = 0; c < ncol; ++c) {
             cstart[c] = (int)items.size();
             for (int i : ok) {
                 if (vi[i] < 0) continue;
@@ -1033,7 +1047,7 @@ ifmm_status factor_fused(ifmm_h* hs, int n, int workers, ifmm_status* st_out) {
                 for (int q = L.cstart[c]; q < L.cstart[c + 1]; ++q) items.push_back(make_int2(vi[i], L.boxes[q]));
             }
         }
-        cstart[9] = (int)items.size();
+        cstart[ncol] = (int)items.size();
         for (int i : ok)
             if (vi[i] >= 0) cudaStreamWaitEvent(B, evs[i], 0);
         LevelView<T>* d_views = nullptr;
@@ -1048,7 +1062,7 @@ ifmm_status factor_fused(ifmm_h* hs, int n, int workers, ifmm_status* st_out) {
             LevelView<T> Lr = views[vi[rep] >= 0 ? vi[rep] : 0];
             Lr.nmax = nmax;
             Lr.RC = rc;
-            for (int c = 0; c < 9; ++c) {
+            for (int c = 0; c < ncol; ++c) {
                 const int cnt = cstart[c + 1] - cstart[c];
                 if (cnt > 0)
                     launch_factor_colour<T>(Lr, nullptr, cnt, c, smax, 0, B, nullptr, d_items + cstart[c], d_views);
@@ -1120,7 +1134,7 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
     for (int k = kap; k >= 2; --k) {
         FLevel& L = h->lv[k];
         LevelView<T> v = solve_view<T>(h, L);
-        for (int c = 0; c < 9; ++c) {
+        for (int c = 0; c < ncolours(h->dim); ++c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             launch_forward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vr[k - 1], vxs, nrhs, h->st);
         }
@@ -1129,7 +1143,7 @@ ifmm_status solve_core(ifmm_handle* h, int nrhs, T* rhs_leaf, T* x_leaf) {
     for (int k = 2; k <= kap; ++k) {
         FLevel& L = h->lv[k];
         LevelView<T> v = solve_view<T>(h, L);
-        for (int c = 8; c >= 0; --c) {
+        for (int c = ncolours(h->dim) - 1; c >= 0; --c) {
             int cnt = L.cstart[c + 1] - L.cstart[c];
             launch_backward_colour<T>(v, L.d_boxes + L.cstart[c], cnt, c, L.d_yoff, vr[k], vx[k], vx[k - 1], vxs,
                                       nrhs, (T*)pp, part_cap, (int*)pc, cnt_cap, h->st);
@@ -1162,7 +1176,7 @@ ifmm_status matvec_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y,
     double* out = (double*)pout;
     std::vector<double*> ym(kap + 1, nullptr), zm(kap + 1, nullptr);
     for (int k = 2; k <= kap; ++k) {
-        size_t len = sizeof(double) * ((size_t)1 << (2 * k)) * r0 * nrhs;
+        size_t len = sizeof(double) * ((size_t)1 << (h->dim * k)) * r0 * nrhs;
         void* a = nullptr;
         void* b = nullptr;
         CKS(workspace(h, 120 + 2 * k, len, &a));
@@ -1171,11 +1185,11 @@ ifmm_status matvec_impl(ifmm_handle* h, const double* x, int64_t ldx, double* y,
         zm[k] = (double*)b;
     }
     launch_mv_permute_in(x, ldx, h->N, nrhs, h->d_perm, xt, h->st);
-    launch_mv_leaf_up(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
-    for (int k = kap - 1; k >= 2; --k) launch_mv_up(k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
-    for (int k = 2; k <= kap; ++k) launch_mv_m2l(k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
-    for (int k = 2; k < kap; ++k) launch_mv_down(k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
-    launch_mv_leaf_down(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
+    launch_mv_leaf_up(h->dim, kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up(h->dim, k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l(h->dim, k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down(h->dim, k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down(h->dim, kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
                         h->d_p2p, out, nrhs, h->st);
     launch_mv_permute_out(out, h->N, nrhs, h->d_perm, y, ldy, h->st);
     CK(cudaGetLastError());
@@ -1194,7 +1208,7 @@ ifmm_status matvec_dfl_impl(ifmm_handle* h, const double* x, int64_t ldx, double
     dfl* out = (dfl*)pout;
     std::vector<dfl*> ym(kap + 1, nullptr), zm(kap + 1, nullptr);
     for (int k = 2; k <= kap; ++k) {
-        size_t len = sizeof(dfl) * ((size_t)1 << (2 * k)) * r0 * nrhs;
+        size_t len = sizeof(dfl) * ((size_t)1 << (h->dim * k)) * r0 * nrhs;
         void* a = nullptr;
         void* b = nullptr;
         CKS(workspace(h, 150 + 2 * k, len, &a));
@@ -1203,11 +1217,11 @@ ifmm_status matvec_dfl_impl(ifmm_handle* h, const double* x, int64_t ldx, double
         zm[k] = (dfl*)b;
     }
     launch_mv_permute_in<dfl>(x, ldx, h->N, nrhs, h->d_perm, xt, h->st);
-    launch_mv_leaf_up<dfl>(kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
-    for (int k = kap - 1; k >= 2; --k) launch_mv_up<dfl>(k, h->ops[k].d_W0_2, r0, ym[k + 1], ym[k], nrhs, h->st);
-    for (int k = 2; k <= kap; ++k) launch_mv_m2l<dfl>(k, h->ops[k].d_far0_2, r0, ym[k], zm[k], nrhs, h->st);
-    for (int k = 2; k < kap; ++k) launch_mv_down<dfl>(k, h->ops[k].d_W0_2, r0, zm[k], zm[k + 1], nrhs, h->st);
-    launch_mv_leaf_down<dfl>(kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt,
+    launch_mv_leaf_up<dfl>(h->dim, kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up<dfl>(h->dim, k, h->ops[k].d_W0_2, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l<dfl>(h->dim, k, h->ops[k].d_far0_2, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down<dfl>(h->dim, k, h->ops[k].d_W0_2, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down<dfl>(h->dim, kap, h->ops[kap].d_W0_2, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt,
                              h->d_p2p_off, h->d_p2p2, out, nrhs, h->st);
     launch_mv_permute_out<dfl>(out, h->N, nrhs, h->d_perm, y, ldy, h->st);
     CK(cudaGetLastError());
@@ -1495,6 +1509,7 @@ void ifmm_default_params(ifmm_params* p) {
     p->leaf_max = 64;
     p->tc_products = 0;
     p->svd_eps = 0.0;
+    p->z0 = 0.0;
 }
 
 // Smallest depth 2..10 of the uniform tree whose fullest leaf holds at most leaf_max points, with the
@@ -1524,9 +1539,16 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
                        ifmm_h* out) {
     if (out) *out = nullptr;
     if (!pts_host || !p || !out || N <= 0 || N >= (1ll << 31)) return IFMM_ERR_INVALID_ARG;
-    if (p->dim != 2 || (p->depth != 0 && (p->depth < 2 || p->depth > 10)) || p->cheb_p < 1 || p->cheb_p > 8)
+    if ((p->dim != 2 && p->dim != 3) || (p->depth != 0 && (p->depth < 2 || p->depth > 10)) || p->cheb_p < 1 ||
+        p->cheb_p > 8)
         return IFMM_ERR_INVALID_ARG;
     if (p->depth == 0 && p->leaf_max <= 0) return IFMM_ERR_INVALID_ARG;
+    // octree: p^3 <= 64 Chebyshev nodes (the QR of the bases keeps 64 columns in shared memory),
+    // an explicit depth <= 6, the double-float or FP64 products (the tensor-core replay keeps the
+    // quadtree's 8 neighbour panels per box)
+    if (p->dim == 3 && (p->cheb_p > 4 || p->depth == 0 || p->depth > 6 || p->tc_products != 0))
+        return IFMM_ERR_INVALID_ARG;
+    if (!std::isfinite(p->z0)) return IFMM_ERR_INVALID_ARG;
     if (kernel < IFMM_K_INV_R || kernel > IFMM_K_R2LOG_REG) return IFMM_ERR_INVALID_ARG;
     if (kernel != IFMM_K_INV_R && !(p->kparam[0] > 0.0)) return IFMM_ERR_INVALID_ARG;
     if (!(p->eps >= 0.0) || !std::isfinite(p->diag)) return IFMM_ERR_INVALID_ARG;
@@ -1536,11 +1558,11 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     if (p->r_cap > 0 && p->r_cap < p->cheb_p * p->cheb_p) return IFMM_ERR_INVALID_ARG;
     if (p->tc_products < 0 || p->tc_products > 2) return IFMM_ERR_INVALID_ARG;
     if (!(p->svd_eps >= 0.0 && p->svd_eps < 1.0)) return IFMM_ERR_INVALID_ARG;
-    for (int64_t i = 0; i < 2 * N; ++i)
+    for (int64_t i = 0; i < (int64_t)p->dim * N; ++i)
         if (!std::isfinite(pts_host[i])) return IFMM_ERR_INVALID_ARG;
     ifmm_handle* h = new ifmm_handle();
     h->prm = *p;
-    if (!(h->prm.box[2] > 0.0)) { h->prm.box[0] = 0.0; h->prm.box[1] = 0.0; h->prm.box[2] = 1.0; }
+    if (!(h->prm.box[2] > 0.0)) { h->prm.box[0] = 0.0; h->prm.box[1] = 0.0; h->prm.box[2] = 1.0; h->prm.z0 = 0.0; }
     if (h->prm.refine_maxit <= 0) h->prm.refine_maxit = 100;
     if (h->prm.refine_restart < 0 || h->prm.refine_restart > 200) {
         delete h;
@@ -1553,7 +1575,8 @@ ifmm_status ifmm_build(const double* pts_host, int64_t N, int kernel, const ifmm
     cudaGetDevice(&h->device);
     h->pool = library_pool(h->device);
     h->p = p->cheb_p;
-    h->r0 = p->cheb_p * p->cheb_p;
+    h->dim = p->dim;
+    h->r0 = p->dim == 3 ? p->cheb_p * p->cheb_p * p->cheb_p : p->cheb_p * p->cheb_p;
     h->st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     ifmm_status s = do_build(h, pts_host);
@@ -1645,7 +1668,7 @@ ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* statu
     bool fused = true;
     for (int i = 1; i < n; ++i)
         fused = fused && hs[i]->device == hs[0]->device && hs[i]->prm.precision == hs[0]->prm.precision &&
-                hs[i]->prm.tc_products == hs[0]->prm.tc_products;
+                hs[i]->prm.tc_products == hs[0]->prm.tc_products && hs[i]->dim == hs[0]->dim;
     if (fused) {
         DeviceGuard dg(hs[0]->device);
         if (workers <= 0) workers = std::min(n, 16);
@@ -1796,7 +1819,7 @@ extern "C" ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double
     size_t need = 2 * vec;
     std::vector<size_t> lvl(kap + 1, 0);
     for (int k = 2; k <= kap; ++k) {
-        lvl[k] = align256(sizeof(double) * ((size_t)1 << (2 * k)) * r0 * nrhs);
+        lvl[k] = align256(sizeof(double) * ((size_t)1 << (h->dim * k)) * r0 * nrhs);
         need += 2 * lvl[k];
     }
     if (need > kNoAllocScratchBytes) {
@@ -1838,11 +1861,11 @@ extern "C" ifmm_status ifmm_matvec_noalloc(ifmm_h h, const double* x_dev, double
     }
     // every scratch vector is written before it is read (the M2L launch clears the locals first)
     launch_mv_permute_in(x_dev, ld, h->N, nrhs, h->d_perm, xt, h->st);
-    launch_mv_leaf_up(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
-    for (int k = kap - 1; k >= 2; --k) launch_mv_up(k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
-    for (int k = 2; k <= kap; ++k) launch_mv_m2l(k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
-    for (int k = 2; k < kap; ++k) launch_mv_down(k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
-    launch_mv_leaf_down(kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
+    launch_mv_leaf_up(h->dim, kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, xt, ym[kap], nrhs, h->st);
+    for (int k = kap - 1; k >= 2; --k) launch_mv_up(h->dim, k, h->ops[k].d_W0, r0, ym[k + 1], ym[k], nrhs, h->st);
+    for (int k = 2; k <= kap; ++k) launch_mv_m2l(h->dim, k, h->ops[k].d_far0, r0, ym[k], zm[k], nrhs, h->st);
+    for (int k = 2; k < kap; ++k) launch_mv_down(h->dim, k, h->ops[k].d_W0, r0, zm[k], zm[k + 1], nrhs, h->st);
+    launch_mv_leaf_down(h->dim, kap, h->ops[kap].d_W0, h->d_leaf_start, h->d_leaf_count, r0, zm[kap], xt, h->d_p2p_off,
                         h->d_p2p, out, nrhs, h->st);
     launch_mv_permute_out(out, h->N, nrhs, h->d_perm, y_dev, ld, h->st);
     CK(cudaGetLastError());

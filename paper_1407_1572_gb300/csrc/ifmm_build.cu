@@ -1,9 +1,9 @@
 // ifmm_build.cu -- tree, Chebyshev operators and the FP64 FMM matvec, sm_103a.
 //
 // Build (assembly time t_a of Table "table_notations"):
-//   points -> leaf keys (Morton code of the leaf, Section 4.2: uniform 2^d tree, Morton order)
-//   -> bitonic sort -> tree order, leaf counts;
-//   leaf bases V_b[a, m] = S_m(x_a), the tensor Lagrange basis at p x p first-kind Chebyshev
+//   points -> leaf keys (Morton code of the leaf, Section 4.2: uniform 2^d tree, d = 2 or 3,
+//   Morton order) -> bitonic sort -> tree order, leaf counts;
+//   leaf bases V_b[a, m] = S_m(x_a), the tensor Lagrange basis at p^d first-kind Chebyshev
 //   nodes of the leaf (Section 5), orthonormalised by column-pivoted Householder QR, V = Q Rt;
 //   parent bases: the stacked children transfers Rt_c T_c (T_c[m', m] = parent basis m at child
 //   node m'), orthonormalised the same way;
@@ -18,30 +18,30 @@
 
 namespace ifmm {
 
-IFMM_DEVINL bool in_grid2(int x, int y, int side) { return x >= 0 && y >= 0 && x < side && y < side; }
-
-IFMM_DEVINL unsigned long long spread_bits(unsigned v) {
-    unsigned long long x = v;
-    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
-    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
-    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
-    x = (x | (x << 2)) & 0x3333333333333333ull;
-    x = (x | (x << 1)) & 0x5555555555555555ull;
-    return x;
+// Morton code of a cell: the bits of x, y (and z) interleaved, d bits per level
+IFMM_DEVINL unsigned long long morton_code(Cell c, int dim) {
+    unsigned long long m = 0;
+    for (int bit = 0; bit < 10; ++bit) {
+        m |= (unsigned long long)((c.x >> bit) & 1) << (dim * bit);
+        m |= (unsigned long long)((c.y >> bit) & 1) << (dim * bit + 1);
+        if (dim == 3) m |= (unsigned long long)((c.z >> bit) & 1) << (dim * bit + 2);
+    }
+    return m;
 }
-IFMM_DEVINL unsigned compact_bits(unsigned long long x) {
-    x &= 0x5555555555555555ull;
-    x = (x | (x >> 1)) & 0x3333333333333333ull;
-    x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
-    x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
-    x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
-    x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
-    return (unsigned)x;
+IFMM_DEVINL Cell morton_cell(unsigned long long m, int dim) {
+    Cell c{0, 0, 0};
+    for (int bit = 0; bit < 10; ++bit) {
+        c.x |= (int)((m >> (dim * bit)) & 1) << bit;
+        c.y |= (int)((m >> (dim * bit + 1)) & 1) << bit;
+        if (dim == 3) c.z |= (int)((m >> (dim * bit + 2)) & 1) << bit;
+    }
+    return c;
 }
 
-IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay, double bx, double by) {
-    double dx = ax - bx, dy = ay - by;
-    double r = sqrt(dx * dx + dy * dy);
+IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay, double az, double bx, double by,
+                               double bz) {
+    const double dx = ax - bx, dy = ay - by, dz = az - bz;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
     if (kernel == 0) return 1.0 / r;
     if (kernel == 2) return r / (kparam0 * kparam0) * exp(-r / kparam0);  // d/dl of exp(-r / l)
     if (kernel >= 3) {
@@ -59,26 +59,30 @@ IFMM_DEVINL double kernel_eval(int kernel, double kparam0, double ax, double ay,
 // ---------------------------------------------------------------------------------------------
 // tree
 // ---------------------------------------------------------------------------------------------
-__global__ void k_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
-                            unsigned long long* keys, int64_t npad, int* status) {
+__global__ void k_leaf_keys(const double* pts, int64_t N, int depth, int dim, double x0, double y0, double z0,
+                            double L, unsigned long long* keys, int64_t npad, int* status) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npad) return;
     if (t >= N) { keys[t] = ~0ull; return; }
     const int side = 1 << depth;
-    double ux = (pts[2 * t] - x0) / L, uy = (pts[2 * t + 1] - y0) / L;
-    if (!(ux >= 0.0 && ux <= 1.0 && uy >= 0.0 && uy <= 1.0)) {
-        atomicOr(status, DEV_ERR_RANGE);
-        ux = fmin(fmax(ux, 0.0), 1.0);
-        uy = fmin(fmax(uy, 0.0), 1.0);
+    const double org[3] = {x0, y0, z0};
+    int c[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) {
+        double u = (pts[dim * t + i] - org[i]) / L;
+        if (!(u >= 0.0 && u <= 1.0)) {
+            atomicOr(status, DEV_ERR_RANGE);
+            u = fmin(fmax(u, 0.0), 1.0);
+        }
+        c[i] = min((int)floor(u * side), side - 1);
     }
-    int ix = min((int)floor(ux * side), side - 1), iy = min((int)floor(uy * side), side - 1);
-    unsigned long long m = spread_bits((unsigned)ix) | (spread_bits((unsigned)iy) << 1);
+    const unsigned long long m = morton_code(Cell{c[0], c[1], c[2]}, dim);
     keys[t] = (m << 32) | (unsigned long long)t;
 }
 
-void launch_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
+void launch_leaf_keys(const double* pts, int64_t N, int depth, int dim, double x0, double y0, double z0, double L,
                       unsigned long long* keys, int64_t npad, int* status, cudaStream_t st) {
-    k_leaf_keys<<<(unsigned)((npad + 255) / 256), 256, 0, st>>>(pts, N, depth, x0, y0, L, keys, npad, status); count_launches(1);
+    k_leaf_keys<<<(unsigned)((npad + 255) / 256), 256, 0, st>>>(pts, N, depth, dim, x0, y0, z0, L, keys, npad, status);
+    count_launches(1);
 }
 
 __global__ void k_bitonic_step(unsigned long long* keys, int64_t npad, int64_t j, int64_t k) {
@@ -127,23 +131,25 @@ void launch_bitonic_sort(unsigned long long* keys, int64_t npad, cudaStream_t st
     }
 }
 
-__global__ void k_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
-                                 double* px, double* py, int* leaf_count, int depth) {
+__global__ void k_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int dim, int64_t* perm,
+                                 double* px, double* py, double* pz, int* leaf_count, int depth) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     unsigned long long key = keys[t];
     int64_t idx = (int64_t)(key & 0xffffffffull);
-    unsigned long long m = key >> 32;
-    int ix = (int)compact_bits(m), iy = (int)compact_bits(m >> 1);
+    const Cell c = morton_cell(key >> 32, dim);
     perm[t] = idx;
-    px[t] = pts[2 * idx];
-    py[t] = pts[2 * idx + 1];
-    atomicAdd(&leaf_count[ix + (1 << depth) * iy], 1);
+    px[t] = pts[dim * idx];
+    py[t] = pts[dim * idx + 1];
+    pz[t] = dim == 3 ? pts[dim * idx + 2] : 0.0;
+    atomicAdd(&leaf_count[cell_index(c, 1 << depth)], 1);
 }
 
-void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
-                           double* px, double* py, int* leaf_count, int depth, cudaStream_t st) {
-    k_scatter_sorted<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(keys, pts, N, perm, px, py, leaf_count, depth); count_launches(1);
+void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int dim, int64_t* perm,
+                           double* px, double* py, double* pz, int* leaf_count, int depth, cudaStream_t st) {
+    k_scatter_sorted<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(keys, pts, N, dim, perm, px, py, pz, leaf_count,
+                                                                  depth);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -161,7 +167,8 @@ IFMM_DEVINL double lagrange1(int p, const double* t, int m, double x) {
 // leaf level's kept singular vectors, p^2 x rk in a p^2 x p^2 array, rk = *rsvd) the
 // orthonormalised matrix is V U and Rt is mapped back to node values: Rt <- Rt U^T.
 __global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const double* px, const double* py,
-                                                         const int64_t* leaf_start, const int* leaf_count,
+                                                         const double* pz, const int64_t* leaf_start,
+                                                         const int* leaf_count,
                                                          const double* cheb, double* W0, double* Rt, int* rank0,
                                                          double* Ascr, double* Vscr, const double* U,
                                                          const int* rsvd) {
@@ -171,21 +178,23 @@ __global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const doub
     __shared__ int cperm[64];
     const int b = blockIdx.x;
     const int side = 1 << a.depth;
-    const int bx = b % side, by = b / side;
+    const Cell cb = cell_of(b, side, a.dim);
     const int n = leaf_count[b];
     const int64_t s0 = leaf_start[b];
     const int p = a.p, r0 = a.r0;
     const double h = a.L / side;
-    const double lx = a.x0 + bx * h, ly = a.y0 + by * h;
+    const double lx = a.x0 + cb.x * h, ly = a.y0 + cb.y * h, lz = a.z0 + cb.z * h;
     double* A = Ascr + s0 * r0;
     double* Q = W0 + s0 * r0;
     const int rk = U ? *rsvd : r0;
     double* S = U ? Q : A;   // the interpolation matrix; with U it is projected into A below
     for (int t = threadIdx.x; t < n * r0; t += blockDim.x) {
         int i = t / r0, m = t - i * r0;
-        int mx = m % p, my = m / p;
+        int mx = m % p, my = (m / p) % p, mz = m / (p * p);
         double ux = 2.0 * (px[s0 + i] - lx) / h - 1.0, uy = 2.0 * (py[s0 + i] - ly) / h - 1.0;
-        S[(size_t)i * r0 + m] = lagrange1(p, cheb, mx, ux) * lagrange1(p, cheb, my, uy);
+        double v = lagrange1(p, cheb, mx, ux) * lagrange1(p, cheb, my, uy);
+        if (a.dim == 3) v *= lagrange1(p, cheb, mz, 2.0 * (pz[s0 + i] - lz) / h - 1.0);
+        S[(size_t)i * r0 + m] = v;
     }
     if (U) {
         __syncthreads();
@@ -218,20 +227,21 @@ __global__ void __launch_bounds__(kThreads) k_leaf_basis(BuildArgs a, const doub
     if (threadIdx.x == 0) rank0[b] = rank;
 }
 
-void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
-                       const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
-                       int max_n, const double* U, const int* rsvd, cudaStream_t st) {
+void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const double* pz,
+                       const int64_t* leaf_start, const int* leaf_count, const double* cheb, double* W0, double* Rt,
+                       int* rank0, int max_n, const double* U, const int* rsvd, cudaStream_t st) {
     (void)max_n;
     // scratch lives in the second half of W0's allocation (the caller allocates 3 N r0 doubles)
     double* Ascr = W0 + a.N * a.r0;
     double* Vscr = W0 + 2 * a.N * a.r0;
-    k_leaf_basis<<<1 << (2 * a.depth), kThreads, 0, st>>>(a, px, py, leaf_start, leaf_count, cheb, W0, Rt, rank0,
-                                                          Ascr, Vscr, U, rsvd); count_launches(1);
+    k_leaf_basis<<<1 << (a.dim * a.depth), kThreads, 0, st>>>(a, px, py, pz, leaf_start, leaf_count, cheb, W0, Rt,
+                                                              rank0, Ascr, Vscr, U, rsvd);
+    count_launches(1);
 }
 
-// per parent P at level k: Z stacks the rows (Rt_c T_c)[t, :], t < rank_c, of the four children
+// per parent P at level k: Z stacks the rows (Rt_c T_c)[t, :], t < rank_c, of the 2^d children
 // (Morton order) -> Z = Q Rt_P; Q is scattered into W0_P with rows c*r0 + t (zero rows for the
-// components a child does not have). Scratch: Z, reflectors and the compact Q, each 4 r0 x r0 per box,
+// components a child does not have). Scratch: Z, reflectors and the compact Q, each 2^d r0 x r0 per box,
 // in the tail of the level's W0 allocation. With the SVD compression (U, rsvd of this level, as in
 // k_leaf_basis) Z is orthonormalised in U's coordinates, Z U, and Rt mapped back, Rt U^T.
 __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, const double* Rt_child,
@@ -244,18 +254,18 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
     __shared__ int cperm[64];
     const int b = blockIdx.x;
     const int side = 1 << k, cs = side << 1;
-    const int bx = b % side, by = b / side;
-    const int r0 = a.r0;
-    int cg[4], off[5];
+    const Cell cb = cell_of(b, side, a.dim);
+    const int r0 = a.r0, nk = 1 << a.dim;
+    int cg[8], off[9];
     off[0] = 0;
-    for (int c = 0; c < 4; ++c) {
-        cg[c] = (2 * bx + (c & 1)) + cs * (2 * by + (c >> 1));
+    for (int c = 0; c < nk; ++c) {
+        cg[c] = cell_index(child_cell(cb, c), cs);
         off[c + 1] = off[c] + rank_child[cg[c]];
     }
-    const int m = off[4];
+    const int m = off[nk];
     const int rk = U ? *rsvd : r0;
-    double* Z = Zscr + (int64_t)b * 4 * r0 * r0;
-    double* Q = Qscr + (int64_t)b * 4 * r0 * r0;
+    double* Z = Zscr + (int64_t)b * nk * r0 * r0;
+    double* Q = Qscr + (int64_t)b * nk * r0 * r0;
     double* Z0 = U ? Q : Z;   // the stacked rows; with U projected into Z below
     for (int t = threadIdx.x; t < m * r0; t += blockDim.x) {
         int row = t / r0, col = t - row * r0;
@@ -280,11 +290,11 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
     }
     double* R = Rt + (int64_t)b * r0 * r0;
     for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) R[t] = 0.0;
-    double* W = W0 + (int64_t)b * 4 * r0 * r0;
-    for (int t = threadIdx.x; t < 4 * r0 * r0; t += blockDim.x) W[t] = 0.0;
+    double* W = W0 + (int64_t)b * nk * r0 * r0;
+    for (int t = threadIdx.x; t < nk * r0 * r0; t += blockDim.x) W[t] = 0.0;
     __syncthreads();
     int rank = 0;
-    if (m > 0) rank = cta_cpqr(Z, m, rk, r0, 1e-13, Q, r0, R, r0, Vscr + (int64_t)b * 4 * r0 * r0, beta, cperm, red, ired);
+    if (m > 0) rank = cta_cpqr(Z, m, rk, r0, 1e-13, Q, r0, R, r0, Vscr + (int64_t)b * nk * r0 * r0, beta, cperm, red, ired);
     if (U && rank > 0) {
         for (int t = threadIdx.x; t < rank * r0; t += blockDim.x) {   // Rt U^T through Z (rank <= m)
             int i = t / r0, l = t - i * r0;
@@ -307,17 +317,19 @@ __global__ void __launch_bounds__(kThreads) k_parent_basis(BuildArgs a, int k, c
 void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
                          const double* Tc, double* W0, double* Rt, int* rank0, const double* U, const int* rsvd,
                          cudaStream_t st) {
-    int64_t nb = 1ll << (2 * k);
-    double* Zscr = W0 + nb * 4 * a.r0 * a.r0;
-    double* Vscr = W0 + 2 * nb * 4 * a.r0 * a.r0;
-    double* Qscr = W0 + 3 * nb * 4 * a.r0 * a.r0;
+    int64_t nb = 1ll << (a.dim * k);
+    const int64_t nk = 1 << a.dim;
+    double* Zscr = W0 + nb * nk * a.r0 * a.r0;
+    double* Vscr = W0 + 2 * nb * nk * a.r0 * a.r0;
+    double* Qscr = W0 + 3 * nb * nk * a.r0 * a.r0;
     k_parent_basis<<<(unsigned)nb, kThreads, 0, st>>>(a, k, Rt_child, rank_child, Tc, W0, Rt, rank0, Zscr, Vscr,
                                                       Qscr, U, rsvd); count_launches(1);
 }
 
 // The SVD compression of the Chebyshev interpolation (Section 5, "Chebyshev interpolation followed by
 // SVD"), one level per launch, one CTA, top level first. G (m x r0, global scratch) stacks
-// K_d^T for the 40 interaction offsets d of a box (K_d[i, l] = K(node_i, node_l + h d), h the box side
+// K_d^T for the interaction offsets d of a box (2 <= max_i |d_i| <= 3: 40 in 2D, 316 in 3D;
+// K_d[i, l] = K(node_i, node_l + h d), h the box side
 // of level k) and, below the top level, the parent's kept directions seen from each child position,
 // (T_c U_{k-1} Sigma_{k-1})^T, so that the kept bases stay nested. G = Q R by Householder QR
 // (cta_cpqr, no cut), then a one-sided Jacobi SVD of R in shared memory: in each round the r0
@@ -336,34 +348,37 @@ __global__ void __launch_bounds__(kThreads) k_svd_level(BuildArgs a, int k, doub
     __shared__ int ired[32];
     __shared__ double beta[64];
     __shared__ int cperm[64];
-    __shared__ int offs[40];
+    __shared__ int offs[316];
     __shared__ double snorm[64];
     __shared__ int s_rot;
     const int r0 = a.r0, p = a.p;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double h = a.L / (double)(1 << k);
     const int rp = Up ? *rp_dev : 0;
-    const int m = 40 * r0 + 4 * rp;
+    const int noff = a.dim == 3 ? 316 : 40, nk = 1 << a.dim;
+    const int m = noff * r0 + nk * rp;
     if (threadIdx.x == 0) {
         int o = 0;
-        for (int dy = -3; dy <= 3; ++dy)
-            for (int dx = -3; dx <= 3; ++dx)
-                if (max(abs(dx), abs(dy)) >= 2) offs[o++] = (dx + 3) + 7 * (dy + 3);
+        for (int dz = (a.dim == 3 ? -3 : 0); dz <= (a.dim == 3 ? 3 : 0); ++dz)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dx = -3; dx <= 3; ++dx)
+                    if (max(abs(dx), max(abs(dy), abs(dz))) >= 2) offs[o++] = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 40 * r0 * r0; t += blockDim.x) {
+    auto node = [&](int m_, int c) { return 0.5 * (cheb[c == 0 ? m_ % p : (c == 1 ? (m_ / p) % p : m_ / (p * p))] + 1.0); };
+    for (int t = threadIdx.x; t < noff * r0 * r0; t += blockDim.x) {
         const int o = t / (r0 * r0), l = (t / r0) % r0, i = t % r0;
-        const int dx = offs[o] % 7 - 3, dy = offs[o] / 7 - 3;
-        const double ax = 0.5 * (cheb[i % p] + 1.0) * h, ay = 0.5 * (cheb[i / p] + 1.0) * h;
-        const double cx = (0.5 * (cheb[l % p] + 1.0) + dx) * h, cy = (0.5 * (cheb[l / p] + 1.0) + dy) * h;
-        G[t] = kernel_eval(a.kernel, a.kparam0, ax, ay, cx, cy);
+        const int dx = offs[o] % 7 - 3, dy = (offs[o] / 7) % 7 - 3, dz = offs[o] / 49 - 3;
+        const double az = a.dim == 3 ? node(i, 2) * h : 0.0, cz = a.dim == 3 ? (node(l, 2) + dz) * h : 0.0;
+        G[t] = kernel_eval(a.kernel, a.kparam0, node(i, 0) * h, node(i, 1) * h, az, (node(l, 0) + dx) * h,
+                           (node(l, 1) + dy) * h, cz);
     }
-    for (int t = threadIdx.x; t < 4 * rp * r0; t += blockDim.x) {
+    for (int t = threadIdx.x; t < nk * rp * r0; t += blockDim.x) {
         const int c = t / (rp * r0), j = (t / r0) % rp, i = t % r0;
         const double* T = Tc + (size_t)c * r0 * r0;
         double v = 0.0;
         for (int l = 0; l < r0; ++l) v += T[(size_t)i * r0 + l] * Up[(size_t)l * r0 + j];
-        G[(size_t)40 * r0 * r0 + t] = v * sp[j];
+        G[(size_t)noff * r0 * r0 + t] = v * sp[j];
     }
     double* R = ssm;             // r0 x r0
     double* V = ssm + r0 * r0;   // r0 x r0
@@ -440,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_level(BuildArgs a, int k, doub
 void launch_svd_level(const BuildArgs& a, int k, double svd_eps, const double* cheb, const double* Tc,
                       const double* Up, const double* sp, const int* rp, double* U, double* sig, int* rk,
                       double* scratch, cudaStream_t st) {
-    const size_t mmax = (size_t)44 * a.r0;
+    const size_t mmax = (size_t)(a.dim == 3 ? 324 : 44) * a.r0;
     double* G = scratch;
     double* Qs = G + mmax * a.r0;
     double* Vs = Qs + mmax * a.r0;
@@ -454,7 +469,7 @@ void launch_svd_level(const BuildArgs& a, int k, double svd_eps, const double* c
     count_launches(1);
 }
 
-size_t svd_scratch_doubles(int r0) { return (size_t)3 * 44 * r0 * r0; }
+size_t svd_scratch_doubles(int r0, int dim) { return (size_t)3 * (dim == 3 ? 324 : 44) * r0 * r0; }
 
 // M2L_bq = Rt_b K(nodes_b, nodes_q) Rt_q^T for q in the interaction list of b
 __global__ void __launch_bounds__(kThreads) k_m2l_build(BuildArgs a, int k, const double* cheb, const double* Rt,
@@ -462,20 +477,24 @@ __global__ void __launch_bounds__(kThreads) k_m2l_build(BuildArgs a, int k, cons
     extern __shared__ double msm[];  // Kc (r0 x r0), tmp (r0 x r0)
     const int b = blockIdx.x, j = blockIdx.y;
     const int side = 1 << k;
-    const int bx = b % side, by = b / side;
-    const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
+    const Cell cb = cell_of(b, side, a.dim);
+    const Cell cq = region_cell(cb, j, a.dim);
     const int r0 = a.r0, p = a.p;
-    double* out = far0 + ((int64_t)b * 36 + j) * r0 * r0;
-    if (!in_grid2(qx, qy, side) || max(abs(qx - bx), abs(qy - by)) <= 1) return;
-    const int q = qx + side * qy;
+    const int nreg = nregion(a.dim);
+    double* out = far0 + ((int64_t)b * nreg + j) * r0 * r0;
+    if (!cell_in(cq, side) || cheb_dist(cq, cb) <= 1) return;
+    const int q = cell_index(cq, side);
     const double h = a.L / side;
     double* Kc = msm;
     double* tmp = msm + r0 * r0;
+    const bool d3 = a.dim == 3;
     for (int t = threadIdx.x; t < r0 * r0; t += blockDim.x) {
         int m = t / r0, l = t - m * r0;
-        double ax = a.x0 + (bx + 0.5 * (cheb[m % p] + 1.0)) * h, ay = a.y0 + (by + 0.5 * (cheb[m / p] + 1.0)) * h;
-        double cx = a.x0 + (qx + 0.5 * (cheb[l % p] + 1.0)) * h, cy = a.y0 + (qy + 0.5 * (cheb[l / p] + 1.0)) * h;
-        Kc[t] = kernel_eval(a.kernel, a.kparam0, ax, ay, cx, cy);
+        double ax = a.x0 + (cb.x + 0.5 * (cheb[m % p] + 1.0)) * h, ay = a.y0 + (cb.y + 0.5 * (cheb[(m / p) % p] + 1.0)) * h;
+        double cx = a.x0 + (cq.x + 0.5 * (cheb[l % p] + 1.0)) * h, cy = a.y0 + (cq.y + 0.5 * (cheb[(l / p) % p] + 1.0)) * h;
+        double az = d3 ? a.z0 + (cb.z + 0.5 * (cheb[m / (p * p)] + 1.0)) * h : 0.0;
+        double cz = d3 ? a.z0 + (cq.z + 0.5 * (cheb[l / (p * p)] + 1.0)) * h : 0.0;
+        Kc[t] = kernel_eval(a.kernel, a.kparam0, ax, ay, az, cx, cy, cz);
     }
     __syncthreads();
     const double* Rb = Rt + (int64_t)b * r0 * r0;
@@ -503,29 +522,31 @@ void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const doubl
         cudaFuncSetAttribute(k_m2l_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr.store(true);
     }
-    k_m2l_build<<<dim3(1u << (2 * k), 36), kThreads, smem, st>>>(a, k, cheb, Rt, far0); count_launches(1);
+    k_m2l_build<<<dim3(1u << (a.dim * k), nregion(a.dim)), kThreads, smem, st>>>(a, k, cheb, Rt, far0);
+    count_launches(1);
 }
 
 // leaf P2P blocks and the matrix scale s_A (largest column norm of the diagonal blocks)
 __global__ void __launch_bounds__(kThreads) k_p2p_build(BuildArgs a, const double* px, const double* py,
-                                                        const int64_t* leaf_start, const int* leaf_count,
-                                                        const int64_t* p2p_off, double* p2p,
+                                                        const double* pz, const int64_t* leaf_start,
+                                                        const int* leaf_count, const int64_t* p2p_off, double* p2p,
                                                         unsigned long long* sA_bits) {
     const int b = blockIdx.x, d = blockIdx.y;
-    const int side = 1 << a.depth;
-    const int bx = b % side, by = b / side;
-    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
-    if (!in_grid2(qx, qy, side)) return;
-    const int q = qx + side * qy;
+    const int side = 1 << a.depth, nd = ndirs(a.dim);
+    const Cell cq = cell_dir(cell_of(b, side, a.dim), d, a.dim);
+    if (!cell_in(cq, side)) return;
+    const int q = cell_index(cq, side);
     const int nb_ = leaf_count[b], nq = leaf_count[q];
     const int64_t sb = leaf_start[b], sq = leaf_start[q];
-    double* out = p2p + p2p_off[(int64_t)b * 9 + d];
+    double* out = p2p + p2p_off[(int64_t)b * nd + d];
     for (int t = threadIdx.x; t < nb_ * nq; t += blockDim.x) {
         int i = t / nq, j = t - i * nq;
-        double v = (b == q && i == j) ? a.diag : kernel_eval(a.kernel, a.kparam0, px[sb + i], py[sb + i], px[sq + j], py[sq + j]);
+        double v = (b == q && i == j) ? a.diag
+                                      : kernel_eval(a.kernel, a.kparam0, px[sb + i], py[sb + i], pz[sb + i], px[sq + j],
+                                                    py[sq + j], pz[sq + j]);
         out[t] = v;
     }
-    if (d != 4) return;
+    if (d != nd / 2) return;
     __syncthreads();
     double mx = 0.0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
@@ -536,11 +557,12 @@ __global__ void __launch_bounds__(kThreads) k_p2p_build(BuildArgs a, const doubl
     if (mx > 0.0) atomicMax(sA_bits, (unsigned long long)__double_as_longlong(mx));
 }
 
-void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
-                      const int* leaf_count, const int64_t* p2p_off, double* p2p, double* sA_bits,
-                      cudaStream_t st) {
-    k_p2p_build<<<dim3(1u << (2 * a.depth), 9), kThreads, 0, st>>>(a, px, py, leaf_start, leaf_count, p2p_off, p2p,
-                                                                   reinterpret_cast<unsigned long long*>(sA_bits)); count_launches(1);
+void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const double* pz,
+                      const int64_t* leaf_start, const int* leaf_count, const int64_t* p2p_off, double* p2p,
+                      double* sA_bits, cudaStream_t st) {
+    k_p2p_build<<<dim3(1u << (a.dim * a.depth), ndirs(a.dim)), kThreads, 0, st>>>(
+        a, px, py, pz, leaf_start, leaf_count, p2p_off, p2p, reinterpret_cast<unsigned long long*>(sA_bits));
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -594,49 +616,53 @@ __global__ void __launch_bounds__(kThreads) k_mv_leaf_up(const T* W0, const int6
         [&](int i, int j, T v) { yb[(size_t)i * nrhs + j] = v; }, sm);
 }
 template <typename T>
-void launch_mv_leaf_up(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+void launch_mv_leaf_up(int dim, int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
                        const T* xt, T* y, int nrhs, cudaStream_t st) {
-    k_mv_leaf_up<T><<<1u << (2 * depth), kThreads, 0, st>>>(W0, leaf_start, leaf_count, r0, xt, y, nrhs); count_launches(1);
+    k_mv_leaf_up<T><<<1u << (dim * depth), kThreads, 0, st>>>(W0, leaf_start, leaf_count, r0, xt, y, nrhs);
+    count_launches(1);
 }
 
-// M2M: y_P = W0_P^T [y_c]  (W0_P rows c*r0 + t)
+// M2M: y_P = W0_P^T [y_c]  (W0_P rows c*r0 + t, 2^d children)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs) {
+__global__ void __launch_bounds__(kThreads) k_mv_up(int dim, int k, const T* W0, int r0, const T* ychild, T* y,
+                                                    int nrhs) {
     __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
-    const int side = 1 << k, cs = side << 1;
-    const int bx = b % side, by = b / side;
-    const T* W = W0 + (int64_t)b * 4 * r0 * r0;
+    const int side = 1 << k, cs = side << 1, nk = 1 << dim;
+    const Cell cb = cell_of(b, side, dim);
+    const T* W = W0 + (int64_t)b * nk * r0 * r0;
     T* yb = y + (int64_t)b * r0 * nrhs;
     cta_gemm<T>(
-        r0, nrhs, 4 * r0, [&](int i, int kk) { return W[(size_t)kk * r0 + i]; },
+        r0, nrhs, nk * r0, [&](int i, int kk) { return W[(size_t)kk * r0 + i]; },
         [&](int kk, int j) {
             int c = kk / r0, t = kk - c * r0;
-            int cg = (2 * bx + (c & 1)) + cs * (2 * by + (c >> 1));
+            int cg = cell_index(child_cell(cb, c), cs);
             return ychild[((int64_t)cg * r0 + t) * nrhs + j];
         },
         [&](int i, int j, T v) { yb[(size_t)i * nrhs + j] = v; }, sm);
 }
 template <typename T>
-void launch_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st) {
-    k_mv_up<T><<<1u << (2 * k), kThreads, 0, st>>>(k, W0, r0, ychild, y, nrhs); count_launches(1);
+void launch_mv_up(int dim, int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st) {
+    k_mv_up<T><<<1u << (dim * k), kThreads, 0, st>>>(dim, k, W0, r0, ychild, y, nrhs);
+    count_launches(1);
 }
 
 // M2L: z_b = sum_{q in I_b} M2L_bq y_q
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs) {
+__global__ void __launch_bounds__(kThreads) k_mv_m2l(int dim, int k, const T* far0, int r0, const T* y, T* z,
+                                                     int nrhs) {
     __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
-    const int side = 1 << k;
-    const int bx = b % side, by = b / side;
+    const int side = 1 << k, nreg = nregion(dim);
+    const Cell cb = cell_of(b, side, dim);
     T* zb = z + (int64_t)b * r0 * nrhs;
     for (int t = threadIdx.x; t < r0 * nrhs; t += blockDim.x) zb[t] = (T)0;
     __syncthreads();
-    for (int j = 0; j < 36; ++j) {
-        const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
-        if (!in_grid2(qx, qy, side) || max(abs(qx - bx), abs(qy - by)) <= 1) continue;
-        const int q = qx + side * qy;
-        const T* M = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+    for (int j = 0; j < nreg; ++j) {
+        const Cell cq = region_cell(cb, j, dim);
+        if (!cell_in(cq, side) || cheb_dist(cq, cb) <= 1) continue;
+        const int q = cell_index(cq, side);
+        const T* M = far0 + ((int64_t)b * nreg + j) * r0 * r0;
         const T* yq = y + (int64_t)q * r0 * nrhs;
         cta_gemm<T>(
             r0, nrhs, r0, [&](int i, int kk) { return M[(size_t)i * r0 + kk]; },
@@ -646,20 +672,22 @@ __global__ void __launch_bounds__(kThreads) k_mv_m2l(int k, const T* far0, int r
     }
 }
 template <typename T>
-void launch_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st) {
-    k_mv_m2l<T><<<1u << (2 * k), kThreads, 0, st>>>(k, far0, r0, y, z, nrhs); count_launches(1);
+void launch_mv_m2l(int dim, int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st) {
+    k_mv_m2l<T><<<1u << (dim * k), kThreads, 0, st>>>(dim, k, far0, r0, y, z, nrhs);
+    count_launches(1);
 }
 
 // L2L: z_c += W0_P[rows of c] z_P, one block per child box c at level k+1
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs) {
+__global__ void __launch_bounds__(kThreads) k_mv_down(int dim, int k, const T* W0, int r0, const T* z, T* zchild,
+                                                      int nrhs) {
     __shared__ T sm[gemm_smem<T>::value];
     const int cgi = blockIdx.x;
-    const int cs = 2 << k;
-    const int cx = cgi % cs, cy = cgi / cs;
-    const int P = (cx >> 1) + (cs >> 1) * (cy >> 1);
-    const int c = (cx & 1) + 2 * (cy & 1);
-    const T* W = W0 + ((int64_t)P * 4 + c) * r0 * r0;
+    const int cs = 2 << k, nk = 1 << dim;
+    const Cell cc = cell_of(cgi, cs, dim);
+    const int P = cell_index(Cell{cc.x >> 1, cc.y >> 1, cc.z >> 1}, cs >> 1);
+    const int c = (cc.x & 1) + 2 * (cc.y & 1) + 4 * (cc.z & 1);
+    const T* W = W0 + ((int64_t)P * nk + c) * r0 * r0;
     const T* zP = z + (int64_t)P * r0 * nrhs;
     T* zc = zchild + (int64_t)cgi * r0 * nrhs;
     cta_gemm<T>(
@@ -668,19 +696,20 @@ __global__ void __launch_bounds__(kThreads) k_mv_down(int k, const T* W0, int r0
         [&](int i, int j, T v) { zc[(size_t)i * nrhs + j] += v; }, sm);
 }
 template <typename T>
-void launch_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st) {
-    k_mv_down<T><<<1u << (2 * (k + 1)), kThreads, 0, st>>>(k, W0, r0, z, zchild, nrhs); count_launches(1);
+void launch_mv_down(int dim, int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st) {
+    k_mv_down<T><<<1u << (dim * (k + 1)), kThreads, 0, st>>>(dim, k, W0, r0, z, zchild, nrhs);
+    count_launches(1);
 }
 
 // L2P + P2P: out_b = W0_b z_b + sum_{q in N_b} P2P_bq x_q
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start,
+__global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int dim, int depth, const T* W0, const int64_t* leaf_start,
                                                            const int* leaf_count, int r0, const T* z, const T* xt,
                                                            const int64_t* p2p_off, const T* p2p, T* out, int nrhs) {
     __shared__ T sm[gemm_smem<T>::value];
     const int b = blockIdx.x;
-    const int side = 1 << depth;
-    const int bx = b % side, by = b / side;
+    const int side = 1 << depth, nd = ndirs(dim);
+    const Cell cb = cell_of(b, side, dim);
     const int64_t s0 = leaf_start[b];
     const int n = leaf_count[b];
     const T* W = W0 + s0 * r0;
@@ -691,12 +720,12 @@ __global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const T* W
         [&](int kk, int j) { return zb[(size_t)kk * nrhs + j]; },
         [&](int i, int j, T v) { ob[(size_t)i * nrhs + j] = v; }, sm);
     __syncthreads();
-    for (int d = 0; d < 9; ++d) {
-        const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
-        if (!in_grid2(qx, qy, side)) continue;
-        const int q = qx + side * qy;
+    for (int d = 0; d < nd; ++d) {
+        const Cell cq = cell_dir(cb, d, dim);
+        if (!cell_in(cq, side)) continue;
+        const int q = cell_index(cq, side);
         const int nq = leaf_count[q];
-        const T* B = p2p + p2p_off[(int64_t)b * 9 + d];
+        const T* B = p2p + p2p_off[(int64_t)b * nd + d];
         const T* xq = xt + leaf_start[q] * nrhs;
         cta_gemm<T>(
             n, nrhs, nq, [&](int i, int kk) { return B[(size_t)i * nq + kk]; },
@@ -706,11 +735,12 @@ __global__ void __launch_bounds__(kThreads) k_mv_leaf_down(int depth, const T* W
     }
 }
 template <typename T>
-void launch_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+void launch_mv_leaf_down(int dim, int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
                          const T* z, const T* xt, const int64_t* p2p_off, const T* p2p, T* out, int nrhs,
                          cudaStream_t st) {
-    k_mv_leaf_down<T><<<1u << (2 * depth), kThreads, 0, st>>>(depth, W0, leaf_start, leaf_count, r0, z, xt, p2p_off,
-                                                              p2p, out, nrhs); count_launches(1);
+    k_mv_leaf_down<T><<<1u << (dim * depth), kThreads, 0, st>>>(dim, depth, W0, leaf_start, leaf_count, r0, z, xt,
+                                                                p2p_off, p2p, out, nrhs);
+    count_launches(1);
 }
 
 // split of an FP64 array into double-float pairs
@@ -755,12 +785,12 @@ void launch_split_dfl(const double* a, dfl* b, int64_t n, cudaStream_t st) {
 #define IFMM_MV_INSTANTIATE(T)                                                                                    \
     template void launch_mv_permute_in<T>(const double*, int64_t, int64_t, int, const int64_t*, T*, cudaStream_t); \
     template void launch_mv_permute_out<T>(const T*, int64_t, int, const int64_t*, double*, int64_t, cudaStream_t); \
-    template void launch_mv_leaf_up<T>(int, const T*, const int64_t*, const int*, int, const T*, T*, int,         \
+    template void launch_mv_leaf_up<T>(int, int, const T*, const int64_t*, const int*, int, const T*, T*, int,    \
                                        cudaStream_t);                                                            \
-    template void launch_mv_up<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                           \
-    template void launch_mv_m2l<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                          \
-    template void launch_mv_down<T>(int, const T*, int, const T*, T*, int, cudaStream_t);                         \
-    template void launch_mv_leaf_down<T>(int, const T*, const int64_t*, const int*, int, const T*, const T*,      \
+    template void launch_mv_up<T>(int, int, const T*, int, const T*, T*, int, cudaStream_t);                      \
+    template void launch_mv_m2l<T>(int, int, const T*, int, const T*, T*, int, cudaStream_t);                     \
+    template void launch_mv_down<T>(int, int, const T*, int, const T*, T*, int, cudaStream_t);                    \
+    template void launch_mv_leaf_down<T>(int, int, const T*, const int64_t*, const int*, int, const T*, const T*, \
                                          const int64_t*, const T*, T*, int, cudaStream_t);
 IFMM_MV_INSTANTIATE(double)
 IFMM_MV_INSTANTIATE(dfl)

@@ -19,12 +19,6 @@ constexpr int kThreads = 256;  // block size of every per-box kernel
 
 IFMM_DEVINL int colour_of(int ix, int iy) { return (ix % 3) + 3 * (iy % 3); }
 
-// index of box (qx, qy) in the 6 x 6 grid made of the children of the 3 x 3 neighbourhood of
-// p's parent; every neighbour and every interaction-list box of p lies in it
-IFMM_DEVINL int region36(int px, int py, int qx, int qy) {
-    return (qx - 2 * (px >> 1) + 2) + 6 * (qy - 2 * (py >> 1) + 2);
-}
-
 template <typename T>
 IFMM_DEVINL T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -1,8 +1,9 @@
 // ifmm_factor.cu -- elimination (Algorithm 1) and replay (Algorithm 2) kernels, sm_103a.
 //
 // One colour of one level is eliminated by five launches over the boxes of that colour
-// (colour = (ix mod 3) + 3 (iy mod 3): boxes of one colour are at Chebyshev distance >= 3, so
-// their neighbourhoods N_e, and every block they touch, are disjoint):
+// (colour = (ix mod 3) + 3 (iy mod 3) (+ 9 (iz mod 3) in 3D): boxes of one colour are at Chebyshev
+// distance >= 3, so their neighbourhoods N_e, and every block they touch, are disjoint). A launch's
+// blockIdx.y is a neighbour direction (3^d of them) or an ordered pair of directions (9^d):
 //   k_pivot    form Piv_e = [[P2P_ee, L2P_ee], [P2M_ee, 0]] (rows P2P(e,k), P2M(e,k), columns
 //              x_e, z_e) and invert it in FP64 (Gauss-Jordan, partial pivoting);
 //   k_panel    X = Piv_e^{-1} [B; 0] for every neighbour column block (B = row P2P_e at the
@@ -40,26 +41,32 @@ template <typename T> struct AccOf { using type = double; };
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<dfl> { using type = dfl; };
 
+// (2D grid test of the tensor-core replay kernels, which serve quadtrees only)
 IFMM_DEVINL bool in_grid(int x, int y, int side) { return x >= 0 && y >= 0 && x < side && y < side; }
 
 template <typename T>
 IFMM_DEVINL T* block_at(const LevelView<T>& L, int p, int q, int& ld) {
-    int px = p % L.side, py = p / L.side, qx = q % L.side, qy = q / L.side;
-    int j = region36(px, py, qx, qy);
-    int64_t o = L.boff[(int64_t)p * 36 + j];
-    ld = L.bld[(int64_t)p * 36 + j];
+    const int j = region_index(cell_of(p, L.side, L.dim), cell_of(q, L.side, L.dim), L.dim);
+    int64_t o = L.boff[(int64_t)p * L.nreg + j];
+    ld = L.bld[(int64_t)p * L.nreg + j];
     return o < 0 ? nullptr : L.blk + o;
 }
 
-// column offset inside X of the block of neighbour direction dsel (dsel == 4: the y_e block)
+// offset of the fill of the ordered direction pair (da, db) of box e
 template <typename T>
-IFMM_DEVINL int xcol_offset(const LevelView<T>& L, int ex, int ey, int dsel) {
+IFMM_DEVINL int64_t fill_off(const LevelView<T>& L, int e, int da, int db) {
+    return L.fsoff[((int64_t)e * L.nd + da) * L.nd + db];
+}
+
+// column offset inside X of the block of neighbour direction dsel (dsel == ctr: the y_e block)
+template <typename T>
+IFMM_DEVINL int xcol_offset(const LevelView<T>& L, Cell ce, int dsel) {
     int off = 0;
-    for (int d = 0; d < 9; ++d) {
-        if (d == 4) continue;
+    for (int d = 0; d < L.nd; ++d) {
+        if (d == L.ctr) continue;
         if (d == dsel) return off;
-        int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
-        if (in_grid(qx, qy, L.side)) off += L.n[qx + L.side * qy];
+        const Cell cq = cell_dir(ce, d, L.dim);
+        if (cell_in(cq, L.side)) off += L.n[cell_index(cq, L.side)];
     }
     return off;
 }
@@ -68,15 +75,14 @@ IFMM_DEVINL int xcol_offset(const LevelView<T>& L, int ex, int ey, int dsel) {
 // directions da, db. For a symmetric kernel only the pair with da < db is stored (F_ba = F_ab^T).
 template <typename T>
 IFMM_DEVINL T fill_at(const LevelView<T>& L, int e, int da, int db, int wa, int wb, int i, int j) {
-    if (!L.symmetric || da < db) return L.Fs[L.fsoff[(int64_t)e * 81 + da * 9 + db] + (size_t)i * wb + j];
-    return L.Fs[L.fsoff[(int64_t)e * 81 + db * 9 + da] + (size_t)j * wa + i];
+    if (!L.symmetric || da < db) return L.Fs[fill_off(L, e, da, db) + (size_t)i * wb + j];
+    return L.Fs[fill_off(L, e, db, da) + (size_t)j * wa + i];
 }
 
 // active width of box b while eliminating colour c: r_b once eliminated, n_b before
 template <typename T>
 IFMM_DEVINL int active_width(const LevelView<T>& L, int b, int colour) {
-    int bx = b % L.side, by = b / L.side;
-    return colour_of(bx, by) < colour ? L.r[b] : L.n[b];
+    return cell_colour(cell_of(b, L.side, L.dim)) < colour ? L.r[b] : L.n[b];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -334,30 +340,30 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L0, BoxList<T> 
     __shared__ GS sm[gemm_smem<GS>::value];
     const int e = bl.box(blockIdx.x);
     const int d = blockIdx.y;
-    const int ex = e % L.side, ey = e / L.side;
-    const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
-    if (!in_grid(qx, qy, L.side)) return;
+    const Cell ce = cell_of(e, L.side, L.dim);
+    const Cell cq = cell_dir(ce, d, L.dim);
+    if (!cell_in(cq, L.side)) return;
     const int n = L.n[e], r = L.r[e], s = n + r;
     T* X = L.Xs + L.xsoff[e];
     const int ldx = L.xsld[e];
     const T* Pi = L.Pi + L.pioff[e];
     const int ldpi = L.pild[e];
-    if (d == 4) {
+    if (d == L.ctr) {
         if (blockIdx.z != 0) return;
-        int cy = xcol_offset(L, ex, ey, 4);
+        int cy = xcol_offset(L, ce, L.ctr);
         for (int t = threadIdx.x; t < s * r; t += blockDim.x) {
             int i = t / r, j = t - i * r;
             X[(size_t)i * ldx + cy + j] = -Pi[(size_t)i * ldpi + n + j];
         }
         return;
     }
-    const int q = qx + L.side * qy;
+    const int q = cell_index(cq, L.side);
     const int wq = active_width(L, q, colour);
     int ldb;
     const T* B = block_at(L, e, q, ldb);
     if (blockIdx.z == 0) {
         // B panel (row P2P_e at q's active unknown), n x wq, kept for the back substitution
-        T* Bp = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+        T* Bp = L.Bp + L.bpoff[(int64_t)e * L.nd + d];
         for (int t = threadIdx.x; t < n * wq; t += blockDim.x) {
             int i = t / wq, j = t - i * wq;
             Bp[t] = B[(size_t)i * ldb + j];
@@ -365,13 +371,13 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L0, BoxList<T> 
         // C panel (q's active equation at x_e), wq x n, kept for the forward replay and the Schur step
         int ldc;
         const T* C = block_at(L, q, e, ldc);
-        T* Cp = L.Cp + L.cpoff[(int64_t)e * 9 + d];
+        T* Cp = L.Cp + L.cpoff[(int64_t)e * L.nd + d];
         for (int t = threadIdx.x; t < wq * n; t += blockDim.x) {
             int i = t / n, j = t - i * n;
             Cp[t] = C[(size_t)i * ldc + j];
         }
     }
-    const int cx = xcol_offset(L, ex, ey, d);
+    const int cx = xcol_offset(L, ce, d);
     factor_gemm<T, DF>(
         L, s, wq, n, [&](int i, int k) { return Pi[(size_t)i * ldpi + k]; },
         [&](int k, int j) { return B[(size_t)k * ldb + j]; },
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_panel(LevelView<T> L0, BoxList<T> 
 }
 
 // ---------------------------------------------------------------------------------------------
-// k_schur: one (p, q) pair of neighbours of e per block (p, q in N_e; dp == 4 is row M2L_e)
+// k_schur: one (p, q) pair of neighbours of e per block (p, q in N_e; dp == ctr is row M2L_e)
 // ---------------------------------------------------------------------------------------------
 // GM selects the product: 0 = the working precision (FP64 exact extent, or FP32), 1 = double-float
 // on the FP32 pipe, 2 = the tensor cores (ifmm_tc.cuh: digit-split bf16 MMAs, 128 threads, dynamic
@@ -406,22 +412,21 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
         }
     };
     const int e = bl.box(blockIdx.x);
-    const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
-    const int ex = e % L.side, ey = e / L.side;
-    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
-    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
-    if (!in_grid(px, py, L.side) || !in_grid(qx, qy, L.side)) return;
-    const int p = px + L.side * py, q = qx + L.side * qy;
+    const int dp = blockIdx.y / L.nd, dq = blockIdx.y % L.nd;
+    const Cell ce = cell_of(e, L.side, L.dim);
+    const Cell cp = cell_dir(ce, dp, L.dim), cq = cell_dir(ce, dq, L.dim);
+    if (!cell_in(cp, L.side) || !cell_in(cq, L.side)) return;
+    const int p = cell_index(cp, L.side), q = cell_index(cq, L.side);
     const int n = L.n[e], r = L.r[e];
     const T* X = L.Xs + L.xsoff[e];
     const int ldx = L.xsld[e];
-    if (dp == 4) {
+    if (dp == L.ctr) {
         // row M2L_e has -I at z_e: A[M2L_e, gamma] = X_gamma[z rows]
         if (blockIdx.z != 0) return;
         int ld;
         T* dst = block_at(L, e, q, ld);
-        const int w = (dq == 4) ? r : active_width(L, q, colour);
-        const int cx = xcol_offset(L, ex, ey, dq);
+        const int w = (dq == L.ctr) ? r : active_width(L, q, colour);
+        const int cx = xcol_offset(L, ce, dq);
         for (int t = threadIdx.x; t < r * w; t += blockDim.x) {
             int i = t / w, j = t - i * w;
             dst[(size_t)i * ld + j] = X[(size_t)(n + i) * ldx + cx + j];
@@ -429,11 +434,11 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
         return;
     }
     // symmetric kernel: the (q, p) block is the transpose of the (p, q) block, written by that block
-    if (L.symmetric && dq != 4 && dp > dq) return;
+    if (L.symmetric && dq != L.ctr && dp > dq) return;
     const int wp = active_width(L, p, colour);
-    const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
-    const int cx = xcol_offset(L, ex, ey, dq);
-    if (dq == 4) {
+    const T* C = L.Cp + L.cpoff[(int64_t)e * L.nd + dp];
+    const int cx = xcol_offset(L, ce, dq);
+    if (dq == L.ctr) {
         // new column y_e in row rho_p: M2P_pe or M2L_pe = -C_p X_y[x rows]
         int ld;
         T* dst = block_at(L, p, e, ld);
@@ -448,8 +453,8 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
         return;
     }
     const int wq = active_width(L, q, colour);
-    const int dist = max(abs(px - qx), abs(py - qy));
-    const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
+    const int dist = cheb_dist(cp, cq);
+    const bool Ep = cell_colour(cp) < colour, Eq = cell_colour(cq) < colour;
     if (dist <= 1 || (Ep && Eq)) {
         // neighbours: dense update in place; both eliminated: M2L_pq updated directly
         int ld, ld2 = 0;
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_schur(Lev
                  if (dst2) dst2[(size_t)j * ld2 + i] = (T)((Acc)dst2[(size_t)j * ld2 + i] - v);
              });
     } else {
-        T* F = L.Fs + L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
+        T* F = L.Fs + fill_off(L, e, dp, dq);
         gemm(wp, wq, n, [&](int i, int k) { return C[(size_t)i * n + k]; },
              [&](int k, int j) { return X[(size_t)k * ldx + cx + j]; },
              [&](int i, int j, Acc v) { F[(size_t)i * wq + j] = (T)(-v); });
@@ -501,6 +506,7 @@ IFMM_DEVINL dfl gs_axpy(dfl r, dfl s, dfl u) {
 
 // gscr: the FP64 work arrays live in the colour's global scratch (L.Cws) instead of shared memory
 // (wide fills, whose arrays exceed the shared-memory budget of the launch)
+constexpr int kMaxPartners = 19;
 template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<T> bl, int colour, int gscr) {
     const LevelView<T>& L = bl.view(L0, blockIdx.x);
@@ -514,17 +520,18 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     __shared__ int s_flag;
     const int e = bl.box(blockIdx.x);
     const int dq = blockIdx.y;
-    if (dq == 4) return;
-    const int ex = e % L.side, ey = e / L.side;
-    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
-    if (!in_grid(qx, qy, L.side) || colour_of(qx, qy) < colour) return;
-    const int q = qx + L.side * qy;
-    int parts[8], np = 0;
-    for (int dp = 0; dp < 9; ++dp) {
-        if (dp == 4 || dp == dq) continue;
-        int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
-        if (!in_grid(px, py, L.side)) continue;
-        if (max(abs(px - qx), abs(py - qy)) == 2) parts[np++] = dp;
+    if (dq == L.ctr) return;
+    const Cell ce = cell_of(e, L.side, L.dim);
+    const Cell cq = cell_dir(ce, dq, L.dim);
+    if (!cell_in(cq, L.side) || cell_colour(cq) < colour) return;
+    const int q = cell_index(cq, L.side);
+    // partners: the neighbours of e at Chebyshev distance 2 from q (at most 5 in 2D, 19 in 3D)
+    int parts[kMaxPartners], np = 0;
+    for (int dp = 0; dp < L.nd; ++dp) {
+        if (dp == L.ctr || dp == dq) continue;
+        const Cell cp = cell_dir(ce, dp, L.dim);
+        if (!cell_in(cp, L.side)) continue;
+        if (cheb_dist(cp, cq) == 2) parts[np++] = dp;
     }
     if (np == 0) return;
     const int nq = L.n[q];
@@ -534,16 +541,16 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     // update writes each fill pair as a block and its transpose (F_pq^T = F_qp bit for bit), so the
     // row fills F_qp alone make up S_q (reading R2)
     const bool half = L.symmetric != 0;
-    int wps[8], m = 0;
+    int wps[kMaxPartners], m = 0;
     for (int t = 0; t < np; ++t) {
         int dp = parts[t];
-        int p = (ex + dp % 3 - 1) + L.side * (ey + dp / 3 - 1);
+        int p = cell_index(cell_dir(ce, dp, L.dim), L.side);
         wps[t] = active_width(L, p, colour);
         m += (half ? 1 : 2) * wps[t];
     }
     if (nq == 0 || m == 0) return;
-    T* R = L.Rs + L.rsoff[(int64_t)e * 9 + dq];
-    double* csm = gscr ? L.Cws + L.cwsoff[(int64_t)e * 9 + dq] : csm_dyn;
+    T* R = L.Rs + L.rsoff[(int64_t)e * L.nd + dq];
+    double* csm = gscr ? L.Cws + L.cwsoff[(int64_t)e * L.nd + dq] : csm_dyn;
     {
         int c0 = 0;
         for (int t = 0; t < np; ++t) {
@@ -747,22 +754,21 @@ __global__ void __launch_bounds__(kThreads) k_redirect(LevelView<T> L0, BoxList<
     using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS sm[gemm_smem<GS>::value];
     const int e = bl.box(blockIdx.x);
-    const int dp = blockIdx.y / 9, dq = blockIdx.y % 9;
-    if (dp == 4 || dq == 4 || dp == dq) return;
-    const int ex = e % L.side, ey = e / L.side;
-    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
-    const int qx = ex + dq % 3 - 1, qy = ey + dq / 3 - 1;
-    if (!in_grid(px, py, L.side) || !in_grid(qx, qy, L.side)) return;
-    if (max(abs(px - qx), abs(py - qy)) != 2) return;
-    const bool Ep = colour_of(px, py) < colour, Eq = colour_of(qx, qy) < colour;
+    const int dp = blockIdx.y / L.nd, dq = blockIdx.y % L.nd;
+    if (dp == L.ctr || dq == L.ctr || dp == dq) return;
+    const Cell ce = cell_of(e, L.side, L.dim);
+    const Cell cp = cell_dir(ce, dp, L.dim), cq = cell_dir(ce, dq, L.dim);
+    if (!cell_in(cp, L.side) || !cell_in(cq, L.side)) return;
+    if (cheb_dist(cp, cq) != 2) return;
+    const bool Ep = cell_colour(cp) < colour, Eq = cell_colour(cq) < colour;
     if (Ep && Eq) return;
     if (L.symmetric && dp > dq) return;   // M2L_qp += G_pq^T below
-    const int p = px + L.side * py, q = qx + L.side * qy;
+    const int p = cell_index(cp, L.side), q = cell_index(cq, L.side);
     const int wp = Ep ? L.r[p] : L.n[p];
     const int wq = Eq ? L.r[q] : L.n[q];
     const int rp = L.r[p], rq = L.r[q];
     const int RC = L.RC;
-    const int64_t fo = L.fsoff[(int64_t)e * 81 + dp * 9 + dq];
+    const int64_t fo = fill_off(L, e, dp, dq);
     const T* F = L.Fs + fo;   // wp x wq
     T* F2 = L.Fs2 + fo;       // wp x rq
     int ld, ld2 = 0;
@@ -944,12 +950,13 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     // or 32 for the double-float products)
     const int tw = L.gemm_dfl ? 32 : 64;
     const int tiles = ((L.nmax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw);
-    const int zs = std::max(1, std::min(tiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
+    const int nd = L.nd, npair = nd * nd, nact = L.dim == 3 ? 343 : 49;   // active pairs, roughly
+    const int zs = std::max(1, std::min(tiles, (608 + nboxes * nact - 1) / (nboxes * nact)));
     const int zp = std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8)));
     if (ev) cudaEventRecord(ev[1], st);
     const bool df = std::is_same<T, double>::value && L.gemm_dfl;
-    if (df) k_panel<T, true><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, bl, colour);
-    else k_panel<T, false><<<dim3(nboxes, 9, zp), kThreads, 0, st>>>(L, bl, colour);
+    if (df) k_panel<T, true><<<dim3(nboxes, nd, zp), kThreads, 0, st>>>(L, bl, colour);
+    else k_panel<T, false><<<dim3(nboxes, nd, zp), kThreads, 0, st>>>(L, bl, colour);
     if (ev) cudaEventRecord(ev[2], st);
     if (df && L.gemm_tc) {
         // tensor-core products: output tiles of 128 x 32, 82.6 KB of dynamic shared memory
@@ -959,31 +966,32 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
             tc_attr.store(true);
         }
         const int ttiles = ((L.nmax + tc::kTM - 1) / tc::kTM) * ((L.nmax + tc::kTN - 1) / tc::kTN);
-        const int zt = std::max(1, std::min(ttiles, (608 + nboxes * 49 - 1) / (nboxes * 49)));
-        k_schur<T, 2><<<dim3(nboxes, 81, zt), tc::kThreads, tc::kSmemBytes, st>>>(L, bl, colour);
+        const int zt = std::max(1, std::min(ttiles, (608 + nboxes * nact - 1) / (nboxes * nact)));
+        k_schur<T, 2><<<dim3(nboxes, npair, zt), tc::kThreads, tc::kSmemBytes, st>>>(L, bl, colour);
     } else if (df) {
-        k_schur<T, 1><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, bl, colour);
+        k_schur<T, 1><<<dim3(nboxes, npair, zs), kThreads, 0, st>>>(L, bl, colour);
     } else {
-        k_schur<T, 0><<<dim3(nboxes, 81, zs), kThreads, 0, st>>>(L, bl, colour);
+        k_schur<T, 0><<<dim3(nboxes, npair, zs), kThreads, 0, st>>>(L, bl, colour);
     }
     if (ev) cudaEventRecord(ev[3], st);
     // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
-    // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax)
+    // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax
+    // in 2D, 2 x 19 in 3D)
     // arrays above 64 KB go to the colour's global scratch (read through L1 / L2) so that wide fills
     // neither fail nor cut the number of resident blocks
-    size_t csmem = (size_t)(smax_bound + 8 * L.RC + 10 * L.nmax) * sizeof(double);
+    size_t csmem = (size_t)(smax_bound + 8 * L.RC + (L.dim == 3 ? 38 : 10) * L.nmax) * sizeof(double);
     const int gscr = (csmem > (size_t)64 * 1024 || !L.Cws) ? 1 : 0;
     if (gscr && !L.Cws) {
         k_set_flag<<<1, 1, 0, st>>>(L.status, DEV_ERR_SIZE);   // no scratch was provided: refuse
         count_launches(1);
     } else if (df) {
-        k_compress<T, true><<<dim3(nboxes, 9), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
+        k_compress<T, true><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
     } else {
-        k_compress<T, false><<<dim3(nboxes, 9), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
+        k_compress<T, false><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
     }
     if (ev) cudaEventRecord(ev[4], st);
-    if (df) k_redirect<T, true><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, bl, colour);
-    else k_redirect<T, false><<<dim3(nboxes, 81), kThreads, 0, st>>>(L, bl, colour);
+    if (df) k_redirect<T, true><<<dim3(nboxes, npair), kThreads, 0, st>>>(L, bl, colour);
+    else k_redirect<T, false><<<dim3(nboxes, npair), kThreads, 0, st>>>(L, bl, colour);
     if (ev) cudaEventRecord(ev[5], st);
     count_launches(5);
 }
@@ -995,13 +1003,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
 template <typename T>
 __global__ void k_init_p2p_leaf(LevelView<T> L, const double* p2p0, const int64_t* p2p0_off) {
     const int b = blockIdx.x, d = blockIdx.y;
-    const int bx = b % L.side, by = b / L.side;
-    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
-    if (!in_grid(qx, qy, L.side)) return;
-    const int q = qx + L.side * qy;
+    const Cell cq = cell_dir(cell_of(b, L.side, L.dim), d, L.dim);
+    if (!cell_in(cq, L.side)) return;
+    const int q = cell_index(cq, L.side);
     int ld;
     T* dst = block_at(L, b, q, ld);
-    const double* src = p2p0 + p2p0_off[(int64_t)b * 9 + d];
+    const double* src = p2p0 + p2p0_off[(int64_t)b * L.nd + d];
     const int nb_ = L.n[b], nq = L.n[q];
     for (int t = threadIdx.x; t < nb_ * nq; t += blockDim.x) {
         int i = t / nq, j = t - i * nq;
@@ -1010,21 +1017,23 @@ __global__ void k_init_p2p_leaf(LevelView<T> L, const double* p2p0, const int64_
 }
 
 template <typename T>
-__global__ void k_init_p2p_parent(LevelView<T> L, LevelView<T> C, const int* xoff5) {
-    const int b = blockIdx.x, d = blockIdx.y / 16, ab = blockIdx.y % 16;
-    const int a = ab / 4, bb = ab % 4;
-    const int bx = b % L.side, by = b / L.side;
-    const int qx = bx + d % 3 - 1, qy = by + d / 3 - 1;
-    if (!in_grid(qx, qy, L.side)) return;
-    const int q = qx + L.side * qy;
-    const int ca = (2 * bx + (a & 1)) + C.side * (2 * by + (a >> 1));
-    const int db = (2 * qx + (bb & 1)) + C.side * (2 * qy + (bb >> 1));
+__global__ void k_init_p2p_parent(LevelView<T> L, LevelView<T> C, const int* xoff) {
+    // blockIdx.y = (direction, child a of b, child bb of q); 2^d children, 2^d + 1 offsets per box
+    const int nk = 1 << L.dim, nk2 = nk * nk;
+    const int b = blockIdx.x, d = blockIdx.y / nk2, ab = blockIdx.y % nk2;
+    const int a = ab / nk, bb = ab % nk;
+    const Cell cb = cell_of(b, L.side, L.dim);
+    const Cell cq = cell_dir(cb, d, L.dim);
+    if (!cell_in(cq, L.side)) return;
+    const int q = cell_index(cq, L.side);
+    const int ca = cell_index(child_cell(cb, a), C.side);
+    const int db = cell_index(child_cell(cq, bb), C.side);
     int lds;
     const T* src = block_at(C, ca, db, lds);
     if (!src) return;
     int ld;
     T* dst = block_at(L, b, q, ld);
-    const int ro = xoff5[b * 5 + a], co = xoff5[q * 5 + bb];
+    const int ro = xoff[b * (nk + 1) + a], co = xoff[q * (nk + 1) + bb];
     const int rr = C.r[ca], rc = C.r[db];
     for (int t = threadIdx.x; t < rr * rc; t += blockDim.x) {
         int i = t / rc, j = t - i * rc;
@@ -1035,16 +1044,16 @@ __global__ void k_init_p2p_parent(LevelView<T> L, LevelView<T> C, const int* xof
 template <typename T>
 __global__ void k_init_far(LevelView<T> L, const double* far0, const int* rank0, int r0) {
     const int b = blockIdx.x, j = blockIdx.y;
-    const int bx = b % L.side, by = b / L.side;
-    const int qx = 2 * (bx >> 1) - 2 + j % 6, qy = 2 * (by >> 1) - 2 + j / 6;
-    if (!in_grid(qx, qy, L.side)) return;
-    if (max(abs(qx - bx), abs(qy - by)) <= 1) return;
-    const int q = qx + L.side * qy;
-    const int64_t o = L.boff[(int64_t)b * 36 + j];
+    const Cell cb = cell_of(b, L.side, L.dim);
+    const Cell cq = region_cell(cb, j, L.dim);
+    if (!cell_in(cq, L.side)) return;
+    if (cheb_dist(cq, cb) <= 1) return;
+    const int q = cell_index(cq, L.side);
+    const int64_t o = L.boff[(int64_t)b * L.nreg + j];
     if (o < 0) return;
     T* dst = L.blk + o;
-    const int ld = L.bld[(int64_t)b * 36 + j];
-    const double* src = far0 + ((int64_t)b * 36 + j) * r0 * r0;
+    const int ld = L.bld[(int64_t)b * L.nreg + j];
+    const double* src = far0 + ((int64_t)b * L.nreg + j) * r0 * r0;
     const int rb = rank0[b], rq = rank0[q];
     for (int t = threadIdx.x; t < rb * rq; t += blockDim.x) {
         int i = t / rq, jj = t - i * rq;
@@ -1054,7 +1063,7 @@ __global__ void k_init_far(LevelView<T> L, const double* far0, const int* rank0,
 
 template <typename T>
 __global__ void k_init_w(LevelView<T> L, int is_leaf, const double* W0, const int64_t* w0_rowoff, int r0,
-                         const int* xoff5, const int* rank_child, int child_side) {
+                         const int* xoff, const int* rank_child, int child_side) {
     const int b = blockIdx.x;
     const int RC = L.RC;
     T* W = L.W + L.voff[b] * RC;
@@ -1067,12 +1076,13 @@ __global__ void k_init_w(LevelView<T> L, int is_leaf, const double* W0, const in
             W[(size_t)i * RC + j] = (T)src[(size_t)i * r0 + j];
         }
     } else {
-        const double* src = W0 + (int64_t)b * 4 * r0 * r0;
-        const int bx = b % L.side, by = b / L.side;
-        for (int c = 0; c < 4; ++c) {
-            const int cg = (2 * bx + (c & 1)) + child_side * (2 * by + (c >> 1));
+        const int nk = 1 << L.dim;
+        const double* src = W0 + (int64_t)b * nk * r0 * r0;
+        const Cell cb = cell_of(b, L.side, L.dim);
+        for (int c = 0; c < nk; ++c) {
+            const int cg = cell_index(child_cell(cb, c), child_side);
             const int rc = rank_child[cg];
-            const int ro = xoff5[b * 5 + c];
+            const int ro = xoff[b * (nk + 1) + c];
             for (int t = threadIdx.x; t < rc * rb; t += blockDim.x) {
                 int i = t / rb, j = t - i * rb;
                 W[(size_t)(ro + i) * RC + j] = (T)src[(size_t)(c * r0 + i) * r0 + j];
@@ -1083,16 +1093,17 @@ __global__ void k_init_w(LevelView<T> L, int is_leaf, const double* W0, const in
 
 template <typename T>
 void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, const int64_t* p2p0_off,
-                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff5,
+                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff,
                        const double* far0, const int* rank0, const int* rank0_child, const LevelView<T>* child,
                        cudaStream_t st) {
+    const int nk = 1 << L.dim;
     if (is_leaf) {
-        k_init_p2p_leaf<T><<<dim3(L.nb, 9), kThreads, 0, st>>>(L, p2p0, p2p0_off);
+        k_init_p2p_leaf<T><<<dim3(L.nb, L.nd), kThreads, 0, st>>>(L, p2p0, p2p0_off);
     } else {
-        k_init_p2p_parent<T><<<dim3(L.nb, 9 * 16), kThreads, 0, st>>>(L, *child, xoff5);
+        k_init_p2p_parent<T><<<dim3(L.nb, L.nd * nk * nk), kThreads, 0, st>>>(L, *child, xoff);
     }
-    k_init_far<T><<<dim3(L.nb, 36), kThreads, 0, st>>>(L, far0, rank0, r0);
-    k_init_w<T><<<L.nb, kThreads, 0, st>>>(L, is_leaf, W0, w0_rowoff, r0, xoff5, rank0_child,
+    k_init_far<T><<<dim3(L.nb, L.nreg), kThreads, 0, st>>>(L, far0, rank0, r0);
+    k_init_w<T><<<L.nb, kThreads, 0, st>>>(L, is_leaf, W0, w0_rowoff, r0, xoff, rank0_child,
                                            is_leaf ? 0 : child->side);
     count_launches(3);
 }
@@ -1597,16 +1608,15 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_fwd_upd(L
     IFMM_REPLAY_SMEM(T, GM)
     const int e = boxes[blockIdx.x];
     const int dp = blockIdx.y;
-    if (dp == 4) return;
-    const int ex = e % L.side, ey = e / L.side;
-    const int px = ex + dp % 3 - 1, py = ey + dp / 3 - 1;
-    if (!in_grid(px, py, L.side)) return;
-    const int p = px + L.side * py;
-    const bool Ep = colour_of(px, py) < colour;
+    if (dp == L.ctr) return;
+    const Cell cp = cell_dir(cell_of(e, L.side, L.dim), dp, L.dim);
+    if (!cell_in(cp, L.side)) return;
+    const int p = cell_index(cp, L.side);
+    const bool Ep = cell_colour(cp) < colour;
     const int wp = Ep ? L.r[p] : L.n[p];
     const int n = L.n[e];
     if (wp == 0) return;
-    const T* C = L.Cp + L.cpoff[(int64_t)e * 9 + dp];
+    const T* C = L.Cp + L.cpoff[(int64_t)e * L.nd + dp];
     const T* v = vx + L.voff[e] * nrhs;
     T* tgt = Ep ? vec_km1 + yoff[p] * nrhs : vec_k + L.voff[p] * nrhs;
     ReplayGemm<GM>::template run<T>(
@@ -1640,9 +1650,10 @@ void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, 
     const int tw = ReplayTile<T, 0>::M;   // output tile of the CTA GEMM
     const int tr = (nrhs + tw - 1) / tw;
     const int z1 = std::max(1, std::min(((smax + tw - 1) / tw) * tr, (608 + nboxes - 1) / nboxes));
-    const int z2 = std::max(1, std::min(((L.nmax + tw - 1) / tw) * tr, (608 + nboxes * 8 - 1) / (nboxes * 8)));
+    const int nn = L.nd - 1;   // neighbours other than e
+    const int z2 = std::max(1, std::min(((L.nmax + tw - 1) / tw) * tr, (608 + nboxes * nn - 1) / (nboxes * nn)));
     k_fwd_piv<T, 0><<<dim3(nboxes, 1, z1), kThreads, 0, st>>>(L, boxes, yoff, vec_k, vec_km1, vx, nrhs);
-    k_fwd_upd<T, 0><<<dim3(nboxes, 9, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
+    k_fwd_upd<T, 0><<<dim3(nboxes, L.nd, z2), kThreads, 0, st>>>(L, boxes, colour, yoff, vec_k, vec_km1, vx, nrhs);
 }
 
 // back substitution, first half: w = rhs_e - sum_q B_q u_q as one GEMM over the concatenated
@@ -1669,37 +1680,39 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_bwd_w(Lev
                                                                             int64_t pstride) {
     using Acc = typename AccOf<T>::type;
     IFMM_REPLAY_SMEM(T, GM)
-    __shared__ const T* sB[8];
-    __shared__ const T* sU[8];
-    __shared__ int sOff[9], sW[8];
+    // the neighbours other than e: 8 in 2D, 26 in 3D
+    __shared__ const T* sB[26];
+    __shared__ const T* sU[26];
+    __shared__ int sOff[27], sW[26];
     __shared__ int s_last;
     const int e = boxes[blockIdx.x];
-    const int ex = e % L.side, ey = e / L.side;
+    const Cell ce = cell_of(e, L.side, L.dim);
     const int n = L.n[e];
+    const int nn = L.nd - 1;
     const int tg = blockIdx.z % zt, kz = blockIdx.z / zt;
     if (threadIdx.x == 0) {
         int cnt_ = 0, off = 0;
-        for (int d = 0; d < 9; ++d) {
-            if (d == 4) continue;
-            const int qx = ex + d % 3 - 1, qy = ey + d / 3 - 1;
-            if (!in_grid(qx, qy, L.side)) continue;
-            const int q = qx + L.side * qy;
-            const bool Eq = colour_of(qx, qy) < colour;
+        for (int d = 0; d < L.nd; ++d) {
+            if (d == L.ctr) continue;
+            const Cell cq = cell_dir(ce, d, L.dim);
+            if (!cell_in(cq, L.side)) continue;
+            const int q = cell_index(cq, L.side);
+            const bool Eq = cell_colour(cq) < colour;
             const int wq = Eq ? L.r[q] : L.n[q];
-            sB[cnt_] = L.Bp + L.bpoff[(int64_t)e * 9 + d];
+            sB[cnt_] = L.Bp + L.bpoff[(int64_t)e * L.nd + d];
             sU[cnt_] = Eq ? x_km1 + yoff[q] * nrhs : x_k + L.voff[q] * nrhs;
             sW[cnt_] = wq;
             sOff[cnt_] = off;
             off += wq;
             ++cnt_;
         }
-        for (int c = cnt_; c < 9; ++c) sOff[c] = off;
+        for (int c = cnt_; c <= nn; ++c) sOff[c] = off;
     }
     __syncthreads();
-    const int K = sOff[8];
+    const int K = sOff[nn];
     auto seg = [&](int k) {
         int c = 0;
-        while (c < 7 && k >= sOff[c + 1]) ++c;
+        while (c < nn - 1 && k >= sOff[c + 1]) ++c;
         return c;
     };
     auto la = [&](int i, int k) {

@@ -58,43 +58,88 @@ struct SlabSet {
     const int64_t* eoff;   // [nb * kSlabRecs] offset of its row exponents
 };
 
+// Geometry of one level of the uniform tree (Section 4.2), in d = 2 (quadtree) or d = 3 (octree,
+// the paper's extension to three dimensions). Box b sits at grid cell (b mod s, (b / s) mod s,
+// b / s^2) (z = 0 in 2D). Its neighbour in direction dq (0 <= dq < 3^d) is the cell displaced by
+// (dq mod 3 - 1, (dq / 3) mod 3 - 1, dq / 9 - 1); direction 3^d / 2 (4 or 13) is the box itself,
+// and a lower direction index means a lower grid index. The 6^d region of a box p is made of the
+// children of its parent's neighbours: every neighbour and every interaction-list box of p is in it.
+// Colour (reading R1): (x mod 3) + 3 (y mod 3) + 9 (z mod 3), 3^d colours.
+struct Cell { int x, y, z; };
+#if defined(__CUDACC__)
+#define IFMM_HD __host__ __device__ __forceinline__
+#else
+#define IFMM_HD inline
+#endif
+IFMM_HD Cell cell_of(int b, int side, int dim) {
+    return Cell{b % side, (b / side) % side, dim == 3 ? b / (side * side) : 0};
+}
+IFMM_HD int cell_index(Cell c, int side) { return c.x + side * (c.y + side * c.z); }
+IFMM_HD bool cell_in(Cell c, int side) {
+    return c.x >= 0 && c.y >= 0 && c.z >= 0 && c.x < side && c.y < side && c.z < side;
+}
+IFMM_HD Cell cell_dir(Cell c, int dq, int dim) {
+    return Cell{c.x + dq % 3 - 1, c.y + (dq / 3) % 3 - 1, dim == 3 ? c.z + dq / 9 - 1 : c.z};
+}
+IFMM_HD int dir_index(Cell from, Cell to, int dim) {
+    return (to.x - from.x + 1) + 3 * (to.y - from.y + 1) + (dim == 3 ? 9 * (to.z - from.z + 1) : 0);
+}
+IFMM_HD int cheb_dist(Cell a, Cell b) {
+    const int dx = a.x > b.x ? a.x - b.x : b.x - a.x, dy = a.y > b.y ? a.y - b.y : b.y - a.y;
+    const int dz = a.z > b.z ? a.z - b.z : b.z - a.z;
+    return dx > dy ? (dx > dz ? dx : dz) : (dy > dz ? dy : dz);
+}
+IFMM_HD int cell_colour(Cell c) { return (c.x % 3) + 3 * (c.y % 3) + 9 * (c.z % 3); }
+IFMM_HD int region_index(Cell p, Cell q, int dim) {
+    return (q.x - 2 * (p.x >> 1) + 2) + 6 * (q.y - 2 * (p.y >> 1) + 2) + (dim == 3 ? 36 * (q.z - 2 * (p.z >> 1) + 2) : 0);
+}
+IFMM_HD Cell region_cell(Cell p, int j, int dim) {
+    return Cell{2 * (p.x >> 1) - 2 + j % 6, 2 * (p.y >> 1) - 2 + (j / 6) % 6, dim == 3 ? 2 * (p.z >> 1) - 2 + j / 36 : p.z};
+}
+IFMM_HD int ndirs(int dim) { return dim == 3 ? 27 : 9; }
+IFMM_HD int nregion(int dim) { return dim == 3 ? 216 : 36; }
+IFMM_HD int ncolours(int dim) { return dim == 3 ? 27 : 9; }
+// child c = a + 2 b (+ 4 e) of a box: cell (2 x + a, 2 y + b, 2 z + e)
+IFMM_HD Cell child_cell(Cell c, int ch) { return Cell{2 * c.x + (ch & 1), 2 * c.y + ((ch >> 1) & 1), 2 * c.z + ((ch >> 2) & 1)}; }
+
 // Device view of one tree level during elimination (Algorithm 1) and replay (Algorithm 2).
 // Box b of level k sits at grid position (b % side, b / side). Its particle unknowns x_b number
 // n[b]; its multipoles y_b and locals z_b number r[b] (the rank, grows by compression).
 //
-// blk: for every box p and every box q of the 6 x 6 region made of the children of p's parent's
-// neighbours (index region36), the block between the active equation of p and the active unknown
-// of q (Algorithm 1's P2P, P2L, M2P or M2L by elimination status) for neighbours, the M2L block
-// for interaction-list boxes. Offsets boff[p*36 + j] (-1: no block), leading dimension bld.
+// blk: for every box p and every box q of p's 6^d region (region_index), the block between the
+// active equation of p and the active unknown of q (Algorithm 1's P2P, P2L, M2P or M2L by
+// elimination status) for neighbours, the M2L block for interaction-list boxes. Offsets
+// boff[p * nreg + j] (-1: no block), leading dimension bld.
 template <typename T>
 struct LevelView {
     int k, side, nb, RC;       // level, boxes per side, boxes, rank cap of the level
+    int dim, nd, ctr, nreg;    // dimension, 3^d directions, the box's own direction, 6^d region
     int nmax;                  // largest n at the level (sizes the tile split of big blocks)
     const int* n;              // [nb] particle count (leaf) or sum of the children's ranks
     int* r;                    // [nb] rank
     const int64_t* voff;       // [nb+1] prefix of n: rows of box b in level vectors and in W
-    const int64_t* boff;       // [nb*36]
-    const int* bld;            // [nb*36]
+    const int64_t* boff;       // [nb * nreg]
+    const int* bld;            // [nb * nreg]
     T* blk;
     T* W;                      // (sum n) x RC: L2P_bb = W rows voff[b].., P2M_bb = its transpose
     // factors kept for the solve
     const int64_t* pioff;      // [nb] inverse pivot block, s x s with leading dimension pild
     const int* pild;
     T* Pi;
-    const int64_t* cpoff;      // [nb*9] C panel of neighbour direction d: rows of the neighbour
+    const int64_t* cpoff;      // [nb * nd] C panel of neighbour direction d: rows of the neighbour
     T* Cp;                     //        at column x_b (w x n_b, leading dimension n_b)
-    const int64_t* bpoff;      // [nb*9] B panel: row P2P_b at the neighbour's column (n_b x w,
+    const int64_t* bpoff;      // [nb * nd] B panel: row P2P_b at the neighbour's column (n_b x w,
     T* Bp;                     //        leading dimension w)
     // per-colour scratch (offsets restart at every colour)
     const int64_t* xsoff;      // [nb] X = Pi [B; 0] for every column block, s x xsld
     const int* xsld;
     T* Xs;
-    const int64_t* fsoff;      // [nb*81] well-separated fill of ordered pair (dp, dq)
+    const int64_t* fsoff;      // [nb * nd * nd] well-separated fill of ordered pair (dp, dq)
     T* Fs;
     T* Fs2;                    // same layout: intermediate of the redirect
-    const int64_t* rsoff;      // [nb*9] residual of the fill being compressed
+    const int64_t* rsoff;      // [nb * nd] residual of the fill being compressed
     T* Rs;
-    const int64_t* cwsoff;     // [nb*9] the compression's FP64 work arrays (basis vector, coefficients,
+    const int64_t* cwsoff;     // [nb * nd] the compression's FP64 work arrays (basis vector, coefficients,
     double* Cws;               //        column norms) when they do not fit in shared memory
     double* pws;               // FP64 pivot workspace for blocks too large for shared memory
     const int64_t* psoff;      // [nb]
@@ -154,7 +199,7 @@ void launch_backward_colour(const LevelView<T>& L, const int* boxes, int nboxes,
                             int* cnt, int cnt_cap, cudaStream_t st);
 template <typename T>
 void launch_init_level(const LevelView<T>& L, int is_leaf, const double* p2p0, const int64_t* p2p0_off,
-                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoff5,
+                       const double* W0, const int64_t* w0_rowoff, int r0, const int* xoffs,
                        const double* far0, const int* rank0, const int* rank0_child, const LevelView<T>* child,
                        cudaStream_t st);
 template <typename T>
@@ -179,42 +224,44 @@ struct BuildArgs {
     int64_t N;
     int depth, p, r0, kernel;
     double kparam0, diag, x0, y0, L;
+    int dim;       // 2 or 3
+    double z0;     // 3D: lower z of the root cube
 };
-void launch_leaf_keys(const double* pts, int64_t N, int depth, double x0, double y0, double L,
+void launch_leaf_keys(const double* pts, int64_t N, int depth, int dim, double x0, double y0, double z0, double L,
                       unsigned long long* keys, int64_t npad, int* status, cudaStream_t st);
 void launch_bitonic_sort(unsigned long long* keys, int64_t npad, cudaStream_t st);
-void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int64_t* perm,
-                           double* px, double* py, int* leaf_count, int depth, cudaStream_t st);
-void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
-                       const int* leaf_count, const double* cheb, double* W0, double* Rt, int* rank0,
-                       int max_n, const double* U, const int* rsvd, cudaStream_t st);
+void launch_scatter_sorted(const unsigned long long* keys, const double* pts, int64_t N, int dim, int64_t* perm,
+                           double* px, double* py, double* pz, int* leaf_count, int depth, cudaStream_t st);
+void launch_leaf_basis(const BuildArgs& a, const double* px, const double* py, const double* pz,
+                       const int64_t* leaf_start, const int* leaf_count, const double* cheb, double* W0, double* Rt,
+                       int* rank0, int max_n, const double* U, const int* rsvd, cudaStream_t st);
 void launch_svd_level(const BuildArgs& a, int k, double svd_eps, const double* cheb, const double* Tc,
                       const double* Up, const double* sp, const int* rp, double* U, double* sig, int* rk,
                       double* scratch, cudaStream_t st);
-size_t svd_scratch_doubles(int r0);
+size_t svd_scratch_doubles(int r0, int dim);
 void launch_parent_basis(const BuildArgs& a, int k, const double* Rt_child, const int* rank_child,
                          const double* Tc, double* W0, double* Rt, int* rank0, const double* U, const int* rsvd,
                          cudaStream_t st);
 void launch_m2l_build(const BuildArgs& a, int k, const double* cheb, const double* Rt, double* far0,
                       cudaStream_t st);
-void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const int64_t* leaf_start,
-                      const int* leaf_count, const int64_t* p2p_off, double* p2p, double* sA_bits,
-                      cudaStream_t st);
-// FMM matvec pieces, element type T = double (residuals) or dfl (inner Krylov steps)
+void launch_p2p_build(const BuildArgs& a, const double* px, const double* py, const double* pz,
+                      const int64_t* leaf_start, const int* leaf_count, const int64_t* p2p_off, double* p2p,
+                      double* sA_bits, cudaStream_t st);
+// FMM matvec pieces, element type T = double (residuals) or dfl (inner Krylov steps); dim = 2 or 3
 template <typename T>
 void launch_mv_permute_in(const double* x, int64_t ld, int64_t N, int nrhs, const int64_t* perm, T* xt,
                           cudaStream_t st);
 template <typename T>
-void launch_mv_leaf_up(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+void launch_mv_leaf_up(int dim, int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
                        const T* xt, T* y, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_mv_up(int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st);
+void launch_mv_up(int dim, int k, const T* W0, int r0, const T* ychild, T* y, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_mv_m2l(int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st);
+void launch_mv_m2l(int dim, int k, const T* far0, int r0, const T* y, T* z, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_mv_down(int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st);
+void launch_mv_down(int dim, int k, const T* W0, int r0, const T* z, T* zchild, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_mv_leaf_down(int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
+void launch_mv_leaf_down(int dim, int depth, const T* W0, const int64_t* leaf_start, const int* leaf_count, int r0,
                          const T* z, const T* xt, const int64_t* p2p_off, const T* p2p, T* out, int nrhs,
                          cudaStream_t st);
 template <typename T>

@@ -32,7 +32,7 @@ class ifmm_params(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
                 ("refine_restart", ctypes.c_int),
                 ("refine_inner", ctypes.c_double),
-                ("leaf_max", ctypes.c_int), ("tc_products", ctypes.c_int), ("svd_eps", ctypes.c_double)]
+                ("leaf_max", ctypes.c_int), ("tc_products", ctypes.c_int), ("svd_eps", ctypes.c_double), ("z0", ctypes.c_double)]
 
 
 class ifmm_stats(ctypes.Structure):
@@ -136,7 +136,8 @@ def _check(h, status: int, allow=()):
 # ---- C-ABI names ---------------------------------------------------------------------------
 
 def ifmm_build(points: np.ndarray, kernel: int, params: ifmm_params, stream: int = 0):
-    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+    """points: N x dim (params.dim = 2 or 3)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, params.dim)
     h = ctypes.c_void_p()
     st = load().ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), pts.shape[0], kernel, ctypes.byref(params),
                            ctypes.c_void_p(stream), ctypes.byref(h))
@@ -215,8 +216,8 @@ def ifmm_tc_dgemm(a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: i
     return _check(None, load().ifmm_tc_dgemm(a_ptr, lda, b_ptr, ldb, c_ptr, ldc, M, N, K, stream))
 
 
-def ifmm_get_ranks(h, level: int) -> np.ndarray:
-    out = np.zeros(4 ** level, dtype=np.int32)
+def ifmm_get_ranks(h, level: int, dim: int = 2) -> np.ndarray:
+    out = np.zeros(1 << (dim * level), dtype=np.int32)
     _check(h, load().ifmm_get_ranks(h, level, out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
@@ -255,7 +256,7 @@ class IFMM:
         self._torch = torch
         self.params = params if params is not None else default_params()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.N = int(np.asarray(points).reshape(-1, 2).shape[0])
+        self.N = int(np.asarray(points).reshape(-1, self.params.dim).shape[0])
         self.h = ifmm_build(points, kernel, self.params, self.stream.cuda_stream)
 
     def close(self):
@@ -308,7 +309,7 @@ class IFMM:
         return x.reshape(np.asarray(b).shape)
 
     def ranks(self, level: int) -> np.ndarray:
-        return ifmm_get_ranks(self.h, level)
+        return ifmm_get_ranks(self.h, level, self.params.dim)
 
     def stats(self) -> dict:
         return ifmm_get_stats(self.h)

@@ -37,8 +37,9 @@ def test_default_params_and_struct_layout():
     pts = np.zeros((4, 2))
     bad = ifmm.default_params(depth=1)
     assert lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), 4, 0, ctypes.byref(bad), None, ctypes.byref(h)) == 1
-    bad = ifmm.default_params(dim=3)
+    bad = ifmm.default_params(dim=4)
     assert lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), 4, 0, ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    assert p.svd_eps == 0.0 and p.z0 == 0.0
     pts[0, 0] = float("nan")
     ok = ifmm.default_params()
     assert lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), 4, 0, ctypes.byref(ok), None, ctypes.byref(h)) == 1
@@ -53,13 +54,17 @@ def test_default_params_and_struct_layout():
     (dict(eps=-1e-6), 0, 4), (dict(diag=float("inf")), 0, 4), (dict(precision=3), 0, 4),
     (dict(tau_ref=3), 0, 4), (dict(r_cap=8), 0, 4), (dict(refine_restart=201), 0, 4),
     (dict(refine_restart=-1), 0, 4), (dict(tc_products=3), 0, 4), (dict(tc_products=-1), 0, 4), (dict(), 0, 0),
+    (dict(svd_eps=-1e-3), 0, 4), (dict(svd_eps=1.0), 0, 4), (dict(dim=1), 0, 4),
+    # octree limits: p^3 <= 64, an explicit depth <= 6, no tensor-core replay
+    (dict(dim=3, cheb_p=5), 0, 4), (dict(dim=3, depth=0), 0, 4), (dict(dim=3, depth=7), 0, 4),
+    (dict(dim=3, tc_products=1), 0, 4), (dict(dim=3, z0=float("nan")), 0, 4),
 ])
 def test_build_rejects_each_out_of_range_argument_on_the_host(change, kernel, n):
     """Every range ifmm.h states for ifmm_build is checked before any device call: the call returns
     IFMM_ERR_INVALID_ARG and leaves the output handle NULL."""
     import numpy as np
     lib = ifmm.load()
-    pts = np.full((max(n, 1), 2), 0.5)
+    pts = np.full((max(n, 1), 3), 0.5)   # room for three coordinates per point
     prm = ifmm.default_params(**change)
     h = ctypes.c_void_p(1)
     st = lib.ifmm_build(pts.ctypes.data_as(ctypes.c_void_p), n, kernel, ctypes.byref(prm), None, ctypes.byref(h))

@@ -31,7 +31,7 @@ def _loss_and_grads(adj, pts, b, xs, ell, sig2, **prm):
     x = adj.solve_exp(pts, bt, ell_t, sig_t, **prm)
     loss = ((x - xs_t) ** 2).sum()
     loss.backward()
-    return float(loss), bt.grad.cpu().numpy(), float(ell_t.grad), float(sig_t.grad)
+    return float(loss.detach()), bt.grad.cpu().numpy(), float(ell_t.grad), float(sig_t.grad)
 
 
 def _loss(adj, pts, b, xs, ell, sig2, **prm):
