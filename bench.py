@@ -381,18 +381,19 @@ ARITH = {
 }
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel, from a bounded
-# ncu capture (one kernel, two launches, 65,536 points; profiles/), scaled to the bench's N by the
-# kernel's algorithmic flops per launch; keyed by the SHA-256 of the kernel sources it was taken on,
-# so that it reads null once a source differs. Empty: no capture of the current sources.
+# DRAM traffic of a kernel (dram__bytes_read.sum + dram__bytes_write.sum) per eliminated box, from a
+# bounded ncu capture of one leaf-level launch at 65,536 points (profiles/), scaled to a launch of
+# the bench by the boxes it eliminates on average (the units of the launch; a leaf box of 64 points
+# costs the same at any N); keyed by the SHA-256 of the kernel sources it was taken on, so that it
+# reads null once a source differs. Empty: no capture of the current sources.
 TRAFFIC = {}
 TRAFFIC_SRC = {}
 
 
-def _traffic(precision, n, name, flops_pl):
+def _traffic(precision, name, boxes_per_launch):
     import hashlib
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1407_1572_gb300", "csrc")
-    if not TRAFFIC_SRC:
+    if not TRAFFIC_SRC or not boxes_per_launch:
         return None
     for f, h in TRAFFIC_SRC.items():
         with open(os.path.join(csrc, f), "rb") as fh:
@@ -401,10 +402,10 @@ def _traffic(precision, n, name, flops_pl):
     rec = TRAFFIC.get((precision, name))
     if not rec:
         return None
-    return rec["bytes_per_launch"] * flops_pl / rec["flops_per_launch"]
+    return rec["bytes_per_box"] * boxes_per_launch
 
 
-def _kernel_roofline(stats, precision, i, pipes, n=0):
+def _kernel_roofline(stats, precision, i, pipes, boxes=0):
     from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
     ms, launches, flops = stats["kernel_ms"], stats["kernel_launches"], stats["kernel_flops"]
     name = FACTOR_KERNELS[i]
@@ -433,7 +434,7 @@ def _kernel_roofline(stats, precision, i, pipes, n=0):
     else:
         peak, src = pipes["fp64"], f"FP64 pipe, {pipes['source']}"
     ach = flops_pl / t / 1e12
-    traffic = _traffic(precision, n, name, flops_pl)
+    traffic = _traffic(precision, name, boxes / nl if boxes else 0)
     out = {"kernel": name, "arith": arith, "share_of_factor_kernels": ms[i] / max(sum(ms), 1e-30),
            "avg_launch_ms": ms[i] / nl, "launches": launches[i], "flops_per_launch": flops_pl,
            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -444,13 +445,14 @@ def _kernel_roofline(stats, precision, i, pipes, n=0):
     return out
 
 
-def roofline(stats, precision, peaks, peak_kind, pipes, n=0):
+def roofline(stats, precision, peaks, peak_kind, pipes, boxes=0):
     """Dominant factor kernel (CUDA-event time); `schur` adds the Schur-update kernel, the dense
-    contraction of the elimination, against the peak of its own arithmetic."""
+    contraction of the elimination, against the peak of its own arithmetic. boxes: the boxes one
+    factorisation eliminates (all levels), for the traffic per launch."""
     ms = stats["kernel_ms"]
     top = max(range(5), key=lambda i: ms[i])
-    out = _kernel_roofline(stats, precision, top, pipes, n)
-    out["schur"] = _kernel_roofline(stats, precision, 2, pipes, n)
+    out = _kernel_roofline(stats, precision, top, pipes, boxes)
+    out["schur"] = _kernel_roofline(stats, precision, 2, pipes, boxes)
     # the Schur step's algorithmic bytes, for the intensity against HBM
     nl = max(stats["kernel_launches"][2], 1)
     bytes_pl = stats["schur_bytes"] / nl
@@ -662,7 +664,8 @@ def run_gpu(args):
     value = whole_job_value(world, N, ms)
     launches_per_step = st["launches_factor"] + st["launches_solve"]
     peaks, peak_kind = load_peaks()
-    rf = roofline(st, precision, peaks, peak_kind, pipe_peaks(pipes_measured), N)
+    boxes = sum(4 ** k for k in range(2, w["depth"] + 1))   # uniform points: no empty box
+    rf = roofline(st, precision, peaks, peak_kind, pipe_peaks(pipes_measured), boxes)
 
     # end to end through the C ABI with host buffers in pinned memory (copies inside the timed region)
     b_pin = torch.empty((nrhs, N), dtype=torch.float64, pin_memory=True)

@@ -35,7 +35,7 @@ def test_pipe_peaks_derive_the_double_float_rate_from_the_fp32_rate():
 
 
 def test_roofline_picks_the_dominant_kernel_and_divides_by_its_own_peak():
-    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", PIPES, n=4096)
+    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", PIPES)
     assert rf["kernel"] == "k_compress"
     t = 250.0 / 54 / 1000.0
     assert math.isclose(rf["achieved"], 1.6e11 / 54 / t / 1e12, rel_tol=1e-12)
@@ -57,25 +57,28 @@ def test_roofline_picks_the_dominant_kernel_and_divides_by_its_own_peak():
 
 
 def test_roofline_in_fp64_uses_the_fp64_peak_everywhere():
-    rf = bench.roofline(_stats(), "fp64", PEAKS, "measured", PIPES, n=4096)
+    rf = bench.roofline(_stats(), "fp64", PEAKS, "measured", PIPES)
     assert rf["peak"] == PIPES["fp64"] and rf["schur"]["peak"] == PIPES["fp64"]
     # the Schur update's ridge lies above the FP64 peak, so the attainable roofline is that peak
     assert rf["schur"]["attainable"] == PIPES["fp64"]
 
 
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
-    """A bounded capture's DRAM bytes per launch, scaled by the kernel's flops per launch, while the
-    kernel sources hash as they did when it was taken; null once a source differs."""
+    """A bounded capture's DRAM bytes per eliminated box, times the boxes of an average launch, while
+    the kernel sources hash as they did when it was taken; null once a source differs."""
     csrc = os.path.join(ROOT, "paper_1407_1572_gb300", "csrc")
     files = ["ifmm_factor.cu", "ifmm_common.cuh"]
     now = {f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() for f in files}
     monkeypatch.setattr(bench, "TRAFFIC_SRC", now)
-    monkeypatch.setattr(bench, "TRAFFIC", {("mixed_solve", "k_compress"): {"bytes_per_launch": 2.0e8,
-                                                                           "flops_per_launch": 1.0e9}})
-    assert bench._traffic("mixed_solve", 0, "k_compress", 4.0e9) == 8.0e8
-    assert bench._traffic("fp64", 0, "k_compress", 4.0e9) is None
+    monkeypatch.setattr(bench, "TRAFFIC", {("mixed_solve", "k_compress"): {"bytes_per_box": 3.0e6}})
+    assert bench._traffic("mixed_solve", "k_compress", 400.0) == 1.2e9
+    assert bench._traffic("fp64", "k_compress", 400.0) is None
+    # through the roofline: 54 launches over 21,840 boxes
+    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", PIPES, boxes=21840)
+    assert math.isclose(rf["traffic"], 3.0e6 * 21840 / 54)
+    assert math.isclose(rf["achieved_dram_gbs"], rf["traffic"] / (250.0 / 54 / 1000.0) / 1e9)
     monkeypatch.setattr(bench, "TRAFFIC_SRC", {f: "0" * 64 for f in files})
-    assert bench._traffic("mixed_solve", 0, "k_compress", 4.0e9) is None
+    assert bench._traffic("mixed_solve", "k_compress", 400.0) is None
 
 
 def test_replica_seeds_differ_per_rank_and_the_value_counts_every_rank():
