@@ -468,6 +468,58 @@ def roofline(stats, precision, peaks, peak_kind, pipes, boxes=0):
     return out
 
 
+# the octree workload (d = 3): points uniform in the unit cube, 64 per leaf, 1/r + sqrt(N) I (the 3D
+# Laplace kernel), Chebyshev 3 x 3 x 3, eps 1e-6, refined to an estimated error of 1e-7 (2^15 points:
+# the 2^18-point octree takes 44 s per step, too long for a bench leg)
+OCTREE = dict(N=1 << 15, depth=3, cheb_p=3, eps=1e-6, nrhs=8, seed=1413, refine_tol=1e-7, steps=3)
+
+
+def run_octree(precision: str):
+    """One warm-up and OCTREE['steps'] timed factor + solve steps of the octree workload on this GPU
+    (CUDA events on the solver's stream), error against the manufactured solution."""
+    import torch
+
+    from paper_1407_1572_gb300 import ifmm, inputs
+
+    o = OCTREE
+    N, nrhs = o["N"], o["nrhs"]
+    stream = torch.cuda.current_stream()
+    pts = inputs.uniform(o["seed"], 3 * N).reshape(N, 3)
+    prm = ifmm.default_params(dim=3, depth=o["depth"], cheb_p=o["cheb_p"], eps=o["eps"], diag=math.sqrt(N),
+                              precision=precision_code(ifmm, precision), tau_ref=1, refine_tol=o["refine_tol"],
+                              refine_maxit=200, refine_restart=60)
+    g = ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm, stream)
+    xs = torch.from_numpy(inputs.rhs(o["seed"] + 1, N, nrhs).T.copy()).cuda()
+    b = torch.empty_like(xs)
+    ifmm.ifmm_matvec(g.h, xs.data_ptr(), b.data_ptr(), nrhs, N)
+    x = torch.empty_like(xs)
+
+    def step():
+        ifmm.ifmm_factor(g.h, allow_overflow=True)
+        ifmm.ifmm_solve(g.h, b.data_ptr(), x.data_ptr(), nrhs, N, allow_noconv=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(o["steps"]):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / o["steps"]
+    st = ifmm.ifmm_get_stats(g.h)
+    err = float(((x - xs).norm(dim=1) / xs.norm(dim=1)).max().item())
+    g.close()
+    return {"value": N / (ms / 1000.0), "unit": "unknowns/s", "ms_per_step": ms, "steps": o["steps"], "warmup": 1,
+            "err": err, "meets_err_1e-6": err <= 1e-6, "precision": PRECISION_DESC[precision],
+            "t_factor_ms": st["t_factor_ms"], "t_solve_ms": st["t_solve_ms"], "refine_iters": st["refine_iters"],
+            "max_rank": st["max_rank"], "device_gb": st["device_bytes"] / 1e9,
+            "kernel_ms": dict(zip(ifmm.FACTOR_KERNELS, st["kernel_ms"])),
+            "workload": (f"octree: {N} points uniform in the unit cube, depth {o['depth']} (64 per leaf), "
+                         f"Chebyshev {o['cheb_p']}^3, 1/r + sqrt(N) I, eps {o['eps']:g}, {nrhs} RHS, "
+                         f"refined to {o['refine_tol']:g}")}
+
+
 BATCH = dict(count=256, seed=1409, nmin=2048, nmax=32768, rhs_min=1, rhs_max=16, cheb_p=4, eps=1e-6, leaf_max=64,
              refine_tol=1e-7, wave=64, workers=48)
 
@@ -713,6 +765,12 @@ def run_gpu(args):
             so.close()
         solver = None
 
+    if args.octree and rank == 0:
+        if solver is not None:
+            solver.close()
+            solver = None
+        extra["octree_gpu"] = run_octree(precision)
+
     if args.batch:   # every rank runs its share of the independent systems
         if solver is not None:
             solver.close()
@@ -775,6 +833,8 @@ def main():
     ap.add_argument("--batch", dest="batch", action="store_true", default=True,
                     help="also time the batched workload of 256 uneven systems (default)")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-octree", dest="octree", action="store_false", default=True,
+                    help="skip the 3D (octree) workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
