@@ -565,12 +565,13 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // reference norm: largest column norm of S_q
+    // reference norm: largest column norm of S_q, one column per thread (consecutive threads read
+    // consecutive columns of a row: coalesced; a warp per column reads 32 rows m apart)
     double mloc = 0.0;
-    for (int j = warp; j < m; j += nw) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
         double s = 0.0;
-        for (int i = lane; i < nq; i += 32) { double v = (double)R[(size_t)i * m + j]; s += v * v; }
-        s = warp_sum(s);
+#pragma unroll 4
+        for (int i = 0; i < nq; ++i) { const double v = (double)R[(size_t)i * m + j]; s = fma(v, v, s); }
         mloc = fmax(mloc, sqrt(s));
     }
     const double smax = block_max(mloc, vred);
@@ -643,6 +644,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         const int j = gid + rd * ngr;
         E sq = E(0);
         if (j < m)
+#pragma unroll 4
             for (int i = gl; i < nq; i += g) { const E v = Re[(size_t)i * m + j]; gs_fma(sq, v, v); }
         sq = group_sum(sq);
         if (j < m && gl == 0) nrm2[j] = gs_d(sq);
@@ -678,12 +680,14 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         for (int pass = 0; pass < 2; ++pass) {
             for (int t = threadIdx.x; t < rc; t += blockDim.x) {
                 double sc = 0.0;
+#pragma unroll 4
                 for (int i = 0; i < nq; ++i) sc += (double)W[(size_t)i * RC + t] * u[i];
                 coef[t] = sc;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < nq; i += blockDim.x) {
                 double acc = u[i];
+#pragma unroll 4
                 for (int t = 0; t < rc; ++t) acc -= (double)W[(size_t)i * RC + t] * coef[t];
                 u[i] = acc;
             }
@@ -713,10 +717,12 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
             const int j = gid + rd * ngr;
             E sp = E(0);
             if (j < m)
+#pragma unroll 4
                 for (int i = gl; i < nq; i += g) gs_fma(sp, ue[i], Re[(size_t)i * m + j]);
             sp = group_sum(sp);
             E sq = E(0);
             if (j < m)
+#pragma unroll 4
                 for (int i = gl; i < nq; i += g) {
                     const E v = gs_axpy(Re[(size_t)i * m + j], sp, ue[i]);   // R_ij - sp u_i
                     Re[(size_t)i * m + j] = v;
