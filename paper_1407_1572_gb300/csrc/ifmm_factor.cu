@@ -507,6 +507,7 @@ IFMM_DEVINL dfl gs_axpy(dfl r, dfl s, dfl u) {
 // gscr: the FP64 work arrays live in the colour's global scratch (L.Cws) instead of shared memory
 // (wide fills, whose arrays exceed the shared-memory budget of the launch)
 constexpr int kMaxPartners = 19;
+constexpr int kGB = 4;   // column elements a thread of the Gram-Schmidt loads ahead
 template <typename T, bool DF>
 __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<T> bl, int colour, int gscr) {
     const LevelView<T>& L = bl.view(L0, blockIdx.x);
@@ -555,10 +556,38 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         int c0 = 0;
         for (int t = 0; t < np; ++t) {
             int dp = parts[t], wp = wps[t];
-            for (int u = threadIdx.x; u < nq * wp; u += blockDim.x) {
-                int i = u / wp, j = u - i * wp;
-                R[(size_t)i * m + c0 + j] = fill_at(L, e, dq, dp, nq, wp, i, j);                // F_qp
-                if (!half) R[(size_t)i * m + c0 + wp + j] = fill_at(L, e, dp, dq, wp, nq, j, i);  // F_pq^T
+            if (half) {
+                // F_qp is stored as is (dq < dp, nq x wp) or as its transpose F_pq (wp x nq); either
+                // way element u of the stored block is read in order (coalesced), four per thread
+                // before their stores so that the loads are in flight together
+                const bool direct = dq < dp;
+                const T* F = L.Fs + (direct ? fill_off(L, e, dq, dp) : fill_off(L, e, dp, dq));
+                const int tot = nq * wp;
+                constexpr int kB = 4;
+                for (int u0 = threadIdx.x; u0 < tot; u0 += kB * (int)blockDim.x) {
+                    T v[kB];
+                    int64_t dst[kB];
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) {
+                        const int u = u0 + k * (int)blockDim.x;
+                        dst[k] = -1;
+                        if (u < tot) {
+                            const int a = direct ? u / wp : u / nq, b = direct ? u - a * wp : u - a * nq;
+                            const int i = direct ? a : b, j = direct ? b : a;
+                            v[k] = F[u];
+                            dst[k] = (int64_t)i * m + c0 + j;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kB; ++k)
+                        if (dst[k] >= 0) R[dst[k]] = v[k];
+                }
+            } else {
+                for (int u = threadIdx.x; u < nq * wp; u += blockDim.x) {
+                    int i = u / wp, j = u - i * wp;
+                    R[(size_t)i * m + c0 + j] = fill_at(L, e, dq, dp, nq, wp, i, j);                // F_qp
+                    R[(size_t)i * m + c0 + wp + j] = fill_at(L, e, dp, dq, wp, nq, j, i);            // F_pq^T
+                }
             }
             c0 += (half ? 1 : 2) * wp;
         }
@@ -643,9 +672,17 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     for (int rd = 0; rd < rounds; ++rd) {
         const int j = gid + rd * ngr;
         E sq = E(0);
-        if (j < m)
-#pragma unroll 4
-            for (int i = gl; i < nq; i += g) { const E v = Re[(size_t)i * m + j]; gs_fma(sq, v, v); }
+        if (j < m) {
+            int i = gl;
+            for (; i + (kGB - 1) * g < nq; i += kGB * g) {
+                E x[kGB];
+#pragma unroll
+                for (int k = 0; k < kGB; ++k) x[k] = Re[(size_t)(i + k * g) * m + j];
+#pragma unroll
+                for (int k = 0; k < kGB; ++k) gs_fma(sq, x[k], x[k]);
+            }
+            for (; i < nq; i += g) { const E v = Re[(size_t)i * m + j]; gs_fma(sq, v, v); }
+        }
         sq = group_sum(sq);
         if (j < m && gl == 0) nrm2[j] = gs_d(sq);
     }
@@ -715,19 +752,41 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         // pass (one more multiply-add per element, no extra memory traffic)
         for (int rd = 0; rd < rounds; ++rd) {
             const int j = gid + rd * ngr;
+            // kGB elements of the column loaded together before they are used (stores to R would
+            // otherwise keep the compiler from hoisting the next loads); same order of operations
             E sp = E(0);
-            if (j < m)
-#pragma unroll 4
-                for (int i = gl; i < nq; i += g) gs_fma(sp, ue[i], Re[(size_t)i * m + j]);
+            if (j < m) {
+                int i = gl;
+                for (; i + (kGB - 1) * g < nq; i += kGB * g) {
+                    E x[kGB];
+#pragma unroll
+                    for (int k = 0; k < kGB; ++k) x[k] = Re[(size_t)(i + k * g) * m + j];
+#pragma unroll
+                    for (int k = 0; k < kGB; ++k) gs_fma(sp, ue[i + k * g], x[k]);
+                }
+                for (; i < nq; i += g) gs_fma(sp, ue[i], Re[(size_t)i * m + j]);
+            }
             sp = group_sum(sp);
             E sq = E(0);
-            if (j < m)
-#pragma unroll 4
-                for (int i = gl; i < nq; i += g) {
-                    const E v = gs_axpy(Re[(size_t)i * m + j], sp, ue[i]);   // R_ij - sp u_i
+            if (j < m) {
+                int i = gl;
+                for (; i + (kGB - 1) * g < nq; i += kGB * g) {
+                    E x[kGB];
+#pragma unroll
+                    for (int k = 0; k < kGB; ++k) x[k] = Re[(size_t)(i + k * g) * m + j];
+#pragma unroll
+                    for (int k = 0; k < kGB; ++k) {
+                        const E v = gs_axpy(x[k], sp, ue[i + k * g]);   // R_ij - sp u_i
+                        Re[(size_t)(i + k * g) * m + j] = v;
+                        gs_fma(sq, v, v);
+                    }
+                }
+                for (; i < nq; i += g) {
+                    const E v = gs_axpy(Re[(size_t)i * m + j], sp, ue[i]);
                     Re[(size_t)i * m + j] = v;
                     gs_fma(sq, v, v);
                 }
+            }
             sq = group_sum(sq);
             if (j < m && gl == 0) nrm2[j] = gs_d(sq);
         }
