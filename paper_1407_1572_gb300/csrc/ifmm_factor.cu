@@ -1775,9 +1775,16 @@ __global__ void __launch_bounds__(GM == 2 ? tc::kThreads : kThreads) k_bwd_w(Lev
     }
     __syncthreads();
     const int K = sOff[nn];
+    // segment of column k: the number of segment starts sOff[1..nn-1] at or below k (sOff is
+    // nondecreasing); unrolled for the quadtree's 8 neighbours
     auto seg = [&](int k) {
         int c = 0;
-        while (c < nn - 1 && k >= sOff[c + 1]) ++c;
+        if (nn == 8) {
+#pragma unroll
+            for (int t = 1; t < 8; ++t) c += sOff[t] <= k ? 1 : 0;
+        } else {
+            for (int t = 1; t < nn; ++t) c += sOff[t] <= k ? 1 : 0;
+        }
         return c;
     };
     auto la = [&](int i, int k) {
