@@ -559,7 +559,9 @@ def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
     leaf <= 64 points, empty leaves kept), 1-16 right-hand sides each, 1/r + sqrt(N) I, rank 16,
     eps 1e-6, refined to 1e-7. Systems are built, factored (ifmm_factor_batch) and solved
     (ifmm_solve_batch) in waves of 64, half uniform and half blobs per wave, each system on its own
-    stream; one untimed warm-up wave of 16 first. Timed: the batched factor + solve calls. Over
+    stream; one untimed warm-up wave of 16 first. Timed: the batched factor + solve calls, in two
+    sweeps: with the fixed launch-split rule, then with the table ifmm_autotune builds (untimed) on
+    the first wave's systems; `value` is the tuned sweep's, the fixed rule's is reported beside it. Over
     several ranks every rank runs its share (partition_work on N x nrhs) and the job's time is the
     slowest rank's (strong scaling: the 256 systems are fixed)."""
     import torch
@@ -574,7 +576,7 @@ def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
     uni = [systems[i] for i in mine if i < half]
     blob = [systems[i] for i in mine if i >= half]
 
-    def wave(sy):
+    def wave(sy, tune=False):
         handles, xs_l, bs_l, xo_l = [], [], [], []
         for s in sy:
             n = s["points"].shape[0]
@@ -590,6 +592,10 @@ def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
             bs_l.append(b)
             xo_l.append(torch.empty_like(xs))
         torch.cuda.synchronize()
+        if tune:   # untimed: the autotuner's table for this wave's launches (ifmm_autotune)
+            t0 = time.perf_counter()
+            ifmm.ifmm_autotune([g.h for g in handles], workers=c["workers"])
+            tune_s.append(time.perf_counter() - t0)
         t1 = time.perf_counter()
         ifmm.ifmm_factor_batch([g.h for g in handles], workers=c["workers"], allow_overflow=True)
         t2 = time.perf_counter()
@@ -604,19 +610,32 @@ def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
             g.close()
         return t2 - t1, t3 - t2, err, depths
 
+    tune_s = []
+    ifmm.ifmm_autotune_clear()
     if uni or blob:
         wave(uni[:8] + blob[:8])
     if dist:
         dist.barrier()
-    tf = ts = err = 0.0
-    depths = []
     per = c["wave"] // 2
-    for w in range(max(-(-len(uni) // per), -(-len(blob) // per))):
-        f_, s_, e_, d_ = wave(uni[w * per:(w + 1) * per] + blob[w * per:(w + 1) * per])
-        tf += f_
-        ts += s_
-        err = max(err, e_)
-        depths += d_
+    nw = max(-(-len(uni) // per), -(-len(blob) // per))
+
+    def sweep(tuned):
+        tf = ts = err = 0.0
+        depths = []
+        for w in range(nw):
+            f_, s_, e_, d_ = wave(uni[w * per:(w + 1) * per] + blob[w * per:(w + 1) * per], tune=tuned and w == 0)
+            tf += f_
+            ts += s_
+            err = max(err, e_)
+            depths += d_
+        return tf, ts, err, depths
+
+    # the fixed launch rule, then the table the autotuner builds on the first wave (kept for the rest)
+    tf0, ts0, err0, _ = sweep(False)
+    tf, ts, err, depths = sweep(True)
+    table_size = ifmm.ifmm_autotune_size()
+    ifmm.ifmm_autotune_clear()
+    t0, tf0, ts0, err0, _, _ = aggregate_batched(tf0, ts0, err0, 0, 0, dist, "cuda")
     t, tf, ts, err, dmin, dmax = aggregate_batched(tf, ts, err, min(depths, default=99), max(depths, default=0),
                                                    dist, "cuda")
     n_tot = sum(s["points"].shape[0] for s in systems)
@@ -625,6 +644,10 @@ def run_batched(precision: str, rank: int = 0, world: int = 1, dist=None):
             "scaling": "strong", "rhs_columns_x_N": unk, "t_factor_s": tf, "t_solve_s": ts, "err": err,
             "meets_err_1e-6": err <= 1e-6, "depth_range": [int(dmin), int(dmax)], "precision": PRECISION_DESC[precision],
             "workers": c["workers"], "timing": "host clock around the blocking batched calls (device synchronised)",
+            "autotune": {"table_entries": table_size, "tuning_s": sum(tune_s),
+                         "value_fixed_rule": n_tot / t0, "t_factor_s_fixed_rule": tf0, "t_solve_s_fixed_rule": ts0,
+                         "err_fixed_rule": err0,
+                         "note": "value uses the autotuner's launch splits, tuned (untimed) on the first wave"},
             "workload": ("256 systems, N log-uniform in [2048, 32768], half uniform / half Gaussian blobs "
                          "(8 centres, sigma 0.05), automatic depth (leaf <= 64), 1-16 RHS, 1/r + sqrt(N) I, "
                          "rank 16, eps 1e-6, refined to 1e-7")}

@@ -210,6 +210,28 @@ ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* statu
 ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
                              const int64_t* ld, int workers, ifmm_status* status_out);
 
+/* Autotuner of the batched launches (no counterpart in the paper, which solves one system). The
+ * panel and Schur-update launches of a colour split each box's (panel) or each neighbour pair's
+ * (Schur) product over `split` thread blocks, each taking every split-th output tile. A
+ * process-wide table maps a bucket -- (kernel, double-float products or not, ceil(log2) of the
+ * level's largest block n, ceil(log2) of the launch's box count) -- to a split; a launch whose
+ * bucket has no entry uses the fixed rule. A split changes only which block computes which tile,
+ * so results are identical bit for bit whatever the table holds.
+ * ifmm_autotune factors the given systems with ifmm_factor_batch (one warm-up, then once per
+ * candidate split 1, 2, 4, 8, 16 for the panel and then the Schur launches), times every launch
+ * with CUDA events, enters the fastest split of each bucket in the table and factors the systems
+ * once more with it (they are left factored). Arguments and errors as ifmm_factor_batch; a
+ * failing factorisation ends the tuning with the table unchanged.
+ * ifmm_autotune_save / ifmm_autotune_load write / read the table as text (one bucket per line:
+ * kernel df log2_nmax log2_boxes split; '#' lines are comments); load replaces the table and
+ * rejects a malformed file (IFMM_ERR_INVALID_ARG, table unchanged). ifmm_autotune_clear empties
+ * it; ifmm_autotune_size returns its number of entries. The table functions are host-only. */
+ifmm_status ifmm_autotune(ifmm_h* hs, int n, int workers);
+ifmm_status ifmm_autotune_save(const char* path);
+ifmm_status ifmm_autotune_load(const char* path);
+void ifmm_autotune_clear(void);
+int ifmm_autotune_size(void);
+
 /* As ifmm_solve with host buffers: copies b in and x out inside the call (one copy per column, or
  * one for the block when ld = N). Page-locked host buffers (cudaHostAlloc or pinned tensors) copy
  * at the link's rate; pageable ones are staged by the driver, several times slower. */

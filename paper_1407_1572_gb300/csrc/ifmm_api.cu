@@ -12,6 +12,7 @@
 #include <mutex>
 #include <atomic>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -1710,6 +1711,93 @@ ifmm_status ifmm_factor_batch(ifmm_h* hs, int n, int workers, ifmm_status* statu
         return s;
     });
 }
+
+// Autotuner of the batched launches (no counterpart in the paper): times the panel and Schur
+// launches of ifmm_factor_batch on the given systems for each candidate split and keeps, per
+// bucket of (kernel, double-float products, ceil(log2 nmax), ceil(log2 boxes)), the fastest.
+ifmm_status ifmm_autotune(ifmm_h* hs, int n, int workers) {
+    if (!hs || n <= 0) return IFMM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i]) return IFMM_ERR_INVALID_ARG;
+    DeviceGuard dg(hs[0]->device);
+    static const int cand[5] = {1, 2, 4, 8, 16};
+    // warm-up: one-time kernel set-up out of the measured runs
+    ifmm_status s = ifmm_factor_batch(hs, n, workers, nullptr);
+    if (s != IFMM_OK && s != IFMM_ERR_RANK_OVERFLOW) return s;
+    auto table = tune_table_get();
+    for (int kernel = 0; kernel < 2; ++kernel) {
+        std::map<std::tuple<int, int, int, int>, std::vector<double>> times;
+        for (int c = 0; c < 5; ++c) {
+            tune_set_force(kernel == 0 ? cand[c] : 0, kernel == 1 ? cand[c] : 0);
+            tune_record(true);
+            s = ifmm_factor_batch(hs, n, workers, nullptr);
+            cudaDeviceSynchronize();
+            tune_record(false);
+            auto m = tune_collect(kernel);
+            if (s != IFMM_OK && s != IFMM_ERR_RANK_OVERFLOW) {
+                tune_set_force(0, 0);
+                return s;
+            }
+            for (auto& kv : m) {
+                auto& v = times[kv.first];
+                v.resize(5, 1e300);
+                v[c] = kv.second;
+            }
+        }
+        for (auto& kv : times) {
+            int bc = 0;
+            for (int c = 1; c < 5; ++c)
+                if (kv.second[c] < kv.second[bc]) bc = c;
+            table[kv.first] = cand[bc];
+        }
+    }
+    tune_set_force(0, 0);
+    tune_table_set(table);
+    return ifmm_factor_batch(hs, n, workers, nullptr);   // leave the systems factored with the table
+}
+
+ifmm_status ifmm_autotune_save(const char* path) {
+    if (!path) return IFMM_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "w");
+    if (!f) return IFMM_ERR_INVALID_ARG;
+    std::fprintf(f, "# ifmm autotune table: kernel (0 panel, 1 Schur), double-float products (0/1), "
+                    "ceil(log2 nmax), ceil(log2 boxes of the launch), split\n");
+    for (auto& kv : tune_table_get())
+        std::fprintf(f, "%d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                     std::get<3>(kv.first), kv.second);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? IFMM_OK : IFMM_ERR_INVALID_ARG;
+}
+
+ifmm_status ifmm_autotune_load(const char* path) {
+    if (!path) return IFMM_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return IFMM_ERR_INVALID_ARG;
+    std::map<std::tuple<int, int, int, int>, int> t;
+    char line[512];
+    bool ok = true;
+    while (std::fgets(line, sizeof(line), f)) {
+        const char* c = line;
+        while (*c == ' ' || *c == '\t') ++c;
+        if (*c == '#' || *c == '\n' || *c == '\r' || *c == 0) continue;
+        int k, df, lb, bb, z;
+        char extra = 0;
+        if (std::sscanf(c, "%d %d %d %d %d %c", &k, &df, &lb, &bb, &z, &extra) != 5 || k < 0 || k > 1 || df < 0 ||
+            df > 1 || lb < 0 || lb > 30 || bb < 0 || bb > 30 || z < 1 || z > 64) {
+            ok = false;
+            break;
+        }
+        t[std::make_tuple(k, df, lb, bb)] = z;
+    }
+    std::fclose(f);
+    if (!ok) return IFMM_ERR_INVALID_ARG;
+    tune_table_set(t);
+    return IFMM_OK;
+}
+
+void ifmm_autotune_clear(void) { tune_table_set({}); }
+
+int ifmm_autotune_size(void) { return (int)tune_table_get().size(); }
 
 ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
                              const int64_t* ld, int workers, ifmm_status* status_out) {

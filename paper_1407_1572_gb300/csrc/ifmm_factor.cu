@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -899,6 +900,71 @@ int dynamic_smem_limit(const void* fn) {
 
 __global__ void k_set_flag(int* status, int flag) { atomicOr(status, flag); }
 
+// ---------------------------------------------------------------------------------------------
+// Autotuner of the split of the panel and Schur launches: how many blocks share one box's (panel)
+// or one pair's (Schur) product, i.e. the output tiles each block takes. A table maps a bucket --
+// (kernel, double-float products or not, ceil(log2 nmax), ceil(log2 boxes of the launch)), the
+// launch's block size s and its box count -- to the split that ran fastest when it was measured; a
+// bucket without an entry takes the fixed rule. A split only changes which block computes which
+// output tile, never the arithmetic of a tile, so every split gives the same results bit for bit.
+// The table is process-wide (one mutex); tuning records the launches' device times with events.
+// ---------------------------------------------------------------------------------------------
+namespace tune {
+using Key = std::tuple<int, int, int, int>;
+std::mutex mu;
+std::map<Key, int> table;
+int force[2] = {0, 0};   // while tuning: the candidate split of the panel / Schur launches (0: none)
+bool recording = false;
+struct Rec { Key key; cudaEvent_t e0, e1; };
+std::vector<Rec> recs;
+
+int ceil_log2(int v) {
+    int b = 0;
+    while (b < 30 && (1 << b) < v) ++b;
+    return b;
+}
+// the split of a launch: the forced candidate while tuning, else the table's entry, else the rule
+int split(const Key& k, int rule) {
+    std::lock_guard<std::mutex> lk(mu);
+    const int f = force[std::get<0>(k)];
+    if (f > 0) return f;
+    auto it = table.find(k);
+    return it != table.end() ? it->second : rule;
+}
+}  // namespace tune
+
+void tune_set_force(int panel, int schur) {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    tune::force[0] = panel;
+    tune::force[1] = schur;
+}
+void tune_record(bool on) {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    tune::recording = on;
+}
+// device milliseconds of the recorded launches, summed per bucket, for one kernel; clears the records
+std::map<std::tuple<int, int, int, int>, double> tune_collect(int kernel) {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    std::map<tune::Key, double> out;
+    for (auto& r : tune::recs) {
+        float ms = 0.f;
+        if (std::get<0>(r.key) == kernel && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) out[r.key] += ms;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    tune::recs.clear();
+    cudaGetLastError();
+    return out;
+}
+void tune_table_set(const std::map<std::tuple<int, int, int, int>, int>& t) {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    tune::table = t;
+}
+std::map<std::tuple<int, int, int, int>, int> tune_table_get() {
+    std::lock_guard<std::mutex> lk(tune::mu);
+    return tune::table;
+}
+
 // largest pivot size s = n + r over the boxes of a colour at the time of their elimination (the
 // ranks grow on the device), into *out
 template <typename T>
@@ -1016,13 +1082,29 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     const int tw = L.gemm_dfl ? 32 : 64;
     const int tiles = ((L.nmax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw);
     const int nd = L.nd, npair = nd * nd, nact = L.dim == 3 ? 343 : 49;   // active pairs, roughly
-    const int zs = std::max(1, std::min(tiles, (608 + nboxes * nact - 1) / (nboxes * nact)));
-    const int zp = std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8)));
-    if (ev) cudaEventRecord(ev[1], st);
     const bool df = std::is_same<T, double>::value && L.gemm_dfl;
+    const tune::Key kp{0, df ? 1 : 0, tune::ceil_log2(L.nmax), tune::ceil_log2(nboxes)};
+    const tune::Key ks{1, df ? 1 : 0, tune::ceil_log2(L.nmax), tune::ceil_log2(nboxes)};
+    const int zs = tune::split(ks, std::max(1, std::min(tiles, (608 + nboxes * nact - 1) / (nboxes * nact))));
+    const int zp = tune::split(
+        kp, std::max(1, std::min(((smax + tw - 1) / tw) * ((L.nmax + tw - 1) / tw), (608 + nboxes * 8 - 1) / (nboxes * 8))));
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};   // panel start / end, Schur start / end
+    bool rec;
+    {
+        std::lock_guard<std::mutex> lk(tune::mu);
+        rec = tune::recording;
+    }
+    if (rec)
+        for (auto& e : tev) cudaEventCreate(&e);
+    if (rec) cudaEventRecord(tev[0], st);
+    if (ev) cudaEventRecord(ev[1], st);
     if (df) k_panel<T, true><<<dim3(nboxes, nd, zp), kThreads, 0, st>>>(L, bl, colour);
     else k_panel<T, false><<<dim3(nboxes, nd, zp), kThreads, 0, st>>>(L, bl, colour);
     if (ev) cudaEventRecord(ev[2], st);
+    if (rec) {
+        cudaEventRecord(tev[1], st);
+        cudaEventRecord(tev[2], st);
+    }
     if (df && L.gemm_tc) {
         // tensor-core products: output tiles of 128 x 32, 82.6 KB of dynamic shared memory
         static std::atomic<bool> tc_attr{false};
@@ -1039,6 +1121,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         k_schur<T, 0><<<dim3(nboxes, npair, zs), kThreads, 0, st>>>(L, bl, colour);
     }
     if (ev) cudaEventRecord(ev[3], st);
+    if (rec) {
+        cudaEventRecord(tev[3], st);
+        std::lock_guard<std::mutex> lk(tune::mu);
+        tune::recs.push_back({kp, tev[0], tev[1]});
+        tune::recs.push_back({ks, tev[2], tev[3]});
+    }
     // u holds a neighbour's n_q rows (sized by the level bound, not by this colour's pivots), then
     // 8 x RC coefficients, then the column norms of the stacked fill (at most 2 x 5 partners x nmax
     // in 2D, 2 x 19 in 3D)

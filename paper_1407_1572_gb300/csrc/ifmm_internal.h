@@ -1,6 +1,8 @@
 // ifmm_internal.h -- structures shared by the host orchestration and the CUDA kernels.
 #pragma once
 #include <cstdint>
+#include <map>
+#include <tuple>
 #include <cuda_runtime.h>
 
 namespace ifmm {
@@ -180,6 +182,12 @@ struct SolveView {
 };
 
 // ---- launchers (ifmm_factor.cu) -----------------------------------------------------------
+// autotuner of the panel / Schur launch splits: candidate forcing, event records, the table
+void tune_set_force(int panel, int schur);
+void tune_record(bool on);
+std::map<std::tuple<int, int, int, int>, double> tune_collect(int kernel);
+void tune_table_set(const std::map<std::tuple<int, int, int, int>, int>& t);
+std::map<std::tuple<int, int, int, int>, int> tune_table_get();
 // ev (optional): 6 events recorded before each of the five launches and after the last
 template <typename T>
 // smem_pivot_s: the level's bound on a pivot's size; exact_sizing: read the colour's actual largest

@@ -64,7 +64,8 @@ _lib = None
 SYMBOLS = ["ifmm_default_params", "ifmm_auto_depth", "ifmm_build", "ifmm_factor", "ifmm_factor_batch",
            "ifmm_solve", "ifmm_solve_T", "ifmm_solve_batch", "ifmm_solve_host",
            "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_tc_dgemm", "ifmm_get_ranks", "ifmm_get_stats",
-           "ifmm_last_error", "ifmm_destroy"]
+           "ifmm_last_error", "ifmm_destroy", "ifmm_autotune", "ifmm_autotune_save", "ifmm_autotune_load",
+           "ifmm_autotune_clear", "ifmm_autotune_size"]
 
 
 def library_path() -> str:
@@ -109,6 +110,15 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ifmm_solve_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(ip), ctypes.POINTER(i64), ip, ctypes.POINTER(ip)]
     lib.ifmm_solve_batch.restype = ip
+    lib.ifmm_autotune.argtypes = [ctypes.POINTER(vp), ip, ip]
+    lib.ifmm_autotune.restype = ip
+    for name in ("ifmm_autotune_save", "ifmm_autotune_load"):
+        getattr(lib, name).argtypes = [ctypes.c_char_p]
+        getattr(lib, name).restype = ip
+    lib.ifmm_autotune_clear.argtypes = []
+    lib.ifmm_autotune_clear.restype = None
+    lib.ifmm_autotune_size.argtypes = []
+    lib.ifmm_autotune_size.restype = ip
     _lib = lib
     return lib
 
@@ -163,6 +173,31 @@ def ifmm_factor_batch(handles, workers: int = 0, allow_overflow: bool = False):
     if bad:
         raise IFMMError(out[bad[0]], f"system {bad[0]}: " + load().ifmm_last_error(handles[bad[0]]).decode())
     return out
+
+
+def ifmm_autotune(handles, workers: int = 0) -> int:
+    """Tune the panel / Schur launch splits on these systems (see include/ifmm.h); returns the size of
+    the process-wide table. The systems are left factored."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    _check(None, load().ifmm_autotune(hs, n, workers), allow=(IFMM_ERR_RANK_OVERFLOW,))
+    return load().ifmm_autotune_size()
+
+
+def ifmm_autotune_save(path: str) -> None:
+    _check(None, load().ifmm_autotune_save(os.fsencode(path)))
+
+
+def ifmm_autotune_load(path: str) -> None:
+    _check(None, load().ifmm_autotune_load(os.fsencode(path)))
+
+
+def ifmm_autotune_clear() -> None:
+    load().ifmm_autotune_clear()
+
+
+def ifmm_autotune_size() -> int:
+    return load().ifmm_autotune_size()
 
 
 def ifmm_solve_batch(handles, b_ptrs, x_ptrs, nrhs, lds, workers: int = 0, allow_noconv: bool = False):
