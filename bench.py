@@ -462,6 +462,13 @@ def roofline(stats, precision, peaks, peak_kind, pipes, boxes=0):
     top = max(range(5), key=lambda i: ms[i])
     out = _kernel_roofline(stats, precision, top, pipes, boxes)
     out["schur"] = _kernel_roofline(stats, precision, 2, pipes, boxes)
+    # every factor kernel against the peak of its own arithmetic (CUDA-event time per launch)
+    from paper_1407_1572_gb300.ifmm import FACTOR_KERNELS
+    out["factor_kernels"] = {}
+    for i, name in enumerate(FACTOR_KERNELS):
+        k = _kernel_roofline(stats, precision, i, pipes, boxes)
+        out["factor_kernels"][name] = {f: k[f] for f in ("arith", "launches", "avg_launch_ms", "achieved", "peak",
+                                                         "frac", "share_of_factor_kernels")}
     # the Schur step's algorithmic bytes, for the intensity against HBM
     nl = max(stats["kernel_launches"][2], 1)
     bytes_pl = stats["schur_bytes"] / nl
@@ -702,6 +709,7 @@ def run_gpu(args):
     N, nrhs = w["N"], w["nrhs"]
     precision = args.precision
     stream = torch.cuda.current_stream()
+    ifmm.ifmm_set_compress_cluster(args.compress_cluster)
 
     def make_solver(prec):
         prm = ifmm.default_params(depth=w["depth"], cheb_p=w["cheb_p"], eps=w["eps"], diag=math.sqrt(N),
@@ -824,6 +832,7 @@ def run_gpu(args):
                 "config": {"workload": workload_desc(w, PRECISION_DESC[precision]),
                            "N": N, "depth": w["depth"], "cheb_p": w["cheb_p"], "nrhs": nrhs, "eps": w["eps"],
                            "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "compress_cluster": args.compress_cluster,
                            "l2": "inputs larger than L2 (factor touches tens of GB per step)",
                            "err": err, "refine_iters": st["refine_iters"], "max_rank": st["max_rank"],
                            "t_factor_ms": st["t_factor_ms"], "t_solve_ms": st["t_solve_ms"],
@@ -862,6 +871,8 @@ def main():
     ap.add_argument("--tc-products", type=int, default=0, choices=[0, 1, 2],
                     help="mixed_solve: tensor-core products in the replay (1), the replay and the Schur "
                          "update (2), or double-float on the FP32 pipe (0)")
+    ap.add_argument("--compress-cluster", type=int, default=8, choices=[1, 2, 4, 8],
+                    help="largest thread-block cluster one fill compression may use (1: one block each)")
     ap.add_argument("--batch", dest="batch", action="store_true", default=True,
                     help="also time the batched workload of 256 uneven systems (default)")
     ap.add_argument("--no-batch", dest="batch", action="store_false")

@@ -232,6 +232,14 @@ ifmm_status ifmm_autotune_load(const char* path);
 void ifmm_autotune_clear(void);
 int ifmm_autotune_size(void);
 
+/* Largest thread-block cluster over which one fill compression of Algorithm 1 (Section 4.2) may
+ * be spread (1, 2, 4 or 8; default 8; process-wide, read at each factorisation launch). Where a
+ * colour has few boxes (the upper levels of the tree) the blocks of a cluster each take a slice
+ * of the stacked fill's columns; the arithmetic per column is the same as with one block, so
+ * ranks, bases and solutions are the same bit for bit for every setting. 1 turns the clusters
+ * off. Errors: INVALID_ARG for any other value (setting unchanged). Host-only. */
+ifmm_status ifmm_set_compress_cluster(int max_blocks);
+
 /* As ifmm_solve with host buffers: copies b in and x out inside the call (one copy per column, or
  * one for the block when ld = N). Page-locked host buffers (cudaHostAlloc or pinned tensors) copy
  * at the link's rate; pageable ones are staged by the driver, several times slower. */

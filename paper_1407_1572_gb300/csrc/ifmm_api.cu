@@ -1799,6 +1799,10 @@ void ifmm_autotune_clear(void) { tune_table_set({}); }
 
 int ifmm_autotune_size(void) { return (int)tune_table_get().size(); }
 
+ifmm_status ifmm_set_compress_cluster(int max_blocks) {
+    return set_compress_cluster(max_blocks) == 0 ? IFMM_OK : IFMM_ERR_INVALID_ARG;
+}
+
 ifmm_status ifmm_solve_batch(ifmm_h* hs, int n, const double* const* b_dev, double* const* x_dev, const int* nrhs,
                              const int64_t* ld, int workers, ifmm_status* status_out) {
     if (!hs || n <= 0 || !b_dev || !x_dev || !nrhs || !ld) return IFMM_ERR_INVALID_ARG;

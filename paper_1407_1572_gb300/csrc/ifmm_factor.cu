@@ -37,6 +37,15 @@ namespace ifmm {
 static thread_local long long g_launches = 0;
 void count_launches(int n) { g_launches += n; }
 long long launches_so_far() { return g_launches; }
+int num_sms();
+
+// largest cluster of blocks one compression may be spread over (1: one block per compression)
+static std::atomic<int> compress_cluster_max{8};
+int set_compress_cluster(int c) {
+    if (c != 1 && c != 2 && c != 4 && c != 8) return -1;
+    compress_cluster_max.store(c);
+    return 0;
+}
 
 template <typename T> struct AccOf { using type = double; };
 template <> struct AccOf<float> { using type = float; };
@@ -507,20 +516,49 @@ IFMM_DEVINL dfl gs_axpy(dfl r, dfl s, dfl u) {
 
 // gscr: the FP64 work arrays live in the colour's global scratch (L.Cws) instead of shared memory
 // (wide fills, whose arrays exceed the shared-memory budget of the launch)
+// C > 1: one compression is spread over a cluster of C blocks (few boxes per colour: the upper
+// levels). Block c owns the columns [c mc, (c + 1) mc) of the stacked fill (mc = ceil(m / C)): it
+// gathers, projects and updates those columns and keeps their norms; the pivot column is chosen
+// over the cluster (candidates exchanged through distributed shared memory, one cluster barrier
+// per step) and read from global memory past L1; every block then forms the same direction u
+// (same operations in the same order) and writes the same basis column. Per column the arithmetic
+// is the single-block one, so the result is the same bit for bit.
 constexpr int kMaxPartners = 19;
 constexpr int kGB = 4;   // column elements a thread of the Gram-Schmidt loads ahead
+IFMM_DEVINL double load_cg(const double* p) { return __ldcg(p); }
+IFMM_DEVINL float load_cg(const float* p) { return __ldcg(p); }
+IFMM_DEVINL dfl load_cg(const dfl* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return dfl(v.x, v.y);
+}
 template <typename T, bool DF>
-__global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<T> bl, int colour, int gscr) {
-    const LevelView<T>& L = bl.view(L0, blockIdx.x);
+__global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<T> bl, int colour, int gscr, int C) {
+    namespace cg = cooperative_groups;
+    const int crank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const LevelView<T>& L = bl.view(L0, blockIdx.x / C);
     using Acc = typename AccOf<T>::type;
     extern __shared__ double csm_dyn[];  // u (nq), per-warp coefficients (8 * RC), column norms (m)
     using GS = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     __shared__ GS gsm[gemm_smem<GS>::value];
     __shared__ double vred[32];
     __shared__ int ired[32];
-    __shared__ double s_val;
-    __shared__ int s_flag;
-    const int e = bl.box(blockIdx.x);
+    __shared__ double s_cval[2];   // this block's pivot candidate, double-buffered by step parity
+    __shared__ int s_cidx[2];
+    // the cluster's best (value, index) over the blocks' candidates of parity slot sl: ties to the
+    // lowest column (the single-block rule); read by every block after the cluster barrier
+    auto cluster_best = [&](int sl, double* val) {
+        cg::cluster_group cl = cg::this_cluster();
+        double bv = -1.0;
+        int bi = -1;
+        for (int j = 0; j < C; ++j) {
+            const double v = *cl.map_shared_rank(&s_cval[sl], j);
+            const int i = *cl.map_shared_rank(&s_cidx[sl], j);
+            if (i >= 0 && (bi < 0 || v > bv || (v == bv && i < bi))) { bv = v; bi = i; }
+        }
+        *val = bv;
+        return bi;
+    };
+    const int e = bl.box(blockIdx.x / C);
     const int dq = blockIdx.y;
     if (dq == L.ctr) return;
     const Cell ce = cell_of(e, L.side, L.dim);
@@ -551,12 +589,19 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         m += (half ? 1 : 2) * wps[t];
     }
     if (nq == 0 || m == 0) return;
+    // this block's columns [j0, j1) (all of them for a single block)
+    const int mc = (m + C - 1) / C;
+    const int j0 = min(m, crank * mc), j1 = min(m, j0 + mc), mloc = j1 - j0;
     T* R = L.Rs + L.rsoff[(int64_t)e * L.nd + dq];
     double* csm = gscr ? L.Cws + L.cwsoff[(int64_t)e * L.nd + dq] : csm_dyn;
     {
         int c0 = 0;
         for (int t = 0; t < np; ++t) {
             int dp = parts[t], wp = wps[t];
+            if (c0 >= j1 || c0 + (half ? 1 : 2) * wp <= j0) {   // no column of this block
+                c0 += (half ? 1 : 2) * wp;
+                continue;
+            }
             if (half) {
                 // F_qp is stored as is (dq < dp, nq x wp) or as its transpose F_pq (wp x nq); either
                 // way element u of the stored block is read in order (coalesced), four per thread
@@ -576,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
                             const int a = direct ? u / wp : u / nq, b = direct ? u - a * wp : u - a * nq;
                             const int i = direct ? a : b, j = direct ? b : a;
                             v[k] = F[u];
-                            dst[k] = (int64_t)i * m + c0 + j;
+                            if (c0 + j >= j0 && c0 + j < j1) dst[k] = (int64_t)i * m + c0 + j;
                         }
                     }
 #pragma unroll
@@ -586,8 +631,10 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
             } else {
                 for (int u = threadIdx.x; u < nq * wp; u += blockDim.x) {
                     int i = u / wp, j = u - i * wp;
-                    R[(size_t)i * m + c0 + j] = fill_at(L, e, dq, dp, nq, wp, i, j);                // F_qp
-                    R[(size_t)i * m + c0 + wp + j] = fill_at(L, e, dp, dq, wp, nq, j, i);            // F_pq^T
+                    if (c0 + j >= j0 && c0 + j < j1)
+                        R[(size_t)i * m + c0 + j] = fill_at(L, e, dq, dp, nq, wp, i, j);            // F_qp
+                    if (c0 + wp + j >= j0 && c0 + wp + j < j1)
+                        R[(size_t)i * m + c0 + wp + j] = fill_at(L, e, dp, dq, wp, nq, j, i);       // F_pq^T
                 }
             }
             c0 += (half ? 1 : 2) * wp;
@@ -597,14 +644,24 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // reference norm: largest column norm of S_q, one column per thread (consecutive threads read
     // consecutive columns of a row: coalesced; a warp per column reads 32 rows m apart)
-    double mloc = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double nmx = 0.0;
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
         double s = 0.0;
 #pragma unroll 4
         for (int i = 0; i < nq; ++i) { const double v = (double)R[(size_t)i * m + j]; s = fma(v, v, s); }
-        mloc = fmax(mloc, sqrt(s));
+        nmx = fmax(nmx, sqrt(s));
     }
-    const double smax = block_max(mloc, vred);
+    double smax = block_max(nmx, vred);
+    if (C > 1) {
+        // the largest over the cluster (slot 0 holds it, read by every block before the second
+        // barrier, after which slot 0 may be reused)
+        if (threadIdx.x == 0) { s_cval[0] = smax; s_cidx[0] = 0; }
+        cg::this_cluster().sync();
+        double v;
+        (void)cluster_best(0, &v);
+        smax = v;
+        cg::this_cluster().sync();
+    }
     if (!(smax > 0.0)) return;
     const double tau = L.eps * (L.tau_ref == 1 ? L.sA : smax);
     T* W = L.W + L.voff[q] * RC;
@@ -615,20 +672,22 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     // classical Gram-Schmidt per column.
     const int passes = sizeof(T) == 8 ? 1 : 2;
     if (half && passes == 1 && rq0 > 0) {
-        T* Cm = R + (size_t)nq * m;
+        // (this block's columns: column j of the products is column j0 + j of R)
+        T* Cm = R + (size_t)nq * m + j0;
+        T* Rj = R + j0;
         factor_gemm<T, DF>(
-            L, rq0, m, nq, [&](int i, int k) { return W[(size_t)k * RC + i]; },
-            [&](int k, int j) { return R[(size_t)k * m + j]; },
+            L, rq0, mloc, nq, [&](int i, int k) { return W[(size_t)k * RC + i]; },
+            [&](int k, int j) { return Rj[(size_t)k * m + j]; },
             [&](int i, int j, Acc v) { Cm[(size_t)i * m + j] = (T)v; }, gsm, 0, 1);
         __syncthreads();
         factor_gemm<T, DF>(
-            L, nq, m, rq0, [&](int i, int k) { return W[(size_t)i * RC + k]; },
+            L, nq, mloc, rq0, [&](int i, int k) { return W[(size_t)i * RC + k]; },
             [&](int k, int j) { return Cm[(size_t)k * m + j]; },
-            [&](int i, int j, Acc v) { R[(size_t)i * m + j] = (T)((Acc)R[(size_t)i * m + j] - v); }, gsm, 0, 1);
+            [&](int i, int j, Acc v) { Rj[(size_t)i * m + j] = (T)((Acc)Rj[(size_t)i * m + j] - v); }, gsm, 0, 1);
         __syncthreads();
     }
     for (int pass = 0; pass < passes && rq0 > 0 && !(half && passes == 1); ++pass) {
-        for (int j = warp; j < m; j += nw) {
+        for (int j = j0 + warp; j < j1; j += nw) {
             double* c = coef + warp * RC;
             for (int t = 0; t < rq0; ++t) {
                 Acc s = 0;
@@ -648,32 +707,36 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     }
     const int limit = min(nq, RC);
     double* u = csm;
-    double* nrm2 = coef + 8 * RC;   // squared column norms of R, exact after every step
+    double* nrm2 = coef + 8 * RC;   // squared norms of this block's columns of R (column j0 + j at j)
     // the column work of the Gram-Schmidt: FP64, or double-float on the FP32 pipe when the products
     // are double-float (the basis, the re-orthogonalisation, the norms that decide the pivots and the
     // ranks, and the threshold test stay FP64)
     using E = std::conditional_t<DF && std::is_same<T, double>::value, dfl, Acc>;
     E* Re = reinterpret_cast<E*>(R);
-    E* ue = reinterpret_cast<E*>(nrm2 + m);   // u in E (nq entries)
+    E* ue = reinterpret_cast<E*>(nrm2 + (C > 1 ? mloc : m));   // u in E (nq entries)
     if constexpr (std::is_same<E, dfl>::value) {
         // R to double-float in place (the split works on the bit pattern: no FP64 arithmetic)
-        for (int t = threadIdx.x; t < nq * m; t += blockDim.x) Re[t] = dfl((double)R[t]);
+        for (int t = threadIdx.x; t < nq * mloc; t += blockDim.x) {
+            const int i = t / mloc, j = j0 + (t - i * mloc);
+            Re[(size_t)i * m + j] = dfl((double)R[(size_t)i * m + j]);
+        }
         __syncthreads();
     }
-    // g threads per column (a power of two dividing 32; more when the columns are few), ngr
-    // groups; every warp runs the same number of column rounds so the group shuffles converge
+    // g threads per column (a power of two dividing 32; more when the columns are few; set by the
+    // whole width m so that a column is summed in the same order in a cluster), ngr groups; every
+    // warp runs the same number of column rounds so the group shuffles converge
     int g = 1;
     while (g < 8 && g * 2 * m <= (int)blockDim.x) g *= 2;
     const int ngr = (int)blockDim.x / g, gid = (int)threadIdx.x / g, gl = (int)threadIdx.x % g;
-    const int rounds = (m + ngr - 1) / ngr;
+    const int rounds = (mloc + ngr - 1) / ngr;
     auto group_sum = [&](E v) {
         for (int o = g >> 1; o > 0; o >>= 1) v = v + gs_shfl(v, o);
         return v;
     };
     for (int rd = 0; rd < rounds; ++rd) {
-        const int j = gid + rd * ngr;
+        const int j = j0 + gid + rd * ngr;
         E sq = E(0);
-        if (j < m) {
+        if (j < j1) {
             int i = gl;
             for (; i + (kGB - 1) * g < nq; i += kGB * g) {
                 E x[kGB];
@@ -685,33 +748,40 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
             for (; i < nq; i += g) { const E v = Re[(size_t)i * m + j]; gs_fma(sq, v, v); }
         }
         sq = group_sum(sq);
-        if (j < m && gl == 0) nrm2[j] = gs_d(sq);
+        if (j < j1 && gl == 0) nrm2[j - j0] = gs_d(sq);
     }
     __syncthreads();
     int add = 0;
-    for (;;) {
+    for (int step = 0;; ++step) {
         // largest remaining column norm, ties to the lowest column (reading R2). The norms are
         // recomputed from the updated columns at every step, so the pivot is chosen on exact norms
         // as in the oracle: an estimate (a downdated norm) lets nearly equal columns swap order,
         // and a different pivot order leaves a different remainder below the threshold.
         double best = -1.0;
         int bi = -1;
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const double v = nrm2[j];
+        for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
+            const double v = nrm2[j - j0];
             if (bi < 0 || v > best) { best = v; bi = j; }
         }
         double b2;
-        const int jb = block_argmax(best, bi, vred, ired, &b2);
+        int jb = block_argmax(best, bi, vred, ired, &b2);
+        if (C > 1) {
+            if (threadIdx.x == 0) { s_cval[step & 1] = b2; s_cidx[step & 1] = jb; }
+            // also orders this block's column updates (global memory) before the others' reads
+            cg::this_cluster().sync();
+            jb = cluster_best(step & 1, &b2);
+        }
         if (jb < 0) break;
         const double bv = sqrt(b2);
         if (!(bv > tau)) break;
         if (rq0 + add >= limit) {
-            if (limit < nq && threadIdx.x == 0) atomicOr(L.status, DEV_ERR_OVERFLOW);
+            if (limit < nq && threadIdx.x == 0 && crank == 0) atomicOr(L.status, DEV_ERR_OVERFLOW);
             break;
         }
         const int rc = rq0 + add;
         const double ib = 1.0 / bv;
-        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = gs_d(Re[(size_t)i * m + jb]) * ib;
+        // (the pivot column may belong to another block of the cluster: read past L1)
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) u[i] = gs_d(load_cg(Re + (size_t)i * m + jb)) * ib;
         __syncthreads();
         // re-orthogonalise u against the current basis, twice (one thread per basis vector for the
         // coefficients, one per row for the update)
@@ -736,13 +806,17 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         nn = block_sum(nn, vred);
         const double nu = sqrt(nn);
         if (!(nu >= 0.5)) {
-            // numerically inside the current span: drop this column
-            for (int i = threadIdx.x; i < nq; i += blockDim.x) Re[(size_t)i * m + jb] = E(0);
-            if (threadIdx.x == 0) nrm2[jb] = 0.0;
+            // numerically inside the current span: drop this column (its owner clears it)
+            if (jb >= j0 && jb < j1) {
+                for (int i = threadIdx.x; i < nq; i += blockDim.x) Re[(size_t)i * m + jb] = E(0);
+                if (threadIdx.x == 0) nrm2[jb - j0] = 0.0;
+            }
             __syncthreads();
             continue;
         }
         const double inu = 1.0 / nu;
+        // every block of a cluster writes the same basis column (the same values), so each reads
+        // back its own writes in the next re-orthogonalisation
         for (int i = threadIdx.x; i < nq; i += blockDim.x) {
             u[i] *= inu;
             W[(size_t)i * RC + rc] = (T)u[i];
@@ -752,11 +826,11 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         // remove u from every column; the squared norm of the updated column is summed in the same
         // pass (one more multiply-add per element, no extra memory traffic)
         for (int rd = 0; rd < rounds; ++rd) {
-            const int j = gid + rd * ngr;
+            const int j = j0 + gid + rd * ngr;
             // kGB elements of the column loaded together before they are used (stores to R would
             // otherwise keep the compiler from hoisting the next loads); same order of operations
             E sp = E(0);
-            if (j < m) {
+            if (j < j1) {
                 int i = gl;
                 for (; i + (kGB - 1) * g < nq; i += kGB * g) {
                     E x[kGB];
@@ -769,7 +843,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
             }
             sp = group_sum(sp);
             E sq = E(0);
-            if (j < m) {
+            if (j < j1) {
                 int i = gl;
                 for (; i + (kGB - 1) * g < nq; i += kGB * g) {
                     E x[kGB];
@@ -789,12 +863,12 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
                 }
             }
             sq = group_sum(sq);
-            if (j < m && gl == 0) nrm2[j] = gs_d(sq);
+            if (j < j1 && gl == 0) nrm2[j - j0] = gs_d(sq);
         }
         __syncthreads();
         ++add;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && crank == 0) {
         L.r[q] = rq0 + add;
         // projection onto the complement of the old basis (two products of nq x m x rq0 per pass)
         // and the pivoted Gram-Schmidt: per appended direction a dot product, an update and a norm
@@ -806,8 +880,8 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         atomicAdd(&L.counters[5], proj + gs);
         atomicAdd(&L.counters[7], proj);
     }
-    (void)s_val;
-    (void)s_flag;
+    // no block leaves while another may still read its candidate slots
+    if (C > 1) cg::this_cluster().sync();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1134,13 +1208,67 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     // neither fail nor cut the number of resident blocks
     size_t csmem = (size_t)(smax_bound + 8 * L.RC + (L.dim == 3 ? 38 : 10) * L.nmax) * sizeof(double);
     const int gscr = (csmem > (size_t)64 * 1024 || !L.Cws) ? 1 : 0;
-    if (gscr && !L.Cws) {
+    // few boxes (the upper levels): one cluster of Cc blocks per compression, each block a slice of
+    // the fill's columns, so that the colour's few compressions occupy more SMs; the work arrays of
+    // a block (u, coefficients, the norms of its columns, u again) then fit in shared memory
+    int Cc = 1;
+    const int cmax = compress_cluster_max.load();
+    while (Cc < cmax && (size_t)nboxes * (nd - 1) / 2 * Cc < (size_t)2 * num_sms()) Cc *= 2;
+    const size_t mbound = (size_t)(L.symmetric ? (L.dim == 3 ? 19 : 5) : (L.dim == 3 ? 38 : 10)) * L.nmax;
+    auto cl_smem = [&](int cc) {
+        return (size_t)(smax_bound + 8 * L.RC + (mbound + cc - 1) / cc + L.nmax) * sizeof(double);
+    };
+    while (Cc > 1 && cl_smem(Cc) > (size_t)dynamic_smem_limit(df ? (const void*)k_compress<T, true>
+                                                                      : (const void*)k_compress<T, false>))
+        Cc = 1;
+    bool launched = false;
+    if (Cc > 1) {
+        const size_t cbytes = cl_smem(Cc);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nboxes * Cc), (unsigned)nd);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = cbytes;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = Cc;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // (the cluster shape is checked once per instantiation, size and shared memory; a shape that
+        // cannot be scheduled, or a refused launch, falls back to one block per compression)
+        static std::mutex occ_mu;
+        static std::map<std::tuple<const void*, int, size_t>, int> occ;
+        auto kfn = df ? (const void*)k_compress<T, true> : (const void*)k_compress<T, false>;
+        int active = 0;
+        {
+            std::lock_guard<std::mutex> lk(occ_mu);
+            const auto key = std::make_tuple(kfn, Cc, cbytes);
+            auto it = occ.find(key);
+            if (it != occ.end()) active = it->second;
+            else {
+                if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess) active = 0;
+                cudaGetLastError();
+                occ[key] = active;
+            }
+        }
+        if (active >= 1) {
+            const cudaError_t err = df ? cudaLaunchKernelEx(&cfg, k_compress<T, true>, L, bl, colour, 0, Cc)
+                                       : cudaLaunchKernelEx(&cfg, k_compress<T, false>, L, bl, colour, 0, Cc);
+            if (err == cudaSuccess) launched = true;
+            else cudaGetLastError();
+        }
+    }
+    if (launched) {
+        // one compression per cluster
+    } else if (gscr && !L.Cws) {
         k_set_flag<<<1, 1, 0, st>>>(L.status, DEV_ERR_SIZE);   // no scratch was provided: refuse
         count_launches(1);
     } else if (df) {
-        k_compress<T, true><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
+        k_compress<T, true><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr, 1);
     } else {
-        k_compress<T, false><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr);
+        k_compress<T, false><<<dim3(nboxes, nd), kThreads, gscr ? 0 : csmem, st>>>(L, bl, colour, gscr, 1);
     }
     if (ev) cudaEventRecord(ev[4], st);
     if (df) k_redirect<T, true><<<dim3(nboxes, npair), kThreads, 0, st>>>(L, bl, colour);

@@ -43,6 +43,8 @@ struct dfl {
 // kernels launched by this library in this process (every launcher adds its launches)
 void count_launches(int n);
 long long launches_so_far();
+// largest cluster one compression launch may use (1, 2, 4 or 8); -1 for any other value
+int set_compress_cluster(int c);
 
 // device status flags (bit set by any block that fails)
 enum : int { DEV_ERR_SINGULAR = 1, DEV_ERR_OVERFLOW = 2, DEV_ERR_RANGE = 4, DEV_ERR_SIZE = 8, DEV_ERR_TIMEOUT = 16 };

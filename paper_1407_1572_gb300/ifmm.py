@@ -65,7 +65,7 @@ SYMBOLS = ["ifmm_default_params", "ifmm_auto_depth", "ifmm_build", "ifmm_factor"
            "ifmm_solve", "ifmm_solve_T", "ifmm_solve_batch", "ifmm_solve_host",
            "ifmm_matvec", "ifmm_matvec_noalloc", "ifmm_tc_dgemm", "ifmm_get_ranks", "ifmm_get_stats",
            "ifmm_last_error", "ifmm_destroy", "ifmm_autotune", "ifmm_autotune_save", "ifmm_autotune_load",
-           "ifmm_autotune_clear", "ifmm_autotune_size"]
+           "ifmm_autotune_clear", "ifmm_autotune_size", "ifmm_set_compress_cluster"]
 
 
 def library_path() -> str:
@@ -119,6 +119,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.ifmm_autotune_clear.restype = None
     lib.ifmm_autotune_size.argtypes = []
     lib.ifmm_autotune_size.restype = ip
+    lib.ifmm_set_compress_cluster.argtypes = [ip]
+    lib.ifmm_set_compress_cluster.restype = ip
     _lib = lib
     return lib
 
@@ -198,6 +200,11 @@ def ifmm_autotune_clear() -> None:
 
 def ifmm_autotune_size() -> int:
     return load().ifmm_autotune_size()
+
+
+def ifmm_set_compress_cluster(max_blocks: int) -> None:
+    """Largest cluster one compression may be spread over (1, 2, 4 or 8; 1 turns clusters off)."""
+    _check(None, load().ifmm_set_compress_cluster(int(max_blocks)))
 
 
 def ifmm_solve_batch(handles, b_ptrs, x_ptrs, nrhs, lds, workers: int = 0, allow_noconv: bool = False):

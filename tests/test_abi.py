@@ -87,3 +87,13 @@ def test_no_cpu_fallback_without_a_device():
     assert st == ifmm.IFMM_ERR_CUDA and not h.value
     with pytest.raises(RuntimeError):   # the wrapper fails before the build (no CUDA stream)
         ifmm.IFMM(pts, ifmm.IFMM_K_INV_R, prm)
+
+
+def test_compress_cluster_setting_is_checked_on_the_host():
+    lib = ifmm.load()
+    for bad in (0, 3, 16, -1):
+        assert lib.ifmm_set_compress_cluster(bad) == 1
+    for ok in (1, 2, 4, 8):
+        assert lib.ifmm_set_compress_cluster(ok) == 0
+    with pytest.raises(ifmm.IFMMError):
+        ifmm.ifmm_set_compress_cluster(5)
