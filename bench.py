@@ -375,7 +375,7 @@ ARITH = {
     "fp64": {k: "FP64" for k in ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")},
     "mixed_solve": {"k_pivot": "FP64",
                     "k_panel": "double-float GEMM", "k_schur": "double-float GEMM",
-                    "k_compress": "double-float projection GEMMs + FP64 Gram-Schmidt",
+                    "k_compress": "double-float projection GEMMs and Gram-Schmidt column work + FP64 re-orthogonalisation",
                     "k_redirect": "double-float GEMM"},
     "mixed": {k: "FP32" for k in ("k_panel", "k_schur", "k_compress", "k_redirect")} | {"k_pivot": "FP64"},
 }
@@ -424,15 +424,18 @@ def _kernel_roofline(stats, precision, i, pipes, boxes=0):
     arith = ARITH[precision][name]
     parts = None
     if name == "k_compress" and precision == "mixed_solve":
-        # two pipes in one kernel: the projection products in double-float on the FP32 pipe, the
-        # pivoted Gram-Schmidt in FP64; the peak is the rate at which the kernel's own mix of the
-        # two would run if each part ran at its pipe's peak (time-weighted)
+        # two pipes in one kernel: the projection products and the Gram-Schmidt's column work (dot
+        # products, updates, norms) in double-float on the FP32 pipe, the re-orthogonalisation of
+        # each new direction in FP64; the peak is the rate at which the kernel's own mix would run
+        # if each part ran at its pipe's peak (time-weighted)
         proj = stats["compress_proj_flops"] / nl
-        gs = flops_pl - proj
-        t_ideal = proj / (pipes["dfl"] * 1e12) + gs / (pipes["fp64"] * 1e12)
+        reorth = stats.get("compress_reorth_flops", 0.0) / nl
+        cols = flops_pl - proj - reorth
+        t_ideal = (proj + cols) / (pipes["dfl"] * 1e12) + reorth / (pipes["fp64"] * 1e12)
         peak = flops_pl / t_ideal / 1e12 if t_ideal > 0 else pipes["fp64"]
         src = f"time-weighted blend of the double-float ({pipes['dfl']:.2f}) and FP64 ({pipes['fp64']:.2f}) peaks, {pipes['source']}"
-        parts = {"projection_flops_per_launch": proj, "gram_schmidt_flops_per_launch": gs,
+        parts = {"projection_flops_per_launch": proj, "gram_schmidt_column_flops_per_launch": cols,
+                 "reorthogonalisation_flops_per_launch": reorth,
                  "projection_share_of_flops": proj / max(flops_pl, 1.0)}
     elif name == "k_compress" and precision == "fp64":
         peak, src = pipes["fp64"], f"FP64 pipe, {pipes['source']}"
@@ -734,6 +737,15 @@ def run_gpu(args):
         ifmm.ifmm_factor(hh, allow_overflow=True)
         ifmm.ifmm_solve(hh, b.data_ptr(), x.data_ptr(), nrhs, N, allow_noconv=True)
 
+    tuned = None
+    if args.autotune:
+        # untimed, before the warm-up: the panel / Schur launch splits of this system's levels,
+        # timed candidate by candidate on its own factorisation (ifmm_autotune); the results do
+        # not depend on the splits, only the launch shapes do
+        ifmm.ifmm_autotune_clear()
+        t_tune = time.perf_counter()
+        ifmm.ifmm_autotune([h], workers=1)
+        tuned = {"table_entries": ifmm.ifmm_autotune_size(), "tuning_s": time.perf_counter() - t_tune}
     for _ in range(args.warmup):
         step(h)
     torch.cuda.synchronize()
@@ -781,6 +793,8 @@ def run_gpu(args):
         for other in [q for q in ("fp64", "mixed_solve", "mixed") if q != precision]:
             so = make_solver(other)
             ifmm.ifmm_matvec(so.h, xs.data_ptr(), b.data_ptr(), nrhs, N)
+            if args.autotune:
+                ifmm.ifmm_autotune([so.h], workers=1)   # tuned as the headline was (untimed)
             step(so.h)
             torch.cuda.synchronize()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -833,6 +847,7 @@ def run_gpu(args):
                            "N": N, "depth": w["depth"], "cheb_p": w["cheb_p"], "nrhs": nrhs, "eps": w["eps"],
                            "parallelism": "replicas" if world > 1 else "1 GPU",
                            "compress_cluster": args.compress_cluster,
+                           "autotune": tuned,
                            "l2": "inputs larger than L2 (factor touches tens of GB per step)",
                            "err": err, "refine_iters": st["refine_iters"], "max_rank": st["max_rank"],
                            "t_factor_ms": st["t_factor_ms"], "t_solve_ms": st["t_solve_ms"],
@@ -871,8 +886,10 @@ def main():
     ap.add_argument("--tc-products", type=int, default=0, choices=[0, 1, 2],
                     help="mixed_solve: tensor-core products in the replay (1), the replay and the Schur "
                          "update (2), or double-float on the FP32 pipe (0)")
-    ap.add_argument("--compress-cluster", type=int, default=8, choices=[1, 2, 4, 8],
+    ap.add_argument("--compress-cluster", type=int, default=16, choices=[1, 2, 4, 8, 16],
                     help="largest thread-block cluster one fill compression may use (1: one block each)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True,
+                    help="headline: keep the fixed launch-split rule instead of tuning the splits first")
     ap.add_argument("--batch", dest="batch", action="store_true", default=True,
                     help="also time the batched workload of 256 uneven systems (default)")
     ap.add_argument("--no-batch", dest="batch", action="store_false")

@@ -146,9 +146,13 @@ typedef struct {
     int64_t launches_solve;  /* kernels launched by the last ifmm_solve / ifmm_solve_host          */
     double compress_proj_flops; /* the part of kernel_flops[3] spent projecting the fill onto the
                               complement of the old basis (products; double-float in
-                              IFMM_MIXED_SOLVE); the rest is the FP64 pivoted Gram-Schmidt        */
+                              IFMM_MIXED_SOLVE); the rest is the pivoted Gram-Schmidt              */
     int svd_ranks[16];     /* singular vectors kept per level (index = level) with svd_eps > 0;
                               0 otherwise                                                           */
+    double compress_reorth_flops; /* the part of kernel_flops[3] spent re-orthogonalising each new
+                              direction against the basis (FP64 in every mode); the rest beyond
+                              compress_proj_flops is the Gram-Schmidt's column work (dot products,
+                              updates and norms: double-float in IFMM_MIXED_SOLVE, else FP64)        */
 } ifmm_stats;
 
 /* Default parameters: dim 2, depth 3, cheb_p 4, r_cap 0, eps 1e-10, diag 1, unit square,
@@ -233,7 +237,8 @@ void ifmm_autotune_clear(void);
 int ifmm_autotune_size(void);
 
 /* Largest thread-block cluster over which one fill compression of Algorithm 1 (Section 4.2) may
- * be spread (1, 2, 4 or 8; default 8; process-wide, read at each factorisation launch). Where a
+ * be spread (1, 2, 4, 8 or 16; default 16, where the device can schedule it, else 8;
+ * process-wide, read at each factorisation launch). Where a
  * colour has few boxes (the upper levels of the tree) the blocks of a cluster each take a slice
  * of the stacked fill's columns; the arithmetic per column is the same as with one block, so
  * ranks, bases and solutions are the same bit for bit for every setting. 1 turns the clusters

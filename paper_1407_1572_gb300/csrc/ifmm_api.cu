@@ -272,8 +272,8 @@ ifmm_status do_build(ifmm_handle* h, const double* pts_host) {
     const int p = h->p, r0 = h->r0;
     CKS(dalloc(h, &h->d_status, sizeof(int) * 4));
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
-    CKS(dalloc(h, &h->d_counters, sizeof(double) * 8));
-    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
+    CKS(dalloc(h, &h->d_counters, sizeof(double) * kCounters));
+    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * kCounters, h->st));
     double* d_pts = nullptr;
     CKS(dalloc(h, &d_pts, sizeof(double) * dim * N));
     CK(cudaMemcpyAsync(d_pts, pts_host, sizeof(double) * dim * N, cudaMemcpyHostToDevice, h->st));
@@ -817,7 +817,7 @@ template <typename T>
 ifmm_status factor_begin(ifmm_handle* h) {
     h->lv.assign(h->depth + 1, FLevel());
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, h->st));
-    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * 8, h->st));
+    CK(cudaMemsetAsync(h->d_counters, 0, sizeof(double) * kCounters, h->st));
     for (int k = 0; k < 16; ++k) h->stats.level_ms[k] = 0.0;
     for (int t = 0; t < 5; ++t) {
         h->stats.kernel_ms[t] = 0.0;
@@ -883,9 +883,9 @@ ifmm_status factor_finish(ifmm_handle* h, long long l0) {
     CKS(dalloc(h, &d_col, sizeof(double) * (size_t)(M + 1)));
     launch_dense_invert(h->d_Dinv, (int)M, d_perm, d_col, h->d_status, h->st);
     int hs = 0;
-    double cnt[8];
+    double cnt[kCounters];
     CK(cudaMemcpyAsync(&hs, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(cnt, h->d_counters, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(cnt, h->d_counters, sizeof(double) * kCounters, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     dfree_ptr(h, d_perm);
@@ -905,6 +905,7 @@ ifmm_status factor_finish(ifmm_handle* h, long long l0) {
     const int fidx[5] = {3, 4, 0, 5, 6};
     for (int t = 0; t < 5; ++t) h->stats.kernel_flops[t] = cnt[fidx[t]];
     h->stats.compress_proj_flops = cnt[7];
+    h->stats.compress_reorth_flops = cnt[8];
     h->stats.launches_factor = launches_so_far() - l0;
     h->stats.rank_overflows = 0;
     h->factored = true;

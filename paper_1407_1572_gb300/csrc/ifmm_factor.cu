@@ -40,9 +40,9 @@ long long launches_so_far() { return g_launches; }
 int num_sms();
 
 // largest cluster of blocks one compression may be spread over (1: one block per compression)
-static std::atomic<int> compress_cluster_max{8};
+static std::atomic<int> compress_cluster_max{16};
 int set_compress_cluster(int c) {
-    if (c != 1 && c != 2 && c != 4 && c != 8) return -1;
+    if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return -1;
     compress_cluster_max.store(c);
     return 0;
 }
@@ -155,6 +155,28 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L0, BoxList<T> 
     }
 }
 
+// The best (largest value, ties to the lowest index; index < 0: no candidate) of the candidates
+// (*val, *idx) that the C blocks of a cluster hold in shared memory: lane j of every warp reads block
+// j's, the warp reduces them, and lane 0's result is broadcast, so that every thread of every block
+// takes the same choice (the comparisons are the same in all of them, whatever the values).
+template <class CL>
+IFMM_DEVINL int cluster_pick(CL& cl, double* val, int* idx, int C, double* vout) {
+    const int lane = (int)threadIdx.x & 31;
+    double v = -1.0;
+    int i = -1;
+    if (lane < C) {
+        v = *cl.map_shared_rank(val, lane);
+        i = *cl.map_shared_rank(idx, lane);
+    }
+    for (int o = C >> 1; o > 0; o >>= 1) {   // (C a power of two: lanes 0 .. C-1 combine)
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (oi >= 0 && (i < 0 || ov > v || (ov == v && oi < i))) { v = ov; i = oi; }
+    }
+    *vout = __shfl_sync(0xffffffffu, v, 0);
+    return __shfl_sync(0xffffffffu, i, 0);
+}
+
 // ---------------------------------------------------------------------------------------------
 // k_pivot_cluster: the same balanced FP64 Gauss-Jordan inversion for large pivot blocks, spread
 // over a cluster of C blocks (one box per cluster). Row i lives in block i mod C (local row
@@ -165,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_pivot(LevelView<T> L0, BoxList<T> 
 // block copies it (cluster barrier) and updates its own rows. Every block runs the same
 // number of cluster barriers (the pivot choice is computed identically in all of them).
 // Shared memory: slab (rows_loc x s, or in the box's global FP64 workspace when slab_global),
-// prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 8 (portable).
+// prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 16 (16: non-portable).
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, BoxList<T> bl, int C, int smax,
@@ -248,15 +270,8 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
         if (threadIdx.x == 0) { s_cval = bv; s_cidx = li; }
         cl.sync();
         // global pivot: identical choice in every block
-        double gv = -1.0;
-        int p = -1;
-        for (int j = 0; j < C; ++j) {
-            const double* rv = cl.map_shared_rank(&s_cval, j);
-            const int* ri = cl.map_shared_rank(&s_cidx, j);
-            const double v = *rv;
-            const int idx = *ri;
-            if (idx >= 0 && (p < 0 || v > gv || (v == gv && idx < p))) { gv = v; p = idx; }
-        }
+        double gv;
+        const int p = cluster_pick(cl, &s_cval, &s_cidx, C, &gv);
         if (p < 0 || !(gv > 0.0) || !isfinite(gv)) {
             if (threadIdx.x == 0 && c == 0) atomicOr(L.status, DEV_ERR_SINGULAR);
             cl.sync();  // every block leaves at the same step, after all candidate reads
@@ -548,15 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     // lowest column (the single-block rule); read by every block after the cluster barrier
     auto cluster_best = [&](int sl, double* val) {
         cg::cluster_group cl = cg::this_cluster();
-        double bv = -1.0;
-        int bi = -1;
-        for (int j = 0; j < C; ++j) {
-            const double v = *cl.map_shared_rank(&s_cval[sl], j);
-            const int i = *cl.map_shared_rank(&s_cidx[sl], j);
-            if (i >= 0 && (bi < 0 || v > bv || (v == bv && i < bi))) { bv = v; bi = i; }
-        }
-        *val = bv;
-        return bi;
+        return cluster_pick(cl, &s_cval[sl], &s_cidx[sl], C, val);
     };
     const int e = bl.box(blockIdx.x / C);
     const int dq = blockIdx.y;
@@ -879,6 +886,7 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
         atomicAdd(&L.counters[2], proj + gs);
         atomicAdd(&L.counters[5], proj + gs);
         atomicAdd(&L.counters[7], proj);
+        atomicAdd(&L.counters[8], 8.0 * (double)nq * ((double)add * rq0 + 0.5 * add * (add - 1)));
     }
     // no block leaves while another may still read its candidate slots
     if (C > 1) cg::this_cluster().sync();
@@ -970,6 +978,54 @@ int dynamic_smem_limit(const void* fn) {
     cudaGetLastError();
     lim[{fn, dev}] = v;
     return v;
+}
+
+// Launch of kfn over clusters of c blocks along x (grid.x a multiple of c). Whether the shape can be
+// scheduled is asked once per (kernel, c, shared memory); c = 16 (beyond the portable 8) is opted
+// into per kernel. False: nothing was launched (the caller takes a smaller cluster or none).
+template <typename... KArgs, typename... Args>
+bool launch_clustered(void (*kfn)(KArgs...), int c, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> occ;
+    if (c > 8) {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto key = std::make_tuple((const void*)kfn, -1, (size_t)0);
+        if (occ.find(key) == occ.end()) {
+            occ[key] = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+            cudaGetLastError();
+        }
+        if (!occ[key]) return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int active = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto key = std::make_tuple((const void*)kfn, c, smem);
+        auto it = occ.find(key);
+        if (it != occ.end()) active = it->second;
+        else {
+            if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess) active = 0;
+            cudaGetLastError();
+            occ[key] = active;
+        }
+    }
+    if (active < 1) return false;
+    if (cudaLaunchKernelEx(&cfg, kfn, args...) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 __global__ void k_set_flag(int* status, int flag) { atomicOr(status, flag); }
@@ -1094,59 +1150,29 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
         return (glob ? 0 : rows * smax * sizeof(double)) + (smax + rows) * sizeof(double) + (smax + rows) * sizeof(int);
     };
     if (smax >= 96) {
-        // few boxes: spread each over several SMs; many boxes: keep a CTA within 72 KB so that
-        // three share an SM (a pivot is a chain of s dependent steps; resident CTAs hide it)
-        while (C < 8 && nboxes * C < 2 * 152) C *= 2;
+        // few boxes: spread each over several SMs (up to 16 at the upper levels); many boxes: keep
+        // a CTA within 72 KB so that three share an SM (a pivot is a chain of s dependent steps;
+        // resident CTAs hide it)
+        while (C < 8 && nboxes * C < 2 * num_sms()) C *= 2;
+        if (C == 8 && nboxes * 8 < num_sms()) C = 16;
         while (C < 8 && cl_bytes(C, 0) > 72 * 1024) C *= 2;
-        if (cl_bytes(C, 0) > 200 * 1024) slab_global = 1;   // slab rows in the FP64 workspace (L2)
-        if (slab_global && !L.pws) C = 1;
     }
     if (ev) cudaEventRecord(ev[0], st);
     if (C > 1) {
-        // (falls back to C = 1 below when the cluster shape cannot be scheduled)
         static std::atomic<bool> cl_attr[2] = {false, false};
         if (!cl_attr[sizeof(T) == 8].load()) {
             cudaFuncSetAttribute(k_pivot_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
             cl_attr[sizeof(T) == 8].store(true);
         }
-        auto kfn = k_pivot_cluster<T>;
-        const size_t cbytes = cl_bytes(C, slab_global);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(nboxes * C));
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = cbytes;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = C;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        // schedulability of the cluster shape, cached per (instantiation, C, shared memory)
-        static std::mutex occ_mu;
-        static std::map<std::tuple<const void*, int, size_t>, int> occ;
-        int active = 0;
-        {
-            std::lock_guard<std::mutex> lk(occ_mu);
-            const auto key = std::make_tuple((const void*)kfn, C, cbytes);
-            auto it = occ.find(key);
-            if (it != occ.end()) active = it->second;
-            else {
-                if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess) {
-                    cudaGetLastError();
-                    active = 0;
-                }
-                occ[key] = active;
-            }
-        }
-        if (active < 1) {
-            cudaGetLastError();
-            C = 1;   // this cluster shape cannot be scheduled: one block per box
-        } else if (cudaLaunchKernelEx(&cfg, kfn, L, bl, C, smax, slab_global) != cudaSuccess) {
-            cudaGetLastError();
-            C = 1;   // launch refused: one block per box instead
-        }
+    }
+    // a cluster shape that cannot be scheduled, or a refused launch, falls back to 8 blocks, then to
+    // one block per box
+    for (bool done = false; C > 1 && !done;) {
+        slab_global = cl_bytes(C, 0) > 200 * 1024 ? 1 : 0;   // slab rows in the FP64 workspace (L2)
+        if (!(slab_global && !L.pws))
+            done = launch_clustered(k_pivot_cluster<T>, C, dim3((unsigned)(nboxes * C)), cl_bytes(C, slab_global), st,
+                                    L, bl, C, smax, slab_global);
+        if (!done) C = C > 8 ? 8 : 1;
     }
     if (C == 1) {
         k_pivot<T><<<nboxes, kThreads, smem, st>>>(L, bl, smax, use_smem);
@@ -1222,43 +1248,12 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
                                                                       : (const void*)k_compress<T, false>))
         Cc = 1;
     bool launched = false;
-    if (Cc > 1) {
-        const size_t cbytes = cl_smem(Cc);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(nboxes * Cc), (unsigned)nd);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = cbytes;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = Cc;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        // (the cluster shape is checked once per instantiation, size and shared memory; a shape that
-        // cannot be scheduled, or a refused launch, falls back to one block per compression)
-        static std::mutex occ_mu;
-        static std::map<std::tuple<const void*, int, size_t>, int> occ;
-        auto kfn = df ? (const void*)k_compress<T, true> : (const void*)k_compress<T, false>;
-        int active = 0;
-        {
-            std::lock_guard<std::mutex> lk(occ_mu);
-            const auto key = std::make_tuple(kfn, Cc, cbytes);
-            auto it = occ.find(key);
-            if (it != occ.end()) active = it->second;
-            else {
-                if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) != cudaSuccess) active = 0;
-                cudaGetLastError();
-                occ[key] = active;
-            }
-        }
-        if (active >= 1) {
-            const cudaError_t err = df ? cudaLaunchKernelEx(&cfg, k_compress<T, true>, L, bl, colour, 0, Cc)
-                                       : cudaLaunchKernelEx(&cfg, k_compress<T, false>, L, bl, colour, 0, Cc);
-            if (err == cudaSuccess) launched = true;
-            else cudaGetLastError();
-        }
+    for (; Cc > 1 && !launched; Cc = Cc > 8 ? 8 : 1) {
+        launched = df ? launch_clustered(k_compress<T, true>, Cc, dim3((unsigned)(nboxes * Cc), (unsigned)nd),
+                                         cl_smem(Cc), st, L, bl, colour, 0, Cc)
+                      : launch_clustered(k_compress<T, false>, Cc, dim3((unsigned)(nboxes * Cc), (unsigned)nd),
+                                         cl_smem(Cc), st, L, bl, colour, 0, Cc);
+        if (launched) break;
     }
     if (launched) {
         // one compression per cluster

@@ -43,7 +43,9 @@ struct dfl {
 // kernels launched by this library in this process (every launcher adds its launches)
 void count_launches(int n);
 long long launches_so_far();
-// largest cluster one compression launch may use (1, 2, 4 or 8); -1 for any other value
+// entries of the factorisation's device counter array (LevelView::counters)
+constexpr int kCounters = 16;
+// largest cluster one compression launch may use (1, 2, 4, 8 or 16); -1 for any other value
 int set_compress_cluster(int c);
 
 // device status flags (bit set by any block that fails)
@@ -150,7 +152,8 @@ struct LevelView {
     int* status;               // device error bits (DEV_ERR_*)
     double* counters;          // [0] schur flops, [1] schur bytes, [2] all factor flops,
                                // [3] pivot, [4] panel, [5] compress, [6] redirect flops,
-                               // [7] the projection part of [5]
+                               // [7] the projection part of [5], [8] its re-orthogonalisation
+                               // part (kCounters entries)
     double eps, sA;
     int tau_ref;
     int symmetric;             // kernel symmetric: F_pq = F_qp^T in exact arithmetic

@@ -46,7 +46,7 @@ class ifmm_stats(ctypes.Structure):
                 ("last_update", ctypes.c_double), ("last_residual", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
                 ("launches_solve", ctypes.c_int64), ("compress_proj_flops", ctypes.c_double),
-                ("svd_ranks", ctypes.c_int * 16)]
+                ("svd_ranks", ctypes.c_int * 16), ("compress_reorth_flops", ctypes.c_double)]
 
 
 FACTOR_KERNELS = ("k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect")
@@ -203,7 +203,7 @@ def ifmm_autotune_size() -> int:
 
 
 def ifmm_set_compress_cluster(max_blocks: int) -> None:
-    """Largest cluster one compression may be spread over (1, 2, 4 or 8; 1 turns clusters off)."""
+    """Largest cluster one compression may be spread over (1, 2, 4, 8 or 16; 1 turns clusters off)."""
     _check(None, load().ifmm_set_compress_cluster(int(max_blocks)))
 
 

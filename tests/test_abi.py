@@ -91,9 +91,9 @@ def test_no_cpu_fallback_without_a_device():
 
 def test_compress_cluster_setting_is_checked_on_the_host():
     lib = ifmm.load()
-    for bad in (0, 3, 16, -1):
+    for bad in (0, 3, 32, -1):
         assert lib.ifmm_set_compress_cluster(bad) == 1
-    for ok in (1, 2, 4, 8):
+    for ok in (1, 2, 4, 8, 16):
         assert lib.ifmm_set_compress_cluster(ok) == 0
     with pytest.raises(ifmm.IFMMError):
         ifmm.ifmm_set_compress_cluster(5)

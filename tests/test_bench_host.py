@@ -25,7 +25,7 @@ def _stats():
     # five factor kernels in the order k_pivot, k_panel, k_schur, k_compress, k_redirect
     return {"kernel_ms": [100.0, 50.0, 180.0, 250.0, 40.0], "kernel_launches": [54, 54, 54, 54, 54],
             "kernel_flops": [1e11, 2e11, 3.9e11, 1.6e11, 5e10], "schur_bytes": 1.0e11,
-            "compress_proj_flops": 1.2e11}
+            "compress_proj_flops": 1.2e11, "compress_reorth_flops": 1.0e10}
 
 
 def test_pipe_peaks_derive_the_double_float_rate_from_the_fp32_rate():
@@ -39,9 +39,10 @@ def test_roofline_picks_the_dominant_kernel_and_divides_by_its_own_peak():
     assert rf["kernel"] == "k_compress"
     t = 250.0 / 54 / 1000.0
     assert math.isclose(rf["achieved"], 1.6e11 / 54 / t / 1e12, rel_tol=1e-12)
-    # two pipes: the projection (1.2e11 flops) in double-float, the Gram-Schmidt (4e10) in FP64;
-    # the peak is the rate of that mix with each part at its own pipe's peak
-    t_ideal = 1.2e11 / 54 / (PIPES["dfl"] * 1e12) + 0.4e11 / 54 / (PIPES["fp64"] * 1e12)
+    # two pipes: the projection (1.2e11 flops) and the Gram-Schmidt column work (3e10) in
+    # double-float, the re-orthogonalisation (1e10) in FP64; the peak is the rate of that mix with
+    # each part at its own pipe's peak
+    t_ideal = 1.5e11 / 54 / (PIPES["dfl"] * 1e12) + 0.1e11 / 54 / (PIPES["fp64"] * 1e12)
     assert math.isclose(rf["peak"], 1.6e11 / 54 / t_ideal / 1e12, rel_tol=1e-12)
     assert math.isclose(rf["frac"], rf["achieved"] / rf["peak"])
     assert math.isclose(rf["projection_share_of_flops"], 0.75)

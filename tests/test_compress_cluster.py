@@ -21,7 +21,7 @@ def ifmm():
     from paper_1407_1572_gb300 import ifmm as m
     m.load()
     yield m
-    m.ifmm_set_compress_cluster(8)
+    m.ifmm_set_compress_cluster(16)
 
 
 def _run(ifmm, pts, prm, nrhs, seed):
@@ -52,13 +52,15 @@ def test_clustered_compression_is_bitwise_the_single_block_one(ifmm, dim, N, dep
                               precision=prec, refine_tol=0.0, refine_maxit=0)
     out = {}
     try:
-        for c in (1, 8):
+        for c in (1, 4, 16):
             ifmm.ifmm_set_compress_cluster(c)
             out[c] = _run(ifmm, pts, prm, 4, 31 + N)
     finally:
-        ifmm.ifmm_set_compress_cluster(8)
-    (r1, x1), (r8, x8) = out[1], out[8]
-    assert len(r1) == len(r8)
-    for k, (a, b) in enumerate(zip(r1, r8)):
-        assert np.array_equal(a, b), f"ranks differ at level {k + 2}"
-    assert torch.equal(x1, x8), f"solutions differ: max {float((x1 - x8).abs().max()):.3e}"
+        ifmm.ifmm_set_compress_cluster(16)
+    r1, x1 = out[1]
+    for c in (4, 16):
+        rc, xc = out[c]
+        assert len(r1) == len(rc)
+        for k, (a, b) in enumerate(zip(r1, rc)):
+            assert np.array_equal(a, b), f"cluster {c}: ranks differ at level {k + 2}"
+        assert torch.equal(x1, xc), f"cluster {c}: solutions differ: max {float((x1 - xc).abs().max()):.3e}"
