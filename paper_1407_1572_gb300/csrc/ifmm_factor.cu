@@ -187,7 +187,7 @@ IFMM_DEVINL int cluster_pick(CL& cl, double* val, int* idx, int C, double* vout)
 // block copies it (cluster barrier) and updates its own rows. Every block runs the same
 // number of cluster barriers (the pivot choice is computed identically in all of them).
 // Shared memory: slab (rows_loc x s, or in the box's global FP64 workspace when slab_global),
-// prow (s), fcol (rows_loc), perm (s), used (rows_loc). Cluster sizes up to 16 (16: non-portable).
+// prow (s), fcol (2 x rows_loc), perm (s), used (rows_loc). Cluster sizes up to 16 (16: non-portable).
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, BoxList<T> bl, int C, int smax,
@@ -200,7 +200,6 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double dsm[];
     __shared__ double vred[32];
-    __shared__ int ired[32];
     __shared__ double s_cval;
     __shared__ int s_cidx;
     __shared__ double s_alpha;
@@ -211,8 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
     const int rows_max = (smax + C - 1) / C;
     double* base = slab_global ? dsm : dsm + (size_t)rows_max * smax;
     S* prow = reinterpret_cast<S*>(base);             // smax
-    S* fcol = prow + smax;                            // rows_max
-    int* perm = reinterpret_cast<int*>(fcol + rows_max);  // smax
+    S* fcol = prow + smax;                            // 2 x rows_max
+    int* perm = reinterpret_cast<int*>(fcol + 2 * rows_max);  // smax
     int* used = perm + smax;                          // rows_max
     const int rows_loc = s > c ? (s - c + C - 1) / C : 0;
     // local row tl of this block is global row c + tl C: in shared memory (slab_global = 0) at
@@ -253,21 +252,35 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
         j += dc;
         if (j >= s) { j -= s; ++tl; }
     }
-    for (int t = threadIdx.x; t < rows_loc; t += blockDim.x) used[t] = 0;
+    __syncthreads();   // the slab's rows are written by other threads than those that read column 0
+    // column k of the local rows before step k: fcol[k & 1] (written by step k - 1, for every row:
+    // the pivot row as it is scaled, the others as they are updated), so that neither the pivot
+    // search nor the update reads a column of the slab with a stride of s
+    for (int t = threadIdx.x; t < rows_loc; t += blockDim.x) {
+        used[t] = 0;
+        fcol[t] = slab[(size_t)t * sstride];
+    }
     __syncthreads();
     for (int k = 0; k < s; ++k) {
-        // local candidate among unused rows
-        double best = -1.0;
-        int bi = -1;
-        for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) {
-            if (used[tl]) continue;
-            const double v = sc_mag(slab[(size_t)tl * sstride + k]);
-            const int gi = c + tl * C;
-            if (bi < 0 || v > best || (v == best && gi < bi)) { best = v; bi = gi; }
+        const S* fc = fcol + (k & 1) * rows_max;
+        S* fn = fcol + ((k + 1) & 1) * rows_max;
+        // local candidate among unused rows (one warp; ties to the lowest row)
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = -1;
+            for (int tl = threadIdx.x; tl < rows_loc; tl += 32) {
+                if (used[tl]) continue;
+                const double v = sc_mag(fc[tl]);
+                const int gi = c + tl * C;
+                if (bi < 0 || v > best || (v == best && gi < bi)) { best = v; bi = gi; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+            }
+            if (threadIdx.x == 0) { s_cval = best; s_cidx = bi; }
         }
-        double bv;
-        const int li = block_argmax(best, bi, vred, ired, &bv);
-        if (threadIdx.x == 0) { s_cval = bv; s_cidx = li; }
         cl.sync();
         // global pivot: identical choice in every block
         double gv;
@@ -280,13 +293,13 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
         const int owner = p % C, tp = p / C;
         if (threadIdx.x == 0) perm[k] = p;
         if (c == owner) {
-            // every thread reads the pivot before the thread with j == k overwrites it
-            const S d = S(1.0 / (double)slab[(size_t)tp * sstride + k]);
-            __syncthreads();
+            // the pivot A[p][k] is fc[tp], so no barrier separates its read from the row's overwrite
+            const S d = S(1.0 / (double)fc[tp]);
             for (int j = threadIdx.x; j < s; j += blockDim.x) {
                 const S v = (j == k) ? d : sc_mul(slab[(size_t)tp * sstride + j], d);
                 slab[(size_t)tp * sstride + j] = v;
                 prow[j] = v;
+                if (j == k + 1) fn[tp] = v;
             }
             if (threadIdx.x == 0) used[tp] = 1;
         }
@@ -295,14 +308,17 @@ __global__ void __launch_bounds__(kThreads) k_pivot_cluster(LevelView<T> L0, Box
             const S* rp = cl.map_shared_rank(prow, owner);
             for (int j = threadIdx.x; j < s; j += blockDim.x) prow[j] = rp[j];
         }
-        for (int tl = threadIdx.x; tl < rows_loc; tl += blockDim.x) fcol[tl] = slab[(size_t)tl * sstride + k];
         __syncthreads();
         const S d = prow[k];
         for (int tl = tl0, j = j0; tl < rows_loc;) {
             if (!(c == owner && tl == tp)) {
-                const S f = fcol[tl];
+                const S f = fc[tl];
                 if (j == k) slab[(size_t)tl * sstride + k] = sc_neg(sc_mul(f, d));
-                else slab[(size_t)tl * sstride + j] = sc_fms(slab[(size_t)tl * sstride + j], f, prow[j]);
+                else {
+                    const S v = sc_fms(slab[(size_t)tl * sstride + j], f, prow[j]);
+                    slab[(size_t)tl * sstride + j] = v;
+                    if (j == k + 1) fn[tl] = v;
+                }
             }
             tl += dr;
             j += dc;
@@ -1147,7 +1163,7 @@ void launch_factor_colour(const LevelView<T>& L, const int* boxes, int nboxes, i
     int C = 1, slab_global = 0;
     auto cl_bytes = [&](int cc, int glob) {
         const size_t rows = (size_t)(smax + cc - 1) / cc;
-        return (glob ? 0 : rows * smax * sizeof(double)) + (smax + rows) * sizeof(double) + (smax + rows) * sizeof(int);
+        return (glob ? 0 : rows * smax * sizeof(double)) + (smax + 2 * rows) * sizeof(double) + (smax + rows) * sizeof(int);
     };
     if (smax >= 96) {
         // few boxes: spread each over several SMs (up to 16 at the upper levels); many boxes: keep
