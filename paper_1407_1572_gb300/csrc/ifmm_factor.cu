@@ -1939,8 +1939,8 @@ void launch_forward_colour(const LevelView<T>& L, const int* boxes, int nboxes, 
             return;
         }
     }
-    const int tw = ReplayTile<T, 0>::M;   // output tile of the CTA GEMM
-    const int tr = (nrhs + tw - 1) / tw;
+    const int tw = ReplayTile<T, 0>::M, th = ReplayTile<T, 0>::N;   // output tile of the CTA GEMM
+    const int tr = (nrhs + th - 1) / th;
     const int z1 = std::max(1, std::min(((smax + tw - 1) / tw) * tr, (608 + nboxes - 1) / nboxes));
     const int nn = L.nd - 1;   // neighbours other than e
     const int z2 = std::max(1, std::min(((L.nmax + tw - 1) / tw) * tr, (608 + nboxes * nn - 1) / (nboxes * nn)));
