@@ -738,10 +738,15 @@ __global__ void __launch_bounds__(kThreads) k_compress(LevelView<T> L0, BoxList<
     E* Re = reinterpret_cast<E*>(R);
     E* ue = reinterpret_cast<E*>(nrm2 + (C > 1 ? mloc : m));   // u in E (nq entries)
     if constexpr (std::is_same<E, dfl>::value) {
-        // R to double-float in place (the split works on the bit pattern: no FP64 arithmetic)
-        for (int t = threadIdx.x; t < nq * mloc; t += blockDim.x) {
-            const int i = t / mloc, j = j0 + (t - i * mloc);
-            Re[(size_t)i * m + j] = dfl((double)R[(size_t)i * m + j]);
+        // R to double-float in place (the split works on the bit pattern: no FP64 arithmetic); a
+        // single block converts whole rows without an index division per element
+        if (mloc == m) {
+            for (int t = threadIdx.x; t < nq * m; t += blockDim.x) Re[t] = dfl((double)R[t]);
+        } else {
+            for (int t = threadIdx.x; t < nq * mloc; t += blockDim.x) {
+                const int i = t / mloc, j = j0 + (t - i * mloc);
+                Re[(size_t)i * m + j] = dfl((double)R[(size_t)i * m + j]);
+            }
         }
         __syncthreads();
     }
