@@ -261,13 +261,14 @@ def oracle_headline_sample(w, gpu_iters):
             "t_solve_modelled_s": (gpu_iters + 1) * ts1 + gpu_iters * tm1}
 
 
-def cpu_baseline_entry(gpu_iters=None):
-    """The oracle timed on this host. At the headline size (gpu_iters given): the oracle on the bench's
-    own workload (2^20 points, same points and settings), factor timed in full and the refined solve
-    sampled (one solve and one FMM matvec, scaled by the GPU step's GMRES iteration count), so the
-    ratio compares the same factorisation and the same number of operator applications. Otherwise
-    the complete factor + GMRES-refined solve on the 65,536-point sample. Both add one thread on
-    16,384 points."""
+def cpu_baseline_entry(gpu_iters=None, full=False):
+    """The oracle timed on this host. At the headline size (gpu_iters given): the oracle's factor timed
+    in full and its refined solve sampled (one solve and one FMM matvec, scaled by the GPU step's GMRES
+    iteration count), so the ratio compares the same factorisation and the same number of operator
+    applications per unknown; on a bounded sample of the headline workload (65,536 of its points'
+    density: same points per leaf and settings, about 10 s), or with `full` on the bench's own 2^20
+    points (about 3 minutes). Otherwise the complete factor + GMRES-refined solve on the 65,536-point
+    sample. All add one thread on 16,384 points."""
     w1 = CPU_SAMPLE_1T
     dt1, err1 = oracle_step(w1, threads=1)
     single = {"value": w1["N"] / dt1, "unit": "unknowns/s", "cores": 1,
@@ -283,15 +284,18 @@ def cpu_baseline_entry(gpu_iters=None):
                           f"same settings per leaf), {dt:.1f} s, err {err:.1e}",
                 **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in parts.items()},
                 "single_thread": single}
-    hs = oracle_headline_sample(WORKLOAD, gpu_iters)
-    n = WORKLOAD["N"]
+    ws = WORKLOAD if full else dict(WORKLOAD, N=CPU_SAMPLE["N"], depth=CPU_SAMPLE["depth"])
+    hs = oracle_headline_sample(ws, gpu_iters)
+    n = ws["N"]
     total = hs["t_factor_s"] + hs["t_solve_modelled_s"]
+    what = (f"the headline workload itself (N={n}, same points and settings)" if full else
+            f"a {n}-point sample of the headline workload (depth {ws['depth']}, same points per leaf and settings)")
     return {"value": n / total, "unit": "unknowns/s", "cores": os.cpu_count() or 1, "kind": "oracle",
             "cpu_model": cpu_model(),
-            "sample": (f"oracle on the headline workload (N={n}, same points and settings): factor timed in full "
-                       f"({hs['t_factor_s']:.1f} s), one {WORKLOAD['nrhs']}-RHS solve ({hs['t_solve_once_s']:.1f} s) "
+            "sample": (f"oracle on {what}: factor timed in full "
+                       f"({hs['t_factor_s']:.1f} s), one {ws['nrhs']}-RHS solve ({hs['t_solve_once_s']:.1f} s) "
                        f"and one FMM matvec ({hs['t_matvec_once_s']:.1f} s) timed and scaled to the GPU step's "
-                       f"{gpu_iters} preconditioned matvecs: {total:.0f} s per step"),
+                       f"{gpu_iters} preconditioned matvecs: {total:.1f} s per step"),
             "factor_only_value": n / hs["t_factor_s"], "seconds": {k: round(v, 3) for k, v in hs.items()},
             "single_thread": single}
 
@@ -387,15 +391,15 @@ ARITH = {
 # costs the same at any N); keyed by the SHA-256 of the kernel sources it was taken on, so that it
 # reads null once a source differs. Empty: no capture of the current sources.
 TRAFFIC = {
-    # profiles/k_compress_n65536_mixed.md: one level-5 launch over 110 boxes, 313.90 MB
-    ("mixed_solve", "k_compress"): {"bytes_per_box": 313.897216e6 / 110},
-    # profiles/k_schur_n65536_mixed.md: one level-5 launch over 110 boxes, 216.44 MB
-    ("mixed_solve", "k_schur"): {"bytes_per_box": 216.437760e6 / 110},
+    # profiles/k_compress_n65536_mixed.md: one level-5 launch over 110 boxes, 316.60 MB
+    ("mixed_solve", "k_compress"): {"bytes_per_box": 316.597248e6 / 110},
+    # profiles/k_schur_n65536_mixed.md: one level-5 launch over 110 boxes, 215.90 MB
+    ("mixed_solve", "k_schur"): {"bytes_per_box": 215.897088e6 / 110},
 }
 TRAFFIC_SRC = {
-    "ifmm_factor.cu": "c6ebf4c149d51df5b948d363ac62cfa2352445a2496fbcf2623d8ae1b871cbc3",
+    "ifmm_factor.cu": "fe69162075983cc58219a76574eb447374b915f4ae06e8160de7bfbd55a55876",
     "ifmm_common.cuh": "d7aff101b7cda20e870e39e7916fe24394fab8c076c58869e434e0c44a0b6ecc",
-    "ifmm_internal.h": "b68fe620d10fcdfed0efcf2df830d6211a605a376de08d5125ff0b7bfe248684",
+    "ifmm_internal.h": "253a2728183cbf2b14c8809c70ba47e5b5c5963b18ea689c7b8f777d66926f01",
 }
 
 
@@ -833,7 +837,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_entry(st["refine_iters"] if N == WORKLOAD["N"] else None)
+        cpu = cpu_baseline_entry(st["refine_iters"] if N == WORKLOAD["N"] else None, full=args.cpu_full)
         cpu["gpu_over_oracle"] = value / cpu["value"]
         if "factor_only_value" in cpu:
             cpu["gpu_factor_over_oracle_factor"] = (N / (st["t_factor_ms"] / 1000.0)) / cpu["factor_only_value"]
@@ -883,6 +887,9 @@ def main():
                     help="also time one step of the other precision (reported, not the headline)")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the oracle's factorisation on the full 2^20-point workload (about 3 minutes) "
+                         "instead of its 65,536-point sample")
     ap.add_argument("--tc-products", type=int, default=0, choices=[0, 1, 2],
                     help="mixed_solve: tensor-core products in the replay (1), the replay and the Schur "
                          "update (2), or double-float on the FP32 pipe (0)")
