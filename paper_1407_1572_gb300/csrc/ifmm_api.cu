@@ -1260,6 +1260,9 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
     CKS(workspace(h, 61, sizeof(double) * vec, &pu));
     CKS(workspace(h, 62, sizeof(double) * vec, &pr));
     CKS(workspace(h, 63, sizeof(double) * (size_t)(m + 2) * nrhs * 2, &pd));
+    void* pp = nullptr;   // per-block partial sums of the reductions (summed in a fixed order)
+    CKS(workspace(h, 64, sizeof(double) * reduction_scratch_doubles(N, nrhs, m + 1), &pp));
+    double* part = (double*)pp;
     double* V = (double*)pV;
     double* u = (double*)pu;
     double* r = (double*)pr;
@@ -1286,11 +1289,11 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
             if (fresh64) CKS(matvec_impl(h, x, ld, u, N, nrhs));
             else CKS(matvec_dfl_impl(h, x, ld, u, N, nrhs));
             CK(cudaMemsetAsync(dv, 0, sizeof(double) * 2 * nrhs, h->st));
-            launch_residual(b, u, r, N, nrhs, ld, dv, h->st);
+            launch_residual(b, u, r, N, nrhs, ld, dv, part, h->st);
             CKS(solve_once<T>(h, r, N, V, N, nrhs));
         }
         CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
-        launch_colnorm2(V, N, N, nrhs, dv, h->st);
+        launch_colnorm2(V, N, N, nrhs, dv, part, h->st);
         CKS(fetch(1));
         est = 0.0;
         for (int c = 0; c < nrhs; ++c) {
@@ -1321,7 +1324,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
             CKS(solve_once<T>(h, u, N, Vn, N, nrhs));
             for (int pass = 0; pass < 2; ++pass) {
                 CK(cudaMemsetAsync(dv, 0, sizeof(double) * (size_t)(j + 1) * nrhs, h->st));
-                launch_krylov_dots(V, j + 1, Vn, N, nrhs, dv, h->st);
+                launch_krylov_dots(V, j + 1, Vn, N, nrhs, dv, part, h->st);
                 CKS(fetch(j + 1));
                 for (int i = 0; i <= j; ++i)
                     for (int c = 0; c < nrhs; ++c) {
@@ -1332,7 +1335,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
                 launch_krylov_lincomb(V, j + 1, dv, Vn, N, N, nrhs, h->st);
             }
             CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
-            launch_colnorm2(Vn, N, N, nrhs, dv, h->st);
+            launch_colnorm2(Vn, N, N, nrhs, dv, part, h->st);
             CKS(fetch(1));
             est = 0.0;
             for (int c = 0; c < nrhs; ++c) {
@@ -1375,7 +1378,7 @@ ifmm_status gmres_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         CK(cudaMemcpyAsync(dv, y.data(), sizeof(double) * (size_t)k * nrhs, cudaMemcpyHostToDevice, h->st));
         launch_krylov_lincomb(V, k, dv, x, ld, N, nrhs, h->st);
         CK(cudaMemsetAsync(dv, 0, sizeof(double) * nrhs, h->st));
-        launch_colnorm2(x, ld, N, nrhs, dv, h->st);
+        launch_colnorm2(x, ld, N, nrhs, dv, part, h->st);
         CKS(fetch(1));
         for (int c = 0; c < nrhs; ++c) xn[c] = std::sqrt(hv[c]);
         if (it >= h->prm.refine_maxit) break;
@@ -1403,6 +1406,9 @@ ifmm_status solve_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
     CKS(workspace(h, 31, sizeof(double) * (size_t)N * nrhs, &pd));
     CKS(workspace(h, 32, sizeof(double) * (size_t)N * nrhs, &pa));
     CKS(workspace(h, 33, sizeof(double) * 2 * (size_t)nrhs, &pn));
+    void* pp = nullptr;   // per-block partial sums of the norms (summed in a fixed order)
+    CKS(workspace(h, 64, sizeof(double) * reduction_scratch_doubles(N, nrhs, 1), &pp));
+    double* part = (double*)pp;
     double* r = (double*)pr;
     double* d = (double*)pd;
     double* ax = (double*)pa;
@@ -1416,7 +1422,7 @@ ifmm_status solve_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
     for (;;) {
         CKS(solve_once<T>(h, rhs, ldr, d, N, nrhs));
         CK(cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * nrhs, h->st));
-        launch_axpy_norms(x, d, N, nrhs, ld, nrm, h->st);
+        launch_axpy_norms(x, d, N, nrhs, ld, nrm, part, h->st);
         CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         ++it;
@@ -1425,7 +1431,7 @@ ifmm_status solve_impl(ifmm_handle* h, const double* b, double* x, int nrhs, int
         if (upd <= h->prm.refine_tol || it >= h->prm.refine_maxit) break;
         CKS(matvec_impl(h, x, ld, ax, N, nrhs));
         CK(cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * nrhs, h->st));
-        launch_residual(b, ax, r, N, nrhs, ld, nrm, h->st);
+        launch_residual(b, ax, r, N, nrhs, ld, nrm, part, h->st);
         CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         double res = 0.0;

@@ -796,8 +796,28 @@ IFMM_MV_INSTANTIATE(double)
 IFMM_MV_INSTANTIATE(dfl)
 #undef IFMM_MV_INSTANTIATE
 
+// The refinement's reductions over N run in two steps so that they give the same bits run after
+// run: each block writes its partial sum to part[block * nout + output] (no atomics), then
+// k_sum_partials adds the partials of every output in block order.
+__global__ void k_sum_partials(const double* part, int nblk, int nout, double* out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    double s = 0.0;
+    for (int x = 0; x < nblk; ++x) s += part[(size_t)x * nout + o];
+    out[o] += s;
+}
+static void sum_partials(const double* part, int nblk, int nout, double* out, cudaStream_t st) {
+    k_sum_partials<<<(nout + 255) / 256, 256, 0, st>>>(part, nblk, nout, out);
+    count_launches(1);
+}
+static int vec_blocks(int64_t N) { return (int)std::min<int64_t>((N + 255) / 256, 1024); }
+static int dot_blocks(int64_t N) { return (int)((N + 4095) / 4096); }
+size_t reduction_scratch_doubles(int64_t N, int nrhs, int cnt) {
+    return std::max((size_t)dot_blocks(N) * (size_t)std::max(cnt, 1), (size_t)vec_blocks(N) * 2) * (size_t)nrhs;
+}
+
 // x += d (d with leading dimension N); nrm[2j] += ||d_j||^2, nrm[2j+1] += ||x_j||^2 (x after the update)
-__global__ void k_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm) {
+__global__ void k_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* part) {
     __shared__ double red[32];
     const int j = blockIdx.y;
     double sd = 0.0, sx = 0.0;
@@ -809,17 +829,19 @@ __global__ void k_axpy_norms(double* x, const double* d, int64_t N, int nrhs, in
         sx += xv * xv;
     }
     sd = block_sum(sd, red);
-    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j], sd);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 2 * nrhs + 2 * j] = sd;
     sx = block_sum(sx, red);
-    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j + 1], sx);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 2 * nrhs + 2 * j + 1] = sx;
 }
-void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm, cudaStream_t st) {
-    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
-    k_axpy_norms<<<dim3(gx, nrhs), 256, 0, st>>>(x, d, N, nrhs, ld, nrm); count_launches(1);
+void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm, double* part,
+                       cudaStream_t st) {
+    const int gx = vec_blocks(N);
+    k_axpy_norms<<<dim3(gx, nrhs), 256, 0, st>>>(x, d, N, nrhs, ld, part); count_launches(1);
+    sum_partials(part, gx, 2 * nrhs, nrm, st);
 }
 
 // r = b - ax; nrm[2j] += ||r_j||^2, nrm[2j+1] += ||b_j||^2
-__global__ void k_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld, double* nrm) {
+__global__ void k_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld, double* part) {
     __shared__ double red[32];
     const int j = blockIdx.y;
     double sr = 0.0, sb = 0.0;
@@ -831,14 +853,15 @@ __global__ void k_residual(const double* b, const double* ax, double* r, int64_t
         sb += bv * bv;
     }
     sr = block_sum(sr, red);
-    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j], sr);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 2 * nrhs + 2 * j] = sr;
     sb = block_sum(sb, red);
-    if (threadIdx.x == 0) atomicAdd(&nrm[2 * j + 1], sb);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 2 * nrhs + 2 * j + 1] = sb;
 }
 void launch_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld, double* nrm,
-                     cudaStream_t st) {
-    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
-    k_residual<<<dim3(gx, nrhs), 256, 0, st>>>(b, ax, r, N, nrhs, ld, nrm); count_launches(1);
+                     double* part, cudaStream_t st) {
+    const int gx = vec_blocks(N);
+    k_residual<<<dim3(gx, nrhs), 256, 0, st>>>(b, ax, r, N, nrhs, ld, part); count_launches(1);
+    sum_partials(part, gx, 2 * nrhs, nrm, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -846,7 +869,7 @@ void launch_residual(const double* b, const double* ax, double* r, int64_t N, in
 // ---------------------------------------------------------------------------------------------
 // out[i * nrhs + c] += sum_n V_i[n, c] w[n, c] for i < cnt (V_i = V + i * N * nrhs)
 __global__ void __launch_bounds__(256) k_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs,
-                                                     double* out) {
+                                                     double* part) {
     __shared__ double red[32];
     constexpr int PER = 16;
     const int c = blockIdx.y;
@@ -866,13 +889,15 @@ __global__ void __launch_bounds__(256) k_krylov_dots(const double* V, int cnt, c
             if (n < N) s += v[n] * wv[t];
         }
         s = block_sum(s, red);
-        if (threadIdx.x == 0) atomicAdd(&out[i * nrhs + c], s);
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * cnt * nrhs + (size_t)i * nrhs + c] = s;
     }
 }
-void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out,
+void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out, double* part,
                         cudaStream_t st) {
-    k_krylov_dots<<<dim3((unsigned)((N + 4095) / 4096), nrhs), 256, 0, st>>>(V, cnt, w, N, nrhs, out);
+    const int gx = dot_blocks(N);
+    k_krylov_dots<<<dim3((unsigned)gx, nrhs), 256, 0, st>>>(V, cnt, w, N, nrhs, part);
     count_launches(1);
+    sum_partials(part, gx, cnt * nrhs, out, st);
 }
 
 // y[n + c * ldy] += sum_i coef[i * nrhs + c] V_i[n, c]
@@ -893,7 +918,7 @@ void launch_krylov_lincomb(const double* V, int cnt, const double* coef, double*
 }
 
 // out[c] += ||y[:, c]||^2 ; then optionally y[:, c] *= scale[c]
-__global__ void k_colnorm2(const double* y, int64_t ldy, int64_t N, double* out) {
+__global__ void k_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* part) {
     __shared__ double red[32];
     const int c = blockIdx.y;
     double s = 0.0;
@@ -902,12 +927,13 @@ __global__ void k_colnorm2(const double* y, int64_t ldy, int64_t N, double* out)
         s += v * v;
     }
     s = block_sum(s, red);
-    if (threadIdx.x == 0) atomicAdd(&out[c], s);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * nrhs + c] = s;
 }
-void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, cudaStream_t st) {
-    int gx = (int)std::min<int64_t>((N + 255) / 256, 1024);
-    k_colnorm2<<<dim3(gx, nrhs), 256, 0, st>>>(y, ldy, N, out);
+void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, double* part, cudaStream_t st) {
+    const int gx = vec_blocks(N);
+    k_colnorm2<<<dim3(gx, nrhs), 256, 0, st>>>(y, ldy, N, nrhs, part);
     count_launches(1);
+    sum_partials(part, gx, nrhs, out, st);
 }
 
 __global__ void k_colscale(double* y, int64_t ldy, int64_t N, const double* scale) {

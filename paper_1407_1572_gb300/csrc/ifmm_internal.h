@@ -282,18 +282,20 @@ void launch_mv_permute_out(const T* yt, int64_t N, int nrhs, const int64_t* perm
                            cudaStream_t st);
 // b = a split into double-float pairs, n elements
 void launch_split_dfl(const double* a, dfl* b, int64_t n, cudaStream_t st);
-// refinement helpers
-void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm,
+// refinement helpers; their sums over N are reduced in a fixed order through `part`, a device
+// scratch of reduction_scratch_doubles(N, nrhs, cnt) doubles (cnt: the most dot products of one call)
+size_t reduction_scratch_doubles(int64_t N, int nrhs, int cnt);
+void launch_axpy_norms(double* x, const double* d, int64_t N, int nrhs, int64_t ld, double* nrm, double* part,
                        cudaStream_t st);
 void launch_residual(const double* b, const double* ax, double* r, int64_t N, int nrhs, int64_t ld,
-                     double* nrm, cudaStream_t st);
+                     double* nrm, double* part, cudaStream_t st);
 
 // Krylov vectors (FP64, column-major N x nrhs, basis vector i at V + i N nrhs)
-void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out,
+void launch_krylov_dots(const double* V, int cnt, const double* w, int64_t N, int nrhs, double* out, double* part,
                         cudaStream_t st);
 void launch_krylov_lincomb(const double* V, int cnt, const double* coef, double* y, int64_t ldy, int64_t N, int nrhs,
                            cudaStream_t st);
-void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, cudaStream_t st);
+void launch_colnorm2(const double* y, int64_t ldy, int64_t N, int nrhs, double* out, double* part, cudaStream_t st);
 void launch_colscale(double* y, int64_t ldy, int64_t N, int nrhs, const double* scale, cudaStream_t st);
 
 }  // namespace ifmm
