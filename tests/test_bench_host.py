@@ -170,3 +170,19 @@ def test_batched_results_combine_over_two_gloo_ranks():
     for _, (t, tf, ts, err, dmin, dmax) in out:
         assert (t, tf, ts, dmin, dmax) == (4.5, 2.0, 2.5, 3.0, 7.0)   # slowest rank: 2.0 + 2.5
         assert math.isclose(err, 1e-7)
+
+
+def test_roofline_reports_every_factor_kernel_against_its_own_peak():
+    rf = bench.roofline(_stats(), "mixed_solve", PEAKS, "measured", PIPES)
+    fk = rf["factor_kernels"]
+    assert list(fk) == ["k_pivot", "k_panel", "k_schur", "k_compress", "k_redirect"]
+    st = _stats()
+    for i, (name, k) in enumerate(fk.items()):
+        t = st["kernel_ms"][i] / 54 / 1000.0
+        assert math.isclose(k["achieved"], st["kernel_flops"][i] / 54 / t / 1e12, rel_tol=1e-12)
+        assert math.isclose(k["frac"], k["achieved"] / k["peak"], rel_tol=1e-12)
+    # pivots in FP64, the products in double-float, the compression on its blend
+    assert fk["k_pivot"]["peak"] == PIPES["fp64"]
+    assert fk["k_panel"]["peak"] == PIPES["dfl"] and fk["k_redirect"]["peak"] == PIPES["dfl"]
+    assert PIPES["fp64"] < fk["k_compress"]["peak"] < PIPES["dfl"]
+    assert math.isclose(sum(k["share_of_factor_kernels"] for k in fk.values()), 1.0)
